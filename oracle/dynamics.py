@@ -1,0 +1,212 @@
+"""Oracle for the extended-variable loop: mirror map, OPES bias, Langevin
+middle-scheme steps with constraints, and the Philox counter RNG.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Plain numpy float64,
+written from the paper's equations and the published definitions cited on
+each function.
+"""
+import math
+
+import numpy as np
+
+KB = 0.0083144626  # kJ mol^-1 K^-1
+
+# ------------------------------------------------------------------ Philox
+# Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+# as 1, 2, 3", SC 2011): 10 rounds of two 32x32->64 multiplies with the
+# published multipliers and Weyl key increments.
+_M0, _M1 = 0xD2511F53, 0xCD9E8D57
+_W0, _W1 = 0x9E3779B9, 0xBB67AE85
+_MASK = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    c = [int(x) & _MASK for x in ctr]
+    k0, k1 = int(key[0]) & _MASK, int(key[1]) & _MASK
+    for _ in range(10):
+        p0 = _M0 * c[0]
+        p1 = _M1 * c[2]
+        hi0, lo0 = p0 >> 32, p0 & _MASK
+        hi1, lo1 = p1 >> 32, p1 & _MASK
+        c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+        k0 = (k0 + _W0) & _MASK
+        k1 = (k1 + _W1) & _MASK
+    return c
+
+
+def uniforms(ctr, key):
+    """Four uniforms in (0, 1): (x + 0.5) / 2^32."""
+    return [(x + 0.5) / 4294967296.0 for x in philox4x32_10(ctr, key)]
+
+
+def normals3(ctr, key):
+    """Three standard normals by the Box-Muller transform of the four uniforms
+    (u0, u1) -> (n0, n1), (u2, u3) -> n2."""
+    u = uniforms(ctr, key)
+    r0 = math.sqrt(-2.0 * math.log(u[0]))
+    r1 = math.sqrt(-2.0 * math.log(u[2]))
+    return (r0 * math.cos(2 * math.pi * u[1]), r0 * math.sin(2 * math.pi * u[1]),
+            r1 * math.cos(2 * math.pi * u[3]))
+
+
+def seed_key(seed):
+    return (seed & _MASK, (seed >> 32) & _MASK)
+
+
+def atom_normals(n, step, seed):
+    """Normals for atoms 0..n-1 at a step: counter (i, step_lo, step_hi, 0)."""
+    key = seed_key(seed)
+    out = np.empty((n, 3))
+    for i in range(n):
+        out[i] = normals3((i, step & _MASK, step >> 32, 0), key)
+    return out
+
+
+def theta_normal(step, seed):
+    """Normal for the alchemical variable: counter (0, step_lo, step_hi, 1)."""
+    return normals3((0, step & _MASK, step >> 32, 1), seed_key(seed))[0]
+
+
+# -------------------------------------------------------------- mirror map
+
+def theta_to_lambda(theta):
+    """Eq. 3: lambda = theta on [0, 1], 2 - theta on (1, 2]; theta is wrapped
+    into [0, 2) first.  Returns (lambda, dlambda/dtheta)."""
+    th = theta - 2.0 * math.floor(theta / 2.0)
+    if th <= 1.0:
+        return th, 1.0
+    return 2.0 - th, -1.0
+
+
+# -------------------------------------------------------------------- OPES
+
+class Opes:
+    """One OPES bias on theta (Eq. 11-13).
+
+    kind = "std" (OPES-Standard: nu = 1 - 1/gamma, kernel weight exp(beta V))
+    or "exp" (OPES-Explore: nu = gamma - 1, unit weights).
+    rho_hat(theta) = sum_k w_k G_k(theta) / sum_k w_k with periodic Gaussian
+    kernels of width sigma on theta (period 2); rho_bar is the mean of rho_hat
+    over the kernel centres; V = (nu/beta) ln(rho_hat/rho_bar + eps), and V = 0
+    before the first deposit.
+    """
+
+    def __init__(self, kind, dE, sigma, T):
+        self.kind = kind
+        self.beta = 1.0 / (KB * T)
+        self.gamma = self.beta * dE
+        self.nu = (1.0 - 1.0 / self.gamma) if kind == "std" else (self.gamma - 1.0)
+        self.eps = math.exp(-self.beta * dE / self.nu)
+        self.sigma = sigma
+        self.c = []
+        self.w = []
+        self.rho_bar = 0.0
+
+    @staticmethod
+    def _pdiff(a, b):
+        d = a - b
+        return d - 2.0 * math.floor((d + 1.0) / 2.0)
+
+    def _rho(self, th):
+        if not self.c:
+            return 0.0, 0.0
+        s = ds = 0.0
+        for ck, wk in zip(self.c, self.w):
+            d = self._pdiff(th, ck)
+            g = math.exp(-0.5 * d * d / (self.sigma * self.sigma))
+            s += wk * g
+            ds += wk * g * (-d / (self.sigma * self.sigma))
+        W = sum(self.w)
+        return s / W, ds / W
+
+    def bias(self, th):
+        """(V(theta), dV/dtheta)."""
+        if not self.c:
+            return 0.0, 0.0
+        r, dr = self._rho(th)
+        a = r / self.rho_bar + self.eps
+        return self.nu / self.beta * math.log(a), self.nu / self.beta * (dr / self.rho_bar) / a
+
+    def deposit(self, th):
+        w = math.exp(self.beta * self.bias(th)[0]) if self.kind == "std" else 1.0
+        self.c.append(th - 2.0 * math.floor(th / 2.0))
+        self.w.append(w)
+        self.rho_bar = sum(self._rho(ck)[0] for ck in self.c) / len(self.c)
+
+
+# -------------------------------------------------------------- constraints
+
+def shake(x_new, x_ref, pairs, lengths, w, box, tol=1e-13, max_iter=100000):
+    """Iterate SHAKE to convergence: move x_new along the reference bond
+    vectors (inverse-mass weighted) until every |r_ij| equals its length."""
+    x = x_new.copy()
+    for _ in range(max_iter):
+        worst = 0.0
+        for (i, j), d0 in zip(pairs, lengths):
+            r = x[j] - x[i]
+            r -= box * np.round(r / box)
+            r0 = x_ref[j] - x_ref[i]
+            r0 -= box * np.round(r0 / box)
+            diff = r @ r - d0 * d0
+            worst = max(worst, abs(diff) / (d0 * d0))
+            wsum = w[i] + w[j]
+            if wsum == 0.0:
+                continue
+            g = diff / (2.0 * wsum * (r @ r0))
+            x[i] += g * w[i] * r0
+            x[j] -= g * w[j] * r0
+        if worst < tol:
+            return x
+    raise RuntimeError("SHAKE did not converge")
+
+
+def constraint_list(sysd):
+    """All distance constraints: the three of each rigid water and the X-H list."""
+    pairs, lens = [], []
+    from_geo = {}
+    r_oh = 0.09572
+    ang = math.radians(104.52)
+    r_hh = 2.0 * r_oh * math.sin(ang / 2.0)
+    for o, h1, h2 in np.asarray(sysd.get("waters", np.zeros((0, 3), int))):
+        pairs += [(o, h1), (o, h2), (h1, h2)]
+        lens += [r_oh, r_oh, r_hh]
+    for (i, j), d0 in zip(np.asarray(sysd.get("constraints", np.zeros((0, 2), int))),
+                          np.asarray(sysd.get("constraint_len", np.zeros(0)))):
+        pairs.append((int(i), int(j)))
+        lens.append(float(d0))
+    return pairs, lens
+
+
+# ---------------------------------------------------------------- stepping
+
+def langevin_middle_step(x, v, F, mass, dt, gamma, T, normals, box, pairs, lengths):
+    """One step of the Langevin middle scheme (Zhang et al. 2019, cited in
+    Section 2.6): kick v += dt F/m; half drift; Ornstein-Uhlenbeck
+    v = a v + sqrt(kT (1 - a^2)/m) R, a = exp(-gamma dt); half drift;
+    constrain the new positions; v = (x_new - x)/dt.  Atoms of mass 0 stay
+    fixed."""
+    w = np.where(mass > 0, 1.0 / np.where(mass > 0, mass, 1.0), 0.0)
+    a = math.exp(-gamma * dt)
+    v = v + dt * w[:, None] * F
+    xn = x + 0.5 * dt * v
+    sd = np.sqrt(KB * T * (1.0 - a * a) * w)
+    v = a * v + sd[:, None] * normals
+    xn = xn + 0.5 * dt * v
+    if pairs:
+        xn = shake(xn, x, pairs, lengths, w, box)
+    v = (xn - x) / dt
+    v[w == 0.0] = 0.0
+    xn[w == 0.0] = x[w == 0.0]
+    return xn, v
+
+
+def theta_step(theta, p_theta, dUdl, dlam_dtheta, dV, m, dt, gamma, T, normal):
+    """The same middle scheme for theta with momentum p_theta = m dtheta/dt and
+    generalized force -(dlambda/dtheta) dU/dlambda - dV_OPES/dtheta."""
+    f = -dlam_dtheta * dUdl - dV
+    vt = p_theta / m + dt * f / m
+    th = theta + 0.5 * dt * vt
+    a = math.exp(-gamma * dt)
+    vt = a * vt + math.sqrt(KB * T * (1.0 - a * a) / m) * normal
+    th = th + 0.5 * dt * vt
+    return th - 2.0 * math.floor(th / 2.0), m * vt
