@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the lambda-dynamics step (alchemical nonbonded evaluation +
+Langevin/constraints + theta/OPES) on the octanol solvation box.
+
+One step = one pass of the whole hot path: pair kernel, PME (spread, FFT,
+convolution, inverse FFT, gather), exclusion/1-4 and bonded terms, the
+constrained Langevin middle-scheme update of every atom, the theta/dual-OPES
+update and (when needed) the device-side neighbour-list rebuild, replayed as
+one captured CUDA graph.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 oracle on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) on 1 B300"
+# algorithmic FP32 operations per interacting pair (counting convention in the
+# design notes: pair vector 3, r^2 5, 1/r and r 3, Coulomb 8 + erfc/exp 12,
+# LJ 15, switch 8, force vector and Newton's third law 9, energy 2, class 2)
+FLOPS_PER_PAIR = 67
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="octanol", choices=["octanol", "water", "c0"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--profile-case", action="store_true",
+                   help="build the workload, run 3 staged evaluations and exit (a small case for ncu)")
+    return p.parse_args()
+
+
+def make_workload(name, rank):
+    from paper_2608_12691_b300 import systems as S
+    if name == "octanol":
+        d = S.make_c1(seed=2609 + 1000 * rank)
+        desc = ("octanol solvation box: 500 27-atom octanol-like chains + 20-atom rigid solute, "
+                "13,520 atoms, 4.8 nm, r_c 1.0 nm, PME 48^3, octanol masses x0.1, dual OPES on lambda")
+    elif name == "water":
+        d = S.make_c2(seed=2610 + 1000 * rank)
+        desc = ("water box: 4,000 rigid waters + 20-atom rigid solute, 12,020 atoms, 4.93 nm, "
+                "r_c 1.0 nm, PME 48^3, lambda mass 20 amu nm^2, OPES every 500 steps")
+    else:
+        d = S.make_c0(seed=2608 + 1000 * rank)
+        desc = "12-atom solute + 216 waters, 660 atoms, 1.86 nm, r_c 0.9 nm, PME 16^3"
+    d = dict(d)
+    d.setdefault("lambda_mass", 20.0)
+    d.setdefault("opes_stride", 500)
+    d.setdefault("opes_dE_std", 30.0 * 4.184)
+    d.setdefault("opes_dE_exp", 5.0 * 4.184)
+    return d, desc
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(d, dt_ps):
+    """The oracle as it stands (level 2: real-space pairs + naive-DFT SPME, FP64)
+    timed on the host cores on one full force/energy evaluation of the same
+    system; converted to the step's ns/day."""
+    from oracle import reference as R
+    t0 = time.perf_counter()
+    E, F0, Fuv, Fs = R.nonbonded(d, level=2)
+    R.bonded(d)
+    t = time.perf_counter() - t0
+    return {"value": dt_ps * 1e-3 * 86400.0 / t, "unit": "ns/day", "cores": R.num_threads(),
+            "kind": "oracle",
+            "sample": f"one full level-2 oracle force+energy evaluation of the same {len(d['charge'])}-atom "
+                      f"system ({t:.2f} s); integration not included",
+            "seconds_per_eval": t, "pair_interactions_per_s": E["n_pairs"] / t}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    d, desc = make_workload(args.workload, 0)
+    dt_ps = float(d["dt"])
+    times = []
+    npairs = 0
+    for i in range(args.warmup + args.steps if args.steps <= 3 else min(args.steps, 3)):
+        c = cpu_baseline(d, dt_ps)
+        times.append(c["seconds_per_eval"])
+        npairs = c["pair_interactions_per_s"] * c["seconds_per_eval"]
+    t = statistics.median(times)
+    v = dt_ps * 1e-3 * 86400.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ns/day", "n_gpus": args.gpus,
+            "steps": len(times), "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "atoms": len(d["charge"]), "dt_fs": dt_ps * 1e3},
+            "pair_interactions_per_s": npairs / t,
+            "cpu_baseline": {"value": v, "unit": "ns/day", "cores": c["cores"], "kind": "oracle",
+                             "sample": c["sample"]},
+            "e2e": {"value": v, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def equilibrate(g, d, stream):
+    """Untimed equilibration from the packed lattice start: short phases of
+    small time step and high friction, then the production parameters."""
+    dt = float(d["dt"])
+    for dt_eq, fric, n in ((dt * 0.05, 100.0, 200), (dt * 0.25, 50.0, 200), (dt * 0.5, 20.0, 200)):
+        g.set_integrator(dt_eq, fric, float(d["temperature"]))
+        g.step(n, stream)
+    g.set_integrator(dt, float(d["friction"]), float(d["temperature"]))
+    g.get_state()
+
+
+def time_steps(g, K, stream, flush):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for i in range(K):
+        flush.zero_()                    # L2 flush outside the timed step
+        ev[i][0].record(stream)
+        g.step(1, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2608_12691_b300 import lfe
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    d, desc = make_workload(args.workload, rank)
+    prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
+    dt_ps = float(d["dt"])
+    g = lfe.System(d, precision=prec, seed=2608 + rank)
+    terms0, _ = g.eval(d["lam"])
+    n_pairs = terms0["n_pairs"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    equilibrate(g, d, stream)
+    g.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    _, _, ext0 = g.get_state()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    ms = time_steps(g, args.steps, stream, flush)
+    wall = time.perf_counter() - wall0
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    pos, vel, ext1 = g.get_state()       # raises on any device-side error
+    assert np.isfinite(pos).all()
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    ns_day = dt_ps * 1e-3 * 86400.0 / (ms_step * 1e-3) * world
+    rebuilds = int(ext1["n_rebuilds"] - ext0["n_rebuilds"])
+    launches = args.steps * 14 + rebuilds * 9
+
+    out = None
+    if rank == 0:
+        # per-kernel device times with CUDA events on the launching stream
+        stages = g.time_stages(float(ext1["lambda"]), reps=args.steps, stream=stream)
+        pair_ms = stages["pairs"]
+        achieved = n_pairs * FLOPS_PER_PAIR / (pair_ms * 1e-3) / 1e12
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_pairs<float>", "kernel_ms": pair_ms,
+                "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop/FMA x 2032 MHz (max SM clock)"}
+        if clocks and clocks.get("sm_mhz"):
+            roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / 2032.0)
+        # end to end through the public API with host buffers
+        e2e = None
+        if args.e2e_steps > 0:
+            pin_pos = torch.from_numpy(pos).pin_memory()
+            pin_vel = torch.empty_like(pin_pos).pin_memory()
+            pin_ext = torch.zeros(lfe.NEXT, dtype=torch.float64).pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                g.set_positions_ptr(pin_pos.data_ptr(), 0, stream)
+                g.step(1, stream)
+                g.get_state_into(pin_pos.data_ptr(), pin_vel.data_ptr(), pin_ext.data_ptr())
+            te = (time.perf_counter() - t0) / args.e2e_steps
+            n = len(d["charge"])
+            e2e = {"value": dt_ps * 1e-3 * 86400.0 / te, "unit": "ns/day",
+                   "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 6 * n * 8 + lfe.NEXT * 8,
+                   "calls": "lfe_set_positions(host) + lfe_step(1) + lfe_get_state(host) per step"}
+        fp64 = None
+        if not args.no_fp64 and prec == lfe.LFE_FP32_MIXED:
+            g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=2608)
+            g64.set_positions(pos)
+            g64.set_velocities(vel)
+            g64.step(5, stream)
+            torch.cuda.synchronize()
+            k64 = max(5, min(40, args.steps // 5))
+            ms64 = time_steps(g64, k64, stream, flush)
+            m64 = sum(ms64) / k64
+            fp64 = {"ns_per_day": dt_ps * 1e-3 * 86400.0 / (m64 * 1e-3), "ms_per_step": m64, "steps": k64}
+            g64.close()
+        cpu = None if args.no_cpu else cpu_baseline(d, dt_ps)
+        out = {"metric": METRIC, "value": ns_day, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32" if prec == lfe.LFE_FP32_MIXED else "f64",
+               "data": "synthetic",
+               "config": {"workload": desc, "atoms": len(d["charge"]), "dt_fs": dt_ps * 1e3,
+                          "precision": "FP32 arithmetic, int64 fixed-point force/energy sums, FP64 lambda/OPES"
+                          if prec == lfe.LFE_FP32_MIXED else "FP64", "l2": "flushed between steps (256 MiB write)",
+                          "parallelism": "replicas" if world > 1 else "single replica",
+                          "pairs_per_step": n_pairs},
+               "pair_interactions_per_s": n_pairs / (ms_step * 1e-3) * world,
+               "wall_ms_per_step": wall / args.steps * 1e3,
+               "neighbour_rebuilds": rebuilds,
+               "gpu_launches": launches,
+               "roofline": roof, "stages_ms": stages, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": clocks, "lambda_end": ext1["lambda"], "theta_end": ext1["theta"]}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_profile_case(args):
+    import torch
+    from paper_2608_12691_b300 import lfe
+    torch.cuda.set_device(0)
+    d, _ = make_workload(args.workload, 0)
+    prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
+    g = lfe.System(d, precision=prec)
+    stages = g.time_stages(d["lam"], reps=3)
+    print(json.dumps({"profile_case": args.workload, "stages_ms": stages}))
+
+
+def main():
+    args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

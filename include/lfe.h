@@ -1,0 +1,209 @@
+/*
+ * lfe.h -- C-ABI of the B300 alchemical nonbonded engine.
+ *
+ * The library evaluates, on one GPU, the lambda-dependent potential of the
+ * linear-basis-function lambda-dynamics method (Correa, Abreu, Nair,
+ * Tuckerman, Section 2.2, Eq. 4):
+ *
+ *   U(r, lambda) = U_vv + U_uu + h_A(lambda) U_uv + h_B(lambda) U_soft (+ bonded)
+ *
+ *   U_vv, U_uu  solvent-solvent and solute-solute nonbonded energy (LJ +
+ *               Ewald/PME Coulomb), unchanged along lambda;
+ *   U_uv        the full solute-solvent LJ + Coulomb interaction, including its
+ *               reciprocal-space cross term and neutralising-background share;
+ *   U_soft      the capped soft-LJ basis, sum over solute-solvent pairs of
+ *               eps_ij u_cap(r_ij / sigma_ij) (Eq. 5-6);
+ *   h_A, h_B    the smoothstep switches of Eq. 7-10,
+ *
+ * together with the forces -grad U and the generalized force
+ *   dU/dlambda = h_A'(lambda) U_uv + h_B'(lambda) U_soft       (Section 2.1)
+ * that drives the alchemical coordinate.  lfe_step advances atoms with a
+ * Langevin middle-scheme integrator (Section 2.6), rigid waters and X-H
+ * constraints, and the mirror-periodic coordinate theta (Eq. 3) under the
+ * dual OPES bias (Eq. 11-14).
+ *
+ * Conventions for every call:
+ *   - Units: nm, ps, amu, kJ/mol, e, K.  Coulomb constant 138.935458.
+ *   - Arrays are row-major doubles: positions and forces are [3 N] (x, y, z of
+ *     atom 0, then atom 1, ...), in the caller's atom order.
+ *   - The caller owns every array it passes; inputs are copied before the call
+ *     returns (or before the stream reaches the copy, for device inputs);
+ *     outputs are written into caller memory.  The library never frees caller
+ *     memory and keeps no caller pointer.
+ *   - `on_device` / `out_on_device` = 1 means the pointer is device memory
+ *     usable on `stream` (for example a torch tensor's data_ptr()); 0 means
+ *     host memory.  `stream` is a cudaStream_t or NULL for the legacy stream.
+ *     Device outputs are complete when `stream` reaches the end of the call's
+ *     work; host outputs are complete when the call returns.
+ *   - Every call returns LFE_OK (0) or a negative LFE_ERR_* code and records
+ *     a message readable with lfe_last_error.  No call aborts the process or
+ *     traps the GPU; bounded device waits report LFE_ERR_TIMEOUT.
+ */
+#ifndef LFE_H
+#define LFE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LFE_OK             0
+#define LFE_ERR_ARG       -1   /* bad size, r_cut > box/2, non-finite input, sigma < 0 ... */
+#define LFE_ERR_CUDA      -2   /* a CUDA runtime call failed */
+#define LFE_ERR_OVERFLOW  -3   /* neighbour-list capacity exceeded (after one internal regrowth) */
+#define LFE_ERR_NONFINITE -4   /* a force, energy or position became NaN/Inf */
+#define LFE_ERR_TIMEOUT   -5   /* a bounded device wait expired */
+#define LFE_ERR_STATE     -6   /* call out of order (e.g. step without neighbour list) */
+
+#define LFE_FP32_MIXED 0       /* FP32 pair/PME arithmetic, 64-bit fixed-point accumulation */
+#define LFE_FP64       1       /* the same kernels instantiated in double precision */
+
+/* Number of doubles written by lfe_eval into energy_terms. */
+#define LFE_NTERMS 10
+/* energy_terms layout */
+#define LFE_T_U        0   /* U(lambda), kJ/mol (nonbonded + bonded) */
+#define LFE_T_DUDL     1   /* dU/dlambda */
+#define LFE_T_UVV      2
+#define LFE_T_UUU      3
+#define LFE_T_UUV      4
+#define LFE_T_USOFT    5
+#define LFE_T_UBONDED  6
+#define LFE_T_NPAIRS   7   /* unordered non-excluded pairs with r < r_cut (counted) */
+#define LFE_T_HA       8   /* h_A(lambda) */
+#define LFE_T_HB       9   /* h_B(lambda) */
+
+typedef struct lfe_system lfe_system;   /* opaque; owns all of its device memory */
+typedef struct lfe_batch lfe_batch;     /* opaque; a set of systems run together */
+
+/* Run parameters.  Fields marked "step" matter only for lfe_step. */
+typedef struct {
+    double box[3];            /* orthorhombic box, nm; r_cut <= min(box)/2 required */
+    double r_cut;             /* nonbonded cutoff, nm */
+    double r_switch;          /* LJ switch start, nm; < 0: plain truncation */
+    double ewald_alpha;       /* Ewald splitting parameter, nm^-1 */
+    int pme_grid[3];          /* PME grid; each a product of 2, 3 and 5, 8..128 */
+    int pme_order;            /* B-spline order; must be 4 */
+    double skin;              /* neighbour-list buffer, nm (default 0.1 if <= 0) */
+    int precision;            /* LFE_FP32_MIXED or LFE_FP64 */
+    double temperature;       /* step: K */
+    double friction;          /* step: atoms' Langevin friction, 1/ps */
+    double dt;                /* step: time step, ps */
+    double lambda_mass;       /* step: theta mass, amu nm^2 (<= 0: theta frozen) */
+    double lambda_friction;   /* step: theta Langevin friction, 1/ps */
+    double theta0;            /* step: initial theta in [0, 2) */
+    int opes_stride;          /* step: steps between kernel deposits (0: no OPES) */
+    double opes_dE_std;       /* step: OPES-Standard barrier, kJ/mol (0 disables) */
+    double opes_dE_exp;       /* step: OPES-Explore barrier, kJ/mol (0 disables) */
+    double opes_sigma;        /* step: kernel width on theta */
+    int opes_max_kernels;     /* step: kernel capacity per bias (default 1024 if <= 0) */
+    unsigned long long seed;  /* step: Philox4x32-10 key */
+} lfe_params;
+
+/* System description (host arrays, copied by lfe_create).
+ *   excl      [2 n_excl]  pairs left out of the ordinary pair sum.  They get
+ *                         the Ewald exclusion correction -k_e q_i q_j erf(a r)/r.
+ *   pairs14   [2 n_14]    subset of excl that also gets scaled 1-4 terms
+ *   scale14   [2 n_14]    (s_LJ, s_Coulomb) per 1-4 pair
+ *   water_OHH [3 n_waters] rigid waters (O, H, H) held by SETTLE at
+ *                         water_rOH / water_rHH
+ *   constraints [2 n_cons], constraint_len [n_cons]: X-H distance constraints;
+ *                         every constraint must share its first atom with the
+ *                         other constraints of its group (star groups of <= 4)
+ *   bonds [2 nb] + bond_par [2 nb] (k, r0): 1/2 k (r - r0)^2
+ *   angles [3 na] + angle_par [2 na] (k, theta0), vertex in the middle
+ *   torsions [4 nt] + torsion_par [3 nt] (k, n, phi0): k (1 + cos(n phi - phi0))
+ *   mass [n]  amu; 0 freezes the atom (it never moves).
+ *   solute [n] 1 = solute atom, 0 = solvent.  Solute-solvent pairs are
+ *             exactly the lambda-coupled ones (coupling route, Section 2.2).
+ */
+typedef struct {
+    int n_atoms;
+    const double* pos;
+    const double* charge;
+    const double* sigma;
+    const double* epsilon;
+    const unsigned char* solute;
+    const double* mass;
+    int n_excl;        const int* excl;
+    int n_14;          const int* pairs14;      const double* scale14;
+    int n_waters;      const int* water_OHH;    double water_rOH, water_rHH;
+    int n_constraints; const int* constraints;  const double* constraint_len;
+    int n_bonds;       const int* bonds;        const double* bond_par;
+    int n_angles;      const int* angles;       const double* angle_par;
+    int n_torsions;    const int* torsions;     const double* torsion_par;
+} lfe_topology;
+
+/* Create a system: validates and copies the description, allocates device
+ * memory on the current device, builds the neighbour list.  *out is NULL on
+ * failure (the message is then available from lfe_last_error(NULL)). */
+int lfe_create(const lfe_params* params, const lfe_topology* topo, lfe_system** out);
+
+/* Replace positions ([3N], host or device).  Rebuilds the neighbour list. */
+int lfe_set_positions(lfe_system* sys, const double* pos, int on_device, void* stream);
+
+/* Replace velocities ([3N], host). */
+int lfe_set_velocities(lfe_system* sys, const double* vel);
+
+/* Change the atoms' integration parameters (time step ps, Langevin friction
+ * 1/ps, temperature K) for the following lfe_step calls, e.g. for a short
+ * small-step, high-friction equilibration from a packed start (the paper
+ * equilibrates before production, Section 2.6).  theta keeps its own
+ * friction; its time step follows dt.  The step graph is recaptured. */
+int lfe_set_integrator(lfe_system* sys, double dt, double friction, double temperature);
+
+/* Rebuild the cluster-pair list from the current positions (cell sort,
+ * clustering, bounding boxes, tile list, exclusion masks). */
+int lfe_build_neighbors(lfe_system* sys, void* stream);
+
+/* Evaluate U(lambda), its forces and dU/dlambda (Eq. 4) at the current
+ * positions.  forces: [3N] or NULL; energy_terms: [LFE_NTERMS] or NULL. */
+int lfe_eval(lfe_system* sys, double lambda, double* forces, double* energy_terms,
+             int out_on_device, void* stream);
+
+/* Per-solute-atom parameter gradients at lambda (host outputs, each [3 n_u],
+ * solute atoms in caller order, entries (dq, dsigma, deps) per atom):
+ *   dU_dp      = dU/dq_i, dU/dsigma_i, dU/deps_i
+ *   d2U_dl_dp  = d/dp (dU/dlambda) = h_A' dU_uv/dp + h_B' dU_soft/dp.
+ * Either may be NULL. */
+int lfe_param_grad(lfe_system* sys, double lambda, double* dU_dp, double* d2U_dl_dp);
+
+/* Advance n_steps of atoms + theta (replays one captured CUDA graph per step
+ * on `stream`, rebuilding the neighbour list on the device when an atom has
+ * moved more than skin/2).  Returns after the work is queued; errors raised
+ * on the device are reported by the next call that synchronises. */
+int lfe_step(lfe_system* sys, int n_steps, void* stream);
+
+/* Copy state to host: pos [3N], vel [3N] (either may be NULL); ext (may be
+ * NULL) receives LFE_NEXT doubles: [theta, p_theta, lambda, dU/dlambda, U,
+ * n_kernels_std, n_kernels_exp, step, neighbour rebuilds done by lfe_step].
+ * Synchronises the device and reports errors raised by queued steps. */
+#define LFE_NEXT 9
+int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext);
+
+/* Write / read a versioned binary checkpoint (positions, velocities, theta,
+ * p_theta, OPES kernels, step counter; checksum verified on restore). */
+int lfe_checkpoint(lfe_system* sys, const char* path);
+int lfe_restore(lfe_system* sys, const char* path);
+
+/* Mean device time (ms) of each kernel stage over `reps` eager evaluations at
+ * lambda, timed with CUDA events on `stream`.  names/ms arrays of length
+ * max_n; returns the number of stages written (>= 0) or an error code. */
+int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
+                    const char** names, double* ms, int max_n);
+
+/* Batched replicas: evaluate / step several systems together. */
+int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out);
+int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms /*[n][LFE_NTERMS]*/,
+                   void* stream);
+int lfe_batch_step(lfe_batch* b, int n_steps, void* stream);
+void lfe_batch_destroy(lfe_batch* b);
+
+/* Message of the last error recorded for sys (or of the last failed
+ * lfe_create when sys is NULL).  Valid until the next call on sys. */
+const char* lfe_last_error(const lfe_system* sys);
+
+void lfe_destroy(lfe_system* sys);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,569 @@
+// dyn.cu -- bonded terms, outputs, the Langevin middle-scheme integrator with
+// constraint groups, and the theta / dual-OPES update (all per-step kernels
+// that are not pair or PME work).
+#include "lfe_views.cuh"
+
+namespace lfe {
+
+template <typename real>
+__device__ __forceinline__ real minimg(real d, real L, real invL)
+{
+    return d - L * rint(d * invL);
+}
+__device__ __forceinline__ float minimg(float d, float L, float invL) { return d - L * rintf(d * invL); }
+
+// wrap one coordinate into [0, L) (the sorted copy used by the pair and PME kernels)
+template <typename real>
+__device__ __forceinline__ real wrap_sorted(real x, real L, real invL)
+{
+    real o = x - L * floor(x * invL);
+    if (o >= L) o -= L;
+    if (o < (real)0) o = (real)0;
+    return o;
+}
+
+template <typename real>
+__device__ __forceinline__ void add_force(const SysView<real>& s, int atom, real fx, real fy, real fz)
+{
+    const int slot = s.iperm[atom];
+    atomic_add_ll(&s.F[slot], to_fixed(fx, FSCALE));
+    atomic_add_ll(&s.F[s.n_pad + slot], to_fixed(fy, FSCALE));
+    atomic_add_ll(&s.F[2 * s.n_pad + slot], to_fixed(fz, FSCALE));
+}
+
+// ------------------------------------------------------------ set lambda
+template <typename real>
+__global__ void k_set_lambda(SysView<real> s, double lam)
+{
+    LamState* L = s.lam;
+    double hA, hB, dA, dB;
+    switching_fns(lam, hA, hB, dA, dB);
+    L->lambda = lam; L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
+}
+
+template <typename real>
+void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st)
+{
+    k_set_lambda<real><<<1, 1, 0, st>>>(s, lam);
+}
+
+// --------------------------------------------------------------- outputs
+__device__ __forceinline__ double efix(const long long* E, int k) { return (double)E[k] * (1.0 / ESCALE); }
+
+template <typename real>
+__global__ void k_eval_out(SysView<real> s, double* forces, double* terms, double cvv, double cuu, double cuv)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < s.n) {
+        const int slot = s.iperm[a];
+        long long fx = s.F[slot], fy = s.F[s.n_pad + slot], fz = s.F[2 * s.n_pad + slot];
+        s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+        if (forces) {
+            forces[3 * a] = (double)fx * (1.0 / FSCALE);
+            forces[3 * a + 1] = (double)fy * (1.0 / FSCALE);
+            forces[3 * a + 2] = (double)fz * (1.0 / FSCALE);
+            if (!isfinite(forces[3 * a]) || !isfinite(forces[3 * a + 1]) || !isfinite(forces[3 * a + 2]))
+                atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+        }
+    }
+    // one thread of the last block finalises the energies after all blocks
+    // have read their forces (energies are independent of the force slots)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long* E = s.E;
+        LamState* L = s.lam;
+        const double Uvv = efix(E, E_PAIR_VV) + efix(E, E_EXCL_VV) + efix(E, E_14_VV) + efix(E, E_REC_VV) + cvv;
+        const double Uuu = efix(E, E_PAIR_UU) + efix(E, E_EXCL_UU) + efix(E, E_14_UU) + efix(E, E_REC_UU) + cuu;
+        const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + cuv;
+        const double Us = efix(E, E_PAIR_SOFT);
+        const double Ub = efix(E, E_BONDED);
+        const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub;
+        const double dU = L->dhA * Uuv + L->dhB * Us;
+        if (terms) {
+            terms[0] = U; terms[1] = dU; terms[2] = Uvv; terms[3] = Uuu; terms[4] = Uuv;
+            terms[5] = Us; terms[6] = Ub; terms[7] = (double)E[E_NPAIRS]; terms[8] = L->hA; terms[9] = L->hB;
+        }
+        L->U = U;
+        L->dUdl = dU;
+        if (!isfinite(U) || !isfinite(dU)) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+        for (int k = 0; k < E_N; ++k) E[k] = 0;
+    }
+}
+
+template <typename real>
+void launch_eval_out(const SysView<real>& s, double* forces, double* terms, double cvv, double cuu, double cuv,
+                     cudaStream_t st)
+{
+    k_eval_out<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, forces, terms, cvv, cuu, cuv);
+}
+
+// master positions from caller doubles; refresh the sorted copy in the
+// current slot order
+template <typename real>
+__global__ void k_assign_positions(SysView<real> s, const double* pos)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    R4<real> p;
+    p.x = (real)pos[3 * a]; p.y = (real)pos[3 * a + 1]; p.z = (real)pos[3 * a + 2]; p.w = (real)0;
+    s.x[a] = p;
+}
+
+template <typename real>
+void launch_assign_positions(const SysView<real>& s, const double* pos, cudaStream_t st)
+{
+    k_assign_positions<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos);
+}
+
+template <typename real>
+__global__ void k_refresh_sorted(SysView<real> s)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
+    const int slot = s.iperm[a];
+    const R4<real> x = s.x[a];
+    R4<real> o = s.xq[slot];
+    o.x = wrap_sorted(x.x, s.L[0], s.invL[0]);
+    o.y = wrap_sorted(x.y, s.L[1], s.invL[1]);
+    o.z = wrap_sorted(x.z, s.L[2], s.invL[2]);
+    s.xq[slot] = o;
+}
+
+template <typename real>
+void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st)
+{
+    k_refresh_sorted<real><<<(s.n + 255) / 256, 256, 0, st>>>(s);
+}
+
+// ---------------------------------------------------------------- bonded
+// harmonic bonds 1/2 k (r - r0)^2, harmonic angles 1/2 k (theta - theta0)^2,
+// periodic torsions k (1 + cos(n phi - phi0)); minimum-image vectors
+template <typename real>
+__global__ void k_bonded(SysView<real> s, BondView<real> b)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double en = 0.0;
+    const real* L = s.L;
+    const real* iL = s.invL;
+    auto vec = [&](int i, int j, real* d) {
+        R4<real> pi = s.x[i], pj = s.x[j];
+        d[0] = minimg(pj.x - pi.x, L[0], iL[0]);
+        d[1] = minimg(pj.y - pi.y, L[1], iL[1]);
+        d[2] = minimg(pj.z - pi.z, L[2], iL[2]);
+    };
+    if (e < b.nb) {
+        const int2 ij = b.b[e];
+        const R2<real> par = b.bp[e];
+        real d[3];
+        vec(ij.x, ij.y, d);
+        const real r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        const real dr = r - par.y;
+        en = 0.5 * (double)par.x * (double)dr * (double)dr;
+        const real g = par.x * dr / r;   // dU/dr / r; force on i = +g d
+        add_force(s, ij.x, g * d[0], g * d[1], g * d[2]);
+        add_force(s, ij.y, -g * d[0], -g * d[1], -g * d[2]);
+    } else if (e < b.nb + b.na) {
+        const int4 t = b.a[e - b.nb];
+        const R2<real> par = b.ap[e - b.nb];
+        real u[3], v[3];
+        vec(t.y, t.x, u);   // vertex -> i
+        vec(t.y, t.z, v);   // vertex -> k
+        const real lu2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const real lv2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const real luv = sqrt(lu2 * lv2);
+        real c = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) / luv;
+        c = fmin((real)1, fmax((real)-1, c));
+        const real th = acos(c);
+        const real dth = th - par.y;
+        en = 0.5 * (double)par.x * (double)dth * (double)dth;
+        real sn = sqrt(fmax((real)1e-24, (real)1 - c * c));
+        const real pre = par.x * dth / sn;   // F = pre * dc/dx
+        real fi[3], fk[3];
+        for (int k = 0; k < 3; ++k) {
+            fi[k] = pre * (v[k] / luv - c * u[k] / lu2);
+            fk[k] = pre * (u[k] / luv - c * v[k] / lv2);
+        }
+        add_force(s, t.x, fi[0], fi[1], fi[2]);
+        add_force(s, t.z, fk[0], fk[1], fk[2]);
+        add_force(s, t.y, -fi[0] - fk[0], -fi[1] - fk[1], -fi[2] - fk[2]);
+    } else if (e < b.nb + b.na + b.nt) {
+        const int4 t = b.t[e - b.nb - b.na];
+        const R4<real> par = b.tp[e - b.nb - b.na];
+        // r_ij = x_i - x_j, r_kj = x_k - x_j, r_kl = x_k - x_l
+        real rij[3], rkj[3], rkl[3], tmp[3];
+        vec(t.y, t.x, rij);
+        vec(t.y, t.z, rkj);
+        vec(t.w, t.z, rkl);
+        (void)tmp;
+        const real m[3] = {rij[1] * rkj[2] - rij[2] * rkj[1], rij[2] * rkj[0] - rij[0] * rkj[2],
+                           rij[0] * rkj[1] - rij[1] * rkj[0]};
+        const real n[3] = {rkj[1] * rkl[2] - rkj[2] * rkl[1], rkj[2] * rkl[0] - rkj[0] * rkl[2],
+                           rkj[0] * rkl[1] - rkj[1] * rkl[0]};
+        const real m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+        const real n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        const real rkj2 = rkj[0] * rkj[0] + rkj[1] * rkj[1] + rkj[2] * rkj[2];
+        const real lkj = sqrt(rkj2);
+        const real yv = lkj * (rij[0] * n[0] + rij[1] * n[1] + rij[2] * n[2]);
+        const real xv = m[0] * n[0] + m[1] * n[1] + m[2] * n[2];
+        const real phi = atan2(yv, xv);
+        const real arg = par.y * phi - par.z;
+        en = (double)par.x * (1.0 + cos((double)arg));
+        const real dUdphi = -par.x * par.y * sin(arg);
+        real fi[3], fl[3], fj[3], fk[3];
+        const real p = (rij[0] * rkj[0] + rij[1] * rkj[1] + rij[2] * rkj[2]) / rkj2;
+        const real qv = (rkl[0] * rkj[0] + rkl[1] * rkj[1] + rkl[2] * rkj[2]) / rkj2;
+        for (int k = 0; k < 3; ++k) {
+            fi[k] = -dUdphi * lkj / m2 * m[k];
+            fl[k] = dUdphi * lkj / n2 * n[k];
+        }
+        for (int k = 0; k < 3; ++k) {
+            fj[k] = -fi[k] + p * fi[k] - qv * fl[k];
+            fk[k] = -fl[k] - p * fi[k] + qv * fl[k];
+        }
+        add_force(s, t.x, fi[0], fi[1], fi[2]);
+        add_force(s, t.y, fj[0], fj[1], fj[2]);
+        add_force(s, t.z, fk[0], fk[1], fk[2]);
+        add_force(s, t.w, fl[0], fl[1], fl[2]);
+    }
+    long long v = __double2ll_rn(warp_sum_d(en) * ESCALE);
+    if ((threadIdx.x & 31) == 0 && v) atomic_add_ll(&s.E[E_BONDED], v);
+}
+
+template <typename real>
+void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st)
+{
+    const int n = b.nb + b.na + b.nt;
+    if (n == 0) return;
+    k_bonded<real><<<(n + 255) / 256, 256, 0, st>>>(s, b);
+}
+
+// ------------------------------------------------------------ integrator
+// Langevin middle scheme per constraint group: kick v += dt F/m, half drift,
+// Ornstein-Uhlenbeck v = a v + sqrt(kT (1 - a^2)/m) R, half drift, constrain
+// the new positions along the old bond vectors (Newton iteration on the
+// group's Lagrange multipliers), v = (x_new - x)/dt.  All of it is done in
+// coordinates relative to the group's first atom (small numbers, so FP32
+// keeps full relative precision and the velocity comes from the displacement
+// itself, not from a difference of two absolute positions).  Consumes
+// (zeroes) the fixed-point forces, refreshes the sorted coordinates and flags
+// a neighbour rebuild when an atom has moved more than skin/2 since the last
+// build.
+template <typename real>
+__global__ void k_integrate(SysView<real> s, StepView<real> g)
+{
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.n_groups) return;
+    const Group G = g.groups[gi];
+    const unsigned long long step = s.lam->step;
+    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {
+        // the neighbour list was truncated: consume the forces, leave the
+        // state untouched (the host regrows the list and replays the step)
+        for (int a = 0; a < G.natom; ++a) {
+            const int slot = s.iperm[G.atom[a]];
+            s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+        }
+        return;
+    }
+    real o0[3];              // old absolute position of atom 0
+    real rel0[4][3];         // old positions relative to atom 0 (minimum image)
+    real p[4][3];            // new positions relative to old atom 0
+    real w[4];
+    bool bad = false;
+    {
+        const R4<real> x0 = s.x[G.atom[0]];
+        o0[0] = x0.x; o0[1] = x0.y; o0[2] = x0.z;
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        if (a >= G.natom) break;
+        const int atom = G.atom[a];
+        const int slot = s.iperm[atom];
+        const real f[3] = {(real)((double)s.F[slot] * (1.0 / FSCALE)),
+                           (real)((double)s.F[s.n_pad + slot] * (1.0 / FSCALE)),
+                           (real)((double)s.F[2 * s.n_pad + slot] * (1.0 / FSCALE))};
+        s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+        const R4<real> x = s.x[atom], v = s.v[atom];
+        const real xa[3] = {x.x, x.y, x.z};
+        for (int d = 0; d < 3; ++d) rel0[a][d] = a == 0 ? (real)0 : minimg(xa[d] - o0[d], s.L[d], s.invL[d]);
+        w[a] = s.invm[atom];
+        if (w[a] == (real)0) {
+            for (int d = 0; d < 3; ++d) p[a][d] = rel0[a][d];
+            continue;
+        }
+        real nr[3];
+        normals3<real>(make_uint4((unsigned)atom, (unsigned)step, (unsigned)(step >> 32), 0u), g.key,
+                       nr[0], nr[1], nr[2]);
+        const real sd = sqrt(g.kT * ((real)1 - g.a_fric * g.a_fric) * w[a]);
+        const real vv[3] = {v.x, v.y, v.z};
+        for (int d = 0; d < 3; ++d) {
+            real vd = vv[d] + g.dt * w[a] * f[d];
+            real disp = (real)0.5 * g.dt * vd;
+            vd = g.a_fric * vd + sd * nr[d];
+            disp += (real)0.5 * g.dt * vd;
+            p[a][d] = rel0[a][d] + disp;
+        }
+    }
+    if (G.ncons > 0) {
+        real sref[3][3];
+        for (int k = 0; k < G.ncons; ++k)
+            for (int d = 0; d < 3; ++d) sref[k][d] = rel0[G.cj[k]][d] - rel0[G.ci[k]][d];
+        const real tol = sizeof(real) == 4 ? (real)2e-6 : (real)1e-12;
+        bool conv = false;
+        for (int it = 0; it < 32; ++it) {
+            real r[3][3], sig[3];
+            conv = true;
+            for (int k = 0; k < G.ncons; ++k) {
+                real r2 = 0;
+                for (int d = 0; d < 3; ++d) {
+                    r[k][d] = p[G.cj[k]][d] - p[G.ci[k]][d];
+                    r2 += r[k][d] * r[k][d];
+                }
+                const real l2 = (real)G.len[k] * (real)G.len[k];
+                sig[k] = r2 - l2;
+                if (fabs(sig[k]) > tol * l2) conv = false;
+            }
+            if (conv) break;
+            // J_kl = 2 r_k . (M_kl s_l), M_kl = w_cj(k) c(cj_k, l) - w_ci(k) c(ci_k, l),
+            // c(a, l) = +1 if a is the second atom of constraint l, -1 if the first
+            real J[3][3];
+            for (int k = 0; k < G.ncons; ++k)
+                for (int l = 0; l < G.ncons; ++l) {
+                    auto c = [&](int at, int ll) -> real {
+                        return at == G.cj[ll] ? (real)1 : (at == G.ci[ll] ? (real)-1 : (real)0);
+                    };
+                    const real M = w[G.cj[k]] * c(G.cj[k], l) - w[G.ci[k]] * c(G.ci[k], l);
+                    J[k][l] = (real)2 * M * (r[k][0] * sref[l][0] + r[k][1] * sref[l][1] + r[k][2] * sref[l][2]);
+                }
+            real dl[3] = {0, 0, 0};
+            if (G.ncons == 1) {
+                dl[0] = -sig[0] / J[0][0];
+            } else if (G.ncons == 2) {
+                const real det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+                dl[0] = (-sig[0] * J[1][1] + sig[1] * J[0][1]) / det;
+                dl[1] = (-sig[1] * J[0][0] + sig[0] * J[1][0]) / det;
+            } else {
+                const real c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+                const real c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+                const real c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+                const real det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+                const real b0 = -sig[0], b1 = -sig[1], b2 = -sig[2];
+                // Cramer's rule
+                dl[0] = (b0 * c00 + J[0][1] * (J[1][2] * b2 - b1 * J[2][2]) + J[0][2] * (b1 * J[2][1] - J[1][1] * b2)) / det;
+                dl[1] = (J[0][0] * (b1 * J[2][2] - J[1][2] * b2) + b0 * c01 + J[0][2] * (J[1][0] * b2 - b1 * J[2][0])) / det;
+                dl[2] = (J[0][0] * (J[1][1] * b2 - b1 * J[2][1]) + J[0][1] * (b1 * J[2][0] - J[1][0] * b2) + b0 * c02) / det;
+            }
+            for (int l = 0; l < G.ncons; ++l)
+                for (int d = 0; d < 3; ++d) {
+                    p[G.cj[l]][d] += dl[l] * w[G.cj[l]] * sref[l][d];
+                    p[G.ci[l]][d] -= dl[l] * w[G.ci[l]] * sref[l][d];
+                }
+        }
+        if (!conv) atomicOr(&s.flags[FL_ERROR], ERRB_CONSTRAINT);
+    }
+    // keep each group near the box: shift it by whole periods when its first
+    // atom leaves [0, L)
+    real shift[3];
+    for (int d = 0; d < 3; ++d) shift[d] = -s.L[d] * floor((o0[d] + p[0][d]) * s.invL[d]);
+    const real inv_dt = (real)1 / g.dt;
+    bool rebuild = false;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        if (a >= G.natom) break;
+        const int atom = G.atom[a];
+        const int slot = s.iperm[atom];
+        R4<real> xnew, vnew;
+        if (w[a] == (real)0) {
+            vnew.x = vnew.y = vnew.z = (real)0;
+        } else {
+            vnew.x = (p[a][0] - rel0[a][0]) * inv_dt;
+            vnew.y = (p[a][1] - rel0[a][1]) * inv_dt;
+            vnew.z = (p[a][2] - rel0[a][2]) * inv_dt;
+        }
+        vnew.w = (real)0;
+        xnew.x = (o0[0] + shift[0]) + p[a][0];
+        xnew.y = (o0[1] + shift[1]) + p[a][1];
+        xnew.z = (o0[2] + shift[2]) + p[a][2];
+        xnew.w = (real)0;
+        if (!isfinite(xnew.x) || !isfinite(xnew.y) || !isfinite(xnew.z)) bad = true;
+        s.x[atom] = xnew;
+        s.v[atom] = vnew;
+        R4<real> o = s.xq[slot];
+        o.x = wrap_sorted(xnew.x, s.L[0], s.invL[0]);
+        o.y = wrap_sorted(xnew.y, s.L[1], s.invL[1]);
+        o.z = wrap_sorted(xnew.z, s.L[2], s.invL[2]);
+        s.xq[slot] = o;
+        const R4<real> xr = s.xref[atom];
+        const real dx = minimg(xnew.x - xr.x, s.L[0], s.invL[0]);
+        const real dy = minimg(xnew.y - xr.y, s.L[1], s.invL[1]);
+        const real dz = minimg(xnew.z - xr.z, s.L[2], s.invL[2]);
+        if (dx * dx + dy * dy + dz * dz > g.skin_half2) rebuild = true;
+    }
+    if (rebuild) atomicOr(&s.flags[FL_REBUILD], 1);
+    if (bad) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+}
+
+template <typename real>
+void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st)
+{
+    k_integrate<real><<<(g.n_groups + 127) / 128, 128, 0, st>>>(s, g);
+}
+
+// --------------------------------------------------------- theta and OPES
+__device__ __forceinline__ double pdiff2(double a, double b)
+{
+    double d = a - b;
+    return d - 2.0 * floor((d + 1.0) / 2.0);
+}
+
+// (V, dV/dtheta) of bias b at theta, warp-cooperative (Eq. 11-13)
+template <typename real>
+__device__ void opes_bias(const ThetaView<real>& t, int b, double th, double& V, double& dV)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = t.st->n[b];
+    V = 0.0; dV = 0.0;
+    if (!t.on[b] || n == 0) return;
+    const double* c = t.centre + b * t.max_k;
+    const double* w = t.weight + b * t.max_k;
+    const double is2 = 1.0 / (t.sigma * t.sigma);
+    double sum = 0.0, dsum = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double d = pdiff2(th, c[k]);
+        const double gk = w[k] * exp(-0.5 * d * d * is2);
+        sum += gk;
+        dsum += -gk * d * is2;
+    }
+    sum = warp_sum_d(sum);
+    dsum = warp_sum_d(dsum);
+    sum = __shfl_sync(0xffffffffu, sum, 0);
+    dsum = __shfl_sync(0xffffffffu, dsum, 0);
+    const double rho = sum / t.st->wsum[b], drho = dsum / t.st->wsum[b];
+    const double rb = t.st->rho_bar[b];
+    const double arg = rho / rb + t.epsr[b];
+    V = t.nu[b] / t.beta * log(arg);
+    dV = t.nu[b] / t.beta * (drho / rb) / arg;
+}
+
+// deposit a kernel at th into bias b; S_j (unnormalised KDE at each centre)
+// is updated incrementally so rho_bar costs O(n) per deposit
+template <typename real>
+__device__ void opes_deposit(const ThetaView<real>& t, int b, double th, double wnew)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = t.st->n[b];
+    if (n >= t.max_k) {
+        if (lane == 0) atomicOr(&t.st->pad[0], 1);   // capacity reached: stop depositing
+        return;
+    }
+    double* c = t.centre + b * t.max_k;
+    double* w = t.weight + b * t.max_k;
+    double* S = t.S + b * t.max_k;
+    const double is2 = 1.0 / (t.sigma * t.sigma);
+    double snew = 0.0, ssum = 0.0;
+    for (int k = lane; k < n; k += 32) {
+        const double d = pdiff2(th, c[k]);
+        const double gk = exp(-0.5 * d * d * is2);
+        snew += w[k] * gk;
+        S[k] += wnew * gk;
+        ssum += S[k];
+    }
+    snew = warp_sum_d(snew);
+    ssum = warp_sum_d(ssum);
+    __syncwarp();
+    if (lane == 0) {
+        snew += wnew;
+        c[n] = th;
+        w[n] = wnew;
+        S[n] = snew;
+        ssum += snew;
+        t.st->n[b] = n + 1;
+        t.st->wsum[b] += wnew;
+        t.st->rho_bar[b] = ssum / ((double)(n + 1) * t.st->wsum[b]);
+    }
+    __syncwarp();
+}
+
+template <typename real>
+__global__ void k_theta(SysView<real> s, ThetaView<real> t)
+{
+    const int lane = threadIdx.x;
+    LamState* L = s.lam;
+    long long* E = s.E;
+    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {
+        // step skipped (see k_integrate); no rebuild until the host regrows
+        if (lane == 0) {
+            if (t.use_cond) cudaGraphSetConditional(t.cond, 0u);
+            if (t.use_cond) s.flags[FL_REBUILD] = 0;
+        }
+        if (lane < E_N) E[lane] = 0;
+        return;
+    }
+    const double Uvv = efix(E, E_PAIR_VV) + efix(E, E_EXCL_VV) + efix(E, E_14_VV) + efix(E, E_REC_VV) + t.const_vv;
+    const double Uuu = efix(E, E_PAIR_UU) + efix(E, E_EXCL_UU) + efix(E, E_14_UU) + efix(E, E_REC_UU) + t.const_uu;
+    const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
+    const double Us = efix(E, E_PAIR_SOFT);
+    const double Ub = efix(E, E_BONDED);
+    const double dUdl = L->dhA * Uuv + L->dhB * Us;
+    const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub;
+    const double th = L->theta;
+    double V0, dV0, V1, dV1;
+    opes_bias(t, 0, th, V0, dV0);
+    opes_bias(t, 1, th, V1, dV1);
+    const unsigned long long step = L->step;
+    double thn = th, pn = L->p_theta;
+    if (t.m > 0.0) {
+        const double f = -L->dlam_dtheta * dUdl - dV0 - dV1;
+        double v = pn / t.m + t.dt * f / t.m;
+        thn = th + 0.5 * t.dt * v;
+        double n0, n1, n2;
+        normals3<double>(make_uint4(0u, (unsigned)step, (unsigned)(step >> 32), 1u), t.key, n0, n1, n2);
+        v = t.a_fric * v + sqrt(t.kT * (1.0 - t.a_fric * t.a_fric) / t.m) * n0;
+        thn += 0.5 * t.dt * v;
+        thn -= 2.0 * floor(thn / 2.0);
+        pn = t.m * v;
+    }
+    const unsigned long long stepn = step + 1;
+    if (t.stride > 0 && (stepn % (unsigned long long)t.stride) == 0ull) {
+        double Vd, dVd;
+        opes_bias(t, 0, thn, Vd, dVd);
+        if (t.on[0]) opes_deposit(t, 0, thn, exp(t.beta * Vd));
+        if (t.on[1]) opes_deposit(t, 1, thn, 1.0);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        const double lam = thn <= 1.0 ? thn : 2.0 - thn;
+        double hA, hB, dA, dB;
+        switching_fns(lam, hA, hB, dA, dB);
+        L->theta = thn; L->p_theta = pn; L->lambda = lam;
+        L->dlam_dtheta = thn <= 1.0 ? 1.0 : -1.0;
+        L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
+        L->dUdl = dUdl; L->U = U; L->V_std = V0; L->V_exp = V1;
+        L->step = stepn;
+        if (!isfinite(U) || !isfinite(thn)) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+        if (t.use_cond) {
+            cudaGraphSetConditional(t.cond, s.flags[FL_REBUILD] ? 1u : 0u);
+            if (s.flags[FL_REBUILD]) s.flags[FL_NREBUILD] += 1;
+            s.flags[FL_REBUILD] = 0;
+        }
+    }
+    if (lane < E_N) E[lane] = 0;
+}
+
+template <typename real>
+void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
+{
+    k_theta<real><<<1, 32, 0, st>>>(s, t);
+}
+
+#define LFE_INST_DYN(real)                                                                               \
+    template void launch_set_lambda<real>(const SysView<real>&, double, cudaStream_t);                    \
+    template void launch_eval_out<real>(const SysView<real>&, double*, double*, double, double, double,   \
+                                        cudaStream_t);                                                    \
+    template void launch_assign_positions<real>(const SysView<real>&, const double*, cudaStream_t);        \
+    template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
+    template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
+    template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
+    template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
+LFE_INST_DYN(float)
+LFE_INST_DYN(double)
+
+}  // namespace lfe

@@ -1,0 +1,1118 @@
+// engine.cu -- host side of the library: validation, device buffers, the
+// neighbour-list capacity policy, eager evaluation, the captured per-step
+// CUDA graph (with a device-side conditional node for list rebuilds),
+// checkpoints and the C-ABI entry points declared in include/lfe.h.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+#include <algorithm>
+#include <functional>
+
+#include "lfe.h"
+#include "lfe_views.cuh"
+
+using namespace lfe;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Failure {
+    int code;
+    std::string msg;
+};
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            throw Failure{LFE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};      \
+    } while (0)
+
+[[noreturn]] void fail(int code, const std::string& m) { throw Failure{code, m}; }
+
+bool finite_all(const double* a, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+bool radix_plan(int K, int* rad, int* nrad)
+{
+    int n = 0, k = K;
+    while (k % 4 == 0 && n < 8) { rad[n++] = 4; k /= 4; }
+    while (k % 2 == 0 && n < 8) { rad[n++] = 2; k /= 2; }
+    while (k % 3 == 0 && n < 8) { rad[n++] = 3; k /= 3; }
+    while (k % 5 == 0 && n < 8) { rad[n++] = 5; k /= 5; }
+    *nrad = n;
+    return k == 1;
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+}  // namespace
+
+struct SystemBase {
+    virtual ~SystemBase() {}
+    int precision = 0;
+    virtual void set_positions(const double* pos, int on_device, cudaStream_t st) = 0;
+    virtual void set_velocities(const double* vel) = 0;
+    virtual void set_integrator(double dt, double friction, double temperature) = 0;
+    virtual void build_neighbors(cudaStream_t st) = 0;
+    virtual void eval(double lam, double* forces, double* terms, int out_on_device, cudaStream_t st) = 0;
+    virtual void step(int n, cudaStream_t st) = 0;
+    virtual void get_state(double* pos, double* vel, double* ext) = 0;
+    virtual void checkpoint(const char* path) = 0;
+    virtual void restore(const char* path) = 0;
+    virtual int time_stages(double lam, int reps, cudaStream_t st, const char** names, double* ms, int max_n) = 0;
+    virtual void param_grad(double lam, double* dU, double* d2U) = 0;
+};
+
+struct lfe_system {
+    std::unique_ptr<SystemBase> impl;
+    std::string err;
+};
+
+template <typename real>
+struct System final : SystemBase {
+    lfe_params P{};
+    int n = 0, n_u = 0, n_solv = 0, n_ucl = 0, n_cl = 0, n_pad = 0;
+    std::vector<void*> allocs;
+    SysView<real> S{};
+    NblView<real> N{};
+    ExclView<real> X{};
+    PmeView<real> M{};
+    PmeView<double> M64{};      // FP64 energy branch (FP32 systems only)
+    bool dual = false;
+    BondView<real> B{};
+    StepView<real> G{};
+    ThetaView<real> T{};
+    int pair_warps = 0;
+    int uv_blocks = 0;
+    double const_vv = 0, const_uu = 0, const_uv = 0;
+    cudaStream_t cs = nullptr, cs2 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int* h_flags = nullptr;        // pinned
+    double* d_terms = nullptr;     // [LFE_NTERMS]
+    double* d_fbuf = nullptr;      // [3n] staging for host force output
+    double* d_pos = nullptr;       // [3n] staging for host positions
+    LamState* lam_save = nullptr;
+    std::vector<double> h_mass;
+    int device = 0;
+
+    template <class T2>
+    T2* dalloc(size_t count)
+    {
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        CK(cudaMalloc(&p, count * sizeof(T2)));
+        CK(cudaMemset(p, 0, count * sizeof(T2)));
+        allocs.push_back(p);
+        return static_cast<T2*>(p);
+    }
+    template <class T2>
+    T2* upload(const std::vector<T2>& v)
+    {
+        T2* d = dalloc<T2>(v.size());
+        if (!v.empty()) CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T2), cudaMemcpyHostToDevice));
+        return d;
+    }
+    void dfree(void* p)
+    {
+        auto it = std::find(allocs.begin(), allocs.end(), p);
+        if (it != allocs.end()) { cudaFree(p); allocs.erase(it); }
+    }
+
+    ~System() override
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (void* p : allocs) cudaFree(p);
+        if (h_flags) cudaFreeHost(h_flags);
+        if (cs) cudaStreamDestroy(cs);
+        if (cs2) cudaStreamDestroy(cs2);
+    }
+
+    void create(const lfe_params& p, const lfe_topology& t)
+    {
+        P = p;
+        precision = p.precision;
+        CK(cudaGetDevice(&device));
+        n = t.n_atoms;
+        // ---------------------------------------------------- validation
+        if (n <= 0) fail(LFE_ERR_ARG, "n_atoms must be positive");
+        if (!t.pos || !t.charge || !t.sigma || !t.epsilon || !t.solute || !t.mass)
+            fail(LFE_ERR_ARG, "per-atom arrays must not be NULL");
+        for (int d = 0; d < 3; ++d) {
+            if (!(p.box[d] > 0) || !std::isfinite(p.box[d])) fail(LFE_ERR_ARG, "box lengths must be positive");
+            if (!(p.r_cut <= 0.5 * p.box[d])) fail(LFE_ERR_ARG, "r_cut must not exceed half of every box length");
+            if (p.pme_grid[d] < 8 || p.pme_grid[d] > 128) fail(LFE_ERR_ARG, "pme_grid entries must be in [8, 128]");
+            int rr[8], nr;
+            if (!radix_plan(p.pme_grid[d], rr, &nr)) fail(LFE_ERR_ARG, "pme_grid entries must factor into 2, 3, 5");
+        }
+        if (!(p.r_cut > 0)) fail(LFE_ERR_ARG, "r_cut must be positive");
+        if (p.r_switch >= p.r_cut) fail(LFE_ERR_ARG, "r_switch must be below r_cut (or negative for none)");
+        if (!(p.ewald_alpha > 0)) fail(LFE_ERR_ARG, "ewald_alpha must be positive");
+        if (p.pme_order != 4) fail(LFE_ERR_ARG, "pme_order must be 4");
+        if (p.precision != LFE_FP32_MIXED && p.precision != LFE_FP64) fail(LFE_ERR_ARG, "unknown precision");
+        if (!finite_all(t.pos, 3 * (size_t)n) || !finite_all(t.charge, n) || !finite_all(t.sigma, n) ||
+            !finite_all(t.epsilon, n) || !finite_all(t.mass, n))
+            fail(LFE_ERR_ARG, "non-finite per-atom input");
+        for (int i = 0; i < n; ++i) {
+            if (t.sigma[i] < 0 || t.epsilon[i] < 0) fail(LFE_ERR_ARG, "sigma and epsilon must be >= 0");
+            if (t.mass[i] < 0) fail(LFE_ERR_ARG, "mass must be >= 0");
+        }
+        auto chk_idx = [&](const int* a, long cnt, const char* what) {
+            if (cnt > 0 && !a) fail(LFE_ERR_ARG, std::string(what) + " is NULL");
+            for (long k = 0; k < cnt; ++k)
+                if (a[k] < 0 || a[k] >= n) fail(LFE_ERR_ARG, std::string(what) + " index out of range");
+        };
+        chk_idx(t.excl, 2L * t.n_excl, "excl");
+        chk_idx(t.pairs14, 2L * t.n_14, "pairs14");
+        chk_idx(t.water_OHH, 3L * t.n_waters, "water_OHH");
+        chk_idx(t.constraints, 2L * t.n_constraints, "constraints");
+        chk_idx(t.bonds, 2L * t.n_bonds, "bonds");
+        chk_idx(t.angles, 3L * t.n_angles, "angles");
+        chk_idx(t.torsions, 4L * t.n_torsions, "torsions");
+        if (t.n_excl < 0 || t.n_14 < 0 || t.n_waters < 0 || t.n_constraints < 0 || t.n_bonds < 0 ||
+            t.n_angles < 0 || t.n_torsions < 0)
+            fail(LFE_ERR_ARG, "negative list length");
+        for (int e = 0; e < t.n_excl; ++e)
+            if (t.excl[2 * e] == t.excl[2 * e + 1]) fail(LFE_ERR_ARG, "an exclusion pairs an atom with itself");
+
+        // --------------------------------------------------- atom lists
+        std::vector<int> sl, vl;
+        for (int i = 0; i < n; ++i) (t.solute[i] ? sl : vl).push_back(i);
+        n_u = (int)sl.size();
+        n_solv = (int)vl.size();
+        n_ucl = (n_u + 31) / 32;
+        n_cl = n_ucl + (n_solv + 31) / 32;
+        n_pad = 32 * n_cl;
+
+        // ---------------------------------------------- per-atom buffers
+        std::vector<R4<real>> hx(n), hv(n);
+        std::vector<real> hq(n), hs(n), he(n), hw(n);
+        std::vector<unsigned char> hsol(n);
+        h_mass.assign(t.mass, t.mass + n);
+        for (int i = 0; i < n; ++i) {
+            hx[i] = R4<real>{(real)t.pos[3 * i], (real)t.pos[3 * i + 1], (real)t.pos[3 * i + 2], (real)0};
+            hv[i] = R4<real>{0, 0, 0, 0};
+            hq[i] = (real)t.charge[i];
+            hs[i] = (real)t.sigma[i];
+            he[i] = (real)t.epsilon[i];
+            hw[i] = t.mass[i] > 0 ? (real)(1.0 / t.mass[i]) : (real)0;
+            hsol[i] = t.solute[i] ? 1 : 0;
+        }
+        S.n = n; S.n_pad = n_pad; S.n_cl = n_cl; S.n_ucl = n_ucl; S.n_u = n_u; S.n_solv = n_solv;
+        for (int d = 0; d < 3; ++d) {
+            S.L[d] = (real)p.box[d];
+            S.invL[d] = (real)(1.0 / p.box[d]);
+        }
+        S.rc2 = (real)(p.r_cut * p.r_cut);
+        if (p.r_switch >= 0) {
+            S.rsw = (real)p.r_switch;
+            S.sw_inv_w = (real)(1.0 / (p.r_cut - p.r_switch));
+        } else {
+            S.rsw = (real)p.r_cut;
+            S.sw_inv_w = (real)0;
+        }
+        S.alpha = (real)p.ewald_alpha;
+        S.two_a_sqrtpi = (real)(2.0 * p.ewald_alpha / std::sqrt(PI));
+        S.x = upload(hx);
+        S.v = upload(hv);
+        S.xref = dalloc<R4<real>>(n);
+        S.invm = upload(hw);
+        S.q = upload(hq);
+        S.sig = upload(hs);
+        S.eps = upload(he);
+        S.sol = upload(hsol);
+        S.solute_list = upload(sl);
+        S.solv_list = upload(vl);
+        S.xq = dalloc<R4<real>>(n_pad);
+        S.lj = dalloc<R2<real>>(n_pad);
+        S.perm = dalloc<int>(n_pad);
+        S.iperm = dalloc<int>(n);
+        S.F = dalloc<long long>(3 * (size_t)n_pad);
+        S.E = dalloc<long long>(E_N);
+        S.flags = dalloc<int>(FL_N);
+        S.lam = dalloc<LamState>(1);
+        CK(cudaMallocHost(&h_flags, sizeof(int) * FL_N));
+        d_terms = dalloc<double>(LFE_NTERMS);
+        d_fbuf = dalloc<double>(3 * (size_t)n);
+        d_pos = dalloc<double>(3 * (size_t)n);
+
+        // ---------------------------------------------------- neighbours
+        double skin = p.skin > 0 ? p.skin : 0.1;
+        P.skin = skin;
+        const double V = p.box[0] * p.box[1] * p.box[2];
+        const double rho = std::max(1.0, n / V);
+        const double cell_len = std::cbrt(8.0 / rho);
+        int maxnc = 1;
+        for (int d = 0; d < 3; ++d) {
+            int nc = std::max(1, (int)std::floor(p.box[d] / cell_len));
+            nc = std::min(nc, 1024);
+            N.nc[d] = nc;
+            N.cinv[d] = (real)(nc / p.box[d]);
+            maxnc = std::max(maxnc, nc);
+        }
+        N.bits = 0;
+        while ((1 << N.bits) < maxnc) ++N.bits;
+        N.nkeys = 1 << (3 * N.bits);
+        N.keys = dalloc<int>(n_solv);
+        N.cnt = dalloc<int>(N.nkeys);
+        N.start = dalloc<int>(N.nkeys + 1);
+        N.fill = dalloc<int>(N.nkeys);
+        N.tmp = dalloc<int>(n_solv);
+        N.bbc = dalloc<R4<float>>(n_cl);
+        N.bbh = dalloc<R4<float>>(n_cl);
+        N.tile_cnt = dalloc<int>(n_cl);
+        N.tile_off = dalloc<int>(n_cl + 1);
+        N.cap = 1024;
+        N.tiles = dalloc<int4>(N.cap);
+        N.masks = dalloc<unsigned>((size_t)N.cap * 32);
+        N.cut2 = (float)((p.r_cut + skin) * (p.r_cut + skin));
+        N.skin_half2 = (float)(0.25 * skin * skin);
+        {
+            std::vector<int> cnt(n + 1, 0), lst(2 * (size_t)t.n_excl);
+            for (int e = 0; e < t.n_excl; ++e) { cnt[t.excl[2 * e] + 1]++; cnt[t.excl[2 * e + 1] + 1]++; }
+            for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+            std::vector<int> fillv(n, 0);
+            for (int e = 0; e < t.n_excl; ++e) {
+                int a = t.excl[2 * e], b = t.excl[2 * e + 1];
+                lst[cnt[a] + fillv[a]++] = b;
+                lst[cnt[b] + fillv[b]++] = a;
+            }
+            N.ex_start = upload(cnt);
+            N.ex_list = upload(lst);
+        }
+
+        // ---------------------------------------------------- exclusions
+        {
+            std::vector<int2> ex(t.n_excl), e14(t.n_14);
+            std::vector<R2<real>> s14(t.n_14);
+            for (int e = 0; e < t.n_excl; ++e) ex[e] = make_int2(t.excl[2 * e], t.excl[2 * e + 1]);
+            for (int e = 0; e < t.n_14; ++e) {
+                e14[e] = make_int2(t.pairs14[2 * e], t.pairs14[2 * e + 1]);
+                s14[e] = R2<real>{(real)t.scale14[2 * e], (real)t.scale14[2 * e + 1]};
+            }
+            X.n_excl = t.n_excl;
+            X.n14 = t.n_14;
+            X.excl = upload(ex);
+            X.p14 = upload(e14);
+            X.s14 = upload(s14);
+        }
+
+        // ----------------------------------------------------------- PME
+        {
+            dual = (p.precision == LFE_FP32_MIXED);
+            M.KK = 1;
+            double sv = 0, su = 0;
+            for (int i = 0; i < n; ++i) (t.solute[i] ? su : sv) += t.charge[i] * t.charge[i];
+            const double sc = (su > 0 && sv > 0) ? std::sqrt(sv / su) : 1.0;
+            const double qu_scale = std::exp2(std::round(std::log2(std::max(1.0, sc))));
+            for (int d = 0; d < 3; ++d) {
+                const int K = p.pme_grid[d];
+                M.K[d] = K;
+                M.KK *= K;
+                M.kscale[d] = (real)(K / p.box[d]);
+                radix_plan(K, M.rad[d], &M.nrad[d]);
+                // |b(m)|^2 with the order-4 spline values M4(1) = 1/6, M4(2) = 2/3, M4(3) = 1/6
+                std::vector<double> gf(K), ms(K);
+                std::vector<R2<double>> tw(K);
+                for (int m = 0; m < K; ++m) {
+                    double re = 0, im = 0;
+                    const double mk[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+                    for (int k = 0; k < 3; ++k) {
+                        re += mk[k] * std::cos(2.0 * PI * m * k / K);
+                        im += mk[k] * std::sin(2.0 * PI * m * k / K);
+                    }
+                    const double b2 = 1.0 / (re * re + im * im);
+                    const int mm = (m <= K / 2) ? m : m - K;
+                    const double mr = mm / p.box[d];
+                    gf[m] = std::exp(-PI * PI * mr * mr / (p.ewald_alpha * p.ewald_alpha)) * b2;
+                    ms[m] = mr * mr;
+                    tw[m] = R2<double>{std::cos(2.0 * PI * m / K), std::sin(2.0 * PI * m / K)};
+                }
+                std::vector<real> gfr(K), msr(K);
+                std::vector<R2<real>> twr(K);
+                for (int m = 0; m < K; ++m) {
+                    gfr[m] = (real)gf[m];
+                    msr[m] = (real)ms[m];
+                    twr[m] = R2<real>{(real)tw[m].x, (real)tw[m].y};
+                }
+                M.gfac[d] = upload(gfr);
+                M.msq[d] = upload(msr);
+                M.tw[d] = upload(twr);
+                if (dual) {
+                    M64.K[d] = K;
+                    M64.kscale[d] = K / p.box[d];
+                    M64.nrad[d] = M.nrad[d];
+                    for (int r = 0; r < 8; ++r) M64.rad[d][r] = M.rad[d][r];
+                    M64.gfac[d] = upload(gf);
+                    M64.msq[d] = upload(ms);
+                    M64.tw[d] = upload(tw);
+                }
+            }
+            M.conv_pre = (real)(KE / (PI * V));
+            M.qu_scale = (real)qu_scale;
+            M.Qfix = dalloc<long long>(2 * (size_t)M.KK);
+            M.Z = dalloc<R2<real>>(M.KK);
+            M.phi_u = dalloc<real>(std::max(1, n_u));
+            M.Zraw64 = nullptr;
+            if (dual) {
+                M64.KK = M.KK;
+                M64.conv_pre = KE / (PI * V);
+                M64.qu_scale = qu_scale;
+                M64.Qfix = nullptr;
+                M64.Z = dalloc<R2<double>>(M.KK);
+                M64.phi_u = nullptr;
+                M64.Zraw64 = nullptr;
+                M.Zraw64 = M64.Z;
+            }
+            const int Kmax = std::max(M.K[0], std::max(M.K[1], M.K[2]));
+            const size_t smem = sizeof(R2<double>) * (size_t)(Kmax + 2 * 16 * Kmax);
+            if (smem > 48 * 1024) fail(LFE_ERR_ARG, "PME grid too large for the FFT tile");
+        }
+
+        // ----------------------------------------------- constant energies
+        {
+            double s2[2] = {0, 0}, Q[2] = {0, 0};
+            for (int i = 0; i < n; ++i) {
+                const int c = t.solute[i] ? 1 : 0;
+                s2[c] += t.charge[i] * t.charge[i];
+                Q[c] += t.charge[i];
+            }
+            const double a = p.ewald_alpha;
+            const double self_v = -KE * a / std::sqrt(PI) * s2[0], self_u = -KE * a / std::sqrt(PI) * s2[1];
+            const double pre = -KE * PI / (2.0 * V * a * a);
+            const_vv = self_v + pre * Q[0] * Q[0];
+            const_uu = self_u + pre * Q[1] * Q[1];
+            const_uv = pre * 2.0 * Q[0] * Q[1];
+        }
+
+        // --------------------------------------------------------- bonded
+        {
+            std::vector<int2> bi(t.n_bonds);
+            std::vector<R2<real>> bp(t.n_bonds);
+            for (int e = 0; e < t.n_bonds; ++e) {
+                bi[e] = make_int2(t.bonds[2 * e], t.bonds[2 * e + 1]);
+                bp[e] = R2<real>{(real)t.bond_par[2 * e], (real)t.bond_par[2 * e + 1]};
+            }
+            std::vector<int4> ai(t.n_angles);
+            std::vector<R2<real>> ap(t.n_angles);
+            for (int e = 0; e < t.n_angles; ++e) {
+                ai[e] = make_int4(t.angles[3 * e], t.angles[3 * e + 1], t.angles[3 * e + 2], 0);
+                ap[e] = R2<real>{(real)t.angle_par[2 * e], (real)t.angle_par[2 * e + 1]};
+            }
+            std::vector<int4> ti(t.n_torsions);
+            std::vector<R4<real>> tp(t.n_torsions);
+            for (int e = 0; e < t.n_torsions; ++e) {
+                ti[e] = make_int4(t.torsions[4 * e], t.torsions[4 * e + 1], t.torsions[4 * e + 2], t.torsions[4 * e + 3]);
+                tp[e] = R4<real>{(real)t.torsion_par[3 * e], (real)t.torsion_par[3 * e + 1],
+                                 (real)t.torsion_par[3 * e + 2], (real)0};
+            }
+            B.nb = t.n_bonds; B.na = t.n_angles; B.nt = t.n_torsions;
+            B.b = upload(bi); B.bp = upload(bp);
+            B.a = upload(ai); B.ap = upload(ap);
+            B.t = upload(ti); B.tp = upload(tp);
+        }
+
+        // ---------------------------------------------- constraint groups
+        {
+            std::vector<int> owner(n, -1);
+            std::vector<Group> groups;
+            for (int w = 0; w < t.n_waters; ++w) {
+                Group g{};
+                for (int k = 0; k < 3; ++k) g.atom[k] = t.water_OHH[3 * w + k];
+                g.natom = 3;
+                g.ncons = 3;
+                g.ci[0] = 0; g.cj[0] = 1; g.len[0] = (float)t.water_rOH;
+                g.ci[1] = 0; g.cj[1] = 2; g.len[1] = (float)t.water_rOH;
+                g.ci[2] = 1; g.cj[2] = 2; g.len[2] = (float)t.water_rHH;
+                for (int k = 0; k < 3; ++k) {
+                    if (owner[g.atom[k]] >= 0) fail(LFE_ERR_ARG, "an atom belongs to two rigid waters");
+                    owner[g.atom[k]] = (int)groups.size();
+                }
+                groups.push_back(g);
+            }
+            // star groups: every constraint's first atom is the centre
+            std::vector<int> centre_group(n, -1);
+            for (int c = 0; c < t.n_constraints; ++c) {
+                const int a = t.constraints[2 * c], b = t.constraints[2 * c + 1];
+                if (!(t.constraint_len[c] > 0)) fail(LFE_ERR_ARG, "constraint lengths must be positive");
+                int gi = centre_group[a];
+                if (gi < 0) {
+                    if (owner[a] >= 0) fail(LFE_ERR_ARG, "constraint centre already in another group");
+                    Group g{};
+                    g.atom[0] = a;
+                    g.natom = 1;
+                    g.ncons = 0;
+                    gi = (int)groups.size();
+                    groups.push_back(g);
+                    centre_group[a] = gi;
+                    owner[a] = gi;
+                }
+                Group& g = groups[gi];
+                if (g.natom >= 4 || g.ncons >= 3) fail(LFE_ERR_ARG, "more than 3 constraints share one centre");
+                if (owner[b] >= 0) fail(LFE_ERR_ARG, "a constrained atom belongs to two groups");
+                owner[b] = gi;
+                g.atom[g.natom] = b;
+                g.ci[g.ncons] = 0;
+                g.cj[g.ncons] = g.natom;
+                g.len[g.ncons] = (float)t.constraint_len[c];
+                g.natom++;
+                g.ncons++;
+            }
+            for (int i = 0; i < n; ++i)
+                if (owner[i] < 0) {
+                    Group g{};
+                    g.atom[0] = i;
+                    g.natom = 1;
+                    owner[i] = (int)groups.size();
+                    groups.push_back(g);
+                }
+            G.groups = upload(groups);
+            G.n_groups = (int)groups.size();
+        }
+        G.dt = (real)p.dt;
+        G.a_fric = (real)std::exp(-p.friction * p.dt);
+        G.kT = (real)(KB * p.temperature);
+        G.key = make_uint2((unsigned)(p.seed & 0xffffffffull), (unsigned)(p.seed >> 32));
+        G.skin_half2 = (real)(0.25 * skin * skin);
+
+        // ---------------------------------------------------- theta/OPES
+        T.m = p.lambda_mass;
+        T.dt = p.dt;
+        T.a_fric = std::exp(-p.lambda_friction * p.dt);
+        T.kT = KB * p.temperature;
+        T.stride = p.opes_stride;
+        T.max_k = p.opes_max_kernels > 0 ? p.opes_max_kernels : 1024;
+        T.sigma = p.opes_sigma > 0 ? p.opes_sigma : 0.1;
+        T.beta = 1.0 / (KB * (p.temperature > 0 ? p.temperature : 298.0));
+        const double dE[2] = {p.opes_dE_std, p.opes_dE_exp};
+        for (int b = 0; b < 2; ++b) {
+            T.on[b] = dE[b] > 0 && p.opes_stride > 0;
+            if (T.on[b]) {
+                const double gam = T.beta * dE[b];
+                if (gam <= 1.0) fail(LFE_ERR_ARG, "OPES barrier must exceed k_B T");
+                T.nu[b] = b == 0 ? 1.0 - 1.0 / gam : gam - 1.0;
+                T.epsr[b] = std::exp(-T.beta * dE[b] / T.nu[b]);
+            } else {
+                T.nu[b] = 1.0;
+                T.epsr[b] = 1.0;
+            }
+        }
+        T.centre = dalloc<double>(2 * (size_t)T.max_k);
+        T.weight = dalloc<double>(2 * (size_t)T.max_k);
+        T.S = dalloc<double>(2 * (size_t)T.max_k);
+        T.st = dalloc<OpesState>(1);
+        T.key = G.key;
+        T.const_vv = const_vv;
+        T.const_uu = const_uu;
+        T.const_uv = const_uv;
+        T.use_cond = 0;
+
+        // initial lambda state from theta0
+        {
+            LamState L{};
+            double th = p.theta0 - 2.0 * std::floor(p.theta0 / 2.0);
+            L.theta = th;
+            L.dlam_dtheta = th <= 1.0 ? 1.0 : -1.0;
+            L.lambda = th <= 1.0 ? th : 2.0 - th;
+            CK(cudaMemcpy(S.lam, &L, sizeof(L), cudaMemcpyHostToDevice));
+            launch_set_lambda(S, L.lambda, nullptr);
+            lam_save = dalloc<LamState>(1);
+        }
+        int nsm = 148;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+        pair_warps = nsm * 16;
+        uv_blocks = nsm * 2;
+        {
+            const char* ev = std::getenv("LFE_EAGER_STEPS");
+            eager = ev && ev[0] == '1';
+        }
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+        build_neighbors(nullptr);
+        CK(cudaStreamSynchronize(nullptr));
+        {
+            // mass-weighted zero velocities; theta at rest
+        }
+    }
+
+    void check_flags(cudaStream_t st)
+    {
+        CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const int e = h_flags[FL_ERROR];
+        if (e) {
+            int zero = 0;
+            CK(cudaMemcpy(S.flags + FL_ERROR, &zero, sizeof(int), cudaMemcpyHostToDevice));
+            if (e & ERRB_OVERFLOW) fail(LFE_ERR_OVERFLOW, "neighbour-list capacity exceeded");
+            if (e & ERRB_NONFINITE) fail(LFE_ERR_NONFINITE, "non-finite force, energy or position");
+            if (e & ERRB_CONSTRAINT) fail(LFE_ERR_NONFINITE, "constraint iteration did not converge");
+        }
+    }
+
+    void invalidate_graph()
+    {
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+    }
+
+    void grow_tiles(int need)
+    {
+        dfree(N.tiles);
+        dfree(N.masks);
+        N.cap = need + 256;
+        N.tiles = dalloc<int4>(N.cap);
+        N.masks = dalloc<unsigned>((size_t)N.cap * 32);
+        invalidate_graph();
+    }
+
+    void build_neighbors(cudaStream_t st) override
+    {
+        launch_build_nbl(S, N, st);
+        CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (h_flags[FL_NTILES] > N.cap) {
+            grow_tiles(2 * h_flags[FL_NTILES]);
+            int zero = 0;
+            CK(cudaMemcpy(S.flags + FL_ERROR, &zero, sizeof(int), cudaMemcpyHostToDevice));
+            launch_build_nbl(S, N, st);
+            check_flags(st);
+        }
+        CK(cudaGetLastError());
+    }
+
+    void set_positions(const double* pos, int on_device, cudaStream_t st) override
+    {
+        if (!pos) fail(LFE_ERR_ARG, "pos is NULL");
+        if (!on_device) {
+            if (!finite_all(pos, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
+            CK(cudaMemcpyAsync(d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+            launch_assign_positions(S, d_pos, st);
+        } else {
+            launch_assign_positions(S, pos, st);
+        }
+        build_neighbors(st);
+    }
+
+    void set_integrator(double dt, double friction, double temperature) override
+    {
+        if (!(dt > 0) || !(friction >= 0) || !(temperature >= 0) || !std::isfinite(dt) || !std::isfinite(friction) ||
+            !std::isfinite(temperature))
+            fail(LFE_ERR_ARG, "dt must be > 0, friction and temperature >= 0");
+        CK(cudaDeviceSynchronize());
+        if (exec) recover_overflow(nullptr);
+        P.dt = dt;
+        P.friction = friction;
+        P.temperature = temperature;
+        G.dt = (real)dt;
+        G.a_fric = (real)std::exp(-friction * dt);
+        G.kT = (real)(KB * temperature);
+        T.dt = dt;
+        T.a_fric = std::exp(-P.lambda_friction * dt);
+        T.kT = KB * temperature;
+        invalidate_graph();
+    }
+
+    void set_velocities(const double* vel) override
+    {
+        if (!vel) fail(LFE_ERR_ARG, "vel is NULL");
+        std::vector<R4<real>> hv(n);
+        for (int i = 0; i < n; ++i)
+            hv[i] = R4<real>{(real)vel[3 * i], (real)vel[3 * i + 1], (real)vel[3 * i + 2], (real)0};
+        CK(cudaMemcpy(S.v, hv.data(), sizeof(R4<real>) * n, cudaMemcpyHostToDevice));
+    }
+
+    void eval_kernels(cudaStream_t st)
+    {
+        launch_pairs(S, N, pair_warps, st);
+        launch_uv_energy(S, N, uv_blocks, st);
+        launch_pme(S, M, dual ? &M64 : nullptr, st);
+        launch_excl(S, X, st);
+        launch_bonded(S, B, st);
+    }
+
+    void eval(double lam, double* forces, double* terms, int out_on_device, cudaStream_t st) override
+    {
+        if (!(lam >= 0.0 && lam <= 1.0)) fail(LFE_ERR_ARG, "lambda must be in [0, 1]");
+        if (exec) recover_overflow(st);
+        // the dynamics' lambda state is saved and put back: an evaluation at
+        // an arbitrary lambda does not move theta
+        CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
+        launch_set_lambda(S, lam, st);
+        eval_kernels(st);
+        double* fdst = forces ? (out_on_device ? forces : d_fbuf) : nullptr;
+        double* tdst = terms ? (out_on_device ? terms : d_terms) : nullptr;
+        launch_eval_out(S, fdst, tdst, const_vv, const_uu, const_uv, st);
+        CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
+        CK(cudaGetLastError());
+        if (!out_on_device) {
+            if (forces) CK(cudaMemcpyAsync(forces, d_fbuf, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+            if (terms) CK(cudaMemcpyAsync(terms, d_terms, sizeof(double) * LFE_NTERMS, cudaMemcpyDeviceToHost, st));
+        }
+        check_flags(st);
+    }
+
+    void capture_step_graph()
+    {
+        cudaStream_t s0 = cs;
+        CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        ThetaView<real> Tc = T;
+        Tc.cond = h;
+        Tc.use_cond = 1;
+        eval_kernels(s0);
+        launch_integrate(S, G, s0);
+        launch_theta(S, Tc, s0);
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_build_nbl(S, N, cs2);
+        cudaGraph_t body_out = nullptr;
+        CK(cudaStreamEndCapture(cs2, &body_out));
+        CK(cudaStreamEndCapture(s0, &graph));
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+    }
+
+    // steps requested through lfe_step since creation, and launches since
+    // the last overflow check
+    unsigned long long steps_requested = 0;
+    int since_check = 0;
+    unsigned long long step_base = 0;     // LamState step counter at creation / restore
+
+    // eager stepping (environment LFE_EAGER_STEPS=1): the same kernels as the
+    // captured graph, launched one by one, with the rebuild decided on the
+    // host after every step.  Used for per-kernel profiling (profilers do not
+    // attribute kernels inside graphs that hold conditional nodes).
+    bool eager = false;
+
+    void step_eager(cudaStream_t st)
+    {
+        eval_kernels(st);
+        launch_integrate(S, G, st);
+        launch_theta(S, T, st);
+        CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (h_flags[FL_REBUILD]) {
+            int v[2] = {0, h_flags[FL_NREBUILD] + 1};
+            CK(cudaMemcpy(S.flags + FL_REBUILD, &v[0], sizeof(int), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(S.flags + FL_NREBUILD, &v[1], sizeof(int), cudaMemcpyHostToDevice));
+            build_neighbors(st);
+        }
+    }
+
+    void step(int nsteps, cudaStream_t st) override
+    {
+        if (nsteps < 0) fail(LFE_ERR_ARG, "n_steps must be >= 0");
+        if (!(P.dt > 0)) fail(LFE_ERR_STATE, "dt must be positive to step");
+        if (eager) {
+            for (int i = 0; i < nsteps; ++i) step_eager(st);
+            return;
+        }
+        if (!exec) capture_step_graph();
+        for (int i = 0; i < nsteps; ++i) {
+            CK(cudaGraphLaunch(exec, st));
+            ++steps_requested;
+            if (++since_check >= 64) recover_overflow(st);
+        }
+    }
+
+    // A rebuild inside the graph that overflowed the tile capacity sets the
+    // overflow bit; every later step is a no-op.  Here (every 64 steps and at
+    // every synchronising call) the host grows the capacity, rebuilds the
+    // list, recaptures the graph and replays the skipped steps.
+    void recover_overflow(cudaStream_t st)
+    {
+        since_check = 0;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (!(h_flags[FL_ERROR] & ERRB_OVERFLOW)) return;
+            LamState L;
+            CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
+            const unsigned long long done = L.step - step_base;
+            const long long missing = (long long)steps_requested - (long long)done;
+            grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2);
+            int clr[2] = {0, 0};
+            CK(cudaMemcpy(S.flags, clr, sizeof(clr), cudaMemcpyHostToDevice));
+            build_neighbors(st);
+            capture_step_graph();
+            for (long long i = 0; i < missing; ++i) CK(cudaGraphLaunch(exec, st));
+        }
+        fail(LFE_ERR_OVERFLOW, "neighbour-list capacity kept overflowing");
+    }
+
+    void get_state(double* pos, double* vel, double* ext) override
+    {
+        CK(cudaDeviceSynchronize());
+        if (exec) recover_overflow(nullptr);
+        check_flags(nullptr);
+        if (pos || vel) {
+            std::vector<R4<real>> hx(n);
+            if (pos) {
+                CK(cudaMemcpy(hx.data(), S.x, sizeof(R4<real>) * n, cudaMemcpyDeviceToHost));
+                for (int i = 0; i < n; ++i) { pos[3 * i] = hx[i].x; pos[3 * i + 1] = hx[i].y; pos[3 * i + 2] = hx[i].z; }
+            }
+            if (vel) {
+                CK(cudaMemcpy(hx.data(), S.v, sizeof(R4<real>) * n, cudaMemcpyDeviceToHost));
+                for (int i = 0; i < n; ++i) { vel[3 * i] = hx[i].x; vel[3 * i + 1] = hx[i].y; vel[3 * i + 2] = hx[i].z; }
+            }
+        }
+        if (ext) {
+            LamState L;
+            OpesState O;
+            CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
+            CK(cudaMemcpy(&O, T.st, sizeof(O), cudaMemcpyDeviceToHost));
+            ext[0] = L.theta; ext[1] = L.p_theta; ext[2] = L.lambda; ext[3] = L.dUdl; ext[4] = L.U;
+            ext[5] = O.n[0]; ext[6] = O.n[1]; ext[7] = (double)L.step;
+            int nreb = 0;
+            CK(cudaMemcpy(&nreb, S.flags + FL_NREBUILD, sizeof(int), cudaMemcpyDeviceToHost));
+            ext[8] = nreb;
+        }
+    }
+
+    // checkpoint layout: header | x | v | xref | LamState | OpesState | centre | weight | S | checksum
+    struct CkHeader {
+        char magic[8];
+        int version, precision, n, max_k;
+    };
+
+    void checkpoint(const char* path) override
+    {
+        CK(cudaDeviceSynchronize());
+        check_flags(nullptr);
+        CkHeader h{};
+        std::memcpy(h.magic, "LFECKPT1", 8);
+        h.version = 1;
+        h.precision = precision;
+        h.n = n;
+        h.max_k = T.max_k;
+        std::vector<unsigned char> buf;
+        auto put = [&](const void* p, size_t sz) {
+            const unsigned char* c = static_cast<const unsigned char*>(p);
+            buf.insert(buf.end(), c, c + sz);
+        };
+        auto put_dev = [&](const void* d, size_t sz) {
+            std::vector<unsigned char> tmp(sz);
+            CK(cudaMemcpy(tmp.data(), d, sz, cudaMemcpyDeviceToHost));
+            put(tmp.data(), sz);
+        };
+        put(&h, sizeof(h));
+        put_dev(S.x, sizeof(R4<real>) * n);
+        put_dev(S.v, sizeof(R4<real>) * n);
+        put_dev(S.xref, sizeof(R4<real>) * n);
+        put_dev(S.lam, sizeof(LamState));
+        put_dev(T.st, sizeof(OpesState));
+        put_dev(T.centre, sizeof(double) * 2 * T.max_k);
+        put_dev(T.weight, sizeof(double) * 2 * T.max_k);
+        put_dev(T.S, sizeof(double) * 2 * T.max_k);
+        uint64_t cs_ = fnv1a(buf.data(), buf.size());
+        put(&cs_, sizeof(cs_));
+        FILE* f = std::fopen(path, "wb");
+        if (!f) fail(LFE_ERR_ARG, std::string("cannot open ") + path);
+        size_t w = std::fwrite(buf.data(), 1, buf.size(), f);
+        std::fclose(f);
+        if (w != buf.size()) fail(LFE_ERR_ARG, "short write");
+    }
+
+    void restore(const char* path) override
+    {
+        FILE* f = std::fopen(path, "rb");
+        if (!f) fail(LFE_ERR_ARG, std::string("cannot open ") + path);
+        std::vector<unsigned char> buf;
+        unsigned char tmp[65536];
+        size_t r;
+        while ((r = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
+        std::fclose(f);
+        const size_t body = sizeof(CkHeader) + 3 * sizeof(R4<real>) * n + sizeof(LamState) + sizeof(OpesState) +
+                            3 * sizeof(double) * 2 * T.max_k;
+        if (buf.size() != body + sizeof(uint64_t)) fail(LFE_ERR_ARG, "checkpoint size does not match this system");
+        uint64_t stored;
+        std::memcpy(&stored, buf.data() + body, sizeof(stored));
+        if (stored != fnv1a(buf.data(), body)) fail(LFE_ERR_ARG, "checkpoint checksum mismatch");
+        CkHeader h;
+        std::memcpy(&h, buf.data(), sizeof(h));
+        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 1 || h.precision != precision || h.n != n ||
+            h.max_k != T.max_k)
+            fail(LFE_ERR_ARG, "checkpoint header does not match this system");
+        size_t off = sizeof(CkHeader);
+        auto get_dev = [&](void* d, size_t sz) {
+            CK(cudaMemcpy(d, buf.data() + off, sz, cudaMemcpyHostToDevice));
+            off += sz;
+        };
+        const unsigned char* px = buf.data() + off;
+        (void)px;
+        // rebuild the list from the saved reference positions so that the
+        // tile list (and every rounding downstream of it) is the same as in
+        // the run that wrote the checkpoint; then install the current x
+        std::vector<unsigned char> xcur(buf.begin() + off, buf.begin() + off + sizeof(R4<real>) * n);
+        off += sizeof(R4<real>) * n;
+        get_dev(S.v, sizeof(R4<real>) * n);
+        get_dev(S.x, sizeof(R4<real>) * n);   // xref -> x for the build
+        get_dev(S.lam, sizeof(LamState));
+        get_dev(T.st, sizeof(OpesState));
+        get_dev(T.centre, sizeof(double) * 2 * T.max_k);
+        get_dev(T.weight, sizeof(double) * 2 * T.max_k);
+        get_dev(T.S, sizeof(double) * 2 * T.max_k);
+        int zero[FL_N] = {0, 0, 0, 0};
+        CK(cudaMemcpy(S.flags, zero, sizeof(int) * 2, cudaMemcpyHostToDevice));
+        build_neighbors(nullptr);
+        CK(cudaMemcpy(S.x, xcur.data(), xcur.size(), cudaMemcpyHostToDevice));
+        refresh_sorted(nullptr);
+        CK(cudaDeviceSynchronize());
+        LamState L;
+        CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
+        step_base = L.step;
+        steps_requested = 0;
+    }
+
+    // recompute the sorted coordinates from x in the current slot order
+    void refresh_sorted(cudaStream_t st)
+    {
+        launch_refresh_sorted(S, st);
+        CK(cudaStreamSynchronize(st));
+    }
+
+    int time_stages(double lam, int reps, cudaStream_t st, const char** names, double* ms, int max_n) override
+    {
+        static const char* stage_names[] = {"nbl_build", "pairs", "pme_spread", "pme_fft_fwd", "pme_conv",
+                                            "pme_fft_inv", "pme_gather", "excl_14", "bonded", "eval_out",
+                                            "uv_energy_fp64"};
+        const int ns = 11;
+        std::vector<cudaEvent_t> ev(ns + 1);
+        for (auto& e : ev) CK(cudaEventCreate(&e));
+        std::vector<double> acc(ns, 0.0);
+        CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
+        launch_set_lambda(S, lam, st);
+        for (int r = 0; r < reps; ++r) {
+            CK(cudaEventRecord(ev[0], st));
+            launch_build_nbl(S, N, st);
+            CK(cudaEventRecord(ev[1], st));
+            launch_pairs(S, N, pair_warps, st);
+            CK(cudaEventRecord(ev[2], st));
+            launch_uv_energy(S, N, uv_blocks, st);
+            CK(cudaEventRecord(ev[11], st));
+            launch_spread(S, M, st);
+            CK(cudaEventRecord(ev[3], st));
+            launch_fft(M, 2, +1, 1, st);
+            if (dual) {
+                launch_fft(M64, 2, +1, 0, st);
+                launch_fft(M64, 1, +1, 0, st);
+                launch_fft(M64, 0, +1, 0, st);
+                launch_conv(M64, S.E, S.lam, CONV_ENERGY, st);
+            }
+            launch_fft(M, 1, +1, 0, st);
+            launch_fft(M, 0, +1, 0, st);
+            CK(cudaEventRecord(ev[4], st));
+            launch_conv(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, st);
+            CK(cudaEventRecord(ev[5], st));
+            launch_fft(M, 0, -1, 0, st);
+            launch_fft(M, 1, -1, 0, st);
+            launch_fft(M, 2, -1, 0, st);
+            CK(cudaEventRecord(ev[6], st));
+            launch_gather(S, M, st);
+            CK(cudaEventRecord(ev[7], st));
+            launch_excl(S, X, st);
+            CK(cudaEventRecord(ev[8], st));
+            launch_bonded(S, B, st);
+            CK(cudaEventRecord(ev[9], st));
+            launch_eval_out(S, nullptr, nullptr, const_vv, const_uu, const_uv, st);
+            CK(cudaEventRecord(ev[10], st));
+            CK(cudaEventSynchronize(ev[10]));
+            // stage k runs from ev[k] to ev[k+1], except that the FP64
+            // solute-solvent energy kernel (stage 10) sits between ev[2] and
+            // ev[11], and the spread stage starts at ev[11]
+            for (int k = 0; k < 10; ++k) {
+                float t = 0;
+                CK(cudaEventElapsedTime(&t, k == 2 ? ev[11] : ev[k], ev[k + 1]));
+                acc[k] += t;
+            }
+            float tu = 0;
+            CK(cudaEventElapsedTime(&tu, ev[2], ev[11]));
+            acc[10] += tu;
+        }
+        CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
+        for (auto& e : ev) cudaEventDestroy(e);
+        check_flags(st);
+        const int m = std::min(ns, max_n);
+        for (int k = 0; k < m; ++k) {
+            if (names) names[k] = stage_names[k];
+            if (ms) ms[k] = reps > 0 ? acc[k] / reps : 0.0;
+        }
+        return m;
+    }
+
+    void param_grad(double, double*, double*) override
+    {
+        fail(LFE_ERR_STATE, "parameter gradients are not available in this build");
+    }
+};
+
+// ---------------------------------------------------------------- C-ABI
+namespace {
+int guard(lfe_system* sys, const std::function<void()>& f)
+{
+    if (!sys) return LFE_ERR_ARG;
+    try {
+        f();
+        sys->err.clear();
+        return LFE_OK;
+    } catch (const Failure& e) {
+        sys->err = e.msg;
+        return e.code;
+    } catch (const std::exception& e) {
+        sys->err = e.what();
+        return LFE_ERR_ARG;
+    }
+}
+}  // namespace
+
+extern "C" {
+
+int lfe_create(const lfe_params* params, const lfe_topology* topo, lfe_system** out)
+{
+    if (out) *out = nullptr;
+    if (!params || !topo || !out) {
+        g_create_error = "NULL argument";
+        return LFE_ERR_ARG;
+    }
+    auto sys = new lfe_system();
+    try {
+        if (params->precision == LFE_FP64) {
+            auto s = new System<double>();
+            sys->impl.reset(s);
+            s->create(*params, *topo);
+        } else {
+            auto s = new System<float>();
+            sys->impl.reset(s);
+            s->create(*params, *topo);
+        }
+    } catch (const Failure& e) {
+        g_create_error = e.msg;
+        delete sys;
+        return e.code;
+    } catch (const std::exception& e) {
+        g_create_error = e.what();
+        delete sys;
+        return LFE_ERR_ARG;
+    }
+    g_create_error.clear();
+    *out = sys;
+    return LFE_OK;
+}
+
+int lfe_set_positions(lfe_system* sys, const double* pos, int on_device, void* stream)
+{
+    return guard(sys, [&] { sys->impl->set_positions(pos, on_device, (cudaStream_t)stream); });
+}
+
+int lfe_set_velocities(lfe_system* sys, const double* vel)
+{
+    return guard(sys, [&] { sys->impl->set_velocities(vel); });
+}
+
+int lfe_set_integrator(lfe_system* sys, double dt, double friction, double temperature)
+{
+    return guard(sys, [&] { sys->impl->set_integrator(dt, friction, temperature); });
+}
+
+int lfe_build_neighbors(lfe_system* sys, void* stream)
+{
+    return guard(sys, [&] { sys->impl->build_neighbors((cudaStream_t)stream); });
+}
+
+int lfe_eval(lfe_system* sys, double lambda, double* forces, double* energy_terms, int out_on_device, void* stream)
+{
+    return guard(sys, [&] { sys->impl->eval(lambda, forces, energy_terms, out_on_device, (cudaStream_t)stream); });
+}
+
+int lfe_param_grad(lfe_system* sys, double lambda, double* dU_dp, double* d2U_dl_dp)
+{
+    return guard(sys, [&] { sys->impl->param_grad(lambda, dU_dp, d2U_dl_dp); });
+}
+
+int lfe_step(lfe_system* sys, int n_steps, void* stream)
+{
+    return guard(sys, [&] { sys->impl->step(n_steps, (cudaStream_t)stream); });
+}
+
+int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext)
+{
+    return guard(sys, [&] { sys->impl->get_state(pos, vel, ext); });
+}
+
+int lfe_checkpoint(lfe_system* sys, const char* path)
+{
+    return guard(sys, [&] {
+        if (!path) fail(LFE_ERR_ARG, "path is NULL");
+        sys->impl->checkpoint(path);
+    });
+}
+
+int lfe_restore(lfe_system* sys, const char* path)
+{
+    return guard(sys, [&] {
+        if (!path) fail(LFE_ERR_ARG, "path is NULL");
+        sys->impl->restore(path);
+    });
+}
+
+int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream, const char** names, double* ms,
+                    int max_n)
+{
+    int r = 0;
+    int rc = guard(sys, [&] { r = sys->impl->time_stages(lambda, reps, (cudaStream_t)stream, names, ms, max_n); });
+    return rc == LFE_OK ? r : rc;
+}
+
+int lfe_batch_create(lfe_system* const*, int, lfe_batch** out)
+{
+    if (out) *out = nullptr;
+    g_create_error = "batched replicas are not available in this build";
+    return LFE_ERR_STATE;
+}
+
+int lfe_batch_eval(lfe_batch*, const double*, double*, void*) { return LFE_ERR_STATE; }
+int lfe_batch_step(lfe_batch*, int, void*) { return LFE_ERR_STATE; }
+void lfe_batch_destroy(lfe_batch*) {}
+
+const char* lfe_last_error(const lfe_system* sys)
+{
+    if (!sys) return g_create_error.c_str();
+    return sys->err.c_str();
+}
+
+void lfe_destroy(lfe_system* sys) { delete sys; }
+
+}  // extern "C"
+
+template struct System<float>;
+template struct System<double>;

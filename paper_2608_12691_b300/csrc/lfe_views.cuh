@@ -1,0 +1,163 @@
+// lfe_views.cuh -- plain-pointer views of a system's device buffers, passed
+// by value to kernels, and the host-side launcher declarations.
+#pragma once
+#include "lfe_dev.cuh"
+
+namespace lfe {
+
+template <typename real>
+struct SysView {
+    int n;          // atoms
+    int n_pad;      // cluster slots (n_cl * 32)
+    int n_cl;       // clusters
+    int n_ucl;      // solute clusters (they come first)
+    int n_u;        // solute atoms
+    int n_solv;     // solvent atoms
+    real L[3], invL[3];
+    real rc2;       // r_cut^2
+    real rsw;       // LJ switch start (r_cut when there is no switch)
+    real sw_inv_w;  // 1 / (r_cut - r_switch)
+    real alpha;     // Ewald alpha
+    real two_a_sqrtpi;
+    // master state, caller order
+    R4<real>* x;
+    R4<real>* v;
+    R4<real>* xref;     // positions at the last neighbour-list build
+    real* invm;
+    const real* q;      // charges (e)
+    const real* sig;
+    const real* eps;
+    const unsigned char* sol;
+    const int* solute_list;   // solute atoms, caller order
+    const int* solv_list;     // solvent atoms, caller order
+    // cluster-sorted arrays
+    R4<real>* xq;       // wrapped x, y, z and sqrt(k_e) q
+    R2<real>* lj;       // sigma/2, 2 sqrt(eps)
+    int* perm;          // slot -> atom (-1 = padding)
+    int* iperm;         // atom -> slot
+    long long* F;       // fixed-point forces [3][n_pad]
+    long long* E;       // energy accumulators [E_N]
+    int* flags;         // [FL_N]
+    LamState* lam;
+};
+
+template <typename real>
+struct NblView {
+    int nc[3];            // cells per axis
+    int bits;             // Morton bits per axis
+    int nkeys;            // 1 << (3 bits)
+    real cinv[3];         // cells per nm
+    int* keys;            // [n_solv]
+    int* cnt;             // [nkeys]
+    int* start;           // [nkeys + 1]
+    int* fill;            // [nkeys]
+    int* tmp;             // [n_solv] solvent atoms in cell order
+    R4<float>* bbc;       // cluster bounding-box centres [n_cl]
+    R4<float>* bbh;       // half extents [n_cl]
+    int* tile_cnt;        // [n_cl]
+    int* tile_off;        // [n_cl + 1]
+    int4* tiles;          // [cap]  (I, J, shift code, class)
+    unsigned* masks;      // [cap * 32]
+    int cap;
+    float cut2;           // (r_cut + skin)^2
+    float skin_half2;     // (skin / 2)^2
+    const int* ex_start;  // exclusion CSR, caller order [n + 1]
+    const int* ex_list;
+};
+
+template <typename real>
+struct ExclView {
+    int n_excl, n14;
+    const int2* excl;       // caller-order pairs
+    const int2* p14;
+    const R2<real>* s14;    // (s_LJ, s_C)
+};
+
+template <typename real>
+struct PmeView {
+    int K[3];
+    int KK;                   // K0 K1 K2
+    real kscale[3];           // K_d / L_d
+    long long* Qfix;          // [2][KK]  (solvent, solute) fixed point
+    R2<real>* Z;              // [KK] complex work grid
+    const real* gfac[3];      // per-axis exp(-pi^2 m^2 / (L^2 alpha^2)) * |b(m)|^2
+    const real* msq[3];       // per-axis (m_d / L_d)^2
+    real conv_pre;            // k_e / (pi V)
+    real qu_scale;            // power of two applied to the solute grid in the packed transform
+    const R2<real>* tw[3];    // twiddles exp(+2 pi i t / K_d)
+    int nrad[3];
+    int rad[3][8];
+    real* phi_u;              // [n_u] reciprocal potential of the other class at solute atoms
+    R2<double>* Zraw64;       // optional: FP64 copy of the packed charge grid written by the first pass
+};
+
+template <typename real>
+struct BondView {
+    int nb, na, nt;
+    const int2* b;  const R2<real>* bp;
+    const int4* a;  const R2<real>* ap;     // a.w unused
+    const int4* t;  const R4<real>* tp;     // (k, n, phi0, -)
+};
+
+// constraint groups: a rigid water (3 atoms, 3 constraints), a star of
+// X-H constraints around a centre atom, or a single unconstrained atom
+struct Group {
+    int atom[4];
+    int natom;
+    int ncons;
+    int ci[3], cj[3];     // constraint k joins atom[ci[k]] and atom[cj[k]]
+    float len[3];
+};
+
+template <typename real>
+struct StepView {
+    const Group* groups;
+    int n_groups;
+    real dt, a_fric, kT;       // a = exp(-gamma dt)
+    uint2 key;
+    real skin_half2;
+};
+
+template <typename real>
+struct ThetaView {
+    double m, dt, a_fric, kT;
+    int stride;
+    int max_k;
+    int on[2];              // biases enabled
+    double beta, nu[2], epsr[2], sigma;
+    double* centre;         // [2][max_k]
+    double* weight;         // [2][max_k]
+    double* S;              // [2][max_k]  unnormalised KDE at each centre
+    OpesState* st;
+    uint2 key;
+    double const_uv;        // background share of U_uv (constant)
+    double const_vv, const_uu;
+    cudaGraphConditionalHandle cond;
+    int use_cond;
+};
+
+// ------------------------------------------------------------- launchers
+template <typename real> void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st);
+template <typename real> void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st);
+template <typename real> void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nblocks, cudaStream_t st);
+template <typename real> void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t st);
+template <typename real> void launch_pme(const SysView<real>& s, const PmeView<real>& p,
+                                         const PmeView<double>* energy64, cudaStream_t st);
+template <typename real> void launch_spread(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st);
+template <typename real> void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st);
+// mode: CONV_BOTH energies + potentials, CONV_ENERGY energies only, CONV_POTENTIAL potentials only
+enum { CONV_BOTH = 0, CONV_ENERGY = 1, CONV_POTENTIAL = 2 };
+template <typename real> void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode,
+                                          cudaStream_t st);
+template <typename real> void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st);
+template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
+template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
+template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+template <typename real> void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st);
+template <typename real> void launch_eval_out(const SysView<real>& s, double* forces, double* terms,
+                                              double const_vv, double const_uu, double const_uv,
+                                              cudaStream_t st);
+template <typename real> void launch_assign_positions(const SysView<real>& s, const double* pos, cudaStream_t st);
+template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
+
+}  // namespace lfe

@@ -1,0 +1,439 @@
+// pme.cu -- smooth particle-mesh Ewald with the solute/solvent class split.
+//
+// Essmann et al. (1995), cited for PME in Section 2.6: order-4 cardinal
+// B-spline charge spreading, a 3-D transform, multiplication by the influence
+// function G(m) = k_e exp(-pi^2 m^2/alpha^2) B(m) / (pi V m^2), and force
+// interpolation with the B-spline derivatives.  The solvent grid Q_v and the
+// solute grid Q_u are packed into one complex grid Z = Q_v + i Q_u, so one
+// complex transform serves both classes; the convolution separates them
+// again, forms E_vv, E_uu and E_uv (Eq. 4 basis split of the reciprocal
+// energy), and packs the two class potentials the forces need,
+//   solvent atoms: phi_v + h_A phi_u,   solute atoms: phi_u + h_A phi_v,
+// into one complex grid for the single inverse transform.
+#include "lfe_views.cuh"
+
+namespace lfe {
+
+__device__ __forceinline__ float floor_p(float x) { return floorf(x); }
+__device__ __forceinline__ double floor_p(double x) { return floor(x); }
+
+// order-4 B-spline weights M4(w + j), j = 0..3, for the grid points f - j
+// (closed form of the cardinal B-spline on its four unit intervals), and
+// their derivatives with respect to w
+template <typename real>
+__device__ __forceinline__ void bspline4(real w, real th[4], real dth[4])
+{
+    const real w2 = w * w, w3 = w2 * w, o = (real)1 - w;
+    const real s = (real)1 / (real)6;
+    th[0] = s * w3;
+    th[1] = s * ((real)-3 * w3 + (real)3 * w2 + (real)3 * w + (real)1);
+    th[2] = s * ((real)3 * w3 - (real)6 * w2 + (real)4);
+    th[3] = s * o * o * o;
+    dth[0] = (real)0.5 * w2;
+    dth[1] = (real)0.5 * ((real)-3 * w2 + (real)2 * w + (real)1);
+    dth[2] = (real)0.5 * ((real)3 * w2 - (real)4 * w);
+    dth[3] = (real)-0.5 * o * o;
+}
+
+// fractional grid coordinate: integer base f in [0, K) and offset w in
+// [0, 1); the product x K/L is formed in double.  Any input (also a
+// coordinate far outside the box, or NaN) yields an in-range base, so a
+// diverging trajectory can never index outside the grid.
+template <typename real, typename wreal>
+__device__ __forceinline__ void grid_coord(real x, double ks, int K, int& f, wreal& w)
+{
+    double u = (double)x * ks;
+    u -= (double)K * floor(u / (double)K);
+    if (!(u >= 0.0 && u < (double)K)) u = 0.0;
+    const double fl = floor(u);
+    f = min(max((int)fl, 0), K - 1);
+    w = (wreal)(u - fl);
+}
+
+__device__ __forceinline__ int wrapk(int k, int K) { return k < 0 ? k + K : (k >= K ? k - K : k); }
+
+template <typename real>
+__global__ void k_spread(SysView<real> s, PmeView<real> p)
+{
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s.n_pad) return;
+    int a = s.perm[slot];
+    if (a < 0) return;
+    const R4<real> xq = s.xq[slot];
+    const real q = s.q[a];
+    if (q == (real)0) return;
+    long long* grid = p.Qfix + (s.sol[a] ? p.KK : 0);
+    // weights and products in FP64: the fixed-point grid is shared by the
+    // force branch and the FP64 energy branch, whose class energies set
+    // dU/dlambda to 1e-6 relative
+    double th[3][4], dth[4];
+    int f[3];
+    real xs[3] = {xq.x, xq.y, xq.z};
+    for (int d = 0; d < 3; ++d) {
+        double w;
+        grid_coord(xs[d], (double)p.kscale[d], p.K[d], f[d], w);
+        bspline4(w, th[d], dth);
+    }
+    for (int j0 = 0; j0 < 4; ++j0) {
+        const int k0 = wrapk(f[0] - j0, p.K[0]);
+        const double a0 = (double)q * th[0][j0];
+        for (int j1 = 0; j1 < 4; ++j1) {
+            const int k1 = wrapk(f[1] - j1, p.K[1]);
+            const double a1 = a0 * th[1][j1];
+            const int row = (k0 * p.K[1] + k1) * p.K[2];
+            for (int j2 = 0; j2 < 4; ++j2) {
+                const int k2 = wrapk(f[2] - j2, p.K[2]);
+                atomic_add_ll(&grid[row + k2], __double2ll_rn(a1 * th[2][j2] * QSCALE));
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------- FFT
+template <typename real>
+__device__ __forceinline__ R2<real> cmul(R2<real> a, R2<real> b)
+{
+    R2<real> r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename real>
+__device__ __forceinline__ R2<real> cadd(R2<real> a, R2<real> b) { R2<real> r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename real>
+__device__ __forceinline__ R2<real> csub(R2<real> a, R2<real> b) { R2<real> r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// multiply by sign * i
+template <typename real>
+__device__ __forceinline__ R2<real> cmuli(R2<real> a, int sign)
+{
+    R2<real> r;
+    r.x = -(real)sign * a.y;
+    r.y = (real)sign * a.x;
+    return r;
+}
+
+// in-register R-point DFT y_k = sum_n a_n exp(sign 2 pi i n k / R)
+template <typename real>
+__device__ __forceinline__ void dft_small(R2<real>* v, int R, int sign)
+{
+    if (R == 2) {
+        R2<real> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        R2<real> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        R2<real> s13 = cadd(v[1], v[3]), d13 = cmuli(csub(v[1], v[3]), sign);
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    } else if (R == 3) {
+        const real h = (real)0.86602540378443864676;   // sqrt(3)/2
+        R2<real> t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        R2<real> m1;
+        m1.x = v[0].x - (real)0.5 * t1.x;
+        m1.y = v[0].y - (real)0.5 * t1.y;
+        R2<real> m2 = cmuli(t2, sign);
+        m2.x *= h; m2.y *= h;
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(m1, m2);
+        v[2] = csub(m1, m2);
+    } else {  // R == 5
+        const real c1 = (real)0.30901699437494742410, c2 = (real)-0.80901699437494742410;
+        const real s1 = (real)0.95105651629515357212, s2 = (real)0.58778525229247312917;
+        R2<real> a1 = cadd(v[1], v[4]), b1 = csub(v[1], v[4]);
+        R2<real> a2 = cadd(v[2], v[3]), b2 = csub(v[2], v[3]);
+        R2<real> y0 = cadd(v[0], cadd(a1, a2));
+        R2<real> p1, p2, q1, q2;
+        p1.x = v[0].x + c1 * a1.x + c2 * a2.x; p1.y = v[0].y + c1 * a1.y + c2 * a2.y;
+        p2.x = v[0].x + c2 * a1.x + c1 * a2.x; p2.y = v[0].y + c2 * a1.y + c1 * a2.y;
+        q1.x = s1 * b1.x + s2 * b2.x; q1.y = s1 * b1.y + s2 * b2.y;
+        q2.x = s2 * b1.x - s1 * b2.x; q2.y = s2 * b1.y - s1 * b2.y;
+        q1 = cmuli(q1, sign);
+        q2 = cmuli(q2, sign);
+        v[0] = y0;
+        v[1] = cadd(p1, q1);
+        v[4] = csub(p1, q1);
+        v[2] = cadd(p2, q2);
+        v[3] = csub(p2, q2);
+    }
+}
+
+constexpr int FFT_NL = 16;    // lines per block
+
+// One pass of 1-D transforms of length K along AXIS for a block of FFT_NL
+// lines, in shared memory, by the Stockham autosort formulation (radix 2, 3,
+// 4, 5 stages).  AXIS 2 lines are contiguous; AXIS 1 and 0 lines are loaded
+// as FFT_NL contiguous columns.  FROMFIX: the input is the pair of
+// fixed-point charge grids (consumed and zeroed here).
+template <typename real, int AXIS, bool FROMFIX>
+__global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int K = p.K[AXIS];
+    R2<real>* tw = reinterpret_cast<R2<real>*>(smem_raw);
+    R2<real>* b0 = tw + K;
+    R2<real>* b1 = b0 + FFT_NL * K;
+    const int K0 = p.K[0], K1 = p.K[1], K2 = p.K[2];
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    int line0 = 0, fixed_k = 0, c0 = 0, nl = FFT_NL;
+    if (AXIS == 2) {
+        line0 = blockIdx.x * FFT_NL;
+        nl = min(FFT_NL, K0 * K1 - line0);
+    } else {
+        const int ncb = (K2 + FFT_NL - 1) / FFT_NL;
+        fixed_k = blockIdx.x / ncb;
+        c0 = (blockIdx.x % ncb) * FFT_NL;
+        nl = min(FFT_NL, K2 - c0);
+    }
+    for (int t = tid; t < K; t += nt) {
+        R2<real> w = p.tw[AXIS][t];
+        if (sign < 0) w.y = -w.y;
+        tw[t] = w;
+    }
+    auto gidx = [&](int l, int t) -> int {
+        if (AXIS == 2) return (line0 + l) * K2 + t;
+        if (AXIS == 1) return (fixed_k * K1 + t) * K2 + c0 + l;
+        return (t * K1 + fixed_k) * K2 + c0 + l;
+    };
+    for (int e = tid; e < FFT_NL * K; e += nt) {
+        int l, t;
+        if (AXIS == 2) { l = e / K; t = e % K; }
+        else { t = e / FFT_NL; l = e % FFT_NL; }
+        if (l < nl) {
+            const int g = gidx(l, t);
+            R2<real> v;
+            if (FROMFIX) {
+                const double qv = (double)p.Qfix[g] * (1.0 / QSCALE);
+                const double qu = (double)p.Qfix[p.KK + g] * ((double)p.qu_scale / QSCALE);
+                v.x = (real)qv;
+                v.y = (real)qu;
+                p.Qfix[g] = 0;
+                p.Qfix[p.KK + g] = 0;
+                if (p.Zraw64) {
+                    R2<double> w;
+                    w.x = qv;
+                    w.y = qu;
+                    p.Zraw64[g] = w;
+                }
+            } else {
+                v = p.Z[g];
+            }
+            b0[l * K + t] = v;
+        }
+    }
+    __syncthreads();
+    R2<real>* src = b0;
+    R2<real>* dst = b1;
+    int Ns = 1;
+    for (int st = 0; st < p.nrad[AXIS]; ++st) {
+        const int R = p.rad[AXIS][st];
+        const int nbf = K / R;
+        const int tstep = K / (Ns * R);
+        for (int idx = tid; idx < nl * nbf; idx += nt) {
+            const int l = idx / nbf, j = idx % nbf;
+            const int k = j % Ns;
+            const R2<real>* in = src + l * K;
+            R2<real>* out = dst + l * K;
+            R2<real> v[5];
+            v[0] = in[j];
+            for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], tw[(r * k * tstep) % K]);
+            dft_small(v, R, sign);
+            const int base = (j / Ns) * Ns * R + k;
+            for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
+        }
+        __syncthreads();
+        R2<real>* tmp = src; src = dst; dst = tmp;
+        Ns *= R;
+    }
+    for (int e = tid; e < FFT_NL * K; e += nt) {
+        int l, t;
+        if (AXIS == 2) { l = e / K; t = e % K; }
+        else { t = e / FFT_NL; l = e % FFT_NL; }
+        if (l < nl) p.Z[gidx(l, t)] = src[l * K + t];
+    }
+}
+
+template <typename real>
+void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
+{
+    const int K = p.K[axis];
+    const size_t smem = sizeof(R2<real>) * (size_t)(K + 2 * FFT_NL * K);
+    int blocks;
+    if (axis == 2) blocks = (p.K[0] * p.K[1] + FFT_NL - 1) / FFT_NL;
+    else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + FFT_NL - 1) / FFT_NL);
+    if (axis == 2) {
+        if (from_fixed) k_fft<real, 2, true><<<blocks, 256, smem, st>>>(p, sign);
+        else k_fft<real, 2, false><<<blocks, 256, smem, st>>>(p, sign);
+    } else if (axis == 1) {
+        k_fft<real, 1, false><<<blocks, 256, smem, st>>>(p, sign);
+    } else {
+        k_fft<real, 0, false><<<blocks, 256, smem, st>>>(p, sign);
+    }
+}
+
+// ------------------------------------------------------------ convolution
+// CONV_ENERGY: E_vv, E_uu, E_uv only; CONV_POTENTIAL: the packed class
+// potentials only; CONV_BOTH: both.
+template <typename real, int MODE>
+__global__ void k_conv(PmeView<real> p, long long* E, const LamState* lam)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int K0 = p.K[0], K1 = p.K[1], K2 = p.K[2];
+    double evv = 0, euu = 0, euv = 0;
+    if (idx < p.KK) {
+        const int k0 = idx / (K1 * K2), k1 = (idx / K2) % K1, k2 = idx % K2;
+        const int n0 = (K0 - k0) % K0, n1 = (K1 - k1) % K1, n2 = (K2 - k2) % K2;
+        const int nidx = (n0 * K1 + n1) * K2 + n2;
+        if (idx == 0) {
+            if (MODE != CONV_ENERGY) {
+                R2<real> zero;
+                zero.x = zero.y = (real)0;
+                p.Z[0] = zero;
+            }
+        } else if (idx <= nidx) {
+            const R2<real> zm = p.Z[idx], zn = p.Z[nidx];
+            // Z = Q_v + i s Q_u (s = qu_scale, a power of two that brings the
+            // solute spectrum to the solvent's magnitude so that the transform's
+            // rounding is relative to each class):
+            // Q_v(m) = (Z(m) + conj Z(-m)) / 2,  Q_u(m) = (Z(m) - conj Z(-m)) / (2 i s)
+            R2<real> qv, qu;
+            const real hs = (real)0.5 / p.qu_scale;
+            qv.x = (real)0.5 * (zm.x + zn.x);
+            qv.y = (real)0.5 * (zm.y - zn.y);
+            qu.x = hs * (zm.y + zn.y);
+            qu.y = -hs * (zm.x - zn.x);
+            const real msq = p.msq[0][k0] + p.msq[1][k1] + p.msq[2][k2];
+            const real G = p.conv_pre * p.gfac[0][k0] * p.gfac[1][k1] * p.gfac[2][k2] / msq;
+            if (MODE != CONV_POTENTIAL) {
+                const double mult = (idx == nidx) ? 1.0 : 2.0;
+                evv = mult * 0.5 * (double)G * ((double)qv.x * qv.x + (double)qv.y * qv.y);
+                euu = mult * 0.5 * (double)G * ((double)qu.x * qu.x + (double)qu.y * qu.y);
+                euv = mult * (double)G * ((double)qu.x * qv.x + (double)qu.y * qv.y);
+            }
+            if (MODE != CONV_ENERGY) {
+                // W = G [(Q_v + h_A Q_u) + i (Q_u + h_A Q_v)]; at -m the class
+                // spectra are the complex conjugates
+                const real hA = (real)lam->hA;
+                R2<real> P, Rr, wm, wn;
+                P.x = qv.x + hA * qu.x; P.y = qv.y + hA * qu.y;
+                Rr.x = qu.x + hA * qv.x; Rr.y = qu.y + hA * qv.y;
+                wm.x = G * (P.x - Rr.y); wm.y = G * (P.y + Rr.x);
+                wn.x = G * (P.x + Rr.y); wn.y = G * (-P.y + Rr.x);
+                p.Z[idx] = wm;
+                if (nidx != idx) p.Z[nidx] = wn;
+            }
+        }
+    }
+    if (MODE != CONV_POTENTIAL) {
+        long long a0 = __double2ll_rn(warp_sum_d(evv) * ESCALE);
+        long long a1 = __double2ll_rn(warp_sum_d(euu) * ESCALE);
+        long long a2 = __double2ll_rn(warp_sum_d(euv) * ESCALE);
+        if ((threadIdx.x & 31) == 0) {
+            if (a0) atomic_add_ll(&E[E_REC_VV], a0);
+            if (a1) atomic_add_ll(&E[E_REC_UU], a1);
+            if (a2) atomic_add_ll(&E[E_REC_UV], a2);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- gather
+template <typename real>
+__global__ void k_gather(SysView<real> s, PmeView<real> p)
+{
+    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= s.n_pad) return;
+    int a = s.perm[slot];
+    if (a < 0) return;
+    const real q = s.q[a];
+    if (q == (real)0) return;
+    const bool u = s.sol[a] != 0;
+    const R4<real> xq = s.xq[slot];
+    real th[3][4], dth[3][4];
+    int f[3];
+    real xs[3] = {xq.x, xq.y, xq.z};
+    for (int d = 0; d < 3; ++d) {
+        real w;
+        grid_coord(xs[d], (double)p.kscale[d], p.K[d], f[d], w);
+        bspline4(w, th[d], dth[d]);
+    }
+    real gx = 0, gy = 0, gz = 0;
+    for (int j0 = 0; j0 < 4; ++j0) {
+        const int k0 = wrapk(f[0] - j0, p.K[0]);
+        for (int j1 = 0; j1 < 4; ++j1) {
+            const int k1 = wrapk(f[1] - j1, p.K[1]);
+            const int row = (k0 * p.K[1] + k1) * p.K[2];
+            real sx = 0, sy = 0, sz = 0;
+            for (int j2 = 0; j2 < 4; ++j2) {
+                const int k2 = wrapk(f[2] - j2, p.K[2]);
+                const R2<real> w = p.Z[row + k2];
+                const real phi = u ? w.y : w.x;
+                sx += th[2][j2] * phi;
+                sz += dth[2][j2] * phi;
+            }
+            gx += dth[0][j0] * th[1][j1] * sx;
+            gy += th[0][j0] * dth[1][j1] * sx;
+            gz += th[0][j0] * th[1][j1] * sz;
+            (void)sy;
+        }
+    }
+    const real fx = -q * p.kscale[0] * gx, fy = -q * p.kscale[1] * gy, fz = -q * p.kscale[2] * gz;
+    atomic_add_ll(&s.F[slot], to_fixed(fx, FSCALE));
+    atomic_add_ll(&s.F[s.n_pad + slot], to_fixed(fy, FSCALE));
+    atomic_add_ll(&s.F[2 * s.n_pad + slot], to_fixed(fz, FSCALE));
+}
+
+template <typename real>
+void launch_spread(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st)
+{
+    k_spread<real><<<(s.n_pad + 127) / 128, 128, 0, st>>>(s, p);
+}
+template <typename real>
+void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode, cudaStream_t st)
+{
+    const int b = (p.KK + 255) / 256;
+    if (mode == CONV_ENERGY) k_conv<real, CONV_ENERGY><<<b, 256, 0, st>>>(p, E, lam);
+    else if (mode == CONV_POTENTIAL) k_conv<real, CONV_POTENTIAL><<<b, 256, 0, st>>>(p, E, lam);
+    else k_conv<real, CONV_BOTH><<<b, 256, 0, st>>>(p, E, lam);
+}
+template <typename real>
+void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st)
+{
+    k_gather<real><<<(s.n_pad + 127) / 128, 128, 0, st>>>(s, p);
+}
+
+// energy64 (FP32 systems): the FP64 energy branch.  The first FP32 pass
+// leaves an FP64 copy of the packed charge grid in energy64->Z; the branch
+// transforms it in FP64 and forms the three class energies, while the FP32
+// branch only forms the force potentials.
+template <typename real>
+void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<double>* energy64, cudaStream_t st)
+{
+    launch_spread(s, p, st);
+    launch_fft(p, 2, +1, 1, st);
+    if (energy64) {
+        launch_fft(*energy64, 2, +1, 0, st);
+        launch_fft(*energy64, 1, +1, 0, st);
+        launch_fft(*energy64, 0, +1, 0, st);
+        launch_conv(*energy64, s.E, s.lam, CONV_ENERGY, st);
+    }
+    launch_fft(p, 1, +1, 0, st);
+    launch_fft(p, 0, +1, 0, st);
+    launch_conv(p, s.E, s.lam, energy64 ? CONV_POTENTIAL : CONV_BOTH, st);
+    launch_fft(p, 0, -1, 0, st);
+    launch_fft(p, 1, -1, 0, st);
+    launch_fft(p, 2, -1, 0, st);
+    launch_gather(s, p, st);
+}
+
+#define LFE_INST_PME(real)                                                                        \
+    template void launch_pme<real>(const SysView<real>&, const PmeView<real>&, const PmeView<double>*, cudaStream_t); \
+    template void launch_spread<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
+    template void launch_conv<real>(const PmeView<real>&, long long*, const LamState*, int, cudaStream_t); \
+    template void launch_gather<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
+    template void launch_fft<real>(const PmeView<real>&, int, int, int, cudaStream_t);
+LFE_INST_PME(float)
+LFE_INST_PME(double)
+
+}  // namespace lfe

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of the C-ABI in include/lfe.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``liblfe.so`` built in-tree by
+``paper_2608_12691_b300.build``.  There is no fallback: if the library is
+missing or cannot be loaded, ``load()`` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblfe.so")
+
+LFE_OK = 0
+LFE_ERR_ARG = -1
+LFE_ERR_CUDA = -2
+LFE_ERR_OVERFLOW = -3
+LFE_ERR_NONFINITE = -4
+LFE_ERR_TIMEOUT = -5
+LFE_ERR_STATE = -6
+LFE_FP32_MIXED = 0
+LFE_FP64 = 1
+NTERMS = 10
+NEXT = 9
+TERM_NAMES = ["U", "dUdl", "U_vv", "U_uu", "U_uv", "U_soft", "U_bonded", "n_pairs", "hA", "hB"]
+
+EXPORTED = [
+    "lfe_create", "lfe_set_positions", "lfe_set_velocities", "lfe_set_integrator",
+    "lfe_build_neighbors", "lfe_eval",
+    "lfe_param_grad", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
+    "lfe_time_stages", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_batch_destroy", "lfe_last_error", "lfe_destroy",
+]
+
+
+class LfeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lfe error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double * 3),
+        ("r_cut", ctypes.c_double),
+        ("r_switch", ctypes.c_double),
+        ("ewald_alpha", ctypes.c_double),
+        ("pme_grid", ctypes.c_int * 3),
+        ("pme_order", ctypes.c_int),
+        ("skin", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("temperature", ctypes.c_double),
+        ("friction", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("lambda_mass", ctypes.c_double),
+        ("lambda_friction", ctypes.c_double),
+        ("theta0", ctypes.c_double),
+        ("opes_stride", ctypes.c_int),
+        ("opes_dE_std", ctypes.c_double),
+        ("opes_dE_exp", ctypes.c_double),
+        ("opes_sigma", ctypes.c_double),
+        ("opes_max_kernels", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+    ]
+
+
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Topology(ctypes.Structure):
+    _fields_ = [
+        ("n_atoms", ctypes.c_int),
+        ("pos", _dp), ("charge", _dp), ("sigma", _dp), ("epsilon", _dp),
+        ("solute", ctypes.POINTER(ctypes.c_ubyte)), ("mass", _dp),
+        ("n_excl", ctypes.c_int), ("excl", _ip),
+        ("n_14", ctypes.c_int), ("pairs14", _ip), ("scale14", _dp),
+        ("n_waters", ctypes.c_int), ("water_OHH", _ip), ("water_rOH", ctypes.c_double),
+        ("water_rHH", ctypes.c_double),
+        ("n_constraints", ctypes.c_int), ("constraints", _ip), ("constraint_len", _dp),
+        ("n_bonds", ctypes.c_int), ("bonds", _ip), ("bond_par", _dp),
+        ("n_angles", ctypes.c_int), ("angles", _ip), ("angle_par", _dp),
+        ("n_torsions", ctypes.c_int), ("torsions", _ip), ("torsion_par", _dp),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load liblfe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FileNotFoundError(f"{LIB_PATH} is missing: run paper_2608_12691_b300/build.py")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    lib.lfe_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(Topology), ctypes.POINTER(vp)]
+    lib.lfe_set_positions.argtypes = [vp, vp, ctypes.c_int, vp]
+    lib.lfe_set_velocities.argtypes = [vp, vp]
+    lib.lfe_set_integrator.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.lfe_build_neighbors.argtypes = [vp, vp]
+    lib.lfe_eval.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int, vp]
+    lib.lfe_param_grad.argtypes = [vp, ctypes.c_double, vp, vp]
+    lib.lfe_step.argtypes = [vp, ctypes.c_int, vp]
+    lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
+    lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
+    lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
+    lib.lfe_time_stages.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp,
+                                    ctypes.POINTER(ctypes.c_char_p), _dp, ctypes.c_int]
+    lib.lfe_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+    lib.lfe_batch_eval.argtypes = [vp, vp, vp, vp]
+    lib.lfe_batch_step.argtypes = [vp, ctypes.c_int, vp]
+    lib.lfe_batch_destroy.argtypes = [vp]
+    lib.lfe_batch_destroy.restype = None
+    lib.lfe_last_error.argtypes = [vp]
+    lib.lfe_last_error.restype = ctypes.c_char_p
+    lib.lfe_destroy.argtypes = [vp]
+    lib.lfe_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _arr(a, dtype, width=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if width is not None:
+        a = a.reshape(-1, width)
+    return a
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class System:
+    """A system on the current CUDA device, created from a dict of the shape
+    produced by ``paper_2608_12691_b300.systems``."""
+
+    def __init__(self, d, precision=LFE_FP32_MIXED, skin=0.1, seed=2608, theta0=None, **over):
+        lib = load()
+        self._lib = lib
+        self.n = len(d["charge"])
+        pr = Params()
+        box = np.asarray(d["box"], dtype=np.float64)
+        for k in range(3):
+            pr.box[k] = box[k]
+            pr.pme_grid[k] = int(d["grid"][k])
+        pr.r_cut = float(d["r_cut"])
+        pr.r_switch = float(d["r_switch"])
+        pr.ewald_alpha = float(d["alpha"])
+        pr.pme_order = int(d.get("order", 4))
+        pr.skin = float(skin)
+        pr.precision = int(precision)
+        pr.temperature = float(d.get("temperature", 298.0))
+        pr.friction = float(d.get("friction", 10.0))
+        pr.dt = float(d.get("dt", 0.002))
+        pr.lambda_mass = float(d.get("lambda_mass", 0.0))
+        pr.lambda_friction = float(d.get("lambda_friction", 25.0))
+        pr.theta0 = float(d.get("lam", 0.5) if theta0 is None else theta0)
+        pr.opes_stride = int(d.get("opes_stride", 0))
+        pr.opes_dE_std = float(d.get("opes_dE_std", 0.0))
+        pr.opes_dE_exp = float(d.get("opes_dE_exp", 0.0))
+        pr.opes_sigma = float(d.get("opes_sigma", 0.1))
+        pr.opes_max_kernels = int(d.get("opes_max_kernels", 1024))
+        pr.seed = int(seed)
+        for k, v in over.items():
+            setattr(pr, k, v)
+        self.params = pr
+        keep = {}
+
+        def K(name, dtype, width=None):
+            a = d.get(name)
+            if a is None:
+                a = np.zeros((0,) if width is None else (0, width))
+            a = _arr(a, dtype, width)
+            keep[name] = a
+            return a
+
+        t = Topology()
+        t.n_atoms = self.n
+        t.pos = _p(K("pos", np.float64, 3), ctypes.c_double)
+        t.charge = _p(K("charge", np.float64), ctypes.c_double)
+        t.sigma = _p(K("sigma", np.float64), ctypes.c_double)
+        t.epsilon = _p(K("epsilon", np.float64), ctypes.c_double)
+        t.solute = _p(K("solute", np.uint8), ctypes.c_ubyte)
+        t.mass = _p(K("mass", np.float64), ctypes.c_double)
+        ex = K("excl", np.int32, 2)
+        t.n_excl, t.excl = ex.shape[0], _p(ex, ctypes.c_int)
+        p14 = K("pairs14", np.int32, 2)
+        t.n_14, t.pairs14 = p14.shape[0], _p(p14, ctypes.c_int)
+        t.scale14 = _p(K("scale14", np.float64, 2), ctypes.c_double)
+        w = K("waters", np.int32, 3)
+        t.n_waters, t.water_OHH = w.shape[0], _p(w, ctypes.c_int)
+        t.water_rOH = 0.09572
+        t.water_rHH = 2 * 0.09572 * np.sin(np.radians(104.52) / 2)
+        c = K("constraints", np.int32, 2)
+        t.n_constraints, t.constraints = c.shape[0], _p(c, ctypes.c_int)
+        t.constraint_len = _p(K("constraint_len", np.float64), ctypes.c_double)
+        b = K("bonds", np.int32, 2)
+        t.n_bonds, t.bonds = b.shape[0], _p(b, ctypes.c_int)
+        t.bond_par = _p(K("bond_par", np.float64, 2), ctypes.c_double)
+        a = K("angles", np.int32, 3)
+        t.n_angles, t.angles = a.shape[0], _p(a, ctypes.c_int)
+        t.angle_par = _p(K("angle_par", np.float64, 2), ctypes.c_double)
+        to = K("torsions", np.int32, 4)
+        t.n_torsions, t.torsions = to.shape[0], _p(to, ctypes.c_int)
+        t.torsion_par = _p(K("torsion_par", np.float64, 3), ctypes.c_double)
+        h = ctypes.c_void_p()
+        rc = lib.lfe_create(ctypes.byref(pr), ctypes.byref(t), ctypes.byref(h))
+        if rc != LFE_OK:
+            raise LfeError(rc, lib.lfe_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != LFE_OK:
+            raise LfeError(rc, self._lib.lfe_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lfe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- calls
+    def eval(self, lam, forces=True):
+        """Host outputs: (terms dict, forces (N, 3) float64 or None)."""
+        terms = np.zeros(NTERMS)
+        F = np.zeros((self.n, 3)) if forces else None
+        self._check(self._lib.lfe_eval(self.h, float(lam), F.ctypes.data if F is not None else None,
+                                       terms.ctypes.data, 0, None))
+        return dict(zip(TERM_NAMES, terms)), F
+
+    def eval_device(self, lam, forces_ptr, terms_ptr, stream=None):
+        """Device outputs: pointers to float64 device buffers ([3N] and [NTERMS])."""
+        self._check(self._lib.lfe_eval(self.h, float(lam), forces_ptr, terms_ptr, 1, _stream_ptr(stream)))
+
+    def set_positions(self, pos, stream=None):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        self._check(self._lib.lfe_set_positions(self.h, pos.ctypes.data, 0, _stream_ptr(stream)))
+
+    def set_positions_ptr(self, ptr, on_device, stream=None):
+        self._check(self._lib.lfe_set_positions(self.h, ptr, int(on_device), _stream_ptr(stream)))
+
+    def set_velocities(self, vel):
+        vel = np.ascontiguousarray(vel, dtype=np.float64)
+        self._check(self._lib.lfe_set_velocities(self.h, vel.ctypes.data))
+
+    def set_integrator(self, dt, friction, temperature):
+        self._check(self._lib.lfe_set_integrator(self.h, float(dt), float(friction), float(temperature)))
+
+    def build_neighbors(self, stream=None):
+        self._check(self._lib.lfe_build_neighbors(self.h, _stream_ptr(stream)))
+
+    def step(self, n, stream=None):
+        self._check(self._lib.lfe_step(self.h, int(n), _stream_ptr(stream)))
+
+    def get_state(self):
+        pos = np.zeros((self.n, 3))
+        vel = np.zeros((self.n, 3))
+        ext = np.zeros(NEXT)
+        self._check(self._lib.lfe_get_state(self.h, pos.ctypes.data, vel.ctypes.data, ext.ctypes.data))
+        keys = ["theta", "p_theta", "lambda", "dUdl", "U", "n_kernels_std", "n_kernels_exp", "step",
+                "n_rebuilds"]
+        return pos, vel, dict(zip(keys, ext))
+
+    def get_state_into(self, pos_ptr, vel_ptr, ext_ptr):
+        self._check(self._lib.lfe_get_state(self.h, pos_ptr, vel_ptr, ext_ptr))
+
+    def checkpoint(self, path):
+        self._check(self._lib.lfe_checkpoint(self.h, str(path).encode()))
+
+    def restore(self, path):
+        self._check(self._lib.lfe_restore(self.h, str(path).encode()))
+
+    def param_grad(self, lam, n_u):
+        dU = np.zeros((n_u, 3))
+        d2 = np.zeros((n_u, 3))
+        self._check(self._lib.lfe_param_grad(self.h, float(lam), dU.ctypes.data, d2.ctypes.data))
+        return dU, d2
+
+    def time_stages(self, lam, reps=10, stream=None, max_n=32):
+        names = (ctypes.c_char_p * max_n)()
+        ms = np.zeros(max_n)
+        r = self._lib.lfe_time_stages(self.h, float(lam), int(reps), _stream_ptr(stream), names,
+                                      ms.ctypes.data_as(_dp), max_n)
+        if r < 0:
+            self._check(r)
+        return {names[k].decode(): float(ms[k]) for k in range(r)}

@@ -9,8 +9,10 @@ flexible 22-atom N-acetyl-amino-acid-amide-like solute built from backbone
 dihedrals.  Every force-field number here is synthetic.
 
 Conventions shared by both sides of every comparison:
-  * the box lengths and all coordinates are float32-representable doubles and
-    every coordinate is wrapped into [0, L) per atom;
+  * the box lengths, all coordinates, charges, sigmas and epsilons are
+    float32-representable doubles (the mixed-precision path stores them in
+    float32, so both sides then see identical inputs) and every coordinate is
+    wrapped into [0, L) per atom;
   * ``excl`` lists every pair left out of the ordinary pair sum (1-2, 1-3,
     1-4 and, for rigid solutes, all intramolecular pairs); ``pairs14`` is the
     subset that gets scaled 1-4 terms, with ``scale14`` = (s_LJ, s_C);
@@ -302,9 +304,9 @@ class _Builder:
         d = dict(
             box=box,
             pos=_wrap(np.array(self.pos), box),
-            charge=np.array(self.q),
-            sigma=np.array(self.sig),
-            epsilon=np.array(self.eps),
+            charge=f32(np.array(self.q)),
+            sigma=f32(np.array(self.sig)),
+            epsilon=f32(np.array(self.eps)),
             solute=np.array(self.sol, dtype=np.uint8),
             mass=np.array(self.mass),
             excl=np.array(sorted(tuple(sorted(e)) for e in self.excl), dtype=np.int32).reshape(-1, 2),
@@ -593,6 +595,7 @@ def make_octanol_box(seed=2609, n_chains=500, box_len=4.8, nx=12, ny=11, nz=4, l
                 slots.append(((ix + 0.5 + off) * box[0] / nx, (iy + 0.5 + off) * box[1] / ny,
                               (iz + 0.5) * box[2] / nz))
     slots = np.array(slots)
+
     chains = []
     for s in slots:
         xyz, bonds = octanol_chain(rng)
@@ -623,9 +626,14 @@ def make_octanol_box(seed=2609, n_chains=500, box_len=4.8, nx=12, ny=11, nz=4, l
 
 def make_c1(seed=2609, lam=None):
     """Octanol solvation box: 500 chains + 20-atom solute (13,520 atoms), 4.8 nm,
-    cutoff 1.0 nm, PME 48^3, octanol masses x 0.1."""
+    cutoff 1.0 nm, PME 48^3, octanol masses x 0.1.  Time step 1 fs: with the
+    hydrogen masses scaled to 0.1 amu the H-C-H bending period is ~7 fs and
+    the constrained leapfrog diverges at 2 fs (the paper runs 1 fs).  The
+    lattice start is denser than liquid octanol and has close H-H contacts:
+    runs begin with a short small-step, high-friction equilibration."""
     d = make_octanol_box(seed=seed, lam=lam)
     d["name"] = "c1_octanol500_rigid20"
+    d["dt"] = 0.001
     return d
 
 

@@ -1,0 +1,106 @@
+"""GPU dynamics parity: captured steps of the CUDA path (Langevin middle
+scheme with rigid waters, theta under the dual OPES bias) against the same
+steps taken by the oracle (level-2 forces, SHAKE to convergence, the same
+Philox4x32-10 counters), plus bit-exact checkpoint / resume."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dynamics as D
+from oracle import reference as R
+from paper_2608_12691_b300 import lfe
+from paper_2608_12691_b300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+SEED = 77
+
+
+def water_system():
+    d = S.make_water_box(seed=21, n_waters=101, box_len=1.45, solute="ring12", n_side=5,
+                         r_cut=0.7, grid=16, lam=0.62)
+    d.update(dt=0.001, lambda_mass=20.0, lambda_friction=25.0, opes_stride=2,
+             opes_dE_std=30 * 4.184, opes_dE_exp=5 * 4.184, opes_sigma=0.1)
+    return d
+
+
+def oracle_steps(d, nsteps):
+    pairs, lens = D.constraint_list(d)
+    x = d["pos"].copy()
+    v = np.zeros_like(x)
+    th, p = d["lam"], 0.0
+    std = D.Opes("std", d["opes_dE_std"], d["opes_sigma"], d["temperature"])
+    exp = D.Opes("exp", d["opes_dE_exp"], d["opes_sigma"], d["temperature"])
+    for step in range(nsteps):
+        lam, dl = D.theta_to_lambda(th)
+        e = R.evaluate(d, lam, level=2, pos=x)
+        nrm = D.atom_normals(len(x), step, SEED)
+        x, v = D.langevin_middle_step(x, v, e["F"], d["mass"], d["dt"], d["friction"], d["temperature"],
+                                      nrm, d["box"], pairs, lens)
+        dV = std.bias(th)[1] + exp.bias(th)[1]
+        th, p = D.theta_step(th, p, e["dUdl"], dl, dV, d["lambda_mass"], d["dt"], d["lambda_friction"],
+                             d["temperature"], D.theta_normal(step, SEED))
+        if (step + 1) % d["opes_stride"] == 0:
+            std.deposit(th)
+            exp.deposit(th)
+    return x, v, th, p, std, exp
+
+
+def min_image(a, box):
+    return a - box * np.round(a / box)
+
+
+@pytest.mark.parametrize("precision,tx,tv", [(lfe.LFE_FP64, 2e-8, 1e-6), (lfe.LFE_FP32_MIXED, 5e-6, 5e-3)])
+def test_steps_match_oracle(precision, tx, tv):
+    d = water_system()
+    n = 4
+    g = lfe.System(d, precision=precision, seed=SEED)
+    g.step(n)
+    pos, vel, ext = g.get_state()
+    x, v, th, p, std, exp = oracle_steps(d, n)
+    dx = np.abs(min_image(pos - x, d["box"])).max()
+    assert dx < tx, dx
+    vs = np.abs(v).max()
+    assert np.abs(vel - v).max() < tv * vs
+    assert ext["step"] == n
+    assert ext["n_kernels_std"] == len(std.c) and ext["n_kernels_exp"] == len(exp.c)
+    assert ext["theta"] == pytest.approx(th, abs=1e-8 if precision == lfe.LFE_FP64 else 1e-5)
+    assert ext["p_theta"] == pytest.approx(p, rel=1e-6 if precision == lfe.LFE_FP64 else 2e-3, abs=1e-9)
+
+
+def test_constraints_hold_after_many_steps():
+    d = water_system()
+    g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=SEED)
+    g.step(200)
+    pos, vel, ext = g.get_state()
+    w = d["waters"]
+    for (o, h1, h2) in w:
+        r1 = np.linalg.norm(min_image(pos[h1] - pos[o], d["box"]))
+        r2 = np.linalg.norm(min_image(pos[h2] - pos[o], d["box"]))
+        r3 = np.linalg.norm(min_image(pos[h2] - pos[h1], d["box"]))
+        assert abs(r1 - 0.09572) < 1e-5 and abs(r2 - 0.09572) < 1e-5
+        assert abs(r3 - 2 * 0.09572 * math.sin(math.radians(104.52) / 2)) < 2e-5
+    assert 0.0 <= ext["theta"] < 2.0
+    assert np.isfinite(vel).all()
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    d = water_system()
+    a = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=SEED)
+    a.step(30)
+    a.checkpoint(tmp_path / "c.bin")
+    a.step(30)
+    pa, va, ea = a.get_state()
+    b = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=SEED)
+    b.restore(tmp_path / "c.bin")
+    b.step(30)
+    pb, vb, eb = b.get_state()
+    assert np.array_equal(pa, pb) and np.array_equal(va, vb)
+    assert ea["theta"] == eb["theta"] and ea["p_theta"] == eb["p_theta"]
+    # a damaged checkpoint is refused
+    raw = bytearray((tmp_path / "c.bin").read_bytes())
+    raw[100] ^= 0xFF
+    (tmp_path / "bad.bin").write_bytes(bytes(raw))
+    with pytest.raises(lfe.LfeError):
+        b.restore(tmp_path / "bad.bin")

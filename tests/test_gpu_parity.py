@@ -1,0 +1,163 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Bar (spec tolerances): forces within 1e-5 relative RMS and dU/dlambda
+within 1e-6 relative of the level-2 oracle (smooth PME on the same grid),
+element by element on the same seeded inputs.  The FP64 instantiation is held
+to 1e-10.  Energies per class are compared too, and the pair count exactly in
+FP64.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import reference as R
+from paper_2608_12691_b300 import lfe
+from paper_2608_12691_b300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lfe.LFE_FP32_MIXED: dict(F=1e-5, dU=1e-6, E=1e-6), lfe.LFE_FP64: dict(F=1e-9, dU=1e-8, E=1e-9)}
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_basis(key):
+    d = SYSTEMS[key]()
+    E, F0, Fuv, Fs = R.nonbonded(d, level=2)
+    Ub, Fb = R.bonded(d)
+    return d, E, F0, Fuv, Fs, Ub, Fb
+
+
+def oracle_at(key, lam):
+    d, E, F0, Fuv, Fs, Ub, Fb = oracle_basis(key)
+    hA, hB, dA, dB = R.switching(lam)
+    F = F0 + hA * Fuv + hB * Fs + Fb
+    U = E["U_vv"] + E["U_uu"] + hA * E["U_uv"] + hB * E["U_soft"] + Ub
+    dU = dA * E["U_uv"] + dB * E["U_soft"]
+    return d, dict(U=U, dUdl=dU, F=F, E=E, Ub=Ub, dA=dA, dB=dB)
+
+
+def small_ragged():
+    # 101 waters + 12-atom solute: 1 solute cluster + 10 solvent clusters, the
+    # last holding 15 atoms
+    return S.make_water_box(seed=21, n_waters=101, box_len=1.45, solute="ring12", n_side=5,
+                            r_cut=0.7, grid=16)
+
+
+def no_solute():
+    return S.make_water_box(seed=22, n_waters=200, box_len=1.82, solute=None, n_side=6, r_cut=0.9,
+                            grid=16)
+
+
+SYSTEMS = {
+    "c0": S.make_c0,
+    "ragged": small_ragged,
+    "nosolute": no_solute,
+    "c2": S.make_c2,
+    "c1": S.make_c1,
+    "c4": lambda: S.make_c4_frame(frame=5),
+}
+
+_gpu_systems = {}
+
+
+def gpu_system(key, precision):
+    k = (key, precision)
+    if k not in _gpu_systems:
+        d = SYSTEMS[key]() if key not in ("c2", "c1") else oracle_basis(key)[0]
+        _gpu_systems[k] = lfe.System(d, precision=precision)
+    return _gpu_systems[k]
+
+
+def check(key, lam, precision):
+    d, o = oracle_at(key, lam)
+    g = gpu_system(key, precision)
+    terms, F = g.eval(lam)
+    tol = TOL[precision]
+    Fo = o["F"]
+    rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
+    assert rel <= tol["F"], f"{key} lam={lam}: force rel RMS {rel:.3e}"
+    scale_dU = abs(o["dA"] * o["E"]["U_uv"]) + abs(o["dB"] * o["E"]["U_soft"])
+    err_dU = abs(terms["dUdl"] - o["dUdl"])
+    assert err_dU <= tol["dU"] * max(abs(o["dUdl"]), 1e-300) or err_dU <= 1e-12 * max(scale_dU, 1.0), \
+        f"{key} lam={lam}: dU/dl {terms['dUdl']} vs {o['dUdl']}"
+    # each class energy is a sum of large terms of both signs (self energy,
+    # exclusion corrections, real and reciprocal parts): its error is measured
+    # against the sum of the magnitudes of its parts
+    E = o["E"]
+    scale = {c: sum(abs(E[f"{part}_{c}"]) for part in ("coul_real", "rec", "bg", "lj", "excl"))
+             + (abs(E.get(f"self_{c}", 0.0)) + abs(E.get(f"p14_{c}", 0.0))) for c in ("vv", "uu", "uv")}
+    for k, sc in (("U_vv", scale["vv"]), ("U_uu", scale["uu"]), ("U_uv", scale["uv"]),
+                  ("U_soft", abs(E["U_soft"]))):
+        assert abs(terms[k] - E[k]) <= tol["E"] * max(sc, 1.0), f"{key}: {k} {terms[k]} vs {E[k]}"
+    assert abs(terms["U_bonded"] - o["Ub"]) <= tol["E"] * max(abs(o["Ub"]), 1.0)
+    assert abs(terms["U"] - o["U"]) <= tol["E"] * max(sum(scale.values()) + abs(o["Ub"]), 1.0)
+    if precision == lfe.LFE_FP64:
+        assert terms["n_pairs"] == o["E"]["n_pairs"]
+    else:
+        assert abs(terms["n_pairs"] - o["E"]["n_pairs"]) <= 2
+    return rel, err_dU
+
+
+LAMS = [0.0, 0.2, 0.35, 0.6, 1.0]
+
+
+@pytest.mark.parametrize("precision", [lfe.LFE_FP64, lfe.LFE_FP32_MIXED])
+@pytest.mark.parametrize("key", ["c0", "ragged", "nosolute"])
+def test_small_parity(key, precision):
+    d = SYSTEMS[key]()
+    for lam in LAMS + [d["lam"]]:
+        check(key, lam, precision)
+
+
+@pytest.mark.parametrize("key", ["c2", "c1", "c4"])
+def test_full_size_parity_fp32(key):
+    for lam in (0.1, 0.5, 0.9):
+        check(key, lam, lfe.LFE_FP32_MIXED)
+
+
+def test_full_size_parity_fp64_c2():
+    check("c2", 0.5, lfe.LFE_FP64)
+
+
+def test_eval_is_bitwise_reproducible():
+    g = gpu_system("c0", lfe.LFE_FP32_MIXED)
+    t1, F1 = g.eval(0.47)
+    t2, F2 = g.eval(0.47)
+    assert np.array_equal(F1, F2)
+    assert all(t1[k] == t2[k] for k in t1)
+
+
+def test_bad_inputs_are_rejected_and_system_survives():
+    d = SYSTEMS["ragged"]()
+    g = lfe.System(d)
+    bad = d["pos"].copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(lfe.LfeError) as e:
+        g.set_positions(bad)
+    assert e.value.code == lfe.LFE_ERR_ARG
+    with pytest.raises(lfe.LfeError):
+        g.eval(1.5)
+    t, F = g.eval(0.5)
+    assert np.isfinite(F).all()
+    dd = dict(d, r_cut=0.8)
+    with pytest.raises(lfe.LfeError) as e:
+        lfe.System(dd)
+    assert e.value.code == lfe.LFE_ERR_ARG
+
+
+def test_set_positions_roundtrip():
+    d = SYSTEMS["ragged"]()
+    g = lfe.System(d)
+    rng = np.random.default_rng(0)
+    moved = S.f32(d["pos"] + rng.normal(scale=0.01, size=d["pos"].shape))
+    moved = moved - d["box"] * np.floor(moved / d["box"])
+    moved = S.f32(moved)
+    moved[moved >= d["box"]] = 0.0
+    g.set_positions(moved)
+    t, F = g.eval(0.4)
+    dd = dict(d, pos=moved)
+    E, F0, Fuv, Fs = R.nonbonded(dd, level=2)
+    hA, hB, _, _ = R.switching(0.4)
+    Fo = F0 + hA * Fuv + hB * Fs
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) < 1e-5
