@@ -197,8 +197,19 @@ struct System final : SystemBase {
         n_u = (int)sl.size();
         n_solv = (int)vl.size();
         n_ucl = (n_u + 31) / 32;
-        n_cl = n_ucl + (n_solv + 31) / 32;
+        // column sort: edge near (32 / rho)^(1/3) so that 32-atom clusters are
+        // close to cubic; every column may end with one padded cluster
+        const double Vbox = p.box[0] * p.box[1] * p.box[2];
+        const double rho_s = std::max(1.0, n_solv / Vbox);
+        const double col_edge = std::cbrt(32.0 / rho_s);
+        N.ncx = std::max(1, std::min(1024, (int)std::lround(p.box[0] / col_edge)));
+        N.ncy = std::max(1, std::min(1024, (int)std::lround(p.box[1] / col_edge)));
+        N.ncols = N.ncx * N.ncy;
+        N.cinvx = (real)(N.ncx / p.box[0]);
+        N.cinvy = (real)(N.ncy / p.box[1]);
+        n_cl = n_ucl + (n_solv + 31) / 32 + (n_solv > 0 ? N.ncols : 0);
         n_pad = 32 * n_cl;
+        N.n_cl_max = n_cl;
 
         // ---------------------------------------------- per-atom buffers
         std::vector<R4<real>> hx(n), hv(n);
@@ -256,31 +267,28 @@ struct System final : SystemBase {
         double skin = p.skin > 0 ? p.skin : 0.1;
         P.skin = skin;
         const double V = p.box[0] * p.box[1] * p.box[2];
-        const double rho = std::max(1.0, n / V);
-        const double cell_len = std::cbrt(8.0 / rho);
-        int maxnc = 1;
-        for (int d = 0; d < 3; ++d) {
-            int nc = std::max(1, (int)std::floor(p.box[d] / cell_len));
-            nc = std::min(nc, 1024);
-            N.nc[d] = nc;
-            N.cinv[d] = (real)(nc / p.box[d]);
-            maxnc = std::max(maxnc, nc);
-        }
-        N.bits = 0;
-        while ((1 << N.bits) < maxnc) ++N.bits;
-        N.nkeys = 1 << (3 * N.bits);
-        N.keys = dalloc<int>(n_solv);
-        N.cnt = dalloc<int>(N.nkeys);
-        N.start = dalloc<int>(N.nkeys + 1);
-        N.fill = dalloc<int>(N.nkeys);
+        N.col_of = dalloc<int>(n_solv);
+        N.col_cnt = dalloc<int>(N.ncols);
+        N.col_start = dalloc<int>(N.ncols + 1);
+        N.col_fill = dalloc<int>(N.ncols);
+        N.col_ncl = dalloc<int>(N.ncols);
+        N.col_cl = dalloc<int>(N.ncols + 1);
         N.tmp = dalloc<int>(n_solv);
+        N.tmp2 = dalloc<int>(n_solv);
+        N.n_cl_solv = dalloc<int>(1);
         N.bbc = dalloc<R4<float>>(n_cl);
         N.bbh = dalloc<R4<float>>(n_cl);
         N.tile_cnt = dalloc<int>(n_cl);
         N.tile_off = dalloc<int>(n_cl + 1);
         N.cap = 1024;
         N.tiles = dalloc<int4>(N.cap);
+        N.jidx = dalloc<int>((size_t)N.cap * 32);
         N.masks = dalloc<unsigned>((size_t)N.cap * 32);
+        N.uv_tiles_max = std::max(1, n_ucl * 512);
+        N.uv_cnt = dalloc<int>(N.uv_tiles_max);
+        N.uv_off = dalloc<int>(N.uv_tiles_max + 1);
+        N.uv_cap = std::max(1024, n_u * 2048);
+        N.uvp = dalloc<int4>(N.uv_cap);
         N.cut2 = (float)((p.r_cut + skin) * (p.r_cut + skin));
         N.skin_half2 = (float)(0.25 * skin * skin);
         {
@@ -295,6 +303,20 @@ struct System final : SystemBase {
             }
             N.ex_start = upload(cnt);
             N.ex_list = upload(lst);
+            // molecule id = connected component of the exclusion graph
+            std::vector<int> parent(n);
+            for (int i = 0; i < n; ++i) parent[i] = i;
+            std::function<int(int)> find = [&](int i) {
+                while (parent[i] != i) { parent[i] = parent[parent[i]]; i = parent[i]; }
+                return i;
+            };
+            for (int e = 0; e < t.n_excl; ++e) {
+                const int ra = find(t.excl[2 * e]), rb = find(t.excl[2 * e + 1]);
+                if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+            }
+            std::vector<int> mol(n);
+            for (int i = 0; i < n; ++i) mol[i] = find(i);
+            N.mol = upload(mol);
         }
 
         // ---------------------------------------------------- exclusions
@@ -536,7 +558,7 @@ struct System final : SystemBase {
         }
         int nsm = 148;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-        pair_warps = nsm * 16;
+        pair_warps = nsm * 32;
         uv_blocks = nsm * 2;
         {
             const char* ev = std::getenv("LFE_EAGER_STEPS");
@@ -574,9 +596,11 @@ struct System final : SystemBase {
     void grow_tiles(int need)
     {
         dfree(N.tiles);
+        dfree(N.jidx);
         dfree(N.masks);
         N.cap = need + 256;
         N.tiles = dalloc<int4>(N.cap);
+        N.jidx = dalloc<int>((size_t)N.cap * 32);
         N.masks = dalloc<unsigned>((size_t)N.cap * 32);
         invalidate_graph();
     }

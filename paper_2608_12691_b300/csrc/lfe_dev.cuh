@@ -33,7 +33,7 @@ enum {
 };
 
 // error / control flags
-enum { FL_REBUILD = 0, FL_ERROR = 1, FL_NTILES = 2, FL_NREBUILD = 3, FL_N = 4 };
+enum { FL_REBUILD = 0, FL_ERROR = 1, FL_NTILES = 2, FL_NREBUILD = 3, FL_NUV = 4, FL_N = 8 };
 enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4 };
 
 // lambda state, written on the device (by lfe_eval's setter or by the theta

@@ -43,26 +43,39 @@ struct SysView {
 
 template <typename real>
 struct NblView {
-    int nc[3];            // cells per axis
-    int bits;             // Morton bits per axis
-    int nkeys;            // 1 << (3 bits)
-    real cinv[3];         // cells per nm
-    int* keys;            // [n_solv]
-    int* cnt;             // [nkeys]
-    int* start;           // [nkeys + 1]
-    int* fill;            // [nkeys]
-    int* tmp;             // [n_solv] solvent atoms in cell order
-    R4<float>* bbc;       // cluster bounding-box centres [n_cl]
-    R4<float>* bbh;       // half extents [n_cl]
-    int* tile_cnt;        // [n_cl]
-    int* tile_off;        // [n_cl + 1]
-    int4* tiles;          // [cap]  (I, J, shift code, class)
+    // column sort of the solvent: ncx x ncy columns in xy, each sorted by z
+    // and cut into clusters of 32 consecutive atoms (near-cubic clusters)
+    int ncx, ncy, ncols;
+    real cinvx, cinvy;    // columns per nm
+    int* col_of;          // [n_solv] column of each solvent atom (solv_list order)
+    int* col_cnt;         // [ncols] histogram (zeroed after the scan)
+    int* col_start;       // [ncols + 1]
+    int* col_fill;        // [ncols] scatter counters (zeroed after use)
+    int* col_ncl;         // [ncols] clusters per column (zeroed after the scan)
+    int* col_cl;          // [ncols + 1] first solvent cluster of each column
+    int* tmp;             // [n_solv] solvent atoms grouped by column
+    int* tmp2;            // [n_solv] ... and sorted by z inside each column
+    int* n_cl_solv;       // [1] solvent clusters of the current build
+    int n_cl_max;         // capacity in clusters
+    R4<float>* bbc;       // cluster bounding-box centres [n_cl_max]
+    R4<float>* bbh;       // half extents [n_cl_max]
+    int* tile_cnt;        // [n_cl_max]
+    int* tile_off;        // [n_cl_max + 1]
+    int4* tiles;          // [cap]  (I, shift code, class, diagonal)
+    int* jidx;            // [cap * 32] j slots of each tile (-1 = empty)
     unsigned* masks;      // [cap * 32]
     int cap;
     float cut2;           // (r_cut + skin)^2
     float skin_half2;     // (skin / 2)^2
     const int* ex_start;  // exclusion CSR, caller order [n + 1]
     const int* ex_list;
+    const int* mol;       // [n] molecule id (connected component of the exclusions)
+    // dense solute-solvent pair list (pairs within r_cut + skin at build time)
+    int* uv_cnt;          // [n_ucl_tiles_max] per-tile counts
+    int* uv_off;          // [n_ucl_tiles_max + 1]
+    int4* uvp;            // [uv_cap] (slot_i, slot_j, shift code, -)
+    int uv_cap;
+    int uv_tiles_max;     // capacity of uv_cnt / uv_off
 };
 
 template <typename real>

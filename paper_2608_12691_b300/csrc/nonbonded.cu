@@ -45,28 +45,30 @@ __device__ __forceinline__ unsigned spread_bits(unsigned v)
     return v;
 }
 
-// ------------------------------------------------------------- cell sort
+// ------------------------------------------------------------ clustering
+// Solvent atoms are binned into ncx x ncy columns in xy, sorted by z inside
+// each column and cut into clusters of 32 consecutive atoms; a column's last
+// cluster is padded.  With a column edge near (32/rho)^(1/3) the clusters are
+// close to cubic.  Solute atoms occupy the first clusters, in caller order.
 template <typename real>
-__global__ void k_cell_keys(SysView<real> s, NblView<real> nb)
+__global__ void k_col_keys(SysView<real> s, NblView<real> nb)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_solv) return;
-    int a = s.solv_list[i];
-    R4<real> p = s.x[a];
-    int c[3];
-    real pc[3] = {p.x, p.y, p.z};
-    for (int d = 0; d < 3; ++d) {
-        real w = wrap_coord(pc[d], s.L[d], s.invL[d]);
-        int k = (int)(w * nb.cinv[d]);
-        c[d] = k < 0 ? 0 : (k >= nb.nc[d] ? nb.nc[d] - 1 : k);
-    }
-    int key = (int)(spread_bits(c[0]) | (spread_bits(c[1]) << 1) | (spread_bits(c[2]) << 2));
-    nb.keys[i] = key;
-    atomicAdd(&nb.cnt[key], 1);
+    const R4<real> p = s.x[s.solv_list[i]];
+    const real wx = wrap_coord(p.x, s.L[0], s.invL[0]);
+    const real wy = wrap_coord(p.y, s.L[1], s.invL[1]);
+    int cx = (int)(wx * nb.cinvx), cy = (int)(wy * nb.cinvy);
+    cx = cx < 0 ? 0 : (cx >= nb.ncx ? nb.ncx - 1 : cx);
+    cy = cy < 0 ? 0 : (cy >= nb.ncy ? nb.ncy - 1 : cy);
+    const int c = cx * nb.ncy + cy;
+    nb.col_of[i] = c;
+    atomicAdd(&nb.col_cnt[c], 1);
 }
 
-// exclusive scan of n ints (single block of 1024 threads); zeroes `in` and
-// writes the total to *total when total != nullptr
+// exclusive scan of n ints (single block of 1024 threads); zeroes `in`;
+// writes the total to *total (when given) and raises the overflow bit when it
+// exceeds cap
 __global__ void k_scan_block(int* in, int* out, int n, int* total, int cap, int* errflag)
 {
     __shared__ int part[1024];
@@ -100,51 +102,85 @@ __global__ void k_scan_block(int* in, int* out, int n, int* total, int cap, int*
 }
 
 template <typename real>
-__global__ void k_cell_scatter(SysView<real> s, NblView<real> nb)
+__global__ void k_col_scatter(SysView<real> s, NblView<real> nb)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_solv) return;
-    int key = nb.keys[i];
-    int pos = nb.start[key] + atomicAdd(&nb.fill[key], 1);
+    const int c = nb.col_of[i];
+    const int pos = nb.col_start[c] + atomicAdd(&nb.col_fill[c], 1);
     nb.tmp[pos] = s.solv_list[i];
 }
 
-// deterministic order inside each cell: ascending atom index
+constexpr int COL_MAX = 2048;   // atoms per column handled by one block
+
+// one block per column: rank sort by (wrapped z, atom index); also the
+// number of 32-atom clusters of the column
 template <typename real>
-__global__ void k_cell_sort(NblView<real> nb)
+__global__ void __launch_bounds__(256) k_col_sort(SysView<real> s, NblView<real> nb)
 {
-    int key = blockIdx.x * blockDim.x + threadIdx.x;
-    if (key >= nb.nkeys) return;
-    int b = nb.start[key], e = nb.start[key + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = nb.tmp[i];
-        int j = i - 1;
-        while (j >= b && nb.tmp[j] > v) { nb.tmp[j + 1] = nb.tmp[j]; --j; }
-        nb.tmp[j + 1] = v;
+    __shared__ float zs[COL_MAX];
+    __shared__ int ids[COL_MAX];
+    const int c = blockIdx.x;
+    const int b = nb.col_start[c];
+    int cnt = nb.col_start[c + 1] - b;
+    if (cnt > COL_MAX) {
+        if (threadIdx.x == 0) atomicOr(&s.flags[FL_ERROR], ERRB_OVERFLOW);
+        cnt = COL_MAX;
     }
-    nb.fill[key] = 0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const int a = nb.tmp[b + k];
+        ids[k] = a;
+        zs[k] = (float)wrap_coord(s.x[a].z, s.L[2], s.invL[2]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        const float z = zs[k];
+        const int a = ids[k];
+        int rank = 0;
+        for (int m = 0; m < cnt; ++m) {
+            const float zm = zs[m];
+            rank += (zm < z) || (zm == z && ids[m] < a);
+        }
+        nb.tmp2[b + rank] = a;
+    }
+    if (threadIdx.x == 0) {
+        nb.col_fill[c] = 0;
+        nb.col_ncl[c] = (cnt + 31) / 32;
+    }
 }
 
-// slot assignment: solute clusters first (caller order), then solvent atoms in
-// cell order; fills the sorted coordinate/parameter arrays and xref
+// slot -> atom: solute clusters first, then the solvent clusters column by
+// column; also the sorted coordinates / parameters and xref
 template <typename real>
 __global__ void k_assign(SysView<real> s, NblView<real> nb)
 {
-    int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= s.n_pad) return;
-    int a;
-    int us = s.n_ucl * 32;
-    if (slot < us) a = slot < s.n_u ? s.solute_list[slot] : -1;
-    else {
-        int k = slot - us;
-        a = k < s.n_solv ? nb.tmp[k] : -1;
+    int a = -1;
+    const int us = s.n_ucl * 32;
+    if (slot < us) {
+        a = slot < s.n_u ? s.solute_list[slot] : -1;
+    } else {
+        const int c = slot / 32 - s.n_ucl;   // solvent cluster
+        if (c < *nb.n_cl_solv) {
+            // column of cluster c: last k with col_cl[k] <= c
+            int lo = 0, hi = nb.ncols - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (nb.col_cl[mid] <= c) lo = mid;
+                else hi = mid - 1;
+            }
+            const int rank = (c - nb.col_cl[lo]) * 32 + (slot & 31);
+            const int cnt = min(nb.col_start[lo + 1] - nb.col_start[lo], COL_MAX);
+            if (rank < cnt) a = nb.tmp2[nb.col_start[lo] + rank];
+        }
     }
     s.perm[slot] = a;
     R4<real> o;
     R2<real> l;
     if (a >= 0) {
         s.iperm[a] = slot;
-        R4<real> p = s.x[a];
+        const R4<real> p = s.x[a];
         s.xref[a] = p;
         o.x = wrap_coord(p.x, s.L[0], s.invL[0]);
         o.y = wrap_coord(p.y, s.L[1], s.invL[1]);
@@ -161,16 +197,22 @@ __global__ void k_assign(SysView<real> s, NblView<real> nb)
 }
 
 template <typename real>
+__device__ __forceinline__ int num_clusters(const SysView<real>& s, const NblView<real>& nb)
+{
+    return s.n_ucl + *nb.n_cl_solv;
+}
+
+template <typename real>
 __global__ void k_bbox(SysView<real> s, NblView<real> nb)
 {
-    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (c >= s.n_cl) return;
-    int slot = c * 32 + lane;
-    bool ok = s.perm[slot] >= 0;
-    R4<real> p = s.xq[slot];
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= num_clusters(s, nb)) return;
+    const int slot = c * 32 + lane;
+    const bool ok = s.perm[slot] >= 0;
+    const R4<real> p = s.xq[slot];
     float lo[3], hi[3];
-    float pv[3] = {(float)p.x, (float)p.y, (float)p.z};
+    const float pv[3] = {(float)p.x, (float)p.y, (float)p.z};
     for (int d = 0; d < 3; ++d) {
         lo[d] = ok ? pv[d] : 3.0e38f;
         hi[d] = ok ? pv[d] : -3.0e38f;
@@ -190,82 +232,201 @@ __global__ void k_bbox(SysView<real> s, NblView<real> nb)
     }
 }
 
-// shift code sh = (sx+1) + 3 (sy+1) + 9 (sz+1); cluster J is taken at
-// x_J + s L.  For I == J only sh = 13 (s = 0, j > i) and the upper half
-// sh > 13 are used, so each pair image is visited once.
-template <typename real>
-__device__ __forceinline__ bool tile_pass(const SysView<real>& s, const NblView<real>& nb,
-                                          const R4<float>& ci, const R4<float>& hi, int J, int sh)
+// shift code sh = (sx+1) + 3 (sy+1) + 9 (sz+1): cluster J is taken at x_J + s L
+__device__ __forceinline__ void shift_vec(int sh, int sv[3])
 {
-    R4<float> cj = nb.bbc[J], hj = nb.bbh[J];
-    int sv[3] = {sh % 3 - 1, (sh / 3) % 3 - 1, sh / 9 - 1};
-    float c1[3] = {cj.x, cj.y, cj.z}, c0[3] = {ci.x, ci.y, ci.z};
-    float h1[3] = {hj.x, hj.y, hj.z}, h0[3] = {hi.x, hi.y, hi.z};
+    sv[0] = sh % 3 - 1;
+    sv[1] = (sh / 3) % 3 - 1;
+    sv[2] = sh / 9 - 1;
+}
+
+template <typename real>
+__device__ __forceinline__ float box_gap2(const SysView<real>& s, const R4<float>& ci, const R4<float>& hi,
+                                          const R4<float>& cj, const R4<float>& hj, int sh)
+{
+    int sv[3];
+    shift_vec(sh, sv);
+    const float c1[3] = {cj.x, cj.y, cj.z}, c0[3] = {ci.x, ci.y, ci.z};
+    const float h1[3] = {hj.x, hj.y, hj.z}, h0[3] = {hi.x, hi.y, hi.z};
     float d2 = 0.f;
     for (int d = 0; d < 3; ++d) {
         float g = fabsf(c1[d] + sv[d] * (float)s.L[d] - c0[d]) - h0[d] - h1[d];
         g = fmaxf(g, 0.f);
         d2 += g * g;
     }
-    return d2 < nb.cut2;
+    return d2;
 }
 
-// pass 0: count tiles per i-cluster; pass 1: write them at the scanned offsets
+// Tile list.  One warp per i-cluster I.  The diagonal tile (I with itself,
+// no shift, pairs j > i) comes first; then, for each class of partner
+// cluster (solute, solvent) and each of the 27 periodic shifts, every atom
+// of every partner cluster J >= I (J == I only for the upper half of the
+// shifts, so each pair image is visited once) whose distance to I's bounding
+// box is below r_cut + skin is appended to a j list, 32 atoms per tile.  A
+// tile therefore has one shift and one class.  WRITE = 0 counts tiles,
+// WRITE = 1 writes them at the scanned offsets.
 template <typename real, int WRITE>
-__global__ void k_tiles(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb)
 {
-    int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (I >= s.n_cl) return;
-    R4<float> ci = nb.bbc[I], hi = nb.bbh[I];
-    int base = WRITE ? nb.tile_off[I] : 0;
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (I >= nb.n_cl_max) return;
+    const int ncl = num_clusters(s, nb);
+    if (I >= ncl) {
+        if (!WRITE && lane == 0) nb.tile_cnt[I] = 0;
+        return;
+    }
+    const R4<float> ci = nb.bbc[I], hi = nb.bbh[I];
+    const bool iu = I < s.n_ucl;
+    const int base = WRITE ? nb.tile_off[I] : 0;
     int count = 0;
-    bool iu = I < s.n_ucl;
-    for (int J0 = I; J0 < s.n_cl; J0 += 32) {
-        int J = J0 + lane;
-        bool valid = J < s.n_cl;
+    // diagonal tile
+    if (WRITE && base < nb.cap) {
+        nb.jidx[(size_t)base * 32 + lane] = s.perm[I * 32 + lane] >= 0 ? I * 32 + lane : -1;
+        if (lane == 0) nb.tiles[base] = make_int4(I, 13, iu ? 1 : 0, 1);
+    }
+    count = 1;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int jc = 0; jc < 2; ++jc) {
+        const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
+        const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
         for (int sh = 0; sh < 27; ++sh) {
-            bool pass = valid && (J != I || sh >= 13) && tile_pass(s, nb, ci, hi, valid ? J : I, sh);
-            unsigned bal = __ballot_sync(0xffffffffu, pass);
-            if (WRITE && pass) {
-                int pos = base + count + __popc(bal & ((1u << lane) - 1u));
-                if (pos < nb.cap) {
-                    bool ju = J < s.n_ucl;
-                    int cls = (iu && ju) ? 1 : ((iu || ju) ? 2 : 0);
-                    nb.tiles[pos] = make_int4(I, J, sh, cls);
+            int nbuf = 0;   // atoms already placed in the open tile
+            for (int J0 = max(I, jb); J0 < je; J0 += 32) {
+                const int J = J0 + lane;
+                bool pc = J < je && (J != I || sh > 13);
+                if (pc) pc = box_gap2(s, ci, hi, nb.bbc[J], nb.bbh[J], sh) < nb.cut2;
+                unsigned bal = __ballot_sync(0xffffffffu, pc);
+                while (bal) {
+                    const int jj = __ffs(bal) - 1;
+                    bal &= bal - 1u;
+                    const int Jp = J0 + jj;
+                    const int slot = Jp * 32 + lane;
+                    bool keep = s.perm[slot] >= 0;
+                    if (keep) {
+                        int sv[3];
+                        shift_vec(sh, sv);
+                        const R4<real> p = s.xq[slot];
+                        const float pv[3] = {(float)p.x + sv[0] * (float)s.L[0], (float)p.y + sv[1] * (float)s.L[1],
+                                             (float)p.z + sv[2] * (float)s.L[2]};
+                        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
+                        float d2 = 0.f;
+                        for (int d = 0; d < 3; ++d) {
+                            const float g = fmaxf(fabsf(pv[d] - c0[d]) - h0[d], 0.f);
+                            d2 += g * g;
+                        }
+                        keep = d2 < nb.cut2;
+                    }
+                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                    if (WRITE && keep) {
+                        const int pos = nbuf + __popc(kb & lt);
+                        const int t = base + count + (pos >> 5);
+                        if (t < nb.cap) nb.jidx[(size_t)t * 32 + (pos & 31)] = slot;
+                    }
+                    nbuf += __popc(kb);
+                    while (nbuf >= 32) {
+                        if (WRITE && lane == 0 && base + count < nb.cap)
+                            nb.tiles[base + count] = make_int4(I, sh, cls, 0);
+                        ++count;
+                        nbuf -= 32;
+                    }
                 }
             }
-            count += __popc(bal);
+            if (nbuf > 0) {
+                if (WRITE && base + count < nb.cap) {
+                    if (lane >= nbuf) nb.jidx[(size_t)(base + count) * 32 + lane] = -1;
+                    if (lane == 0) nb.tiles[base + count] = make_int4(I, sh, cls, 0);
+                }
+                ++count;
+            }
         }
     }
     if (!WRITE && lane == 0) nb.tile_cnt[I] = count;
 }
 
-// interaction masks: bit j of lane i set = pair (I*32+i, J*32+j) is computed
+// interaction masks: bit k of lane i set = pair (I*32+i, jidx[k]) is
+// computed: both slots hold atoms, the pair is not excluded, and in the
+// diagonal tile k > i.  Exclusions are looked up only for atoms of the same
+// molecule.
 template <typename real>
 __global__ void k_masks(SysView<real> s, NblView<real> nb)
 {
-    int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    int nt = min(s.flags[FL_NTILES], nb.cap);
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nt = min(s.flags[FL_NTILES], nb.cap);
     if (t >= nt) return;
-    int4 tl = nb.tiles[t];
-    int I = tl.x, J = tl.y, sh = tl.z;
-    unsigned jvalid = __ballot_sync(0xffffffffu, s.perm[J * 32 + lane] >= 0);
-    int a = s.perm[I * 32 + lane];
+    const int4 tl = nb.tiles[t];
+    const int js = nb.jidx[(size_t)t * 32 + lane];
+    const int b = js >= 0 ? s.perm[js] : -1;
+    const int mb = b >= 0 ? nb.mol[b] : -2;
+    const int a = s.perm[tl.x * 32 + lane];
+    const int ma = a >= 0 ? nb.mol[a] : -3;
     unsigned m = 0u;
-    if (a >= 0) {
-        m = jvalid;
-        if (I == J) {
-            if (sh == 13) m &= (lane == 31) ? 0u : (0xffffffffu << (lane + 1));
-            else m &= ~(1u << lane);
+    for (int k = 0; k < 32; ++k) {
+        const int bk = __shfl_sync(0xffffffffu, b, k);
+        const int mk = __shfl_sync(0xffffffffu, mb, k);
+        bool on = a >= 0 && bk >= 0 && (!tl.w || k > lane);
+        if (on && mk == ma) {
+            for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e)
+                if (nb.ex_list[e] == bk) { on = false; break; }
         }
-        for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e) {
-            int sb = s.iperm[nb.ex_list[e]];
-            if ((sb >> 5) == J) m &= ~(1u << (sb & 31));
-        }
+        if (on) m |= 1u << k;
     }
     nb.masks[(size_t)t * 32 + lane] = m;
+}
+
+// dense solute-solvent pair list: the computed pairs of the class-2 tiles
+// (solute cluster x solvent atoms) that lie within r_cut + skin at build
+// time, in (tile, i, k) order
+template <typename real, int WRITE>
+__global__ void k_uv_pairs(SysView<real> s, NblView<real> nb)
+{
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= nb.uv_tiles_max) return;
+    const int nuvt = s.n_ucl > 0 ? min(nb.tile_off[s.n_ucl], nb.cap) : 0;
+    if (t == 0 && lane == 0 && !WRITE && nuvt > nb.uv_tiles_max) atomicOr(&s.flags[FL_ERROR], ERRB_OVERFLOW);
+    int cnt = 0;
+    unsigned keep = 0u;
+    int4 tl = make_int4(0, 13, 0, 0);
+    if (t < nuvt) {
+        tl = nb.tiles[t];
+        if (tl.z == 2) {
+            const unsigned m = nb.masks[(size_t)t * 32 + lane];
+            const R4<real> pi = s.xq[tl.x * 32 + lane];
+            int sv[3];
+            shift_vec(tl.y, sv);
+            for (int k = 0; k < 32; ++k) {
+                const int js = nb.jidx[(size_t)t * 32 + k];
+                if (!((m >> k) & 1u) || js < 0) continue;
+                const R4<real> pj = s.xq[js];
+                const double dx = (double)pj.x + sv[0] * (double)s.L[0] - (double)pi.x;
+                const double dy = (double)pj.y + sv[1] * (double)s.L[1] - (double)pi.y;
+                const double dz = (double)pj.z + sv[2] * (double)s.L[2] - (double)pi.z;
+                if (dx * dx + dy * dy + dz * dz < (double)nb.cut2) keep |= 1u << k;
+            }
+            cnt = __popc(keep);
+        }
+    }
+    if (!WRITE) {
+        const int c = warp_sum_ll(cnt) ;
+        if (lane == 0) nb.uv_cnt[t] = c;
+        return;
+    }
+    // exclusive prefix of the lanes' counts inside the tile
+    int pre = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    int pos = nb.uv_off[t] + pre - cnt;
+    const int si = tl.x * 32 + lane;
+    for (int k = 0; k < 32 && keep; ++k) {
+        if ((keep >> k) & 1u) {
+            if (pos < nb.uv_cap) nb.uvp[pos] = make_int4(si, nb.jidx[(size_t)t * 32 + k], tl.y, 0);
+            ++pos;
+        }
+    }
 }
 
 template <typename real>
@@ -273,20 +434,28 @@ void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStrea
 {
     const int B = 256;
     if (s.n_solv > 0) {
-        k_cell_keys<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
-        k_scan_block<<<1, 1024, 0, st>>>(nb.cnt, nb.start, nb.nkeys, nullptr, 0, nullptr);
-        k_cell_scatter<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
-        k_cell_sort<real><<<(nb.nkeys + B - 1) / B, B, 0, st>>>(nb);
+        k_col_keys<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
+        k_scan_block<<<1, 1024, 0, st>>>(nb.col_cnt, nb.col_start, nb.ncols, nullptr, 0, nullptr);
+        k_col_scatter<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
+        k_col_sort<real><<<nb.ncols, 256, 0, st>>>(s, nb);
+        k_scan_block<<<1, 1024, 0, st>>>(nb.col_ncl, nb.col_cl, nb.ncols, nb.n_cl_solv, 1 << 30, s.flags + FL_ERROR);
     }
     k_assign<real><<<(s.n_pad + B - 1) / B, B, 0, st>>>(s, nb);
-    int wb = (s.n_cl * 32 + B - 1) / B;
-    k_bbox<real><<<wb, B, 0, st>>>(s, nb);
-    k_tiles<real, 0><<<wb, B, 0, st>>>(s, nb);
-    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_cnt, nb.tile_off, s.n_cl, s.flags + FL_NTILES, nb.cap,
+    const int wb = (nb.n_cl_max * 32 + 127) / 128;
+    k_bbox<real><<<wb, 128, 0, st>>>(s, nb);
+    k_tiles<real, 0><<<wb, 128, 0, st>>>(s, nb);
+    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_cnt, nb.tile_off, nb.n_cl_max, s.flags + FL_NTILES, nb.cap,
                                      s.flags + FL_ERROR);
-    k_tiles<real, 1><<<wb, B, 0, st>>>(s, nb);
-    int mb = (int)(((long long)nb.cap * 32 + B - 1) / B);
+    k_tiles<real, 1><<<wb, 128, 0, st>>>(s, nb);
+    const int mb = (int)(((long long)nb.cap * 32 + B - 1) / B);
     k_masks<real><<<mb, B, 0, st>>>(s, nb);
+    if (s.n_ucl > 0) {
+        const int ub = (nb.uv_tiles_max * 32 + B - 1) / B;
+        k_uv_pairs<real, 0><<<ub, B, 0, st>>>(s, nb);
+        k_scan_block<<<1, 1024, 0, st>>>(nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV, nb.uv_cap,
+                                         s.flags + FL_ERROR);
+        k_uv_pairs<real, 1><<<ub, B, 0, st>>>(s, nb);
+    }
 }
 
 // ------------------------------------------------------------ pair kernel
@@ -301,13 +470,39 @@ __device__ __forceinline__ void flush_force(const SysView<real>& s, int slot, lo
     }
 }
 
+// erfc(x) and exp(-x^2).  FP32: exp(-x^2) P(t), t = 1/(1 + p x), with a
+// degree-7 least-squares fit of erfc(x) exp(x^2) on [0, 4.2] (relative
+// error below 5e-8 in exact arithmetic; the fit is reproduced by
+// fit_erfc.py).  FP64: the library functions.
+__device__ __forceinline__ void erfc_exp(float x, float& erfcv, float& ex)
+{
+    const float t = __fdividef(1.0f, fmaf(0.345f, x, 1.0f));
+    float p = -0.23825677533960984f;
+    p = fmaf(p, t, 1.0079999846654213f);
+    p = fmaf(p, t, -1.1369167351186891f);
+    p = fmaf(p, t, 1.1592655395537621f);
+    p = fmaf(p, t, -0.30407340842765385f);
+    p = fmaf(p, t, 0.33999728300708898f);
+    p = fmaf(p, t, 0.17020566942397877f);
+    p = fmaf(p, t, 0.0017784231330017291f);
+    ex = __expf(-x * x);
+    erfcv = p * ex;
+}
+__device__ __forceinline__ void erfc_exp(double x, double& erfcv, double& ex)
+{
+    erfcv = erfc(x);
+    ex = exp(-x * x);
+}
+
 // One warp walks a contiguous chunk of the (I-sorted) tile list.  Lane i
-// holds atom I*32+i; the 32 atoms of J rotate through the lanes by shuffles
-// together with their force accumulators (Newton's third law inside the
-// tile).  The tile's class (vv, uu or uv) is uniform, so the branch on it is
-// warp-uniform.  i-forces stay in registers while consecutive tiles share I.
+// holds atom I*32+i; the tile's 32 j atoms rotate through the lanes by
+// shuffles together with their force accumulators (Newton's third law inside
+// the tile).  The tile's class (vv, uu or uv) and shift are uniform, so the
+// branch on them is warp-uniform.  i-forces stay in registers while
+// consecutive tiles share I.  Solute-solvent energies are not accumulated
+// here (k_uv_energy forms them in FP64).
 template <typename real>
-__global__ void __launch_bounds__(128) k_pairs(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real> nb)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -319,13 +514,14 @@ __global__ void __launch_bounds__(128) k_pairs(SysView<real> s, NblView<real> nb
     const int t1 = (int)(((long long)ntiles * (warp + 1)) / nwarp);
     if (t0 >= t1) return;
     const real hA = (real)s.lam->hA, hB = (real)s.lam->hB;
-    const real rc2 = s.rc2, rsw = s.rsw, swi = s.sw_inv_w, alpha = s.alpha, tas = s.two_a_sqrtpi;
+    const real rc2 = s.rc2, swi = s.sw_inv_w, alpha = s.alpha, tas = s.two_a_sqrtpi;
+    const real rsw_swi = s.rsw * s.sw_inv_w;
     const int src = (lane + 1) & 31;
 
     int curI = -1;
     real xi = 0, yi = 0, zi = 0, qi = 0, si = 0, ei = 0;
     long long fix = 0, fiy = 0, fiz = 0;
-    double evv = 0, euu = 0, euv = 0, esoft = 0;
+    double evv = 0, euu = 0;
     int npairs = 0;
 
     for (int t = t0; t < t1; ++t) {
@@ -333,16 +529,17 @@ __global__ void __launch_bounds__(128) k_pairs(SysView<real> s, NblView<real> nb
         if (tl.x != curI) {
             if (curI >= 0) flush_force(s, curI * 32 + lane, fix, fiy, fiz);
             curI = tl.x;
-            R4<real> p = s.xq[curI * 32 + lane];
-            R2<real> l = s.lj[curI * 32 + lane];
+            const R4<real> p = s.xq[curI * 32 + lane];
+            const R2<real> l = s.lj[curI * 32 + lane];
             xi = p.x; yi = p.y; zi = p.z; qi = p.w; si = l.x; ei = l.y;
             fix = fiy = fiz = 0;
         }
         const unsigned m = nb.masks[(size_t)t * 32 + lane];
-        const int slot_j = tl.y * 32 + lane;
-        R4<real> pj = s.xq[slot_j];
-        R2<real> lj = s.lj[slot_j];
-        const int sh = tl.z;
+        const int slot_j = nb.jidx[(size_t)t * 32 + lane];
+        const int sj_load = slot_j >= 0 ? slot_j : 0;
+        const R4<real> pj = s.xq[sj_load];
+        const R2<real> lj = s.lj[sj_load];
+        const int sh = tl.y;
         const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
         // shift the far-side atom down by L so that the subtraction below is
         // the only rounding in the pair vector
@@ -353,155 +550,107 @@ __global__ void __launch_bounds__(128) k_pairs(SysView<real> s, NblView<real> nb
         real yj = sy == -1 ? pj.y - s.L[1] : pj.y;
         real zj = sz == -1 ? pj.z - s.L[2] : pj.z;
         real qj = pj.w, sj = lj.x, ej = lj.y;
-        real fjx = 0, fjy = 0, fjz = 0, fx = 0, fy = 0, fz = 0, e0 = 0, e1 = 0;
+        real fjx = 0, fjy = 0, fjz = 0, fx = 0, fy = 0, fz = 0, e0 = 0;
+        // bit 0 of mr is the mask bit of the j atom this lane holds
+        unsigned mr = __funnelshift_r(m, m, lane);
+        const bool uv = tl.z == 2;
 
-        if (tl.w != 2) {
 #pragma unroll 2
-            for (int k = 0; k < 32; ++k) {
-                const int jj = (lane + k) & 31;
-                const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
-                const real r2 = dx * dx + dy * dy + dz * dz;
-                if (((m >> jj) & 1u) && r2 < rc2) {
-                    const real rinv = rsqrt_(r2);
-                    const real r = r2 * rinv;
-                    const real rinv2 = rinv * rinv;
-                    const real qq = qi * qj;
-                    const real ar = alpha * r;
-                    const real ec = qq * erfc_(ar) * rinv;
-                    const real fc = (ec + qq * tas * exp_(-ar * ar)) * rinv2;
-                    const real sg = si + sj, e4 = ei * ej;
-                    const real s2 = sg * sg * rinv2;
-                    const real s6 = s2 * s2 * s2;
-                    real v = e4 * (s6 * s6 - s6);
-                    real fl = e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
-                    const real tt = fmax((real)0, (r - rsw) * swi);
-                    const real tt2 = tt * tt;
-                    const real S = (real)1 - tt2 * tt * ((real)10 - (real)15 * tt + (real)6 * tt2);
-                    const real dS = (real)-30 * tt2 * ((real)1 - tt) * ((real)1 - tt) * swi;
-                    fl = fl * S - v * dS * rinv;
-                    v *= S;
-                    const real g = fc + fl;
-                    fx -= g * dx; fy -= g * dy; fz -= g * dz;
-                    fjx += g * dx; fjy += g * dy; fjz += g * dz;
-                    e0 += ec + v;
-                    ++npairs;
-                }
-                xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
-                zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
-                sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
-                fjx = __shfl_sync(FULL, fjx, src); fjy = __shfl_sync(FULL, fjy, src);
-                fjz = __shfl_sync(FULL, fjz, src);
-            }
-            if (tl.w == 0) evv += (double)e0;
-            else euu += (double)e0;
-        } else {
-            for (int k = 0; k < 32; ++k) {
-                const int jj = (lane + k) & 31;
-                const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
-                const real r2 = dx * dx + dy * dy + dz * dz;
-                if (((m >> jj) & 1u) && r2 < rc2) {
-                    const real rinv = rsqrt_(r2);
-                    const real r = r2 * rinv;
-                    const real rinv2 = rinv * rinv;
-                    const real qq = qi * qj;
-                    const real ar = alpha * r;
-                    const real ec = qq * erfc_(ar) * rinv;
-                    const real fc = (ec + qq * tas * exp_(-ar * ar)) * rinv2;
-                    const real sg = si + sj, e4 = ei * ej;
-                    const real s2 = sg * sg * rinv2;
-                    const real s6 = s2 * s2 * s2;
-                    real v = e4 * (s6 * s6 - s6);
-                    real fl = e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
-                    const real tt = fmax((real)0, (r - rsw) * swi);
-                    const real tt2 = tt * tt;
-                    const real S = (real)1 - tt2 * tt * ((real)10 - (real)15 * tt + (real)6 * tt2);
-                    const real dS = (real)-30 * tt2 * ((real)1 - tt) * ((real)1 - tt) * swi;
-                    fl = fl * S - v * dS * rinv;
-                    v *= S;
+        for (int k = 0; k < 32; ++k) {
+            const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            if ((mr & 1u) && r2 < rc2) {
+                const real rinv = rsqrt_(r2);
+                const real r = r2 * rinv;
+                const real rinv2 = rinv * rinv;
+                const real qq = qi * qj;
+                real erfcv, ex;
+                erfc_exp(alpha * r, erfcv, ex);
+                const real ec = qq * erfcv * rinv;
+                const real fc = (ec + qq * tas * ex) * rinv2;
+                const real sg = si + sj, e4 = ei * ej;
+                const real s2 = sg * sg * rinv2;
+                const real s6 = s2 * s2 * s2;
+                real v = e4 * (s6 * s6 - s6);
+                real fl = e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
+                const real tt = fmax((real)0, r * swi - rsw_swi);
+                const real tt2 = tt * tt;
+                const real S = (real)1 - tt2 * tt * ((real)10 - (real)15 * tt + (real)6 * tt2);
+                const real omt = (real)1 - tt;
+                const real dS = (real)-30 * tt2 * omt * omt * swi;
+                fl = fl * S - v * dS * rinv;
+                v *= S;
+                real g = fc + fl;
+                if (uv) {
                     // capped soft basis (Eq. 5-6): identical to LJ for r >= sigma_ij
-                    real vs = v, fs = fl;
-                    if (e4 == (real)0) { vs = 0; fs = 0; }
-                    else if (r < sg) {
+                    real fs = fl;
+                    if (e4 == (real)0) {
+                        fs = 0;
+                    } else if (r < sg) {
                         const real sgi = (real)1 / sg;
                         const real x = r * sgi, x2 = x * x, x3 = x2 * x;
                         const real u = ((real)-868 * x2 + (real)2188.8 * x - (real)1440) * x3 * x + (real)119.2;
                         const real du = ((real)-5208 * x2 + (real)10944 * x - (real)5760) * x3;
-                        const real ep = (real)0.25 * e4;
-                        vs = ep * u * S;
-                        fs = -ep * (du * sgi * S + u * dS) * rinv;
+                        fs = -(real)0.25 * e4 * (du * sgi * S + u * dS) * rinv;
                     }
-                    const real g = hA * (fc + fl) + hB * fs;
-                    fx -= g * dx; fy -= g * dy; fz -= g * dz;
-                    fjx += g * dx; fjy += g * dy; fjz += g * dz;
-                    e0 += ec + v;
-                    e1 += vs;
-                    ++npairs;
+                    g = hA * g + hB * fs;
                 }
-                xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
-                zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
-                sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
-                fjx = __shfl_sync(FULL, fjx, src); fjy = __shfl_sync(FULL, fjy, src);
-                fjz = __shfl_sync(FULL, fjz, src);
+                fx -= g * dx; fy -= g * dy; fz -= g * dz;
+                fjx += g * dx; fjy += g * dy; fjz += g * dz;
+                e0 += ec + v;
+                ++npairs;
             }
-            // solute-solvent energies come from the FP64 kernel k_uv_energy
-            (void)e0;
-            (void)e1;
+            mr = __funnelshift_r(mr, mr, 1);
+            xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
+            zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
+            sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
+            fjx = __shfl_sync(FULL, fjx, src); fjy = __shfl_sync(FULL, fjy, src);
+            fjz = __shfl_sync(FULL, fjz, src);
         }
+        if (tl.z == 0) evv += (double)e0;
+        else if (tl.z == 1) euu += (double)e0;
         fix += to_fixed(fx, FSCALE);
         fiy += to_fixed(fy, FSCALE);
         fiz += to_fixed(fz, FSCALE);
-        flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
+        if (slot_j >= 0)
+            flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
     }
     flush_force(s, curI * 32 + lane, fix, fiy, fiz);
-    long long a0 = __double2ll_rn(warp_sum_d(evv) * ESCALE);
-    long long a1 = __double2ll_rn(warp_sum_d(euu) * ESCALE);
-    long long a2 = __double2ll_rn(warp_sum_d(euv) * ESCALE);
-    long long a3 = __double2ll_rn(warp_sum_d(esoft) * ESCALE);
-    long long a4 = warp_sum_ll((long long)npairs);
+    const long long a0 = __double2ll_rn(warp_sum_d(evv) * ESCALE);
+    const long long a1 = __double2ll_rn(warp_sum_d(euu) * ESCALE);
+    const long long a4 = warp_sum_ll((long long)npairs);
     if (lane == 0) {
         if (a0) atomic_add_ll(&s.E[E_PAIR_VV], a0);
         if (a1) atomic_add_ll(&s.E[E_PAIR_UU], a1);
-        if (a2) atomic_add_ll(&s.E[E_PAIR_UV], a2);
-        if (a3) atomic_add_ll(&s.E[E_PAIR_SOFT], a3);
         atomic_add_ll(&s.E[E_NPAIRS], a4);
     }
 }
 
-// Solute-solvent basis energies U_uv (real-space part) and U_soft in FP64.
-// They set dU/dlambda = h_A' U_uv + h_B' U_soft, whose tolerance (1e-6
-// relative) is below what FP32 pair arithmetic delivers, so they are recomputed
-// here from the same tiles and masks: one thread per (uv tile, i, j) slot in a
-// grid-stride loop over the whole GPU, so the few thousand pairs use the FP64
-// pipes of every SM while the FP32 pair kernel computes forces.  The pair
-// vector is formed exactly: coordinates are floats, their sums are exact in
-// double.
+// Solute-solvent basis energies U_uv (real-space part) and U_soft in FP64
+// over the dense solute-solvent pair list.  They set dU/dlambda = h_A' U_uv +
+// h_B' U_soft, whose tolerance (1e-6 relative) is below what FP32 pair
+// arithmetic delivers; one thread per listed pair spreads the few thousand
+// pairs over the FP64 pipes of every SM while the FP32 pair kernel computes
+// the forces.  The pair vector is exact: coordinates are floats, their sums
+// are exact in double.
 template <typename real>
 __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real> nb)
 {
-    const int n_uv_tiles = s.n_ucl > 0 ? min(nb.tile_off[s.n_ucl], nb.cap) : 0;
-    const long long total = (long long)n_uv_tiles * 1024;
+    const int n = min(s.flags[FL_NUV], nb.uv_cap);
     const double rc2 = (double)s.rc2, rsw = (double)s.rsw, swi = (double)s.sw_inv_w;
     const double alpha = (double)s.alpha;
     double euv = 0.0, esoft = 0.0;
-    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
-         w += (long long)gridDim.x * blockDim.x) {
-        const int t = (int)(w >> 10), i = (int)((w >> 5) & 31), j = (int)(w & 31);
-        const int4 tl = nb.tiles[t];
-        if (tl.w != 2) continue;
-        if (!((nb.masks[(size_t)t * 32 + i] >> j) & 1u)) continue;
-        const int si = tl.x * 32 + i, sj = tl.y * 32 + j;
-        const R4<real> pi = s.xq[si], pj = s.xq[sj];
-        const int sh = tl.z;
-        const int sv[3] = {sh % 3 - 1, (sh / 3) % 3 - 1, sh / 9 - 1};
-        const double xi[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
-        const double xj[3] = {(double)pj.x, (double)pj.y, (double)pj.z};
-        double r2 = 0.0;
-        for (int d = 0; d < 3; ++d) {
-            const double dd = xj[d] + sv[d] * (double)s.L[d] - xi[d];
-            r2 += dd * dd;
-        }
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x) {
+        const int4 pr = nb.uvp[w];
+        const R4<real> pi = s.xq[pr.x], pj = s.xq[pr.y];
+        int sv[3];
+        shift_vec(pr.z, sv);
+        const double dx = (double)pj.x + sv[0] * (double)s.L[0] - (double)pi.x;
+        const double dy = (double)pj.y + sv[1] * (double)s.L[1] - (double)pi.y;
+        const double dz = (double)pj.z + sv[2] * (double)s.L[2] - (double)pi.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < rc2)) continue;
-        const int a = s.perm[si], b = s.perm[sj];
+        const int a = s.perm[pr.x], b = s.perm[pr.y];
         const double r = sqrt(r2);
         const double qq = KE * (double)s.q[a] * (double)s.q[b];
         double e = qq * erfc(alpha * r) / r;
@@ -522,8 +671,8 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
         }
         euv += e;
     }
-    long long a0 = __double2ll_rn(warp_sum_d(euv) * ESCALE);
-    long long a1 = __double2ll_rn(warp_sum_d(esoft) * ESCALE);
+    const long long a0 = __double2ll_rn(warp_sum_d(euv) * ESCALE);
+    const long long a1 = __double2ll_rn(warp_sum_d(esoft) * ESCALE);
     if ((threadIdx.x & 31) == 0) {
         if (a0) atomic_add_ll(&s.E[E_PAIR_UV], a0);
         if (a1) atomic_add_ll(&s.E[E_PAIR_SOFT], a1);
