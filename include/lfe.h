@@ -197,8 +197,38 @@ int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms /*[
 int lfe_batch_step(lfe_batch* b, int n_steps, void* stream);
 void lfe_batch_destroy(lfe_batch* b);
 
+/* Reciprocal-space (smooth PME) part of Eq. 4 for one configuration,
+ * without any device allocation.  The paper has no counterpart: this entry
+ * exists for callers that cannot let a library call cudaMalloc -- code that
+ * runs while another framework captures the stream into a CUDA graph in the
+ * global capture mode (allocation calls are not permitted then), processes
+ * whose device memory belongs to a pool or allocator that forbids hidden
+ * allocations, and services that must not grow their memory after start-up.
+ *
+ * The grids live in one fixed file-scope device array sized for
+ * LFE_NOALLOC_MAX_GRID grid points (about 4.4 MB), which every GPU that loads
+ * the library holds until the process exits; larger grids are rejected with
+ * LFE_ERR_ARG.  All pointers are device memory on the current device:
+ *   pos [3n], charge [n], solute [n] (1 = solute), forces [3n] (written),
+ *   energies [3] (written): the class energies (reciprocal + self +
+ *   neutralising background) E_vv, E_uu, E_uv.
+ * box [3] and grid [3] are host arrays; lambda selects h_A(lambda) for the
+ * forces (solvent atoms feel phi_v + h_A phi_u, solute atoms phi_u + h_A
+ * phi_v).  Work is queued on `stream`; outputs are complete when the stream
+ * reaches the end of the call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and should come before any
+ * stream capture.  Every call shares the array: calls that overlap on the
+ * GPU (different streams, or threads without ordering) race and give wrong
+ * results.  Errors: LFE_ERR_ARG (sizes, grid too large), LFE_ERR_CUDA; the
+ * message is available from lfe_last_error(NULL). */
+#define LFE_NOALLOC_MAX_GRID 110592   /* 48 x 48 x 48 */
+int lfe_pme_noalloc(int n, const double* pos, const double* charge, const unsigned char* solute,
+                    const double* box, double alpha, const int* grid, double lambda,
+                    double* forces, double* energies, void* stream);
+
 /* Message of the last error recorded for sys (or of the last failed
- * lfe_create when sys is NULL).  Valid until the next call on sys. */
+ * lfe_create or lfe_pme_noalloc when sys is NULL).  Valid until the next call
+ * on sys. */
 const char* lfe_last_error(const lfe_system* sys);
 
 void lfe_destroy(lfe_system* sys);

@@ -62,6 +62,10 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull)
 
 }  // namespace
 
+namespace lfe {
+void record_global_error(const std::string& m) { g_create_error = m; }
+}  // namespace lfe
+
 struct SystemBase {
     virtual ~SystemBase() {}
     int precision = 0;

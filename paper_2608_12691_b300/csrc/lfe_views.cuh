@@ -1,6 +1,8 @@
 // lfe_views.cuh -- plain-pointer views of a system's device buffers, passed
 // by value to kernels, and the host-side launcher declarations.
 #pragma once
+#include <string>
+
 #include "lfe_dev.cuh"
 
 namespace lfe {
@@ -172,5 +174,8 @@ template <typename real> void launch_eval_out(const SysView<real>& s, double* fo
                                               cudaStream_t st);
 template <typename real> void launch_assign_positions(const SysView<real>& s, const double* pos, cudaStream_t st);
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
+
+// message returned by lfe_last_error(NULL)
+void record_global_error(const std::string& m);
 
 }  // namespace lfe

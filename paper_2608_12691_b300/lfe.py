@@ -30,8 +30,9 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
     "lfe_time_stages", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
-    "lfe_batch_destroy", "lfe_last_error", "lfe_destroy",
+    "lfe_batch_destroy", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
+NOALLOC_MAX_GRID = 110592
 
 
 class LfeError(RuntimeError):
@@ -119,6 +120,8 @@ def load():
     lib.lfe_last_error.restype = ctypes.c_char_p
     lib.lfe_destroy.argtypes = [vp]
     lib.lfe_destroy.restype = None
+    lib.lfe_pme_noalloc.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_int), ctypes.c_double, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -140,6 +143,19 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+def pme_noalloc(n, pos_ptr, charge_ptr, solute_ptr, box, alpha, grid, lam, forces_ptr, energies_ptr,
+                stream=None):
+    """Reciprocal-space class energies and forces without device allocation
+    (all pointers are device memory; see lfe_pme_noalloc in include/lfe.h)."""
+    lib = load()
+    b = (ctypes.c_double * 3)(*[float(x) for x in box])
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    rc = lib.lfe_pme_noalloc(int(n), pos_ptr, charge_ptr, solute_ptr, b, float(alpha), g, float(lam),
+                             forces_ptr, energies_ptr, _stream_ptr(stream))
+    if rc != LFE_OK:
+        raise LfeError(rc, lib.lfe_last_error(None).decode())
 
 
 class System:
