@@ -243,49 +243,49 @@ void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t
 // group's Lagrange multipliers), v = (x_new - x)/dt.  All of it is done in
 // coordinates relative to the group's first atom (small numbers, so FP32
 // keeps full relative precision and the velocity comes from the displacement
-// itself, not from a difference of two absolute positions).  Consumes
-// (zeroes) the fixed-point forces, refreshes the sorted coordinates and flags
-// a neighbour rebuild when an atom has moved more than skin/2 since the last
-// build.
-template <typename real>
-__global__ void k_integrate(SysView<real> s, StepView<real> g)
+// itself, not from a difference of two absolute positions).  The group shape
+// (single atom, rigid water, X-Hn star) is a template parameter so that every
+// array index is a compile-time constant and the state stays in registers.
+// Consumes (zeroes) the fixed-point forces, refreshes the sorted coordinates
+// and flags a neighbour rebuild when an atom has moved more than skin/2 since
+// the last build.
+template <int KIND, int NA>
+struct Shape {
+    static constexpr int NC = KIND == GROUP_WATER ? 3 : NA - 1;
+    static __device__ __forceinline__ constexpr int ci(int k) { return KIND == GROUP_WATER ? (k == 2 ? 1 : 0) : 0; }
+    static __device__ __forceinline__ constexpr int cj(int k) { return KIND == GROUP_WATER ? (k == 0 ? 1 : 2) : k + 1; }
+};
+
+template <typename real, int KIND, int NA>
+__device__ __forceinline__ void integrate_group(const SysView<real>& s, const StepView<real>& g, const Group& G,
+                                                unsigned long long step)
 {
-    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gi >= g.n_groups) return;
-    const Group G = g.groups[gi];
-    const unsigned long long step = s.lam->step;
-    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {
-        // the neighbour list was truncated: consume the forces, leave the
-        // state untouched (the host regrows the list and replays the step)
-        for (int a = 0; a < G.natom; ++a) {
-            const int slot = s.iperm[G.atom[a]];
-            s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
-        }
-        return;
-    }
-    real o0[3];              // old absolute position of atom 0
-    real rel0[4][3];         // old positions relative to atom 0 (minimum image)
-    real p[4][3];            // new positions relative to old atom 0
-    real w[4];
-    bool bad = false;
+    using Sh = Shape<KIND, NA>;
+    constexpr int NC = Sh::NC;
+    real o0[3];
+    real rel0[NA][3];
+    real p[NA][3];
+    real w[NA];
+    int slot[NA];
     {
         const R4<real> x0 = s.x[G.atom[0]];
         o0[0] = x0.x; o0[1] = x0.y; o0[2] = x0.z;
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        if (a >= G.natom) break;
+    for (int a = 0; a < NA; ++a) {
         const int atom = G.atom[a];
-        const int slot = s.iperm[atom];
-        const real f[3] = {(real)((double)s.F[slot] * (1.0 / FSCALE)),
-                           (real)((double)s.F[s.n_pad + slot] * (1.0 / FSCALE)),
-                           (real)((double)s.F[2 * s.n_pad + slot] * (1.0 / FSCALE))};
-        s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+        slot[a] = s.iperm[atom];
+        const real f[3] = {(real)((double)s.F[slot[a]] * (1.0 / FSCALE)),
+                           (real)((double)s.F[s.n_pad + slot[a]] * (1.0 / FSCALE)),
+                           (real)((double)s.F[2 * s.n_pad + slot[a]] * (1.0 / FSCALE))};
+        s.F[slot[a]] = 0; s.F[s.n_pad + slot[a]] = 0; s.F[2 * s.n_pad + slot[a]] = 0;
         const R4<real> x = s.x[atom], v = s.v[atom];
         const real xa[3] = {x.x, x.y, x.z};
+#pragma unroll
         for (int d = 0; d < 3; ++d) rel0[a][d] = a == 0 ? (real)0 : minimg(xa[d] - o0[d], s.L[d], s.invL[d]);
         w[a] = s.invm[atom];
         if (w[a] == (real)0) {
+#pragma unroll
             for (int d = 0; d < 3; ++d) p[a][d] = rel0[a][d];
             continue;
         }
@@ -294,6 +294,7 @@ __global__ void k_integrate(SysView<real> s, StepView<real> g)
                        nr[0], nr[1], nr[2]);
         const real sd = sqrt(g.kT * ((real)1 - g.a_fric * g.a_fric) * w[a]);
         const real vv[3] = {v.x, v.y, v.z};
+#pragma unroll
         for (int d = 0; d < 3; ++d) {
             real vd = vv[d] + g.dt * w[a] * f[d];
             real disp = (real)0.5 * g.dt * vd;
@@ -302,19 +303,23 @@ __global__ void k_integrate(SysView<real> s, StepView<real> g)
             p[a][d] = rel0[a][d] + disp;
         }
     }
-    if (G.ncons > 0) {
-        real sref[3][3];
-        for (int k = 0; k < G.ncons; ++k)
-            for (int d = 0; d < 3; ++d) sref[k][d] = rel0[G.cj[k]][d] - rel0[G.ci[k]][d];
+    if (NC > 0) {
+        real sref[NC > 0 ? NC : 1][3];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sref[k][d] = rel0[Sh::cj(k)][d] - rel0[Sh::ci(k)][d];
         const real tol = sizeof(real) == 4 ? (real)2e-6 : (real)1e-12;
         bool conv = false;
         for (int it = 0; it < 32; ++it) {
-            real r[3][3], sig[3];
+            real r[NC > 0 ? NC : 1][3], sig[NC > 0 ? NC : 1];
             conv = true;
-            for (int k = 0; k < G.ncons; ++k) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
                 real r2 = 0;
+#pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    r[k][d] = p[G.cj[k]][d] - p[G.ci[k]][d];
+                    r[k][d] = p[Sh::cj(k)][d] - p[Sh::ci(k)][d];
                     r2 += r[k][d] * r[k][d];
                 }
                 const real l2 = (real)G.len[k] * (real)G.len[k];
@@ -324,37 +329,41 @@ __global__ void k_integrate(SysView<real> s, StepView<real> g)
             if (conv) break;
             // J_kl = 2 r_k . (M_kl s_l), M_kl = w_cj(k) c(cj_k, l) - w_ci(k) c(ci_k, l),
             // c(a, l) = +1 if a is the second atom of constraint l, -1 if the first
-            real J[3][3];
-            for (int k = 0; k < G.ncons; ++k)
-                for (int l = 0; l < G.ncons; ++l) {
-                    auto c = [&](int at, int ll) -> real {
-                        return at == G.cj[ll] ? (real)1 : (at == G.ci[ll] ? (real)-1 : (real)0);
-                    };
-                    const real M = w[G.cj[k]] * c(G.cj[k], l) - w[G.ci[k]] * c(G.ci[k], l);
+            real J[NC > 0 ? NC : 1][NC > 0 ? NC : 1];
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+#pragma unroll
+                for (int l = 0; l < NC; ++l) {
+                    const real cjj = Sh::cj(k) == Sh::cj(l) ? (real)1 : (Sh::cj(k) == Sh::ci(l) ? (real)-1 : (real)0);
+                    const real cii = Sh::ci(k) == Sh::cj(l) ? (real)1 : (Sh::ci(k) == Sh::ci(l) ? (real)-1 : (real)0);
+                    const real M = w[Sh::cj(k)] * cjj - w[Sh::ci(k)] * cii;
                     J[k][l] = (real)2 * M * (r[k][0] * sref[l][0] + r[k][1] * sref[l][1] + r[k][2] * sref[l][2]);
                 }
-            real dl[3] = {0, 0, 0};
-            if (G.ncons == 1) {
+            real dl[NC > 0 ? NC : 1];
+            if (NC == 1) {
                 dl[0] = -sig[0] / J[0][0];
-            } else if (G.ncons == 2) {
-                const real det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-                dl[0] = (-sig[0] * J[1][1] + sig[1] * J[0][1]) / det;
-                dl[1] = (-sig[1] * J[0][0] + sig[0] * J[1][0]) / det;
+            } else if (NC == 2) {
+                const real det = J[0][0] * J[1][NC - 1] - J[0][NC - 1] * J[NC - 1][0];
+                dl[0] = (-sig[0] * J[NC - 1][NC - 1] + sig[NC - 1] * J[0][NC - 1]) / det;
+                dl[NC - 1] = (-sig[NC - 1] * J[0][0] + sig[0] * J[NC - 1][0]) / det;
             } else {
-                const real c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-                const real c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-                const real c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-                const real det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-                const real b0 = -sig[0], b1 = -sig[1], b2 = -sig[2];
+                constexpr int A = NC > 2 ? 1 : 0, Bq = NC > 2 ? 2 : 0;
+                const real c00 = J[A][A] * J[Bq][Bq] - J[A][Bq] * J[Bq][A];
+                const real c01 = J[A][Bq] * J[Bq][0] - J[A][0] * J[Bq][Bq];
+                const real c02 = J[A][0] * J[Bq][A] - J[A][A] * J[Bq][0];
+                const real det = J[0][0] * c00 + J[0][A] * c01 + J[0][Bq] * c02;
+                const real b0 = -sig[0], b1 = -sig[A], b2 = -sig[Bq];
                 // Cramer's rule
-                dl[0] = (b0 * c00 + J[0][1] * (J[1][2] * b2 - b1 * J[2][2]) + J[0][2] * (b1 * J[2][1] - J[1][1] * b2)) / det;
-                dl[1] = (J[0][0] * (b1 * J[2][2] - J[1][2] * b2) + b0 * c01 + J[0][2] * (J[1][0] * b2 - b1 * J[2][0])) / det;
-                dl[2] = (J[0][0] * (J[1][1] * b2 - b1 * J[2][1]) + J[0][1] * (b1 * J[2][0] - J[1][0] * b2) + b0 * c02) / det;
+                dl[0] = (b0 * c00 + J[0][A] * (J[A][Bq] * b2 - b1 * J[Bq][Bq]) + J[0][Bq] * (b1 * J[Bq][A] - J[A][A] * b2)) / det;
+                dl[A] = (J[0][0] * (b1 * J[Bq][Bq] - J[A][Bq] * b2) + b0 * c01 + J[0][Bq] * (J[A][0] * b2 - b1 * J[Bq][0])) / det;
+                dl[Bq] = (J[0][0] * (J[A][A] * b2 - b1 * J[Bq][A]) + J[0][A] * (b1 * J[Bq][0] - J[A][0] * b2) + b0 * c02) / det;
             }
-            for (int l = 0; l < G.ncons; ++l)
+#pragma unroll
+            for (int l = 0; l < NC; ++l)
+#pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    p[G.cj[l]][d] += dl[l] * w[G.cj[l]] * sref[l][d];
-                    p[G.ci[l]][d] -= dl[l] * w[G.ci[l]] * sref[l][d];
+                    p[Sh::cj(l)][d] += dl[l] * w[Sh::cj(l)] * sref[l][d];
+                    p[Sh::ci(l)][d] -= dl[l] * w[Sh::ci(l)] * sref[l][d];
                 }
         }
         if (!conv) atomicOr(&s.flags[FL_ERROR], ERRB_CONSTRAINT);
@@ -362,14 +371,13 @@ __global__ void k_integrate(SysView<real> s, StepView<real> g)
     // keep each group near the box: shift it by whole periods when its first
     // atom leaves [0, L)
     real shift[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) shift[d] = -s.L[d] * floor((o0[d] + p[0][d]) * s.invL[d]);
     const real inv_dt = (real)1 / g.dt;
-    bool rebuild = false;
+    bool rebuild = false, bad = false;
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        if (a >= G.natom) break;
+    for (int a = 0; a < NA; ++a) {
         const int atom = G.atom[a];
-        const int slot = s.iperm[atom];
         R4<real> xnew, vnew;
         if (w[a] == (real)0) {
             vnew.x = vnew.y = vnew.z = (real)0;
@@ -386,25 +394,53 @@ __global__ void k_integrate(SysView<real> s, StepView<real> g)
         if (!isfinite(xnew.x) || !isfinite(xnew.y) || !isfinite(xnew.z)) bad = true;
         s.x[atom] = xnew;
         s.v[atom] = vnew;
-        R4<real> o = s.xq[slot];
+        R4<real> o = s.xq[slot[a]];
         o.x = wrap_sorted(xnew.x, s.L[0], s.invL[0]);
         o.y = wrap_sorted(xnew.y, s.L[1], s.invL[1]);
         o.z = wrap_sorted(xnew.z, s.L[2], s.invL[2]);
-        s.xq[slot] = o;
+        s.xq[slot[a]] = o;
         const R4<real> xr = s.xref[atom];
         const real dx = minimg(xnew.x - xr.x, s.L[0], s.invL[0]);
         const real dy = minimg(xnew.y - xr.y, s.L[1], s.invL[1]);
         const real dz = minimg(xnew.z - xr.z, s.L[2], s.invL[2]);
         if (dx * dx + dy * dy + dz * dz > g.skin_half2) rebuild = true;
     }
-    if (rebuild) atomicOr(&s.flags[FL_REBUILD], 1);
-    if (bad) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+    // one atomic per warp (thousands of groups cross the skin at once)
+    const unsigned act = __activemask();
+    const bool any_rebuild = __any_sync(act, rebuild), any_bad = __any_sync(act, bad);
+    if ((threadIdx.x & 31) == __ffs(act) - 1) {
+        if (any_rebuild && !s.flags[FL_REBUILD]) atomicOr(&s.flags[FL_REBUILD], 1);
+        if (any_bad) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+    }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real> g)
+{
+    const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= g.n_groups) return;
+    const Group G = g.groups[gi];
+    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {
+        // the neighbour list was truncated: consume the forces, leave the
+        // state untouched (the host regrows the list and replays the step)
+        for (int a = 0; a < G.natom; ++a) {
+            const int slot = s.iperm[G.atom[a]];
+            s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+        }
+        return;
+    }
+    const unsigned long long step = s.lam->step;
+    if (G.kind == GROUP_WATER) integrate_group<real, GROUP_WATER, 3>(s, g, G, step);
+    else if (G.kind == GROUP_STAR && G.natom == 4) integrate_group<real, GROUP_STAR, 4>(s, g, G, step);
+    else if (G.kind == GROUP_STAR && G.natom == 3) integrate_group<real, GROUP_STAR, 3>(s, g, G, step);
+    else if (G.kind == GROUP_STAR && G.natom == 2) integrate_group<real, GROUP_STAR, 2>(s, g, G, step);
+    else integrate_group<real, GROUP_SINGLE, 1>(s, g, G, step);
 }
 
 template <typename real>
 void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st)
 {
-    k_integrate<real><<<(g.n_groups + 127) / 128, 128, 0, st>>>(s, g);
+    k_integrate<real><<<(g.n_groups + 63) / 64, 64, 0, st>>>(s, g);
 }
 
 // --------------------------------------------------------- theta and OPES
@@ -488,15 +524,7 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const int lane = threadIdx.x;
     LamState* L = s.lam;
     long long* E = s.E;
-    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {
-        // step skipped (see k_integrate); no rebuild until the host regrows
-        if (lane == 0) {
-            if (t.use_cond) cudaGraphSetConditional(t.cond, 0u);
-            if (t.use_cond) s.flags[FL_REBUILD] = 0;
-        }
-        if (lane < E_N) E[lane] = 0;
-        return;
-    }
+    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) return;   // step skipped (see k_integrate)
     const double Uvv = efix(E, E_PAIR_VV) + efix(E, E_EXCL_VV) + efix(E, E_14_VV) + efix(E, E_REC_VV) + t.const_vv;
     const double Uuu = efix(E, E_PAIR_UU) + efix(E, E_EXCL_UU) + efix(E, E_14_UU) + efix(E, E_REC_UU) + t.const_uu;
     const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
@@ -537,21 +565,43 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         L->dlam_dtheta = thn <= 1.0 ? 1.0 : -1.0;
         L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
         L->dUdl = dUdl; L->U = U; L->V_std = V0; L->V_exp = V1;
-        L->step = stepn;
         if (!isfinite(U) || !isfinite(thn)) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+    }
+}
+
+// end of a step, after the atoms and theta have moved: advance the step
+// counter (the Philox counter of both integrators), clear the energy
+// accumulators, and (inside the captured graph) choose whether the
+// conditional neighbour-list rebuild runs
+template <typename real>
+__global__ void k_step_end(SysView<real> s, ThetaView<real> t)
+{
+    const int lane = threadIdx.x;
+    if (lane == 0 && !(s.flags[FL_ERROR] & ERRB_OVERFLOW)) {
+        s.lam->step += 1;
         if (t.use_cond) {
-            cudaGraphSetConditional(t.cond, s.flags[FL_REBUILD] ? 1u : 0u);
-            if (s.flags[FL_REBUILD]) s.flags[FL_NREBUILD] += 1;
+            const int rb = s.flags[FL_REBUILD];
+            cudaGraphSetConditional(t.cond, rb ? 1u : 0u);
+            if (rb) s.flags[FL_NREBUILD] += 1;
             s.flags[FL_REBUILD] = 0;
         }
+    } else if (lane == 0 && t.use_cond) {
+        cudaGraphSetConditional(t.cond, 0u);
+        s.flags[FL_REBUILD] = 0;
     }
-    if (lane < E_N) E[lane] = 0;
+    if (lane < E_N) s.E[lane] = 0;
 }
 
 template <typename real>
 void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
 {
     k_theta<real><<<1, 32, 0, st>>>(s, t);
+}
+
+template <typename real>
+void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
+{
+    k_step_end<real><<<1, 32, 0, st>>>(s, t);
 }
 
 #define LFE_INST_DYN(real)                                                                               \
@@ -562,7 +612,8 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
     template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
     template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
-    template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
+    template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \
+    template void launch_step_end<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
 LFE_INST_DYN(float)
 LFE_INST_DYN(double)
 

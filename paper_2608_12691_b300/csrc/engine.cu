@@ -105,6 +105,8 @@ struct System final : SystemBase {
     int uv_blocks = 0;
     double const_vv = 0, const_uu = 0, const_uv = 0;
     cudaStream_t cs = nullptr, cs2 = nullptr;
+    cudaStream_t br[4] = {nullptr, nullptr, nullptr, nullptr};   // capture branches
+    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* h_flags = nullptr;        // pinned
@@ -146,6 +148,12 @@ struct System final : SystemBase {
         if (h_flags) cudaFreeHost(h_flags);
         if (cs) cudaStreamDestroy(cs);
         if (cs2) cudaStreamDestroy(cs2);
+        for (int k = 0; k < 4; ++k) {
+            if (br[k]) cudaStreamDestroy(br[k]);
+            if (ev_join[k]) cudaEventDestroy(ev_join[k]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_z) cudaEventDestroy(ev_z);
     }
 
     void create(const lfe_params& p, const lfe_topology& t)
@@ -352,6 +360,7 @@ struct System final : SystemBase {
                 M.K[d] = K;
                 M.KK *= K;
                 M.kscale[d] = (real)(K / p.box[d]);
+                M.kscale64[d] = K / p.box[d];
                 radix_plan(K, M.rad[d], &M.nrad[d]);
                 // |b(m)|^2 with the order-4 spline values M4(1) = 1/6, M4(2) = 2/3, M4(3) = 1/6
                 std::vector<double> gf(K), ms(K);
@@ -383,6 +392,7 @@ struct System final : SystemBase {
                 if (dual) {
                     M64.K[d] = K;
                     M64.kscale[d] = K / p.box[d];
+                    M64.kscale64[d] = K / p.box[d];
                     M64.nrad[d] = M.nrad[d];
                     for (int r = 0; r < 8; ++r) M64.rad[d][r] = M.rad[d][r];
                     M64.gfac[d] = upload(gf);
@@ -407,7 +417,7 @@ struct System final : SystemBase {
                 M.Zraw64 = M64.Z;
             }
             const int Kmax = std::max(M.K[0], std::max(M.K[1], M.K[2]));
-            const size_t smem = sizeof(R2<double>) * (size_t)(Kmax + 2 * 16 * Kmax);
+            const size_t smem = sizeof(R2<double>) * (size_t)(Kmax + 2 * 16 * (Kmax + 1));
             if (smem > 48 * 1024) fail(LFE_ERR_ARG, "PME grid too large for the FFT tile");
         }
 
@@ -466,6 +476,7 @@ struct System final : SystemBase {
                 g.ci[0] = 0; g.cj[0] = 1; g.len[0] = (float)t.water_rOH;
                 g.ci[1] = 0; g.cj[1] = 2; g.len[1] = (float)t.water_rOH;
                 g.ci[2] = 1; g.cj[2] = 2; g.len[2] = (float)t.water_rHH;
+                g.kind = GROUP_WATER;
                 for (int k = 0; k < 3; ++k) {
                     if (owner[g.atom[k]] >= 0) fail(LFE_ERR_ARG, "an atom belongs to two rigid waters");
                     owner[g.atom[k]] = (int)groups.size();
@@ -484,6 +495,7 @@ struct System final : SystemBase {
                     g.atom[0] = a;
                     g.natom = 1;
                     g.ncons = 0;
+                    g.kind = GROUP_STAR;
                     gi = (int)groups.size();
                     groups.push_back(g);
                     centre_group[a] = gi;
@@ -505,9 +517,14 @@ struct System final : SystemBase {
                     Group g{};
                     g.atom[0] = i;
                     g.natom = 1;
+                    g.kind = GROUP_SINGLE;
                     owner[i] = (int)groups.size();
                     groups.push_back(g);
                 }
+            // same-shape groups next to each other keep warps on one code path
+            std::stable_sort(groups.begin(), groups.end(), [](const Group& x, const Group& y) {
+                return x.kind != y.kind ? x.kind < y.kind : x.natom < y.natom;
+            });
             G.groups = upload(groups);
             G.n_groups = (int)groups.size();
         }
@@ -570,6 +587,12 @@ struct System final : SystemBase {
         }
         CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+        for (int k = 0; k < 4; ++k) {
+            CK(cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_z, cudaEventDisableTiming));
         build_neighbors(nullptr);
         CK(cudaStreamSynchronize(nullptr));
         {
@@ -695,6 +718,44 @@ struct System final : SystemBase {
         check_flags(st);
     }
 
+    // The evaluation as four concurrent branches (used inside the captured
+    // step graph): pair kernel | FP32 PME chain | FP64 PME energy branch (it
+    // starts once the first FP32 pass has left the FP64 copy of the charge
+    // grid) | FP64 solute-solvent energies, exclusions and bonded terms.  The
+    // branches only meet in atomic fixed-point accumulators, so their order
+    // does not change any result.  B300 runs the FP64 branches on the FP64
+    // pipes while the FP32 pair and PME kernels use the FP32 pipes.
+    void eval_kernels_branched(cudaStream_t s0)
+    {
+        CK(cudaEventRecord(ev_fork, s0));
+        for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
+        launch_pairs(S, N, pair_warps, br[0]);
+        launch_spread(S, M, br[1]);
+        launch_fft(M, 2, +1, 1, br[1]);
+        CK(cudaEventRecord(ev_z, br[1]));
+        launch_fft(M, 1, +1, 0, br[1]);
+        launch_fft(M, 0, +1, 0, br[1]);
+        launch_conv(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, br[1]);
+        launch_fft(M, 0, -1, 0, br[1]);
+        launch_fft(M, 1, -1, 0, br[1]);
+        launch_fft(M, 2, -1, 0, br[1]);
+        launch_gather(S, M, br[1]);
+        if (dual) {
+            CK(cudaStreamWaitEvent(br[2], ev_z, 0));
+            launch_fft(M64, 2, +1, 0, br[2]);
+            launch_fft(M64, 1, +1, 0, br[2]);
+            launch_fft(M64, 0, +1, 0, br[2]);
+            launch_conv(M64, S.E, S.lam, CONV_ENERGY, br[2]);
+        }
+        launch_uv_energy(S, N, uv_blocks, br[3]);
+        launch_excl(S, X, br[3]);
+        launch_bonded(S, B, br[3]);
+        for (int k = 0; k < 4; ++k) {
+            CK(cudaEventRecord(ev_join[k], br[k]));
+            CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
+        }
+    }
+
     void capture_step_graph()
     {
         cudaStream_t s0 = cs;
@@ -707,9 +768,15 @@ struct System final : SystemBase {
         ThetaView<real> Tc = T;
         Tc.cond = h;
         Tc.use_cond = 1;
-        eval_kernels(s0);
+        eval_kernels_branched(s0);
+        // atoms and theta move concurrently; the step ends when both are done
+        CK(cudaEventRecord(ev_fork, s0));
+        CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
+        launch_theta(S, Tc, br[0]);
+        CK(cudaEventRecord(ev_join[0], br[0]));
         launch_integrate(S, G, s0);
-        launch_theta(S, Tc, s0);
+        CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
+        launch_step_end(S, Tc, s0);
         const cudaGraphNode_t* deps = nullptr;
         size_t ndeps = 0;
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
@@ -747,6 +814,7 @@ struct System final : SystemBase {
         eval_kernels(st);
         launch_integrate(S, G, st);
         launch_theta(S, T, st);
+        launch_step_end(S, T, st);
         CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (h_flags[FL_REBUILD]) {

@@ -93,6 +93,7 @@ struct PmeView {
     int K[3];
     int KK;                   // K0 K1 K2
     real kscale[3];           // K_d / L_d
+    double kscale64[3];       // K_d / L_d in double (fractional coordinates)
     long long* Qfix;          // [2][KK]  (solvent, solute) fixed point
     R2<real>* Z;              // [KK] complex work grid
     const real* gfac[3];      // per-axis exp(-pi^2 m^2 / (L^2 alpha^2)) * |b(m)|^2
@@ -116,12 +117,14 @@ struct BondView {
 
 // constraint groups: a rigid water (3 atoms, 3 constraints), a star of
 // X-H constraints around a centre atom, or a single unconstrained atom
+enum { GROUP_SINGLE = 0, GROUP_WATER = 1, GROUP_STAR = 2 };
 struct Group {
     int atom[4];
     int natom;
     int ncons;
     int ci[3], cj[3];     // constraint k joins atom[ci[k]] and atom[cj[k]]
     float len[3];
+    int kind;             // GROUP_*: water (0-1, 0-2, 1-2) or star (0-k) shapes
 };
 
 template <typename real>
@@ -168,6 +171,7 @@ template <typename real> void launch_gather(const SysView<real>& s, const PmeVie
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
 template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+template <typename real> void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
 template <typename real> void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st);
 template <typename real> void launch_eval_out(const SysView<real>& s, double* forces, double* terms,
                                               double const_vv, double const_uu, double const_uv,

@@ -303,6 +303,7 @@ extern "C" int lfe_pme_noalloc(int n, const double* pos, const double* charge, c
         M.K[d] = M64.K[d] = grid[d];
         M.kscale[d] = (float)(grid[d] / box[d]);
         M64.kscale[d] = grid[d] / box[d];
+        M.kscale64[d] = M64.kscale64[d] = grid[d] / box[d];
         M.nrad[d] = M64.nrad[d] = nrad[d];
         for (int r = 0; r < 8; ++r) M.rad[d][r] = M64.rad[d][r] = rad[d][r];
         M.gfac[d] = dsc->gfac[d];

@@ -287,10 +287,28 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
     }
     count = 1;
     const unsigned lt = (1u << lane) - 1u;
+    // every atom lies in [0, L): a shift -1 (+1) along an axis can bring a
+    // partner within the cutoff only if I's box reaches within r_cut + skin
+    // of the lower (upper) face
+    const float cut = sqrtf(nb.cut2);
+    bool okm[3], okp[3];
+    {
+        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
+        for (int d = 0; d < 3; ++d) {
+            okm[d] = c0[d] - h0[d] < cut;
+            okp[d] = c0[d] + h0[d] > (float)s.L[d] - cut;
+        }
+    }
     for (int jc = 0; jc < 2; ++jc) {
         const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
         const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
         for (int sh = 0; sh < 27; ++sh) {
+            int svs[3];
+            shift_vec(sh, svs);
+            bool allowed = true;
+            for (int d = 0; d < 3; ++d)
+                if ((svs[d] < 0 && !okm[d]) || (svs[d] > 0 && !okp[d])) allowed = false;
+            if (!allowed) continue;
             int nbuf = 0;   // atoms already placed in the open tile
             for (int J0 = max(I, jb); J0 < je; J0 += 32) {
                 const int J = J0 + lane;
@@ -346,13 +364,15 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
 
 // interaction masks: bit k of lane i set = pair (I*32+i, jidx[k]) is
 // computed: both slots hold atoms, the pair is not excluded, and in the
-// diagonal tile k > i.  Exclusions are looked up only for atoms of the same
-// molecule.
+// diagonal tile k > i.  Exclusions are searched only when the tile holds
+// atoms of lane i's molecule: each excluded partner's slot is looked up in
+// the tile's ascending j slots by bisection.
 template <typename real>
-__global__ void k_masks(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(128) k_masks(SysView<real> s, NblView<real> nb)
 {
+    __shared__ int jsl[4][32];
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
     const int nt = min(s.flags[FL_NTILES], nb.cap);
     if (t >= nt) return;
     const int4 tl = nb.tiles[t];
@@ -361,55 +381,75 @@ __global__ void k_masks(SysView<real> s, NblView<real> nb)
     const int mb = b >= 0 ? nb.mol[b] : -2;
     const int a = s.perm[tl.x * 32 + lane];
     const int ma = a >= 0 ? nb.mol[a] : -3;
-    unsigned m = 0u;
+    jsl[wl][lane] = js >= 0 ? js : 0x7fffffff;
+    __syncwarp();
+    const unsigned valid = __ballot_sync(0xffffffffu, b >= 0);
+    unsigned m = 0u, same = 0u;
     for (int k = 0; k < 32; ++k) {
-        const int bk = __shfl_sync(0xffffffffu, b, k);
         const int mk = __shfl_sync(0xffffffffu, mb, k);
-        bool on = a >= 0 && bk >= 0 && (!tl.w || k > lane);
-        if (on && mk == ma) {
-            for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e)
-                if (nb.ex_list[e] == bk) { on = false; break; }
+        same |= (mk == ma ? 1u : 0u) << k;
+    }
+    if (a >= 0) {
+        m = valid;
+        if (tl.w) m &= lane == 31 ? 0u : (0xffffffffu << (lane + 1));
+    }
+    if (m & same) {
+        for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e) {
+            const int sb = s.iperm[nb.ex_list[e]];
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (jsl[wl][mid] < sb) lo = mid + 1;
+                else hi = mid;
+            }
+            if (jsl[wl][lo] == sb) m &= ~(1u << lo);
         }
-        if (on) m |= 1u << k;
     }
     nb.masks[(size_t)t * 32 + lane] = m;
 }
 
 // dense solute-solvent pair list: the computed pairs of the class-2 tiles
 // (solute cluster x solvent atoms) that lie within r_cut + skin at build
-// time, in (tile, i, k) order
+// time, in (tile, i, k) order.  Lanes hold the tile's j atoms; the i atoms
+// are broadcast one by one, so each row costs one ballot.
 template <typename real, int WRITE>
-__global__ void k_uv_pairs(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real> nb)
 {
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= nb.uv_tiles_max) return;
     const int nuvt = s.n_ucl > 0 ? min(nb.tile_off[s.n_ucl], nb.cap) : 0;
     if (t == 0 && lane == 0 && !WRITE && nuvt > nb.uv_tiles_max) atomicOr(&s.flags[FL_ERROR], ERRB_OVERFLOW);
-    int cnt = 0;
-    unsigned keep = 0u;
+    unsigned keep = 0u;   // row of lane i: bits k of kept pairs (i, k)
     int4 tl = make_int4(0, 13, 0, 0);
+    int js = -1;
     if (t < nuvt) {
         tl = nb.tiles[t];
         if (tl.z == 2) {
-            const unsigned m = nb.masks[(size_t)t * 32 + lane];
+            js = nb.jidx[(size_t)t * 32 + lane];
+            const unsigned mi = nb.masks[(size_t)t * 32 + lane];
             const R4<real> pi = s.xq[tl.x * 32 + lane];
+            const R4<real> pj = s.xq[js >= 0 ? js : 0];
             int sv[3];
             shift_vec(tl.y, sv);
-            for (int k = 0; k < 32; ++k) {
-                const int js = nb.jidx[(size_t)t * 32 + k];
-                if (!((m >> k) & 1u) || js < 0) continue;
-                const R4<real> pj = s.xq[js];
-                const double dx = (double)pj.x + sv[0] * (double)s.L[0] - (double)pi.x;
-                const double dy = (double)pj.y + sv[1] * (double)s.L[1] - (double)pi.y;
-                const double dz = (double)pj.z + sv[2] * (double)s.L[2] - (double)pi.z;
-                if (dx * dx + dy * dy + dz * dz < (double)nb.cut2) keep |= 1u << k;
+            const float xj = (float)pj.x + sv[0] * (float)s.L[0];
+            const float yj = (float)pj.y + sv[1] * (float)s.L[1];
+            const float zj = (float)pj.z + sv[2] * (float)s.L[2];
+            for (int i = 0; i < 32; ++i) {
+                const float xi = __shfl_sync(0xffffffffu, (float)pi.x, i);
+                const float yi = __shfl_sync(0xffffffffu, (float)pi.y, i);
+                const float zi = __shfl_sync(0xffffffffu, (float)pi.z, i);
+                const unsigned mrow = __shfl_sync(0xffffffffu, mi, i);
+                const float dx = xj - xi, dy = yj - yi, dz = zj - zi;
+                const bool in = js >= 0 && ((mrow >> lane) & 1u) && dx * dx + dy * dy + dz * dz < nb.cut2;
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (lane == i) keep = bal;
             }
-            cnt = __popc(keep);
         }
     }
+    const int cnt = __popc(keep);
     if (!WRITE) {
-        const int c = warp_sum_ll(cnt) ;
+        const int c = (int)warp_sum_ll(cnt);
         if (lane == 0) nb.uv_cnt[t] = c;
         return;
     }
@@ -421,9 +461,10 @@ __global__ void k_uv_pairs(SysView<real> s, NblView<real> nb)
     }
     int pos = nb.uv_off[t] + pre - cnt;
     const int si = tl.x * 32 + lane;
-    for (int k = 0; k < 32 && keep; ++k) {
+    for (int k = 0; k < 32; ++k) {
+        const int jk = __shfl_sync(0xffffffffu, js, k);
         if ((keep >> k) & 1u) {
-            if (pos < nb.uv_cap) nb.uvp[pos] = make_int4(si, nb.jidx[(size_t)t * 32 + k], tl.y, 0);
+            if (pos < nb.uv_cap) nb.uvp[pos] = make_int4(si, jk, tl.y, 0);
             ++pos;
         }
     }
@@ -447,14 +488,14 @@ void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStrea
     k_scan_block<<<1, 1024, 0, st>>>(nb.tile_cnt, nb.tile_off, nb.n_cl_max, s.flags + FL_NTILES, nb.cap,
                                      s.flags + FL_ERROR);
     k_tiles<real, 1><<<wb, 128, 0, st>>>(s, nb);
-    const int mb = (int)(((long long)nb.cap * 32 + B - 1) / B);
-    k_masks<real><<<mb, B, 0, st>>>(s, nb);
+    const int mb = (int)(((long long)nb.cap * 32 + 127) / 128);
+    k_masks<real><<<mb, 128, 0, st>>>(s, nb);
     if (s.n_ucl > 0) {
-        const int ub = (nb.uv_tiles_max * 32 + B - 1) / B;
-        k_uv_pairs<real, 0><<<ub, B, 0, st>>>(s, nb);
+        const int ub = (nb.uv_tiles_max * 32 + 127) / 128;
+        k_uv_pairs<real, 0><<<ub, 128, 0, st>>>(s, nb);
         k_scan_block<<<1, 1024, 0, st>>>(nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV, nb.uv_cap,
                                          s.flags + FL_ERROR);
-        k_uv_pairs<real, 1><<<ub, B, 0, st>>>(s, nb);
+        k_uv_pairs<real, 1><<<ub, 128, 0, st>>>(s, nb);
     }
 }
 

@@ -71,7 +71,7 @@ __global__ void k_spread(SysView<real> s, PmeView<real> p)
     real xs[3] = {xq.x, xq.y, xq.z};
     for (int d = 0; d < 3; ++d) {
         double w;
-        grid_coord(xs[d], (double)p.kscale[d], p.K[d], f[d], w);
+        grid_coord(xs[d], p.kscale64[d], p.K[d], f[d], w);
         bspline4(w, th[d], dth);
     }
     for (int j0 = 0; j0 < 4; ++j0) {
@@ -171,9 +171,10 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
 {
     extern __shared__ unsigned char smem_raw[];
     const int K = p.K[AXIS];
+    const int LD = K + 1;   // padded line stride: the column loads of axes 0 and 1 hit distinct banks
     R2<real>* tw = reinterpret_cast<R2<real>*>(smem_raw);
     R2<real>* b0 = tw + K;
-    R2<real>* b1 = b0 + FFT_NL * K;
+    R2<real>* b1 = b0 + FFT_NL * LD;
     const int K0 = p.K[0], K1 = p.K[1], K2 = p.K[2];
     const int tid = threadIdx.x, nt = blockDim.x;
 
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
             } else {
                 v = p.Z[g];
             }
-            b0[l * K + t] = v;
+            b0[l * LD + t] = v;
         }
     }
     __syncthreads();
@@ -234,8 +235,8 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
         for (int idx = tid; idx < nl * nbf; idx += nt) {
             const int l = idx / nbf, j = idx % nbf;
             const int k = j % Ns;
-            const R2<real>* in = src + l * K;
-            R2<real>* out = dst + l * K;
+            const R2<real>* in = src + l * LD;
+            R2<real>* out = dst + l * LD;
             R2<real> v[5];
             v[0] = in[j];
             for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], tw[(r * k * tstep) % K]);
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
         int l, t;
         if (AXIS == 2) { l = e / K; t = e % K; }
         else { t = e / FFT_NL; l = e % FFT_NL; }
-        if (l < nl) p.Z[gidx(l, t)] = src[l * K + t];
+        if (l < nl) p.Z[gidx(l, t)] = src[l * LD + t];
     }
 }
 
@@ -259,7 +260,7 @@ template <typename real>
 void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
 {
     const int K = p.K[axis];
-    const size_t smem = sizeof(R2<real>) * (size_t)(K + 2 * FFT_NL * K);
+    const size_t smem = sizeof(R2<real>) * (size_t)(K + 2 * FFT_NL * (K + 1));
     int blocks;
     if (axis == 2) blocks = (p.K[0] * p.K[1] + FFT_NL - 1) / FFT_NL;
     else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + FFT_NL - 1) / FFT_NL);
@@ -355,7 +356,7 @@ __global__ void k_gather(SysView<real> s, PmeView<real> p)
     real xs[3] = {xq.x, xq.y, xq.z};
     for (int d = 0; d < 3; ++d) {
         real w;
-        grid_coord(xs[d], (double)p.kscale[d], p.K[d], f[d], w);
+        grid_coord(xs[d], p.kscale64[d], p.K[d], f[d], w);
         bspline4(w, th[d], dth[d]);
     }
     real gx = 0, gy = 0, gz = 0;
