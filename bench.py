@@ -29,6 +29,10 @@ METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) o
 # design notes: pair vector 3, r^2 5, 1/r and r 3, Coulomb 8 + erfc/exp 12,
 # LJ 15, switch 8, force vector and Newton's third law 9, energy 2, class 2)
 FLOPS_PER_PAIR = 67
+# DRAM bytes (read + write) of one k_pairs<float> launch on the octanol workload, from an ncu
+# capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum); reset to
+# None whenever the pair kernel changes
+PAIR_DRAM_BYTES_OCTANOL = 4.234496e6 + 0.0
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
@@ -233,8 +237,9 @@ def run_ours(args):
         pair_ms = stages["pairs"]
         achieved = n_pairs * FLOPS_PER_PAIR / (pair_ms * 1e-3) / 1e12
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
+        traffic = PAIR_DRAM_BYTES_OCTANOL if (args.workload == "octanol" and prec == lfe.LFE_FP32_MIXED) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_pairs<float>", "kernel_ms": pair_ms,
+                "traffic": traffic, "kernel": "k_pairs<float>", "kernel_ms": pair_ms,
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop/FMA x 2032 MHz (max SM clock)"}
         if clocks and clocks.get("sm_mhz"):
             roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / 2032.0)
