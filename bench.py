@@ -13,6 +13,8 @@ host cores on a bounded sample of the same workload.
 """
 import argparse
 import json
+
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -48,6 +50,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--batch-replicas", type=int, default=32,
+                   help="replicas in the batched leg (half water, half octanol; 0 skips it)")
+    p.add_argument("--batch-steps", type=int, default=40)
     p.add_argument("--profile-case", action="store_true",
                    help="build the workload, run 3 staged evaluations and exit (a small case for ncu)")
     return p.parse_args()
@@ -167,6 +172,64 @@ def equilibrate(g, d, stream):
     g.get_state()
 
 
+def batched_leg(args, stream, flush):
+    """Replicas at lambda_r = r/(R-1), alternately the water system (12,020
+    atoms, 2 fs) and the octanol system (13,520 atoms, 1 fs): mixed precision
+    advanced together (one graph launch per step) versus the same replicas in
+    FP64 advanced one after another with their own graphs."""
+    import torch
+    from paper_2608_12691_b300 import lfe
+    from paper_2608_12691_b300 import systems as S
+    R = args.batch_replicas
+    t0 = time.perf_counter()
+    dicts = []
+    for r in range(R):
+        lam = r / (R - 1)
+        d = S.make_c2(seed=5000 + r, lam=lam) if r % 2 == 0 else S.make_c1(seed=6000 + r, lam=lam)
+        dicts.append(d)
+    t_gen = time.perf_counter() - t0
+    reps = [lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=7000 + r, theta0=d["lam"]) for r, d in enumerate(dicts)]
+    b = lfe.Batch(reps)
+    for frac, fric in ((0.05, 100.0), (0.25, 50.0), (0.5, 20.0), (1.0, None)):
+        for d, g in zip(dicts, reps):
+            g.set_integrator(float(d["dt"]) * frac, fric if fric else float(d["friction"]), float(d["temperature"]))
+        b.step(200 if fric else args.warmup, stream)
+    torch.cuda.synchronize()
+    for g in reps:
+        g.get_state()
+    K = args.batch_steps
+    ms = time_steps(b, K, stream, flush)
+    for g in reps:
+        pos, _, _ = g.get_state()
+        assert np.isfinite(pos).all()
+    ms_step = sum(ms) / K
+    ns_day = sum(float(d["dt"]) for d in dicts) * 1e-3 * 86400.0 / (ms_step * 1e-3)
+    pairs = sum(g.eval(d["lam"])[0]["n_pairs"] for g, d in zip(reps, dicts))
+    # FP64, one replica after another
+    k64 = max(3, K // 8)
+    t64 = 0.0
+    for d, g in zip(dicts, reps):
+        p, v, _ = g.get_state()
+        g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=1)
+        g64.set_positions(p)
+        g64.set_velocities(v)
+        g64.step(2, stream)
+        torch.cuda.synchronize()
+        t64 += sum(time_steps(g64, k64, stream, flush)) / k64
+        g64.close()
+    ns_day64 = sum(float(d["dt"]) for d in dicts) * 1e-3 * 86400.0 / (t64 * 1e-3)
+    b.close()
+    for g in reps:
+        g.close()
+    return {"replicas": R, "atoms": int(sum(len(d["charge"]) for d in dicts)),
+            "mixed_batched": {"ms_per_step": ms_step, "ns_per_day_x_replica": ns_day,
+                              "pair_interactions_per_s": pairs / (ms_step * 1e-3), "steps": K},
+            "fp64_per_replica": {"ms_per_step_all_replicas": t64, "ns_per_day_x_replica": ns_day64,
+                                 "steps": k64},
+            "speedup_mixed_batched_vs_fp64_per_replica": ns_day / ns_day64,
+            "setup_s": t_gen}
+
+
 def time_steps(g, K, stream, flush):
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -273,6 +336,7 @@ def run_ours(args):
             fp64 = {"ns_per_day": dt_ps * 1e-3 * 86400.0 / (m64 * 1e-3), "ms_per_step": m64, "steps": k64}
             g64.close()
         cpu = None if args.no_cpu else cpu_baseline(d, dt_ps)
+        batched = batched_leg(args, stream, flush) if args.batch_replicas > 1 else None
         out = {"metric": METRIC, "value": ns_day, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32" if prec == lfe.LFE_FP32_MIXED else "f64",
@@ -286,7 +350,8 @@ def run_ours(args):
                "wall_ms_per_step": wall / args.steps * 1e3,
                "neighbour_rebuilds": rebuilds,
                "gpu_launches": launches,
-               "roofline": roof, "stages_ms": stages, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "stages_ms": stages, "fp64": fp64, "batched": batched, "cpu_baseline": cpu,
+               "e2e": e2e,
                "clocks": clocks, "lambda_end": ext1["lambda"], "theta_end": ext1["theta"]}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -190,11 +190,21 @@ int lfe_restore(lfe_system* sys, const char* path);
 int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
                     const char** names, double* ms, int max_n);
 
-/* Batched replicas: evaluate / step several systems together. */
+/* Batched replicas (lambda windows, solvents, solutes; sizes may differ):
+ * lfe_batch_create groups existing systems (not copied; they must outlive
+ * the batch and must not be destroyed while it exists).  lfe_batch_step
+ * advances every replica n_steps with one graph launch per step: the graph
+ * holds each replica's full step (evaluation, integrators, its own
+ * device-side neighbour-list rebuild) as an independent chain, so the GPU
+ * runs the replicas concurrently; results are identical to stepping each
+ * system alone.  lfe_batch_eval evaluates replica i at lambdas[i] and writes
+ * energy_terms[i][LFE_NTERMS] (host); positions and velocities are read with
+ * lfe_get_state on each system.  Errors of a batch call are described by
+ * lfe_batch_last_error. */
 int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out);
-int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms /*[n][LFE_NTERMS]*/,
-                   void* stream);
+int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms, void* stream);
 int lfe_batch_step(lfe_batch* b, int n_steps, void* stream);
+const char* lfe_batch_last_error(const lfe_batch* b);
 void lfe_batch_destroy(lfe_batch* b);
 
 /* Reciprocal-space (smooth PME) part of Eq. 4 for one configuration,

@@ -80,6 +80,15 @@ struct SystemBase {
     virtual void restore(const char* path) = 0;
     virtual int time_stages(double lam, int reps, cudaStream_t st, const char** names, double* ms, int max_n) = 0;
     virtual void param_grad(double lam, double* dU, double* d2U) = 0;
+    // batched replicas: record this system's whole step (evaluation, both
+    // integrators, step end and its own conditional rebuild node) on stream
+    // s, which is being captured into a larger graph
+    virtual void record_step(cudaStream_t s) = 0;
+    virtual void note_batch_steps(int n) = 0;
+    virtual bool overflow_pending(cudaStream_t st) = 0;
+    virtual void recover(cudaStream_t st) = 0;
+    virtual cudaStream_t side_stream() = 0;
+    unsigned generation = 0;   // bumped whenever device buffers are reallocated
 };
 
 struct lfe_system {
@@ -622,6 +631,7 @@ struct System final : SystemBase {
 
     void grow_tiles(int need)
     {
+        ++generation;
         dfree(N.tiles);
         dfree(N.jidx);
         dfree(N.masks);
@@ -677,6 +687,7 @@ struct System final : SystemBase {
         T.a_fric = std::exp(-P.lambda_friction * dt);
         T.kT = KB * temperature;
         invalidate_graph();
+        ++generation;
     }
 
     void set_velocities(const double* vel) override
@@ -754,6 +765,58 @@ struct System final : SystemBase {
             CK(cudaEventRecord(ev_join[k], br[k]));
             CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
         }
+    }
+
+    cudaStream_t side_stream() override { return cs2; }
+
+    void record_step(cudaStream_t s0) override
+    {
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        ThetaView<real> Tc = T;
+        Tc.cond = h;
+        Tc.use_cond = 1;
+        eval_kernels(s0);
+        launch_integrate(S, G, s0);
+        launch_theta(S, Tc, s0);
+        launch_step_end(S, Tc, s0);
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_build_nbl(S, N, cs2);
+        cudaGraph_t body_out = nullptr;
+        CK(cudaStreamEndCapture(cs2, &body_out));
+    }
+
+    void note_batch_steps(int n) override
+    {
+        steps_requested += (unsigned long long)n;
+    }
+
+    bool overflow_pending(cudaStream_t st) override
+    {
+        CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return (h_flags[FL_ERROR] & ERRB_OVERFLOW) != 0;
+    }
+
+    void recover(cudaStream_t st) override
+    {
+        if (!exec) capture_step_graph();
+        recover_overflow(st);
     }
 
     void capture_step_graph()
@@ -1072,6 +1135,94 @@ struct System final : SystemBase {
     }
 };
 
+// ------------------------------------------------------- batched replicas
+// Replicas (lambda windows, solvents, solutes; uneven sizes) advance together:
+// one captured CUDA graph holds every replica's step as its own chain of
+// kernels (each with its own device-side conditional rebuild), forked from
+// and joined to one stream, so one graph launch moves all replicas and the
+// GPU runs the chains concurrently.
+struct lfe_batch {
+    std::vector<lfe_system*> sys;
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> join;
+    cudaStream_t s0 = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int since_check = 0;
+    std::vector<unsigned> gens;
+    std::string err;
+
+    ~lfe_batch()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto s : lanes) if (s) cudaStreamDestroy(s);
+        for (auto e : join) if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (s0) cudaStreamDestroy(s0);
+    }
+
+    void invalidate()
+    {
+        if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+        if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+    }
+
+    void capture()
+    {
+        CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        CK(cudaEventRecord(fork, s0));
+        for (size_t i = 0; i < sys.size(); ++i) {
+            CK(cudaStreamWaitEvent(lanes[i], fork, 0));
+            sys[i]->impl->record_step(lanes[i]);
+            CK(cudaEventRecord(join[i], lanes[i]));
+            CK(cudaStreamWaitEvent(s0, join[i], 0));
+        }
+        CK(cudaStreamEndCapture(s0, &graph));
+        CK(cudaGraphInstantiate(&exec, graph, 0));
+        gens.clear();
+        for (auto* s : sys) gens.push_back(s->impl->generation);
+    }
+
+    bool stale() const
+    {
+        for (size_t i = 0; i < sys.size(); ++i)
+            if (sys[i]->impl->generation != gens[i]) return true;
+        return false;
+    }
+
+    // every 64 steps: replicas whose list overflowed are regrown and replay
+    // their skipped steps alone; the batch graph is then recaptured
+    void check(cudaStream_t st)
+    {
+        since_check = 0;
+        bool any = false;
+        for (auto* s : sys)
+            if (s->impl->overflow_pending(st)) {
+                s->impl->recover(st);
+                any = true;
+            }
+        if (any) invalidate();
+    }
+
+    void step(int n, cudaStream_t st)
+    {
+        if (exec && stale()) invalidate();
+        if (!exec) capture();
+        for (int k = 0; k < n; ++k) {
+            CK(cudaGraphLaunch(exec, st));
+            for (auto* s : sys) s->impl->note_batch_steps(1);
+            if (++since_check >= 64) {
+                check(st);
+                if (!exec) capture();
+            }
+        }
+    }
+};
+
+const char* lfe_batch_last_error_impl(const lfe_batch* b) { return b ? b->err.c_str() : ""; }
+
 // ---------------------------------------------------------------- C-ABI
 namespace {
 int guard(lfe_system* sys, const std::function<void()>& f)
@@ -1189,16 +1340,67 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream, cons
     return rc == LFE_OK ? r : rc;
 }
 
-int lfe_batch_create(lfe_system* const*, int, lfe_batch** out)
+int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out)
 {
     if (out) *out = nullptr;
-    g_create_error = "batched replicas are not available in this build";
-    return LFE_ERR_STATE;
+    if (!systems || n <= 0 || !out) {
+        g_create_error = "lfe_batch_create: need a non-empty array of systems";
+        return LFE_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j)
+            if (!systems[i] || systems[i] == systems[j]) {
+                g_create_error = "lfe_batch_create: systems must be distinct and non-NULL";
+                return LFE_ERR_ARG;
+            }
+    auto b = new lfe_batch();
+    b->sys.assign(systems, systems + n);
+    try {
+        CK(cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking));
+        b->lanes.resize(n);
+        for (int i = 0; i < n; ++i) CK(cudaStreamCreateWithFlags(&b->lanes[i], cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        b->join.resize(n);
+        for (int i = 0; i < n; ++i) CK(cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming));
+    } catch (const Failure& e) {
+        g_create_error = e.msg;
+        delete b;
+        return e.code;
+    }
+    g_create_error.clear();
+    *out = b;
+    return LFE_OK;
 }
 
-int lfe_batch_eval(lfe_batch*, const double*, double*, void*) { return LFE_ERR_STATE; }
-int lfe_batch_step(lfe_batch*, int, void*) { return LFE_ERR_STATE; }
-void lfe_batch_destroy(lfe_batch*) {}
+int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms, void* stream)
+{
+    if (!b || !lambdas) return LFE_ERR_ARG;
+    for (size_t i = 0; i < b->sys.size(); ++i) {
+        const int rc = lfe_eval(b->sys[i], lambdas[i], nullptr, energy_terms ? energy_terms + LFE_NTERMS * i : nullptr,
+                                0, stream);
+        if (rc != LFE_OK) {
+            b->err = "replica " + std::to_string(i) + ": " + b->sys[i]->err;
+            return rc;
+        }
+    }
+    return LFE_OK;
+}
+
+int lfe_batch_step(lfe_batch* b, int n_steps, void* stream)
+{
+    if (!b || n_steps < 0) return LFE_ERR_ARG;
+    try {
+        b->step(n_steps, (cudaStream_t)stream);
+    } catch (const Failure& e) {
+        b->err = e.msg;
+        return e.code;
+    }
+    return LFE_OK;
+}
+
+void lfe_batch_destroy(lfe_batch* b) { delete b; }
+
+const char* lfe_batch_last_error(const lfe_batch* b) { return lfe_batch_last_error_impl(b); }
 
 const char* lfe_last_error(const lfe_system* sys)
 {

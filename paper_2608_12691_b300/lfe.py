@@ -30,7 +30,7 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
     "lfe_time_stages", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
-    "lfe_batch_destroy", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
+    "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
 
@@ -116,6 +116,8 @@ def load():
     lib.lfe_batch_step.argtypes = [vp, ctypes.c_int, vp]
     lib.lfe_batch_destroy.argtypes = [vp]
     lib.lfe_batch_destroy.restype = None
+    lib.lfe_batch_last_error.argtypes = [vp]
+    lib.lfe_batch_last_error.restype = ctypes.c_char_p
     lib.lfe_last_error.argtypes = [vp]
     lib.lfe_last_error.restype = ctypes.c_char_p
     lib.lfe_destroy.argtypes = [vp]
@@ -317,3 +319,42 @@ class System:
         if r < 0:
             self._check(r)
         return {names[k].decode(): float(ms[k]) for k in range(r)}
+
+
+class Batch:
+    """Replicas advanced together by one graph launch per step (lfe_batch_*)."""
+
+    def __init__(self, systems):
+        lib = load()
+        self._lib = lib
+        self.systems = list(systems)
+        arr = (ctypes.c_void_p * len(self.systems))(*[s.h.value for s in self.systems])
+        h = ctypes.c_void_p()
+        rc = lib.lfe_batch_create(arr, len(self.systems), ctypes.byref(h))
+        if rc != LFE_OK:
+            raise LfeError(rc, lib.lfe_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != LFE_OK:
+            raise LfeError(rc, self._lib.lfe_batch_last_error(self.h).decode())
+
+    def step(self, n, stream=None):
+        self._check(self._lib.lfe_batch_step(self.h, int(n), _stream_ptr(stream)))
+
+    def eval(self, lambdas):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        terms = np.zeros((len(self.systems), NTERMS))
+        self._check(self._lib.lfe_batch_eval(self.h, lam.ctypes.data, terms.ctypes.data, None))
+        return [dict(zip(TERM_NAMES, t)) for t in terms]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lfe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
