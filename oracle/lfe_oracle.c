@@ -54,6 +54,13 @@
  *   Fuv   = -grad U_uv
  *   Fsoft = -grad U_soft
  * so that F(lambda) = F0 + h_A Fuv + h_B Fsoft.
+ *
+ * orc_param_grad gives the class-resolved derivatives of the same energies
+ * with respect to every atom's charge, sigma and epsilon (the gradients that
+ * force-field fitting to solvation free energies needs); the reciprocal part
+ * is the potential of each class at the atom's site.  Reading: where
+ * eps_i = 0 the derivative of eps_ij = sqrt(eps_i eps_j) is singular and is
+ * reported as 0.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -325,7 +332,7 @@ static void self_background(const orc_params* p, int n, const double* q,
 /* ------------------------------------------- level 1: direct Ewald k-sum */
 
 static void ewald_ksum(const orc_params* p, int n, const double* pos, const double* q,
-                       const unsigned char* solute, double* E, double* F0, double* Fuv)
+                       const unsigned char* solute, double* E, double* F0, double* Fuv, double* phi2)
 {
     const double a = p->alpha;
     const double V = p->box[0] * p->box[1] * p->box[2];
@@ -391,6 +398,7 @@ static void ewald_ksum(const orc_params* p, int n, const double* pos, const doub
 #pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
         double f0[3] = {0, 0, 0}, fuv[3] = {0, 0, 0};
+        double pv = 0.0, pu = 0.0;
         int own = solute[i] ? 2 : 0, oth = solute[i] ? 0 : 2;
         for (int t = 0; t < nk; ++t) {
             int mx = ml[3 * t], my = ml[3 * t + 1], mz = ml[3 * t + 2];
@@ -407,6 +415,13 @@ static void ewald_ksum(const orc_params* p, int n, const double* pos, const doub
                 f0[d] += gk[t] * kv[3 * t + d] * im_own;
                 fuv[d] += gk[t] * kv[3 * t + d] * im_oth;
             }
+            /* potential of class c at r_i: (4 pi k_e / V) sum_full g Re(S_c* e^{i k r_i}) */
+            pv += gk[t] * (S[4 * t] * c + S[4 * t + 1] * sn);
+            pu += gk[t] * (S[4 * t + 2] * c + S[4 * t + 3] * sn);
+        }
+        if (phi2) {
+            phi2[2 * i] = fpre * pv;
+            phi2[2 * i + 1] = fpre * pu;
         }
         for (int d = 0; d < 3; ++d) {
             if (F0) F0[3 * i + d] += fpre * q[i] * f0[d];
@@ -486,7 +501,7 @@ static void dft_axis(double* re, double* im, const int K[3], int ax, int sign)
 }
 
 static void spme(const orc_params* p, int n, const double* pos, const double* q,
-                 const unsigned char* solute, double* E, double* F0, double* Fuv)
+                 const unsigned char* solute, double* E, double* F0, double* Fuv, double* phi2)
 {
     const int K[3] = {p->grid[0], p->grid[1], p->grid[2]};
     const int no = p->order;
@@ -568,6 +583,7 @@ static void spme(const orc_params* p, int n, const double* pos, const double* q,
         int f[3];
         for (int d = 0; d < 3; ++d) f[d] = (int)floor(u[3 * i + d]);
         double g0[3] = {0, 0, 0}, g1[3] = {0, 0, 0};
+        double pot[2] = {0.0, 0.0};
         for (int j0 = 0; j0 < no; ++j0)
             for (int j1 = 0; j1 < no; ++j1)
                 for (int j2 = 0; j2 < no; ++j2) {
@@ -584,7 +600,13 @@ static void spme(const orc_params* p, int n, const double* pos, const double* q,
                         g0[d] += grad[d] * Qr[own][idx];
                         g1[d] += grad[d] * Qr[oth][idx];
                     }
+                    pot[0] += w[0] * w[1] * w[2] * Qr[0][idx];
+                    pot[1] += w[0] * w[1] * w[2] * Qr[1][idx];
                 }
+        if (phi2) {
+            phi2[2 * i] = pot[0];
+            phi2[2 * i + 1] = pot[1];
+        }
         for (int d = 0; d < 3; ++d) {
             if (F0) F0[3 * i + d] -= q[i] * g0[d];
             if (Fuv) Fuv[3 * i + d] -= q[i] * g1[d];
@@ -634,8 +656,8 @@ int orc_nonbonded(const orc_params* p, int n, const double* pos, const double* q
     pair14_terms(p, pos, q, sig, eps, solute, n14, p14, s14, E, F0, Fuv);
     if (p->level != 0) {
         self_background(p, n, q, solute, E);
-        if (p->level == 1) ewald_ksum(p, n, pos, q, solute, E, F0, Fuv);
-        else spme(p, n, pos, q, solute, E, F0, Fuv);
+        if (p->level == 1) ewald_ksum(p, n, pos, q, solute, E, F0, Fuv, NULL);
+        else spme(p, n, pos, q, solute, E, F0, Fuv, NULL);
     }
     E[0] = E[4] + E[7] + E[10] + E[12] + E[15] + E[18] + E[21];
     E[1] = E[5] + E[8] + E[11] + E[13] + E[16] + E[19] + E[22];
@@ -753,4 +775,125 @@ int orc_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+
+/* ------------------------------------------------- parameter gradients
+ *
+ * Derivatives of the class energies with respect to each atom's charge,
+ * sigma and epsilon (the differentiation configuration: gradients of U and
+ * dU/dlambda with respect to solute parameters).  Output G[9 n]:
+ *   G[9 i + 3 p + c],  p = 0 charge, 1 sigma, 2 epsilon,
+ *                      c = 0 the atom's own class (U_vv for a solvent atom,
+ *                            U_uu for a solute atom), 1 U_uv, 2 U_soft.
+ * Then dU/dp_i = G_own + h_A G_uv + h_B G_soft and
+ * d2U/dlambda dp_i = h_A' G_uv + h_B' G_soft (Eq. 4 is linear in the bases).
+ * Coulomb: d/dq_i of k_e q_i q_j f(r) is k_e q_j f(r) for every pair term
+ * (erfc real space, -erf exclusion correction, scaled 1-4), -2 k_e alpha/sqrt(pi) q_i
+ * for the self term, the derivative of the background, and the reciprocal
+ * potential of each class at r_i (level 1: k-sum; level 2: SPME grid
+ * interpolation).  LJ: sigma_ij = (sigma_i + sigma_j)/2 and eps_ij = sqrt(eps_i
+ * eps_j), so d sigma_ij / d sigma_i = 1/2 and dE/d eps_i = E / (2 eps_i)
+ * (eps_i > 0; 0 otherwise).  Returns 0 on success. */
+int orc_param_grad(const orc_params* p, int n, const double* pos, const double* q,
+                   const double* sig, const double* eps, const unsigned char* solute,
+                   int n_excl, const int* excl, int n14, const int* p14, const double* s14,
+                   double* G)
+{
+    if (n <= 0 || !G) return -1;
+    memset(G, 0, sizeof(double) * 9 * (size_t)n);
+    const double rc = p->r_cut, rs = p->r_switch, a = p->alpha, rc2 = rc * rc;
+    const double V = p->box[0] * p->box[1] * p->box[2];
+    int *st, *li;
+    build_exclusion_csr(n, n_excl, excl, &st, &li);
+    /* real-space pairs: loop over i, derivatives with respect to atom i's parameters */
+#pragma omp parallel
+    {
+        char* mark = (char*)calloc((size_t)n, 1);
+#pragma omp for schedule(dynamic, 16)
+        for (int i = 0; i < n; ++i) {
+            for (int e = st[i]; e < st[i + 1]; ++e) mark[li[e]] = 1;
+            double* g = G + 9 * (size_t)i;
+            for (int j = 0; j < n; ++j) {
+                if (j == i || mark[j]) continue;
+                double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1],
+                               pos[3 * j + 2] - pos[3 * i + 2]};
+                min_image(d, p->box);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 >= rc2) continue;
+                double r = sqrt(r2);
+                int c = pair_class(solute[i], solute[j]) == 2 ? 1 : 0;
+                g[0 + c] += ORC_KE * q[j] * erfc(a * r) / r;
+                double sg = 0.5 * (sig[i] + sig[j]), ep = sqrt(eps[i] * eps[j]);
+                if (ep > 0.0) {
+                    double dS, S = orc_switch(r, rc, rs, &dS);
+                    double s6 = pow(sg / r, 6);
+                    double elj = 4.0 * ep * (s6 * s6 - s6) * S;
+                    g[3 + c] += 12.0 * ep / sg * (2.0 * s6 * s6 - s6) * S;
+                    if (eps[i] > 0.0) g[6 + c] += elj / (2.0 * eps[i]);
+                    if (c == 1 && sg > 0.0) {
+                        double du, u = orc_ucap(r / sg, &du);
+                        double es = ep * u * S;
+                        g[3 + 2] += -ep * du * (r / sg) / (2.0 * sg) * S;
+                        if (eps[i] > 0.0) g[6 + 2] += es / (2.0 * eps[i]);
+                    }
+                }
+            }
+            for (int e = st[i]; e < st[i + 1]; ++e) mark[li[e]] = 0;
+        }
+        free(mark);
+    }
+    free(st); free(li);
+    /* exclusion corrections and 1-4 terms: both atoms of the pair */
+    for (int e = 0; e < n_excl; ++e) {
+        int i = excl[2 * e], j = excl[2 * e + 1];
+        double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
+        min_image(d, p->box);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        double f = r < 1e-12 ? 2.0 * a / sqrt(ORC_PI) : erf(a * r) / r;
+        int c = pair_class(solute[i], solute[j]) == 2 ? 1 : 0;
+        G[9 * (size_t)i + c] += -ORC_KE * q[j] * f;
+        G[9 * (size_t)j + c] += -ORC_KE * q[i] * f;
+    }
+    for (int e = 0; e < n14; ++e) {
+        int i = p14[2 * e], j = p14[2 * e + 1];
+        double sLJ = s14[2 * e], sC = s14[2 * e + 1];
+        double d[3] = {pos[3 * j] - pos[3 * i], pos[3 * j + 1] - pos[3 * i + 1], pos[3 * j + 2] - pos[3 * i + 2]};
+        min_image(d, p->box);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        int c = pair_class(solute[i], solute[j]) == 2 ? 1 : 0;
+        G[9 * (size_t)i + c] += sC * ORC_KE * q[j] / r;
+        G[9 * (size_t)j + c] += sC * ORC_KE * q[i] / r;
+        double sg = 0.5 * (sig[i] + sig[j]), ep = sqrt(eps[i] * eps[j]);
+        if (ep > 0.0) {
+            double s6 = pow(sg / r, 6);
+            double elj = 4.0 * ep * (s6 * s6 - s6);
+            double ds = sLJ * 12.0 * ep / sg * (2.0 * s6 * s6 - s6);
+            G[9 * (size_t)i + 3 + c] += ds;
+            G[9 * (size_t)j + 3 + c] += ds;
+            if (eps[i] > 0.0) G[9 * (size_t)i + 6 + c] += sLJ * elj / (2.0 * eps[i]);
+            if (eps[j] > 0.0) G[9 * (size_t)j + 6 + c] += sLJ * elj / (2.0 * eps[j]);
+        }
+    }
+    if (p->level != 0) {
+        /* self and background */
+        double Q[2] = {0, 0};
+        for (int i = 0; i < n; ++i) Q[solute[i] ? 1 : 0] += q[i];
+        double pre = -ORC_KE * ORC_PI / (2.0 * V * a * a);
+        double* phi2 = (double*)malloc(sizeof(double) * 2 * (size_t)n);
+        double E[ORC_NE];
+        memset(E, 0, sizeof(E));
+        if (p->level == 1) ewald_ksum(p, n, pos, q, solute, E, NULL, NULL, phi2);
+        else spme(p, n, pos, q, solute, E, NULL, NULL, phi2);
+        for (int i = 0; i < n; ++i) {
+            int u = solute[i] ? 1 : 0;
+            double* g = G + 9 * (size_t)i;
+            g[0] += -2.0 * ORC_KE * a / sqrt(ORC_PI) * q[i] + 2.0 * pre * Q[u];
+            g[1] += 2.0 * pre * Q[1 - u];
+            g[0] += phi2[2 * i + u];        /* own class potential */
+            g[1] += phi2[2 * i + 1 - u];    /* other class potential: the uv cross term */
+        }
+        free(phi2);
+    }
+    return 0;
 }
