@@ -103,8 +103,9 @@ typedef struct {
  *                         the Ewald exclusion correction -k_e q_i q_j erf(a r)/r.
  *   pairs14   [2 n_14]    subset of excl that also gets scaled 1-4 terms
  *   scale14   [2 n_14]    (s_LJ, s_Coulomb) per 1-4 pair
- *   water_OHH [3 n_waters] rigid waters (O, H, H) held by SETTLE at
- *                         water_rOH / water_rHH
+ *   water_OHH [3 n_waters] rigid waters (O, H, H) held at water_rOH /
+ *                         water_rHH by an exact Newton solve of the three
+ *                         distance constraints (the result SETTLE gives)
  *   constraints [2 n_cons], constraint_len [n_cons]: X-H distance constraints;
  *                         every constraint must share its first atom with the
  *                         other constraints of its group (star groups of <= 4)
@@ -159,12 +160,36 @@ int lfe_build_neighbors(lfe_system* sys, void* stream);
 int lfe_eval(lfe_system* sys, double lambda, double* forces, double* energy_terms,
              int out_on_device, void* stream);
 
-/* Per-solute-atom parameter gradients at lambda (host outputs, each [3 n_u],
- * solute atoms in caller order, entries (dq, dsigma, deps) per atom):
- *   dU_dp      = dU/dq_i, dU/dsigma_i, dU/deps_i
- *   d2U_dl_dp  = d/dp (dU/dlambda) = h_A' dU_uv/dp + h_B' dU_soft/dp.
- * Either may be NULL. */
-int lfe_param_grad(lfe_system* sys, double lambda, double* dU_dp, double* d2U_dl_dp);
+/* Gradients of U(lambda) and dU/dlambda (Eq. 4, with the capped soft basis of
+ * Eq. 5-6 and the switching functions of Eq. 7-10) with respect to each solute
+ * atom's charge q_i, LJ sigma_i and LJ epsilon_i, at the current positions.
+ * Solute atoms are in caller order (ascending atom index); per atom the
+ * entries are (q, sigma, epsilon):
+ *   dU_dp      [3 n_u]  dU/dp_i = dU_uu/dp_i + h_A dU_uv/dp_i + h_B dU_soft/dp_i
+ *   d2U_dl_dp  [3 n_u]  d2U/(dlambda dp_i) = h_A' dU_uv/dp_i + h_B' dU_soft/dp_i
+ *   basis      [9 n_u]  the class derivatives: basis[9 i + 3 p + c] with c = 0
+ *                       dU_uu/dp, 1 dU_uv/dp, 2 dU_soft/dp
+ * Any output may be NULL.  Lorentz-Berthelot mixing: d sigma_ij / d sigma_i =
+ * 1/2 and d eps_ij / d eps_i = eps_ij / (2 eps_i); where eps_i = 0 the epsilon
+ * derivative is singular and is reported as 0.  The reciprocal part uses the
+ * smooth-PME grid of the system; bonded terms do not depend on these
+ * parameters.  Everything is computed in FP64 on the device, in either
+ * precision mode.  out_on_device != 0: outputs are device pointers, written
+ * in stream order; otherwise host pointers, and the call returns after
+ * synchronising.  lambda outside [0, 1] or a system without solute atoms:
+ * LFE_ERR_ARG.  The dynamics' lambda state is left unchanged. */
+int lfe_param_grad(lfe_system* sys, double lambda, double* dU_dp, double* d2U_dl_dp, double* basis,
+                   int out_on_device, void* stream);
+
+/* Replace the solute atoms' charges, LJ sigma and LJ epsilon (each [n_u] in
+ * solute caller order; NULL leaves that parameter unchanged; on_device != 0
+ * means device pointers).  Values are checked (finite; sigma, epsilon >= 0:
+ * LFE_ERR_ARG otherwise, nothing changed).  The self and neutralising-
+ * background energies follow the new charges and captured step graphs are
+ * rebuilt on the next lfe_step.  Returns after synchronising.  The packed-
+ * transform scale of the solute PME grid keeps the value chosen at creation. */
+int lfe_set_solute_params(lfe_system* sys, const double* charge, const double* sigma, const double* epsilon,
+                          int on_device, void* stream);
 
 /* Advance n_steps of atoms + theta (replays one captured CUDA graph per step
  * on `stream`, rebuilding the neighbour list on the device when an atom has

@@ -11,6 +11,7 @@
 #include <vector>
 #include <algorithm>
 #include <functional>
+#include <type_traits>
 
 #include "lfe.h"
 #include "lfe_views.cuh"
@@ -79,7 +80,9 @@ struct SystemBase {
     virtual void checkpoint(const char* path) = 0;
     virtual void restore(const char* path) = 0;
     virtual int time_stages(double lam, int reps, cudaStream_t st, const char** names, double* ms, int max_n) = 0;
-    virtual void param_grad(double lam, double* dU, double* d2U) = 0;
+    virtual void param_grad(double lam, double* dU, double* d2U, double* basis, int on_device, cudaStream_t st) = 0;
+    virtual void set_solute_params(const double* q, const double* sig, const double* eps, int on_device,
+                                   cudaStream_t st) = 0;
     // batched replicas: record this system's whole step (evaluation, both
     // integrators, step end and its own conditional rebuild node) on stream
     // s, which is being captured into a larger graph
@@ -123,6 +126,14 @@ struct System final : SystemBase {
     double* d_fbuf = nullptr;      // [3n] staging for host force output
     double* d_pos = nullptr;       // [3n] staging for host positions
     LamState* lam_save = nullptr;
+    LamState* lam0 = nullptr;      // all-zero lambda state (h_A = 0: unmixed class potentials)
+    real* d_q = nullptr;           // writable views of S.q, S.sig, S.eps
+    real* d_sig = nullptr;
+    real* d_eps = nullptr;
+    double* d_pg = nullptr;        // [15 n_u] parameter-gradient outputs (dU, d2U, basis)
+    double* d_pstage = nullptr;    // [3 n_u] staged solute parameters
+    std::vector<double> h_q, h_sig, h_eps;   // parameters as given (caller order)
+    std::vector<int> h_solute;               // solute atoms, caller order
     std::vector<double> h_mass;
     int device = 0;
 
@@ -265,9 +276,18 @@ struct System final : SystemBase {
         S.v = upload(hv);
         S.xref = dalloc<R4<real>>(n);
         S.invm = upload(hw);
-        S.q = upload(hq);
-        S.sig = upload(hs);
-        S.eps = upload(he);
+        d_q = upload(hq);
+        d_sig = upload(hs);
+        d_eps = upload(he);
+        S.q = d_q;
+        S.sig = d_sig;
+        S.eps = d_eps;
+        h_q.assign(t.charge, t.charge + n);
+        h_sig.assign(t.sigma, t.sigma + n);
+        h_eps.assign(t.epsilon, t.epsilon + n);
+        h_solute = sl;
+        d_pg = dalloc<double>(15 * (size_t)std::max(1, n_u));
+        d_pstage = dalloc<double>(3 * (size_t)std::max(1, n_u));
         S.sol = upload(hsol);
         S.solute_list = upload(sl);
         S.solv_list = upload(vl);
@@ -344,16 +364,19 @@ struct System final : SystemBase {
         {
             std::vector<int2> ex(t.n_excl), e14(t.n_14);
             std::vector<R2<real>> s14(t.n_14);
+            std::vector<R2<double>> s14d(t.n_14);
             for (int e = 0; e < t.n_excl; ++e) ex[e] = make_int2(t.excl[2 * e], t.excl[2 * e + 1]);
             for (int e = 0; e < t.n_14; ++e) {
                 e14[e] = make_int2(t.pairs14[2 * e], t.pairs14[2 * e + 1]);
                 s14[e] = R2<real>{(real)t.scale14[2 * e], (real)t.scale14[2 * e + 1]};
+                s14d[e] = R2<double>{t.scale14[2 * e], t.scale14[2 * e + 1]};
             }
             X.n_excl = t.n_excl;
             X.n14 = t.n_14;
             X.excl = upload(ex);
             X.p14 = upload(e14);
             X.s14 = upload(s14);
+            X.s14d = upload(s14d);
         }
 
         // ----------------------------------------------------------- PME
@@ -431,20 +454,7 @@ struct System final : SystemBase {
         }
 
         // ----------------------------------------------- constant energies
-        {
-            double s2[2] = {0, 0}, Q[2] = {0, 0};
-            for (int i = 0; i < n; ++i) {
-                const int c = t.solute[i] ? 1 : 0;
-                s2[c] += t.charge[i] * t.charge[i];
-                Q[c] += t.charge[i];
-            }
-            const double a = p.ewald_alpha;
-            const double self_v = -KE * a / std::sqrt(PI) * s2[0], self_u = -KE * a / std::sqrt(PI) * s2[1];
-            const double pre = -KE * PI / (2.0 * V * a * a);
-            const_vv = self_v + pre * Q[0] * Q[0];
-            const_uu = self_u + pre * Q[1] * Q[1];
-            const_uv = pre * 2.0 * Q[0] * Q[1];
-        }
+        constant_energies();
 
         // --------------------------------------------------------- bonded
         {
@@ -585,6 +595,7 @@ struct System final : SystemBase {
             CK(cudaMemcpy(S.lam, &L, sizeof(L), cudaMemcpyHostToDevice));
             launch_set_lambda(S, L.lambda, nullptr);
             lam_save = dalloc<LamState>(1);
+            lam0 = dalloc<LamState>(1);
         }
         int nsm = 148;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
@@ -607,6 +618,29 @@ struct System final : SystemBase {
         {
             // mass-weighted zero velocities; theta at rest
         }
+    }
+
+    // self and neutralising-background energies of each class (they depend
+    // on the charges only)
+    void constant_energies()
+    {
+        std::vector<unsigned char> is_u(n, 0);
+        for (int a : h_solute) is_u[a] = 1;
+        double s2[2] = {0, 0}, Q[2] = {0, 0};
+        for (int i = 0; i < n; ++i) {
+            const int c = is_u[i];
+            s2[c] += h_q[i] * h_q[i];
+            Q[c] += h_q[i];
+        }
+        const double a = P.ewald_alpha, V = P.box[0] * P.box[1] * P.box[2];
+        const double self_v = -KE * a / std::sqrt(PI) * s2[0], self_u = -KE * a / std::sqrt(PI) * s2[1];
+        const double pre = -KE * PI / (2.0 * V * a * a);
+        const_vv = self_v + pre * Q[0] * Q[0];
+        const_uu = self_u + pre * Q[1] * Q[1];
+        const_uv = pre * 2.0 * Q[0] * Q[1];
+        T.const_vv = const_vv;
+        T.const_uu = const_uu;
+        T.const_uv = const_uv;
     }
 
     void check_flags(cudaStream_t st)
@@ -1129,9 +1163,97 @@ struct System final : SystemBase {
         return m;
     }
 
-    void param_grad(double, double*, double*) override
+    // Parameter gradients of the solute atoms at lambda.  The class
+    // potentials come from one more FP64 reciprocal pass with h_A = 0 (the
+    // FP64 copy of the charge grid for FP32 systems, the FP64 grid itself
+    // for FP64 systems); the kernel recomputes every real-space interaction
+    // of each solute atom.
+    void param_grad(double lam, double* dU, double* d2U, double* basis, int on_device, cudaStream_t st) override
     {
-        fail(LFE_ERR_STATE, "parameter gradients are not available in this build");
+        if (!(lam >= 0.0 && lam <= 1.0)) fail(LFE_ERR_ARG, "lambda must be in [0, 1]");
+        if (n_u == 0) fail(LFE_ERR_ARG, "the system has no solute atoms");
+        if (exec) recover_overflow(st);
+        CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
+        launch_set_lambda(S, lam, st);
+        const PmeView<double>* P64;
+        if constexpr (std::is_same<real, double>::value) P64 = &M;
+        else P64 = &M64;
+        launch_spread(S, M, st);
+        launch_fft(M, 2, +1, 1, st);
+        if (dual) launch_fft(M64, 2, +1, 0, st);
+        launch_fft(*P64, 1, +1, 0, st);
+        launch_fft(*P64, 0, +1, 0, st);
+        launch_conv(*P64, S.E, lam0, CONV_POTENTIAL, st);
+        launch_fft(*P64, 0, -1, 0, st);
+        launch_fft(*P64, 1, -1, 0, st);
+        launch_fft(*P64, 2, -1, 0, st);
+        AdjConst c{};
+        for (int d = 0; d < 3; ++d) {
+            c.L[d] = P.box[d];
+            c.invL[d] = 1.0 / P.box[d];
+        }
+        c.alpha = P.ewald_alpha;
+        c.two_a_sqrtpi = 2.0 * P.ewald_alpha / std::sqrt(PI);
+        c.rc2 = P.r_cut * P.r_cut;
+        c.rsw = P.r_switch >= 0 ? P.r_switch : P.r_cut;
+        c.swi = P.r_switch >= 0 ? 1.0 / (P.r_cut - P.r_switch) : 0.0;
+        c.bg_pre = -KE * PI / (2.0 * P.box[0] * P.box[1] * P.box[2] * P.ewald_alpha * P.ewald_alpha);
+        double* g_dU = d_pg;
+        double* g_d2 = d_pg + 3 * (size_t)n_u;
+        double* g_b = d_pg + 6 * (size_t)n_u;
+        launch_param_grad(S, N, X, M, P64->Z, c, g_dU, g_d2, g_b, st);
+        CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
+        CK(cudaGetLastError());
+        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (dU) CK(cudaMemcpyAsync(dU, g_dU, sizeof(double) * 3 * n_u, kind, st));
+        if (d2U) CK(cudaMemcpyAsync(d2U, g_d2, sizeof(double) * 3 * n_u, kind, st));
+        if (basis) CK(cudaMemcpyAsync(basis, g_b, sizeof(double) * 9 * n_u, kind, st));
+        if (!on_device) CK(cudaStreamSynchronize(st));
+    }
+
+    // Replace the solute atoms' charges, sigma and epsilon (each [n_u] in
+    // solute caller order, NULL = unchanged).  The constant self and
+    // background energies follow the new charges; captured step graphs are
+    // rebuilt because those constants are kernel arguments.
+    void set_solute_params(const double* q, const double* sig, const double* eps, int on_device,
+                           cudaStream_t st) override
+    {
+        if (n_u == 0) fail(LFE_ERR_ARG, "the system has no solute atoms");
+        const double* src[3] = {q, sig, eps};
+        std::vector<double> v[3];
+        for (int k = 0; k < 3; ++k) {
+            v[k].resize(n_u);
+            std::vector<double>& cur = k == 0 ? h_q : (k == 1 ? h_sig : h_eps);
+            if (!src[k]) {
+                for (int b = 0; b < n_u; ++b) v[k][b] = cur[h_solute[b]];
+            } else if (on_device) {
+                CK(cudaMemcpyAsync(v[k].data(), src[k], sizeof(double) * n_u, cudaMemcpyDeviceToHost, st));
+            } else {
+                std::copy(src[k], src[k] + n_u, v[k].begin());
+            }
+        }
+        if (on_device) CK(cudaStreamSynchronize(st));
+        for (int k = 0; k < 3; ++k)
+            for (int b = 0; b < n_u; ++b) {
+                if (!std::isfinite(v[k][b])) fail(LFE_ERR_ARG, "non-finite solute parameter");
+                if (k > 0 && v[k][b] < 0) fail(LFE_ERR_ARG, "sigma and epsilon must be >= 0");
+            }
+        CK(cudaDeviceSynchronize());
+        if (exec) recover_overflow(nullptr);
+        for (int b = 0; b < n_u; ++b) {
+            h_q[h_solute[b]] = v[0][b];
+            h_sig[h_solute[b]] = v[1][b];
+            h_eps[h_solute[b]] = v[2][b];
+        }
+        for (int k = 0; k < 3; ++k)
+            CK(cudaMemcpyAsync(d_pstage + (size_t)k * n_u, v[k].data(), sizeof(double) * n_u,
+                               cudaMemcpyHostToDevice, st));
+        launch_set_solute_params(S, d_q, d_sig, d_eps, d_pstage, st);
+        CK(cudaStreamSynchronize(st));
+        CK(cudaGetLastError());
+        constant_energies();
+        invalidate_graph();
+        ++generation;
     }
 };
 
@@ -1301,9 +1423,20 @@ int lfe_eval(lfe_system* sys, double lambda, double* forces, double* energy_term
     return guard(sys, [&] { sys->impl->eval(lambda, forces, energy_terms, out_on_device, (cudaStream_t)stream); });
 }
 
-int lfe_param_grad(lfe_system* sys, double lambda, double* dU_dp, double* d2U_dl_dp)
+int lfe_param_grad(lfe_system* sys, double lambda, double* dU_dp, double* d2U_dl_dp, double* basis,
+                   int out_on_device, void* stream)
 {
-    return guard(sys, [&] { sys->impl->param_grad(lambda, dU_dp, d2U_dl_dp); });
+    return guard(sys, [&] {
+        sys->impl->param_grad(lambda, dU_dp, d2U_dl_dp, basis, out_on_device, (cudaStream_t)stream);
+    });
+}
+
+int lfe_set_solute_params(lfe_system* sys, const double* charge, const double* sigma, const double* epsilon,
+                          int on_device, void* stream)
+{
+    return guard(sys, [&] {
+        sys->impl->set_solute_params(charge, sigma, epsilon, on_device, (cudaStream_t)stream);
+    });
 }
 
 int lfe_step(lfe_system* sys, int n_steps, void* stream)

@@ -86,6 +86,7 @@ struct ExclView {
     const int2* excl;       // caller-order pairs
     const int2* p14;
     const R2<real>* s14;    // (s_LJ, s_C)
+    const R2<double>* s14d; // the same scales in FP64 (parameter gradients)
 };
 
 template <typename real>
@@ -154,6 +155,15 @@ struct ThetaView {
     int use_cond;
 };
 
+// FP64 geometry and Ewald constants of the parameter-gradient kernel
+struct AdjConst {
+    double L[3], invL[3];
+    double alpha, two_a_sqrtpi;   // Ewald alpha and 2 alpha / sqrt(pi)
+    double rc2;                   // r_cut^2
+    double rsw, swi;              // LJ switch start and 1 / (r_cut - r_sw) (0: no switch)
+    double bg_pre;                // -k_e pi / (2 V alpha^2)
+};
+
 // ------------------------------------------------------------- launchers
 template <typename real> void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st);
 template <typename real> void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st);
@@ -178,6 +188,13 @@ template <typename real> void launch_eval_out(const SysView<real>& s, double* fo
                                               cudaStream_t st);
 template <typename real> void launch_assign_positions(const SysView<real>& s, const double* pos, cudaStream_t st);
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
+// phi: FP64 grid of the class potentials (phi_v real, phi_u imaginary)
+template <typename real> void launch_param_grad(const SysView<real>& s, const NblView<real>& nb,
+                                                const ExclView<real>& ex, const PmeView<real>& pm,
+                                                const R2<double>* phi, const AdjConst& c, double* dU,
+                                                double* d2U, double* basis, cudaStream_t st);
+template <typename real> void launch_set_solute_params(const SysView<real>& s, real* q, real* sig, real* eps,
+                                                       const double* stage, cudaStream_t st);
 
 // message returned by lfe_last_error(NULL)
 void record_global_error(const std::string& m);

@@ -28,7 +28,7 @@ TERM_NAMES = ["U", "dUdl", "U_vv", "U_uu", "U_uv", "U_soft", "U_bonded", "n_pair
 EXPORTED = [
     "lfe_create", "lfe_set_positions", "lfe_set_velocities", "lfe_set_integrator",
     "lfe_build_neighbors", "lfe_eval",
-    "lfe_param_grad", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
+    "lfe_param_grad", "lfe_set_solute_params", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
     "lfe_time_stages", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
     "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
@@ -104,7 +104,8 @@ def load():
     lib.lfe_set_integrator.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.lfe_build_neighbors.argtypes = [vp, vp]
     lib.lfe_eval.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int, vp]
-    lib.lfe_param_grad.argtypes = [vp, ctypes.c_double, vp, vp]
+    lib.lfe_param_grad.argtypes = [vp, ctypes.c_double, vp, vp, vp, ctypes.c_int, vp]
+    lib.lfe_set_solute_params.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
     lib.lfe_step.argtypes = [vp, ctypes.c_int, vp]
     lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
@@ -194,6 +195,7 @@ class System:
         for k, v in over.items():
             setattr(pr, k, v)
         self.params = pr
+        self._n_u = int(np.count_nonzero(np.asarray(d["solute"])))
         keep = {}
 
         def K(name, dtype, width=None):
@@ -305,11 +307,40 @@ class System:
     def restore(self, path):
         self._check(self._lib.lfe_restore(self.h, str(path).encode()))
 
-    def param_grad(self, lam, n_u):
+    @property
+    def n_solute(self):
+        return self._n_u
+
+    def param_grad(self, lam):
+        """Host outputs (dU/dp [n_u, 3], d2U/dlambda dp [n_u, 3], class
+        derivatives [n_u, 3 (q, sigma, eps), 3 (uu, uv, soft)]), float64."""
+        n_u = self._n_u
         dU = np.zeros((n_u, 3))
         d2 = np.zeros((n_u, 3))
-        self._check(self._lib.lfe_param_grad(self.h, float(lam), dU.ctypes.data, d2.ctypes.data))
-        return dU, d2
+        basis = np.zeros((n_u, 3, 3))
+        self._check(self._lib.lfe_param_grad(self.h, float(lam), dU.ctypes.data, d2.ctypes.data,
+                                             basis.ctypes.data, 0, None))
+        return dU, d2, basis
+
+    def param_grad_device(self, lam, dU_ptr, d2_ptr, basis_ptr=None, stream=None):
+        """Device outputs: float64 device buffers [3 n_u], [3 n_u], [9 n_u] (any may be None)."""
+        self._check(self._lib.lfe_param_grad(self.h, float(lam), dU_ptr, d2_ptr, basis_ptr, 1,
+                                             _stream_ptr(stream)))
+
+    def set_solute_params(self, charge=None, sigma=None, epsilon=None):
+        """New solute charges / sigma / epsilon ([n_u] float64 host arrays; None = unchanged)."""
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+                for a in (charge, sigma, epsilon)]
+        for a in keep:
+            if a is not None and a.shape[0] != self._n_u:
+                raise ValueError(f"expected {self._n_u} solute values, got {a.shape[0]}")
+        ptrs = [None if a is None else a.ctypes.data for a in keep]
+        self._check(self._lib.lfe_set_solute_params(self.h, *ptrs, 0, None))
+
+    def set_solute_params_device(self, charge_ptr=None, sigma_ptr=None, epsilon_ptr=None, stream=None):
+        """Same, from float64 device buffers of n_u entries (None = unchanged)."""
+        self._check(self._lib.lfe_set_solute_params(self.h, charge_ptr, sigma_ptr, epsilon_ptr, 1,
+                                                    _stream_ptr(stream)))
 
     def time_stages(self, lam, reps=10, stream=None, max_n=32):
         names = (ctypes.c_char_p * max_n)()
