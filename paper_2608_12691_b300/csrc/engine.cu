@@ -319,8 +319,9 @@ struct System final : SystemBase {
         N.n_cl_solv = dalloc<int>(1);
         N.bbc = dalloc<R4<float>>(n_cl);
         N.bbh = dalloc<R4<float>>(n_cl);
-        N.tile_cnt = dalloc<int>(n_cl);
-        N.tile_off = dalloc<int>(n_cl + 1);
+        N.tile_cnt = dalloc<int>(27 * (size_t)n_cl);
+        N.tile_tot = dalloc<int>(n_cl);
+        N.tile_off = dalloc<int>((size_t)n_cl + 1);
         N.cap = 1024;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
@@ -377,6 +378,23 @@ struct System final : SystemBase {
             X.p14 = upload(e14);
             X.s14 = upload(s14);
             X.s14d = upload(s14d);
+            X.ex_start = N.ex_start;
+            X.ex_list = N.ex_list;
+            std::vector<int> cnt(n + 1, 0), lst(2 * (size_t)t.n_14), fillv(n, 0);
+            std::vector<R2<real>> ls(2 * (size_t)t.n_14);
+            for (int e = 0; e < t.n_14; ++e) { cnt[t.pairs14[2 * e] + 1]++; cnt[t.pairs14[2 * e + 1] + 1]++; }
+            for (int i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+            for (int e = 0; e < t.n_14; ++e) {
+                const int a = t.pairs14[2 * e], b = t.pairs14[2 * e + 1];
+                const int pa = cnt[a] + fillv[a]++, pb = cnt[b] + fillv[b]++;
+                lst[pa] = b;
+                lst[pb] = a;
+                ls[pa] = s14[e];
+                ls[pb] = s14[e];
+            }
+            X.p14_start = upload(cnt);
+            X.p14_list = upload(lst);
+            X.p14_s = upload(ls);
         }
 
         // ----------------------------------------------------------- PME
@@ -451,6 +469,7 @@ struct System final : SystemBase {
             const int Kmax = std::max(M.K[0], std::max(M.K[1], M.K[2]));
             const size_t smem = sizeof(R2<double>) * (size_t)(Kmax + 2 * 16 * (Kmax + 1));
             if (smem > 48 * 1024) fail(LFE_ERR_ARG, "PME grid too large for the FFT tile");
+            column_groups();
         }
 
         // ----------------------------------------------- constant energies
@@ -620,6 +639,62 @@ struct System final : SystemBase {
         }
     }
 
+    // Column groups of the axis-0 pass of the plane/column transform: chunks
+    // of consecutive k2 at one k1, each with the partner columns (-k1, -k2)
+    // of its columns, so that the convolution's (m, -m) pairs stay inside
+    // one block.  The plane kernels are used when a plane and a group fit in
+    // shared memory.
+    void column_groups()
+    {
+        const int K1 = M.K[1], K2 = M.K[2], K12 = K1 * K2;
+        const int CW = 8;
+        std::vector<char> seen(K12, 0);
+        std::vector<int> start(1, 0), cols, part;
+        int gmax = 0;
+        auto partner = [&](int c) { const int k1 = c / K2, k2 = c % K2; return ((K1 - k1) % K1) * K2 + (K2 - k2) % K2; };
+        for (int k1 = 0; k1 < K1; ++k1)
+            for (int c0 = 0; c0 < K2; c0 += CW) {
+                std::vector<int> g;
+                for (int k2 = c0; k2 < std::min(c0 + CW, K2); ++k2) {
+                    const int c = k1 * K2 + k2;
+                    if (seen[c]) continue;
+                    seen[c] = 1;
+                    g.push_back(c);
+                    const int pc = partner(c);
+                    if (!seen[pc]) { seen[pc] = 1; g.push_back(pc); }
+                }
+                if (g.empty()) continue;
+                std::sort(g.begin(), g.end());
+                for (int c : g) {
+                    cols.push_back(c);
+                    part.push_back((int)(std::lower_bound(g.begin(), g.end(), partner(c)) - g.begin()));
+                }
+                start.push_back((int)cols.size());
+                gmax = std::max(gmax, (int)g.size());
+            }
+        const int* d_start = upload(start);
+        const int* d_cols = upload(cols);
+        const int* d_part = upload(part);
+        int optin = 0;
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+        auto setv = [&](auto& V) {
+            V.ngroups = (int)start.size() - 1;
+            V.cg_max = gmax;
+            V.cg_start = d_start;
+            V.cg_col = d_cols;
+            V.cg_part = d_part;
+            V.planes = (planes_smem(V) + 1024 <= (size_t)optin && columns_smem(V) + 1024 <= (size_t)optin) ? 1 : 0;
+        };
+        setv(M);
+        if (dual) setv(M64);
+        if (dual && !M64.planes) M.planes = 0;   // both branches use one transform layout
+        if (M.planes) {
+            planes_setup(M);
+            if (dual) planes_setup(M64);
+            CK(cudaGetLastError());
+        }
+    }
+
     // self and neutralising-background energies of each class (they depend
     // on the charges only)
     void constant_energies()
@@ -776,21 +851,36 @@ struct System final : SystemBase {
         for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
         launch_pairs(S, N, pair_warps, br[0]);
         launch_spread(S, M, br[1]);
-        launch_fft(M, 2, +1, 1, br[1]);
-        CK(cudaEventRecord(ev_z, br[1]));
-        launch_fft(M, 1, +1, 0, br[1]);
-        launch_fft(M, 0, +1, 0, br[1]);
-        launch_conv(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, br[1]);
-        launch_fft(M, 0, -1, 0, br[1]);
-        launch_fft(M, 1, -1, 0, br[1]);
-        launch_fft(M, 2, -1, 0, br[1]);
+        if (M.planes) {
+            launch_planes(M, PLANE_FWD_FIX, br[1]);
+            CK(cudaEventRecord(ev_z, br[1]));
+            launch_columns(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, br[1]);
+            launch_planes(M, PLANE_INV, br[1]);
+        } else {
+            launch_fft(M, 2, +1, 1, br[1]);
+            CK(cudaEventRecord(ev_z, br[1]));
+            launch_fft(M, 1, +1, 0, br[1]);
+            launch_fft(M, 0, +1, 0, br[1]);
+            launch_conv(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, br[1]);
+            launch_fft(M, 0, -1, 0, br[1]);
+            launch_fft(M, 1, -1, 0, br[1]);
+            launch_fft(M, 2, -1, 0, br[1]);
+        }
         launch_gather(S, M, br[1]);
         if (dual) {
             CK(cudaStreamWaitEvent(br[2], ev_z, 0));
-            launch_fft(M64, 2, +1, 0, br[2]);
-            launch_fft(M64, 1, +1, 0, br[2]);
-            launch_fft(M64, 0, +1, 0, br[2]);
-            launch_conv(M64, S.E, S.lam, CONV_ENERGY, br[2]);
+            if (M64.planes) {
+                // FP64 is scarce on this part: the per-axis passes spread the
+                // axes 2 and 1 over more blocks than one block per plane
+                launch_fft(M64, 2, +1, 0, br[2]);
+                launch_fft(M64, 1, +1, 0, br[2]);
+                launch_columns(M64, S.E, S.lam, CONV_ENERGY, br[2]);
+            } else {
+                launch_fft(M64, 2, +1, 0, br[2]);
+                launch_fft(M64, 1, +1, 0, br[2]);
+                launch_fft(M64, 0, +1, 0, br[2]);
+                launch_conv(M64, S.E, S.lam, CONV_ENERGY, br[2]);
+            }
         }
         launch_uv_energy(S, N, uv_blocks, br[3]);
         launch_excl(S, X, br[3]);
@@ -1115,21 +1205,36 @@ struct System final : SystemBase {
             CK(cudaEventRecord(ev[11], st));
             launch_spread(S, M, st);
             CK(cudaEventRecord(ev[3], st));
-            launch_fft(M, 2, +1, 1, st);
-            if (dual) {
-                launch_fft(M64, 2, +1, 0, st);
-                launch_fft(M64, 1, +1, 0, st);
-                launch_fft(M64, 0, +1, 0, st);
-                launch_conv(M64, S.E, S.lam, CONV_ENERGY, st);
+            if (M.planes) {
+                // fwd: planes (+ the FP64 energy branch); conv: the column
+                // pass with its axis-0 transforms; inv: planes
+                launch_planes(M, PLANE_FWD_FIX, st);
+                if (dual) {
+                    launch_fft(M64, 2, +1, 0, st);
+                    launch_fft(M64, 1, +1, 0, st);
+                    launch_columns(M64, S.E, S.lam, CONV_ENERGY, st);
+                }
+                CK(cudaEventRecord(ev[4], st));
+                launch_columns(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, st);
+                CK(cudaEventRecord(ev[5], st));
+                launch_planes(M, PLANE_INV, st);
+            } else {
+                launch_fft(M, 2, +1, 1, st);
+                if (dual) {
+                    launch_fft(M64, 2, +1, 0, st);
+                    launch_fft(M64, 1, +1, 0, st);
+                    launch_fft(M64, 0, +1, 0, st);
+                    launch_conv(M64, S.E, S.lam, CONV_ENERGY, st);
+                }
+                launch_fft(M, 1, +1, 0, st);
+                launch_fft(M, 0, +1, 0, st);
+                CK(cudaEventRecord(ev[4], st));
+                launch_conv(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, st);
+                CK(cudaEventRecord(ev[5], st));
+                launch_fft(M, 0, -1, 0, st);
+                launch_fft(M, 1, -1, 0, st);
+                launch_fft(M, 2, -1, 0, st);
             }
-            launch_fft(M, 1, +1, 0, st);
-            launch_fft(M, 0, +1, 0, st);
-            CK(cudaEventRecord(ev[4], st));
-            launch_conv(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, st);
-            CK(cudaEventRecord(ev[5], st));
-            launch_fft(M, 0, -1, 0, st);
-            launch_fft(M, 1, -1, 0, st);
-            launch_fft(M, 2, -1, 0, st);
             CK(cudaEventRecord(ev[6], st));
             launch_gather(S, M, st);
             CK(cudaEventRecord(ev[7], st));
@@ -1179,14 +1284,24 @@ struct System final : SystemBase {
         if constexpr (std::is_same<real, double>::value) P64 = &M;
         else P64 = &M64;
         launch_spread(S, M, st);
-        launch_fft(M, 2, +1, 1, st);
-        if (dual) launch_fft(M64, 2, +1, 0, st);
-        launch_fft(*P64, 1, +1, 0, st);
-        launch_fft(*P64, 0, +1, 0, st);
-        launch_conv(*P64, S.E, lam0, CONV_POTENTIAL, st);
-        launch_fft(*P64, 0, -1, 0, st);
-        launch_fft(*P64, 1, -1, 0, st);
-        launch_fft(*P64, 2, -1, 0, st);
+        if (M.planes) {
+            launch_planes(M, PLANE_FWD_FIX, st);
+            if (dual) {
+                launch_fft(M64, 2, +1, 0, st);
+                launch_fft(M64, 1, +1, 0, st);
+            }
+            launch_columns(*P64, S.E, lam0, CONV_POTENTIAL, st);
+            launch_planes(*P64, PLANE_INV, st);
+        } else {
+            launch_fft(M, 2, +1, 1, st);
+            if (dual) launch_fft(M64, 2, +1, 0, st);
+            launch_fft(*P64, 1, +1, 0, st);
+            launch_fft(*P64, 0, +1, 0, st);
+            launch_conv(*P64, S.E, lam0, CONV_POTENTIAL, st);
+            launch_fft(*P64, 0, -1, 0, st);
+            launch_fft(*P64, 1, -1, 0, st);
+            launch_fft(*P64, 2, -1, 0, st);
+        }
         AdjConst c{};
         for (int d = 0; d < 3; ++d) {
             c.L[d] = P.box[d];

@@ -61,8 +61,9 @@ struct NblView {
     int n_cl_max;         // capacity in clusters
     R4<float>* bbc;       // cluster bounding-box centres [n_cl_max]
     R4<float>* bbh;       // half extents [n_cl_max]
-    int* tile_cnt;        // [n_cl_max]
-    int* tile_off;        // [n_cl_max + 1]
+    int* tile_cnt;        // [27 n_cl_max] tiles per (i-cluster, shift), then offsets inside the cluster
+    int* tile_tot;        // [n_cl_max] tiles per i-cluster (zeroed by the scan)
+    int* tile_off;        // [n_cl_max + 1] first tile of each i-cluster
     int4* tiles;          // [cap]  (I, shift code, class, diagonal)
     int* jidx;            // [cap * 32] j slots of each tile (-1 = empty)
     unsigned* masks;      // [cap * 32]
@@ -87,6 +88,12 @@ struct ExclView {
     const int2* p14;
     const R2<real>* s14;    // (s_LJ, s_C)
     const R2<double>* s14d; // the same scales in FP64 (parameter gradients)
+    // per-atom partner lists (caller order, both directions)
+    const int* ex_start;      // [n + 1] exclusion partners
+    const int* ex_list;
+    const int* p14_start;     // [n + 1] 1-4 partners
+    const int* p14_list;
+    const R2<real>* p14_s;    // (s_LJ, s_C) of each 1-4 partner entry
 };
 
 template <typename real>
@@ -106,6 +113,12 @@ struct PmeView {
     int rad[3][8];
     real* phi_u;              // [n_u] reciprocal potential of the other class at solute atoms
     R2<double>* Zraw64;       // optional: FP64 copy of the packed charge grid written by the first pass
+    // plane / column transform (used when a K1 x K2 plane fits in shared memory)
+    int planes;               // 1: plane kernels in use, 0: one kernel per axis
+    int ngroups, cg_max;      // column groups of the axis-0 pass and the largest group
+    const int* cg_start;      // [ngroups + 1]
+    const int* cg_col;        // [K1 K2] flat column index k1 K2 + k2, grouped, ascending in a group
+    const int* cg_part;       // [K1 K2] position in the group of each column's partner (-k1, -k2)
 };
 
 template <typename real>
@@ -178,6 +191,19 @@ enum { CONV_BOTH = 0, CONV_ENERGY = 1, CONV_POTENTIAL = 2 };
 template <typename real> void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode,
                                           cudaStream_t st);
 template <typename real> void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st);
+// plane / column transform: PLANE_FWD_FIX reads the fixed-point grids (and
+// writes the FP64 copy when Zraw64 is set), PLANE_FWD transforms Z in place,
+// PLANE_INV is the inverse transform of axes 1 and 2
+enum { PLANE_FWD_FIX = 0, PLANE_FWD = 1, PLANE_INV = 2 };
+template <typename real> void launch_planes(const PmeView<real>& p, int mode, cudaStream_t st);
+// axis-0 transform of every column group with the convolution (mode as for
+// launch_conv); CONV_POTENTIAL and CONV_BOTH end with the inverse axis-0 transform
+template <typename real> void launch_columns(const PmeView<real>& p, long long* E, const LamState* lam, int mode,
+                                             cudaStream_t st);
+// shared-memory sizes of the plane and column kernels, and their attribute setup
+template <typename real> size_t planes_smem(const PmeView<real>& p);
+template <typename real> size_t columns_smem(const PmeView<real>& p);
+template <typename real> void planes_setup(const PmeView<real>& p);
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
 template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);

@@ -7,6 +7,8 @@
 //   soft LJ   eps_ij u_cap(r / sigma_ij) S(r)          (solute-solvent pairs only)
 // with S the quintic switch on [r_sw, r_c], Lorentz-Berthelot mixing, class
 // weights 1 (vv, uu), h_A (uv Coulomb + LJ) and h_B (soft).
+#include <type_traits>
+
 #include "lfe_views.cuh"
 
 namespace lfe {
@@ -69,34 +71,67 @@ __global__ void k_col_keys(SysView<real> s, NblView<real> nb)
 // exclusive scan of n ints (single block of 1024 threads); zeroes `in`;
 // writes the total to *total (when given) and raises the overflow bit when it
 // exceeds cap
-__global__ void k_scan_block(int* in, int* out, int n, int* total, int cap, int* errflag)
+__global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, int* total, int cap, int* errflag)
 {
-    __shared__ int part[1024];
-    const int tid = threadIdx.x;
+    constexpr int PER_MAX = 32;
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int b = tid * per, e = min(n, b + per);
+    int v[PER_MAX];
     int s = 0;
-    for (int i = b; i < e; ++i) s += in[i];
-    part[tid] = s;
-    __syncthreads();
-    for (int off = 1; off < blockDim.x; off <<= 1) {
-        int v = tid >= off ? part[tid - off] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
+    if (per <= PER_MAX) {
+        // all of this thread's loads in flight at once
+#pragma unroll
+        for (int k = 0; k < PER_MAX; ++k) {
+            v[k] = (k < per && b + k < e) ? in[b + k] : 0;
+            s += v[k];
+        }
+    } else {
+        for (int i = b; i < e; ++i) s += in[i];
     }
-    int run = part[tid] - s;
-    for (int i = b; i < e; ++i) {
-        int v = in[i];
-        out[i] = run;
-        run += v;
-        in[i] = 0;
+    // block-wide exclusive scan of the per-thread sums (warp shuffles)
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        int x = lane < nw ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane < nw) wsum[lane] = x;
+    }
+    __syncthreads();
+    int run = incl - s + (warp > 0 ? wsum[warp - 1] : 0);
+    const int grand = wsum[(blockDim.x >> 5) - 1];
+    if (per <= PER_MAX) {
+#pragma unroll
+        for (int k = 0; k < PER_MAX; ++k) {
+            if (k < per && b + k < e) {
+                out[b + k] = run;
+                run += v[k];
+                in[b + k] = 0;
+            }
+        }
+    } else {
+        for (int i = b; i < e; ++i) {
+            const int x = in[i];
+            out[i] = run;
+            run += x;
+            in[i] = 0;
+        }
     }
     if (tid == blockDim.x - 1) {
-        out[n] = part[tid];
+        out[n] = grand;
         if (total) {
-            *total = part[tid];
-            if (part[tid] > cap) atomicOr(errflag, ERRB_OVERFLOW);
+            *total = grand;
+            if (grand > cap) atomicOr(errflag, ERRB_OVERFLOW);
         }
     }
 }
@@ -257,98 +292,131 @@ __device__ __forceinline__ float box_gap2(const SysView<real>& s, const R4<float
     return d2;
 }
 
-// Tile list.  One warp per i-cluster I.  The diagonal tile (I with itself,
-// no shift, pairs j > i) comes first; then, for each class of partner
-// cluster (solute, solvent) and each of the 27 periodic shifts, every atom
-// of every partner cluster J >= I (J == I only for the upper half of the
-// shifts, so each pair image is visited once) whose distance to I's bounding
-// box is below r_cut + skin is appended to a j list, 32 atoms per tile.  A
-// tile therefore has one shift and one class.  WRITE = 0 counts tiles,
-// WRITE = 1 writes them at the scanned offsets.
+// Tile list.  One warp per (i-cluster I, periodic shift): 27 warps per
+// cluster.  The shift-13 warp (no shift) writes I's diagonal tile (I with
+// itself, pairs j > i) first.  Then, for each class of partner cluster
+// (solute, solvent), every atom of every partner cluster J >= I (J == I only
+// for the upper half of the shifts, so each pair image is visited once)
+// whose distance to I's bounding box is below r_cut + skin is appended to a
+// j list, 32 atoms per tile.  A tile therefore has one shift and one class,
+// and the tiles of one I are contiguous (shift-major).  The warp first lists
+// the partner clusters whose boxes are in range (independent box tests, four
+// chunks of 32 boxes in flight), then filters their atoms eight clusters at a
+// time, so that the chain of dependent loads stays short.  WRITE = 0 counts
+// tiles per (I, shift), WRITE = 1 writes them at the offsets formed by
+// k_tile_prefix (within I) and the scan over clusters.
+constexpr int TILE_CAND = 128;     // partner clusters listed per round (per warp)
+constexpr int TILE_BATCH = 8;      // partner clusters whose atoms are loaded together
+
 template <typename real, int WRITE>
 __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb)
 {
-    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    __shared__ int cand_sh[4][TILE_CAND];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (I >= nb.n_cl_max) return;
+    int* cand = cand_sh[(threadIdx.x >> 5) & 3];
+    if (w >= nb.n_cl_max * 27) return;
+    const int I = w / 27, sh = w - I * 27;
     const int ncl = num_clusters(s, nb);
     if (I >= ncl) {
-        if (!WRITE && lane == 0) nb.tile_cnt[I] = 0;
+        if (!WRITE && lane == 0) nb.tile_cnt[w] = 0;
         return;
     }
     const R4<float> ci = nb.bbc[I], hi = nb.bbh[I];
     const bool iu = I < s.n_ucl;
-    const int base = WRITE ? nb.tile_off[I] : 0;
+    const int base = WRITE ? nb.tile_off[I] + nb.tile_cnt[w] : 0;
     int count = 0;
-    // diagonal tile
-    if (WRITE && base < nb.cap) {
-        nb.jidx[(size_t)base * 32 + lane] = s.perm[I * 32 + lane] >= 0 ? I * 32 + lane : -1;
-        if (lane == 0) nb.tiles[base] = make_int4(I, 13, iu ? 1 : 0, 1);
+    if (sh == 13) {
+        if (WRITE && base < nb.cap) {
+            nb.jidx[(size_t)base * 32 + lane] = s.perm[I * 32 + lane] >= 0 ? I * 32 + lane : -1;
+            if (lane == 0) nb.tiles[base] = make_int4(I, 13, iu ? 1 : 0, 1);
+        }
+        count = 1;
     }
-    count = 1;
-    const unsigned lt = (1u << lane) - 1u;
     // every atom lies in [0, L): a shift -1 (+1) along an axis can bring a
     // partner within the cutoff only if I's box reaches within r_cut + skin
     // of the lower (upper) face
     const float cut = sqrtf(nb.cut2);
-    bool okm[3], okp[3];
+    int svs[3];
+    shift_vec(sh, svs);
+    bool allowed = true;
     {
         const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
         for (int d = 0; d < 3; ++d) {
-            okm[d] = c0[d] - h0[d] < cut;
-            okp[d] = c0[d] + h0[d] > (float)s.L[d] - cut;
+            if (svs[d] < 0 && !(c0[d] - h0[d] < cut)) allowed = false;
+            if (svs[d] > 0 && !(c0[d] + h0[d] > (float)s.L[d] - cut)) allowed = false;
         }
     }
-    for (int jc = 0; jc < 2; ++jc) {
-        const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
-        const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
-        for (int sh = 0; sh < 27; ++sh) {
-            int svs[3];
-            shift_vec(sh, svs);
-            bool allowed = true;
-            for (int d = 0; d < 3; ++d)
-                if ((svs[d] < 0 && !okm[d]) || (svs[d] > 0 && !okp[d])) allowed = false;
-            if (!allowed) continue;
+    const unsigned lt = (1u << lane) - 1u;
+    if (allowed) {
+        const float shx = svs[0] * (float)s.L[0], shy = svs[1] * (float)s.L[1], shz = svs[2] * (float)s.L[2];
+        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
+        for (int jc = 0; jc < 2; ++jc) {
+            const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
+            const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
             int nbuf = 0;   // atoms already placed in the open tile
-            for (int J0 = max(I, jb); J0 < je; J0 += 32) {
-                const int J = J0 + lane;
-                bool pc = J < je && (J != I || sh > 13);
-                if (pc) pc = box_gap2(s, ci, hi, nb.bbc[J], nb.bbh[J], sh) < nb.cut2;
-                unsigned bal = __ballot_sync(0xffffffffu, pc);
-                while (bal) {
-                    const int jj = __ffs(bal) - 1;
-                    bal &= bal - 1u;
-                    const int Jp = J0 + jj;
-                    const int slot = Jp * 32 + lane;
-                    bool keep = s.perm[slot] >= 0;
-                    if (keep) {
-                        int sv[3];
-                        shift_vec(sh, sv);
-                        const R4<real> p = s.xq[slot];
-                        const float pv[3] = {(float)p.x + sv[0] * (float)s.L[0], (float)p.y + sv[1] * (float)s.L[1],
-                                             (float)p.z + sv[2] * (float)s.L[2]};
-                        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
-                        float d2 = 0.f;
-                        for (int d = 0; d < 3; ++d) {
-                            const float g = fmaxf(fabsf(pv[d] - c0[d]) - h0[d], 0.f);
-                            d2 += g * g;
+            int J0 = max(I, jb);
+            while (J0 < je) {
+                // list the partner clusters in range, in ascending order
+                int nc = 0;
+                while (J0 < je && nc + 128 <= TILE_CAND) {
+                    bool pc[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int J = J0 + 32 * u + lane;
+                        pc[u] = J < je && (J != I || sh > 13);
+                        if (pc[u]) pc[u] = box_gap2(s, ci, hi, nb.bbc[J], nb.bbh[J], sh) < nb.cut2;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const unsigned bal = __ballot_sync(0xffffffffu, pc[u]);
+                        if (pc[u]) cand[nc + __popc(bal & lt)] = J0 + 32 * u + lane;
+                        nc += __popc(bal);
+                    }
+                    J0 += 128;
+                }
+                __syncwarp();
+                // filter their atoms, TILE_BATCH clusters per batch of loads
+                for (int c0i = 0; c0i < nc; c0i += TILE_BATCH) {
+                    R4<real> pbuf[TILE_BATCH];
+                    bool live[TILE_BATCH];
+                    int slots[TILE_BATCH];
+#pragma unroll
+                    for (int u = 0; u < TILE_BATCH; ++u) {
+                        slots[u] = c0i + u < nc ? cand[c0i + u] * 32 + lane : -1;
+                        live[u] = slots[u] >= 0 && s.perm[slots[u]] >= 0;
+                        if (slots[u] >= 0) pbuf[u] = s.xq[slots[u]];
+                    }
+#pragma unroll
+                    for (int u = 0; u < TILE_BATCH; ++u) {
+                        if (c0i + u >= nc) break;
+                        bool keep = live[u];
+                        if (keep) {
+                            const float pv[3] = {(float)pbuf[u].x + shx, (float)pbuf[u].y + shy,
+                                                 (float)pbuf[u].z + shz};
+                            float d2 = 0.f;
+                            for (int d = 0; d < 3; ++d) {
+                                const float g = fmaxf(fabsf(pv[d] - c0[d]) - h0[d], 0.f);
+                                d2 += g * g;
+                            }
+                            keep = d2 < nb.cut2;
                         }
-                        keep = d2 < nb.cut2;
-                    }
-                    const unsigned kb = __ballot_sync(0xffffffffu, keep);
-                    if (WRITE && keep) {
-                        const int pos = nbuf + __popc(kb & lt);
-                        const int t = base + count + (pos >> 5);
-                        if (t < nb.cap) nb.jidx[(size_t)t * 32 + (pos & 31)] = slot;
-                    }
-                    nbuf += __popc(kb);
-                    while (nbuf >= 32) {
-                        if (WRITE && lane == 0 && base + count < nb.cap)
-                            nb.tiles[base + count] = make_int4(I, sh, cls, 0);
-                        ++count;
-                        nbuf -= 32;
+                        const unsigned kb = __ballot_sync(0xffffffffu, keep);
+                        if (WRITE && keep) {
+                            const int pos = nbuf + __popc(kb & lt);
+                            const int t = base + count + (pos >> 5);
+                            if (t < nb.cap) nb.jidx[(size_t)t * 32 + (pos & 31)] = slots[u];
+                        }
+                        nbuf += __popc(kb);
+                        while (nbuf >= 32) {
+                            if (WRITE && lane == 0 && base + count < nb.cap)
+                                nb.tiles[base + count] = make_int4(I, sh, cls, 0);
+                            ++count;
+                            nbuf -= 32;
+                        }
                     }
                 }
+                __syncwarp();
             }
             if (nbuf > 0) {
                 if (WRITE && base + count < nb.cap) {
@@ -359,7 +427,7 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
             }
         }
     }
-    if (!WRITE && lane == 0) nb.tile_cnt[I] = count;
+    if (!WRITE && lane == 0) nb.tile_cnt[w] = count;
 }
 
 // interaction masks: bit k of lane i set = pair (I*32+i, jidx[k]) is
@@ -470,6 +538,24 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
     }
 }
 
+// Per-cluster tile totals from the per-(cluster, shift) counts: one warp
+// per cluster turns its 27 counts into offsets inside the cluster (kept in
+// tile_cnt) and writes the cluster's total to tile_tot for the scan.
+__global__ void k_tile_prefix(int* cnt, int* tot, int n_cl)
+{
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (I >= n_cl) return;
+    const int c = lane < 27 ? cnt[I * 27 + lane] : 0;
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane < 27) cnt[I * 27 + lane] = incl - c;
+    if (lane == 26) tot[I] = incl;
+}
+
 template <typename real>
 void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st)
 {
@@ -484,10 +570,12 @@ void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStrea
     k_assign<real><<<(s.n_pad + B - 1) / B, B, 0, st>>>(s, nb);
     const int wb = (nb.n_cl_max * 32 + 127) / 128;
     k_bbox<real><<<wb, 128, 0, st>>>(s, nb);
-    k_tiles<real, 0><<<wb, 128, 0, st>>>(s, nb);
-    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_cnt, nb.tile_off, nb.n_cl_max, s.flags + FL_NTILES, nb.cap,
+    const int tb = (nb.n_cl_max * 27 * 32 + 127) / 128;
+    k_tiles<real, 0><<<tb, 128, 0, st>>>(s, nb);
+    k_tile_prefix<<<wb, 128, 0, st>>>(nb.tile_cnt, nb.tile_tot, nb.n_cl_max);
+    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_tot, nb.tile_off, nb.n_cl_max, s.flags + FL_NTILES, nb.cap,
                                      s.flags + FL_ERROR);
-    k_tiles<real, 1><<<wb, 128, 0, st>>>(s, nb);
+    k_tiles<real, 1><<<tb, 128, 0, st>>>(s, nb);
     const int mb = (int)(((long long)nb.cap * 32 + 127) / 128);
     k_masks<real><<<mb, 128, 0, st>>>(s, nb);
     if (s.n_ucl > 0) {
@@ -535,17 +623,124 @@ __device__ __forceinline__ void erfc_exp(double x, double& erfcv, double& ex)
     ex = exp(-x * x);
 }
 
-// One warp walks a contiguous chunk of the (I-sorted) tile list.  Lane i
-// holds atom I*32+i; the tile's 32 j atoms rotate through the lanes by
-// shuffles together with their force accumulators (Newton's third law inside
-// the tile).  The tile's class (vv, uu or uv) and shift are uniform, so the
-// branch on them is warp-uniform.  i-forces stay in registers while
-// consecutive tiles share I.  Solute-solvent energies are not accumulated
-// here (k_uv_energy forms them in FP64).
+// Force and energy of one pair within the cutoff (dx, dy, dz = r_j - r_i):
+// returns g with force on i = -g (dx, dy, dz) and on j = +g (dx, dy, dz);
+// energy = ec + v (Coulomb erfc and switched LJ; uv energies are formed in
+// FP64 elsewhere).  For solute-solvent pairs g mixes the bases with h_A and
+// the capped soft basis (Eq. 5-6) with h_B.
+template <typename real>
+struct PairConst {
+    real rc2, swi, rsw_swi, alpha, tas, hA, hB;
+};
+
+template <typename real>
+__device__ __forceinline__ real pair_force(real r2, real qq, real sg, real e4, bool uv, const PairConst<real>& c,
+                                           real& ec, real& v)
+{
+    const real rinv = rsqrt_(r2);
+    const real r = r2 * rinv;
+    const real rinv2 = rinv * rinv;
+    real erfcv, ex;
+    erfc_exp(c.alpha * r, erfcv, ex);
+    ec = qq * erfcv * rinv;
+    const real fc = (ec + qq * c.tas * ex) * rinv2;
+    const real s2 = sg * sg * rinv2;
+    const real s6 = s2 * s2 * s2;
+    v = e4 * (s6 * s6 - s6);
+    real fl = e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
+    const real tt = fmax((real)0, r * c.swi - c.rsw_swi);
+    const real tt2 = tt * tt;
+    const real S = (real)1 - tt2 * tt * ((real)10 - (real)15 * tt + (real)6 * tt2);
+    const real omt = (real)1 - tt;
+    const real dS = (real)-30 * tt2 * omt * omt * c.swi;
+    fl = fl * S - v * dS * rinv;
+    v *= S;
+    real g = fc + fl;
+    if (uv) {
+        // capped soft basis (Eq. 5-6): identical to LJ for r >= sigma_ij
+        real fs = fl;
+        if (e4 == (real)0) {
+            fs = 0;
+        } else if (r < sg) {
+            const real sgi = (real)1 / sg;
+            const real x = r * sgi, x2 = x * x, x3 = x2 * x;
+            const real u = ((real)-868 * x2 + (real)2188.8 * x - (real)1440) * x3 * x + (real)119.2;
+            const real du = ((real)-5208 * x2 + (real)10944 * x - (real)5760) * x3;
+            fs = -(real)0.25 * e4 * (du * sgi * S + u * dS) * rinv;
+        }
+        g = c.hA * g + c.hB * fs;
+    }
+    return g;
+}
+
+template <typename real>
+__device__ __forceinline__ PairConst<real> pair_const(const SysView<real>& s)
+{
+    PairConst<real> c;
+    c.rc2 = s.rc2;
+    c.swi = s.sw_inv_w;
+    c.rsw_swi = s.rsw * s.sw_inv_w;
+    c.alpha = s.alpha;
+    c.tas = s.two_a_sqrtpi;
+    c.hA = (real)s.lam->hA;
+    c.hB = (real)s.lam->hB;
+    return c;
+}
+
+// One tile by rotation: lane i holds i atom I*32+i (xi, yi, zi, qi, si, ei,
+// already shifted for the tile); the tile's 32 j atoms (pj, ljv, shifted)
+// rotate through the lanes by shuffles together with their force
+// accumulators (Newton's third law inside the tile).  m: lane i's mask row.
+// Adds the i-force to (fix, fiy, fiz), flushes the j-forces, returns the
+// lane's energy.
+template <typename real>
+__device__ __forceinline__ real tile_rotate(const SysView<real>& s, const PairConst<real>& c, real xit, real yit,
+                                            real zit, real qi, real si, real ei, R4<real> pj, R2<real> ljv,
+                                            unsigned m, bool uv, int slot_j, long long& fix, long long& fiy,
+                                            long long& fiz, int& npairs)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int src = (lane + 1) & 31;
+    real xj = pj.x, yj = pj.y, zj = pj.z, qj = pj.w, sj = ljv.x, ej = ljv.y;
+    real fjx = 0, fjy = 0, fjz = 0, fx = 0, fy = 0, fz = 0, e0 = 0;
+    // bit 0 of mr is the mask bit of the j atom this lane holds
+    unsigned mr = __funnelshift_r(m, m, lane);
+#pragma unroll 2
+    for (int k = 0; k < 32; ++k) {
+        const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
+        const real r2 = dx * dx + dy * dy + dz * dz;
+        if ((mr & 1u) && r2 < c.rc2) {
+            real ec, v;
+            const real g = pair_force(r2, qi * qj, si + sj, ei * ej, uv, c, ec, v);
+            fx -= g * dx; fy -= g * dy; fz -= g * dz;
+            fjx += g * dx; fjy += g * dy; fjz += g * dz;
+            e0 += ec + v;
+            ++npairs;
+        }
+        mr = __funnelshift_r(mr, mr, 1);
+        xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
+        zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
+        sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
+        fjx = __shfl_sync(FULL, fjx, src); fjy = __shfl_sync(FULL, fjy, src);
+        fjz = __shfl_sync(FULL, fjz, src);
+    }
+    fix += to_fixed(fx, FSCALE);
+    fiy += to_fixed(fy, FSCALE);
+    fiz += to_fixed(fz, FSCALE);
+    if (slot_j >= 0)
+        flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
+    return e0;
+}
+
+// One warp walks a contiguous chunk of the (I-sorted) tile list, one tile at
+// a time by rotation; i-forces stay in registers while consecutive tiles
+// share I.  The tile's class (vv, uu or uv) and shift are uniform, so the
+// branch on them is warp-uniform.  Solute-solvent energies are not
+// accumulated here (k_uv_energy forms them in FP64).
 template <typename real>
 __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real> nb)
 {
-    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
@@ -554,17 +749,12 @@ __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real>
     const int t0 = (int)(((long long)ntiles * warp) / nwarp);
     const int t1 = (int)(((long long)ntiles * (warp + 1)) / nwarp);
     if (t0 >= t1) return;
-    const real hA = (real)s.lam->hA, hB = (real)s.lam->hB;
-    const real rc2 = s.rc2, swi = s.sw_inv_w, alpha = s.alpha, tas = s.two_a_sqrtpi;
-    const real rsw_swi = s.rsw * s.sw_inv_w;
-    const int src = (lane + 1) & 31;
-
+    const PairConst<real> c = pair_const(s);
     int curI = -1;
     real xi = 0, yi = 0, zi = 0, qi = 0, si = 0, ei = 0;
     long long fix = 0, fiy = 0, fiz = 0;
     double evv = 0, euu = 0;
     int npairs = 0;
-
     for (int t = t0; t < t1; ++t) {
         const int4 tl = nb.tiles[t];
         if (tl.x != curI) {
@@ -578,8 +768,8 @@ __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real>
         const unsigned m = nb.masks[(size_t)t * 32 + lane];
         const int slot_j = nb.jidx[(size_t)t * 32 + lane];
         const int sj_load = slot_j >= 0 ? slot_j : 0;
-        const R4<real> pj = s.xq[sj_load];
-        const R2<real> lj = s.lj[sj_load];
+        R4<real> pj = s.xq[sj_load];
+        const R2<real> ljv = s.lj[sj_load];
         const int sh = tl.y;
         const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
         // shift the far-side atom down by L so that the subtraction below is
@@ -587,74 +777,13 @@ __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real>
         const real xit = sx == 1 ? xi - s.L[0] : xi;
         const real yit = sy == 1 ? yi - s.L[1] : yi;
         const real zit = sz == 1 ? zi - s.L[2] : zi;
-        real xj = sx == -1 ? pj.x - s.L[0] : pj.x;
-        real yj = sy == -1 ? pj.y - s.L[1] : pj.y;
-        real zj = sz == -1 ? pj.z - s.L[2] : pj.z;
-        real qj = pj.w, sj = lj.x, ej = lj.y;
-        real fjx = 0, fjy = 0, fjz = 0, fx = 0, fy = 0, fz = 0, e0 = 0;
-        // bit 0 of mr is the mask bit of the j atom this lane holds
-        unsigned mr = __funnelshift_r(m, m, lane);
-        const bool uv = tl.z == 2;
-
-#pragma unroll 2
-        for (int k = 0; k < 32; ++k) {
-            const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
-            const real r2 = dx * dx + dy * dy + dz * dz;
-            if ((mr & 1u) && r2 < rc2) {
-                const real rinv = rsqrt_(r2);
-                const real r = r2 * rinv;
-                const real rinv2 = rinv * rinv;
-                const real qq = qi * qj;
-                real erfcv, ex;
-                erfc_exp(alpha * r, erfcv, ex);
-                const real ec = qq * erfcv * rinv;
-                const real fc = (ec + qq * tas * ex) * rinv2;
-                const real sg = si + sj, e4 = ei * ej;
-                const real s2 = sg * sg * rinv2;
-                const real s6 = s2 * s2 * s2;
-                real v = e4 * (s6 * s6 - s6);
-                real fl = e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
-                const real tt = fmax((real)0, r * swi - rsw_swi);
-                const real tt2 = tt * tt;
-                const real S = (real)1 - tt2 * tt * ((real)10 - (real)15 * tt + (real)6 * tt2);
-                const real omt = (real)1 - tt;
-                const real dS = (real)-30 * tt2 * omt * omt * swi;
-                fl = fl * S - v * dS * rinv;
-                v *= S;
-                real g = fc + fl;
-                if (uv) {
-                    // capped soft basis (Eq. 5-6): identical to LJ for r >= sigma_ij
-                    real fs = fl;
-                    if (e4 == (real)0) {
-                        fs = 0;
-                    } else if (r < sg) {
-                        const real sgi = (real)1 / sg;
-                        const real x = r * sgi, x2 = x * x, x3 = x2 * x;
-                        const real u = ((real)-868 * x2 + (real)2188.8 * x - (real)1440) * x3 * x + (real)119.2;
-                        const real du = ((real)-5208 * x2 + (real)10944 * x - (real)5760) * x3;
-                        fs = -(real)0.25 * e4 * (du * sgi * S + u * dS) * rinv;
-                    }
-                    g = hA * g + hB * fs;
-                }
-                fx -= g * dx; fy -= g * dy; fz -= g * dz;
-                fjx += g * dx; fjy += g * dy; fjz += g * dz;
-                e0 += ec + v;
-                ++npairs;
-            }
-            mr = __funnelshift_r(mr, mr, 1);
-            xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
-            zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
-            sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
-            fjx = __shfl_sync(FULL, fjx, src); fjy = __shfl_sync(FULL, fjy, src);
-            fjz = __shfl_sync(FULL, fjz, src);
-        }
+        if (sx == -1) pj.x -= s.L[0];
+        if (sy == -1) pj.y -= s.L[1];
+        if (sz == -1) pj.z -= s.L[2];
+        const real e0 = tile_rotate(s, c, xit, yit, zit, qi, si, ei, pj, ljv, m, tl.z == 2, slot_j, fix, fiy, fiz,
+                                    npairs);
         if (tl.z == 0) evv += (double)e0;
         else if (tl.z == 1) euu += (double)e0;
-        fix += to_fixed(fx, FSCALE);
-        fiy += to_fixed(fy, FSCALE);
-        fiz += to_fixed(fz, FSCALE);
-        if (slot_j >= 0)
-            flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
     }
     flush_force(s, curI * 32 + lane, fix, fiy, fiz);
     const long long a0 = __double2ll_rn(warp_sum_d(evv) * ESCALE);
@@ -681,7 +810,9 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
     const double rc2 = (double)s.rc2, rsw = (double)s.rsw, swi = (double)s.sw_inv_w;
     const double alpha = (double)s.alpha;
     double euv = 0.0, esoft = 0.0;
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n; w += gridDim.x * blockDim.x) {
+    // consecutive pairs go to consecutive blocks, so that a list shorter than
+    // the grid still spreads over every SM's FP64 units
+    for (int w = threadIdx.x * gridDim.x + blockIdx.x; w < n; w += gridDim.x * blockDim.x) {
         const int4 pr = nb.uvp[w];
         const R4<real> pi = s.xq[pr.x], pj = s.xq[pr.y];
         int sv[3];
@@ -737,52 +868,80 @@ void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, c
 
 // ------------------------------------------------- exclusions and 1-4 pairs
 // excluded pair (any distance, minimum image): -k_e q_i q_j erf(alpha r)/r;
-// 1-4 pair: s_C k_e q_i q_j / r + s_LJ 4 eps_ij [(s/r)^12 - (s/r)^6]
+// 1-4 pair: s_C k_e q_i q_j / r + s_LJ 4 eps_ij [(s/r)^12 - (s/r)^6].
+// Gathered per atom (four threads per atom over its exclusion and 1-4
+// partner lists): each pair is evaluated from both ends, so every atom's
+// force is one sum written with one set of atomics instead of one set per
+// pair, and the energy is counted at the end with the lower index.
 template <typename real>
 __global__ void k_excl(SysView<real> s, ExclView<real> ex)
 {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = tid >> 2, sub = tid & 3;
     double acc[6] = {0, 0, 0, 0, 0, 0};   // excl vv, uu, uv, 14 vv, uu, uv
-    if (e < ex.n_excl + ex.n14) {
-        const bool is14 = e >= ex.n_excl;
-        const int2 pr = is14 ? ex.p14[e - ex.n_excl] : ex.excl[e];
-        const int sa = s.iperm[pr.x], sb = s.iperm[pr.y];
-        const R4<real> pa = s.xq[sa], pb = s.xq[sb];
-        real d[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
-        for (int k = 0; k < 3; ++k) d[k] -= s.L[k] * rint_(d[k] * s.invL[k]);
-        const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        real en = 0, g = 0;   // g = -(dE/dr)/r
-        if (r2 > (real)0) {
-            const real rinv = rsqrt_(r2);
-            const real rinv2 = rinv * rinv;
-            const real qq = pa.w * pb.w;
-            if (!is14) {
-                const real ar = s.alpha * r2 * rinv;
-                const real ev = erf_(ar);
-                en = -qq * ev * rinv;
-                // dE/dr = qq erf/r^2 - qq (2a/sqrt(pi)) exp(-a^2 r^2)/r
-                g = -(qq * ev * rinv2 - qq * s.two_a_sqrtpi * exp_(-ar * ar) * rinv) * rinv;
-            } else {
-                const R2<real> sc = ex.s14[e - ex.n_excl];
-                const R2<real> la = s.lj[sa], lb = s.lj[sb];
-                en = sc.y * qq * rinv;
-                g = sc.y * qq * rinv2 * rinv;
-                const real sg = la.x + lb.x, e4 = la.y * lb.y;
-                if (e4 != (real)0) {
-                    const real s2 = sg * sg * rinv2, s6 = s2 * s2 * s2;
-                    en += sc.x * e4 * (s6 * s6 - s6);
-                    g += sc.x * e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
+    real fx = 0, fy = 0, fz = 0;
+    int sa = 0;
+    if (a < s.n) {
+        sa = s.iperm[a];
+        const R4<real> pa = s.xq[sa];
+        const R2<real> la = s.lj[sa];
+        const int ua = s.sol[a];
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool is14 = pass == 1;
+            const int e0 = is14 ? ex.p14_start[a] : ex.ex_start[a];
+            const int e1 = is14 ? ex.p14_start[a + 1] : ex.ex_start[a + 1];
+            for (int e = e0 + sub; e < e1; e += 4) {
+                const int b = is14 ? ex.p14_list[e] : ex.ex_list[e];
+                const int sb = s.iperm[b];
+                const R4<real> pb = s.xq[sb];
+                real d[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
+                for (int k = 0; k < 3; ++k) d[k] -= s.L[k] * rint_(d[k] * s.invL[k]);
+                const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                real en = 0, g = 0;   // g = -(dE/dr)/r
+                if (r2 > (real)0) {
+                    const real rinv = rsqrt_(r2);
+                    const real rinv2 = rinv * rinv;
+                    const real qq = pa.w * pb.w;
+                    if (!is14) {
+                        const real ar = s.alpha * r2 * rinv;
+                        const real ev = erf_(ar);
+                        en = -qq * ev * rinv;
+                        // dE/dr = qq erf/r^2 - qq (2a/sqrt(pi)) exp(-a^2 r^2)/r
+                        g = -(qq * ev * rinv2 - qq * s.two_a_sqrtpi * exp_(-ar * ar) * rinv) * rinv;
+                    } else {
+                        const R2<real> sc = ex.p14_s[e];
+                        const R2<real> lb = s.lj[sb];
+                        en = sc.y * qq * rinv;
+                        g = sc.y * qq * rinv2 * rinv;
+                        const real sg = la.x + lb.x, e4 = la.y * lb.y;
+                        if (e4 != (real)0) {
+                            const real s2 = sg * sg * rinv2, s6 = s2 * s2 * s2;
+                            en += sc.x * e4 * (s6 * s6 - s6);
+                            g += sc.x * e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
+                        }
+                    }
+                }
+                // force on a: -g d (d = r_b - r_a)
+                fx -= g * d[0];
+                fy -= g * d[1];
+                fz -= g * d[2];
+                if (a < b) {
+                    const int ub = s.sol[b];
+                    const int cls = (ua && ub) ? 1 : ((ua || ub) ? 2 : 0);
+                    acc[(is14 ? 3 : 0) + cls] += (double)en;
                 }
             }
-            for (int k = 0; k < 3; ++k) {
-                long long f = to_fixed(g * d[k], FSCALE);
-                atomic_add_ll(&s.F[k * s.n_pad + sa], -f);
-                atomic_add_ll(&s.F[k * s.n_pad + sb], f);
-            }
         }
-        const int ua = s.sol[pr.x], ub = s.sol[pr.y];
-        const int cls = (ua && ub) ? 1 : ((ua || ub) ? 2 : 0);
-        acc[(is14 ? 3 : 0) + cls] = (double)en;
+    }
+    for (int o = 1; o < 4; o <<= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (a < s.n && sub == 0 && (fx != (real)0 || fy != (real)0 || fz != (real)0)) {
+        atomic_add_ll(&s.F[sa], to_fixed(fx, FSCALE));
+        atomic_add_ll(&s.F[s.n_pad + sa], to_fixed(fy, FSCALE));
+        atomic_add_ll(&s.F[2 * s.n_pad + sa], to_fixed(fz, FSCALE));
     }
     const int lane = threadIdx.x & 31;
     for (int c = 0; c < 6; ++c) {
@@ -794,10 +953,9 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
 template <typename real>
 void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t st)
 {
-    int n = ex.n_excl + ex.n14;
-    if (n == 0) return;
+    if (ex.n_excl + ex.n14 == 0) return;
     const int B = 256;
-    k_excl<real><<<(n + B - 1) / B, B, 0, st>>>(s, ex);
+    k_excl<real><<<(4 * s.n + B - 1) / B, B, 0, st>>>(s, ex);
 }
 
 #define LFE_INST(real)                                                                             \

@@ -122,6 +122,56 @@ __device__ __forceinline__ void dft_small(R2<real>* v, int R, int sign)
     }
 }
 
+// One Stockham stage of radix R (compile time, so the R values stay in
+// registers) over nl lines of length K held in shared memory: point t of
+// line l at buf[l * ls + t * es].  LF: consecutive threads take consecutive
+// lines (strided lines), otherwise consecutive points of one line.  tw holds
+// exp(sign 2 pi i t / K).
+template <typename real, bool LF, int R>
+__device__ __forceinline__ void smem_stage(const R2<real>* a, R2<real>* b, int nl, int K, int ls, int es, int Ns,
+                                           const R2<real>* tw, int sign)
+{
+    const int nbf = K / R;
+    const int tstep = K / (Ns * R);
+    const int total = nl * nbf;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        int l, j;
+        if (LF) { l = idx % nl; j = idx / nl; }
+        else { l = idx / nbf; j = idx - l * nbf; }
+        const int k = j % Ns;
+        const R2<real>* in = a + l * ls;
+        R2<real>* out = b + l * ls;
+        R2<real> v[R];
+        v[0] = in[j * es];
+        // r k tstep < K: no reduction of the twiddle index is needed
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(in[(j + r * nbf) * es], tw[r * k * tstep]);
+        dft_small(v, R, sign);
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) out[(base + r * Ns) * es] = v[r];
+    }
+}
+
+// All stages of the radix plan; returns the buffer that holds the result.
+template <typename real, bool LF>
+__device__ R2<real>* smem_fft(R2<real>* a, R2<real>* b, int nl, int K, int ls, int es, const int* rad, int nrad,
+                              const R2<real>* tw, int sign)
+{
+    int Ns = 1;
+    for (int st = 0; st < nrad; ++st) {
+        const int R = rad[st];
+        if (R == 4) smem_stage<real, LF, 4>(a, b, nl, K, ls, es, Ns, tw, sign);
+        else if (R == 2) smem_stage<real, LF, 2>(a, b, nl, K, ls, es, Ns, tw, sign);
+        else if (R == 3) smem_stage<real, LF, 3>(a, b, nl, K, ls, es, Ns, tw, sign);
+        else smem_stage<real, LF, 5>(a, b, nl, K, ls, es, Ns, tw, sign);
+        __syncthreads();
+        R2<real>* t = a; a = b; b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
 constexpr int FFT_NL = 16;    // lines per block
 
 // One pass of 1-D transforms of length K along AXIS for a block of FFT_NL
@@ -188,29 +238,7 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
         }
     }
     __syncthreads();
-    R2<real>* src = b0;
-    R2<real>* dst = b1;
-    int Ns = 1;
-    for (int st = 0; st < p.nrad[AXIS]; ++st) {
-        const int R = p.rad[AXIS][st];
-        const int nbf = K / R;
-        const int tstep = K / (Ns * R);
-        for (int idx = tid; idx < nl * nbf; idx += nt) {
-            const int l = idx / nbf, j = idx % nbf;
-            const int k = j % Ns;
-            const R2<real>* in = src + l * LD;
-            R2<real>* out = dst + l * LD;
-            R2<real> v[5];
-            v[0] = in[j];
-            for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nbf], tw[(r * k * tstep) % K]);
-            dft_small(v, R, sign);
-            const int base = (j / Ns) * Ns * R + k;
-            for (int r = 0; r < R; ++r) out[base + r * Ns] = v[r];
-        }
-        __syncthreads();
-        R2<real>* tmp = src; src = dst; dst = tmp;
-        Ns *= R;
-    }
+    const R2<real>* src = smem_fft<real, false>(b0, b1, nl, K, LD, 1, p.rad[AXIS], p.nrad[AXIS], tw, sign);
     for (int e = tid; e < FFT_NL * K; e += nt) {
         int l, t;
         if (AXIS == 2) { l = e / K; t = e % K; }
@@ -235,6 +263,233 @@ void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cuda
     } else {
         k_fft<real, 0, false><<<blocks, 256, smem, st>>>(p, sign);
     }
+}
+
+// ------------------------------------------ plane / column transform
+// The 3-D transform as two kinds of kernels instead of one launch per axis:
+// a plane kernel transforms the K1 x K2 plane of one k0 along axes 2 and 1
+// in shared memory, and a column kernel transforms groups of axis-0 columns,
+// applies the convolution to every (m, -m) pair (each column group holds the
+// partner column (-k1, -k2) of each of its columns) and, for the potentials,
+// transforms back along axis 0.  Forward: planes then columns; inverse:
+// (columns) then planes.
+
+template <typename real>
+__device__ __forceinline__ void load_twiddles(R2<real>* dst, const R2<real>* src, int K, int sign)
+{
+    for (int t = threadIdx.x; t < K; t += blockDim.x) {
+        R2<real> w = src[t];
+        if (sign < 0) w.y = -w.y;
+        dst[t] = w;
+    }
+}
+
+constexpr int PLANE_THREADS = 512;
+constexpr int COL_THREADS = 256;
+
+template <typename real, int MODE>
+__global__ void __launch_bounds__(PLANE_THREADS) k_plane(PmeView<real> p)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const int K1 = p.K[1], K2 = p.K[2];
+    const int LD = K2 + 1;
+    const int sign = MODE == PLANE_INV ? -1 : +1;
+    R2<real>* tw2 = reinterpret_cast<R2<real>*>(smem_raw);
+    R2<real>* tw1 = tw2 + K2;
+    R2<real>* a = tw1 + K1;
+    R2<real>* b = a + K1 * LD;
+    const int k0 = blockIdx.x;
+    load_twiddles(tw2, p.tw[2], K2, sign);
+    load_twiddles(tw1, p.tw[1], K1, sign);
+    const int base = k0 * K1 * K2;
+    for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
+        const int k1 = e / K2, k2 = e - k1 * K2;
+        const int g = base + e;
+        R2<real> v;
+        if (MODE == PLANE_FWD_FIX) {
+            const double qv = (double)p.Qfix[g] * (1.0 / QSCALE);
+            const double qu = (double)p.Qfix[p.KK + g] * ((double)p.qu_scale / QSCALE);
+            v.x = (real)qv;
+            v.y = (real)qu;
+            p.Qfix[g] = 0;
+            p.Qfix[p.KK + g] = 0;
+            if (p.Zraw64) {
+                R2<double> w;
+                w.x = qv;
+                w.y = qu;
+                p.Zraw64[g] = w;
+            }
+        } else {
+            v = p.Z[g];
+        }
+        a[k1 * LD + k2] = v;
+    }
+    __syncthreads();
+    R2<real>* r;
+    if (MODE == PLANE_INV) {
+        r = smem_fft<real, true>(a, b, K2, K1, 1, LD, p.rad[1], p.nrad[1], tw1, sign);
+        r = smem_fft<real, false>(r, r == a ? b : a, K1, K2, LD, 1, p.rad[2], p.nrad[2], tw2, sign);
+    } else {
+        r = smem_fft<real, false>(a, b, K1, K2, LD, 1, p.rad[2], p.nrad[2], tw2, sign);
+        r = smem_fft<real, true>(r, r == a ? b : a, K2, K1, 1, LD, p.rad[1], p.nrad[1], tw1, sign);
+    }
+    for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
+        const int k1 = e / K2, k2 = e - k1 * K2;
+        p.Z[base + e] = r[k1 * LD + k2];
+    }
+}
+
+template <typename real, int MODE>
+__global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long long* E, const LamState* lam)
+{
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double red[3][COL_THREADS / 32];
+    const int K0 = p.K[0], K1 = p.K[1], K2 = p.K[2];
+    const int K12 = K1 * K2;
+    const int LD = K0 + 1;
+    const int g0 = p.cg_start[blockIdx.x];
+    const int nc = p.cg_start[blockIdx.x + 1] - g0;
+    R2<real>* twf = reinterpret_cast<R2<real>*>(smem_raw);
+    R2<real>* twi = twf + K0;
+    R2<real>* a = twi + K0;
+    R2<real>* b = a + p.cg_max * LD;
+    int* cols = reinterpret_cast<int*>(b + p.cg_max * LD);
+    int* part = cols + p.cg_max;
+    load_twiddles(twf, p.tw[0], K0, +1);
+    load_twiddles(twi, p.tw[0], K0, -1);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        cols[c] = p.cg_col[g0 + c];
+        part[c] = p.cg_part[g0 + c];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * K0; e += blockDim.x) {
+        const int k0 = e / nc, c = e - k0 * nc;
+        a[c * LD + k0] = p.Z[k0 * K12 + cols[c]];
+    }
+    __syncthreads();
+    R2<real>* r = smem_fft<real, false>(a, b, nc, K0, LD, 1, p.rad[0], p.nrad[0], twf, +1);
+    double evv = 0, euu = 0, euv = 0;
+    const real hA = MODE != CONV_ENERGY ? (real)lam->hA : (real)0;
+    for (int e = threadIdx.x; e < nc * K0; e += blockDim.x) {
+        const int c = e / K0, k0 = e - c * K0;
+        const int pc = part[c];
+        const int n0 = k0 == 0 ? 0 : K0 - k0;
+        if (!(c < pc || (c == pc && k0 <= n0))) continue;   // each (m, -m) pair once
+        const int col = cols[c];
+        if (k0 == 0 && col == 0) {
+            if (MODE != CONV_ENERGY) {
+                R2<real> zero;
+                zero.x = zero.y = (real)0;
+                r[c * LD] = zero;
+            }
+            continue;
+        }
+        const int k1 = col / K2, k2 = col - k1 * K2;
+        const R2<real> zm = r[c * LD + k0], zn = r[pc * LD + n0];
+        // Z = Q_v + i s Q_u:  Q_v(m) = (Z(m) + conj Z(-m)) / 2,  Q_u(m) = (Z(m) - conj Z(-m)) / (2 i s)
+        R2<real> qv, qu;
+        const real hs = (real)0.5 / p.qu_scale;
+        qv.x = (real)0.5 * (zm.x + zn.x);
+        qv.y = (real)0.5 * (zm.y - zn.y);
+        qu.x = hs * (zm.y + zn.y);
+        qu.y = -hs * (zm.x - zn.x);
+        const real msq = p.msq[0][k0] + p.msq[1][k1] + p.msq[2][k2];
+        const real G = p.conv_pre * p.gfac[0][k0] * p.gfac[1][k1] * p.gfac[2][k2] / msq;
+        const bool self = (c == pc && k0 == n0);
+        if (MODE != CONV_POTENTIAL) {
+            const double mult = self ? 1.0 : 2.0;
+            evv += mult * 0.5 * (double)G * ((double)qv.x * qv.x + (double)qv.y * qv.y);
+            euu += mult * 0.5 * (double)G * ((double)qu.x * qu.x + (double)qu.y * qu.y);
+            euv += mult * (double)G * ((double)qu.x * qv.x + (double)qu.y * qv.y);
+        }
+        if (MODE != CONV_ENERGY) {
+            // W = G [(Q_v + h_A Q_u) + i (Q_u + h_A Q_v)]; at -m the class
+            // spectra are the complex conjugates
+            R2<real> P, Rr, wm, wn;
+            P.x = qv.x + hA * qu.x; P.y = qv.y + hA * qu.y;
+            Rr.x = qu.x + hA * qv.x; Rr.y = qu.y + hA * qv.y;
+            wm.x = G * (P.x - Rr.y); wm.y = G * (P.y + Rr.x);
+            wn.x = G * (P.x + Rr.y); wn.y = G * (-P.y + Rr.x);
+            r[c * LD + k0] = wm;
+            if (!self) r[pc * LD + n0] = wn;
+        }
+    }
+    if (MODE != CONV_POTENTIAL) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const double v0 = warp_sum_d(evv), v1 = warp_sum_d(euu), v2 = warp_sum_d(euv);
+        if (lane == 0) { red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; }
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            double v = 0;
+            for (int w = 0; w < COL_THREADS / 32; ++w) v += red[threadIdx.x][w];
+            const long long f = __double2ll_rn(v * ESCALE);
+            if (f) atomic_add_ll(&E[E_REC_VV + threadIdx.x], f);
+        }
+    }
+    if (MODE == CONV_ENERGY) return;
+    __syncthreads();
+    R2<real>* o = smem_fft<real, false>(r, r == a ? b : a, nc, K0, LD, 1, p.rad[0], p.nrad[0], twi, -1);
+    for (int e = threadIdx.x; e < nc * K0; e += blockDim.x) {
+        const int k0 = e / nc, c = e - k0 * nc;
+        p.Z[k0 * K12 + cols[c]] = o[c * LD + k0];
+    }
+}
+
+template <typename real>
+size_t planes_smem(const PmeView<real>& p)
+{
+    return sizeof(R2<real>) * (size_t)(p.K[2] + p.K[1] + 2 * p.K[1] * (p.K[2] + 1));
+}
+
+template <typename real>
+size_t columns_smem(const PmeView<real>& p)
+{
+    return sizeof(R2<real>) * (size_t)(2 * p.K[0] + 2 * p.cg_max * (p.K[0] + 1)) + 2 * sizeof(int) * (size_t)p.cg_max;
+}
+
+// The attribute is per kernel and process-wide, while systems with
+// different grids share the kernels: allow the device's whole opt-in
+// shared memory (less the kernel's static shared memory) rather than this
+// grid's need.
+template <typename K>
+static void allow_max_smem(K kernel, int optin)
+{
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) return;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+template <typename real>
+void planes_setup(const PmeView<real>& p)
+{
+    (void)p;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    allow_max_smem(k_plane<real, PLANE_FWD_FIX>, optin);
+    allow_max_smem(k_plane<real, PLANE_FWD>, optin);
+    allow_max_smem(k_plane<real, PLANE_INV>, optin);
+    allow_max_smem(k_columns<real, CONV_ENERGY>, optin);
+    allow_max_smem(k_columns<real, CONV_POTENTIAL>, optin);
+    allow_max_smem(k_columns<real, CONV_BOTH>, optin);
+}
+
+template <typename real>
+void launch_planes(const PmeView<real>& p, int mode, cudaStream_t st)
+{
+    const size_t sm = planes_smem(p);
+    if (mode == PLANE_FWD_FIX) k_plane<real, PLANE_FWD_FIX><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
+    else if (mode == PLANE_FWD) k_plane<real, PLANE_FWD><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
+    else k_plane<real, PLANE_INV><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
+}
+
+template <typename real>
+void launch_columns(const PmeView<real>& p, long long* E, const LamState* lam, int mode, cudaStream_t st)
+{
+    const size_t sm = columns_smem(p);
+    if (mode == CONV_ENERGY) k_columns<real, CONV_ENERGY><<<p.ngroups, COL_THREADS, sm, st>>>(p, E, lam);
+    else if (mode == CONV_POTENTIAL) k_columns<real, CONV_POTENTIAL><<<p.ngroups, COL_THREADS, sm, st>>>(p, E, lam);
+    else k_columns<real, CONV_BOTH><<<p.ngroups, COL_THREADS, sm, st>>>(p, E, lam);
 }
 
 // ------------------------------------------------------------ convolution
@@ -374,6 +629,19 @@ void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t 
 template <typename real>
 void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<double>* energy64, cudaStream_t st)
 {
+    if (p.planes) {
+        launch_spread(s, p, st);
+        launch_planes(p, PLANE_FWD_FIX, st);
+        if (energy64) {
+            launch_fft(*energy64, 2, +1, 0, st);
+            launch_fft(*energy64, 1, +1, 0, st);
+            launch_columns(*energy64, s.E, s.lam, CONV_ENERGY, st);
+        }
+        launch_columns(p, s.E, s.lam, energy64 ? CONV_POTENTIAL : CONV_BOTH, st);
+        launch_planes(p, PLANE_INV, st);
+        launch_gather(s, p, st);
+        return;
+    }
     launch_spread(s, p, st);
     launch_fft(p, 2, +1, 1, st);
     if (energy64) {
@@ -396,7 +664,12 @@ void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<do
     template void launch_spread<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
     template void launch_conv<real>(const PmeView<real>&, long long*, const LamState*, int, cudaStream_t); \
     template void launch_gather<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
-    template void launch_fft<real>(const PmeView<real>&, int, int, int, cudaStream_t);
+    template void launch_fft<real>(const PmeView<real>&, int, int, int, cudaStream_t);                       \
+    template void launch_planes<real>(const PmeView<real>&, int, cudaStream_t);                             \
+    template void launch_columns<real>(const PmeView<real>&, long long*, const LamState*, int, cudaStream_t); \
+    template size_t planes_smem<real>(const PmeView<real>&);                                                \
+    template size_t columns_smem<real>(const PmeView<real>&);                                               \
+    template void planes_setup<real>(const PmeView<real>&);
 LFE_INST_PME(float)
 LFE_INST_PME(double)
 
