@@ -262,6 +262,7 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
 {
     using Sh = Shape<KIND, NA>;
     constexpr int NC = Sh::NC;
+    (void)step;
     real o0[3];
     real rel0[NA][3];
     real p[NA][3];
@@ -289,16 +290,13 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
             for (int d = 0; d < 3; ++d) p[a][d] = rel0[a][d];
             continue;
         }
-        real nr[3];
-        normals3<real>(make_uint4((unsigned)atom, (unsigned)step, (unsigned)(step >> 32), 0u), g.key,
-                       nr[0], nr[1], nr[2]);
-        const real sd = sqrt(g.kT * ((real)1 - g.a_fric * g.a_fric) * w[a]);
+        const real kick[3] = {g.noise[3 * atom], g.noise[3 * atom + 1], g.noise[3 * atom + 2]};
         const real vv[3] = {v.x, v.y, v.z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             real vd = vv[d] + g.dt * w[a] * f[d];
             real disp = (real)0.5 * g.dt * vd;
-            vd = g.a_fric * vd + sd * nr[d];
+            vd = g.a_fric * vd + kick[d];
             disp += (real)0.5 * g.dt * vd;
             p[a][d] = rel0[a][d] + disp;
         }
@@ -443,6 +441,28 @@ void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStrea
     k_integrate<real><<<(g.n_groups + 63) / 64, 64, 0, st>>>(s, g);
 }
 
+// Ornstein-Uhlenbeck kick of every atom for the current step:
+// sqrt(k_B T (1 - a^2) / m) R with R from Philox4x32-10 at counter
+// (atom, step) and Box-Muller; 0 for frozen atoms
+template <typename real>
+__global__ void k_noise(SysView<real> s, StepView<real> g)
+{
+    const int atom = blockIdx.x * blockDim.x + threadIdx.x;
+    if (atom >= s.n) return;
+    const real w = s.invm[atom];
+    real nr[3] = {(real)0, (real)0, (real)0};
+    if (w != (real)0) {
+        const unsigned long long step = s.lam->step;
+        normals3<real>(make_uint4((unsigned)atom, (unsigned)step, (unsigned)(step >> 32), 0u), g.key, nr[0], nr[1],
+                       nr[2]);
+        const real sd = sqrt(g.kT * ((real)1 - g.a_fric * g.a_fric) * w);
+        for (int d = 0; d < 3; ++d) nr[d] *= sd;
+    }
+    g.noise[3 * atom] = nr[0];
+    g.noise[3 * atom + 1] = nr[1];
+    g.noise[3 * atom + 2] = nr[2];
+}
+
 // --------------------------------------------------------- theta and OPES
 __device__ __forceinline__ double pdiff2(double a, double b)
 {
@@ -518,6 +538,33 @@ __device__ void opes_deposit(const ThetaView<real>& t, int b, double th, double 
     __syncwarp();
 }
 
+// OPES biases at the current theta and the theta integrator's normal (one
+// warp); they depend only on the state at the start of the step
+template <typename real>
+__global__ void k_theta_pre(SysView<real> s, ThetaView<real> t)
+{
+    const LamState* L = s.lam;
+    const double th = L->theta;
+    double V0, dV0, V1, dV1;
+    opes_bias(t, 0, th, V0, dV0);
+    opes_bias(t, 1, th, V1, dV1);
+    if (threadIdx.x == 0) {
+        const unsigned long long step = L->step;
+        double n0 = 0.0, n1, n2;
+        if (t.m > 0.0) normals3<double>(make_uint4(0u, (unsigned)step, (unsigned)(step >> 32), 1u), t.key, n0, n1, n2);
+        t.pre->V[0] = V0; t.pre->V[1] = V1;
+        t.pre->dV[0] = dV0; t.pre->dV[1] = dV1;
+        t.pre->noise = n0;
+    }
+}
+
+template <typename real>
+void launch_prestep(const SysView<real>& s, const StepView<real>& g, const ThetaView<real>& t, cudaStream_t st)
+{
+    k_noise<real><<<(s.n + 127) / 128, 128, 0, st>>>(s, g);
+    k_theta_pre<real><<<1, 32, 0, st>>>(s, t);
+}
+
 template <typename real>
 __global__ void k_theta(SysView<real> s, ThetaView<real> t)
 {
@@ -533,17 +580,14 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const double dUdl = L->dhA * Uuv + L->dhB * Us;
     const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub;
     const double th = L->theta;
-    double V0, dV0, V1, dV1;
-    opes_bias(t, 0, th, V0, dV0);
-    opes_bias(t, 1, th, V1, dV1);
+    const double V0 = t.pre->V[0], dV0 = t.pre->dV[0], V1 = t.pre->V[1], dV1 = t.pre->dV[1];
     const unsigned long long step = L->step;
     double thn = th, pn = L->p_theta;
     if (t.m > 0.0) {
         const double f = -L->dlam_dtheta * dUdl - dV0 - dV1;
         double v = pn / t.m + t.dt * f / t.m;
         thn = th + 0.5 * t.dt * v;
-        double n0, n1, n2;
-        normals3<double>(make_uint4(0u, (unsigned)step, (unsigned)(step >> 32), 1u), t.key, n0, n1, n2);
+        const double n0 = t.pre->noise;
         v = t.a_fric * v + sqrt(t.kT * (1.0 - t.a_fric * t.a_fric) / t.m) * n0;
         thn += 0.5 * t.dt * v;
         thn -= 2.0 * floor(thn / 2.0);
@@ -613,6 +657,8 @@ void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStrea
     template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
     template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
     template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \
+    template void launch_prestep<real>(const SysView<real>&, const StepView<real>&, const ThetaView<real>&,  \
+                                       cudaStream_t);                                                       \
     template void launch_step_end<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
 LFE_INST_DYN(float)
 LFE_INST_DYN(double)

@@ -566,6 +566,8 @@ struct System final : SystemBase {
             G.groups = upload(groups);
             G.n_groups = (int)groups.size();
         }
+        G.noise = dalloc<real>(3 * (size_t)n);
+        T.pre = dalloc<ThetaPre>(1);
         G.dt = (real)p.dt;
         G.a_fric = (real)std::exp(-p.friction * p.dt);
         G.kT = (real)(KB * p.temperature);
@@ -845,10 +847,13 @@ struct System final : SystemBase {
     // branches only meet in atomic fixed-point accumulators, so their order
     // does not change any result.  B300 runs the FP64 branches on the FP64
     // pipes while the FP32 pair and PME kernels use the FP32 pipes.
-    void eval_kernels_branched(cudaStream_t s0)
+    // the evaluation as four concurrent branches; with a theta view, the
+    // step's force-independent integrator parts run in the fourth branch
+    void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr)
     {
         CK(cudaEventRecord(ev_fork, s0));
         for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
+        if (pre) launch_prestep(S, G, *pre, br[3]);
         launch_pairs(S, N, pair_warps, br[0]);
         launch_spread(S, M, br[1]);
         if (M.planes) {
@@ -904,6 +909,7 @@ struct System final : SystemBase {
         Tc.cond = h;
         Tc.use_cond = 1;
         eval_kernels(s0);
+        launch_prestep(S, G, Tc, s0);
         launch_integrate(S, G, s0);
         launch_theta(S, Tc, s0);
         launch_step_end(S, Tc, s0);
@@ -955,7 +961,7 @@ struct System final : SystemBase {
         ThetaView<real> Tc = T;
         Tc.cond = h;
         Tc.use_cond = 1;
-        eval_kernels_branched(s0);
+        eval_kernels_branched(s0, &Tc);
         // atoms and theta move concurrently; the step ends when both are done
         CK(cudaEventRecord(ev_fork, s0));
         CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
@@ -999,6 +1005,7 @@ struct System final : SystemBase {
     void step_eager(cudaStream_t st)
     {
         eval_kernels(st);
+        launch_prestep(S, G, T, st);
         launch_integrate(S, G, st);
         launch_theta(S, T, st);
         launch_step_end(S, T, st);

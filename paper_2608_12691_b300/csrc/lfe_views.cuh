@@ -148,6 +148,15 @@ struct StepView {
     real dt, a_fric, kT;       // a = exp(-gamma dt)
     uint2 key;
     real skin_half2;
+    real* noise;               // [3 n] Ornstein-Uhlenbeck kicks of the step, formed ahead by k_noise
+};
+
+// values of the theta step that depend only on the state at its start,
+// formed while the forces are evaluated
+struct ThetaPre {
+    double V[2], dV[2];        // both OPES biases and their theta-derivatives at theta
+    double noise;              // the theta integrator's standard normal
+    double pad;
 };
 
 template <typename real>
@@ -166,6 +175,7 @@ struct ThetaView {
     double const_vv, const_uu;
     cudaGraphConditionalHandle cond;
     int use_cond;
+    ThetaPre* pre;
 };
 
 // FP64 geometry and Ewald constants of the parameter-gradient kernel
@@ -207,6 +217,11 @@ template <typename real> void planes_setup(const PmeView<real>& p);
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
 template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+// the parts of the integrators that do not depend on the step's forces (the
+// atoms' random kicks, the OPES bias at the current theta): launched
+// alongside the force evaluation
+template <typename real> void launch_prestep(const SysView<real>& s, const StepView<real>& g,
+                                             const ThetaView<real>& t, cudaStream_t st);
 template <typename real> void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
 template <typename real> void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st);
 template <typename real> void launch_eval_out(const SysView<real>& s, double* forces, double* terms,

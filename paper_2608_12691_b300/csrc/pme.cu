@@ -285,6 +285,7 @@ __device__ __forceinline__ void load_twiddles(R2<real>* dst, const R2<real>* src
 }
 
 constexpr int PLANE_THREADS = 512;
+constexpr int LOAD_BATCH = 8;     // global loads per thread issued together
 constexpr int COL_THREADS = 256;
 
 template <typename real, int MODE>
@@ -302,27 +303,49 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(PmeView<real> p)
     load_twiddles(tw2, p.tw[2], K2, sign);
     load_twiddles(tw1, p.tw[1], K1, sign);
     const int base = k0 * K1 * K2;
-    for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
-        const int k1 = e / K2, k2 = e - k1 * K2;
-        const int g = base + e;
-        R2<real> v;
-        if (MODE == PLANE_FWD_FIX) {
-            const double qv = (double)p.Qfix[g] * (1.0 / QSCALE);
-            const double qu = (double)p.Qfix[p.KK + g] * ((double)p.qu_scale / QSCALE);
-            v.x = (real)qv;
-            v.y = (real)qu;
-            p.Qfix[g] = 0;
-            p.Qfix[p.KK + g] = 0;
-            if (p.Zraw64) {
-                R2<double> w;
-                w.x = qv;
-                w.y = qu;
-                p.Zraw64[g] = w;
+    const int KP = K1 * K2;
+    // all of a thread's loads of a chunk are issued before any store, so
+    // they are in flight together
+    for (int e0 = 0; e0 < KP; e0 += LOAD_BATCH * PLANE_THREADS) {
+        long long qa[LOAD_BATCH], qb[LOAD_BATCH];
+        R2<real> zv[LOAD_BATCH];
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int e = e0 + u * PLANE_THREADS + threadIdx.x;
+            if (e < KP) {
+                if (MODE == PLANE_FWD_FIX) {
+                    qa[u] = p.Qfix[base + e];
+                    qb[u] = p.Qfix[p.KK + base + e];
+                } else {
+                    zv[u] = p.Z[base + e];
+                }
             }
-        } else {
-            v = p.Z[g];
         }
-        a[k1 * LD + k2] = v;
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int e = e0 + u * PLANE_THREADS + threadIdx.x;
+            if (e >= KP) continue;
+            const int k1 = e / K2, k2 = e - k1 * K2;
+            const int g = base + e;
+            R2<real> v;
+            if (MODE == PLANE_FWD_FIX) {
+                const double qv = (double)qa[u] * (1.0 / QSCALE);
+                const double qu = (double)qb[u] * ((double)p.qu_scale / QSCALE);
+                v.x = (real)qv;
+                v.y = (real)qu;
+                p.Qfix[g] = 0;
+                p.Qfix[p.KK + g] = 0;
+                if (p.Zraw64) {
+                    R2<double> w;
+                    w.x = qv;
+                    w.y = qu;
+                    p.Zraw64[g] = w;
+                }
+            } else {
+                v = zv[u];
+            }
+            a[k1 * LD + k2] = v;
+        }
     }
     __syncthreads();
     R2<real>* r;
@@ -362,9 +385,24 @@ __global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long l
         part[c] = p.cg_part[g0 + c];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < nc * K0; e += blockDim.x) {
-        const int k0 = e / nc, c = e - k0 * nc;
-        a[c * LD + k0] = p.Z[k0 * K12 + cols[c]];
+    for (int e0 = 0; e0 < nc * K0; e0 += LOAD_BATCH * COL_THREADS) {
+        R2<real> zv[LOAD_BATCH];
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int e = e0 + u * COL_THREADS + threadIdx.x;
+            if (e < nc * K0) {
+                const int k0 = e / nc, c = e - k0 * nc;
+                zv[u] = p.Z[k0 * K12 + cols[c]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < LOAD_BATCH; ++u) {
+            const int e = e0 + u * COL_THREADS + threadIdx.x;
+            if (e < nc * K0) {
+                const int k0 = e / nc, c = e - k0 * nc;
+                a[c * LD + k0] = zv[u];
+            }
+        }
     }
     __syncthreads();
     R2<real>* r = smem_fft<real, false>(a, b, nc, K0, LD, 1, p.rad[0], p.nrad[0], twf, +1);
