@@ -649,46 +649,44 @@ struct System final : SystemBase {
     void column_groups()
     {
         const int K1 = M.K[1], K2 = M.K[2], K12 = K1 * K2;
-        const int CW = 8;
-        std::vector<char> seen(K12, 0);
-        std::vector<int> start(1, 0), cols, part;
-        int gmax = 0;
         auto partner = [&](int c) { const int k1 = c / K2, k2 = c % K2; return ((K1 - k1) % K1) * K2 + (K2 - k2) % K2; };
-        for (int k1 = 0; k1 < K1; ++k1)
-            for (int c0 = 0; c0 < K2; c0 += CW) {
-                std::vector<int> g;
-                for (int k2 = c0; k2 < std::min(c0 + CW, K2); ++k2) {
-                    const int c = k1 * K2 + k2;
-                    if (seen[c]) continue;
-                    seen[c] = 1;
-                    g.push_back(c);
-                    const int pc = partner(c);
-                    if (!seen[pc]) { seen[pc] = 1; g.push_back(pc); }
-                }
-                if (g.empty()) continue;
-                std::sort(g.begin(), g.end());
-                for (int c : g) {
-                    cols.push_back(c);
-                    part.push_back((int)(std::lower_bound(g.begin(), g.end(), partner(c)) - g.begin()));
-                }
-                start.push_back((int)cols.size());
-                gmax = std::max(gmax, (int)g.size());
-            }
-        const int* d_start = upload(start);
-        const int* d_cols = upload(cols);
-        const int* d_part = upload(part);
         int optin = 0;
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
-        auto setv = [&](auto& V) {
+        // CW consecutive columns per chunk: 8 in FP32; 4 in FP64, whose
+        // scarce units want more, smaller blocks
+        auto build = [&](auto& V, int CW) {
+            std::vector<char> seen(K12, 0);
+            std::vector<int> start(1, 0), cols, part;
+            int gmax = 0;
+            for (int k1 = 0; k1 < K1; ++k1)
+                for (int c0 = 0; c0 < K2; c0 += CW) {
+                    std::vector<int> g;
+                    for (int k2 = c0; k2 < std::min(c0 + CW, K2); ++k2) {
+                        const int c = k1 * K2 + k2;
+                        if (seen[c]) continue;
+                        seen[c] = 1;
+                        g.push_back(c);
+                        const int pc = partner(c);
+                        if (!seen[pc]) { seen[pc] = 1; g.push_back(pc); }
+                    }
+                    if (g.empty()) continue;
+                    std::sort(g.begin(), g.end());
+                    for (int c : g) {
+                        cols.push_back(c);
+                        part.push_back((int)(std::lower_bound(g.begin(), g.end(), partner(c)) - g.begin()));
+                    }
+                    start.push_back((int)cols.size());
+                    gmax = std::max(gmax, (int)g.size());
+                }
             V.ngroups = (int)start.size() - 1;
             V.cg_max = gmax;
-            V.cg_start = d_start;
-            V.cg_col = d_cols;
-            V.cg_part = d_part;
+            V.cg_start = upload(start);
+            V.cg_col = upload(cols);
+            V.cg_part = upload(part);
             V.planes = (planes_smem(V) + 1024 <= (size_t)optin && columns_smem(V) + 1024 <= (size_t)optin) ? 1 : 0;
         };
-        setv(M);
-        if (dual) setv(M64);
+        build(M, sizeof(real) == 8 ? 4 : 8);
+        if (dual) build(M64, 4);
         if (dual && !M64.planes) M.planes = 0;   // both branches use one transform layout
         if (M.planes) {
             planes_setup(M);

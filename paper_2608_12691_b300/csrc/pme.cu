@@ -15,39 +15,62 @@
 
 namespace lfe {
 
+// Four lanes per atom: lanes 0-2 of the group form the FP64 B-spline
+// weights of one dimension each and share them by shuffles; lane j0 then
+// spreads the 16 points of plane j0 of the atom's 4 x 4 x 4 stencil.  The
+// products are formed in the same order as by one lane per atom.  Weights
+// and products in FP64: the fixed-point grid is shared by the force branch
+// and the FP64 energy branch, whose class energies set dU/dlambda to 1e-6
+// relative.
 template <typename real>
 __global__ void k_spread(SysView<real> s, PmeView<real> p)
 {
-    int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= s.n_pad) return;
-    int a = s.perm[slot];
-    if (a < 0) return;
-    const R4<real> xq = s.xq[slot];
-    const real q = s.q[a];
-    if (q == (real)0) return;
-    long long* grid = p.Qfix + (s.sol[a] ? p.KK : 0);
-    // weights and products in FP64: the fixed-point grid is shared by the
-    // force branch and the FP64 energy branch, whose class energies set
-    // dU/dlambda to 1e-6 relative
-    double th[3][4], dth[4];
-    int f[3];
-    real xs[3] = {xq.x, xq.y, xq.z};
-    for (int d = 0; d < 3; ++d) {
-        double w;
-        grid_coord(xs[d], p.kscale64[d], p.K[d], f[d], w);
-        bspline4(w, th[d], dth);
+    const unsigned FULL = 0xffffffffu;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int slot = tid >> 2, sub = tid & 3;
+    const int lb = (threadIdx.x & 31) & ~3;
+    int a = -1;
+    real q = 0;
+    R4<real> xq;
+    xq.x = xq.y = xq.z = xq.w = (real)0;
+    if (slot < s.n_pad) {
+        a = s.perm[slot];
+        if (a >= 0) {
+            xq = s.xq[slot];
+            q = s.q[a];
+        }
     }
-    for (int j0 = 0; j0 < 4; ++j0) {
-        const int k0 = wrapk(f[0] - j0, p.K[0]);
-        const double a0 = (double)q * th[0][j0];
-        for (int j1 = 0; j1 < 4; ++j1) {
-            const int k1 = wrapk(f[1] - j1, p.K[1]);
-            const double a1 = a0 * th[1][j1];
-            const int row = (k0 * p.K[1] + k1) * p.K[2];
-            for (int j2 = 0; j2 < 4; ++j2) {
-                const int k2 = wrapk(f[2] - j2, p.K[2]);
-                atomic_add_ll(&grid[row + k2], __double2ll_rn(a1 * th[2][j2] * QSCALE));
-            }
+    double th[4], dth[4];
+    int f;
+    {
+        const int d = sub < 3 ? sub : 2;
+        const real x = d == 0 ? xq.x : (d == 1 ? xq.y : xq.z);
+        double w;
+        grid_coord(x, p.kscale64[d], p.K[d], f, w);
+        bspline4(w, th, dth);
+    }
+    double t0[4], t1[4], t2[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        t0[k] = __shfl_sync(FULL, th[k], lb);
+        t1[k] = __shfl_sync(FULL, th[k], lb + 1);
+        t2[k] = __shfl_sync(FULL, th[k], lb + 2);
+    }
+    const int f0 = __shfl_sync(FULL, f, lb), f1 = __shfl_sync(FULL, f, lb + 1), f2 = __shfl_sync(FULL, f, lb + 2);
+    if (a < 0 || q == (real)0) return;
+    long long* grid = p.Qfix + (s.sol[a] ? p.KK : 0);
+    const double th0 = sub == 0 ? t0[0] : (sub == 1 ? t0[1] : (sub == 2 ? t0[2] : t0[3]));
+    const int k0 = wrapk(f0 - sub, p.K[0]);
+    const double a0 = (double)q * th0;
+#pragma unroll
+    for (int j1 = 0; j1 < 4; ++j1) {
+        const int k1 = wrapk(f1 - j1, p.K[1]);
+        const double a1 = a0 * t1[j1];
+        const int row = (k0 * p.K[1] + k1) * p.K[2];
+#pragma unroll
+        for (int j2 = 0; j2 < 4; ++j2) {
+            const int k2 = wrapk(f2 - j2, p.K[2]);
+            atomic_add_ll(&grid[row + k2], __double2ll_rn(a1 * t2[j2] * QSCALE));
         }
     }
 }
@@ -172,14 +195,14 @@ __device__ R2<real>* smem_fft(R2<real>* a, R2<real>* b, int nl, int K, int ls, i
     return a;
 }
 
-constexpr int FFT_NL = 16;    // lines per block
 
 // One pass of 1-D transforms of length K along AXIS for a block of FFT_NL
+// (16 in FP32, 4 in FP64, whose scarce units want more blocks in flight)
 // lines, in shared memory, by the Stockham autosort formulation (radix 2, 3,
 // 4, 5 stages).  AXIS 2 lines are contiguous; AXIS 1 and 0 lines are loaded
 // as FFT_NL contiguous columns.  FROMFIX: the input is the pair of
 // fixed-point charge grids (consumed and zeroed here).
-template <typename real, int AXIS, bool FROMFIX>
+template <typename real, int AXIS, bool FROMFIX, int FFT_NL>
 __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -250,18 +273,20 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
 template <typename real>
 void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
 {
+    constexpr int NL = sizeof(real) == 8 ? 4 : 16;
+    const int threads = 16 * NL;
     const int K = p.K[axis];
-    const size_t smem = sizeof(R2<real>) * (size_t)(K + 2 * FFT_NL * (K + 1));
+    const size_t smem = sizeof(R2<real>) * (size_t)(K + 2 * NL * (K + 1));
     int blocks;
-    if (axis == 2) blocks = (p.K[0] * p.K[1] + FFT_NL - 1) / FFT_NL;
-    else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + FFT_NL - 1) / FFT_NL);
+    if (axis == 2) blocks = (p.K[0] * p.K[1] + NL - 1) / NL;
+    else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + NL - 1) / NL);
     if (axis == 2) {
-        if (from_fixed) k_fft<real, 2, true><<<blocks, 256, smem, st>>>(p, sign);
-        else k_fft<real, 2, false><<<blocks, 256, smem, st>>>(p, sign);
+        if (from_fixed) k_fft<real, 2, true, NL><<<blocks, threads, smem, st>>>(p, sign);
+        else k_fft<real, 2, false, NL><<<blocks, threads, smem, st>>>(p, sign);
     } else if (axis == 1) {
-        k_fft<real, 1, false><<<blocks, 256, smem, st>>>(p, sign);
+        k_fft<real, 1, false, NL><<<blocks, threads, smem, st>>>(p, sign);
     } else {
-        k_fft<real, 0, false><<<blocks, 256, smem, st>>>(p, sign);
+        k_fft<real, 0, false, NL><<<blocks, threads, smem, st>>>(p, sign);
     }
 }
 
@@ -644,7 +669,7 @@ __global__ void k_gather(SysView<real> s, PmeView<real> p)
 template <typename real>
 void launch_spread(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st)
 {
-    k_spread<real><<<(s.n_pad + 127) / 128, 128, 0, st>>>(s, p);
+    k_spread<real><<<(4 * s.n_pad + 127) / 128, 128, 0, st>>>(s, p);
 }
 template <typename real>
 void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode, cudaStream_t st)
