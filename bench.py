@@ -291,7 +291,13 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     ns_day = dt_ps * 1e-3 * 86400.0 / (ms_step * 1e-3) * world
     rebuilds = int(ext1["n_rebuilds"] - ext0["n_rebuilds"])
-    launches = args.steps * 14 + rebuilds * 9
+    # kernels of one captured step (FP32 systems): pair kernel; spread, plane
+    # transform, column pass, inverse plane transform, gather; FP64 energy
+    # branch (two transform passes, column pass); FP64 uv energies,
+    # exclusions/1-4, bonded; kicks and OPES bias; integrator, theta, step
+    # end.  A neighbour-list build adds 15 kernels.
+    per_step = 17 if prec == lfe.LFE_FP32_MIXED else 14
+    launches = args.steps * per_step + rebuilds * 15
 
     out = None
     if rank == 0:

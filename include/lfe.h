@@ -138,7 +138,13 @@ typedef struct {
  * failure (the message is then available from lfe_last_error(NULL)). */
 int lfe_create(const lfe_params* params, const lfe_topology* topo, lfe_system** out);
 
-/* Replace positions ([3N], host or device).  Rebuilds the neighbour list. */
+/* Replace positions ([3N] doubles, host or device, caller order).  Host
+ * positions are checked (non-finite: LFE_ERR_ARG, nothing changed).  The
+ * neighbour list is rebuilt on the device when an atom lies more than skin/2
+ * from where the list was built; otherwise it is kept (it stays valid).  The
+ * call returns after queueing the work on `stream` (host input is copied
+ * before it returns); a capacity overflow in that rebuild is settled by the
+ * next call that synchronises (lfe_eval, lfe_param_grad, lfe_get_state). */
 int lfe_set_positions(lfe_system* sys, const double* pos, int on_device, void* stream);
 
 /* Replace velocities ([3N], host). */

@@ -12,14 +12,16 @@ __device__ __forceinline__ real minimg(real d, real L, real invL)
 }
 __device__ __forceinline__ float minimg(float d, float L, float invL) { return d - L * rintf(d * invL); }
 
-// wrap one coordinate into [0, L) (the sorted copy used by the pair and PME kernels)
+// One coordinate of the cluster-sorted copy used by the pair and PME
+// kernels: the wrapped position at the last list build plus the (minimum-
+// image) displacement since.  It is not re-wrapped between builds: the
+// periodic shift stored with each tile refers to the images of the build, so
+// an atom that crosses a box face must keep a continuous coordinate (it may
+// leave [0, L) by at most skin/2 before the next build).
 template <typename real>
-__device__ __forceinline__ real wrap_sorted(real x, real L, real invL)
+__device__ __forceinline__ real sorted_coord(real x, real xref, real L, real invL)
 {
-    real o = x - L * floor(x * invL);
-    if (o >= L) o -= L;
-    if (o < (real)0) o = (real)0;
-    return o;
+    return wrap_box(xref, L, invL) + minimg(x - xref, L, invL);
 }
 
 template <typename real>
@@ -120,11 +122,11 @@ __global__ void k_refresh_sorted(SysView<real> s)
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= s.n) return;
     const int slot = s.iperm[a];
-    const R4<real> x = s.x[a];
+    const R4<real> x = s.x[a], xr = s.xref[a];
     R4<real> o = s.xq[slot];
-    o.x = wrap_sorted(x.x, s.L[0], s.invL[0]);
-    o.y = wrap_sorted(x.y, s.L[1], s.invL[1]);
-    o.z = wrap_sorted(x.z, s.L[2], s.invL[2]);
+    o.x = sorted_coord(x.x, xr.x, s.L[0], s.invL[0]);
+    o.y = sorted_coord(x.y, xr.y, s.L[1], s.invL[1]);
+    o.z = sorted_coord(x.z, xr.z, s.L[2], s.invL[2]);
     s.xq[slot] = o;
 }
 
@@ -132,6 +134,75 @@ template <typename real>
 void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st)
 {
     k_refresh_sorted<real><<<(s.n + 255) / 256, 256, 0, st>>>(s);
+}
+
+// after new positions: refresh the sorted copy and raise the rebuild flag
+// when an atom lies more than skin/2 from where the list was built
+template <typename real>
+__global__ void k_moved(SysView<real> s, real skin_half2)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    bool far = false;
+    if (a < s.n) {
+        const int slot = s.iperm[a];
+        const R4<real> x = s.x[a];
+        const R4<real> xr = s.xref[a];
+        R4<real> o = s.xq[slot];
+        o.x = sorted_coord(x.x, xr.x, s.L[0], s.invL[0]);
+        o.y = sorted_coord(x.y, xr.y, s.L[1], s.invL[1]);
+        o.z = sorted_coord(x.z, xr.z, s.L[2], s.invL[2]);
+        s.xq[slot] = o;
+        const real dx = minimg(x.x - xr.x, s.L[0], s.invL[0]);
+        const real dy = minimg(x.y - xr.y, s.L[1], s.invL[1]);
+        const real dz = minimg(x.z - xr.z, s.L[2], s.invL[2]);
+        far = !(dx * dx + dy * dy + dz * dz <= skin_half2);   // also true for a non-finite position
+    }
+    if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_REBUILD], 1);
+}
+
+// positions, velocities (caller order, doubles) and the scalar state in one
+// buffer, so that lfe_get_state needs one copy: out[0, 3n) x, [3n, 6n) v,
+// then theta, p_theta, lambda, dU/dlambda, U, kernels of both biases, step,
+// rebuilds, the error bits, the tile count
+template <typename real>
+__global__ void k_pack_state(SysView<real> s, const OpesState* o, double* out)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < s.n) {
+        const R4<real> x = s.x[a], v = s.v[a];
+        out[3 * a] = x.x; out[3 * a + 1] = x.y; out[3 * a + 2] = x.z;
+        double* ov = out + 3 * (size_t)s.n;
+        ov[3 * a] = v.x; ov[3 * a + 1] = v.y; ov[3 * a + 2] = v.z;
+    }
+    if (a == 0) {
+        const LamState* L = s.lam;
+        double* e = out + 6 * (size_t)s.n;
+        e[0] = L->theta; e[1] = L->p_theta; e[2] = L->lambda; e[3] = L->dUdl; e[4] = L->U;
+        e[5] = o->n[0]; e[6] = o->n[1]; e[7] = (double)L->step;
+        e[8] = s.flags[FL_NREBUILD]; e[9] = s.flags[FL_ERROR]; e[10] = s.flags[FL_NTILES];
+    }
+}
+
+template <typename real>
+void launch_pack_state(const SysView<real>& s, const OpesState* o, double* out, cudaStream_t st)
+{
+    k_pack_state<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, o, out);
+}
+
+// the conditional rebuild node of a captured graph follows the rebuild flag
+template <typename real>
+__global__ void k_cond_rebuild(SysView<real> s, cudaGraphConditionalHandle h)
+{
+    const int rb = s.flags[FL_REBUILD];
+    cudaGraphSetConditional(h, rb ? 1u : 0u);
+    s.flags[FL_REBUILD] = 0;
+}
+
+template <typename real>
+void launch_moved(const SysView<real>& s, real skin_half2, cudaGraphConditionalHandle h, cudaStream_t st)
+{
+    k_moved<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, skin_half2);
+    k_cond_rebuild<real><<<1, 1, 0, st>>>(s, h);
 }
 
 // ---------------------------------------------------------------- bonded
@@ -392,12 +463,12 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
         if (!isfinite(xnew.x) || !isfinite(xnew.y) || !isfinite(xnew.z)) bad = true;
         s.x[atom] = xnew;
         s.v[atom] = vnew;
-        R4<real> o = s.xq[slot[a]];
-        o.x = wrap_sorted(xnew.x, s.L[0], s.invL[0]);
-        o.y = wrap_sorted(xnew.y, s.L[1], s.invL[1]);
-        o.z = wrap_sorted(xnew.z, s.L[2], s.invL[2]);
-        s.xq[slot[a]] = o;
         const R4<real> xr = s.xref[atom];
+        R4<real> o = s.xq[slot[a]];
+        o.x = sorted_coord(xnew.x, xr.x, s.L[0], s.invL[0]);
+        o.y = sorted_coord(xnew.y, xr.y, s.L[1], s.invL[1]);
+        o.z = sorted_coord(xnew.z, xr.z, s.L[2], s.invL[2]);
+        s.xq[slot[a]] = o;
         const real dx = minimg(xnew.x - xr.x, s.L[0], s.invL[0]);
         const real dy = minimg(xnew.y - xr.y, s.L[1], s.invL[1]);
         const real dz = minimg(xnew.z - xr.z, s.L[2], s.invL[2]);
@@ -654,6 +725,8 @@ void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStrea
                                         cudaStream_t);                                                    \
     template void launch_assign_positions<real>(const SysView<real>&, const double*, cudaStream_t);        \
     template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
+    template void launch_moved<real>(const SysView<real>&, real, cudaGraphConditionalHandle, cudaStream_t); \
+    template void launch_pack_state<real>(const SysView<real>&, const OpesState*, double*, cudaStream_t);   \
     template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
     template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
     template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \

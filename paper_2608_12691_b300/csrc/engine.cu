@@ -164,8 +164,11 @@ struct System final : SystemBase {
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        if (pos_exec) cudaGraphExecDestroy(pos_exec);
+        if (pos_graph) cudaGraphDestroy(pos_graph);
         for (void* p : allocs) cudaFree(p);
         if (h_flags) cudaFreeHost(h_flags);
+        if (h_state) cudaFreeHost(h_state);
         if (cs) cudaStreamDestroy(cs);
         if (cs2) cudaStreamDestroy(cs2);
         for (int k = 0; k < 4; ++k) {
@@ -766,17 +769,75 @@ struct System final : SystemBase {
         CK(cudaGetLastError());
     }
 
+    // New positions go through a small captured graph: assign, refresh the
+    // sorted copy, and rebuild the neighbour list only when an atom lies more
+    // than skin/2 from where the list was built (a device-side decision, so
+    // the call does not wait for the device).  A capacity overflow in that
+    // rebuild is settled by the next call that synchronises.
+    cudaGraph_t pos_graph = nullptr;
+    cudaGraphExec_t pos_exec = nullptr;
+    unsigned pos_gen = ~0u;
+    bool pos_pending = false;
+
+    void capture_pos_graph()
+    {
+        if (pos_exec) { cudaGraphExecDestroy(pos_exec); pos_exec = nullptr; }
+        if (pos_graph) { cudaGraphDestroy(pos_graph); pos_graph = nullptr; }
+        cudaStream_t s0 = cs;
+        CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        launch_assign_positions(S, d_pos, s0);
+        launch_moved(S, G.skin_half2, h, s0);
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_build_nbl(S, N, cs2);
+        cudaGraph_t body_out = nullptr;
+        CK(cudaStreamEndCapture(cs2, &body_out));
+        CK(cudaStreamEndCapture(s0, &pos_graph));
+        CK(cudaGraphInstantiate(&pos_exec, pos_graph, 0));
+        pos_gen = generation;
+    }
+
+    // after set_positions: a rebuild that ran out of tile capacity is redone
+    // with more capacity (synchronises)
+    void settle_positions(cudaStream_t st)
+    {
+        if (!pos_pending) return;
+        pos_pending = false;
+        CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (h_flags[FL_ERROR] & ERRB_OVERFLOW) {
+            int clr[2] = {0, 0};
+            CK(cudaMemcpy(S.flags, clr, sizeof(clr), cudaMemcpyHostToDevice));
+            grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2);
+            build_neighbors(st);
+        }
+    }
+
     void set_positions(const double* pos, int on_device, cudaStream_t st) override
     {
         if (!pos) fail(LFE_ERR_ARG, "pos is NULL");
-        if (!on_device) {
-            if (!finite_all(pos, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
-            CK(cudaMemcpyAsync(d_pos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-            launch_assign_positions(S, d_pos, st);
-        } else {
-            launch_assign_positions(S, pos, st);
-        }
-        build_neighbors(st);
+        if (!on_device && !finite_all(pos, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
+        CK(cudaMemcpyAsync(d_pos, pos, sizeof(double) * 3 * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           st));
+        if (!pos_exec || pos_gen != generation) capture_pos_graph();
+        CK(cudaGraphLaunch(pos_exec, st));
+        pos_pending = true;
     }
 
     void set_integrator(double dt, double friction, double temperature) override
@@ -820,6 +881,7 @@ struct System final : SystemBase {
     void eval(double lam, double* forces, double* terms, int out_on_device, cudaStream_t st) override
     {
         if (!(lam >= 0.0 && lam <= 1.0)) fail(LFE_ERR_ARG, "lambda must be in [0, 1]");
+        settle_positions(st);
         if (exec) recover_overflow(st);
         // the dynamics' lambda state is saved and put back: an evaluation at
         // an arbitrary lambda does not move theta
@@ -1058,33 +1120,39 @@ struct System final : SystemBase {
         fail(LFE_ERR_OVERFLOW, "neighbour-list capacity kept overflowing");
     }
 
+    // one packing kernel and one copy into pinned memory; the rare overflow
+    // and error cases are handled after it (and the state packed again)
+    double* d_state = nullptr;     // [6n + 16]
+    double* h_state = nullptr;     // pinned copy
+
     void get_state(double* pos, double* vel, double* ext) override
     {
+        if (!d_state) {
+            d_state = dalloc<double>(6 * (size_t)n + 16);
+            CK(cudaMallocHost(&h_state, sizeof(double) * (6 * (size_t)n + 16)));
+        }
         CK(cudaDeviceSynchronize());
-        if (exec) recover_overflow(nullptr);
-        check_flags(nullptr);
-        if (pos || vel) {
-            std::vector<R4<real>> hx(n);
-            if (pos) {
-                CK(cudaMemcpy(hx.data(), S.x, sizeof(R4<real>) * n, cudaMemcpyDeviceToHost));
-                for (int i = 0; i < n; ++i) { pos[3 * i] = hx[i].x; pos[3 * i + 1] = hx[i].y; pos[3 * i + 2] = hx[i].z; }
+        const size_t bytes = sizeof(double) * (6 * (size_t)n + 16);
+        for (int pass = 0; pass < 2; ++pass) {
+            launch_pack_state(S, T.st, d_state, nullptr);
+            CK(cudaMemcpyAsync(h_state, d_state, bytes, cudaMemcpyDeviceToHost, nullptr));
+            CK(cudaStreamSynchronize(nullptr));
+            const int err = (int)h_state[6 * (size_t)n + 9];
+            if (!err) break;
+            if (pass == 1 || !(err & ERRB_OVERFLOW)) {
+                check_flags(nullptr);   // reports the error (clears the bit)
+                break;
             }
-            if (vel) {
-                CK(cudaMemcpy(hx.data(), S.v, sizeof(R4<real>) * n, cudaMemcpyDeviceToHost));
-                for (int i = 0; i < n; ++i) { vel[3 * i] = hx[i].x; vel[3 * i + 1] = hx[i].y; vel[3 * i + 2] = hx[i].z; }
-            }
+            // a neighbour list that ran out of capacity: queued steps replay
+            if (exec) recover_overflow(nullptr);
+            if (pos_pending) settle_positions(nullptr);
         }
-        if (ext) {
-            LamState L;
-            OpesState O;
-            CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
-            CK(cudaMemcpy(&O, T.st, sizeof(O), cudaMemcpyDeviceToHost));
-            ext[0] = L.theta; ext[1] = L.p_theta; ext[2] = L.lambda; ext[3] = L.dUdl; ext[4] = L.U;
-            ext[5] = O.n[0]; ext[6] = O.n[1]; ext[7] = (double)L.step;
-            int nreb = 0;
-            CK(cudaMemcpy(&nreb, S.flags + FL_NREBUILD, sizeof(int), cudaMemcpyDeviceToHost));
-            ext[8] = nreb;
-        }
+        pos_pending = false;
+        const double* e = h_state + 6 * (size_t)n;
+        if (pos) std::memcpy(pos, h_state, sizeof(double) * 3 * n);
+        if (vel) std::memcpy(vel, h_state + 3 * (size_t)n, sizeof(double) * 3 * n);
+        if (ext)
+            for (int k = 0; k < LFE_NEXT; ++k) ext[k] = e[k];
     }
 
     // checkpoint layout: header | x | v | xref | LamState | OpesState | centre | weight | S | checksum
@@ -1282,6 +1350,7 @@ struct System final : SystemBase {
     {
         if (!(lam >= 0.0 && lam <= 1.0)) fail(LFE_ERR_ARG, "lambda must be in [0, 1]");
         if (n_u == 0) fail(LFE_ERR_ARG, "the system has no solute atoms");
+        settle_positions(st);
         if (exec) recover_overflow(st);
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
         launch_set_lambda(S, lam, st);

@@ -36,6 +36,20 @@ enum {
 enum { FL_REBUILD = 0, FL_ERROR = 1, FL_NTILES = 2, FL_NREBUILD = 3, FL_NUV = 4, FL_N = 8 };
 enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4 };
 
+// one coordinate wrapped into [0, L) (the positions the neighbour list is
+// built from)
+__device__ __forceinline__ float floor_w(float x) { return floorf(x); }
+__device__ __forceinline__ double floor_w(double x) { return floor(x); }
+template <typename real>
+__device__ __forceinline__ real wrap_box(real x, real L, real invL)
+{
+    real w = x - L * floor_w(x * invL);
+    if (w >= L) w -= L;
+    if (w < (real)0) w += L;
+    if (w >= L) w = (real)0;
+    return w;
+}
+
 // lambda state, written on the device (by lfe_eval's setter or by the theta
 // integrator) and read by every kernel that depends on lambda.
 struct LamState {

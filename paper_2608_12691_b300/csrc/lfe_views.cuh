@@ -229,6 +229,12 @@ template <typename real> void launch_eval_out(const SysView<real>& s, double* fo
                                               cudaStream_t st);
 template <typename real> void launch_assign_positions(const SysView<real>& s, const double* pos, cudaStream_t st);
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
+// refresh the sorted copy after new positions and set conditional h to
+// "rebuild" when an atom has moved more than skin/2 since the last build
+template <typename real> void launch_pack_state(const SysView<real>& s, const OpesState* o, double* out,
+                                                cudaStream_t st);
+template <typename real> void launch_moved(const SysView<real>& s, real skin_half2, cudaGraphConditionalHandle h,
+                                           cudaStream_t st);
 // phi: FP64 grid of the class potentials (phi_v real, phi_u imaginary)
 template <typename real> void launch_param_grad(const SysView<real>& s, const NblView<real>& nb,
                                                 const ExclView<real>& ex, const PmeView<real>& pm,

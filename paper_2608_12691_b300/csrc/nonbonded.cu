@@ -27,15 +27,6 @@ __device__ __forceinline__ double floor_(double x) { return floor(x); }
 __device__ __forceinline__ float rint_(float x) { return rintf(x); }
 __device__ __forceinline__ double rint_(double x) { return rint(x); }
 
-template <typename real>
-__device__ __forceinline__ real wrap_coord(real x, real L, real invL)
-{
-    real w = x - L * floor_(x * invL);
-    if (w >= L) w -= L;
-    if (w < (real)0) w += L;
-    if (w >= L) w = (real)0;
-    return w;
-}
 
 __device__ __forceinline__ unsigned spread_bits(unsigned v)
 {
@@ -58,8 +49,8 @@ __global__ void k_col_keys(SysView<real> s, NblView<real> nb)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_solv) return;
     const R4<real> p = s.x[s.solv_list[i]];
-    const real wx = wrap_coord(p.x, s.L[0], s.invL[0]);
-    const real wy = wrap_coord(p.y, s.L[1], s.invL[1]);
+    const real wx = wrap_box(p.x, s.L[0], s.invL[0]);
+    const real wy = wrap_box(p.y, s.L[1], s.invL[1]);
     int cx = (int)(wx * nb.cinvx), cy = (int)(wy * nb.cinvy);
     cx = cx < 0 ? 0 : (cx >= nb.ncx ? nb.ncx - 1 : cx);
     cy = cy < 0 ? 0 : (cy >= nb.ncy ? nb.ncy - 1 : cy);
@@ -165,7 +156,7 @@ __global__ void __launch_bounds__(256) k_col_sort(SysView<real> s, NblView<real>
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         const int a = nb.tmp[b + k];
         ids[k] = a;
-        zs[k] = (float)wrap_coord(s.x[a].z, s.L[2], s.invL[2]);
+        zs[k] = (float)wrap_box(s.x[a].z, s.L[2], s.invL[2]);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
@@ -217,9 +208,9 @@ __global__ void k_assign(SysView<real> s, NblView<real> nb)
         s.iperm[a] = slot;
         const R4<real> p = s.x[a];
         s.xref[a] = p;
-        o.x = wrap_coord(p.x, s.L[0], s.invL[0]);
-        o.y = wrap_coord(p.y, s.L[1], s.invL[1]);
-        o.z = wrap_coord(p.z, s.L[2], s.invL[2]);
+        o.x = wrap_box(p.x, s.L[0], s.invL[0]);
+        o.y = wrap_box(p.y, s.L[1], s.invL[1]);
+        o.z = wrap_box(p.z, s.L[2], s.invL[2]);
         o.w = s.q[a] * (real)sqrt(KE);
         l.x = (real)0.5 * s.sig[a];
         l.y = (real)2 * sqrt(s.eps[a]);

@@ -166,6 +166,7 @@ def test_set_solute_params_equals_creating_with_them(precision):
     a = lfe.System(d0, precision=precision)
     a.step(2)                       # a captured graph exists before the change
     a.set_positions(d0["pos"])
+    a.build_neighbors()             # the same list as a fresh build at these positions
     a.set_velocities(np.zeros_like(d0["pos"]))
     a.set_solute_params(q[sol], sig[sol], eps[sol])
     b = lfe.System(d1, precision=precision)

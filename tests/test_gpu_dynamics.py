@@ -104,3 +104,29 @@ def test_checkpoint_resume_is_bitwise(tmp_path):
     (tmp_path / "bad.bin").write_bytes(bytes(raw))
     with pytest.raises(lfe.LfeError):
         b.restore(tmp_path / "bad.bin")
+
+
+@pytest.mark.parametrize("precision", [lfe.LFE_FP64, lfe.LFE_FP32_MIXED])
+def test_forces_stay_exact_when_atoms_cross_the_box_between_builds(precision):
+    # every atom moves 0.03 nm (< skin/2, so the list is kept) and the
+    # positions are re-wrapped into the box, so the atoms next to the faces
+    # jump by a box length; then a few steps follow.  The forces must stay
+    # those of the oracle at the same positions.
+    d = water_system()
+    g = lfe.System(d, precision=precision, seed=SEED)
+    box = d["box"]
+    moved = S.f32(d["pos"] + np.array([0.03, -0.03, 0.03]))
+    wrapped = S.f32(moved - box * np.floor(moved / box))
+    wrapped[wrapped >= box] = 0.0
+    assert np.any(np.floor(moved / box) != 0), "no atom crossed a face"
+    g.set_positions(wrapped)
+    lam = 0.45
+    tol = 1e-9 if precision == lfe.LFE_FP64 else 1e-5
+    t, F = g.eval(lam)
+    o = R.evaluate(d, lam, level=2, pos=wrapped)
+    assert np.linalg.norm(F - o["F"]) / np.linalg.norm(o["F"]) <= tol
+    g.step(5)
+    pos, _, _ = g.get_state()
+    t, F = g.eval(lam)
+    o = R.evaluate(d, lam, level=2, pos=pos)
+    assert np.linalg.norm(F - o["F"]) / np.linalg.norm(o["F"]) <= tol

@@ -146,6 +146,26 @@ def test_bad_inputs_are_rejected_and_system_survives():
     assert e.value.code == lfe.LFE_ERR_ARG
 
 
+def test_set_positions_far_move_rebuilds_on_device():
+    # positions of another configuration of the same topology: every atom
+    # moves far beyond skin/2, so the list is rebuilt inside the call
+    d = SYSTEMS["ragged"]()
+    g = lfe.System(d)
+    rng = np.random.default_rng(3)
+    perm_pos = d["pos"].copy()
+    shift = S.f32(rng.uniform(0.2, 0.4, size=3))
+    perm_pos = S.f32(perm_pos + shift)
+    perm_pos = S.f32(perm_pos - d["box"] * np.floor(perm_pos / d["box"]))
+    perm_pos[perm_pos >= d["box"]] = 0.0
+    for pos in (perm_pos, d["pos"]):
+        g.set_positions(pos)
+        t, F = g.eval(0.7)
+        E, F0, Fuv, Fs = R.nonbonded(dict(d, pos=pos), level=2)
+        hA, hB, _, _ = R.switching(0.7)
+        Fo = F0 + hA * Fuv + hB * Fs
+        assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) < 1e-5
+
+
 def test_set_positions_roundtrip():
     d = SYSTEMS["ragged"]()
     g = lfe.System(d)
