@@ -339,35 +339,52 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
     real p[NA][3];
     real w[NA];
     int slot[NA];
-    {
-        const R4<real> x0 = s.x[G.atom[0]];
-        o0[0] = x0.x; o0[1] = x0.y; o0[2] = x0.z;
-    }
+    // every load of the group is issued before any store (the stores that
+    // clear the forces would otherwise order the next atom's loads after
+    // them), in two dependent rounds: indices and per-atom records, then the
+    // slot-indexed forces and sorted records
+    R4<real> xa4[NA], va4[NA], xr4[NA], xq4[NA];
+    real kick[NA][3];
+    long long fl[NA][3];
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const int atom = G.atom[a];
         slot[a] = s.iperm[atom];
-        const real f[3] = {(real)((double)s.F[slot[a]] * (1.0 / FSCALE)),
-                           (real)((double)s.F[s.n_pad + slot[a]] * (1.0 / FSCALE)),
-                           (real)((double)s.F[2 * s.n_pad + slot[a]] * (1.0 / FSCALE))};
-        s.F[slot[a]] = 0; s.F[s.n_pad + slot[a]] = 0; s.F[2 * s.n_pad + slot[a]] = 0;
-        const R4<real> x = s.x[atom], v = s.v[atom];
-        const real xa[3] = {x.x, x.y, x.z};
+        xa4[a] = s.x[atom];
+        va4[a] = s.v[atom];
+        xr4[a] = s.xref[atom];
+        w[a] = s.invm[atom];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) kick[a][d] = g.noise[3 * atom + d];
+    }
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) fl[a][d] = s.F[(size_t)d * s.n_pad + slot[a]];
+        xq4[a] = s.xq[slot[a]];
+    }
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) s.F[(size_t)d * s.n_pad + slot[a]] = 0;
+    o0[0] = xa4[0].x; o0[1] = xa4[0].y; o0[2] = xa4[0].z;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const real xa[3] = {xa4[a].x, xa4[a].y, xa4[a].z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) rel0[a][d] = a == 0 ? (real)0 : minimg(xa[d] - o0[d], s.L[d], s.invL[d]);
-        w[a] = s.invm[atom];
         if (w[a] == (real)0) {
 #pragma unroll
             for (int d = 0; d < 3; ++d) p[a][d] = rel0[a][d];
             continue;
         }
-        const real kick[3] = {g.noise[3 * atom], g.noise[3 * atom + 1], g.noise[3 * atom + 2]};
-        const real vv[3] = {v.x, v.y, v.z};
+        const real vv[3] = {va4[a].x, va4[a].y, va4[a].z};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            real vd = vv[d] + g.dt * w[a] * f[d];
+            const real f = (real)((double)fl[a][d] * (1.0 / FSCALE));
+            real vd = vv[d] + g.dt * w[a] * f;
             real disp = (real)0.5 * g.dt * vd;
-            vd = g.a_fric * vd + kick[d];
+            vd = g.a_fric * vd + kick[a][d];
             disp += (real)0.5 * g.dt * vd;
             p[a][d] = rel0[a][d] + disp;
         }
@@ -463,8 +480,8 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
         if (!isfinite(xnew.x) || !isfinite(xnew.y) || !isfinite(xnew.z)) bad = true;
         s.x[atom] = xnew;
         s.v[atom] = vnew;
-        const R4<real> xr = s.xref[atom];
-        R4<real> o = s.xq[slot[a]];
+        const R4<real> xr = xr4[a];
+        R4<real> o = xq4[a];
         o.x = sorted_coord(xnew.x, xr.x, s.L[0], s.invL[0]);
         o.y = sorted_coord(xnew.y, xr.y, s.L[1], s.invL[1]);
         o.z = sorted_coord(xnew.z, xr.z, s.L[2], s.invL[2]);
