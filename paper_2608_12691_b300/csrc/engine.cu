@@ -470,8 +470,8 @@ struct System final : SystemBase {
                 M.Zraw64 = M64.Z;
             }
             const int Kmax = std::max(M.K[0], std::max(M.K[1], M.K[2]));
-            const size_t smem = sizeof(R2<double>) * (size_t)(Kmax + 2 * 16 * (Kmax + 1));
-            if (smem > 48 * 1024) fail(LFE_ERR_ARG, "PME grid too large for the FFT tile");
+            if (fft_smem<real>(Kmax) > 48 * 1024 || (dual && fft_smem<double>(Kmax) > 48 * 1024))
+                fail(LFE_ERR_ARG, "PME grid too large for the FFT tile");
             column_groups();
         }
 

@@ -196,6 +196,8 @@ template <typename real> void launch_pme(const SysView<real>& s, const PmeView<r
                                          const PmeView<double>* energy64, cudaStream_t st);
 template <typename real> void launch_spread(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st);
 template <typename real> void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st);
+// shared memory of one per-axis pass of length K (at most 48 KB without opt-in)
+template <typename real> size_t fft_smem(int K);
 // mode: CONV_BOTH energies + potentials, CONV_ENERGY energies only, CONV_POTENTIAL potentials only
 enum { CONV_BOTH = 0, CONV_ENERGY = 1, CONV_POTENTIAL = 2 };
 template <typename real> void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode,

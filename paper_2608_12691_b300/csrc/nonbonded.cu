@@ -864,6 +864,8 @@ void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, c
 // partner lists): each pair is evaluated from both ends, so every atom's
 // force is one sum written with one set of atomics instead of one set per
 // pair, and the energy is counted at the end with the lower index.
+constexpr int EXCL_BATCH = 4;   // partners per lane whose records are loaded together
+
 template <typename real>
 __global__ void k_excl(SysView<real> s, ExclView<real> ex)
 {
@@ -881,10 +883,27 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
             const bool is14 = pass == 1;
             const int e0 = is14 ? ex.p14_start[a] : ex.ex_start[a];
             const int e1 = is14 ? ex.p14_start[a + 1] : ex.ex_start[a + 1];
-            for (int e = e0 + sub; e < e1; e += 4) {
-                const int b = is14 ? ex.p14_list[e] : ex.ex_list[e];
-                const int sb = s.iperm[b];
-                const R4<real> pb = s.xq[sb];
+          for (int eb = e0 + sub; eb < e1; eb += 4 * EXCL_BATCH) {
+            // the partner records of a batch are loaded together (three
+            // dependent rounds: partner, its slot, its coordinates)
+            int bb[EXCL_BATCH], sbb[EXCL_BATCH];
+            R4<real> pbb[EXCL_BATCH];
+#pragma unroll
+            for (int u = 0; u < EXCL_BATCH; ++u) {
+                const int e = eb + 4 * u;
+                bb[u] = e < e1 ? (is14 ? ex.p14_list[e] : ex.ex_list[e]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < EXCL_BATCH; ++u) sbb[u] = bb[u] >= 0 ? s.iperm[bb[u]] : 0;
+#pragma unroll
+            for (int u = 0; u < EXCL_BATCH; ++u) if (bb[u] >= 0) pbb[u] = s.xq[sbb[u]];
+#pragma unroll
+            for (int u = 0; u < EXCL_BATCH; ++u) {
+                const int e = eb + 4 * u;
+                if (e >= e1) break;
+                const int b = bb[u];
+                const int sb = sbb[u];
+                const R4<real> pb = pbb[u];
                 real d[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
                 for (int k = 0; k < 3; ++k) d[k] -= s.L[k] * rint_(d[k] * s.invL[k]);
                 const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -919,9 +938,13 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
                 if (a < b) {
                     const int ub = s.sol[b];
                     const int cls = (ua && ub) ? 1 : ((ua || ub) ? 2 : 0);
-                    acc[(is14 ? 3 : 0) + cls] += (double)en;
+                    const int slotk = (is14 ? 3 : 0) + cls;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c)
+                        if (c == slotk) acc[c] += (double)en;   // constant indices: acc stays in registers
                 }
             }
+          }
         }
     }
     for (int o = 1; o < 4; o <<= 1) {

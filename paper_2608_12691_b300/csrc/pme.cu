@@ -271,12 +271,19 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
 }
 
 template <typename real>
+size_t fft_smem(int K)
+{
+    constexpr int NL = sizeof(real) == 8 ? 4 : 16;
+    return sizeof(R2<real>) * (size_t)(K + 2 * NL * (K + 1));
+}
+
+template <typename real>
 void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
 {
     constexpr int NL = sizeof(real) == 8 ? 4 : 16;
     const int threads = 16 * NL;
     const int K = p.K[axis];
-    const size_t smem = sizeof(R2<real>) * (size_t)(K + 2 * NL * (K + 1));
+    const size_t smem = fft_smem<real>(K);
     int blocks;
     if (axis == 2) blocks = (p.K[0] * p.K[1] + NL - 1) / NL;
     else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + NL - 1) / NL);
@@ -728,6 +735,7 @@ void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<do
     template void launch_conv<real>(const PmeView<real>&, long long*, const LamState*, int, cudaStream_t); \
     template void launch_gather<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
     template void launch_fft<real>(const PmeView<real>&, int, int, int, cudaStream_t);                       \
+    template size_t fft_smem<real>(int);                                                                    \
     template void launch_planes<real>(const PmeView<real>&, int, cudaStream_t);                             \
     template void launch_columns<real>(const PmeView<real>&, long long*, const LamState*, int, cudaStream_t); \
     template size_t planes_smem<real>(const PmeView<real>&);                                                \

@@ -49,9 +49,23 @@ def no_solute():
                             grid=16)
 
 
+def odd_grid():
+    # anisotropic grid of odd and even lengths: column groups with
+    # self-partner columns, radix-3/5 stages on every axis
+    return dict(small_ragged(), grid=[20, 18, 15])
+
+
+def big_grid():
+    # a 100^3 grid: its FP64 plane does not fit in shared memory, so both
+    # precisions take the per-axis transform
+    return dict(small_ragged(), grid=[100, 100, 100])
+
+
 SYSTEMS = {
     "c0": S.make_c0,
     "ragged": small_ragged,
+    "odd_grid": odd_grid,
+    "big_grid": big_grid,
     "nosolute": no_solute,
     "c2": S.make_c2,
     "c1": S.make_c1,
@@ -107,6 +121,13 @@ LAMS = [0.0, 0.2, 0.35, 0.6, 1.0]
 def test_small_parity(key, precision):
     d = SYSTEMS[key]()
     for lam in LAMS + [d["lam"]]:
+        check(key, lam, precision)
+
+
+@pytest.mark.parametrize("precision", [lfe.LFE_FP64, lfe.LFE_FP32_MIXED])
+@pytest.mark.parametrize("key", ["odd_grid", "big_grid"])
+def test_transform_shapes(key, precision):
+    for lam in (0.0, 0.5, 1.0):
         check(key, lam, precision)
 
 
