@@ -34,7 +34,7 @@ FLOPS_PER_PAIR = 67
 # DRAM bytes (read + write) of one k_pairs<float> launch on the octanol workload, from an ncu
 # capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum); reset to
 # None whenever the pair kernel changes
-PAIR_DRAM_BYTES_OCTANOL = 4.234496e6 + 0.0
+PAIR_DRAM_BYTES_OCTANOL = 4.233728e6 + 0.0
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
