@@ -210,3 +210,51 @@ def theta_step(theta, p_theta, dUdl, dlam_dtheta, dV, m, dt, gamma, T, normal):
     vt = a * vt + math.sqrt(KB * T * (1.0 - a * a) / m) * normal
     th = th + 0.5 * dt * vt
     return th - 2.0 * math.floor(th / 2.0), m * vt
+
+
+# ------------------------------------------------ thermodynamic integration
+# Eq. 2: Delta G = integral over lambda in [0, 1] of <dU/dlambda>_lambda.  The
+# conditional mean is accumulated in TI_BINS equal bins of lambda (bin b holds
+# lambda in [b/n, (b+1)/n), lambda = 1 in the last bin) and the profile of the
+# bin means, placed at the bin centres, is integrated by the trapezoid rule;
+# on [0, first centre] and [last centre, 1] the line through the two nearest
+# occupied centres is extended (a constant if only one bin is occupied).
+TI_BINS = 100
+
+
+class TIAccumulator:
+    def __init__(self, n=TI_BINS):
+        self.n = n
+        self.sum = np.zeros(n)
+        self.count = np.zeros(n, dtype=np.int64)
+
+    def add(self, lam, dUdl):
+        b = min(self.n - 1, int(math.floor(lam * self.n)))
+        self.sum[b] += dUdl
+        self.count[b] += 1
+
+    def means(self):
+        m = np.full(self.n, np.nan)
+        occ = self.count > 0
+        m[occ] = self.sum[occ] / self.count[occ]
+        return m
+
+    def delta_g(self):
+        occ = np.flatnonzero(self.count > 0)
+        if occ.size == 0:
+            return float("nan")
+        x = (occ + 0.5) / self.n
+        y = self.sum[occ] / self.count[occ]
+        if occ.size == 1:
+            return float(y[0])
+        total = 0.0
+        for k in range(occ.size - 1):
+            total += 0.5 * (y[k] + y[k + 1]) * (x[k + 1] - x[k])
+        # linear extension to lambda = 0 and lambda = 1
+        s0 = (y[1] - y[0]) / (x[1] - x[0])
+        y0 = y[0] - s0 * x[0]
+        total += 0.5 * (y0 + y[0]) * x[0]
+        s1 = (y[-1] - y[-2]) / (x[-1] - x[-2])
+        y1 = y[-1] + s1 * (1.0 - x[-1])
+        total += 0.5 * (y[-1] + y1) * (1.0 - x[-1])
+        return total
