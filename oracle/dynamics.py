@@ -258,3 +258,64 @@ class TIAccumulator:
         y1 = y[-1] + s1 * (1.0 - x[-1])
         total += 0.5 * (y[-1] + y1) * (1.0 - x[-1])
         return total
+
+
+# ------------------------------------------------------------------ d-AFED
+# Eq. 15: U = sum_k kappa_k / 2 (xi_k(r) - s_k)^2, the difference taken as a
+# periodic angle in [-pi, pi).  xi_k is the dihedral of four atoms, with the
+# oracle's torsion convention and gradient (reference.dihedral_grad, pinned
+# by central differences in the bonded tests).
+
+def wrap_angle(x):
+    """x in [-pi, pi)."""
+    return x - 2.0 * math.pi * math.floor((x + math.pi) / (2.0 * math.pi))
+
+
+def dihedral_grad(pos, idx, box):
+    """(xi, dxi/dr[4, 3]) of the dihedral of atoms idx = (a, b, c, d)."""
+    from . import reference as R
+    return R.dihedral_grad(*(pos[i] for i in idx), box)
+
+
+def dafed_energy_forces(pos, cvs, s, kappa, box):
+    """(U, forces on atoms [N, 3], forces on s [K]) of Eq. 15."""
+    F = np.zeros_like(np.asarray(pos, dtype=np.float64))
+    Fs = np.zeros(len(cvs))
+    U = 0.0
+    for k, idx in enumerate(cvs):
+        xi, g = dihedral_grad(pos, idx, box)
+        dlt = wrap_angle(xi - s[k])
+        U += 0.5 * kappa[k] * dlt * dlt
+        for j, atom in enumerate(idx):
+            F[atom] -= kappa[k] * dlt * g[j]
+        Fs[k] = kappa[k] * dlt
+    return U, F, Fs
+
+
+def dafed_masses(pos, cvs, mass, c, box):
+    """Eq. 16: m_s = c [sum_i ||d xi / d r_i||^2 / m_i]^-1 (massless = fixed atoms skipped)."""
+    out = np.zeros(len(cvs))
+    for k, idx in enumerate(cvs):
+        _, g = dihedral_grad(pos, idx, box)
+        tot = 0.0
+        for j, atom in enumerate(idx):
+            if mass[atom] > 0.0:
+                tot += np.dot(g[j], g[j]) / mass[atom]
+        out[k] = c / tot
+    return out
+
+
+def dafed_normal(k, step, seed):
+    """Normal of auxiliary variable k at a step: counter (k, step_lo, step_hi, 2)."""
+    return normals3((k, step & _MASK, step >> 32, 2), seed_key(seed))[0]
+
+
+def dafed_step(s, p, Fs, m, dt, gamma, T, normal):
+    """Middle scheme for one auxiliary variable at its own temperature T:
+    kick, half drift, Ornstein-Uhlenbeck, half drift; s wrapped into [-pi, pi)."""
+    v = p / m + dt * Fs / m
+    x = s + 0.5 * dt * v
+    a = math.exp(-gamma * dt)
+    v = a * v + math.sqrt(KB * T * (1.0 - a * a) / m) * normal
+    x = x + 0.5 * dt * v
+    return wrap_angle(x), m * v

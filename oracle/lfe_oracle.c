@@ -709,6 +709,18 @@ double orc_dihedral(const double* a, const double* b, const double* c, const dou
     return dihedral(a, b, c, d, box, g);
 }
 
+/* The dihedral and its gradient with respect to the four positions
+ * (grad[3 j + k]: atom j, component k), as used by the torsion forces. */
+double orc_dihedral_grad(const double* a, const double* b, const double* c, const double* d, const double* box,
+                         double* grad)
+{
+    double g[4][3];
+    const double phi = dihedral(a, b, c, d, box, g);
+    for (int j = 0; j < 4; ++j)
+        for (int k = 0; k < 3; ++k) grad[3 * j + k] = g[j][k];
+    return phi;
+}
+
 double orc_bonded(const double* box, int n, const double* pos,
                   int nb, const int* bi, const double* bp,
                   int na, const int* ai, const double* ap,

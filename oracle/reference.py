@@ -67,6 +67,8 @@ def lib():
         _lib.orc_bmod2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         _lib.orc_dihedral.restype = d
         _lib.orc_dihedral.argtypes = [dp, dp, dp, dp, dp]
+        _lib.orc_dihedral_grad.restype = d
+        _lib.orc_dihedral_grad.argtypes = [dp, dp, dp, dp, dp, dp]
         _lib.orc_bonded.restype = d
         _lib.orc_num_threads.restype = ctypes.c_int
     return _lib
@@ -123,6 +125,14 @@ def bmod2(n, K, m):
 def dihedral(a, b, c, d, box):
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (a, b, c, d, box)]
     return lib().orc_dihedral(*[_ptr(x) for x in arrs])
+
+
+def dihedral_grad(a, b, c, d, box):
+    """(phi, dphi/dr [4, 3]) in the convention of the torsion terms."""
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (a, b, c, d, box)]
+    g = np.zeros(12)
+    phi = lib().orc_dihedral_grad(*[_ptr(x) for x in arrs], _ptr(g))
+    return phi, g.reshape(4, 3)
 
 
 # --------------------------------------------------------- nonbonded energy

@@ -219,6 +219,8 @@ DIPEPTIDE_BONDS = [(0, 1), (0, 2), (0, 3), (0, 4), (4, 5), (4, 6), (6, 7), (6, 8
                    (16, 17), (16, 18), (18, 19), (18, 20), (18, 21)]
 DIPEPTIDE_ELEM = ["C", "H", "H", "H", "C", "O", "N", "H", "C", "H", "C", "H", "H", "H",
                   "C", "O", "N", "H", "C", "H", "H", "H"]
+# the torsions coupled to auxiliary variables (d-AFED): phi, psi, chi
+DIPEPTIDE_CVS = [(4, 6, 8, 14), (6, 8, 14, 16), (6, 8, 10, 11)]
 
 
 def solute_dipeptide22(phi, psi, chi):
