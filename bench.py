@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--no-dafed", action="store_true", help="skip the flexible-solute d-AFED leg")
     p.add_argument("--e2e-steps", type=int, default=30)
     p.add_argument("--batch-replicas", type=int, default=32,
                    help="replicas in the batched leg (half water, half octanol; 0 skips it)")
@@ -170,6 +171,33 @@ def equilibrate(g, d, stream):
         g.step(n, stream)
     g.set_integrator(dt, float(d["friction"]), float(d["temperature"]))
     g.get_state()
+
+
+def dafed_leg(args, stream, flush):
+    """The flexible-solute workload of the method: a differentiation frame
+    (22-atom dipeptide-like solute in 4,000 rigid waters, 12,022 atoms) stepped
+    at 1 fs with lambda-dynamics under the dual OPES bias and d-AFED on the
+    phi, psi and chi torsions (1000 K, 50 amu nm^2 rad^-2, 1000 kJ/mol/rad^2)."""
+    import torch
+    from paper_2608_12691_b300 import lfe
+    from paper_2608_12691_b300 import systems as S
+    d = dict(S.make_c4_frame(frame=0))
+    d.update(dt=0.001, lambda_mass=20.0, lambda_friction=25.0, opes_stride=500,
+             opes_dE_std=30.0 * 4.184, opes_dE_exp=5.0 * 4.184, opes_sigma=0.10)
+    g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242)
+    g.set_dafed(S.DIPEPTIDE_CVS, 1000.0, 50.0, temperature=1000.0, friction=25.0)
+    equilibrate(g, d, stream)
+    g.step(20, stream)
+    torch.cuda.synchronize()
+    k = max(20, min(200, args.steps))
+    ms = time_steps(g, k, stream, flush)
+    m = sum(ms) / k
+    _, _, ext = g.get_state()
+    s, _, xi = g.dafed_state()
+    return {"workload": "dipeptide-like 22-atom flexible solute + 4,000 rigid waters, 12,022 atoms, 1 fs, "
+                        "lambda-OPES (dual) + d-AFED on 3 torsions",
+            "ms_per_step": m, "ns_per_day": 0.001 * 1e-3 * 86400.0 / (m * 1e-3), "steps": k,
+            "lambda_end": ext["lambda"], "s_end": [float(x) for x in s], "xi_end": [float(x) for x in xi]}
 
 
 def batched_leg(args, stream, flush):
@@ -343,6 +371,7 @@ def run_ours(args):
             g64.close()
         cpu = None if args.no_cpu else cpu_baseline(d, dt_ps)
         batched = batched_leg(args, stream, flush) if args.batch_replicas > 1 else None
+        dafed = dafed_leg(args, stream, flush) if not args.no_dafed else None
         out = {"metric": METRIC, "value": ns_day, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32" if prec == lfe.LFE_FP32_MIXED else "f64",
@@ -356,7 +385,8 @@ def run_ours(args):
                "wall_ms_per_step": wall / args.steps * 1e3,
                "neighbour_rebuilds": rebuilds,
                "gpu_launches": launches,
-               "roofline": roof, "stages_ms": stages, "fp64": fp64, "batched": batched, "cpu_baseline": cpu,
+               "roofline": roof, "stages_ms": stages, "fp64": fp64, "batched": batched, "dafed": dafed,
+               "cpu_baseline": cpu,
                "e2e": e2e,
                "clocks": clocks, "lambda_end": ext1["lambda"], "theta_end": ext1["theta"]}
         print(json.dumps(out), flush=True)

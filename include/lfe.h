@@ -210,8 +210,50 @@ int lfe_step(lfe_system* sys, int n_steps, void* stream);
 #define LFE_NEXT 9
 int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext);
 
+/* d-AFED (Eq. 15): n_cv torsions xi_k (atoms[4k .. 4k+3], the IUPAC sign:
+ * atan2(|b2| b1 . (b2 x b3), (b1 x b2) . (b2 x b3)) with b1 = r_j - r_i,
+ * b2 = r_k - r_j, b3 = r_l - r_k, minimum images) are coupled to auxiliary
+ * angles s_k by kappa_k / 2 (xi_k - s_k)^2, the difference wrapped into
+ * [-pi, pi).  Each s_k has mass mass[k] (amu nm^2 rad^-2) and is advanced by
+ * the same middle scheme as the atoms at its own temperature (K) with
+ * friction (ps^-1), with the atoms' time step; s0 (rad, may be NULL: the
+ * current torsions) are the initial angles, momenta start at 0.  The
+ * coupling forces join the atomic forces and the coupling energy joins U.
+ * n_cv = 0 removes the coupling.  Indices out of range, a repeated atom in a
+ * torsion, kappa < 0, mass <= 0 or non-finite input: LFE_ERR_ARG.  The
+ * auxiliary angles and momenta are part of checkpoints (a checkpoint restores
+ * only into a system with the same number of coupled torsions).
+ * Paper values: 1000 K, 50 amu nm^2 rad^-2, kappa 1000 kJ mol^-1 rad^-2. */
+int lfe_set_dafed(lfe_system* sys, int n_cv, const int* atoms, const double* kappa, const double* mass,
+                  double temperature, double friction, const double* s0);
+
+/* Current auxiliary angles s [n_cv], momenta p_s [n_cv] and the torsions xi
+ * [n_cv] at the current positions (host arrays, any may be NULL).
+ * Synchronises. */
+int lfe_dafed_state(lfe_system* sys, double* s, double* p_s, double* xi);
+
+/* Eq. 16 at the current positions: mass_out[k] = c [sum_i |d xi_k / d r_i|^2
+ * / m_i]^-1 over the four atoms of torsion k (atoms of mass 0 are fixed and
+ * do not contribute; a torsion with none movable: LFE_ERR_ARG). */
+int lfe_dafed_masses(lfe_system* sys, int n_cv, const int* atoms, double c, double* mass_out);
+
+/* Thermodynamic integration (Eq. 2): every step adds dU/dlambda, evaluated
+ * at that step's lambda, to one of LFE_TI_BINS equal lambda bins (bin b holds
+ * lambda in [b/n, (b+1)/n); lambda = 1 is in the last bin).  lfe_ti returns,
+ * into host arrays of LFE_TI_BINS (either may be NULL), the bin means (NaN
+ * for an empty bin) and sample counts, and in *delta_g (may be NULL) the
+ * integral over lambda in [0, 1] of the mean-force profile: trapezoid rule
+ * over the centres of the occupied bins, with the line through the two
+ * nearest occupied centres extended to lambda = 0 and lambda = 1 (a
+ * constant if one bin is occupied, NaN if none).  reset != 0 clears the
+ * accumulators afterwards.  Synchronises.  The accumulators are part of
+ * checkpoints. */
+#define LFE_TI_BINS 100
+int lfe_ti(lfe_system* sys, double* mean, double* count, double* delta_g, int reset);
+
 /* Write / read a versioned binary checkpoint (positions, velocities, theta,
- * p_theta, OPES kernels, step counter; checksum verified on restore). */
+ * p_theta, OPES kernels, step counter, TI accumulators; checksum verified on
+ * restore). */
 int lfe_checkpoint(lfe_system* sys, const char* path);
 int lfe_restore(lfe_system* sys, const char* path);
 

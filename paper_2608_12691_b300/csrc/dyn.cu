@@ -78,7 +78,7 @@ __global__ void k_eval_out(SysView<real> s, double* forces, double* terms, doubl
         const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + cuv;
         const double Us = efix(E, E_PAIR_SOFT);
         const double Ub = efix(E, E_BONDED);
-        const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub;
+        const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub + efix(E, E_DAFED);
         const double dU = L->dhA * Uuv + L->dhB * Us;
         if (terms) {
             terms[0] = U; terms[1] = dU; terms[2] = Uvv; terms[3] = Uuu; terms[4] = Uuv;
@@ -205,6 +205,44 @@ void launch_moved(const SysView<real>& s, real skin_half2, cudaGraphConditionalH
     k_cond_rebuild<real><<<1, 1, 0, st>>>(s, h);
 }
 
+// Dihedral of atoms (i, j, k, l) from r_ij = x_i - x_j, r_kj = x_k - x_j,
+// r_kl = x_k - x_l (minimum images): phi = atan2(|r_kj| r_ij . n, m . n) with
+// m = r_ij x r_kj, n = r_kj x r_kl (the IUPAC sign), and the forces
+// -dU/dphi grad phi on the four atoms for a given dU/dphi.
+template <typename T>
+struct Torsion {
+    T m[3], n[3], m2, n2, rkj2, lkj, p, q;
+    __device__ __forceinline__ T angle(const T* rij, const T* rkj, const T* rkl)
+    {
+        m[0] = rij[1] * rkj[2] - rij[2] * rkj[1];
+        m[1] = rij[2] * rkj[0] - rij[0] * rkj[2];
+        m[2] = rij[0] * rkj[1] - rij[1] * rkj[0];
+        n[0] = rkj[1] * rkl[2] - rkj[2] * rkl[1];
+        n[1] = rkj[2] * rkl[0] - rkj[0] * rkl[2];
+        n[2] = rkj[0] * rkl[1] - rkj[1] * rkl[0];
+        m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
+        n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+        rkj2 = rkj[0] * rkj[0] + rkj[1] * rkj[1] + rkj[2] * rkj[2];
+        lkj = sqrt(rkj2);
+        p = (rij[0] * rkj[0] + rij[1] * rkj[1] + rij[2] * rkj[2]) / rkj2;
+        q = (rkl[0] * rkj[0] + rkl[1] * rkj[1] + rkl[2] * rkj[2]) / rkj2;
+        const T yv = lkj * (rij[0] * n[0] + rij[1] * n[1] + rij[2] * n[2]);
+        const T xv = m[0] * n[0] + m[1] * n[1] + m[2] * n[2];
+        return atan2(yv, xv);
+    }
+    __device__ __forceinline__ void forces(T dUdphi, T* fi, T* fj, T* fk, T* fl) const
+    {
+        for (int k = 0; k < 3; ++k) {
+            fi[k] = -dUdphi * lkj / m2 * m[k];
+            fl[k] = dUdphi * lkj / n2 * n[k];
+        }
+        for (int k = 0; k < 3; ++k) {
+            fj[k] = -fi[k] + p * fi[k] - q * fl[k];
+            fk[k] = -fl[k] - p * fi[k] + q * fl[k];
+        }
+    }
+};
+
 // ---------------------------------------------------------------- bonded
 // harmonic bonds 1/2 k (r - r0)^2, harmonic angles 1/2 k (theta - theta0)^2,
 // periodic torsions k (1 + cos(n phi - phi0)); minimum-image vectors
@@ -260,36 +298,17 @@ __global__ void k_bonded(SysView<real> s, BondView<real> b)
         const int4 t = b.t[e - b.nb - b.na];
         const R4<real> par = b.tp[e - b.nb - b.na];
         // r_ij = x_i - x_j, r_kj = x_k - x_j, r_kl = x_k - x_l
-        real rij[3], rkj[3], rkl[3], tmp[3];
+        real rij[3], rkj[3], rkl[3];
         vec(t.y, t.x, rij);
         vec(t.y, t.z, rkj);
         vec(t.w, t.z, rkl);
-        (void)tmp;
-        const real m[3] = {rij[1] * rkj[2] - rij[2] * rkj[1], rij[2] * rkj[0] - rij[0] * rkj[2],
-                           rij[0] * rkj[1] - rij[1] * rkj[0]};
-        const real n[3] = {rkj[1] * rkl[2] - rkj[2] * rkl[1], rkj[2] * rkl[0] - rkj[0] * rkl[2],
-                           rkj[0] * rkl[1] - rkj[1] * rkl[0]};
-        const real m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
-        const real n2 = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
-        const real rkj2 = rkj[0] * rkj[0] + rkj[1] * rkj[1] + rkj[2] * rkj[2];
-        const real lkj = sqrt(rkj2);
-        const real yv = lkj * (rij[0] * n[0] + rij[1] * n[1] + rij[2] * n[2]);
-        const real xv = m[0] * n[0] + m[1] * n[1] + m[2] * n[2];
-        const real phi = atan2(yv, xv);
+        Torsion<real> tor;
+        const real phi = tor.angle(rij, rkj, rkl);
         const real arg = par.y * phi - par.z;
         en = (double)par.x * (1.0 + cos((double)arg));
         const real dUdphi = -par.x * par.y * sin(arg);
         real fi[3], fl[3], fj[3], fk[3];
-        const real p = (rij[0] * rkj[0] + rij[1] * rkj[1] + rij[2] * rkj[2]) / rkj2;
-        const real qv = (rkl[0] * rkj[0] + rkl[1] * rkj[1] + rkl[2] * rkj[2]) / rkj2;
-        for (int k = 0; k < 3; ++k) {
-            fi[k] = -dUdphi * lkj / m2 * m[k];
-            fl[k] = dUdphi * lkj / n2 * n[k];
-        }
-        for (int k = 0; k < 3; ++k) {
-            fj[k] = -fi[k] + p * fi[k] - qv * fl[k];
-            fk[k] = -fl[k] - p * fi[k] + qv * fl[k];
-        }
+        tor.forces(dUdphi, fi, fj, fk, fl);
         add_force(s, t.x, fi[0], fi[1], fi[2]);
         add_force(s, t.y, fj[0], fj[1], fj[2]);
         add_force(s, t.z, fk[0], fk[1], fk[2]);
@@ -305,6 +324,115 @@ void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t
     const int n = b.nb + b.na + b.nt;
     if (n == 0) return;
     k_bonded<real><<<(n + 255) / 256, 256, 0, st>>>(s, b);
+}
+
+// ------------------------------------------------------------------ d-AFED
+// Eq. 15: U = sum_k kappa_k / 2 wrap(xi_k - s_k)^2 with wrap into [-pi, pi).
+// One thread per coupled torsion, FP64 geometry from the master positions.
+__device__ __forceinline__ double wrap_pi(double x)
+{
+    return x - 2.0 * PI * floor((x + PI) / (2.0 * PI));
+}
+
+template <typename real>
+__device__ __forceinline__ double dafed_geom(const SysView<real>& s, int4 t, Torsion<double>& tor)
+{
+    auto vec = [&](int i, int j, double* d) {
+        const R4<real> pi = s.x[i], pj = s.x[j];
+        const double dd[3] = {(double)pj.x - (double)pi.x, (double)pj.y - (double)pi.y, (double)pj.z - (double)pi.z};
+        for (int k = 0; k < 3; ++k) d[k] = dd[k] - (double)s.L[k] * rint(dd[k] / (double)s.L[k]);
+    };
+    double rij[3], rkj[3], rkl[3];
+    vec(t.y, t.x, rij);
+    vec(t.y, t.z, rkj);
+    vec(t.w, t.z, rkl);
+    return tor.angle(rij, rkj, rkl);
+}
+
+template <typename real>
+__global__ void k_dafed_force(SysView<real> s, DafedView d)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double en = 0.0;
+    if (k < d.n) {
+        const int4 t = d.atoms[k];
+        Torsion<double> tor;
+        const double xi = dafed_geom(s, t, tor);
+        const double dl = wrap_pi(xi - d.s[k]);
+        en = 0.5 * d.kappa[k] * dl * dl;
+        double fi[3], fj[3], fk[3], fl[3];
+        tor.forces(d.kappa[k] * dl, fi, fj, fk, fl);
+        add_force(s, t.x, (real)fi[0], (real)fi[1], (real)fi[2]);
+        add_force(s, t.y, (real)fj[0], (real)fj[1], (real)fj[2]);
+        add_force(s, t.z, (real)fk[0], (real)fk[1], (real)fk[2]);
+        add_force(s, t.w, (real)fl[0], (real)fl[1], (real)fl[2]);
+        d.fs[k] = d.kappa[k] * dl;
+        d.xi[k] = xi;
+    }
+    const long long v = __double2ll_rn(warp_sum_d(en) * ESCALE);
+    if ((threadIdx.x & 31) == 0 && v) atomic_add_ll(&s.E[E_DAFED], v);
+}
+
+// the auxiliary variables' middle-scheme step at their own temperature
+// (normal from Philox at counter (k, step_lo, step_hi, 2))
+template <typename real>
+__global__ void k_dafed_step(SysView<real> s, DafedView d)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) return;   // step skipped (see k_integrate)
+    const unsigned long long step = s.lam->step;
+    double n0, n1, n2;
+    normals3<double>(make_uint4((unsigned)k, (unsigned)step, (unsigned)(step >> 32), 2u), d.key, n0, n1, n2);
+    const double m = d.mass[k];
+    double v = d.p[k] / m + d.dt * d.fs[k] / m;
+    double x = d.s[k] + 0.5 * d.dt * v;
+    v = d.a_fric * v + sqrt(d.kT * (1.0 - d.a_fric * d.a_fric) / m) * n0;
+    x += 0.5 * d.dt * v;
+    d.s[k] = wrap_pi(x);
+    d.p[k] = m * v;
+}
+
+template <typename real>
+__global__ void k_dafed_probe(SysView<real> s, DafedView d, double c, double* out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= d.n) return;
+    const int4 t = d.atoms[k];
+    Torsion<double> tor;
+    const double xi = dafed_geom(s, t, tor);
+    if (!(c > 0.0)) {
+        out[k] = xi;
+        return;
+    }
+    double g[4][3];
+    tor.forces(-1.0, g[0], g[1], g[2], g[3]);   // -dU/dphi grad phi with dU/dphi = -1: grad phi
+    const int at[4] = {t.x, t.y, t.z, t.w};
+    double tot = 0.0;
+    for (int a = 0; a < 4; ++a) {
+        const double w = (double)s.invm[at[a]];
+        tot += w * (g[a][0] * g[a][0] + g[a][1] * g[a][1] + g[a][2] * g[a][2]);
+    }
+    out[k] = c / tot;
+}
+
+template <typename real>
+void launch_dafed_force(const SysView<real>& s, const DafedView& d, cudaStream_t st)
+{
+    if (d.n == 0) return;
+    k_dafed_force<real><<<(d.n + 31) / 32, 32, 0, st>>>(s, d);
+}
+template <typename real>
+void launch_dafed_step(const SysView<real>& s, const DafedView& d, cudaStream_t st)
+{
+    if (d.n == 0) return;
+    k_dafed_step<real><<<(d.n + 31) / 32, 32, 0, st>>>(s, d);
+}
+template <typename real>
+void launch_dafed_probe(const SysView<real>& s, const DafedView& d, double c, double* out, cudaStream_t st)
+{
+    if (d.n == 0) return;
+    k_dafed_probe<real><<<(d.n + 31) / 32, 32, 0, st>>>(s, d, c, out);
 }
 
 // ------------------------------------------------------------ integrator
@@ -666,7 +794,7 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const double Us = efix(E, E_PAIR_SOFT);
     const double Ub = efix(E, E_BONDED);
     const double dUdl = L->dhA * Uuv + L->dhB * Us;
-    const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub;
+    const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub + efix(E, E_DAFED);
     const double th = L->theta;
     const double V0 = t.pre->V[0], dV0 = t.pre->dV[0], V1 = t.pre->V[1], dV1 = t.pre->dV[1];
     const unsigned long long step = L->step;
@@ -690,6 +818,11 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     }
     __syncwarp();
     if (lane == 0) {
+        // Eq. 2: the mean force is accumulated in lambda bins (at the lambda
+        // of this step's evaluation)
+        const int bin = min(LFE_TI_BINS - 1, max(0, (int)floor(L->lambda * LFE_TI_BINS)));
+        t.ti_sum[bin] += dUdl;
+        t.ti_cnt[bin] += 1ull;
         const double lam = thn <= 1.0 ? thn : 2.0 - thn;
         double hA, hB, dA, dB;
         switching_fns(lam, hA, hB, dA, dB);
@@ -749,6 +882,9 @@ void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStrea
     template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \
     template void launch_prestep<real>(const SysView<real>&, const StepView<real>&, const ThetaView<real>&,  \
                                        cudaStream_t);                                                       \
+    template void launch_dafed_force<real>(const SysView<real>&, const DafedView&, cudaStream_t);            \
+    template void launch_dafed_step<real>(const SysView<real>&, const DafedView&, cudaStream_t);             \
+    template void launch_dafed_probe<real>(const SysView<real>&, const DafedView&, double, double*, cudaStream_t); \
     template void launch_step_end<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
 LFE_INST_DYN(float)
 LFE_INST_DYN(double)

@@ -81,6 +81,11 @@ struct SystemBase {
     virtual void restore(const char* path) = 0;
     virtual int time_stages(double lam, int reps, cudaStream_t st, const char** names, double* ms, int max_n) = 0;
     virtual void param_grad(double lam, double* dU, double* d2U, double* basis, int on_device, cudaStream_t st) = 0;
+    virtual void ti(double* mean, double* count, double* delta_g, int reset) = 0;
+    virtual void set_dafed(int n, const int* atoms, const double* kappa, const double* mass, double temperature,
+                           double friction, const double* s0) = 0;
+    virtual void dafed_state(double* s, double* p, double* xi) = 0;
+    virtual void dafed_masses(int n, const int* atoms, double c, double* out) = 0;
     virtual void set_solute_params(const double* q, const double* sig, const double* eps, int on_device,
                                    cudaStream_t st) = 0;
     // batched replicas: record this system's whole step (evaluation, both
@@ -111,6 +116,7 @@ struct System final : SystemBase {
     PmeView<double> M64{};      // FP64 energy branch (FP32 systems only)
     bool dual = false;
     BondView<real> B{};
+    DafedView D{};
     StepView<real> G{};
     ThetaView<real> T{};
     int pair_warps = 0;
@@ -571,6 +577,8 @@ struct System final : SystemBase {
         }
         G.noise = dalloc<real>(3 * (size_t)n);
         T.pre = dalloc<ThetaPre>(1);
+        T.ti_sum = dalloc<double>(LFE_TI_BINS);
+        T.ti_cnt = dalloc<unsigned long long>(LFE_TI_BINS);
         G.dt = (real)p.dt;
         G.a_fric = (real)std::exp(-p.friction * p.dt);
         G.kT = (real)(KB * p.temperature);
@@ -856,6 +864,8 @@ struct System final : SystemBase {
         T.dt = dt;
         T.a_fric = std::exp(-P.lambda_friction * dt);
         T.kT = KB * temperature;
+        D.dt = dt;
+        D.a_fric = std::exp(-dafed_friction * dt);
         invalidate_graph();
         ++generation;
     }
@@ -876,6 +886,7 @@ struct System final : SystemBase {
         launch_pme(S, M, dual ? &M64 : nullptr, st);
         launch_excl(S, X, st);
         launch_bonded(S, B, st);
+        launch_dafed_force(S, D, st);
     }
 
     void eval(double lam, double* forces, double* terms, int out_on_device, cudaStream_t st) override
@@ -950,6 +961,7 @@ struct System final : SystemBase {
         launch_uv_energy(S, N, uv_blocks, br[3]);
         launch_excl(S, X, br[3]);
         launch_bonded(S, B, br[3]);
+        launch_dafed_force(S, D, br[3]);
         for (int k = 0; k < 4; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
             CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
@@ -972,6 +984,7 @@ struct System final : SystemBase {
         launch_prestep(S, G, Tc, s0);
         launch_integrate(S, G, s0);
         launch_theta(S, Tc, s0);
+        launch_dafed_step(S, D, s0);
         launch_step_end(S, Tc, s0);
         const cudaGraphNode_t* deps = nullptr;
         size_t ndeps = 0;
@@ -1026,6 +1039,7 @@ struct System final : SystemBase {
         CK(cudaEventRecord(ev_fork, s0));
         CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
         launch_theta(S, Tc, br[0]);
+        launch_dafed_step(S, D, br[0]);
         CK(cudaEventRecord(ev_join[0], br[0]));
         launch_integrate(S, G, s0);
         CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
@@ -1068,6 +1082,7 @@ struct System final : SystemBase {
         launch_prestep(S, G, T, st);
         launch_integrate(S, G, st);
         launch_theta(S, T, st);
+        launch_dafed_step(S, D, st);
         launch_step_end(S, T, st);
         CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -1155,10 +1170,155 @@ struct System final : SystemBase {
             for (int k = 0; k < LFE_NEXT; ++k) ext[k] = e[k];
     }
 
-    // checkpoint layout: header | x | v | xref | LamState | OpesState | centre | weight | S | checksum
+    // Eq. 2: bin means and the trapezoid integral of the mean-force profile
+    // over the occupied bin centres, extended linearly to lambda = 0 and 1
+    void ti(double* mean, double* count, double* delta_g, int reset) override
+    {
+        CK(cudaDeviceSynchronize());
+        std::vector<double> sum(LFE_TI_BINS);
+        std::vector<unsigned long long> cnt(LFE_TI_BINS);
+        CK(cudaMemcpy(sum.data(), T.ti_sum, sizeof(double) * LFE_TI_BINS, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(cnt.data(), T.ti_cnt, sizeof(unsigned long long) * LFE_TI_BINS, cudaMemcpyDeviceToHost));
+        std::vector<double> xs, ys;
+        for (int b = 0; b < LFE_TI_BINS; ++b) {
+            const double m = cnt[b] ? sum[b] / (double)cnt[b] : std::nan("");
+            if (mean) mean[b] = m;
+            if (count) count[b] = (double)cnt[b];
+            if (cnt[b]) {
+                xs.push_back((b + 0.5) / LFE_TI_BINS);
+                ys.push_back(m);
+            }
+        }
+        if (delta_g) {
+            const size_t k = xs.size();
+            double g = std::nan("");
+            if (k == 1) {
+                g = ys[0];
+            } else if (k > 1) {
+                g = 0.0;
+                for (size_t i = 0; i + 1 < k; ++i) g += 0.5 * (ys[i] + ys[i + 1]) * (xs[i + 1] - xs[i]);
+                const double lo = ys[0] - (ys[1] - ys[0]) / (xs[1] - xs[0]) * xs[0];
+                const double hi = ys[k - 1] + (ys[k - 1] - ys[k - 2]) / (xs[k - 1] - xs[k - 2]) * (1.0 - xs[k - 1]);
+                g += 0.5 * (lo + ys[0]) * xs[0] + 0.5 * (ys[k - 1] + hi) * (1.0 - xs[k - 1]);
+            }
+            *delta_g = g;
+        }
+        if (reset) {
+            CK(cudaMemset(T.ti_sum, 0, sizeof(double) * LFE_TI_BINS));
+            CK(cudaMemset(T.ti_cnt, 0, sizeof(unsigned long long) * LFE_TI_BINS));
+        }
+    }
+
+    // ------------------------------------------------------------- d-AFED
+    double dafed_friction = 0.0;
+    double* d_probe = nullptr;     // [n_cv] probe output
+
+    void dafed_view_from(int n_cv, const int* atoms, DafedView& V, std::vector<int4>& at)
+    {
+        if (n_cv < 0) fail(LFE_ERR_ARG, "negative number of coupled torsions");
+        if (n_cv > 0 && !atoms) fail(LFE_ERR_ARG, "atoms is NULL");
+        at.resize(n_cv);
+        for (int k = 0; k < n_cv; ++k) {
+            const int* a = atoms + 4 * k;
+            for (int j = 0; j < 4; ++j)
+                if (a[j] < 0 || a[j] >= n) fail(LFE_ERR_ARG, "torsion atom index out of range");
+            if (a[0] == a[1] || a[0] == a[2] || a[0] == a[3] || a[1] == a[2] || a[1] == a[3] || a[2] == a[3])
+                fail(LFE_ERR_ARG, "a torsion repeats an atom");
+            at[k] = make_int4(a[0], a[1], a[2], a[3]);
+        }
+        V.n = n_cv;
+    }
+
+    // couple n torsions to auxiliary angles (Eq. 15); n = 0 switches it off
+    void set_dafed(int n_cv, const int* atoms, const double* kappa, const double* mass, double temperature,
+                   double friction, const double* s0) override
+    {
+        std::vector<int4> at;
+        DafedView V{};
+        dafed_view_from(n_cv, atoms, V, at);
+        if (n_cv > 0) {
+            if (!kappa || !mass) fail(LFE_ERR_ARG, "kappa and mass must not be NULL");
+            for (int k = 0; k < n_cv; ++k) {
+                if (!(kappa[k] >= 0) || !std::isfinite(kappa[k])) fail(LFE_ERR_ARG, "kappa must be finite and >= 0");
+                if (!(mass[k] > 0) || !std::isfinite(mass[k])) fail(LFE_ERR_ARG, "auxiliary masses must be > 0");
+                if (s0 && !std::isfinite(s0[k])) fail(LFE_ERR_ARG, "non-finite initial auxiliary angle");
+            }
+            if (!(temperature >= 0) || !(friction >= 0) || !std::isfinite(temperature) || !std::isfinite(friction))
+                fail(LFE_ERR_ARG, "auxiliary temperature and friction must be >= 0");
+        }
+        CK(cudaDeviceSynchronize());
+        if (exec) recover_overflow(nullptr);
+        for (void* ptr : {(void*)D.atoms, (void*)D.kappa, (void*)D.mass, (void*)D.s, (void*)D.p, (void*)D.fs,
+                          (void*)D.xi, (void*)d_probe})
+            if (ptr) dfree(ptr);
+        D = DafedView{};
+        d_probe = nullptr;
+        if (n_cv > 0) {
+            D.n = n_cv;
+            D.atoms = upload(at);
+            D.kappa = upload(std::vector<double>(kappa, kappa + n_cv));
+            D.mass = upload(std::vector<double>(mass, mass + n_cv));
+            D.s = dalloc<double>(n_cv);
+            D.p = dalloc<double>(n_cv);
+            D.fs = dalloc<double>(n_cv);
+            D.xi = dalloc<double>(n_cv);
+            d_probe = dalloc<double>(n_cv);
+            D.dt = P.dt;
+            dafed_friction = friction;
+            D.a_fric = std::exp(-friction * P.dt);
+            D.kT = KB * temperature;
+            D.key = G.key;
+            if (s0) {
+                std::vector<double> w(n_cv);
+                for (int k = 0; k < n_cv; ++k) w[k] = s0[k] - 2.0 * PI * std::floor((s0[k] + PI) / (2.0 * PI));
+                CK(cudaMemcpy(D.s, w.data(), sizeof(double) * n_cv, cudaMemcpyHostToDevice));
+            } else {
+                launch_dafed_probe(S, D, 0.0, D.s, nullptr);   // start on the torsions
+            }
+            CK(cudaDeviceSynchronize());
+            CK(cudaGetLastError());
+        }
+        invalidate_graph();
+        ++generation;
+    }
+
+    void dafed_state(double* s_out, double* p_out, double* xi_out) override
+    {
+        CK(cudaDeviceSynchronize());
+        if (D.n == 0) return;
+        if (s_out) CK(cudaMemcpy(s_out, D.s, sizeof(double) * D.n, cudaMemcpyDeviceToHost));
+        if (p_out) CK(cudaMemcpy(p_out, D.p, sizeof(double) * D.n, cudaMemcpyDeviceToHost));
+        if (xi_out) {
+            launch_dafed_probe(S, D, 0.0, d_probe, nullptr);
+            CK(cudaMemcpy(xi_out, d_probe, sizeof(double) * D.n, cudaMemcpyDeviceToHost));
+        }
+    }
+
+    // Eq. 16 at the current positions (atoms of mass 0 do not contribute)
+    void dafed_masses(int n_cv, const int* atoms, double c, double* out) override
+    {
+        if (!(c > 0) || !out) fail(LFE_ERR_ARG, "c must be > 0 and out not NULL");
+        std::vector<int4> at;
+        DafedView V{};
+        dafed_view_from(n_cv, atoms, V, at);
+        if (n_cv == 0) return;
+        int4* d_at = upload(at);
+        double* d_out = dalloc<double>(n_cv);
+        V.atoms = d_at;
+        CK(cudaDeviceSynchronize());
+        launch_dafed_probe(S, V, c, d_out, nullptr);
+        CK(cudaMemcpy(out, d_out, sizeof(double) * n_cv, cudaMemcpyDeviceToHost));
+        dfree(d_at);
+        dfree(d_out);
+        for (int k = 0; k < n_cv; ++k)
+            if (!std::isfinite(out[k])) fail(LFE_ERR_ARG, "no movable atom in a torsion");
+    }
+
+    // checkpoint layout: header | x | v | xref | LamState | OpesState | centre | weight | S | TI sums |
+    // TI counts | d-AFED s | d-AFED p | checksum
     struct CkHeader {
         char magic[8];
-        int version, precision, n, max_k;
+        int version, precision, n, max_k, n_cv, pad;
     };
 
     void checkpoint(const char* path) override
@@ -1167,10 +1327,11 @@ struct System final : SystemBase {
         check_flags(nullptr);
         CkHeader h{};
         std::memcpy(h.magic, "LFECKPT1", 8);
-        h.version = 1;
+        h.version = 2;
         h.precision = precision;
         h.n = n;
         h.max_k = T.max_k;
+        h.n_cv = D.n;
         std::vector<unsigned char> buf;
         auto put = [&](const void* p, size_t sz) {
             const unsigned char* c = static_cast<const unsigned char*>(p);
@@ -1190,6 +1351,12 @@ struct System final : SystemBase {
         put_dev(T.centre, sizeof(double) * 2 * T.max_k);
         put_dev(T.weight, sizeof(double) * 2 * T.max_k);
         put_dev(T.S, sizeof(double) * 2 * T.max_k);
+        put_dev(T.ti_sum, sizeof(double) * LFE_TI_BINS);
+        put_dev(T.ti_cnt, sizeof(unsigned long long) * LFE_TI_BINS);
+        if (D.n) {
+            put_dev(D.s, sizeof(double) * D.n);
+            put_dev(D.p, sizeof(double) * D.n);
+        }
         uint64_t cs_ = fnv1a(buf.data(), buf.size());
         put(&cs_, sizeof(cs_));
         FILE* f = std::fopen(path, "wb");
@@ -1209,15 +1376,16 @@ struct System final : SystemBase {
         while ((r = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
         std::fclose(f);
         const size_t body = sizeof(CkHeader) + 3 * sizeof(R4<real>) * n + sizeof(LamState) + sizeof(OpesState) +
-                            3 * sizeof(double) * 2 * T.max_k;
+                            3 * sizeof(double) * 2 * T.max_k + (sizeof(double) + sizeof(unsigned long long)) * LFE_TI_BINS +
+                            2 * sizeof(double) * D.n;
         if (buf.size() != body + sizeof(uint64_t)) fail(LFE_ERR_ARG, "checkpoint size does not match this system");
         uint64_t stored;
         std::memcpy(&stored, buf.data() + body, sizeof(stored));
         if (stored != fnv1a(buf.data(), body)) fail(LFE_ERR_ARG, "checkpoint checksum mismatch");
         CkHeader h;
         std::memcpy(&h, buf.data(), sizeof(h));
-        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 1 || h.precision != precision || h.n != n ||
-            h.max_k != T.max_k)
+        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 2 || h.precision != precision || h.n != n ||
+            h.max_k != T.max_k || h.n_cv != D.n)
             fail(LFE_ERR_ARG, "checkpoint header does not match this system");
         size_t off = sizeof(CkHeader);
         auto get_dev = [&](void* d, size_t sz) {
@@ -1238,6 +1406,12 @@ struct System final : SystemBase {
         get_dev(T.centre, sizeof(double) * 2 * T.max_k);
         get_dev(T.weight, sizeof(double) * 2 * T.max_k);
         get_dev(T.S, sizeof(double) * 2 * T.max_k);
+        get_dev(T.ti_sum, sizeof(double) * LFE_TI_BINS);
+        get_dev(T.ti_cnt, sizeof(unsigned long long) * LFE_TI_BINS);
+        if (D.n) {
+            get_dev(D.s, sizeof(double) * D.n);
+            get_dev(D.p, sizeof(double) * D.n);
+        }
         int zero[FL_N] = {0, 0, 0, 0};
         CK(cudaMemcpy(S.flags, zero, sizeof(int) * 2, cudaMemcpyHostToDevice));
         build_neighbors(nullptr);
@@ -1626,6 +1800,27 @@ int lfe_set_solute_params(lfe_system* sys, const double* charge, const double* s
     return guard(sys, [&] {
         sys->impl->set_solute_params(charge, sigma, epsilon, on_device, (cudaStream_t)stream);
     });
+}
+
+int lfe_set_dafed(lfe_system* sys, int n_cv, const int* atoms, const double* kappa, const double* mass,
+                  double temperature, double friction, const double* s0)
+{
+    return guard(sys, [&] { sys->impl->set_dafed(n_cv, atoms, kappa, mass, temperature, friction, s0); });
+}
+
+int lfe_dafed_state(lfe_system* sys, double* s, double* p_s, double* xi)
+{
+    return guard(sys, [&] { sys->impl->dafed_state(s, p_s, xi); });
+}
+
+int lfe_dafed_masses(lfe_system* sys, int n_cv, const int* atoms, double c, double* mass_out)
+{
+    return guard(sys, [&] { sys->impl->dafed_masses(n_cv, atoms, c, mass_out); });
+}
+
+int lfe_ti(lfe_system* sys, double* mean, double* count, double* delta_g, int reset)
+{
+    return guard(sys, [&] { sys->impl->ti(mean, count, delta_g, reset); });
 }
 
 int lfe_step(lfe_system* sys, int n_steps, void* stream)

@@ -28,7 +28,7 @@ enum {
     E_EXCL_VV, E_EXCL_UU, E_EXCL_UV,
     E_14_VV, E_14_UU, E_14_UV,
     E_REC_VV, E_REC_UU, E_REC_UV,
-    E_BONDED, E_NPAIRS,
+    E_BONDED, E_NPAIRS, E_DAFED,
     E_N = 16
 };
 

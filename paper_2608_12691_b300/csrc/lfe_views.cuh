@@ -3,6 +3,7 @@
 #pragma once
 #include <string>
 
+#include "lfe.h"
 #include "lfe_dev.cuh"
 
 namespace lfe {
@@ -151,6 +152,21 @@ struct StepView {
     real* noise;               // [3 n] Ornstein-Uhlenbeck kicks of the step, formed ahead by k_noise
 };
 
+// d-AFED (Eq. 15): torsions coupled harmonically to auxiliary angles that
+// have their own mass and temperature
+struct DafedView {
+    int n;                    // coupled torsions (0: off)
+    const int4* atoms;        // [n] (i, j, k, l)
+    const double* kappa;      // [n] kJ mol^-1 rad^-2
+    const double* mass;       // [n] amu nm^2 rad^-2
+    double* s;                // [n] auxiliary angles, [-pi, pi)
+    double* p;                // [n] their momenta
+    double* fs;               // [n] force on s of the last evaluation, kappa (xi - s)
+    double* xi;               // [n] torsion values of the last evaluation
+    double dt, a_fric, kT;    // time step, exp(-gamma dt), k_B T of the auxiliary variables
+    uint2 key;
+};
+
 // values of the theta step that depend only on the state at its start,
 // formed while the forces are evaluated
 struct ThetaPre {
@@ -176,6 +192,8 @@ struct ThetaView {
     cudaGraphConditionalHandle cond;
     int use_cond;
     ThetaPre* pre;
+    double* ti_sum;                 // [LFE_TI_BINS] sum of dU/dlambda per lambda bin (Eq. 2)
+    unsigned long long* ti_cnt;     // [LFE_TI_BINS] samples per bin
 };
 
 // FP64 geometry and Ewald constants of the parameter-gradient kernel
@@ -219,6 +237,14 @@ template <typename real> void planes_setup(const PmeView<real>& p);
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
 template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+// d-AFED: forces of Eq. 15 on the atoms and the auxiliary variables (with
+// the coupling energy), and the auxiliary variables' step
+template <typename real> void launch_dafed_force(const SysView<real>& s, const DafedView& d, cudaStream_t st);
+template <typename real> void launch_dafed_step(const SysView<real>& s, const DafedView& d, cudaStream_t st);
+// torsion values of d's atoms at the current positions into out[n]; with
+// c > 0, the masses of Eq. 16 (c [sum_i |d xi / d r_i|^2 / m_i]^-1) instead
+template <typename real> void launch_dafed_probe(const SysView<real>& s, const DafedView& d, double c, double* out,
+                                                 cudaStream_t st);
 // the parts of the integrators that do not depend on the step's forces (the
 // atoms' random kicks, the OPES bias at the current theta): launched
 // alongside the force evaluation

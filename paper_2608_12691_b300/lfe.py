@@ -23,12 +23,14 @@ LFE_FP32_MIXED = 0
 LFE_FP64 = 1
 NTERMS = 10
 NEXT = 9
+TI_BINS = 100
 TERM_NAMES = ["U", "dUdl", "U_vv", "U_uu", "U_uv", "U_soft", "U_bonded", "n_pairs", "hA", "hB"]
 
 EXPORTED = [
     "lfe_create", "lfe_set_positions", "lfe_set_velocities", "lfe_set_integrator",
     "lfe_build_neighbors", "lfe_eval",
-    "lfe_param_grad", "lfe_set_solute_params", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
+    "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
+    "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
     "lfe_time_stages", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
     "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
@@ -107,6 +109,10 @@ def load():
     lib.lfe_param_grad.argtypes = [vp, ctypes.c_double, vp, vp, vp, ctypes.c_int, vp]
     lib.lfe_set_solute_params.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
     lib.lfe_step.argtypes = [vp, ctypes.c_int, vp]
+    lib.lfe_ti.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+    lib.lfe_set_dafed.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp]
+    lib.lfe_dafed_state.argtypes = [vp, vp, vp, vp]
+    lib.lfe_dafed_masses.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, vp]
     lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
     lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
@@ -341,6 +347,45 @@ class System:
         """Same, from float64 device buffers of n_u entries (None = unchanged)."""
         self._check(self._lib.lfe_set_solute_params(self.h, charge_ptr, sigma_ptr, epsilon_ptr, 1,
                                                     _stream_ptr(stream)))
+
+    def ti(self, reset=False):
+        """Eq. 2 estimator: (bin means [TI_BINS] with NaN for empty bins,
+        sample counts [TI_BINS], Delta G)."""
+        mean = np.zeros(TI_BINS)
+        count = np.zeros(TI_BINS)
+        dg = np.zeros(1)
+        self._check(self._lib.lfe_ti(self.h, mean.ctypes.data, count.ctypes.data, dg.ctypes.data, int(reset)))
+        return mean, count, float(dg[0])
+
+    def set_dafed(self, atoms, kappa, mass, temperature=1000.0, friction=25.0, s0=None):
+        """Couple torsions (rows of 4 atom indices) to auxiliary angles (Eq. 15)."""
+        atoms = np.ascontiguousarray(atoms, dtype=np.int32).reshape(-1, 4)
+        k = atoms.shape[0]
+        kappa = np.ascontiguousarray(np.broadcast_to(kappa, (k,)), dtype=np.float64)
+        mass = np.ascontiguousarray(np.broadcast_to(mass, (k,)), dtype=np.float64)
+        s0a = None if s0 is None else np.ascontiguousarray(s0, dtype=np.float64).reshape(k)
+        self._dafed_n = k
+        self._check(self._lib.lfe_set_dafed(self.h, k, atoms.ctypes.data, kappa.ctypes.data, mass.ctypes.data,
+                                            float(temperature), float(friction),
+                                            None if s0a is None else s0a.ctypes.data))
+
+    def dafed_state(self):
+        """(s, p_s, xi at the current positions), each [n_cv]."""
+        k = getattr(self, "_dafed_n", 0)
+        s = np.zeros(k)
+        p = np.zeros(k)
+        xi = np.zeros(k)
+        if k:
+            self._check(self._lib.lfe_dafed_state(self.h, s.ctypes.data, p.ctypes.data, xi.ctypes.data))
+        return s, p, xi
+
+    def dafed_masses(self, atoms, c=300.0):
+        """Eq. 16 auxiliary masses at the current positions."""
+        atoms = np.ascontiguousarray(atoms, dtype=np.int32).reshape(-1, 4)
+        out = np.zeros(atoms.shape[0])
+        self._check(self._lib.lfe_dafed_masses(self.h, atoms.shape[0], atoms.ctypes.data, float(c),
+                                               out.ctypes.data))
+        return out
 
     def time_stages(self, lam, reps=10, stream=None, max_n=32):
         names = (ctypes.c_char_p * max_n)()

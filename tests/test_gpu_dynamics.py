@@ -32,9 +32,11 @@ def oracle_steps(d, nsteps):
     th, p = d["lam"], 0.0
     std = D.Opes("std", d["opes_dE_std"], d["opes_sigma"], d["temperature"])
     exp = D.Opes("exp", d["opes_dE_exp"], d["opes_sigma"], d["temperature"])
+    ti = D.TIAccumulator()
     for step in range(nsteps):
         lam, dl = D.theta_to_lambda(th)
         e = R.evaluate(d, lam, level=2, pos=x)
+        ti.add(lam, e["dUdl"])
         nrm = D.atom_normals(len(x), step, SEED)
         x, v = D.langevin_middle_step(x, v, e["F"], d["mass"], d["dt"], d["friction"], d["temperature"],
                                       nrm, d["box"], pairs, lens)
@@ -44,6 +46,7 @@ def oracle_steps(d, nsteps):
         if (step + 1) % d["opes_stride"] == 0:
             std.deposit(th)
             exp.deposit(th)
+    oracle_steps.ti = ti
     return x, v, th, p, std, exp
 
 
@@ -130,3 +133,31 @@ def test_forces_stay_exact_when_atoms_cross_the_box_between_builds(precision):
     t, F = g.eval(lam)
     o = R.evaluate(d, lam, level=2, pos=pos)
     assert np.linalg.norm(F - o["F"]) / np.linalg.norm(o["F"]) <= tol
+
+
+def test_ti_accumulators_match_oracle_and_survive_checkpoint(tmp_path):
+    # the mean force of every step lands in the same lambda bin with the same
+    # value as in the oracle's steps; a checkpoint carries the accumulators
+    d = water_system()
+    n = 4
+    g = lfe.System(d, precision=lfe.LFE_FP64, seed=SEED)
+    g.step(n)
+    mean, count, dg = g.ti()
+    oracle_steps(d, n)
+    ti = oracle_steps.ti
+    assert np.array_equal(count, ti.count.astype(float))
+    occ = ti.count > 0
+    om = ti.means()
+    # the trajectories agree to ~1e-8 nm after these steps (test_steps_match_oracle),
+    # so the sampled dU/dlambda agree to ~1e-7 relative
+    assert np.all(np.abs(mean[occ] - om[occ]) <= 1e-6 * np.maximum(1.0, np.abs(om[occ])))
+    assert np.all(np.isnan(mean[~occ]))
+    assert dg == pytest.approx(ti.delta_g(), rel=1e-6, abs=1e-6)
+    path = tmp_path / "ti.ckpt"
+    g.checkpoint(path)
+    g2 = lfe.System(d, precision=lfe.LFE_FP64, seed=SEED)
+    g2.restore(path)
+    mean2, count2, dg2 = g2.ti(reset=True)
+    assert np.array_equal(count2, count) and dg2 == dg
+    _, count3, _ = g2.ti()
+    assert count3.sum() == 0
