@@ -328,13 +328,18 @@ struct System final : SystemBase {
         N.n_cl_solv = dalloc<int>(1);
         N.bbc = dalloc<R4<float>>(n_cl);
         N.bbh = dalloc<R4<float>>(n_cl);
-        N.tile_cnt = dalloc<int>(27 * (size_t)n_cl);
-        N.tile_tot = dalloc<int>(n_cl);
-        N.tile_off = dalloc<int>((size_t)n_cl + 1);
+        N.bbc8 = dalloc<R4<float>>(4 * (size_t)n_cl);
+        N.bbh8 = dalloc<R4<float>>(4 * (size_t)n_cl);
+        N.tile_cnt = dalloc<int>(27 * 4 * (size_t)n_cl);
+        N.tile_tot = dalloc<int>(4 * (size_t)n_cl);
+        N.tile_off = dalloc<int>(4 * (size_t)n_cl + 1);
         N.cap = 1024;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
-        N.masks = dalloc<unsigned>((size_t)N.cap * 32);
+        N.masks = dalloc<unsigned>((size_t)N.cap * 8);
+        N.stage_cap = N.cap;
+        N.stage_hdr = dalloc<int4>(N.stage_cap);
+        N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
         N.uv_tiles_max = std::max(1, n_ucl * 512);
         N.uv_cnt = dalloc<int>(N.uv_tiles_max);
         N.uv_off = dalloc<int>(N.uv_tiles_max + 1);
@@ -633,6 +638,7 @@ struct System final : SystemBase {
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
         pair_warps = nsm * 32;
         uv_blocks = nsm * 2;
+        N.n_sm = nsm;
         {
             const char* ev = std::getenv("LFE_EAGER_STEPS");
             eager = ev && ev[0] == '1';
@@ -749,17 +755,30 @@ struct System final : SystemBase {
         if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     }
 
-    void grow_tiles(int need)
+    // tile list of `need` tiles and a staging list of at least `need_stage`
+    // (the staging list holds the same tiles before they are placed)
+    void grow_tiles(int need, int need_stage = 0)
     {
         ++generation;
         dfree(N.tiles);
         dfree(N.jidx);
         dfree(N.masks);
+        dfree(N.stage_hdr);
+        dfree(N.stage_j);
         N.cap = need + 256;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
-        N.masks = dalloc<unsigned>((size_t)N.cap * 32);
+        N.masks = dalloc<unsigned>((size_t)N.cap * 8);
+        N.stage_cap = std::max(N.cap, need_stage + 256);
+        N.stage_hdr = dalloc<int4>(N.stage_cap);
+        N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
         invalidate_graph();
+    }
+
+    // growth after an overflow seen in the flags
+    void grow_for_flags()
+    {
+        grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2, 2 * h_flags[FL_NSTAGE]);
     }
 
     void build_neighbors(cudaStream_t st) override
@@ -767,8 +786,8 @@ struct System final : SystemBase {
         launch_build_nbl(S, N, st);
         CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (h_flags[FL_NTILES] > N.cap) {
-            grow_tiles(2 * h_flags[FL_NTILES]);
+        if (h_flags[FL_NTILES] > N.cap || h_flags[FL_NSTAGE] > N.stage_cap) {
+            grow_tiles(2 * h_flags[FL_NTILES], 2 * h_flags[FL_NSTAGE]);
             int zero = 0;
             CK(cudaMemcpy(S.flags + FL_ERROR, &zero, sizeof(int), cudaMemcpyHostToDevice));
             launch_build_nbl(S, N, st);
@@ -832,7 +851,7 @@ struct System final : SystemBase {
         if (h_flags[FL_ERROR] & ERRB_OVERFLOW) {
             int clr[2] = {0, 0};
             CK(cudaMemcpy(S.flags, clr, sizeof(clr), cudaMemcpyHostToDevice));
-            grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2);
+            grow_for_flags();
             build_neighbors(st);
         }
     }
@@ -1125,7 +1144,7 @@ struct System final : SystemBase {
             CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
             const unsigned long long done = L.step - step_base;
             const long long missing = (long long)steps_requested - (long long)done;
-            grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2);
+            grow_for_flags();
             int clr[2] = {0, 0};
             CK(cudaMemcpy(S.flags, clr, sizeof(clr), cudaMemcpyHostToDevice));
             build_neighbors(st);

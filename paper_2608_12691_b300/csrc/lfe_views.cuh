@@ -62,12 +62,17 @@ struct NblView {
     int n_cl_max;         // capacity in clusters
     R4<float>* bbc;       // cluster bounding-box centres [n_cl_max]
     R4<float>* bbh;       // half extents [n_cl_max]
-    int* tile_cnt;        // [27 n_cl_max] tiles per (i-cluster, shift), then offsets inside the cluster
-    int* tile_tot;        // [n_cl_max] tiles per i-cluster (zeroed by the scan)
-    int* tile_off;        // [n_cl_max + 1] first tile of each i-cluster
-    int4* tiles;          // [cap]  (I, shift code, class, diagonal)
+    R4<float>* bbc8;      // 8-slot sub-cluster boxes [4 n_cl_max] (the i side of the tiles)
+    R4<float>* bbh8;      // their half extents (w < 0: no atoms)
+    int* tile_cnt;        // [27 x 4 n_cl_max] tiles per (i sub-cluster, shift), then offsets inside it
+    int* tile_tot;        // [4 n_cl_max] tiles per i sub-cluster (zeroed by the scan)
+    int* tile_off;        // [4 n_cl_max + 1] first tile of each i sub-cluster
+    int4* stage_hdr;      // [stage_cap] tiles as found: (I8, shift, class, ordinal in (I8, shift); -1 = unused)
+    int* stage_j;         // [stage_cap * 32] their j slots
+    int stage_cap;
+    int4* tiles;          // [cap]  (I8, shift code, class, -)
     int* jidx;            // [cap * 32] j slots of each tile (-1 = empty)
-    unsigned* masks;      // [cap * 32]
+    unsigned* masks;      // [cap * 8] one row of 32 j bits per i atom
     int cap;
     float cut2;           // (r_cut + skin)^2
     float skin_half2;     // (skin / 2)^2
@@ -80,6 +85,7 @@ struct NblView {
     int4* uvp;            // [uv_cap] (slot_i, slot_j, shift code, -)
     int uv_cap;
     int uv_tiles_max;     // capacity of uv_cnt / uv_off
+    int n_sm;             // multiprocessors of the device (grid-stride kernels)
 };
 
 template <typename real>

@@ -228,11 +228,15 @@ __device__ __forceinline__ int num_clusters(const SysView<real>& s, const NblVie
     return s.n_ucl + *nb.n_cl_solv;
 }
 
+// Bounding boxes of every 32-atom cluster (the partner side of the tile
+// search) and of its four 8-slot sub-clusters (the i side of the tiles).  A
+// sub-cluster without atoms gets a negative half extent (no tiles).
 template <typename real>
 __global__ void k_bbox(SysView<real> s, NblView<real> nb)
 {
     const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) s.flags[FL_NSTAGE] = 0;   // the tile staging list starts empty
     if (c >= num_clusters(s, nb)) return;
     const int slot = c * 32 + lane;
     const bool ok = s.perm[slot] >= 0;
@@ -242,20 +246,30 @@ __global__ void k_bbox(SysView<real> s, NblView<real> nb)
     for (int d = 0; d < 3; ++d) {
         lo[d] = ok ? pv[d] : 3.0e38f;
         hi[d] = ok ? pv[d] : -3.0e38f;
-        for (int o = 16; o > 0; o >>= 1) {
-            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
-        }
     }
-    if (lane == 0) {
+    auto emit = [&](R4<float>* cen, R4<float>* half, int idx) {
         R4<float> cc, hh;
+        const bool any = lo[0] <= hi[0];
         cc.x = 0.5f * (lo[0] + hi[0]); cc.y = 0.5f * (lo[1] + hi[1]); cc.z = 0.5f * (lo[2] + hi[2]); cc.w = 0.f;
         // a tiny outward margin keeps the float box conservative
         hh.x = 0.5f * (hi[0] - lo[0]) + 1e-5f; hh.y = 0.5f * (hi[1] - lo[1]) + 1e-5f;
-        hh.z = 0.5f * (hi[2] - lo[2]) + 1e-5f; hh.w = 0.f;
-        nb.bbc[c] = cc;
-        nb.bbh[c] = hh;
-    }
+        hh.z = 0.5f * (hi[2] - lo[2]) + 1e-5f; hh.w = any ? 0.f : -1.f;
+        if (!any) cc.x = cc.y = cc.z = hh.x = hh.y = hh.z = 0.f;
+        cen[idx] = cc;
+        half[idx] = hh;
+    };
+    for (int o = 4; o > 0; o >>= 1)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    if ((lane & 7) == 0) emit(nb.bbc8, nb.bbh8, c * 4 + (lane >> 3));
+    for (int o = 16; o > 4; o >>= 1)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
+    if (lane == 0) emit(nb.bbc, nb.bbh, c);
 }
 
 // shift code sh = (sx+1) + 3 (sy+1) + 9 (sz+1): cluster J is taken at x_J + s L
@@ -283,49 +297,50 @@ __device__ __forceinline__ float box_gap2(const SysView<real>& s, const R4<float
     return d2;
 }
 
-// Tile list.  One warp per (i-cluster I, periodic shift): 27 warps per
-// cluster.  The shift-13 warp (no shift) writes I's diagonal tile (I with
-// itself, pairs j > i) first.  Then, for each class of partner cluster
-// (solute, solvent), every atom of every partner cluster J >= I (J == I only
-// for the upper half of the shifts, so each pair image is visited once)
-// whose distance to I's bounding box is below r_cut + skin is appended to a
-// j list, 32 atoms per tile.  A tile therefore has one shift and one class,
-// and the tiles of one I are contiguous (shift-major).  The warp first lists
-// the partner clusters whose boxes are in range (independent box tests, four
-// chunks of 32 boxes in flight), then filters their atoms eight clusters at a
-// time, so that the chain of dependent loads stays short.  WRITE = 0 counts
-// tiles per (I, shift), WRITE = 1 writes them at the offsets formed by
-// k_tile_prefix (within I) and the scan over clusters.
+// Tile list.  A tile pairs the 8 atoms of one i sub-cluster I8 (slots
+// 8 I8 .. 8 I8 + 7 of the cluster-sorted order) with 32 j atoms under one
+// periodic shift and one class (vv, uu or uv).  One warp per (I8, shift):
+// for each class of partner cluster (solute, solvent) every atom of every
+// 32-atom partner cluster J whose box is within r_cut + skin of I8's box is
+// appended to a j list when the atom itself is within r_cut + skin of that
+// box and lies in a sub-cluster J8 > I8, or in I8 itself under a shift past
+// the middle one (13), or in I8 under no shift (pairs j > i, left to the
+// masks) -- so every pair image is listed once.  The warp first lists the
+// partner clusters whose boxes are in range (four chunks of 32 boxes in
+// flight), then filters their atoms TILE_BATCH clusters per batch of loads.
+//
+// One pass: each round (up to TILE_CAND partner clusters) first filters the
+// atoms, then reserves exactly the tiles it starts in a staging list -- in
+// the order warps happen to get there -- and writes them with their (I8,
+// shift, class, ordinal).  k_place then moves every tile to its final,
+// deterministic place (the tiles of one I8 contiguous and shift-major) from
+// the per-(I8, shift) counts written here.
 constexpr int TILE_CAND = 128;     // partner clusters listed per round (per warp)
 constexpr int TILE_BATCH = 8;      // partner clusters whose atoms are loaded together
 
-template <typename real, int WRITE>
+template <typename real>
 __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb)
 {
     __shared__ int cand_sh[4][TILE_CAND];
+    __shared__ unsigned kb_sh[4][TILE_CAND];
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     int* cand = cand_sh[(threadIdx.x >> 5) & 3];
-    if (w >= nb.n_cl_max * 27) return;
-    const int I = w / 27, sh = w - I * 27;
+    unsigned* kb = kb_sh[(threadIdx.x >> 5) & 3];
+    if (w >= nb.n_cl_max * 4 * 27) return;
+    const int I8 = w / 27, sh = w - I8 * 27;
+    const int I = I8 >> 2;
     const int ncl = num_clusters(s, nb);
-    if (I >= ncl) {
-        if (!WRITE && lane == 0) nb.tile_cnt[w] = 0;
+    const R4<float> ci = nb.bbc8[I8], hi = nb.bbh8[I8];
+    if (I >= ncl || hi.w < 0.f) {
+        if (lane == 0) nb.tile_cnt[w] = 0;
         return;
     }
-    const R4<float> ci = nb.bbc[I], hi = nb.bbh[I];
     const bool iu = I < s.n_ucl;
-    const int base = WRITE ? nb.tile_off[I] + nb.tile_cnt[w] : 0;
-    int count = 0;
-    if (sh == 13) {
-        if (WRITE && base < nb.cap) {
-            nb.jidx[(size_t)base * 32 + lane] = s.perm[I * 32 + lane] >= 0 ? I * 32 + lane : -1;
-            if (lane == 0) nb.tiles[base] = make_int4(I, 13, iu ? 1 : 0, 1);
-        }
-        count = 1;
-    }
+    int count = 0;        // tiles started by this warp (the next tile's ordinal)
+    bool dead = false;    // the staging list ran out: nothing more is written
     // every atom lies in [0, L): a shift -1 (+1) along an axis can bring a
-    // partner within the cutoff only if I's box reaches within r_cut + skin
+    // partner within the cutoff only if I8's box reaches within r_cut + skin
     // of the lower (upper) face
     const float cut = sqrtf(nb.cut2);
     int svs[3];
@@ -342,10 +357,13 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
     if (allowed) {
         const float shx = svs[0] * (float)s.L[0], shy = svs[1] * (float)s.L[1], shz = svs[2] * (float)s.L[2];
         const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
+        // sub-clusters of partner atoms that may pair with I8 under this shift
+        const int j8min = sh >= 13 ? I8 : I8 + 1;
         for (int jc = 0; jc < 2; ++jc) {
             const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
             const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
-            int nbuf = 0;   // atoms already placed in the open tile
+            int nbuf = 0;   // atoms already placed in the open tile (staging slot cur)
+            int cur = -1;
             int J0 = max(I, jb);
             while (J0 < je) {
                 // list the partner clusters in range, in ascending order
@@ -355,7 +373,7 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int J = J0 + 32 * u + lane;
-                        pc[u] = J < je && (J != I || sh > 13);
+                        pc[u] = J < je && 4 * J + 3 >= j8min;
                         if (pc[u]) pc[u] = box_gap2(s, ci, hi, nb.bbc[J], nb.bbh[J], sh) < nb.cut2;
                     }
 #pragma unroll
@@ -367,16 +385,18 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
                     J0 += 128;
                 }
                 __syncwarp();
-                // filter their atoms, TILE_BATCH clusters per batch of loads
+                if (nc == 0) continue;
+                // filter their atoms, TILE_BATCH clusters per batch of loads;
+                // the kept lanes of candidate c go to kb[c]
+                int K = 0;
                 for (int c0i = 0; c0i < nc; c0i += TILE_BATCH) {
                     R4<real> pbuf[TILE_BATCH];
                     bool live[TILE_BATCH];
-                    int slots[TILE_BATCH];
 #pragma unroll
                     for (int u = 0; u < TILE_BATCH; ++u) {
-                        slots[u] = c0i + u < nc ? cand[c0i + u] * 32 + lane : -1;
-                        live[u] = slots[u] >= 0 && s.perm[slots[u]] >= 0;
-                        if (slots[u] >= 0) pbuf[u] = s.xq[slots[u]];
+                        const int slot = c0i + u < nc ? cand[c0i + u] * 32 + lane : -1;
+                        live[u] = slot >= 0 && (slot >> 3) >= j8min && s.perm[slot] >= 0;
+                        if (slot >= 0) pbuf[u] = s.xq[slot];
                     }
 #pragma unroll
                     for (int u = 0; u < TILE_BATCH; ++u) {
@@ -392,84 +412,165 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
                             }
                             keep = d2 < nb.cut2;
                         }
-                        const unsigned kb = __ballot_sync(0xffffffffu, keep);
-                        if (WRITE && keep) {
-                            const int pos = nbuf + __popc(kb & lt);
-                            const int t = base + count + (pos >> 5);
-                            if (t < nb.cap) nb.jidx[(size_t)t * 32 + (pos & 31)] = slots[u];
-                        }
-                        nbuf += __popc(kb);
-                        while (nbuf >= 32) {
-                            if (WRITE && lane == 0 && base + count < nb.cap)
-                                nb.tiles[base + count] = make_int4(I, sh, cls, 0);
-                            ++count;
-                            nbuf -= 32;
-                        }
+                        const unsigned kbu = __ballot_sync(0xffffffffu, keep);
+                        if (lane == 0) kb[c0i + u] = kbu;
+                        K += __popc(kbu);
+                    }
+                }
+                __syncwarp();
+                // reserve exactly the tiles this round starts
+                // (none when the kept atoms all fit in the open tile)
+                if (K == 0) continue;
+                const int nnew = (nbuf + K + 31) / 32 - (nbuf > 0 ? 1 : 0);
+                int r0 = 0;
+                if (lane == 0 && nnew > 0) r0 = atomicAdd(s.flags + FL_NSTAGE, nnew);
+                r0 = __shfl_sync(0xffffffffu, r0, 0);
+                if (!dead && r0 + nnew > nb.stage_cap) {
+                    dead = true;
+                    if (lane == 0) atomicOr(s.flags + FL_ERROR, ERRB_OVERFLOW);
+                    // the open tile keeps what it has
+                    if (nbuf > 0 && lane >= nbuf) nb.stage_j[(size_t)cur * 32 + lane] = -1;
+                }
+                if (dead) {
+                    // the reserved slots inside the list are marked unused
+                    for (int k = r0 + lane; k < min(r0 + nnew, nb.stage_cap); k += 32)
+                        nb.stage_hdr[k] = make_int4(0, 0, 0, -1);
+                    count += nnew;
+                    nbuf = (nbuf + K) & 31;
+                    continue;
+                }
+                int rused = 0;
+                for (int c = 0; c < nc; ++c) {
+                    const unsigned kbu = kb[c];
+                    if (kbu == 0u) continue;
+                    const int nk = __popc(kbu);
+                    // the open tile (or a new one), and the tile after it if the
+                    // kept atoms run past 32
+                    int slotA = cur;
+                    if (nbuf == 0) {
+                        slotA = r0 + rused++;
+                        if (lane == 0) nb.stage_hdr[slotA] = make_int4(I8, sh, cls, count);
+                        ++count;
+                    }
+                    int slotB = -1;
+                    if (nbuf + nk > 32) {
+                        slotB = r0 + rused++;
+                        if (lane == 0) nb.stage_hdr[slotB] = make_int4(I8, sh, cls, count);
+                        ++count;
+                    }
+                    if ((kbu >> lane) & 1u) {
+                        const int pos = nbuf + __popc(kbu & lt);
+                        nb.stage_j[(size_t)(pos < 32 ? slotA : slotB) * 32 + (pos & 31)] = cand[c] * 32 + lane;
+                    }
+                    nbuf += nk;
+                    if (nbuf >= 32) {
+                        nbuf -= 32;
+                        cur = slotB;
+                    } else {
+                        cur = slotA;
                     }
                 }
                 __syncwarp();
             }
-            if (nbuf > 0) {
-                if (WRITE && base + count < nb.cap) {
-                    if (lane >= nbuf) nb.jidx[(size_t)(base + count) * 32 + lane] = -1;
-                    if (lane == 0) nb.tiles[base + count] = make_int4(I, sh, cls, 0);
-                }
-                ++count;
-            }
+            if (nbuf > 0 && !dead && lane >= nbuf) nb.stage_j[(size_t)cur * 32 + lane] = -1;
         }
     }
-    if (!WRITE && lane == 0) nb.tile_cnt[w] = count;
+    if (lane == 0) nb.tile_cnt[w] = count;
 }
 
-// interaction masks: bit k of lane i set = pair (I*32+i, jidx[k]) is
-// computed: both slots hold atoms, the pair is not excluded, and in the
-// diagonal tile k > i.  Exclusions are searched only when the tile holds
-// atoms of lane i's molecule: each excluded partner's slot is looked up in
-// the tile's ascending j slots by bisection.
+// Placement and interaction masks.  Every staged tile goes to its place
+// tile_off[I8] + (tiles of I8 under lower shifts) + ordinal.  Mask: one
+// 32-bit row per i atom (8 rows), bit k set = pair (8 I8 + r, jidx[k]) is
+// computed: both slots hold atoms, the pair is not excluded, and for a j atom
+// of I8 itself under no shift, j > i.  A warp takes four staged tiles at a
+// time (lane = 8 tile + row), grid-striding over the staging list.
+// Exclusions are searched only for rows whose molecule appears among the j
+// atoms: each excluded partner's slot is looked up in the tile's ascending j
+// slots by bisection.
+constexpr int PLACE_BLOCKS_PER_SM = 16;
+
 template <typename real>
-__global__ void __launch_bounds__(128) k_masks(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb)
 {
-    __shared__ int jsl[4][32];
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    __shared__ int jsl[4][4][33];   // [warp][tile][k]: j slot (INT_MAX if empty)
+    __shared__ int jmol[4][4][33];  // [warp][tile][k]: j molecule (-2 if empty)
     const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
-    const int nt = min(s.flags[FL_NTILES], nb.cap);
-    if (t >= nt) return;
-    const int4 tl = nb.tiles[t];
-    const int js = nb.jidx[(size_t)t * 32 + lane];
-    const int b = js >= 0 ? s.perm[js] : -1;
-    const int mb = b >= 0 ? nb.mol[b] : -2;
-    const int a = s.perm[tl.x * 32 + lane];
-    const int ma = a >= 0 ? nb.mol[a] : -3;
-    jsl[wl][lane] = js >= 0 ? js : 0x7fffffff;
-    __syncwarp();
-    const unsigned valid = __ballot_sync(0xffffffffu, b >= 0);
-    unsigned m = 0u, same = 0u;
-    for (int k = 0; k < 32; ++k) {
-        const int mk = __shfl_sync(0xffffffffu, mb, k);
-        same |= (mk == ma ? 1u : 0u) << k;
-    }
-    if (a >= 0) {
-        m = valid;
-        if (tl.w) m &= lane == 31 ? 0u : (0xffffffffu << (lane + 1));
-    }
-    if (m & same) {
-        for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e) {
-            const int sb = s.iperm[nb.ex_list[e]];
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (jsl[wl][mid] < sb) lo = mid + 1;
-                else hi = mid;
-            }
-            if (jsl[wl][lo] == sb) m &= ~(1u << lo);
+    const int g = lane >> 3, r = lane & 7;
+    const int nst = min(s.flags[FL_NSTAGE], nb.stage_cap);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; 4 * q < nst; q += nwarps) {
+        // the four tiles' loads are issued phase by phase
+        int4 h[4];
+        int dest[4], js[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h[u] = 4 * q + u < nst ? nb.stage_hdr[4 * q + u] : make_int4(0, 0, 0, -1);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            dest[u] = h[u].w >= 0 ? nb.tile_off[h[u].x] + nb.tile_cnt[h[u].x * 27 + h[u].y] + h[u].w : -1;
+            if (dest[u] >= nb.cap) dest[u] = -1;
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            js[u] = dest[u] >= 0 ? nb.stage_j[(size_t)(4 * q + u) * 32 + lane] : -1;
+            if (js[u] >= s.n_pad) js[u] = -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = js[u] >= 0 ? s.perm[js[u]] : -1;
+        unsigned valid = 0u;
+        int4 my = make_int4(0, 0, 0, -1);
+        int mydest = -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            jsl[wl][u][lane] = js[u] >= 0 ? js[u] : 0x7fffffff;
+            jmol[wl][u][lane] = b[u] >= 0 ? nb.mol[b[u]] : -2;
+            const unsigned bal = __ballot_sync(0xffffffffu, b[u] >= 0);
+            if (dest[u] >= 0) {
+                nb.jidx[(size_t)dest[u] * 32 + lane] = js[u];
+                if (lane == 0) nb.tiles[dest[u]] = make_int4(h[u].x, h[u].y, h[u].z, 0);
+            }
+            if (u == g) {
+                valid = bal;
+                my = h[u];
+                mydest = dest[u];
+            }
+        }
+        __syncwarp();
+        if (mydest >= 0) {
+            const int islot = my.x * 8 + r;
+            const int a = s.perm[islot];
+            const int ma = a >= 0 ? nb.mol[a] : -3;
+            const int* sl = jsl[wl][g];
+            unsigned same = 0u, before = 0u;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const int sk = sl[k];
+                same |= (jmol[wl][g][k] == ma ? 1u : 0u) << k;
+                // j slots of I8 itself at or before slot i (no shift): not computed
+                before |= (my.y == 13 && sk >= my.x * 8 && sk <= islot ? 1u : 0u) << k;
+            }
+            unsigned m = 0u;
+            if (a >= 0) m = valid & ~before;
+            if (m & same) {
+                for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e) {
+                    const int sb = s.iperm[nb.ex_list[e]];
+                    int lo = 0, hi = 31;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sl[mid] < sb) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    if (sl[lo] == sb) m &= ~(1u << lo);
+                }
+            }
+            nb.masks[(size_t)mydest * 8 + r] = m;
+        }
+        __syncwarp();
     }
-    nb.masks[(size_t)t * 32 + lane] = m;
 }
 
 // dense solute-solvent pair list: the computed pairs of the class-2 tiles
-// (solute cluster x solvent atoms) that lie within r_cut + skin at build
-// time, in (tile, i, k) order.  Lanes hold the tile's j atoms; the i atoms
+// (solute sub-cluster x solvent atoms) that lie within r_cut + skin at build
+// time, in (tile, i, k) order.  Lanes hold the tile's j atoms; the 8 i atoms
 // are broadcast one by one, so each row costs one ballot.
 template <typename real, int WRITE>
 __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real> nb)
@@ -477,24 +578,24 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= nb.uv_tiles_max) return;
-    const int nuvt = s.n_ucl > 0 ? min(nb.tile_off[s.n_ucl], nb.cap) : 0;
+    const int nuvt = s.n_ucl > 0 ? min(nb.tile_off[4 * s.n_ucl], nb.cap) : 0;
     if (t == 0 && lane == 0 && !WRITE && nuvt > nb.uv_tiles_max) atomicOr(&s.flags[FL_ERROR], ERRB_OVERFLOW);
-    unsigned keep = 0u;   // row of lane i: bits k of kept pairs (i, k)
+    unsigned keep = 0u;   // row of lane i < 8: bits k of kept pairs (i, k)
     int4 tl = make_int4(0, 13, 0, 0);
     int js = -1;
     if (t < nuvt) {
         tl = nb.tiles[t];
         if (tl.z == 2) {
             js = nb.jidx[(size_t)t * 32 + lane];
-            const unsigned mi = nb.masks[(size_t)t * 32 + lane];
-            const R4<real> pi = s.xq[tl.x * 32 + lane];
+            const unsigned mi = nb.masks[(size_t)t * 8 + (lane & 7)];
+            const R4<real> pi = s.xq[tl.x * 8 + (lane & 7)];
             const R4<real> pj = s.xq[js >= 0 ? js : 0];
             int sv[3];
             shift_vec(tl.y, sv);
             const float xj = (float)pj.x + sv[0] * (float)s.L[0];
             const float yj = (float)pj.y + sv[1] * (float)s.L[1];
             const float zj = (float)pj.z + sv[2] * (float)s.L[2];
-            for (int i = 0; i < 32; ++i) {
+            for (int i = 0; i < 8; ++i) {
                 const float xi = __shfl_sync(0xffffffffu, (float)pi.x, i);
                 const float yi = __shfl_sync(0xffffffffu, (float)pi.y, i);
                 const float zi = __shfl_sync(0xffffffffu, (float)pi.z, i);
@@ -519,7 +620,7 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
         if (lane >= o) pre += v;
     }
     int pos = nb.uv_off[t] + pre - cnt;
-    const int si = tl.x * 32 + lane;
+    const int si = tl.x * 8 + (lane & 7);
     for (int k = 0; k < 32; ++k) {
         const int jk = __shfl_sync(0xffffffffu, js, k);
         if ((keep >> k) & 1u) {
@@ -561,14 +662,14 @@ void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStrea
     k_assign<real><<<(s.n_pad + B - 1) / B, B, 0, st>>>(s, nb);
     const int wb = (nb.n_cl_max * 32 + 127) / 128;
     k_bbox<real><<<wb, 128, 0, st>>>(s, nb);
-    const int tb = (nb.n_cl_max * 27 * 32 + 127) / 128;
-    k_tiles<real, 0><<<tb, 128, 0, st>>>(s, nb);
-    k_tile_prefix<<<wb, 128, 0, st>>>(nb.tile_cnt, nb.tile_tot, nb.n_cl_max);
-    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_tot, nb.tile_off, nb.n_cl_max, s.flags + FL_NTILES, nb.cap,
+    const int tb = (nb.n_cl_max * 4 * 27 * 32 + 127) / 128;
+    k_tiles<real><<<tb, 128, 0, st>>>(s, nb);
+    k_tile_prefix<<<(nb.n_cl_max * 4 * 32 + 127) / 128, 128, 0, st>>>(nb.tile_cnt, nb.tile_tot, nb.n_cl_max * 4);
+    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_tot, nb.tile_off, nb.n_cl_max * 4, s.flags + FL_NTILES, nb.cap,
                                      s.flags + FL_ERROR);
-    k_tiles<real, 1><<<tb, 128, 0, st>>>(s, nb);
-    const int mb = (int)(((long long)nb.cap * 32 + 127) / 128);
-    k_masks<real><<<mb, 128, 0, st>>>(s, nb);
+    const long long pq = ((long long)nb.stage_cap + 15) / 16;   // blocks of four warps x four tiles
+    const long long pmax = (long long)nb.n_sm * PLACE_BLOCKS_PER_SM;
+    k_place<real><<<(int)(pq < pmax ? pq : pmax), 128, 0, st>>>(s, nb);
     if (s.n_ucl > 0) {
         const int ub = (nb.uv_tiles_max * 32 + 127) / 128;
         k_uv_pairs<real, 0><<<ub, 128, 0, st>>>(s, nb);
@@ -678,27 +779,30 @@ __device__ __forceinline__ PairConst<real> pair_const(const SysView<real>& s)
     return c;
 }
 
-// One tile by rotation: lane i holds i atom I*32+i (xi, yi, zi, qi, si, ei,
-// already shifted for the tile); the tile's 32 j atoms (pj, ljv, shifted)
-// rotate through the lanes by shuffles together with their force
-// accumulators (Newton's third law inside the tile).  m: lane i's mask row.
-// Adds the i-force to (fix, fiy, fiz), flushes the j-forces, returns the
-// lane's energy.
+// One tile by rotation: lane l = 8 g + r holds i atom 8 I8 + r (xit, yit,
+// zit, qi, si, ei, already shifted for the tile) and starts with j entry l
+// (pj, ljv, shifted); within each group of 8 lanes the j atoms rotate by
+// shuffles together with their force accumulators (Newton's third law), so
+// in 8 steps every (r, j entry of group g) pair is met once.  m8: bits of
+// row r for the 8 j entries of group g.  Adds the lane's share of the
+// i-force to (fix, fiy, fiz), flushes the j-forces, returns the lane's energy.
 template <typename real>
 __device__ __forceinline__ real tile_rotate(const SysView<real>& s, const PairConst<real>& c, real xit, real yit,
                                             real zit, real qi, real si, real ei, R4<real> pj, R2<real> ljv,
-                                            unsigned m, bool uv, int slot_j, long long& fix, long long& fiy,
+                                            unsigned m8, bool uv, int slot_j, long long& fix, long long& fiy,
                                             long long& fiz, int& npairs)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int src = (lane + 1) & 31;
+    const int r = lane & 7;
+    const int src = (lane & ~7) | ((r + 1) & 7);
     real xj = pj.x, yj = pj.y, zj = pj.z, qj = pj.w, sj = ljv.x, ej = ljv.y;
     real fjx = 0, fjy = 0, fjz = 0, fx = 0, fy = 0, fz = 0, e0 = 0;
-    // bit 0 of mr is the mask bit of the j atom this lane holds
-    unsigned mr = __funnelshift_r(m, m, lane);
+    // bit 0 of mr is the mask bit of the j entry this lane holds (entry
+    // 8 g + ((r + k) & 7) at step k)
+    unsigned mr = ((m8 >> r) | (m8 << (8 - r))) & 0xffu;
 #pragma unroll 2
-    for (int k = 0; k < 32; ++k) {
+    for (int k = 0; k < 8; ++k) {
         const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
         const real r2 = dx * dx + dy * dy + dz * dz;
         if ((mr & 1u) && r2 < c.rc2) {
@@ -709,7 +813,7 @@ __device__ __forceinline__ real tile_rotate(const SysView<real>& s, const PairCo
             e0 += ec + v;
             ++npairs;
         }
-        mr = __funnelshift_r(mr, mr, 1);
+        mr = ((mr >> 1) | (mr << 7)) & 0xffu;
         xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
         zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
         sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
@@ -724,15 +828,29 @@ __device__ __forceinline__ real tile_rotate(const SysView<real>& s, const PairCo
     return e0;
 }
 
-// One warp walks a contiguous chunk of the (I-sorted) tile list, one tile at
-// a time by rotation; i-forces stay in registers while consecutive tiles
-// share I.  The tile's class (vv, uu or uv) and shift are uniform, so the
-// branch on them is warp-uniform.  Solute-solvent energies are not
+// the four lanes of an i atom (one per j group) add their i-force shares and
+// one of them writes the sum
+template <typename real>
+__device__ __forceinline__ void flush_i(const SysView<real>& s, int islot, long long fx, long long fy, long long fz)
+{
+    for (int o = 8; o < 32; o <<= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if ((threadIdx.x & 31) < 8) flush_force(s, islot, fx, fy, fz);
+}
+
+// One warp walks a contiguous chunk of the (I8-sorted) tile list, one 8 x 32
+// tile at a time by rotation; i-forces stay in registers while consecutive
+// tiles share I8.  The tile's class (vv, uu or uv) and shift are uniform, so
+// the branch on them is warp-uniform.  Solute-solvent energies are not
 // accumulated here (k_uv_energy forms them in FP64).
 template <typename real>
 __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real> nb)
 {
     const int lane = threadIdx.x & 31;
+    const int r = lane & 7, grp = lane >> 3;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     int ntiles = s.flags[FL_NTILES];
@@ -744,23 +862,35 @@ __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real>
     int curI = -1;
     real xi = 0, yi = 0, zi = 0, qi = 0, si = 0, ei = 0;
     long long fix = 0, fiy = 0, fiz = 0;
-    double evv = 0, euu = 0;
+    real evv = 0, euu = 0;
     int npairs = 0;
+    // the next tile's records are loaded while the current one is computed
+    int4 tl_n = nb.tiles[t0];
+    unsigned mk_n = nb.masks[(size_t)t0 * 8 + r];
+    int sj_n = nb.jidx[(size_t)t0 * 32 + lane];
+    R4<real> pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
+    R2<real> lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
     for (int t = t0; t < t1; ++t) {
-        const int4 tl = nb.tiles[t];
+        const int4 tl = tl_n;
+        const unsigned m8 = (mk_n >> (8 * grp)) & 0xffu;
+        const int slot_j = sj_n;
+        R4<real> pj = pj_n;
+        const R2<real> ljv = lj_n;
+        if (t + 1 < t1) {
+            tl_n = nb.tiles[t + 1];
+            mk_n = nb.masks[(size_t)(t + 1) * 8 + r];
+            sj_n = nb.jidx[(size_t)(t + 1) * 32 + lane];
+            pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
+            lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
+        }
         if (tl.x != curI) {
-            if (curI >= 0) flush_force(s, curI * 32 + lane, fix, fiy, fiz);
+            if (curI >= 0) flush_i(s, curI * 8 + r, fix, fiy, fiz);
             curI = tl.x;
-            const R4<real> p = s.xq[curI * 32 + lane];
-            const R2<real> l = s.lj[curI * 32 + lane];
+            const R4<real> p = s.xq[curI * 8 + r];
+            const R2<real> l = s.lj[curI * 8 + r];
             xi = p.x; yi = p.y; zi = p.z; qi = p.w; si = l.x; ei = l.y;
             fix = fiy = fiz = 0;
         }
-        const unsigned m = nb.masks[(size_t)t * 32 + lane];
-        const int slot_j = nb.jidx[(size_t)t * 32 + lane];
-        const int sj_load = slot_j >= 0 ? slot_j : 0;
-        R4<real> pj = s.xq[sj_load];
-        const R2<real> ljv = s.lj[sj_load];
         const int sh = tl.y;
         const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
         // shift the far-side atom down by L so that the subtraction below is
@@ -771,14 +901,14 @@ __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real>
         if (sx == -1) pj.x -= s.L[0];
         if (sy == -1) pj.y -= s.L[1];
         if (sz == -1) pj.z -= s.L[2];
-        const real e0 = tile_rotate(s, c, xit, yit, zit, qi, si, ei, pj, ljv, m, tl.z == 2, slot_j, fix, fiy, fiz,
+        const real e0 = tile_rotate(s, c, xit, yit, zit, qi, si, ei, pj, ljv, m8, tl.z == 2, slot_j, fix, fiy, fiz,
                                     npairs);
-        if (tl.z == 0) evv += (double)e0;
-        else if (tl.z == 1) euu += (double)e0;
+        if (tl.z == 0) evv += e0;
+        else if (tl.z == 1) euu += e0;
     }
-    flush_force(s, curI * 32 + lane, fix, fiy, fiz);
-    const long long a0 = __double2ll_rn(warp_sum_d(evv) * ESCALE);
-    const long long a1 = __double2ll_rn(warp_sum_d(euu) * ESCALE);
+    flush_i(s, curI * 8 + r, fix, fiy, fiz);
+    const long long a0 = __double2ll_rn(warp_sum_d((double)evv) * ESCALE);
+    const long long a1 = __double2ll_rn(warp_sum_d((double)euu) * ESCALE);
     const long long a4 = warp_sum_ll((long long)npairs);
     if (lane == 0) {
         if (a0) atomic_add_ll(&s.E[E_PAIR_VV], a0);
