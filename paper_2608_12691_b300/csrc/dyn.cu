@@ -27,10 +27,9 @@ __device__ __forceinline__ real sorted_coord(real x, real xref, real L, real inv
 template <typename real>
 __device__ __forceinline__ void add_force(const SysView<real>& s, int atom, real fx, real fy, real fz)
 {
-    const int slot = s.iperm[atom];
-    atomic_add_ll(&s.F[slot], to_fixed(fx, FSCALE));
-    atomic_add_ll(&s.F[s.n_pad + slot], to_fixed(fy, FSCALE));
-    atomic_add_ll(&s.F[2 * s.n_pad + slot], to_fixed(fz, FSCALE));
+    atomic_add_ll(&s.Fa[atom], to_fixed(fx, FSCALE));
+    atomic_add_ll(&s.Fa[s.n + atom], to_fixed(fy, FSCALE));
+    atomic_add_ll(&s.Fa[2 * s.n + atom], to_fixed(fz, FSCALE));
 }
 
 // ------------------------------------------------------------ set lambda
@@ -58,8 +57,10 @@ __global__ void k_eval_out(SysView<real> s, double* forces, double* terms, doubl
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < s.n) {
         const int slot = s.iperm[a];
-        long long fx = s.F[slot], fy = s.F[s.n_pad + slot], fz = s.F[2 * s.n_pad + slot];
+        const long long fx = s.F[slot] + s.Fa[a], fy = s.F[s.n_pad + slot] + s.Fa[s.n + a],
+                        fz = s.F[2 * s.n_pad + slot] + s.Fa[2 * s.n + a];
         s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+        s.Fa[a] = 0; s.Fa[s.n + a] = 0; s.Fa[2 * s.n + a] = 0;
         if (forces) {
             forces[3 * a] = (double)fx * (1.0 / FSCALE);
             forces[3 * a + 1] = (double)fy * (1.0 / FSCALE);
@@ -473,7 +474,7 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
     // slot-indexed forces and sorted records
     R4<real> xa4[NA], va4[NA], xr4[NA], xq4[NA];
     real kick[NA][3];
-    long long fl[NA][3];
+    long long fl[NA][3], fla[NA][3];
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const int atom = G.atom[a];
@@ -489,12 +490,18 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
     for (int a = 0; a < NA; ++a) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) fl[a][d] = s.F[(size_t)d * s.n_pad + slot[a]];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) fla[a][d] = s.Fa[(size_t)d * s.n + G.atom[a]];
         xq4[a] = s.xq[slot[a]];
     }
 #pragma unroll
     for (int a = 0; a < NA; ++a)
 #pragma unroll
-        for (int d = 0; d < 3; ++d) s.F[(size_t)d * s.n_pad + slot[a]] = 0;
+        for (int d = 0; d < 3; ++d) {
+            s.F[(size_t)d * s.n_pad + slot[a]] = 0;
+            s.Fa[(size_t)d * s.n + G.atom[a]] = 0;
+            fl[a][d] += fla[a][d];
+        }
     o0[0] = xa4[0].x; o0[1] = xa4[0].y; o0[2] = xa4[0].z;
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
@@ -638,8 +645,9 @@ __global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real
         // the neighbour list was truncated: consume the forces, leave the
         // state untouched (the host regrows the list and replays the step)
         for (int a = 0; a < G.natom; ++a) {
-            const int slot = s.iperm[G.atom[a]];
+            const int atom = G.atom[a], slot = s.iperm[atom];
             s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
+            s.Fa[atom] = 0; s.Fa[s.n + atom] = 0; s.Fa[2 * s.n + atom] = 0;
         }
         return;
     }
@@ -842,19 +850,27 @@ template <typename real>
 __global__ void k_step_end(SysView<real> s, ThetaView<real> t)
 {
     const int lane = threadIdx.x;
-    if (lane == 0 && !(s.flags[FL_ERROR] & ERRB_OVERFLOW)) {
-        s.lam->step += 1;
-        if (t.use_cond) {
-            const int rb = s.flags[FL_REBUILD];
-            cudaGraphSetConditional(t.cond, rb ? 1u : 0u);
-            if (rb) s.flags[FL_NREBUILD] += 1;
-            s.flags[FL_REBUILD] = 0;
-        }
-    } else if (lane == 0 && t.use_cond) {
-        cudaGraphSetConditional(t.cond, 0u);
-        s.flags[FL_REBUILD] = 0;
-    }
+    if (lane == 0 && !(s.flags[FL_ERROR] & ERRB_OVERFLOW)) s.lam->step += 1;
     if (lane < E_N) s.E[lane] = 0;
+}
+
+// first node of a captured step: the neighbour list is rebuilt (by the
+// conditional node that follows) when the previous step left an atom more
+// than skin/2 from where the list was built; no rebuild once a rebuild has
+// overflowed (the steps after it are no-ops until the host regrows the list)
+template <typename real>
+__global__ void k_rebuild_cond(SysView<real> s, cudaGraphConditionalHandle h)
+{
+    const int rb = s.flags[FL_REBUILD] && !(s.flags[FL_ERROR] & ERRB_OVERFLOW);
+    cudaGraphSetConditional(h, rb ? 1u : 0u);
+    if (rb) s.flags[FL_NREBUILD] += 1;
+    s.flags[FL_REBUILD] = 0;
+}
+
+template <typename real>
+void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st)
+{
+    k_rebuild_cond<real><<<1, 1, 0, st>>>(s, h);
 }
 
 template <typename real>
@@ -885,6 +901,7 @@ void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStrea
     template void launch_dafed_force<real>(const SysView<real>&, const DafedView&, cudaStream_t);            \
     template void launch_dafed_step<real>(const SysView<real>&, const DafedView&, cudaStream_t);             \
     template void launch_dafed_probe<real>(const SysView<real>&, const DafedView&, double, double*, cudaStream_t); \
+    template void launch_rebuild_cond<real>(const SysView<real>&, cudaGraphConditionalHandle, cudaStream_t);    \
     template void launch_step_end<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
 LFE_INST_DYN(float)
 LFE_INST_DYN(double)

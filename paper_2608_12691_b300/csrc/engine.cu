@@ -124,7 +124,7 @@ struct System final : SystemBase {
     double const_vv = 0, const_uu = 0, const_uv = 0;
     cudaStream_t cs = nullptr, cs2 = nullptr;
     cudaStream_t br[4] = {nullptr, nullptr, nullptr, nullptr};   // capture branches
-    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_built = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* h_flags = nullptr;        // pinned
@@ -183,6 +183,7 @@ struct System final : SystemBase {
         }
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_z) cudaEventDestroy(ev_z);
+        if (ev_built) cudaEventDestroy(ev_built);
     }
 
     void create(const lfe_params& p, const lfe_topology& t)
@@ -305,6 +306,7 @@ struct System final : SystemBase {
         S.perm = dalloc<int>(n_pad);
         S.iperm = dalloc<int>(n);
         S.F = dalloc<long long>(3 * (size_t)n_pad);
+        S.Fa = dalloc<long long>(3 * (size_t)n);
         S.E = dalloc<long long>(E_N);
         S.flags = dalloc<int>(FL_N);
         S.lam = dalloc<LamState>(1);
@@ -321,7 +323,6 @@ struct System final : SystemBase {
         N.col_cnt = dalloc<int>(N.ncols);
         N.col_start = dalloc<int>(N.ncols + 1);
         N.col_fill = dalloc<int>(N.ncols);
-        N.col_ncl = dalloc<int>(N.ncols);
         N.col_cl = dalloc<int>(N.ncols + 1);
         N.tmp = dalloc<int>(n_solv);
         N.tmp2 = dalloc<int>(n_solv);
@@ -620,7 +621,6 @@ struct System final : SystemBase {
         T.const_vv = const_vv;
         T.const_uu = const_uu;
         T.const_uv = const_uv;
-        T.use_cond = 0;
 
         // initial lambda state from theta0
         {
@@ -651,6 +651,7 @@ struct System final : SystemBase {
         }
         CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_z, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_built, cudaEventDisableTiming));
         build_neighbors(nullptr);
         CK(cudaStreamSynchronize(nullptr));
         {
@@ -781,6 +782,19 @@ struct System final : SystemBase {
         grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2, 2 * h_flags[FL_NSTAGE]);
     }
 
+    // a rebuild left pending by the last step (steps rebuild at their start)
+    // is done before anything outside the step graph reads the list
+    void settle_rebuild(cudaStream_t st)
+    {
+        CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (!h_flags[FL_REBUILD] || (h_flags[FL_ERROR] & ERRB_OVERFLOW)) return;
+        const int v[2] = {0, h_flags[FL_NREBUILD] + 1};
+        CK(cudaMemcpy(S.flags + FL_REBUILD, &v[0], sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(S.flags + FL_NREBUILD, &v[1], sizeof(int), cudaMemcpyHostToDevice));
+        build_neighbors(st);
+    }
+
     void build_neighbors(cudaStream_t st) override
     {
         launch_build_nbl(S, N, st);
@@ -819,22 +833,7 @@ struct System final : SystemBase {
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         launch_assign_positions(S, d_pos, s0);
         launch_moved(S, G.skin_half2, h, s0);
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
-        cudaGraphNodeParams cp{};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        CK(cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_build_nbl(S, N, cs2);
-        cudaGraph_t body_out = nullptr;
-        CK(cudaStreamEndCapture(cs2, &body_out));
+        add_cond_build(s0, h);
         CK(cudaStreamEndCapture(s0, &pos_graph));
         CK(cudaGraphInstantiate(&pos_exec, pos_graph, 0));
         pos_gen = generation;
@@ -913,6 +912,7 @@ struct System final : SystemBase {
         if (!(lam >= 0.0 && lam <= 1.0)) fail(LFE_ERR_ARG, "lambda must be in [0, 1]");
         settle_positions(st);
         if (exec) recover_overflow(st);
+        settle_rebuild(st);
         // the dynamics' lambda state is saved and put back: an evaluation at
         // an arbitrary lambda does not move theta
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
@@ -930,6 +930,30 @@ struct System final : SystemBase {
         check_flags(st);
     }
 
+    // Appends to the graph being captured on st a conditional node (handle h)
+    // whose body rebuilds the neighbour list; st continues after it.
+    void add_cond_build(cudaStream_t st, cudaGraphConditionalHandle h)
+    {
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_build_nbl(S, N, cs2);
+        cudaGraph_t body_out = nullptr;
+        CK(cudaStreamEndCapture(cs2, &body_out));
+    }
+
     // The evaluation as four concurrent branches (used inside the captured
     // step graph): pair kernel | FP32 PME chain | FP64 PME energy branch (it
     // starts once the first FP32 pass has left the FP64 copy of the charge
@@ -938,11 +962,22 @@ struct System final : SystemBase {
     // does not change any result.  B300 runs the FP64 branches on the FP64
     // pipes while the FP32 pair and PME kernels use the FP32 pipes.
     // the evaluation as four concurrent branches; with a theta view, the
-    // step's force-independent integrator parts run in the fourth branch
-    void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr)
+    // step's force-independent integrator parts run in the fourth branch.
+    // With a conditional handle the first branch starts with the step's
+    // conditional rebuild of the neighbour list: only the pair kernel and the
+    // solute-solvent energies (last in the fourth branch, after the rebuild)
+    // read the list and the cluster-sorted copy, so the PME, exclusion and
+    // bonded work runs beside the rebuild.
+    void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr,
+                               const cudaGraphConditionalHandle* rebuild = nullptr)
     {
         CK(cudaEventRecord(ev_fork, s0));
         for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
+        if (rebuild) {
+            launch_rebuild_cond(S, *rebuild, br[0]);
+            add_cond_build(br[0], *rebuild);
+        }
+        CK(cudaEventRecord(ev_built, br[0]));
         if (pre) launch_prestep(S, G, *pre, br[3]);
         launch_pairs(S, N, pair_warps, br[0]);
         launch_spread(S, M, br[1]);
@@ -977,10 +1012,11 @@ struct System final : SystemBase {
                 launch_conv(M64, S.E, S.lam, CONV_ENERGY, br[2]);
             }
         }
-        launch_uv_energy(S, N, uv_blocks, br[3]);
         launch_excl(S, X, br[3]);
         launch_bonded(S, B, br[3]);
         launch_dafed_force(S, D, br[3]);
+        CK(cudaStreamWaitEvent(br[3], ev_built, 0));
+        launch_uv_energy(S, N, uv_blocks, br[3]);
         for (int k = 0; k < 4; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
             CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
@@ -996,31 +1032,14 @@ struct System final : SystemBase {
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        ThetaView<real> Tc = T;
-        Tc.cond = h;
-        Tc.use_cond = 1;
+        launch_rebuild_cond(S, h, s0);
+        add_cond_build(s0, h);
         eval_kernels(s0);
-        launch_prestep(S, G, Tc, s0);
+        launch_prestep(S, G, T, s0);
         launch_integrate(S, G, s0);
-        launch_theta(S, Tc, s0);
+        launch_theta(S, T, s0);
         launch_dafed_step(S, D, s0);
-        launch_step_end(S, Tc, s0);
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
-        cudaGraphNodeParams cp{};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        CK(cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_build_nbl(S, N, cs2);
-        cudaGraph_t body_out = nullptr;
-        CK(cudaStreamEndCapture(cs2, &body_out));
+        launch_step_end(S, T, s0);
     }
 
     void note_batch_steps(int n) override
@@ -1050,35 +1069,16 @@ struct System final : SystemBase {
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        ThetaView<real> Tc = T;
-        Tc.cond = h;
-        Tc.use_cond = 1;
-        eval_kernels_branched(s0, &Tc);
+        eval_kernels_branched(s0, &T, &h);
         // atoms and theta move concurrently; the step ends when both are done
         CK(cudaEventRecord(ev_fork, s0));
         CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
-        launch_theta(S, Tc, br[0]);
+        launch_theta(S, T, br[0]);
         launch_dafed_step(S, D, br[0]);
         CK(cudaEventRecord(ev_join[0], br[0]));
         launch_integrate(S, G, s0);
         CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
-        launch_step_end(S, Tc, s0);
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, &deps, nullptr, &ndeps));
-        cudaGraphNodeParams cp{};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        CK(cudaStreamUpdateCaptureDependencies(s0, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_build_nbl(S, N, cs2);
-        cudaGraph_t body_out = nullptr;
-        CK(cudaStreamEndCapture(cs2, &body_out));
+        launch_step_end(S, T, s0);
         CK(cudaStreamEndCapture(s0, &graph));
         CK(cudaGraphInstantiate(&exec, graph, 0));
     }
@@ -1545,6 +1545,7 @@ struct System final : SystemBase {
         if (n_u == 0) fail(LFE_ERR_ARG, "the system has no solute atoms");
         settle_positions(st);
         if (exec) recover_overflow(st);
+        settle_rebuild(st);
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
         launch_set_lambda(S, lam, st);
         const PmeView<double>* P64;

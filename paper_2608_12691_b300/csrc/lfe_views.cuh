@@ -38,7 +38,9 @@ struct SysView {
     R2<real>* lj;       // sigma/2, 2 sqrt(eps)
     int* perm;          // slot -> atom (-1 = padding)
     int* iperm;         // atom -> slot
-    long long* F;       // fixed-point forces [3][n_pad]
+    long long* F;       // fixed-point forces [3][n_pad] of the neighbour-list terms (slot order)
+    long long* Fa;      // fixed-point forces [3][n] of the other terms (atom order): PME, exclusion
+                        // and 1-4 corrections, bonded, d-AFED -- independent of the list build
     long long* E;       // energy accumulators [E_N]
     int* flags;         // [FL_N]
     LamState* lam;
@@ -54,7 +56,6 @@ struct NblView {
     int* col_cnt;         // [ncols] histogram (zeroed after the scan)
     int* col_start;       // [ncols + 1]
     int* col_fill;        // [ncols] scatter counters (zeroed after use)
-    int* col_ncl;         // [ncols] clusters per column (zeroed after the scan)
     int* col_cl;          // [ncols + 1] first solvent cluster of each column
     int* tmp;             // [n_solv] solvent atoms grouped by column
     int* tmp2;            // [n_solv] ... and sorted by z inside each column
@@ -195,8 +196,6 @@ struct ThetaView {
     uint2 key;
     double const_uv;        // background share of U_uv (constant)
     double const_vv, const_uu;
-    cudaGraphConditionalHandle cond;
-    int use_cond;
     ThetaPre* pre;
     double* ti_sum;                 // [LFE_TI_BINS] sum of dU/dlambda per lambda bin (Eq. 2)
     unsigned long long* ti_cnt;     // [LFE_TI_BINS] samples per bin
@@ -257,6 +256,7 @@ template <typename real> void launch_dafed_probe(const SysView<real>& s, const D
 template <typename real> void launch_prestep(const SysView<real>& s, const StepView<real>& g,
                                              const ThetaView<real>& t, cudaStream_t st);
 template <typename real> void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+template <typename real> void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st);
 template <typename real> void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st);
 template <typename real> void launch_eval_out(const SysView<real>& s, double* forces, double* terms,
                                               double const_vv, double const_uu, double const_uv,

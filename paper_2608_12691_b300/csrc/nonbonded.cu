@@ -59,38 +59,20 @@ __global__ void k_col_keys(SysView<real> s, NblView<real> nb)
     atomicAdd(&nb.col_cnt[c], 1);
 }
 
-// exclusive scan of n ints (single block of 1024 threads); zeroes `in`;
-// writes the total to *total (when given) and raises the overflow bit when it
-// exceeds cap
-__global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, int* total, int cap, int* errflag)
+// exclusive prefix of one value per thread over the block (warp shuffles and
+// one shared-memory pass over the warp sums); *grand = block total
+__device__ __forceinline__ int block_exscan(int v, int* wsum, int* grand)
 {
-    constexpr int PER_MAX = 32;
-    __shared__ int wsum[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (n + blockDim.x - 1) / blockDim.x;
-    const int b = tid * per, e = min(n, b + per);
-    int v[PER_MAX];
-    int s = 0;
-    if (per <= PER_MAX) {
-        // all of this thread's loads in flight at once
-#pragma unroll
-        for (int k = 0; k < PER_MAX; ++k) {
-            v[k] = (k < per && b + k < e) ? in[b + k] : 0;
-            s += v[k];
-        }
-    } else {
-        for (int i = b; i < e; ++i) s += in[i];
-    }
-    // block-wide exclusive scan of the per-thread sums (warp shuffles)
-    int incl = s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = v;
     for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += t;
     }
+    __syncthreads();   // wsum may still be read by a previous scan
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        const int nw = blockDim.x >> 5;
         int x = lane < nw ? wsum[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, x, o);
@@ -99,14 +81,52 @@ __global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, i
         if (lane < nw) wsum[lane] = x;
     }
     __syncthreads();
-    int run = incl - s + (warp > 0 ? wsum[warp - 1] : 0);
-    const int grand = wsum[(blockDim.x >> 5) - 1];
+    *grand = wsum[nw - 1];
+    return incl - v + (warp > 0 ? wsum[warp - 1] : 0);
+}
+
+// exclusive scan of n ints (single block of 1024 threads); zeroes `in`;
+// writes the total to *total (when given) and raises the overflow bit when it
+// exceeds cap.  CL = 1 also scans the 32-atom clusters of each entry,
+// ceil(in / 32), into out2 with their total in *total2 (the column sort).
+template <int CL>
+__global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, int* total, int cap, int* errflag,
+                                                     int* out2, int* total2)
+{
+    constexpr int PER_MAX = 32;
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b = tid * per, e = min(n, b + per);
+    int v[PER_MAX];
+    int s = 0, s2 = 0;
+    if (per <= PER_MAX) {
+        // all of this thread's loads in flight at once
+#pragma unroll
+        for (int k = 0; k < PER_MAX; ++k) {
+            v[k] = (k < per && b + k < e) ? in[b + k] : 0;
+            s += v[k];
+            if (CL) s2 += (v[k] + 31) >> 5;
+        }
+    } else {
+        for (int i = b; i < e; ++i) {
+            s += in[i];
+            if (CL) s2 += (in[i] + 31) >> 5;
+        }
+    }
+    int grand = 0, grand2 = 0;
+    int run = block_exscan(s, wsum, &grand);
+    int run2 = CL ? block_exscan(s2, wsum, &grand2) : 0;
     if (per <= PER_MAX) {
 #pragma unroll
         for (int k = 0; k < PER_MAX; ++k) {
             if (k < per && b + k < e) {
                 out[b + k] = run;
                 run += v[k];
+                if (CL) {
+                    out2[b + k] = run2;
+                    run2 += (v[k] + 31) >> 5;
+                }
                 in[b + k] = 0;
             }
         }
@@ -115,6 +135,10 @@ __global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, i
             const int x = in[i];
             out[i] = run;
             run += x;
+            if (CL) {
+                out2[i] = run2;
+                run2 += (x + 31) >> 5;
+            }
             in[i] = 0;
         }
     }
@@ -123,6 +147,10 @@ __global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, i
         if (total) {
             *total = grand;
             if (grand > cap) atomicOr(errflag, ERRB_OVERFLOW);
+        }
+        if (CL) {
+            out2[n] = grand2;
+            *total2 = grand2;
         }
     }
 }
@@ -139,8 +167,7 @@ __global__ void k_col_scatter(SysView<real> s, NblView<real> nb)
 
 constexpr int COL_MAX = 2048;   // atoms per column handled by one block
 
-// one block per column: rank sort by (wrapped z, atom index); also the
-// number of 32-atom clusters of the column
+// one block per column: rank sort by (wrapped z, atom index)
 template <typename real>
 __global__ void __launch_bounds__(256) k_col_sort(SysView<real> s, NblView<real> nb)
 {
@@ -169,14 +196,12 @@ __global__ void __launch_bounds__(256) k_col_sort(SysView<real> s, NblView<real>
         }
         nb.tmp2[b + rank] = a;
     }
-    if (threadIdx.x == 0) {
-        nb.col_fill[c] = 0;
-        nb.col_ncl[c] = (cnt + 31) / 32;
-    }
+    if (threadIdx.x == 0) nb.col_fill[c] = 0;
 }
 
 // slot -> atom: solute clusters first, then the solvent clusters column by
-// column; also the sorted coordinates / parameters and xref
+// column; also the sorted coordinates / parameters, xref and the clusters'
+// bounding boxes (one warp per cluster)
 template <typename real>
 __global__ void k_assign(SysView<real> s, NblView<real> nb)
 {
@@ -220,32 +245,17 @@ __global__ void k_assign(SysView<real> s, NblView<real> nb)
     }
     s.xq[slot] = o;
     s.lj[slot] = l;
-}
-
-template <typename real>
-__device__ __forceinline__ int num_clusters(const SysView<real>& s, const NblView<real>& nb)
-{
-    return s.n_ucl + *nb.n_cl_solv;
-}
-
-// Bounding boxes of every 32-atom cluster (the partner side of the tile
-// search) and of its four 8-slot sub-clusters (the i side of the tiles).  A
-// sub-cluster without atoms gets a negative half extent (no tiles).
-template <typename real>
-__global__ void k_bbox(SysView<real> s, NblView<real> nb)
-{
-    const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) s.flags[FL_NSTAGE] = 0;   // the tile staging list starts empty
-    if (c >= num_clusters(s, nb)) return;
-    const int slot = c * 32 + lane;
-    const bool ok = s.perm[slot] >= 0;
-    const R4<real> p = s.xq[slot];
+    // the warp holds one cluster: bounding boxes of the cluster (the partner
+    // side of the tile search) and of its four 8-slot sub-clusters (the i
+    // side); a sub-cluster without atoms gets a negative half extent
+    const int c = slot >> 5, lane = slot & 31;
+    if (c >= s.n_ucl + *nb.n_cl_solv) return;
     float lo[3], hi[3];
-    const float pv[3] = {(float)p.x, (float)p.y, (float)p.z};
+    const float pv[3] = {(float)o.x, (float)o.y, (float)o.z};
     for (int d = 0; d < 3; ++d) {
-        lo[d] = ok ? pv[d] : 3.0e38f;
-        hi[d] = ok ? pv[d] : -3.0e38f;
+        lo[d] = a >= 0 ? pv[d] : 3.0e38f;
+        hi[d] = a >= 0 ? pv[d] : -3.0e38f;
     }
     auto emit = [&](R4<float>* cen, R4<float>* half, int idx) {
         R4<float> cc, hh;
@@ -258,18 +268,24 @@ __global__ void k_bbox(SysView<real> s, NblView<real> nb)
         cen[idx] = cc;
         half[idx] = hh;
     };
-    for (int o = 4; o > 0; o >>= 1)
+    for (int o8 = 4; o8 > 0; o8 >>= 1)
         for (int d = 0; d < 3; ++d) {
-            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o8));
+            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o8));
         }
     if ((lane & 7) == 0) emit(nb.bbc8, nb.bbh8, c * 4 + (lane >> 3));
-    for (int o = 16; o > 4; o >>= 1)
+    for (int o32 = 16; o32 > 4; o32 >>= 1)
         for (int d = 0; d < 3; ++d) {
-            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o32));
+            hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o32));
         }
     if (lane == 0) emit(nb.bbc, nb.bbh, c);
+}
+
+template <typename real>
+__device__ __forceinline__ int num_clusters(const SysView<real>& s, const NblView<real>& nb)
+{
+    return s.n_ucl + *nb.n_cl_solv;
 }
 
 // shift code sh = (sx+1) + 3 (sy+1) + 9 (sz+1): cluster J is taken at x_J + s L
@@ -318,43 +334,21 @@ __device__ __forceinline__ float box_gap2(const SysView<real>& s, const R4<float
 constexpr int TILE_CAND = 128;     // partner clusters listed per round (per warp)
 constexpr int TILE_BATCH = 8;      // partner clusters whose atoms are loaded together
 
+// one (I8, shift) search by one warp; returns the number of tiles it started
 template <typename real>
-__global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb)
+__device__ int tile_search(const SysView<real>& s, const NblView<real>& nb, int I8, int sh, int* cand,
+                           unsigned* kb, int lane)
 {
-    __shared__ int cand_sh[4][TILE_CAND];
-    __shared__ unsigned kb_sh[4][TILE_CAND];
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    int* cand = cand_sh[(threadIdx.x >> 5) & 3];
-    unsigned* kb = kb_sh[(threadIdx.x >> 5) & 3];
-    if (w >= nb.n_cl_max * 4 * 27) return;
-    const int I8 = w / 27, sh = w - I8 * 27;
     const int I = I8 >> 2;
     const int ncl = num_clusters(s, nb);
     const R4<float> ci = nb.bbc8[I8], hi = nb.bbh8[I8];
-    if (I >= ncl || hi.w < 0.f) {
-        if (lane == 0) nb.tile_cnt[w] = 0;
-        return;
-    }
     const bool iu = I < s.n_ucl;
     int count = 0;        // tiles started by this warp (the next tile's ordinal)
     bool dead = false;    // the staging list ran out: nothing more is written
-    // every atom lies in [0, L): a shift -1 (+1) along an axis can bring a
-    // partner within the cutoff only if I8's box reaches within r_cut + skin
-    // of the lower (upper) face
-    const float cut = sqrtf(nb.cut2);
     int svs[3];
     shift_vec(sh, svs);
-    bool allowed = true;
-    {
-        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
-        for (int d = 0; d < 3; ++d) {
-            if (svs[d] < 0 && !(c0[d] - h0[d] < cut)) allowed = false;
-            if (svs[d] > 0 && !(c0[d] + h0[d] > (float)s.L[d] - cut)) allowed = false;
-        }
-    }
     const unsigned lt = (1u << lane) - 1u;
-    if (allowed) {
+    {
         const float shx = svs[0] * (float)s.L[0], shy = svs[1] * (float)s.L[1], shz = svs[2] * (float)s.L[2];
         const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
         // sub-clusters of partner atoms that may pair with I8 under this shift
@@ -475,7 +469,59 @@ __global__ void __launch_bounds__(128) k_tiles(SysView<real> s, NblView<real> nb
             if (nbuf > 0 && !dead && lane >= nbuf) nb.stage_j[(size_t)cur * 32 + lane] = -1;
         }
     }
-    if (lane == 0) nb.tile_cnt[w] = count;
+    return count;
+}
+
+// One block per i sub-cluster I8; its TILE_WARPS warps take turns over the
+// shifts that can bring partners within the cutoff: every atom lies in
+// [0, L), so a shift -1 (+1) along an axis is needed only if I8's box reaches
+// within r_cut + skin of the lower (upper) face.  The block then turns the 27
+// counts into offsets inside I8 (tile_cnt) and I8's total (tile_tot).
+constexpr int TILE_WARPS = 2;
+
+template <typename real>
+__global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblView<real> nb)
+{
+    __shared__ int cand_sh[TILE_WARPS][TILE_CAND];
+    __shared__ unsigned kb_sh[TILE_WARPS][TILE_CAND];
+    __shared__ int cnt_sh[27];
+    const int I8 = blockIdx.x;
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = I8 >> 2;
+    const R4<float> ci = nb.bbc8[I8], hi = nb.bbh8[I8];
+    const bool live = I < num_clusters(s, nb) && hi.w >= 0.f;
+    bool ok = live && lane < 27;
+    if (ok) {
+        const float cut = sqrtf(nb.cut2);
+        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
+        int sv[3];
+        shift_vec(lane, sv);
+        for (int d = 0; d < 3; ++d) {
+            if (sv[d] < 0 && !(c0[d] - h0[d] < cut)) ok = false;
+            if (sv[d] > 0 && !(c0[d] + h0[d] > (float)s.L[d] - cut)) ok = false;
+        }
+    }
+    const unsigned allow = __ballot_sync(0xffffffffu, ok);
+    if (wl == 0 && lane < 27 && !ok) cnt_sh[lane] = 0;
+    int k = 0;
+    for (unsigned m = allow; m; m &= m - 1u, ++k) {
+        if (k % TILE_WARPS != wl) continue;
+        const int sh = __ffs(m) - 1;
+        const int count = tile_search(s, nb, I8, sh, cand_sh[wl], kb_sh[wl], lane);
+        if (lane == 0) cnt_sh[sh] = count;
+    }
+    __syncthreads();
+    // offsets of the shifts inside I8, and I8's total for the scan
+    if (wl == 0) {
+        const int c = lane < 27 ? cnt_sh[lane] : 0;
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane < 27) nb.tile_cnt[I8 * 27 + lane] = incl - c;
+        if (lane == 26) nb.tile_tot[I8] = incl;
+    }
 }
 
 // Placement and interaction masks.  Every staged tile goes to its place
@@ -630,51 +676,29 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
     }
 }
 
-// Per-cluster tile totals from the per-(cluster, shift) counts: one warp
-// per cluster turns its 27 counts into offsets inside the cluster (kept in
-// tile_cnt) and writes the cluster's total to tile_tot for the scan.
-__global__ void k_tile_prefix(int* cnt, int* tot, int n_cl)
-{
-    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (I >= n_cl) return;
-    const int c = lane < 27 ? cnt[I * 27 + lane] : 0;
-    int incl = c;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane < 27) cnt[I * 27 + lane] = incl - c;
-    if (lane == 26) tot[I] = incl;
-}
-
 template <typename real>
 void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st)
 {
     const int B = 256;
     if (s.n_solv > 0) {
         k_col_keys<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
-        k_scan_block<<<1, 1024, 0, st>>>(nb.col_cnt, nb.col_start, nb.ncols, nullptr, 0, nullptr);
+        k_scan_block<1><<<1, 1024, 0, st>>>(nb.col_cnt, nb.col_start, nb.ncols, nullptr, 0, nullptr, nb.col_cl,
+                                            nb.n_cl_solv);
         k_col_scatter<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
         k_col_sort<real><<<nb.ncols, 256, 0, st>>>(s, nb);
-        k_scan_block<<<1, 1024, 0, st>>>(nb.col_ncl, nb.col_cl, nb.ncols, nb.n_cl_solv, 1 << 30, s.flags + FL_ERROR);
     }
     k_assign<real><<<(s.n_pad + B - 1) / B, B, 0, st>>>(s, nb);
-    const int wb = (nb.n_cl_max * 32 + 127) / 128;
-    k_bbox<real><<<wb, 128, 0, st>>>(s, nb);
-    const int tb = (nb.n_cl_max * 4 * 27 * 32 + 127) / 128;
-    k_tiles<real><<<tb, 128, 0, st>>>(s, nb);
-    k_tile_prefix<<<(nb.n_cl_max * 4 * 32 + 127) / 128, 128, 0, st>>>(nb.tile_cnt, nb.tile_tot, nb.n_cl_max * 4);
-    k_scan_block<<<1, 1024, 0, st>>>(nb.tile_tot, nb.tile_off, nb.n_cl_max * 4, s.flags + FL_NTILES, nb.cap,
-                                     s.flags + FL_ERROR);
+    k_tiles<real><<<nb.n_cl_max * 4, TILE_WARPS * 32, 0, st>>>(s, nb);
+    k_scan_block<0><<<1, 1024, 0, st>>>(nb.tile_tot, nb.tile_off, nb.n_cl_max * 4, s.flags + FL_NTILES, nb.cap,
+                                        s.flags + FL_ERROR, nullptr, nullptr);
     const long long pq = ((long long)nb.stage_cap + 15) / 16;   // blocks of four warps x four tiles
     const long long pmax = (long long)nb.n_sm * PLACE_BLOCKS_PER_SM;
     k_place<real><<<(int)(pq < pmax ? pq : pmax), 128, 0, st>>>(s, nb);
     if (s.n_ucl > 0) {
         const int ub = (nb.uv_tiles_max * 32 + 127) / 128;
         k_uv_pairs<real, 0><<<ub, 128, 0, st>>>(s, nb);
-        k_scan_block<<<1, 1024, 0, st>>>(nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV, nb.uv_cap,
-                                         s.flags + FL_ERROR);
+        k_scan_block<0><<<1, 1024, 0, st>>>(nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV, nb.uv_cap,
+                                            s.flags + FL_ERROR, nullptr, nullptr);
         k_uv_pairs<real, 1><<<ub, 128, 0, st>>>(s, nb);
     }
 }
@@ -1003,20 +1027,21 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
     const int a = tid >> 2, sub = tid & 3;
     double acc[6] = {0, 0, 0, 0, 0, 0};   // excl vv, uu, uv, 14 vv, uu, uv
     real fx = 0, fy = 0, fz = 0;
-    int sa = 0;
     if (a < s.n) {
-        sa = s.iperm[a];
-        const R4<real> pa = s.xq[sa];
-        const R2<real> la = s.lj[sa];
+        // master positions, charges sqrt(k_e) q and (sigma / 2, 2 sqrt(eps)),
+        // formed as for the cluster-sorted copy
+        R4<real> pa = s.x[a];
+        pa.w = s.q[a] * (real)sqrt(KE);
+        const R2<real> la = {(real)0.5 * s.sig[a], (real)2 * sqrt(s.eps[a])};
         const int ua = s.sol[a];
         for (int pass = 0; pass < 2; ++pass) {
             const bool is14 = pass == 1;
             const int e0 = is14 ? ex.p14_start[a] : ex.ex_start[a];
             const int e1 = is14 ? ex.p14_start[a + 1] : ex.ex_start[a + 1];
           for (int eb = e0 + sub; eb < e1; eb += 4 * EXCL_BATCH) {
-            // the partner records of a batch are loaded together (three
-            // dependent rounds: partner, its slot, its coordinates)
-            int bb[EXCL_BATCH], sbb[EXCL_BATCH];
+            // the partner records of a batch are loaded together (two
+            // dependent rounds: partner, its coordinates and charge)
+            int bb[EXCL_BATCH];
             R4<real> pbb[EXCL_BATCH];
 #pragma unroll
             for (int u = 0; u < EXCL_BATCH; ++u) {
@@ -1024,15 +1049,16 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
                 bb[u] = e < e1 ? (is14 ? ex.p14_list[e] : ex.ex_list[e]) : -1;
             }
 #pragma unroll
-            for (int u = 0; u < EXCL_BATCH; ++u) sbb[u] = bb[u] >= 0 ? s.iperm[bb[u]] : 0;
-#pragma unroll
-            for (int u = 0; u < EXCL_BATCH; ++u) if (bb[u] >= 0) pbb[u] = s.xq[sbb[u]];
+            for (int u = 0; u < EXCL_BATCH; ++u)
+                if (bb[u] >= 0) {
+                    pbb[u] = s.x[bb[u]];
+                    pbb[u].w = s.q[bb[u]] * (real)sqrt(KE);
+                }
 #pragma unroll
             for (int u = 0; u < EXCL_BATCH; ++u) {
                 const int e = eb + 4 * u;
                 if (e >= e1) break;
                 const int b = bb[u];
-                const int sb = sbb[u];
                 const R4<real> pb = pbb[u];
                 real d[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
                 for (int k = 0; k < 3; ++k) d[k] -= s.L[k] * rint_(d[k] * s.invL[k]);
@@ -1050,7 +1076,7 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
                         g = -(qq * ev * rinv2 - qq * s.two_a_sqrtpi * exp_(-ar * ar) * rinv) * rinv;
                     } else {
                         const R2<real> sc = ex.p14_s[e];
-                        const R2<real> lb = s.lj[sb];
+                        const R2<real> lb = {(real)0.5 * s.sig[b], (real)2 * sqrt(s.eps[b])};
                         en = sc.y * qq * rinv;
                         g = sc.y * qq * rinv2 * rinv;
                         const real sg = la.x + lb.x, e4 = la.y * lb.y;
@@ -1083,9 +1109,9 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
         fz += __shfl_xor_sync(0xffffffffu, fz, o);
     }
     if (a < s.n && sub == 0 && (fx != (real)0 || fy != (real)0 || fz != (real)0)) {
-        atomic_add_ll(&s.F[sa], to_fixed(fx, FSCALE));
-        atomic_add_ll(&s.F[s.n_pad + sa], to_fixed(fy, FSCALE));
-        atomic_add_ll(&s.F[2 * s.n_pad + sa], to_fixed(fz, FSCALE));
+        atomic_add_ll(&s.Fa[a], to_fixed(fx, FSCALE));
+        atomic_add_ll(&s.Fa[s.n + a], to_fixed(fy, FSCALE));
+        atomic_add_ll(&s.Fa[2 * s.n + a], to_fixed(fz, FSCALE));
     }
     const int lane = threadIdx.x & 31;
     for (int c = 0; c < 6; ++c) {

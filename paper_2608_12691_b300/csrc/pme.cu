@@ -27,18 +27,16 @@ __global__ void k_spread(SysView<real> s, PmeView<real> p)
 {
     const unsigned FULL = 0xffffffffu;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int slot = tid >> 2, sub = tid & 3;
+    const int atom = tid >> 2, sub = tid & 3;
     const int lb = (threadIdx.x & 31) & ~3;
     int a = -1;
     real q = 0;
     R4<real> xq;
     xq.x = xq.y = xq.z = xq.w = (real)0;
-    if (slot < s.n_pad) {
-        a = s.perm[slot];
-        if (a >= 0) {
-            xq = s.xq[slot];
-            q = s.q[a];
-        }
+    if (atom < s.n) {
+        a = atom;
+        xq = s.x[a];
+        q = s.q[a];
     }
     double th[4], dth[4];
     int f;
@@ -631,14 +629,12 @@ __global__ void k_conv(PmeView<real> p, long long* E, const LamState* lam)
 template <typename real>
 __global__ void k_gather(SysView<real> s, PmeView<real> p)
 {
-    int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= s.n_pad) return;
-    int a = s.perm[slot];
-    if (a < 0) return;
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= s.n) return;
     const real q = s.q[a];
     if (q == (real)0) return;
     const bool u = s.sol[a] != 0;
-    const R4<real> xq = s.xq[slot];
+    const R4<real> xq = s.x[a];
     real th[3][4], dth[3][4];
     int f[3];
     real xs[3] = {xq.x, xq.y, xq.z};
@@ -668,15 +664,15 @@ __global__ void k_gather(SysView<real> s, PmeView<real> p)
         }
     }
     const real fx = -q * p.kscale[0] * gx, fy = -q * p.kscale[1] * gy, fz = -q * p.kscale[2] * gz;
-    atomic_add_ll(&s.F[slot], to_fixed(fx, FSCALE));
-    atomic_add_ll(&s.F[s.n_pad + slot], to_fixed(fy, FSCALE));
-    atomic_add_ll(&s.F[2 * s.n_pad + slot], to_fixed(fz, FSCALE));
+    atomic_add_ll(&s.Fa[a], to_fixed(fx, FSCALE));
+    atomic_add_ll(&s.Fa[s.n + a], to_fixed(fy, FSCALE));
+    atomic_add_ll(&s.Fa[2 * s.n + a], to_fixed(fz, FSCALE));
 }
 
 template <typename real>
 void launch_spread(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st)
 {
-    k_spread<real><<<(4 * s.n_pad + 127) / 128, 128, 0, st>>>(s, p);
+    k_spread<real><<<(4 * s.n + 127) / 128, 128, 0, st>>>(s, p);
 }
 template <typename real>
 void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode, cudaStream_t st)
@@ -689,7 +685,7 @@ void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int 
 template <typename real>
 void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st)
 {
-    k_gather<real><<<(s.n_pad + 127) / 128, 128, 0, st>>>(s, p);
+    k_gather<real><<<(s.n + 127) / 128, 128, 0, st>>>(s, p);
 }
 
 // energy64 (FP32 systems): the FP64 energy branch.  The first FP32 pass
