@@ -167,9 +167,12 @@ __global__ void k_col_scatter(SysView<real> s, NblView<real> nb)
 
 constexpr int COL_MAX = 2048;   // atoms per column handled by one block
 
-// one block per column: rank sort by (wrapped z, atom index)
+// one block per column: rank sort by (wrapped z, atom index); four threads
+// share the count of each atom's rank
+constexpr int COL_THREADS = 1024;
+
 template <typename real>
-__global__ void __launch_bounds__(256) k_col_sort(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(COL_THREADS) k_col_sort(SysView<real> s, NblView<real> nb)
 {
     __shared__ float zs[COL_MAX];
     __shared__ int ids[COL_MAX];
@@ -186,15 +189,21 @@ __global__ void __launch_bounds__(256) k_col_sort(SysView<real> s, NblView<real>
         zs[k] = (float)wrap_box(s.x[a].z, s.L[2], s.invL[2]);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        const float z = zs[k];
-        const int a = ids[k];
+    const int sub = threadIdx.x & 3;
+    for (int k0 = 0; k0 < cnt; k0 += blockDim.x >> 2) {
+        const int k = k0 + (threadIdx.x >> 2);
+        const bool ok = k < cnt;
+        const float z = ok ? zs[k] : 0.f;
+        const int a = ok ? ids[k] : 0;
         int rank = 0;
-        for (int m = 0; m < cnt; ++m) {
-            const float zm = zs[m];
-            rank += (zm < z) || (zm == z && ids[m] < a);
-        }
-        nb.tmp2[b + rank] = a;
+        if (ok)
+            for (int m = sub; m < cnt; m += 4) {
+                const float zm = zs[m];
+                rank += (zm < z) || (zm == z && ids[m] < a);
+            }
+        rank += __shfl_xor_sync(0xffffffffu, rank, 1);
+        rank += __shfl_xor_sync(0xffffffffu, rank, 2);
+        if (ok && sub == 0) nb.tmp2[b + rank] = a;
     }
     if (threadIdx.x == 0) nb.col_fill[c] = 0;
 }
@@ -315,178 +324,180 @@ __device__ __forceinline__ float box_gap2(const SysView<real>& s, const R4<float
 
 // Tile list.  A tile pairs the 8 atoms of one i sub-cluster I8 (slots
 // 8 I8 .. 8 I8 + 7 of the cluster-sorted order) with 32 j atoms under one
-// periodic shift and one class (vv, uu or uv).  One warp per (I8, shift):
-// for each class of partner cluster (solute, solvent) every atom of every
-// 32-atom partner cluster J whose box is within r_cut + skin of I8's box is
-// appended to a j list when the atom itself is within r_cut + skin of that
-// box and lies in a sub-cluster J8 > I8, or in I8 itself under a shift past
-// the middle one (13), or in I8 under no shift (pairs j > i, left to the
-// masks) -- so every pair image is listed once.  The warp first lists the
-// partner clusters whose boxes are in range (four chunks of 32 boxes in
-// flight), then filters their atoms TILE_BATCH clusters per batch of loads.
+// periodic shift and one class (vv, uu or uv).  For each (I8, shift) and
+// each class of partner cluster (solute, solvent) every atom of every 32-atom
+// partner cluster J whose box is within r_cut + skin of I8's box is appended
+// to a j list when the atom itself is within r_cut + skin of that box and
+// lies in a sub-cluster J8 > I8, or in I8 itself under a shift past the
+// middle one (13), or in I8 under no shift (pairs j > i, left to the masks)
+// -- so every pair image is listed once.  One block per I8: its threads list
+// the partner clusters whose boxes are in range (one box per thread), its
+// warps filter those clusters' atoms (TILE_BATCH clusters per warp per batch
+// of loads), and a block scan of the kept counts places every kept atom.
 //
-// One pass: each round (up to TILE_CAND partner clusters) first filters the
-// atoms, then reserves exactly the tiles it starts in a staging list -- in
-// the order warps happen to get there -- and writes them with their (I8,
-// shift, class, ordinal).  k_place then moves every tile to its final,
-// deterministic place (the tiles of one I8 contiguous and shift-major) from
-// the per-(I8, shift) counts written here.
-constexpr int TILE_CAND = 128;     // partner clusters listed per round (per warp)
-constexpr int TILE_BATCH = 8;      // partner clusters whose atoms are loaded together
+// One pass: each round (up to TILE_CAND partner clusters) reserves exactly
+// the tiles it starts in a staging list -- in the order blocks happen to get
+// there -- and writes them with their (I8, shift, class, ordinal).  k_place
+// then moves every tile to its final, deterministic place (the tiles of one
+// I8 contiguous and shift-major) from the per-(I8, shift) counts written
+// here.
+constexpr int TILE_WARPS = 4;      // warps of one block (one i sub-cluster)
+constexpr int TILE_CAND = 256;     // partner clusters listed per round
+constexpr int TILE_BATCH = 8;      // partner clusters whose atoms one warp loads together
 
-// one (I8, shift) search by one warp; returns the number of tiles it started
+struct TileShared {
+    int cand[TILE_CAND];           // partner clusters of the round, ascending
+    unsigned kb[TILE_CAND];        // their kept lanes
+    int kpre[TILE_CAND];           // exclusive prefix of the kept atoms over the round
+    int wcnt[TILE_WARPS];
+    int wsum[32];
+    int r0;                        // staging slots reserved by the round
+    int cnt[27];                   // tiles per shift
+};
+
+// one (I8, shift) search by the whole block; returns the number of tiles
+// started (the same value in every thread)
 template <typename real>
-__device__ int tile_search(const SysView<real>& s, const NblView<real>& nb, int I8, int sh, int* cand,
-                           unsigned* kb, int lane)
+__device__ int tile_search(const SysView<real>& s, const NblView<real>& nb, int I8, int sh, TileShared& sm)
 {
+    const int tid = threadIdx.x, wl = tid >> 5, lane = tid & 31;
+    constexpr int NT = TILE_WARPS * 32;
     const int I = I8 >> 2;
     const int ncl = num_clusters(s, nb);
     const R4<float> ci = nb.bbc8[I8], hi = nb.bbh8[I8];
     const bool iu = I < s.n_ucl;
-    int count = 0;        // tiles started by this warp (the next tile's ordinal)
+    int count = 0;        // tiles started (the next tile's ordinal)
     bool dead = false;    // the staging list ran out: nothing more is written
     int svs[3];
     shift_vec(sh, svs);
     const unsigned lt = (1u << lane) - 1u;
-    {
-        const float shx = svs[0] * (float)s.L[0], shy = svs[1] * (float)s.L[1], shz = svs[2] * (float)s.L[2];
-        const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
-        // sub-clusters of partner atoms that may pair with I8 under this shift
-        const int j8min = sh >= 13 ? I8 : I8 + 1;
-        for (int jc = 0; jc < 2; ++jc) {
-            const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
-            const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
-            int nbuf = 0;   // atoms already placed in the open tile (staging slot cur)
-            int cur = -1;
-            int J0 = max(I, jb);
-            while (J0 < je) {
-                // list the partner clusters in range, in ascending order
-                int nc = 0;
-                while (J0 < je && nc + 128 <= TILE_CAND) {
-                    bool pc[4];
+    const float shx = svs[0] * (float)s.L[0], shy = svs[1] * (float)s.L[1], shz = svs[2] * (float)s.L[2];
+    const float c0[3] = {ci.x, ci.y, ci.z}, h0[3] = {hi.x, hi.y, hi.z};
+    // sub-clusters of partner atoms that may pair with I8 under this shift
+    const int j8min = sh >= 13 ? I8 : I8 + 1;
+    for (int jc = 0; jc < 2; ++jc) {
+        const int jb = jc == 0 ? 0 : s.n_ucl, je = jc == 0 ? s.n_ucl : ncl;
+        const int cls = (iu && jc == 0) ? 1 : ((iu || jc == 0) ? 2 : 0);
+        int nbuf = 0;   // atoms already placed in the open tile (staging slot cur)
+        int cur = -1;
+        int J0 = max(I, jb);
+        while (J0 < je) {
+            // list the partner clusters in range, in ascending order
+            int nc = 0;
+            while (J0 < je && nc + NT <= TILE_CAND) {
+                const int J = J0 + tid;
+                bool pc = J < je && 4 * J + 3 >= j8min;
+                if (pc) pc = box_gap2(s, ci, hi, nb.bbc[J], nb.bbh[J], sh) < nb.cut2;
+                const unsigned bal = __ballot_sync(0xffffffffu, pc);
+                if (lane == 0) sm.wcnt[wl] = __popc(bal);
+                __syncthreads();
+                int off = nc, tot = 0;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int J = J0 + 32 * u + lane;
-                        pc[u] = J < je && 4 * J + 3 >= j8min;
-                        if (pc[u]) pc[u] = box_gap2(s, ci, hi, nb.bbc[J], nb.bbh[J], sh) < nb.cut2;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const unsigned bal = __ballot_sync(0xffffffffu, pc[u]);
-                        if (pc[u]) cand[nc + __popc(bal & lt)] = J0 + 32 * u + lane;
-                        nc += __popc(bal);
-                    }
-                    J0 += 128;
+                for (int w = 0; w < TILE_WARPS; ++w) {
+                    off += w < wl ? sm.wcnt[w] : 0;
+                    tot += sm.wcnt[w];
                 }
-                __syncwarp();
-                if (nc == 0) continue;
-                // filter their atoms, TILE_BATCH clusters per batch of loads;
-                // the kept lanes of candidate c go to kb[c]
-                int K = 0;
-                for (int c0i = 0; c0i < nc; c0i += TILE_BATCH) {
-                    R4<real> pbuf[TILE_BATCH];
-                    bool live[TILE_BATCH];
-#pragma unroll
-                    for (int u = 0; u < TILE_BATCH; ++u) {
-                        const int slot = c0i + u < nc ? cand[c0i + u] * 32 + lane : -1;
-                        live[u] = slot >= 0 && (slot >> 3) >= j8min && s.perm[slot] >= 0;
-                        if (slot >= 0) pbuf[u] = s.xq[slot];
-                    }
-#pragma unroll
-                    for (int u = 0; u < TILE_BATCH; ++u) {
-                        if (c0i + u >= nc) break;
-                        bool keep = live[u];
-                        if (keep) {
-                            const float pv[3] = {(float)pbuf[u].x + shx, (float)pbuf[u].y + shy,
-                                                 (float)pbuf[u].z + shz};
-                            float d2 = 0.f;
-                            for (int d = 0; d < 3; ++d) {
-                                const float g = fmaxf(fabsf(pv[d] - c0[d]) - h0[d], 0.f);
-                                d2 += g * g;
-                            }
-                            keep = d2 < nb.cut2;
-                        }
-                        const unsigned kbu = __ballot_sync(0xffffffffu, keep);
-                        if (lane == 0) kb[c0i + u] = kbu;
-                        K += __popc(kbu);
-                    }
-                }
-                __syncwarp();
-                // reserve exactly the tiles this round starts
-                // (none when the kept atoms all fit in the open tile)
-                if (K == 0) continue;
-                const int nnew = (nbuf + K + 31) / 32 - (nbuf > 0 ? 1 : 0);
-                int r0 = 0;
-                if (lane == 0 && nnew > 0) r0 = atomicAdd(s.flags + FL_NSTAGE, nnew);
-                r0 = __shfl_sync(0xffffffffu, r0, 0);
-                if (!dead && r0 + nnew > nb.stage_cap) {
-                    dead = true;
-                    if (lane == 0) atomicOr(s.flags + FL_ERROR, ERRB_OVERFLOW);
-                    // the open tile keeps what it has
-                    if (nbuf > 0 && lane >= nbuf) nb.stage_j[(size_t)cur * 32 + lane] = -1;
-                }
-                if (dead) {
-                    // the reserved slots inside the list are marked unused
-                    for (int k = r0 + lane; k < min(r0 + nnew, nb.stage_cap); k += 32)
-                        nb.stage_hdr[k] = make_int4(0, 0, 0, -1);
-                    count += nnew;
-                    nbuf = (nbuf + K) & 31;
-                    continue;
-                }
-                int rused = 0;
-                for (int c = 0; c < nc; ++c) {
-                    const unsigned kbu = kb[c];
-                    if (kbu == 0u) continue;
-                    const int nk = __popc(kbu);
-                    // the open tile (or a new one), and the tile after it if the
-                    // kept atoms run past 32
-                    int slotA = cur;
-                    if (nbuf == 0) {
-                        slotA = r0 + rused++;
-                        if (lane == 0) nb.stage_hdr[slotA] = make_int4(I8, sh, cls, count);
-                        ++count;
-                    }
-                    int slotB = -1;
-                    if (nbuf + nk > 32) {
-                        slotB = r0 + rused++;
-                        if (lane == 0) nb.stage_hdr[slotB] = make_int4(I8, sh, cls, count);
-                        ++count;
-                    }
-                    if ((kbu >> lane) & 1u) {
-                        const int pos = nbuf + __popc(kbu & lt);
-                        nb.stage_j[(size_t)(pos < 32 ? slotA : slotB) * 32 + (pos & 31)] = cand[c] * 32 + lane;
-                    }
-                    nbuf += nk;
-                    if (nbuf >= 32) {
-                        nbuf -= 32;
-                        cur = slotB;
-                    } else {
-                        cur = slotA;
-                    }
-                }
-                __syncwarp();
+                if (pc) sm.cand[off + __popc(bal & lt)] = J;
+                nc += tot;
+                J0 += NT;
+                __syncthreads();
             }
-            if (nbuf > 0 && !dead && lane >= nbuf) nb.stage_j[(size_t)cur * 32 + lane] = -1;
+            if (nc == 0) continue;
+            // filter the candidates' atoms: warp wl takes candidates wl, wl + 4, ...
+            for (int cb = wl; cb < nc; cb += TILE_WARPS * TILE_BATCH) {
+                R4<real> pbuf[TILE_BATCH];
+                bool live[TILE_BATCH];
+#pragma unroll
+                for (int u = 0; u < TILE_BATCH; ++u) {
+                    const int c = cb + TILE_WARPS * u;
+                    const int slot = c < nc ? sm.cand[c] * 32 + lane : -1;
+                    live[u] = slot >= 0 && (slot >> 3) >= j8min && s.perm[slot] >= 0;
+                    if (slot >= 0) pbuf[u] = s.xq[slot];
+                }
+#pragma unroll
+                for (int u = 0; u < TILE_BATCH; ++u) {
+                    const int c = cb + TILE_WARPS * u;
+                    if (c >= nc) break;
+                    bool keep = live[u];
+                    if (keep) {
+                        const float pv[3] = {(float)pbuf[u].x + shx, (float)pbuf[u].y + shy,
+                                             (float)pbuf[u].z + shz};
+                        float d2 = 0.f;
+                        for (int d = 0; d < 3; ++d) {
+                            const float g = fmaxf(fabsf(pv[d] - c0[d]) - h0[d], 0.f);
+                            d2 += g * g;
+                        }
+                        keep = d2 < nb.cut2;
+                    }
+                    const unsigned kbu = __ballot_sync(0xffffffffu, keep);
+                    if (lane == 0) sm.kb[c] = kbu;
+                }
+            }
+            __syncthreads();
+            // exclusive prefix of the kept atoms over the candidates (two per thread)
+            const int k0 = 2 * tid < nc ? __popc(sm.kb[2 * tid]) : 0;
+            const int k1 = 2 * tid + 1 < nc ? __popc(sm.kb[2 * tid + 1]) : 0;
+            int K = 0;
+            const int ex = block_exscan(k0 + k1, sm.wsum, &K);
+            if (2 * tid < nc) sm.kpre[2 * tid] = ex;
+            if (2 * tid + 1 < nc) sm.kpre[2 * tid + 1] = ex + k0;
+            // reserve exactly the tiles this round starts (none when the kept
+            // atoms all fit in the open tile)
+            if (K == 0) {
+                __syncthreads();
+                continue;
+            }
+            const int nnew = (nbuf + K + 31) / 32 - (nbuf > 0 ? 1 : 0);
+            if (tid == 0) sm.r0 = nnew > 0 ? atomicAdd(s.flags + FL_NSTAGE, nnew) : 0;
+            __syncthreads();
+            const int r0 = sm.r0;
+            if (!dead && r0 + nnew > nb.stage_cap) {
+                dead = true;
+                if (tid == 0) atomicOr(s.flags + FL_ERROR, ERRB_OVERFLOW);
+                // the open tile keeps what it has
+                if (nbuf > 0 && tid >= nbuf && tid < 32) nb.stage_j[(size_t)cur * 32 + tid] = -1;
+            }
+            const int total = nbuf + K;
+            if (dead) {
+                // the reserved slots inside the list are marked unused
+                for (int k = r0 + tid; k < min(r0 + nnew, nb.stage_cap); k += NT)
+                    nb.stage_hdr[k] = make_int4(0, 0, 0, -1);
+            } else {
+                for (int k = tid; k < nnew; k += NT) nb.stage_hdr[r0 + k] = make_int4(I8, sh, cls, count + k);
+                // every kept atom knows its place: position nbuf + prefix in
+                // the run of tiles that starts with the open one
+                for (int c = wl; c < nc; c += TILE_WARPS) {
+                    const unsigned kbu = sm.kb[c];
+                    if (!((kbu >> lane) & 1u)) continue;
+                    const int pos = nbuf + sm.kpre[c] + __popc(kbu & lt);
+                    const int t = pos >> 5;
+                    const int slot = nbuf > 0 ? (t == 0 ? cur : r0 + t - 1) : r0 + t;
+                    nb.stage_j[(size_t)slot * 32 + (pos & 31)] = sm.cand[c] * 32 + lane;
+                }
+                const int tl = (total - 1) >> 5;
+                cur = nbuf > 0 ? (tl == 0 ? cur : r0 + tl - 1) : r0 + tl;
+            }
+            count += nnew;
+            nbuf = total & 31;
+            if (nbuf == 0) cur = -1;
+            __syncthreads();
         }
+        if (nbuf > 0 && !dead && tid >= nbuf && tid < 32) nb.stage_j[(size_t)cur * 32 + tid] = -1;
     }
     return count;
 }
 
-// One block per i sub-cluster I8; its TILE_WARPS warps take turns over the
-// shifts that can bring partners within the cutoff: every atom lies in
-// [0, L), so a shift -1 (+1) along an axis is needed only if I8's box reaches
-// within r_cut + skin of the lower (upper) face.  The block then turns the 27
+// One block per i sub-cluster I8; its warps search the shifts that can bring
+// partners within the cutoff one after another: every atom lies in [0, L),
+// so a shift -1 (+1) along an axis is needed only if I8's box reaches within
+// r_cut + skin of the lower (upper) face.  The block then turns the 27
 // counts into offsets inside I8 (tile_cnt) and I8's total (tile_tot).
-constexpr int TILE_WARPS = 2;
-
 template <typename real>
 __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblView<real> nb)
 {
-    __shared__ int cand_sh[TILE_WARPS][TILE_CAND];
-    __shared__ unsigned kb_sh[TILE_WARPS][TILE_CAND];
-    __shared__ int cnt_sh[27];
+    __shared__ TileShared sm;
     const int I8 = blockIdx.x;
-    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, wl = tid >> 5, lane = tid & 31;
     const int I = I8 >> 2;
     const R4<float> ci = nb.bbc8[I8], hi = nb.bbh8[I8];
     const bool live = I < num_clusters(s, nb) && hi.w >= 0.f;
@@ -501,19 +512,17 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblV
             if (sv[d] > 0 && !(c0[d] + h0[d] > (float)s.L[d] - cut)) ok = false;
         }
     }
-    const unsigned allow = __ballot_sync(0xffffffffu, ok);
-    if (wl == 0 && lane < 27 && !ok) cnt_sh[lane] = 0;
-    int k = 0;
-    for (unsigned m = allow; m; m &= m - 1u, ++k) {
-        if (k % TILE_WARPS != wl) continue;
+    const unsigned allow = __ballot_sync(0xffffffffu, ok);   // the same in every warp
+    if (tid < 27) sm.cnt[tid] = 0;
+    for (unsigned m = allow; m; m &= m - 1u) {
         const int sh = __ffs(m) - 1;
-        const int count = tile_search(s, nb, I8, sh, cand_sh[wl], kb_sh[wl], lane);
-        if (lane == 0) cnt_sh[sh] = count;
+        const int count = tile_search(s, nb, I8, sh, sm);
+        if (tid == 0) sm.cnt[sh] = count;
     }
     __syncthreads();
     // offsets of the shifts inside I8, and I8's total for the scan
     if (wl == 0) {
-        const int c = lane < 27 ? cnt_sh[lane] : 0;
+        const int c = lane < 27 ? sm.cnt[lane] : 0;
         int incl = c;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -539,7 +548,6 @@ template <typename real>
 __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb)
 {
     __shared__ int jsl[4][4][33];   // [warp][tile][k]: j slot (INT_MAX if empty)
-    __shared__ int jmol[4][4][33];  // [warp][tile][k]: j molecule (-2 if empty)
     const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
     const int g = lane >> 3, r = lane & 7;
     const int nst = min(s.flags[FL_NSTAGE], nb.stage_cap);
@@ -562,13 +570,19 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) b[u] = js[u] >= 0 ? s.perm[js[u]] : -1;
-        unsigned valid = 0u;
-        int4 my = make_int4(0, 0, 0, -1);
+        int jm[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jm[u] = b[u] >= 0 ? nb.mol[b[u]] : -2;
+        // the i row of this lane: tile g, atom 8 I8 + r
+        const int gI8 = g == 0 ? h[0].x : (g == 1 ? h[1].x : (g == 2 ? h[2].x : h[3].x));
+        const int islot = gI8 * 8 + r;
+        const int a = s.perm[islot];
+        const int ma = a >= 0 ? nb.mol[a] : -3;
+        unsigned valid = 0u, same = 0u, before = 0u;
         int mydest = -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             jsl[wl][u][lane] = js[u] >= 0 ? js[u] : 0x7fffffff;
-            jmol[wl][u][lane] = b[u] >= 0 ? nb.mol[b[u]] : -2;
             const unsigned bal = __ballot_sync(0xffffffffu, b[u] >= 0);
             if (dest[u] >= 0) {
                 nb.jidx[(size_t)dest[u] * 32 + lane] = js[u];
@@ -576,24 +590,26 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
             }
             if (u == g) {
                 valid = bal;
-                my = h[u];
                 mydest = dest[u];
+            }
+            // rows of tile u: j atoms of the row's molecule, and (no shift) the
+            // j slots of I8 itself at or before the row's slot (not computed)
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) {
+                const int mr = __shfl_sync(0xffffffffu, ma, 8 * u + rr);
+                const unsigned bs = __ballot_sync(0xffffffffu, jm[u] == mr);
+                unsigned bb = 0u;
+                if (h[u].y == 13)
+                    bb = __ballot_sync(0xffffffffu, js[u] >= h[u].x * 8 && js[u] <= h[u].x * 8 + rr);
+                if (lane == 8 * u + rr) {
+                    same = bs;
+                    before = bb;
+                }
             }
         }
         __syncwarp();
         if (mydest >= 0) {
-            const int islot = my.x * 8 + r;
-            const int a = s.perm[islot];
-            const int ma = a >= 0 ? nb.mol[a] : -3;
             const int* sl = jsl[wl][g];
-            unsigned same = 0u, before = 0u;
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) {
-                const int sk = sl[k];
-                same |= (jmol[wl][g][k] == ma ? 1u : 0u) << k;
-                // j slots of I8 itself at or before slot i (no shift): not computed
-                before |= (my.y == 13 && sk >= my.x * 8 && sk <= islot ? 1u : 0u) << k;
-            }
             unsigned m = 0u;
             if (a >= 0) m = valid & ~before;
             if (m & same) {
@@ -685,7 +701,7 @@ void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStrea
         k_scan_block<1><<<1, 1024, 0, st>>>(nb.col_cnt, nb.col_start, nb.ncols, nullptr, 0, nullptr, nb.col_cl,
                                             nb.n_cl_solv);
         k_col_scatter<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
-        k_col_sort<real><<<nb.ncols, 256, 0, st>>>(s, nb);
+        k_col_sort<real><<<nb.ncols, COL_THREADS, 0, st>>>(s, nb);
     }
     k_assign<real><<<(s.n_pad + B - 1) / B, B, 0, st>>>(s, nb);
     k_tiles<real><<<nb.n_cl_max * 4, TILE_WARPS * 32, 0, st>>>(s, nb);
