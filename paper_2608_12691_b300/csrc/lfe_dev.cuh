@@ -40,6 +40,15 @@ enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4 };
 // built from)
 __device__ __forceinline__ float floor_w(float x) { return floorf(x); }
 __device__ __forceinline__ double floor_w(double x) { return floor(x); }
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while its predecessor in
+// the stream is still running; pdl_wait() returns once the predecessor has
+// completed and its memory is visible, so every such kernel calls it before
+// touching memory.  pdl_trigger() lets the dependent kernel be scheduled
+// early.  Both are no-ops for kernels launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 template <typename real>
 __device__ __forceinline__ real wrap_box(real x, real L, real invL)
 {

@@ -46,6 +46,7 @@ __device__ __forceinline__ unsigned spread_bits(unsigned v)
 template <typename real>
 __global__ void k_col_keys(SysView<real> s, NblView<real> nb)
 {
+    pdl_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_solv) return;
     const R4<real> p = s.x[s.solv_list[i]];
@@ -93,6 +94,8 @@ template <int CL>
 __global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, int* total, int cap, int* errflag,
                                                      int* out2, int* total2)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int PER_MAX = 32;
     __shared__ int wsum[32];
     const int tid = threadIdx.x;
@@ -158,6 +161,8 @@ __global__ void __launch_bounds__(1024) k_scan_block(int* in, int* out, int n, i
 template <typename real>
 __global__ void k_col_scatter(SysView<real> s, NblView<real> nb)
 {
+    pdl_wait();
+    pdl_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s.n_solv) return;
     const int c = nb.col_of[i];
@@ -174,6 +179,8 @@ constexpr int COL_THREADS = 1024;
 template <typename real>
 __global__ void __launch_bounds__(COL_THREADS) k_col_sort(SysView<real> s, NblView<real> nb)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float zs[COL_MAX];
     __shared__ int ids[COL_MAX];
     const int c = blockIdx.x;
@@ -214,6 +221,8 @@ __global__ void __launch_bounds__(COL_THREADS) k_col_sort(SysView<real> s, NblVi
 template <typename real>
 __global__ void k_assign(SysView<real> s, NblView<real> nb)
 {
+    pdl_wait();
+    pdl_trigger();
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= s.n_pad) return;
     int a = -1;
@@ -495,6 +504,8 @@ __device__ int tile_search(const SysView<real>& s, const NblView<real>& nb, int 
 template <typename real>
 __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblView<real> nb)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ TileShared sm;
     const int I8 = blockIdx.x;
     const int tid = threadIdx.x, wl = tid >> 5, lane = tid & 31;
@@ -543,10 +554,13 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblV
 // atoms: each excluded partner's slot is looked up in the tile's ascending j
 // slots by bisection.
 constexpr int PLACE_BLOCKS_PER_SM = 16;
+constexpr int PLACE_EX_BATCH = 8;     // exclusions looked up per batch of loads
 
 template <typename real>
 __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int jsl[4][4][33];   // [warp][tile][k]: j slot (INT_MAX if empty)
     const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
     const int g = lane >> 3, r = lane & 7;
@@ -613,15 +627,26 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
             unsigned m = 0u;
             if (a >= 0) m = valid & ~before;
             if (m & same) {
-                for (int e = nb.ex_start[a]; e < nb.ex_start[a + 1]; ++e) {
-                    const int sb = s.iperm[nb.ex_list[e]];
-                    int lo = 0, hi = 31;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sl[mid] < sb) lo = mid + 1;
-                        else hi = mid;
+                // excluded partners' slots, PLACE_EX_BATCH loads in flight
+                const int e0 = nb.ex_start[a], e1 = nb.ex_start[a + 1];
+                for (int eb = e0; eb < e1; eb += PLACE_EX_BATCH) {
+                    int sbv[PLACE_EX_BATCH];
+#pragma unroll
+                    for (int u = 0; u < PLACE_EX_BATCH; ++u) sbv[u] = eb + u < e1 ? nb.ex_list[eb + u] : -1;
+#pragma unroll
+                    for (int u = 0; u < PLACE_EX_BATCH; ++u) sbv[u] = sbv[u] >= 0 ? s.iperm[sbv[u]] : -1;
+#pragma unroll
+                    for (int u = 0; u < PLACE_EX_BATCH; ++u) {
+                        const int sb = sbv[u];
+                        if (sb < 0) continue;
+                        int lo = 0, hi = 31;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sl[mid] < sb) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        if (sl[lo] == sb) m &= ~(1u << lo);
                     }
-                    if (sl[lo] == sb) m &= ~(1u << lo);
                 }
             }
             nb.masks[(size_t)mydest * 8 + r] = m;
@@ -637,6 +662,8 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
 template <typename real, int WRITE>
 __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real> nb)
 {
+    pdl_wait();
+    pdl_trigger();
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (t >= nb.uv_tiles_max) return;
@@ -692,30 +719,34 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
     }
 }
 
+// The build is a chain of kernels on one stream: every kernel after the
+// first is launched as a programmatic dependent of the one before it.
 template <typename real>
 void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st)
 {
     const int B = 256;
+    bool pdl = false;   // the first kernel follows whatever preceded the build
     if (s.n_solv > 0) {
         k_col_keys<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
-        k_scan_block<1><<<1, 1024, 0, st>>>(nb.col_cnt, nb.col_start, nb.ncols, nullptr, 0, nullptr, nb.col_cl,
-                                            nb.n_cl_solv);
-        k_col_scatter<real><<<(s.n_solv + B - 1) / B, B, 0, st>>>(s, nb);
-        k_col_sort<real><<<nb.ncols, COL_THREADS, 0, st>>>(s, nb);
+        launch_k(true, k_scan_block<1>, 1, 1024, 0, st, nb.col_cnt, nb.col_start, nb.ncols, (int*)nullptr, 0,
+                 (int*)nullptr, nb.col_cl, nb.n_cl_solv);
+        launch_k(true, k_col_scatter<real>, (s.n_solv + B - 1) / B, B, 0, st, s, nb);
+        launch_k(true, k_col_sort<real>, nb.ncols, COL_THREADS, 0, st, s, nb);
+        pdl = true;
     }
-    k_assign<real><<<(s.n_pad + B - 1) / B, B, 0, st>>>(s, nb);
-    k_tiles<real><<<nb.n_cl_max * 4, TILE_WARPS * 32, 0, st>>>(s, nb);
-    k_scan_block<0><<<1, 1024, 0, st>>>(nb.tile_tot, nb.tile_off, nb.n_cl_max * 4, s.flags + FL_NTILES, nb.cap,
-                                        s.flags + FL_ERROR, nullptr, nullptr);
+    launch_k(pdl, k_assign<real>, (s.n_pad + B - 1) / B, B, 0, st, s, nb);
+    launch_k(true, k_tiles<real>, nb.n_cl_max * 4, TILE_WARPS * 32, 0, st, s, nb);
+    launch_k(true, k_scan_block<0>, 1, 1024, 0, st, nb.tile_tot, nb.tile_off, nb.n_cl_max * 4, s.flags + FL_NTILES,
+             nb.cap, s.flags + FL_ERROR, (int*)nullptr, (int*)nullptr);
     const long long pq = ((long long)nb.stage_cap + 15) / 16;   // blocks of four warps x four tiles
     const long long pmax = (long long)nb.n_sm * PLACE_BLOCKS_PER_SM;
-    k_place<real><<<(int)(pq < pmax ? pq : pmax), 128, 0, st>>>(s, nb);
+    launch_k(true, k_place<real>, (int)(pq < pmax ? pq : pmax), 128, 0, st, s, nb);
     if (s.n_ucl > 0) {
         const int ub = (nb.uv_tiles_max * 32 + 127) / 128;
-        k_uv_pairs<real, 0><<<ub, 128, 0, st>>>(s, nb);
-        k_scan_block<0><<<1, 1024, 0, st>>>(nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV, nb.uv_cap,
-                                            s.flags + FL_ERROR, nullptr, nullptr);
-        k_uv_pairs<real, 1><<<ub, 128, 0, st>>>(s, nb);
+        launch_k(true, k_uv_pairs<real, 0>, ub, 128, 0, st, s, nb);
+        launch_k(true, k_scan_block<0>, 1, 1024, 0, st, nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV,
+                 nb.uv_cap, s.flags + FL_ERROR, (int*)nullptr, (int*)nullptr);
+        launch_k(true, k_uv_pairs<real, 1>, ub, 128, 0, st, s, nb);
     }
 }
 
