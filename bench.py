@@ -34,7 +34,7 @@ FLOPS_PER_PAIR = 67
 # DRAM bytes (read + write) of one k_pairs<float> launch on the octanol workload, from an ncu
 # capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum); reset to
 # None whenever the pair kernel changes
-PAIR_DRAM_BYTES_OCTANOL = 4.233728e6 + 0.0
+PAIR_DRAM_BYTES_OCTANOL = 7.134208e6 + 0.0
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
@@ -319,13 +319,16 @@ def run_ours(args):
     ms_step = total_ms / args.steps
     ns_day = dt_ps * 1e-3 * 86400.0 / (ms_step * 1e-3) * world
     rebuilds = int(ext1["n_rebuilds"] - ext0["n_rebuilds"])
-    # kernels of one captured step (FP32 systems): pair kernel; spread, plane
-    # transform, column pass, inverse plane transform, gather; FP64 energy
-    # branch (two transform passes, column pass); FP64 uv energies,
-    # exclusions/1-4, bonded; kicks and OPES bias; integrator, theta, step
-    # end.  A neighbour-list build adds 15 kernels.
-    per_step = 17 if prec == lfe.LFE_FP32_MIXED else 14
-    launches = args.steps * per_step + rebuilds * 15
+    # kernels of one captured step (FP32 systems): rebuild decision, pair
+    # kernel; spread, plane transform, column pass, inverse plane transform,
+    # gather; FP64 energy branch (two transform passes, column pass); kicks
+    # and OPES bias, exclusions/1-4, bonded, FP64 uv energies; integrator,
+    # theta, step end.  A neighbour-list build adds 11 kernels (column keys,
+    # column scan, scatter, column sort, slot assignment, tile search, tile
+    # scan, placement + masks, uv pair count, scan, write).
+    per_step = 18 if prec == lfe.LFE_FP32_MIXED else 15
+    launches = args.steps * per_step + rebuilds * 11
+    n_tiles = int(ext1["n_tiles"])
 
     out = None
     if rank == 0:
@@ -380,7 +383,8 @@ def run_ours(args):
                           "precision": "FP32 arithmetic, int64 fixed-point force/energy sums, FP64 lambda/OPES"
                           if prec == lfe.LFE_FP32_MIXED else "FP64", "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single replica",
-                          "pairs_per_step": n_pairs},
+                          "pairs_per_step": n_pairs, "tiles": n_tiles,
+                          "tile_efficiency": n_pairs / (256.0 * n_tiles) if n_tiles else None},
                "pair_interactions_per_s": n_pairs / (ms_step * 1e-3) * world,
                "wall_ms_per_step": wall / args.steps * 1e3,
                "neighbour_rebuilds": rebuilds,

@@ -205,9 +205,11 @@ int lfe_step(lfe_system* sys, int n_steps, void* stream);
 
 /* Copy state to host: pos [3N], vel [3N] (either may be NULL); ext (may be
  * NULL) receives LFE_NEXT doubles: [theta, p_theta, lambda, dU/dlambda, U,
- * n_kernels_std, n_kernels_exp, step, neighbour rebuilds done by lfe_step].
+ * n_kernels_std, n_kernels_exp, step, neighbour rebuilds done by lfe_step
+ * (and by evaluations that found a rebuild left pending by the last step),
+ * tiles of the current neighbour list (8 i atoms x 32 j atoms each)].
  * Synchronises the device and reports errors raised by queued steps. */
-#define LFE_NEXT 9
+#define LFE_NEXT 10
 int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext);
 
 /* d-AFED (Eq. 15): n_cv torsions xi_k (atoms[4k .. 4k+3], the IUPAC sign:

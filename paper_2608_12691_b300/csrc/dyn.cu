@@ -180,7 +180,7 @@ __global__ void k_pack_state(SysView<real> s, const OpesState* o, double* out)
         double* e = out + 6 * (size_t)s.n;
         e[0] = L->theta; e[1] = L->p_theta; e[2] = L->lambda; e[3] = L->dUdl; e[4] = L->U;
         e[5] = o->n[0]; e[6] = o->n[1]; e[7] = (double)L->step;
-        e[8] = s.flags[FL_NREBUILD]; e[9] = s.flags[FL_ERROR]; e[10] = s.flags[FL_NTILES];
+        e[8] = s.flags[FL_NREBUILD]; e[9] = s.flags[FL_NTILES]; e[10] = s.flags[FL_ERROR];
     }
 }
 

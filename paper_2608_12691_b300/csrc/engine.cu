@@ -1171,7 +1171,7 @@ struct System final : SystemBase {
             launch_pack_state(S, T.st, d_state, nullptr);
             CK(cudaMemcpyAsync(h_state, d_state, bytes, cudaMemcpyDeviceToHost, nullptr));
             CK(cudaStreamSynchronize(nullptr));
-            const int err = (int)h_state[6 * (size_t)n + 9];
+            const int err = (int)h_state[6 * (size_t)n + 10];
             if (!err) break;
             if (pass == 1 || !(err & ERRB_OVERFLOW)) {
                 check_flags(nullptr);   // reports the error (clears the bit)

@@ -22,7 +22,7 @@ LFE_ERR_STATE = -6
 LFE_FP32_MIXED = 0
 LFE_FP64 = 1
 NTERMS = 10
-NEXT = 9
+NEXT = 10
 TI_BINS = 100
 TERM_NAMES = ["U", "dUdl", "U_vv", "U_uu", "U_uv", "U_soft", "U_bonded", "n_pairs", "hA", "hB"]
 
@@ -301,7 +301,7 @@ class System:
         ext = np.zeros(NEXT)
         self._check(self._lib.lfe_get_state(self.h, pos.ctypes.data, vel.ctypes.data, ext.ctypes.data))
         keys = ["theta", "p_theta", "lambda", "dUdl", "U", "n_kernels_std", "n_kernels_exp", "step",
-                "n_rebuilds"]
+                "n_rebuilds", "n_tiles"]
         return pos, vel, dict(zip(keys, ext))
 
     def get_state_into(self, pos_ptr, vel_ptr, ext_ptr):

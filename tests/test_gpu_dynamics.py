@@ -161,3 +161,28 @@ def test_ti_accumulators_match_oracle_and_survive_checkpoint(tmp_path):
     assert np.array_equal(count2, count) and dg2 == dg
     _, count3, _ = g2.ti()
     assert count3.sum() == 0
+
+
+@pytest.mark.parametrize("precision", [lfe.LFE_FP64, lfe.LFE_FP32_MIXED])
+def test_eval_after_a_step_rebuilds_the_pending_list(precision):
+    # a step rebuilds the neighbour list at its start when the step before
+    # left an atom more than skin/2 from the build positions, so the last
+    # step of a call can leave a rebuild pending; an evaluation after it
+    # rebuilds first, and its forces are the oracle's at the current positions
+    d = water_system()
+    g = lfe.System(d, precision=precision, seed=SEED)
+    lam = 0.4
+    tol = 1e-9 if precision == lfe.LFE_FP64 else 1e-5
+    seen = 0
+    for _ in range(400):
+        g.step(1)
+        pos, _, e0 = g.get_state()
+        t, F = g.eval(lam)
+        _, _, e1 = g.get_state()
+        if e1["n_rebuilds"] > e0["n_rebuilds"]:
+            seen += 1
+            o = R.evaluate(d, lam, level=2, pos=pos)
+            assert np.linalg.norm(F - o["F"]) / np.linalg.norm(o["F"]) <= tol
+            if seen == 2:
+                break
+    assert seen == 2, "no rebuild was left pending by a step"
