@@ -141,7 +141,9 @@ def nacl(a=0.5, cells=2, split_solute=False):
                 grid=[32, 32, 32], order=4)
 
 
-MADELUNG_NACL = 1.747564594633
+from test_golden import value as golden_value  # noqa: E402
+
+MADELUNG_NACL = golden_value("madelung_nacl.txt", "madelung_nacl")[0]   # Kittel, ch. 3
 
 
 def test_madelung_nacl_level1():
