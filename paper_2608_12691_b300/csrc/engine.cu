@@ -337,7 +337,7 @@ struct System final : SystemBase {
         N.cap = 1024;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
-        N.masks = dalloc<unsigned>((size_t)N.cap * 8);
+        N.masks = dalloc<unsigned char>((size_t)N.cap * 32);
         N.stage_cap = N.cap;
         N.stage_hdr = dalloc<int4>(N.stage_cap);
         N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
@@ -636,7 +636,7 @@ struct System final : SystemBase {
         }
         int nsm = 148;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-        pair_warps = nsm * 32;
+        pair_warps = nsm * 4 * pairs_blocks_per_sm<real>();   // one resident wave of 4-warp blocks
         uv_blocks = nsm * 2;
         N.n_sm = nsm;
         {
@@ -769,7 +769,7 @@ struct System final : SystemBase {
         N.cap = need + 256;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
-        N.masks = dalloc<unsigned>((size_t)N.cap * 8);
+        N.masks = dalloc<unsigned char>((size_t)N.cap * 32);
         N.stage_cap = std::max(N.cap, need_stage + 256);
         N.stage_hdr = dalloc<int4>(N.stage_cap);
         N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
@@ -1166,10 +1166,15 @@ struct System final : SystemBase {
             CK(cudaMallocHost(&h_state, sizeof(double) * (6 * (size_t)n + 16)));
         }
         CK(cudaDeviceSynchronize());
-        const size_t bytes = sizeof(double) * (6 * (size_t)n + 16);
+        // positions and velocities go straight into the caller's arrays, the
+        // scalar state into the pinned buffer
+        const size_t nv = 3 * (size_t)n;
         for (int pass = 0; pass < 2; ++pass) {
             launch_pack_state(S, T.st, d_state, nullptr);
-            CK(cudaMemcpyAsync(h_state, d_state, bytes, cudaMemcpyDeviceToHost, nullptr));
+            CK(cudaMemcpyAsync(h_state + 2 * nv, d_state + 2 * nv, sizeof(double) * 16, cudaMemcpyDeviceToHost,
+                               nullptr));
+            if (pos) CK(cudaMemcpyAsync(pos, d_state, sizeof(double) * nv, cudaMemcpyDeviceToHost, nullptr));
+            if (vel) CK(cudaMemcpyAsync(vel, d_state + nv, sizeof(double) * nv, cudaMemcpyDeviceToHost, nullptr));
             CK(cudaStreamSynchronize(nullptr));
             const int err = (int)h_state[6 * (size_t)n + 10];
             if (!err) break;
@@ -1183,8 +1188,6 @@ struct System final : SystemBase {
         }
         pos_pending = false;
         const double* e = h_state + 6 * (size_t)n;
-        if (pos) std::memcpy(pos, h_state, sizeof(double) * 3 * n);
-        if (vel) std::memcpy(vel, h_state + 3 * (size_t)n, sizeof(double) * 3 * n);
         if (ext)
             for (int k = 0; k < LFE_NEXT; ++k) ext[k] = e[k];
     }

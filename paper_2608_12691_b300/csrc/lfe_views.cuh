@@ -73,7 +73,7 @@ struct NblView {
     int stage_cap;
     int4* tiles;          // [cap]  (I8, shift code, class, -)
     int* jidx;            // [cap * 32] j slots of each tile (-1 = empty)
-    unsigned* masks;      // [cap * 8] one row of 32 j bits per i atom
+    unsigned char* masks; // [cap * 32] one byte per j entry: bit r = pair (i atom r, j entry) computed
     int cap;
     float cut2;           // (r_cut + skin)^2
     float skin_half2;     // (skin / 2)^2
@@ -234,6 +234,7 @@ inline void launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 
 template <typename real> void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st);
 template <typename real> void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st);
+template <typename real> int pairs_blocks_per_sm();
 template <typename real> void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nblocks, cudaStream_t st);
 template <typename real> void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t st);
 template <typename real> void launch_pme(const SysView<real>& s, const PmeView<real>& p,

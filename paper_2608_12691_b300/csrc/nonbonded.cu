@@ -545,10 +545,11 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblV
 }
 
 // Placement and interaction masks.  Every staged tile goes to its place
-// tile_off[I8] + (tiles of I8 under lower shifts) + ordinal.  Mask: one
-// 32-bit row per i atom (8 rows), bit k set = pair (8 I8 + r, jidx[k]) is
-// computed: both slots hold atoms, the pair is not excluded, and for a j atom
-// of I8 itself under no shift, j > i.  A warp takes four staged tiles at a
+// tile_off[I8] + (tiles of I8 under lower shifts) + ordinal.  Mask: one byte
+// per j entry k, bit r set = pair (8 I8 + r, jidx[k]) is computed: both
+// slots hold atoms, the pair is not excluded, and for a j atom of I8 itself
+// under no shift, j > i.  The rows are formed first (one 32-bit row per i
+// atom) and transposed by shuffles.  A warp takes four staged tiles at a
 // time (lane = 8 tile + row), grid-striding over the staging list.
 // Exclusions are searched only for rows whose molecule appears among the j
 // atoms: each excluded partner's slot is looked up in the tile's ascending j
@@ -622,9 +623,9 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
             }
         }
         __syncwarp();
+        unsigned m = 0u;
         if (mydest >= 0) {
             const int* sl = jsl[wl][g];
-            unsigned m = 0u;
             if (a >= 0) m = valid & ~before;
             if (m & same) {
                 // excluded partners' slots, PLACE_EX_BATCH loads in flight
@@ -649,9 +650,18 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
                     }
                 }
             }
-            nb.masks[(size_t)mydest * 8 + r] = m;
+        } else {
+            m = 0u;
         }
         __syncwarp();
+        // stored by j entry: lane k of tile u gathers bit k of the tile's 8 rows
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            unsigned col = 0u;
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) col |= ((__shfl_sync(0xffffffffu, m, 8 * u + rr) >> lane) & 1u) << rr;
+            if (dest[u] >= 0) nb.masks[(size_t)dest[u] * 32 + lane] = (unsigned char)col;
+        }
     }
 }
 
@@ -676,7 +686,7 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
         tl = nb.tiles[t];
         if (tl.z == 2) {
             js = nb.jidx[(size_t)t * 32 + lane];
-            const unsigned mi = nb.masks[(size_t)t * 8 + (lane & 7)];
+            const unsigned mc = nb.masks[(size_t)t * 32 + lane];
             const R4<real> pi = s.xq[tl.x * 8 + (lane & 7)];
             const R4<real> pj = s.xq[js >= 0 ? js : 0];
             int sv[3];
@@ -688,9 +698,8 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
                 const float xi = __shfl_sync(0xffffffffu, (float)pi.x, i);
                 const float yi = __shfl_sync(0xffffffffu, (float)pi.y, i);
                 const float zi = __shfl_sync(0xffffffffu, (float)pi.z, i);
-                const unsigned mrow = __shfl_sync(0xffffffffu, mi, i);
                 const float dx = xj - xi, dy = yj - yi, dz = zj - zi;
-                const bool in = js >= 0 && ((mrow >> lane) & 1u) && dx * dx + dy * dy + dz * dz < nb.cut2;
+                const bool in = js >= 0 && ((mc >> i) & 1u) && dx * dx + dy * dy + dz * dz < nb.cut2;
                 const unsigned bal = __ballot_sync(0xffffffffu, in);
                 if (lane == i) keep = bal;
             }
@@ -850,78 +859,62 @@ __device__ __forceinline__ PairConst<real> pair_const(const SysView<real>& s)
     return c;
 }
 
-// One tile by rotation: lane l = 8 g + r holds i atom 8 I8 + r (xit, yit,
-// zit, qi, si, ei, already shifted for the tile) and starts with j entry l
-// (pj, ljv, shifted); within each group of 8 lanes the j atoms rotate by
-// shuffles together with their force accumulators (Newton's third law), so
-// in 8 steps every (r, j entry of group g) pair is met once.  m8: bits of
-// row r for the 8 j entries of group g.  Adds the lane's share of the
-// i-force to (fix, fiy, fiz), flushes the j-forces, returns the lane's energy.
+// The 24 i-force sums of an 8-atom sub-cluster (x, y, z of each atom), held
+// per lane, are added over the warp by halving exchanges (each lane keeps
+// the half its partner does not: 12, 6, 3 values) and two final butterfly
+// steps; lane 4 k then holds atom k's totals and writes them.
 template <typename real>
-__device__ __forceinline__ real tile_rotate(const SysView<real>& s, const PairConst<real>& c, real xit, real yit,
-                                            real zit, real qi, real si, real ei, R4<real> pj, R2<real> ljv,
-                                            unsigned m8, bool uv, int slot_j, long long& fix, long long& fiy,
-                                            long long& fiz, int& npairs)
+__device__ __forceinline__ void flush_i8(const SysView<real>& s, int I8, real (&fx)[8], real (&fy)[8],
+                                         real (&fz)[8])
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int r = lane & 7;
-    const int src = (lane & ~7) | ((r + 1) & 7);
-    real xj = pj.x, yj = pj.y, zj = pj.z, qj = pj.w, sj = ljv.x, ej = ljv.y;
-    real fjx = 0, fjy = 0, fjz = 0, fx = 0, fy = 0, fz = 0, e0 = 0;
-    // bit 0 of mr is the mask bit of the j entry this lane holds (entry
-    // 8 g + ((r + k) & 7) at step k)
-    unsigned mr = ((m8 >> r) | (m8 << (8 - r))) & 0xffu;
-#pragma unroll 2
+    real v[24];
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const real dx = xj - xit, dy = yj - yit, dz = zj - zit;
-        const real r2 = dx * dx + dy * dy + dz * dz;
-        if ((mr & 1u) && r2 < c.rc2) {
-            real ec, v;
-            const real g = pair_force(r2, qi * qj, si + sj, ei * ej, uv, c, ec, v);
-            fx -= g * dx; fy -= g * dy; fz -= g * dz;
-            fjx += g * dx; fjy += g * dy; fjz += g * dz;
-            e0 += ec + v;
-            ++npairs;
+        v[3 * k] = fx[k];
+        v[3 * k + 1] = fy[k];
+        v[3 * k + 2] = fz[k];
+    }
+#pragma unroll
+    for (int h = 12, o = 16; h >= 3; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int m = 0; m < h; ++m) {
+            const real a = v[m], b = v[m + h];
+            v[m] = (up ? b : a) + __shfl_xor_sync(FULL, up ? a : b, o);
         }
-        mr = ((mr >> 1) | (mr << 7)) & 0xffu;
-        xj = __shfl_sync(FULL, xj, src); yj = __shfl_sync(FULL, yj, src);
-        zj = __shfl_sync(FULL, zj, src); qj = __shfl_sync(FULL, qj, src);
-        sj = __shfl_sync(FULL, sj, src); ej = __shfl_sync(FULL, ej, src);
-        fjx = __shfl_sync(FULL, fjx, src); fjy = __shfl_sync(FULL, fjy, src);
-        fjz = __shfl_sync(FULL, fjz, src);
     }
-    fix += to_fixed(fx, FSCALE);
-    fiy += to_fixed(fy, FSCALE);
-    fiz += to_fixed(fz, FSCALE);
-    if (slot_j >= 0)
-        flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
-    return e0;
-}
-
-// the four lanes of an i atom (one per j group) add their i-force shares and
-// one of them writes the sum
-template <typename real>
-__device__ __forceinline__ void flush_i(const SysView<real>& s, int islot, long long fx, long long fy, long long fz)
-{
-    for (int o = 8; o < 32; o <<= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        v[m] += __shfl_xor_sync(FULL, v[m], 2);
+        v[m] += __shfl_xor_sync(FULL, v[m], 1);
     }
-    if ((threadIdx.x & 31) < 8) flush_force(s, islot, fx, fy, fz);
+    if ((lane & 3) == 0) {
+        const int k = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        flush_force(s, I8 * 8 + k, to_fixed(v[0], FSCALE), to_fixed(v[1], FSCALE), to_fixed(v[2], FSCALE));
+    }
 }
 
 // One warp walks a contiguous chunk of the (I8-sorted) tile list, one 8 x 32
-// tile at a time by rotation; i-forces stay in registers while consecutive
-// tiles share I8.  The tile's class (vv, uu or uv) and shift are uniform, so
-// the branch on them is warp-uniform.  Solute-solvent energies are not
-// accumulated here (k_uv_energy forms them in FP64).
+// tile at a time.  Lane l holds j entry l of the tile (its force in
+// registers); the tile's 8 i atoms are read one at a time from a per-warp
+// shared-memory record (broadcast), so every step pairs one i atom with the
+// 32 j atoms, and a step none of whose pairs lies within the cutoff is
+// skipped by the whole warp (the j atoms of a tile are neighbours in the
+// column sort, so such steps are common).  Each lane keeps its share of the
+// 8 i-forces in registers over consecutive tiles of the same I8 and the warp
+// adds them when I8 changes.  The tile's class (vv, uu or uv) and shift are
+// uniform, so the branches on them are warp-uniform.  Solute-solvent
+// energies are not accumulated here (k_uv_energy forms them in FP64).
+// 4 resident blocks per multiprocessor (110 registers in FP32, no spills;
+// 5 or 6 blocks measured slower), 3 in FP64.
 template <typename real>
-__global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real> nb)
+__global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs(SysView<real> s, NblView<real> nb)
 {
-    const int lane = threadIdx.x & 31;
-    const int r = lane & 7, grp = lane >> 3;
+    __shared__ R4<real> sxq[4][8];   // [warp][i atom] x, y, z (shifted for the tile), sqrt(k_e) q
+    __shared__ R2<real> slj[4][8];   // [warp][i atom] sigma/2, 2 sqrt(eps)
+    const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     int ntiles = s.flags[FL_NTILES];
@@ -931,53 +924,74 @@ __global__ void __launch_bounds__(128, 8) k_pairs(SysView<real> s, NblView<real>
     if (t0 >= t1) return;
     const PairConst<real> c = pair_const(s);
     int curI = -1;
-    real xi = 0, yi = 0, zi = 0, qi = 0, si = 0, ei = 0;
-    long long fix = 0, fiy = 0, fiz = 0;
+    R4<real> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
+    real fx[8], fy[8], fz[8];
     real evv = 0, euu = 0;
     int npairs = 0;
     // the next tile's records are loaded while the current one is computed
     int4 tl_n = nb.tiles[t0];
-    unsigned mk_n = nb.masks[(size_t)t0 * 8 + r];
+    unsigned mk_n = nb.masks[(size_t)t0 * 32 + lane];
     int sj_n = nb.jidx[(size_t)t0 * 32 + lane];
     R4<real> pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
     R2<real> lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
     for (int t = t0; t < t1; ++t) {
         const int4 tl = tl_n;
-        const unsigned m8 = (mk_n >> (8 * grp)) & 0xffu;
+        const unsigned mc = mk_n;
         const int slot_j = sj_n;
         R4<real> pj = pj_n;
         const R2<real> ljv = lj_n;
         if (t + 1 < t1) {
             tl_n = nb.tiles[t + 1];
-            mk_n = nb.masks[(size_t)(t + 1) * 8 + r];
+            mk_n = nb.masks[(size_t)(t + 1) * 32 + lane];
             sj_n = nb.jidx[(size_t)(t + 1) * 32 + lane];
             pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
             lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
         }
         if (tl.x != curI) {
-            if (curI >= 0) flush_i(s, curI * 8 + r, fix, fiy, fiz);
+            if (curI >= 0) flush_i8(s, curI, fx, fy, fz);
             curI = tl.x;
-            const R4<real> p = s.xq[curI * 8 + r];
-            const R2<real> l = s.lj[curI * 8 + r];
-            xi = p.x; yi = p.y; zi = p.z; qi = p.w; si = l.x; ei = l.y;
-            fix = fiy = fiz = 0;
+            if (lane < 8) {
+                pown = s.xq[curI * 8 + lane];
+                slj[wl][lane] = s.lj[curI * 8 + lane];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) fx[k] = fy[k] = fz[k] = 0;
         }
         const int sh = tl.y;
         const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
         // shift the far-side atom down by L so that the subtraction below is
         // the only rounding in the pair vector
-        const real xit = sx == 1 ? xi - s.L[0] : xi;
-        const real yit = sy == 1 ? yi - s.L[1] : yi;
-        const real zit = sz == 1 ? zi - s.L[2] : zi;
+        if (lane < 8)
+            sxq[wl][lane] = R4<real>{sx == 1 ? pown.x - s.L[0] : pown.x, sy == 1 ? pown.y - s.L[1] : pown.y,
+                                     sz == 1 ? pown.z - s.L[2] : pown.z, pown.w};
         if (sx == -1) pj.x -= s.L[0];
         if (sy == -1) pj.y -= s.L[1];
         if (sz == -1) pj.z -= s.L[2];
-        const real e0 = tile_rotate(s, c, xit, yit, zit, qi, si, ei, pj, ljv, m8, tl.z == 2, slot_j, fix, fiy, fiz,
-                                    npairs);
+        __syncwarp();
+        const bool uv = tl.z == 2;
+        real fjx = 0, fjy = 0, fjz = 0, e0 = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const R4<real> pi = sxq[wl][k];
+            const real dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            if (((mc >> k) & 1u) && r2 < c.rc2) {
+                const R2<real> li = slj[wl][k];
+                real ec, v;
+                const real g = pair_force(r2, pi.w * pj.w, li.x + ljv.x, li.y * ljv.y, uv, c, ec, v);
+                fx[k] -= g * dx; fy[k] -= g * dy; fz[k] -= g * dz;
+                fjx += g * dx; fjy += g * dy; fjz += g * dz;
+                e0 += ec + v;
+                ++npairs;
+            }
+        }
+        __syncwarp();
+        if (slot_j >= 0)
+            flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
         if (tl.z == 0) evv += e0;
         else if (tl.z == 1) euu += e0;
     }
-    flush_i(s, curI * 8 + r, fix, fiy, fiz);
+    flush_i8(s, curI, fx, fy, fz);
     const long long a0 = __double2ll_rn(warp_sum_d((double)evv) * ESCALE);
     const long long a1 = __double2ll_rn(warp_sum_d((double)euu) * ESCALE);
     const long long a4 = warp_sum_ll((long long)npairs);
@@ -1048,6 +1062,15 @@ void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nbloc
 {
     if (s.n_ucl == 0) return;
     k_uv_energy<real><<<nblocks, 256, 0, st>>>(s, nb);
+}
+
+// blocks of k_pairs resident on one multiprocessor (its grid is one wave)
+template <typename real>
+int pairs_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs<real>, 128, 0) != cudaSuccess || nb < 1) nb = 1;
+    return nb;
 }
 
 template <typename real>
@@ -1178,6 +1201,7 @@ void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t 
 #define LFE_INST(real)                                                                             \
     template void launch_build_nbl<real>(const SysView<real>&, const NblView<real>&, cudaStream_t); \
     template void launch_pairs<real>(const SysView<real>&, const NblView<real>&, int, cudaStream_t); \
+    template int pairs_blocks_per_sm<real>();                                                          \
     template void launch_uv_energy<real>(const SysView<real>&, const NblView<real>&, int, cudaStream_t); \
     template void launch_excl<real>(const SysView<real>&, const ExclView<real>&, cudaStream_t);
 LFE_INST(float)
