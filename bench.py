@@ -33,8 +33,8 @@ METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) o
 FLOPS_PER_PAIR = 67
 # DRAM bytes (read + write) of one k_pairs<float> launch on the octanol workload, from an ncu
 # capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum); None until
-# the current version has been captured
-PAIR_DRAM_BYTES_OCTANOL = None
+# the current version has been captured (lane-per-j-entry kernel: 7.153 MB read, 0 written)
+PAIR_DRAM_BYTES_OCTANOL = 7.15264e6 + 0.0
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 
@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-dafed", action="store_true", help="skip the flexible-solute d-AFED leg")
-    p.add_argument("--e2e-steps", type=int, default=30)
+    p.add_argument("--e2e-steps", type=int, default=200)
     p.add_argument("--batch-replicas", type=int, default=32,
                    help="replicas in the batched leg (half water, half octanol; 0 skips it)")
     p.add_argument("--batch-steps", type=int, default=40)
