@@ -1,0 +1,97 @@
+// df64.cuh -- unevaluated sum of two floats (hi + lo, |lo| <= ulp(hi)/2),
+// about 48 significant bits carried on the FP32 pipes.
+//
+// Error-free transformations: the sum of two floats as a float plus its
+// rounding error (Knuth's TwoSum; Dekker's FastTwoSum when the first operand
+// is the larger), and the product as a float plus its error from one fused
+// multiply-add.  Addition follows the accurate double-word sum (two TwoSums,
+// two renormalisations: relative error about 2^-46 even when the operands
+// cancel), multiplication the double-word product with the cross terms added
+// by FMAs (Dekker 1971; Hida, Li and Bailey 2001).  Division: one float
+// quotient corrected by the df64 remainder.
+//
+// B300 runs FP64 at a small fraction of its FP32 rate; transforms whose
+// results must hold about 1e-12 relative error run faster in df64.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace lfe {
+
+struct df64 {
+    float hi, lo;
+    df64() = default;
+    __host__ __device__ explicit df64(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    __host__ __device__ explicit df64(int i) : df64((double)i) {}
+    __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
+    __host__ __device__ static df64 of(float f)
+    {
+        df64 r;
+        r.hi = f;
+        r.lo = 0.0f;
+        return r;
+    }
+};
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b)
+{
+    float s1, s2, t1, t2;
+    df_two_sum(a.hi, b.hi, s1, s2);
+    df_two_sum(a.lo, b.lo, t1, t2);
+    s2 = __fadd_rn(s2, t1);
+    df_fast_two_sum(s1, s2, s1, s2);
+    s2 = __fadd_rn(s2, t2);
+    df64 r;
+    df_fast_two_sum(s1, s2, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df64 operator-(df64 a)
+{
+    df64 r;
+    r.hi = -a.hi;
+    r.lo = -a.lo;
+    return r;
+}
+
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__device__ __forceinline__ df64 operator*(df64 a, df64 b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    df64 r;
+    df_fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ df64 operator/(df64 a, df64 b)
+{
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const df64 r = a - b * df64::of(q1);
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    df64 o;
+    df_fast_two_sum(q1, q2, o.hi, o.lo);
+    return o;
+}
+
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
+
+}  // namespace lfe

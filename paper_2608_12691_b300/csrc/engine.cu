@@ -113,7 +113,8 @@ struct System final : SystemBase {
     NblView<real> N{};
     ExclView<real> X{};
     PmeView<real> M{};
-    PmeView<double> M64{};      // FP64 energy branch (FP32 systems only)
+    PmeView<double> M64{};      // FP32 systems: FP64 copy of the packed charge grid (and the adjoint's FP64 pass)
+    PmeView<df64> M2{};         // FP32 systems: the energy branch in df64
     bool dual = false;
     BondView<real> B{};
     DafedView D{};
@@ -463,6 +464,21 @@ struct System final : SystemBase {
                     M64.gfac[d] = upload(gf);
                     M64.msq[d] = upload(ms);
                     M64.tw[d] = upload(tw);
+                    std::vector<df64> gf2(K), ms2(K);
+                    std::vector<R2<df64>> tw2(K);
+                    for (int m = 0; m < K; ++m) {
+                        gf2[m] = df64(gf[m]);
+                        ms2[m] = df64(ms[m]);
+                        tw2[m] = R2<df64>{df64(tw[m].x), df64(tw[m].y)};
+                    }
+                    M2.K[d] = K;
+                    M2.kscale[d] = df64(K / p.box[d]);
+                    M2.kscale64[d] = K / p.box[d];
+                    M2.nrad[d] = M.nrad[d];
+                    for (int r = 0; r < 8; ++r) M2.rad[d][r] = M.rad[d][r];
+                    M2.gfac[d] = upload(gf2);
+                    M2.msq[d] = upload(ms2);
+                    M2.tw[d] = upload(tw2);
                 }
             }
             M.conv_pre = (real)(KE / (PI * V));
@@ -480,6 +496,14 @@ struct System final : SystemBase {
                 M64.phi_u = nullptr;
                 M64.Zraw64 = nullptr;
                 M.Zraw64 = M64.Z;
+                M2.KK = M.KK;
+                M2.conv_pre = df64(KE / (PI * V));
+                M2.qu_scale = df64(qu_scale);
+                M2.Qfix = nullptr;
+                M2.Z = dalloc<R2<df64>>(M.KK);
+                M2.phi_u = nullptr;
+                M2.Zraw64 = nullptr;
+                M2.Zin64 = M64.Z;
             }
             const int Kmax = std::max(M.K[0], std::max(M.K[1], M.K[2]));
             if (fft_smem<real>(Kmax) > 48 * 1024 || (dual && fft_smem<double>(Kmax) > 48 * 1024))
@@ -705,10 +729,12 @@ struct System final : SystemBase {
         };
         build(M, sizeof(real) == 8 ? 4 : 8);
         if (dual) build(M64, 4);
-        if (dual && !M64.planes) M.planes = 0;   // both branches use one transform layout
+        if (dual) build(M2, 4);
+        if (dual && !(M64.planes && M2.planes)) M.planes = M64.planes = M2.planes = 0;   // one transform layout
         if (M.planes) {
             planes_setup(M);
             if (dual) planes_setup(M64);
+            if (dual) energy_columns_setup(M2);
             CK(cudaGetLastError());
         }
     }
@@ -901,7 +927,7 @@ struct System final : SystemBase {
     {
         launch_pairs(S, N, pair_warps, st);
         launch_uv_energy(S, N, uv_blocks, st);
-        launch_pme(S, M, dual ? &M64 : nullptr, st);
+        launch_pme(S, M, dual ? &M2 : nullptr, st);
         launch_excl(S, X, st);
         launch_bonded(S, B, st);
         launch_dafed_force(S, D, st);
@@ -999,17 +1025,17 @@ struct System final : SystemBase {
         launch_gather(S, M, br[1]);
         if (dual) {
             CK(cudaStreamWaitEvent(br[2], ev_z, 0));
-            if (M64.planes) {
-                // FP64 is scarce on this part: the per-axis passes spread the
-                // axes 2 and 1 over more blocks than one block per plane
-                launch_fft(M64, 2, +1, 0, br[2]);
-                launch_fft(M64, 1, +1, 0, br[2]);
-                launch_columns(M64, S.E, S.lam, CONV_ENERGY, br[2]);
+            if (M2.planes) {
+                // per-axis passes of 4-line blocks for the axes 2 and 1 (many
+                // small blocks beside the other branches), then the column pass
+                launch_fft(M2, 2, +1, 0, br[2]);
+                launch_fft(M2, 1, +1, 0, br[2]);
+                launch_columns(M2, S.E, S.lam, CONV_ENERGY, br[2]);
             } else {
-                launch_fft(M64, 2, +1, 0, br[2]);
-                launch_fft(M64, 1, +1, 0, br[2]);
-                launch_fft(M64, 0, +1, 0, br[2]);
-                launch_conv(M64, S.E, S.lam, CONV_ENERGY, br[2]);
+                launch_fft(M2, 2, +1, 0, br[2]);
+                launch_fft(M2, 1, +1, 0, br[2]);
+                launch_fft(M2, 0, +1, 0, br[2]);
+                launch_conv(M2, S.E, S.lam, CONV_ENERGY, br[2]);
             }
         }
         launch_excl(S, X, br[3]);
@@ -1479,9 +1505,9 @@ struct System final : SystemBase {
                 // pass with its axis-0 transforms; inv: planes
                 launch_planes(M, PLANE_FWD_FIX, st);
                 if (dual) {
-                    launch_fft(M64, 2, +1, 0, st);
-                    launch_fft(M64, 1, +1, 0, st);
-                    launch_columns(M64, S.E, S.lam, CONV_ENERGY, st);
+                    launch_fft(M2, 2, +1, 0, st);
+                    launch_fft(M2, 1, +1, 0, st);
+                    launch_columns(M2, S.E, S.lam, CONV_ENERGY, st);
                 }
                 CK(cudaEventRecord(ev[4], st));
                 launch_columns(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, st);
@@ -1490,10 +1516,10 @@ struct System final : SystemBase {
             } else {
                 launch_fft(M, 2, +1, 1, st);
                 if (dual) {
-                    launch_fft(M64, 2, +1, 0, st);
-                    launch_fft(M64, 1, +1, 0, st);
-                    launch_fft(M64, 0, +1, 0, st);
-                    launch_conv(M64, S.E, S.lam, CONV_ENERGY, st);
+                    launch_fft(M2, 2, +1, 0, st);
+                    launch_fft(M2, 1, +1, 0, st);
+                    launch_fft(M2, 0, +1, 0, st);
+                    launch_conv(M2, S.E, S.lam, CONV_ENERGY, st);
                 }
                 launch_fft(M, 1, +1, 0, st);
                 launch_fft(M, 0, +1, 0, st);

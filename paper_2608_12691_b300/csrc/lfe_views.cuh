@@ -5,6 +5,7 @@
 
 #include "lfe.h"
 #include "lfe_dev.cuh"
+#include "df64.cuh"
 
 namespace lfe {
 
@@ -121,6 +122,7 @@ struct PmeView {
     int rad[3][8];
     real* phi_u;              // [n_u] reciprocal potential of the other class at solute atoms
     R2<double>* Zraw64;       // optional: FP64 copy of the packed charge grid written by the first pass
+    const R2<double>* Zin64;  // optional: FP64 input grid of an axis-2 pass (read instead of Z, converted to real)
     // plane / column transform (used when a K1 x K2 plane fits in shared memory)
     int planes;               // 1: plane kernels in use, 0: one kernel per axis
     int ngroups, cg_max;      // column groups of the axis-0 pass and the largest group
@@ -238,7 +240,7 @@ template <typename real> int pairs_blocks_per_sm();
 template <typename real> void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nblocks, cudaStream_t st);
 template <typename real> void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t st);
 template <typename real> void launch_pme(const SysView<real>& s, const PmeView<real>& p,
-                                         const PmeView<double>* energy64, cudaStream_t st);
+                                         const PmeView<df64>* energy64, cudaStream_t st);
 template <typename real> void launch_spread(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st);
 template <typename real> void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st);
 // shared memory of one per-axis pass of length K (at most 48 KB without opt-in)
@@ -261,6 +263,7 @@ template <typename real> void launch_columns(const PmeView<real>& p, long long* 
 template <typename real> size_t planes_smem(const PmeView<real>& p);
 template <typename real> size_t columns_smem(const PmeView<real>& p);
 template <typename real> void planes_setup(const PmeView<real>& p);
+template <typename real> void energy_columns_setup(const PmeView<real>& p);
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
 template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);

@@ -96,6 +96,16 @@ __device__ __forceinline__ R2<real> cmuli(R2<real> a, int sign)
     return r;
 }
 
+// df64: the sign flip without a df64 product
+template <>
+__device__ __forceinline__ R2<df64> cmuli<df64>(R2<df64> a, int sign)
+{
+    R2<df64> r;
+    r.x = sign > 0 ? -a.y : a.y;
+    r.y = sign > 0 ? a.x : -a.x;
+    return r;
+}
+
 // in-register R-point DFT y_k = sum_n a_n exp(sign 2 pi i n k / R)
 template <typename real>
 __device__ __forceinline__ void dft_small(R2<real>* v, int R, int sign)
@@ -252,6 +262,10 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
                     w.y = qu;
                     p.Zraw64[g] = w;
                 }
+            } else if (p.Zin64) {
+                const R2<double> w = p.Zin64[g];
+                v.x = (real)w.x;
+                v.y = (real)w.y;
             } else {
                 v = p.Z[g];
             }
@@ -466,9 +480,9 @@ __global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long l
         const bool self = (c == pc && k0 == n0);
         if (MODE != CONV_POTENTIAL) {
             const double mult = self ? 1.0 : 2.0;
-            evv += mult * 0.5 * (double)G * ((double)qv.x * qv.x + (double)qv.y * qv.y);
-            euu += mult * 0.5 * (double)G * ((double)qu.x * qu.x + (double)qu.y * qu.y);
-            euv += mult * (double)G * ((double)qu.x * qv.x + (double)qu.y * qv.y);
+            evv += mult * 0.5 * (double)G * ((double)qv.x * (double)qv.x + (double)qv.y * (double)qv.y);
+            euu += mult * 0.5 * (double)G * ((double)qu.x * (double)qu.x + (double)qu.y * (double)qu.y);
+            euv += mult * (double)G * ((double)qu.x * (double)qv.x + (double)qu.y * (double)qv.y);
         }
         if (MODE != CONV_ENERGY) {
             // W = G [(Q_v + h_A Q_u) + i (Q_u + h_A Q_v)]; at -m the class
@@ -542,6 +556,17 @@ void planes_setup(const PmeView<real>& p)
     allow_max_smem(k_columns<real, CONV_BOTH>, optin);
 }
 
+// the column pass of an energy-only branch (no plane kernels)
+template <typename real>
+void energy_columns_setup(const PmeView<real>& p)
+{
+    (void)p;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    allow_max_smem(k_columns<real, CONV_ENERGY>, optin);
+}
+
 template <typename real>
 void launch_planes(const PmeView<real>& p, int mode, cudaStream_t st)
 {
@@ -595,9 +620,9 @@ __global__ void k_conv(PmeView<real> p, long long* E, const LamState* lam)
             const real G = p.conv_pre * p.gfac[0][k0] * p.gfac[1][k1] * p.gfac[2][k2] / msq;
             if (MODE != CONV_POTENTIAL) {
                 const double mult = (idx == nidx) ? 1.0 : 2.0;
-                evv = mult * 0.5 * (double)G * ((double)qv.x * qv.x + (double)qv.y * qv.y);
-                euu = mult * 0.5 * (double)G * ((double)qu.x * qu.x + (double)qu.y * qu.y);
-                euv = mult * (double)G * ((double)qu.x * qv.x + (double)qu.y * qv.y);
+                evv = mult * 0.5 * (double)G * ((double)qv.x * (double)qv.x + (double)qv.y * (double)qv.y);
+                euu = mult * 0.5 * (double)G * ((double)qu.x * (double)qu.x + (double)qu.y * (double)qu.y);
+                euv = mult * (double)G * ((double)qu.x * (double)qv.x + (double)qu.y * (double)qv.y);
             }
             if (MODE != CONV_ENERGY) {
                 // W = G [(Q_v + h_A Q_u) + i (Q_u + h_A Q_v)]; at -m the class
@@ -688,12 +713,13 @@ void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t 
     k_gather<real><<<(s.n + 127) / 128, 128, 0, st>>>(s, p);
 }
 
-// energy64 (FP32 systems): the FP64 energy branch.  The first FP32 pass
-// leaves an FP64 copy of the packed charge grid in energy64->Z; the branch
-// transforms it in FP64 and forms the three class energies, while the FP32
-// branch only forms the force potentials.
+// energy64 (FP32 systems): the energy branch in df64 (about 48 bits).  The
+// first FP32 pass leaves an FP64 copy of the packed charge grid, which
+// energy64's first pass reads (Zin64); the branch transforms it and forms the
+// three class energies, while the FP32 branch only forms the force
+// potentials.
 template <typename real>
-void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<double>* energy64, cudaStream_t st)
+void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<df64>* energy64, cudaStream_t st)
 {
     if (p.planes) {
         launch_spread(s, p, st);
@@ -726,7 +752,7 @@ void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<do
 }
 
 #define LFE_INST_PME(real)                                                                        \
-    template void launch_pme<real>(const SysView<real>&, const PmeView<real>&, const PmeView<double>*, cudaStream_t); \
+    template void launch_pme<real>(const SysView<real>&, const PmeView<real>&, const PmeView<df64>*, cudaStream_t); \
     template void launch_spread<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
     template void launch_conv<real>(const PmeView<real>&, long long*, const LamState*, int, cudaStream_t); \
     template void launch_gather<real>(const SysView<real>&, const PmeView<real>&, cudaStream_t);   \
@@ -739,5 +765,12 @@ void launch_pme(const SysView<real>& s, const PmeView<real>& p, const PmeView<do
     template void planes_setup<real>(const PmeView<real>&);
 LFE_INST_PME(float)
 LFE_INST_PME(double)
+// the df64 energy branch: transforms, column / convolution energy passes
+template void launch_fft<df64>(const PmeView<df64>&, int, int, int, cudaStream_t);
+template size_t fft_smem<df64>(int);
+template void launch_columns<df64>(const PmeView<df64>&, long long*, const LamState*, int, cudaStream_t);
+template size_t columns_smem<df64>(const PmeView<df64>&);
+template void launch_conv<df64>(const PmeView<df64>&, long long*, const LamState*, int, cudaStream_t);
+template void energy_columns_setup<df64>(const PmeView<df64>&);
 
 }  // namespace lfe
