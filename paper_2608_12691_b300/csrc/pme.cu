@@ -770,6 +770,7 @@ template void launch_fft<df64>(const PmeView<df64>&, int, int, int, cudaStream_t
 template size_t fft_smem<df64>(int);
 template void launch_columns<df64>(const PmeView<df64>&, long long*, const LamState*, int, cudaStream_t);
 template size_t columns_smem<df64>(const PmeView<df64>&);
+template size_t planes_smem<df64>(const PmeView<df64>&);
 template void launch_conv<df64>(const PmeView<df64>&, long long*, const LamState*, int, cudaStream_t);
 template void energy_columns_setup<df64>(const PmeView<df64>&);
 
