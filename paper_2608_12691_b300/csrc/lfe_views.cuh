@@ -122,7 +122,7 @@ struct PmeView {
     int rad[3][8];
     real* phi_u;              // [n_u] reciprocal potential of the other class at solute atoms
     R2<double>* Zraw64;       // optional: FP64 copy of the packed charge grid written by the first pass
-    const R2<double>* Zin64;  // optional: FP64 input grid of an axis-2 pass (read instead of Z, converted to real)
+    const R2<double>* Zin64;  // optional: FP64 input grid of the axis-2 (first) per-axis pass, read instead of Z
     // plane / column transform (used when a K1 x K2 plane fits in shared memory)
     int planes;               // 1: plane kernels in use, 0: one kernel per axis
     int ngroups, cg_max;      // column groups of the axis-0 pass and the largest group

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
                     w.y = qu;
                     p.Zraw64[g] = w;
                 }
-            } else if (p.Zin64) {
+            } else if (AXIS == 2 && p.Zin64) {
                 const R2<double> w = p.Zin64[g];
                 v.x = (real)w.x;
                 v.y = (real)w.y;
