@@ -12,6 +12,7 @@
 // into one complex grid for the single inverse transform.
 #include "lfe_views.cuh"
 #include "pme_dev.cuh"
+#include <type_traits>
 
 namespace lfe {
 
@@ -282,20 +283,36 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
     }
 }
 
-template <typename real>
-size_t fft_smem(int K)
+// Lines per block of a per-axis pass: 16 in FP32; 4 in FP64, whose scarce
+// units want more blocks in flight; 16 in df64 (FP32 pipes; measured: step
+// 0.149 ms against 0.152 with 8 and 0.155 with 4 lines on the octanol box)
+// when the block fits in 48 KB of shared memory, else 4.
+template <typename real, int NL>
+size_t fft_smem_nl(int K)
 {
-    constexpr int NL = sizeof(real) == 8 ? 4 : 16;
     return sizeof(R2<real>) * (size_t)(K + 2 * NL * (K + 1));
 }
 
 template <typename real>
-void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
+int fft_lines(int K)
 {
-    constexpr int NL = sizeof(real) == 8 ? 4 : 16;
+    if (sizeof(real) == 4) return 16;
+    if (std::is_same<real, df64>::value && fft_smem_nl<real, 16>(K) <= 48 * 1024) return 16;
+    return 4;
+}
+
+template <typename real>
+size_t fft_smem(int K)
+{
+    return fft_lines<real>(K) == 16 ? fft_smem_nl<real, 16>(K) : fft_smem_nl<real, 4>(K);
+}
+
+template <typename real, int NL>
+void launch_fft_nl(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
+{
     const int threads = 16 * NL;
     const int K = p.K[axis];
-    const size_t smem = fft_smem<real>(K);
+    const size_t smem = fft_smem_nl<real, NL>(K);
     int blocks;
     if (axis == 2) blocks = (p.K[0] * p.K[1] + NL - 1) / NL;
     else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + NL - 1) / NL);
@@ -306,6 +323,19 @@ void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cuda
         k_fft<real, 1, false, NL><<<blocks, threads, smem, st>>>(p, sign);
     } else {
         k_fft<real, 0, false, NL><<<blocks, threads, smem, st>>>(p, sign);
+    }
+}
+
+template <typename real>
+void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cudaStream_t st)
+{
+    if constexpr (sizeof(real) == 4) {
+        launch_fft_nl<real, 16>(p, axis, sign, from_fixed, st);
+    } else if constexpr (std::is_same<real, df64>::value) {
+        if (fft_lines<real>(p.K[axis]) == 16) launch_fft_nl<real, 16>(p, axis, sign, from_fixed, st);
+        else launch_fft_nl<real, 4>(p, axis, sign, from_fixed, st);
+    } else {
+        launch_fft_nl<real, 4>(p, axis, sign, from_fixed, st);
     }
 }
 
