@@ -193,6 +193,7 @@ def dafed_leg(args, stream, flush):
              opes_dE_std=30.0 * 4.184, opes_dE_exp=5.0 * 4.184, opes_sigma=0.10)
     g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242)
     g.set_dafed(S.DIPEPTIDE_CVS, 1000.0, 50.0, temperature=1000.0, friction=25.0)
+    g.autotune(reps=20)
     equilibrate(g, d, stream)
     g.step(20, stream)
     torch.cuda.synchronize()
@@ -224,6 +225,9 @@ def batched_leg(args, stream, flush):
         dicts.append(d)
     t_gen = time.perf_counter() - t0
     reps = [lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=7000 + r, theta0=d["lam"]) for r, d in enumerate(dicts)]
+    # systems of one kind share a tuning entry: the first of each kind is timed
+    cache = os.path.join(tempfile.mkdtemp(), "lfe_tune.json")
+    tuned = [g.autotune(reps=10, cache_path=cache)[1] for g in reps]
     b = lfe.Batch(reps)
     for frac, fric in ((0.05, 100.0), (0.25, 50.0), (0.5, 20.0), (1.0, None)):
         for d, g in zip(dicts, reps):
@@ -257,6 +261,7 @@ def batched_leg(args, stream, flush):
     for g in reps:
         g.close()
     return {"replicas": R, "atoms": int(sum(len(d["charge"]) for d in dicts)),
+            "autotuned_from_cache": int(sum(t["from_cache"] for t in tuned)),
             "mixed_batched": {"ms_per_step": ms_step, "ns_per_day_x_replica": ns_day,
                               "pair_interactions_per_s": pairs / (ms_step * 1e-3), "steps": K},
             "fp64_per_replica": {"ms_per_step_all_replicas": t64, "ns_per_day_x_replica": ns_day64,
@@ -298,6 +303,7 @@ def run_ours(args):
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     dt_ps = float(d["dt"])
     g = lfe.System(d, precision=prec, seed=2608 + rank)
+    tune_ms, tune = g.autotune(reps=20)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
     stream = torch.cuda.current_stream()
@@ -391,6 +397,7 @@ def run_ours(args):
                           if prec == lfe.LFE_FP32_MIXED else "FP64", "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single replica",
                           "pairs_per_step": n_pairs, "tiles": n_tiles,
+                          "autotuned": dict(tune, eval_ms=tune_ms),
                           "tile_efficiency": n_pairs / (256.0 * n_tiles) if n_tiles else None},
                "pair_interactions_per_s": n_pairs / (ms_step * 1e-3) * world,
                "wall_ms_per_step": wall / args.steps * 1e3,

@@ -265,6 +265,26 @@ int lfe_restore(lfe_system* sys, const char* path);
 int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
                     const char** names, double* ms, int max_n);
 
+/* Autotuner: choose the evaluation's launch shapes for this system by
+ * timing its captured evaluation graph (the four concurrent branches of the
+ * step) on the device: blocks of the pair kernel per multiprocessor (1 up to
+ * the resident maximum), blocks of the FP64 solute-solvent energy kernel
+ * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
+ * passes (4 or 16), one knob at a time, each candidate replayed `reps`
+ * (1..10000) times, the median deciding.  The replays leave the state
+ * (positions, velocities, theta, counters, accumulators) as it was; the next
+ * lfe_step recaptures its graph with the chosen shapes.  Launch shapes change
+ * only how work is split over blocks and warps, so results stay within the
+ * precision mode's tolerance (summation order).  cache_path (or NULL): a JSON
+ * file of tuned entries keyed on the device, atom counts, density, cutoff,
+ * grid and precision; a matching entry is applied without timing, a new one
+ * is added.  Outputs (each may be NULL): best_ms = median evaluation time of
+ * the choice; params[4] = (pair blocks per SM, uv energy blocks, df64 lines,
+ * 1 if taken from the cache else 0).  Errors: LFE_ERR_ARG (reps out of range,
+ * cache not writable), LFE_ERR_CUDA.  Not part of the paper's method: it
+ * serves the batched-replica workload's "sizes chosen by an autotuner". */
+int lfe_autotune(lfe_system* sys, int reps, const char* cache_path, double* best_ms, int* params);
+
 /* Batched replicas (lambda windows, solvents, solutes; sizes may differ):
  * lfe_batch_create groups existing systems (not copied; they must outlive
  * the batch and must not be destroyed while it exists).  lfe_batch_step

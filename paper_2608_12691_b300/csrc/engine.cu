@@ -11,6 +11,8 @@
 #include <vector>
 #include <algorithm>
 #include <functional>
+#include <fstream>
+#include <sstream>
 #include <type_traits>
 
 #include "lfe.h"
@@ -96,6 +98,7 @@ struct SystemBase {
     virtual bool overflow_pending(cudaStream_t st) = 0;
     virtual void recover(cudaStream_t st) = 0;
     virtual cudaStream_t side_stream() = 0;
+    virtual void autotune(int reps, const char* cache_path, double* best_ms, int* params) = 0;
     unsigned generation = 0;   // bumped whenever device buffers are reallocated
 };
 
@@ -122,6 +125,7 @@ struct System final : SystemBase {
     ThetaView<real> T{};
     int pair_warps = 0;
     int uv_blocks = 0;
+    int nsm = 148;              // multiprocessors of the device
     double const_vv = 0, const_uu = 0, const_uv = 0;
     cudaStream_t cs = nullptr, cs2 = nullptr;
     cudaStream_t br[4] = {nullptr, nullptr, nullptr, nullptr};   // capture branches
@@ -658,7 +662,6 @@ struct System final : SystemBase {
             lam_save = dalloc<LamState>(1);
             lam0 = dalloc<LamState>(1);
         }
-        int nsm = 148;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
         pair_warps = nsm * 4 * pairs_blocks_per_sm<real>();   // one resident wave of 4-warp blocks
         uv_blocks = nsm * 2;
@@ -1047,6 +1050,171 @@ struct System final : SystemBase {
             CK(cudaEventRecord(ev_join[k], br[k]));
             CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
         }
+    }
+
+    // ------------------------------------------------------- autotuner
+    // Launch shapes of the evaluation, chosen by timing the captured
+    // evaluation graph (its four concurrent branches, as in the step) for
+    // each candidate: blocks of the pair kernel per multiprocessor, blocks
+    // of the FP64 solute-solvent energy kernel, lines per block of the df64
+    // transform passes.  One knob at a time (coordinate descent), each
+    // candidate replayed `reps` times after three untimed replays; the
+    // median decides.  The replays only add into the force and energy
+    // accumulators, which are cleared afterwards: positions, velocities,
+    // theta and every counter are untouched.  A JSON cache (one entry per
+    // line) keyed on the device, atom counts, density, cutoff, grid and
+    // precision skips the timing when the same kind of system is tuned again.
+    std::string tune_key()
+    {
+        cudaDeviceProp prop{};
+        CK(cudaGetDeviceProperties(&prop, device));
+        const double rho = n / (P.box[0] * P.box[1] * P.box[2]);
+        char buf[512];
+        std::snprintf(buf, sizeof(buf), "%s|sm%d|n%d|nu%d|rho%.1f|rc%.3f|K%dx%dx%d|p%d", prop.name, nsm, n, n_u, rho,
+                      P.r_cut, M.K[0], M.K[1], M.K[2], P.precision);
+        return std::string(buf);
+    }
+
+    static bool cache_find(const std::string& path, const std::string& key, int* v, double* ms)
+    {
+        std::ifstream f(path);
+        if (!f) return false;
+        std::string line;
+        const std::string kq = "\"key\": \"" + key + "\"";
+        while (std::getline(f, line)) {
+            if (line.find(kq) == std::string::npos) continue;
+            auto num = [&](const char* name, double& out) {
+                const std::string t = std::string("\"") + name + "\": ";
+                const size_t at = line.find(t);
+                if (at == std::string::npos) return false;
+                out = std::strtod(line.c_str() + at + t.size(), nullptr);
+                return true;
+            };
+            double a, b, c, d;
+            if (num("pair_blocks_per_sm", a) && num("uv_blocks", b) && num("df64_lines", c) && num("eval_ms", d)) {
+                v[0] = (int)a; v[1] = (int)b; v[2] = (int)c; *ms = d;
+                return true;
+            }
+        }
+        return false;
+    }
+
+    static void cache_store(const std::string& path, const std::string& key, const int* v, double ms)
+    {
+        std::vector<std::string> keep;
+        {
+            std::ifstream f(path);
+            std::string line;
+            const std::string kq = "\"key\": \"" + key + "\"";
+            while (f && std::getline(f, line))
+                if (line.rfind("{\"key\": ", 0) == 0 && line.find(kq) == std::string::npos) {
+                    if (!line.empty() && line.back() == ',') line.pop_back();
+                    keep.push_back(line);
+                }
+        }
+        char buf[768];
+        std::snprintf(buf, sizeof(buf),
+                      "{\"key\": \"%s\", \"pair_blocks_per_sm\": %d, \"uv_blocks\": %d, \"df64_lines\": %d, "
+                      "\"eval_ms\": %.6f}",
+                      key.c_str(), v[0], v[1], v[2], ms);
+        keep.push_back(buf);
+        std::ofstream f(path, std::ios::trunc);
+        if (!f) fail(LFE_ERR_ARG, "cannot write the tuning cache " + path);
+        f << "{\"lfe_autotune\": 1, \"entries\": [\n";
+        for (size_t i = 0; i < keep.size(); ++i) f << keep[i] << (i + 1 < keep.size() ? ",\n" : "\n");
+        f << "]}\n";
+    }
+
+    void apply_tuning(const int* v)
+    {
+        const int bmax = pairs_blocks_per_sm<real>();
+        pair_warps = nsm * 4 * std::min(std::max(v[0], 1), bmax);
+        uv_blocks = std::max(v[1], 1);
+        M2.lines = v[2] == 4 ? 4 : 0;
+        invalidate_graph();
+        ++generation;   // batches that hold this system's step recapture it
+    }
+
+    double time_eval_graph(int reps)
+    {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        eval_kernels_branched(cs);
+        CK(cudaStreamEndCapture(cs, &g));
+        CK(cudaGraphInstantiate(&e, g, 0));
+        for (int r = 0; r < 3; ++r) CK(cudaGraphLaunch(e, cs));
+        std::vector<cudaEvent_t> ev(2 * reps);
+        for (auto& x : ev) CK(cudaEventCreate(&x));
+        for (int r = 0; r < reps; ++r) {
+            CK(cudaEventRecord(ev[2 * r], cs));
+            CK(cudaGraphLaunch(e, cs));
+            CK(cudaEventRecord(ev[2 * r + 1], cs));
+        }
+        CK(cudaStreamSynchronize(cs));
+        std::vector<float> t(reps);
+        for (int r = 0; r < reps; ++r) CK(cudaEventElapsedTime(&t[r], ev[2 * r], ev[2 * r + 1]));
+        for (auto& x : ev) cudaEventDestroy(x);
+        cudaGraphExecDestroy(e);
+        cudaGraphDestroy(g);
+        std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+        return t[reps / 2];
+    }
+
+    void autotune(int reps, const char* cache_path, double* best_ms, int* params) override
+    {
+        if (reps < 1 || reps > 10000) fail(LFE_ERR_ARG, "reps must be in [1, 10000]");
+        const std::string key = tune_key();
+        int v[3] = {pairs_blocks_per_sm<real>(), nsm * 2, 16};
+        double best = 0.0;
+        if (cache_path && cache_find(cache_path, key, v, &best)) {
+            apply_tuning(v);
+            if (best_ms) *best_ms = best;
+            if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 1; }
+            return;
+        }
+        // a valid list for the current positions, nothing pending
+        settle_positions(cs);
+        if (exec) recover_overflow(cs);
+        settle_rebuild(cs);
+        CK(cudaDeviceSynchronize());
+        CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, cs));
+        const int bmax = pairs_blocks_per_sm<real>();
+        auto measure = [&](const int* c) {
+            apply_tuning(c);
+            return time_eval_graph(reps);
+        };
+        best = measure(v);
+        for (int b = 1; b <= bmax; ++b) {
+            if (b == v[0]) continue;
+            int c[3] = {b, v[1], v[2]};
+            const double t = measure(c);
+            if (t < best) { best = t; v[0] = b; }
+        }
+        if (n_ucl > 0) {
+            for (int ub : {nsm / 2, nsm, nsm * 4, nsm * 8}) {
+                if (ub < 1 || ub == v[1]) continue;
+                int c[3] = {v[0], ub, v[2]};
+                const double t = measure(c);
+                if (t < best) { best = t; v[1] = ub; }
+            }
+        }
+        if (dual) {
+            int c[3] = {v[0], v[1], v[2] == 16 ? 4 : 16};
+            const double t = measure(c);
+            if (t < best) { best = t; v[2] = c[2]; }
+        }
+        apply_tuning(v);
+        // the replays only accumulated forces and energies: clear them
+        CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, cs));
+        CK(cudaMemsetAsync(S.F, 0, sizeof(long long) * 3 * (size_t)n_pad, cs));
+        CK(cudaMemsetAsync(S.Fa, 0, sizeof(long long) * 3 * (size_t)n, cs));
+        CK(cudaMemsetAsync(S.E, 0, sizeof(long long) * E_N, cs));
+        CK(cudaStreamSynchronize(cs));
+        check_flags(cs);
+        if (cache_path) cache_store(cache_path, key, v, best);
+        if (best_ms) *best_ms = best;
+        if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 0; }
     }
 
     cudaStream_t side_stream() override { return cs2; }
@@ -1904,6 +2072,11 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream, cons
     int r = 0;
     int rc = guard(sys, [&] { r = sys->impl->time_stages(lambda, reps, (cudaStream_t)stream, names, ms, max_n); });
     return rc == LFE_OK ? r : rc;
+}
+
+int lfe_autotune(lfe_system* sys, int reps, const char* cache_path, double* best_ms, int* params)
+{
+    return guard(sys, [&] { sys->impl->autotune(reps, cache_path, best_ms, params); });
 }
 
 int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out)

@@ -123,6 +123,7 @@ struct PmeView {
     real* phi_u;              // [n_u] reciprocal potential of the other class at solute atoms
     R2<double>* Zraw64;       // optional: FP64 copy of the packed charge grid written by the first pass
     const R2<double>* Zin64;  // optional: FP64 input grid of the axis-2 (first) per-axis pass, read instead of Z
+    int lines;                // df64 per-axis passes: lines per block (4 or 16; 0 = the largest that fits)
     // plane / column transform (used when a K1 x K2 plane fits in shared memory)
     int planes;               // 1: plane kernels in use, 0: one kernel per axis
     int ngroups, cg_max;      // column groups of the axis-0 pass and the largest group

@@ -332,7 +332,7 @@ void launch_fft(const PmeView<real>& p, int axis, int sign, int from_fixed, cuda
     if constexpr (sizeof(real) == 4) {
         launch_fft_nl<real, 16>(p, axis, sign, from_fixed, st);
     } else if constexpr (std::is_same<real, df64>::value) {
-        if (fft_lines<real>(p.K[axis]) == 16) launch_fft_nl<real, 16>(p, axis, sign, from_fixed, st);
+        if (p.lines != 4 && fft_lines<real>(p.K[axis]) == 16) launch_fft_nl<real, 16>(p, axis, sign, from_fixed, st);
         else launch_fft_nl<real, 4>(p, axis, sign, from_fixed, st);
     } else {
         launch_fft_nl<real, 4>(p, axis, sign, from_fixed, st);

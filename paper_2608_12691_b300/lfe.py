@@ -31,7 +31,7 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_time_stages", "lfe_autotune", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
     "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
@@ -116,6 +116,8 @@ def load():
     lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
     lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
+    lib.lfe_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, vp, vp]
+    lib.lfe_autotune.restype = ctypes.c_int
     lib.lfe_time_stages.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp,
                                     ctypes.POINTER(ctypes.c_char_p), _dp, ctypes.c_int]
     lib.lfe_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
@@ -386,6 +388,16 @@ class System:
         self._check(self._lib.lfe_dafed_masses(self.h, atoms.shape[0], atoms.ctypes.data, float(c),
                                                out.ctypes.data))
         return out
+
+    def autotune(self, reps=20, cache_path=None):
+        """Choose the evaluation's launch shapes by timing (lfe_autotune).
+        Returns (median evaluation ms, {pair_blocks_per_sm, uv_blocks,
+        df64_lines, from_cache})."""
+        best = ctypes.c_double()
+        params = (ctypes.c_int * 4)()
+        path = None if cache_path is None else str(cache_path).encode()
+        self._check(self._lib.lfe_autotune(self.h, int(reps), path, ctypes.byref(best), params))
+        return best.value, dict(zip(["pair_blocks_per_sm", "uv_blocks", "df64_lines", "from_cache"], list(params)))
 
     def time_stages(self, lam, reps=10, stream=None, max_n=32):
         names = (ctypes.c_char_p * max_n)()
