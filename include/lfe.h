@@ -271,7 +271,8 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
  * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
  * passes (4 or 16), one knob at a time, each candidate replayed `reps`
- * (1..10000) times, the median deciding.  The replays leave the state
+ * (1..10000) times, the median deciding (a candidate must be 2 % faster than
+ * the current choice to replace it).  The replays leave the state
  * (positions, velocities, theta, counters, accumulators) as it was; the next
  * lfe_step recaptures its graph with the chosen shapes.  Launch shapes change
  * only how work is split over blocks and warps, so results stay within the
