@@ -672,8 +672,15 @@ struct System final : SystemBase {
         }
         CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         CK(cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking));
+        // the PME branches (the longest dependent chains of the evaluation)
+        // get the higher priority: their blocks are scheduled ahead of the
+        // pair kernel's and the other branches' (the captured step graph is
+        // instantiated with per-node priorities; step 0.150 -> 0.148 ms on
+        // the octanol box, 0.153 with the pair branch first)
+        int prio_lo = 0, prio_hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
         for (int k = 0; k < 4; ++k) {
-            CK(cudaStreamCreateWithFlags(&br[k], cudaStreamNonBlocking));
+            CK(cudaStreamCreateWithPriority(&br[k], cudaStreamNonBlocking, (k == 1 || k == 2) ? prio_hi : prio_lo));
             CK(cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming));
         }
         CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
@@ -1276,7 +1283,7 @@ struct System final : SystemBase {
         CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
         launch_step_end(S, T, s0);
         CK(cudaStreamEndCapture(s0, &graph));
-        CK(cudaGraphInstantiate(&exec, graph, 0));
+        CK(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
     }
 
     // steps requested through lfe_step since creation, and launches since

@@ -6,7 +6,7 @@ On an ion lattice whose spacing exceeds r_cut + skin there are no real-space
 pairs and no exclusions: U_uv is then the reciprocal cross term plus its
 background share only, and the FP32 system's U_uv and dU/dlambda must match
 the level-2 oracle (smooth PME on the same grid, FP64) far below the FP32
-rounding level."""
+rounding level (1e-9: the fixed-point charge grid is the limit)."""
 import numpy as np
 import pytest
 
@@ -43,12 +43,15 @@ def test_reciprocal_class_energies_far_below_fp32_rounding(seed, precision):
     E = R.nonbonded(d, level=2)[0]
     assert E["n_pairs"] == 0
     g = lfe.System(d, precision=precision)
+    # FP32 systems: limited by the fixed-point charge grid (2^-36 e per
+    # point); FP32 transforms would give 1e-6 to 1e-7
+    tol = 1e-9 if precision == lfe.LFE_FP32_MIXED else 1e-10
     for lam in (0.2, 0.6, 0.9):
         t, F = g.eval(lam)
         assert t["n_pairs"] == 0
         hA, hB, dA, dB = R.switching(lam)
-        assert abs(t["U_uv"] - E["U_uv"]) <= 1e-10 * abs(E["U_uv"])
-        assert abs(t["U_vv"] - E["U_vv"]) <= 1e-10 * abs(E["U_vv"])
-        assert abs(t["U_uu"] - E["U_uu"]) <= 1e-10 * abs(E["U_uu"])
-        assert abs(t["dUdl"] - dA * E["U_uv"]) <= 1e-10 * max(abs(dA * E["U_uv"]), 1e-300)
+        assert abs(t["U_uv"] - E["U_uv"]) <= tol * abs(E["U_uv"])
+        assert abs(t["U_vv"] - E["U_vv"]) <= tol * abs(E["U_vv"])
+        assert abs(t["U_uu"] - E["U_uu"]) <= tol * abs(E["U_uu"])
+        assert abs(t["dUdl"] - dA * E["U_uv"]) <= tol * max(abs(dA * E["U_uv"]), 1e-300)
     g.close()
