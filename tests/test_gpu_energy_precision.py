@@ -43,9 +43,9 @@ def test_reciprocal_class_energies_far_below_fp32_rounding(seed, precision):
     E = R.nonbonded(d, level=2)[0]
     assert E["n_pairs"] == 0
     g = lfe.System(d, precision=precision)
-    # FP32 systems: limited by the fixed-point charge grid (2^-36 e per
-    # point); FP32 transforms would give 1e-6 to 1e-7
-    tol = 1e-9 if precision == lfe.LFE_FP32_MIXED else 1e-10
+    # both modes share the fixed-point charge grid (2^-36 e per point), which
+    # sets the limit near 1e-10; FP32 transforms would give 1e-6 to 1e-7
+    tol = 1e-9
     for lam in (0.2, 0.6, 0.9):
         t, F = g.eval(lam)
         assert t["n_pairs"] == 0

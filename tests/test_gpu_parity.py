@@ -61,12 +61,20 @@ def big_grid():
     return dict(small_ragged(), grid=[100, 100, 100])
 
 
+def solute_only():
+    # the 12-atom rigid solute alone in the C0 box: no solvent clusters, no
+    # solute-solvent pairs (U_uv = U_soft = 0, dU/dlambda = 0)
+    d = S.make_c0()
+    return S.subsystem(d, np.flatnonzero(d["solute"]))
+
+
 SYSTEMS = {
     "c0": S.make_c0,
     "ragged": small_ragged,
     "odd_grid": odd_grid,
     "big_grid": big_grid,
     "nosolute": no_solute,
+    "soluteonly": solute_only,
     "c2": S.make_c2,
     "c1": S.make_c1,
     "c4": lambda: S.make_c4_frame(frame=5),
@@ -117,7 +125,7 @@ LAMS = [0.0, 0.2, 0.35, 0.6, 1.0]
 
 
 @pytest.mark.parametrize("precision", [lfe.LFE_FP64, lfe.LFE_FP32_MIXED])
-@pytest.mark.parametrize("key", ["c0", "ragged", "nosolute"])
+@pytest.mark.parametrize("key", ["c0", "ragged", "nosolute", "soluteonly"])
 def test_small_parity(key, precision):
     d = SYSTEMS[key]()
     for lam in LAMS + [d["lam"]]:
@@ -147,6 +155,13 @@ def test_eval_is_bitwise_reproducible():
     t2, F2 = g.eval(0.47)
     assert np.array_equal(F1, F2)
     assert all(t1[k] == t2[k] for k in t1)
+
+
+def test_empty_system_is_rejected():
+    d = S.subsystem(S.make_c0(), np.zeros(0, dtype=np.int64))
+    with pytest.raises(lfe.LfeError) as e:
+        lfe.System(d)
+    assert e.value.code == lfe.LFE_ERR_ARG
 
 
 def test_bad_inputs_are_rejected_and_system_survives():
