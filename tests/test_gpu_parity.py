@@ -62,10 +62,17 @@ def big_grid():
 
 
 def solute_only():
-    # the 12-atom rigid solute alone in the C0 box: no solvent clusters, no
-    # solute-solvent pairs (U_uv = U_soft = 0, dU/dlambda = 0)
+    # the 12-atom solute alone in the C0 box: no solvent clusters, no
+    # solute-solvent pairs (U_uv = U_soft = 0, dU/dlambda = 0).  Its
+    # exclusions are dropped so that its 66 pairs are real-space pairs (with
+    # every pair excluded the net force is a small remainder of cancelling
+    # reciprocal and correction terms, and a relative force norm is
+    # ill-conditioned), Coulomb only (bonded atoms would overlap in LJ)
     d = S.make_c0()
-    return S.subsystem(d, np.flatnonzero(d["solute"]))
+    d = S.subsystem(d, np.flatnonzero(d["solute"]))
+    d["excl"] = np.zeros((0, 2), dtype=np.int32)
+    d["epsilon"] = np.zeros_like(d["epsilon"])
+    return d
 
 
 SYSTEMS = {
