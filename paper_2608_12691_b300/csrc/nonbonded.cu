@@ -1104,82 +1104,73 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
         pa.w = s.q[a] * (real)sqrt(KE);
         const R2<real> la = {(real)0.5 * s.sig[a], (real)2 * sqrt(s.eps[a])};
         const int ua = s.sol[a];
-        // both partner lists at once: each round loads up to EXCL_BATCH
-        // exclusion and EXCL_BATCH 1-4 partners of this lane (two dependent
-        // load phases: partner indices, then their coordinates and charges)
-        const int* lists[2] = {ex.ex_list, ex.p14_list};
-        int eb[2] = {ex.ex_start[a] + sub, ex.p14_start[a] + sub};
-        const int ee[2] = {ex.ex_start[a + 1], ex.p14_start[a + 1]};
-        while (eb[0] < ee[0] || eb[1] < ee[1]) {
-            int bb[2][EXCL_BATCH];
-            R4<real> pbb[2][EXCL_BATCH];
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool is14 = pass == 1;
+            const int e0 = is14 ? ex.p14_start[a] : ex.ex_start[a];
+            const int e1 = is14 ? ex.p14_start[a + 1] : ex.ex_start[a + 1];
+          for (int eb = e0 + sub; eb < e1; eb += 4 * EXCL_BATCH) {
+            // the partner records of a batch are loaded together (two
+            // dependent rounds: partner, its coordinates and charge)
+            int bb[EXCL_BATCH];
+            R4<real> pbb[EXCL_BATCH];
 #pragma unroll
-            for (int pass = 0; pass < 2; ++pass)
+            for (int u = 0; u < EXCL_BATCH; ++u) {
+                const int e = eb + 4 * u;
+                bb[u] = e < e1 ? (is14 ? ex.p14_list[e] : ex.ex_list[e]) : -1;
+            }
 #pragma unroll
-                for (int u = 0; u < EXCL_BATCH; ++u) {
-                    const int e = eb[pass] + 4 * u;
-                    bb[pass][u] = e < ee[pass] ? lists[pass][e] : -1;
+            for (int u = 0; u < EXCL_BATCH; ++u)
+                if (bb[u] >= 0) {
+                    pbb[u] = s.x[bb[u]];
+                    pbb[u].w = s.q[bb[u]] * (real)sqrt(KE);
                 }
 #pragma unroll
-            for (int pass = 0; pass < 2; ++pass)
-#pragma unroll
-                for (int u = 0; u < EXCL_BATCH; ++u)
-                    if (bb[pass][u] >= 0) {
-                        pbb[pass][u] = s.x[bb[pass][u]];
-                        pbb[pass][u].w = s.q[bb[pass][u]] * (real)sqrt(KE);
-                    }
-#pragma unroll
-            for (int pass = 0; pass < 2; ++pass) {
-                const bool is14 = pass == 1;
-#pragma unroll
-                for (int u = 0; u < EXCL_BATCH; ++u) {
-                    const int e = eb[pass] + 4 * u;
-                    if (e >= ee[pass]) break;
-                    const int b = bb[pass][u];
-                    const R4<real> pb = pbb[pass][u];
-                    real d[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
-                    for (int k = 0; k < 3; ++k) d[k] -= s.L[k] * rint_(d[k] * s.invL[k]);
-                    const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    real en = 0, g = 0;   // g = -(dE/dr)/r
-                    if (r2 > (real)0) {
-                        const real rinv = rsqrt_(r2);
-                        const real rinv2 = rinv * rinv;
-                        const real qq = pa.w * pb.w;
-                        if (!is14) {
-                            const real ar = s.alpha * r2 * rinv;
-                            const real ev = erf_(ar);
-                            en = -qq * ev * rinv;
-                            // dE/dr = qq erf/r^2 - qq (2a/sqrt(pi)) exp(-a^2 r^2)/r
-                            g = -(qq * ev * rinv2 - qq * s.two_a_sqrtpi * exp_(-ar * ar) * rinv) * rinv;
-                        } else {
-                            const R2<real> sc = ex.p14_s[e];
-                            const R2<real> lb = {(real)0.5 * s.sig[b], (real)2 * sqrt(s.eps[b])};
-                            en = sc.y * qq * rinv;
-                            g = sc.y * qq * rinv2 * rinv;
-                            const real sg = la.x + lb.x, e4 = la.y * lb.y;
-                            if (e4 != (real)0) {
-                                const real s2 = sg * sg * rinv2, s6 = s2 * s2 * s2;
-                                en += sc.x * e4 * (s6 * s6 - s6);
-                                g += sc.x * e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
-                            }
+            for (int u = 0; u < EXCL_BATCH; ++u) {
+                const int e = eb + 4 * u;
+                if (e >= e1) break;
+                const int b = bb[u];
+                const R4<real> pb = pbb[u];
+                real d[3] = {pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
+                for (int k = 0; k < 3; ++k) d[k] -= s.L[k] * rint_(d[k] * s.invL[k]);
+                const real r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                real en = 0, g = 0;   // g = -(dE/dr)/r
+                if (r2 > (real)0) {
+                    const real rinv = rsqrt_(r2);
+                    const real rinv2 = rinv * rinv;
+                    const real qq = pa.w * pb.w;
+                    if (!is14) {
+                        const real ar = s.alpha * r2 * rinv;
+                        const real ev = erf_(ar);
+                        en = -qq * ev * rinv;
+                        // dE/dr = qq erf/r^2 - qq (2a/sqrt(pi)) exp(-a^2 r^2)/r
+                        g = -(qq * ev * rinv2 - qq * s.two_a_sqrtpi * exp_(-ar * ar) * rinv) * rinv;
+                    } else {
+                        const R2<real> sc = ex.p14_s[e];
+                        const R2<real> lb = {(real)0.5 * s.sig[b], (real)2 * sqrt(s.eps[b])};
+                        en = sc.y * qq * rinv;
+                        g = sc.y * qq * rinv2 * rinv;
+                        const real sg = la.x + lb.x, e4 = la.y * lb.y;
+                        if (e4 != (real)0) {
+                            const real s2 = sg * sg * rinv2, s6 = s2 * s2 * s2;
+                            en += sc.x * e4 * (s6 * s6 - s6);
+                            g += sc.x * e4 * ((real)12 * s6 * s6 - (real)6 * s6) * rinv2;
                         }
                     }
-                    // force on a: -g d (d = r_b - r_a)
-                    fx -= g * d[0];
-                    fy -= g * d[1];
-                    fz -= g * d[2];
-                    if (a < b) {
-                        const int ub = s.sol[b];
-                        const int cls = (ua && ub) ? 1 : ((ua || ub) ? 2 : 0);
-                        const int slotk = (is14 ? 3 : 0) + cls;
+                }
+                // force on a: -g d (d = r_b - r_a)
+                fx -= g * d[0];
+                fy -= g * d[1];
+                fz -= g * d[2];
+                if (a < b) {
+                    const int ub = s.sol[b];
+                    const int cls = (ua && ub) ? 1 : ((ua || ub) ? 2 : 0);
+                    const int slotk = (is14 ? 3 : 0) + cls;
 #pragma unroll
-                        for (int c = 0; c < 6; ++c)
-                            if (c == slotk) acc[c] += (double)en;   // constant indices: acc stays in registers
-                    }
+                    for (int c = 0; c < 6; ++c)
+                        if (c == slotk) acc[c] += (double)en;   // constant indices: acc stays in registers
                 }
             }
-            eb[0] += 4 * EXCL_BATCH;
-            eb[1] += 4 * EXCL_BATCH;
+          }
         }
     }
     for (int o = 1; o < 4; o <<= 1) {
@@ -1194,7 +1185,6 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
     }
     const int lane = threadIdx.x & 31;
     for (int c = 0; c < 6; ++c) {
-        if (!__any_sync(0xffffffffu, acc[c] != 0.0)) continue;   // class absent from this warp
         long long v = __double2ll_rn(warp_sum_d(acc[c]) * ESCALE);
         if (lane == 0 && v) atomic_add_ll(&s.E[(c < 3 ? E_EXCL_VV : E_14_VV) + (c % 3)], v);
     }
