@@ -270,6 +270,24 @@ def batched_leg(args, stream, flush):
             "setup_s": t_gen}
 
 
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (every rank gets it); the timed region
+    of the slowest rank sets the whole job's time."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_ns_day(dt_ps, ms_per_step, world):
+    """Whole-job ns/day: every rank advances its own replica (same system
+    size, own seed) by one step of dt_ps in ms_per_step (the slowest rank's)."""
+    return dt_ps * 1e-3 * 86400.0 / (ms_per_step * 1e-3) * world
+
+
 def time_steps(g, K, stream, flush):
     import torch
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -324,13 +342,9 @@ def run_ours(args):
     clocks = sampler.stop() if sampler else None
     pos, vel, ext1 = g.get_state()       # raises on any device-side error
     assert np.isfinite(pos).all()
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms), world, "cuda")
     ms_step = total_ms / args.steps
-    ns_day = dt_ps * 1e-3 * 86400.0 / (ms_step * 1e-3) * world
+    ns_day = weak_scaling_ns_day(dt_ps, ms_step, world)
     rebuilds = int(ext1["n_rebuilds"] - ext0["n_rebuilds"])
     # kernels of one captured step (FP32 systems): rebuild decision, pair
     # kernel; spread, plane transform, column pass, inverse plane transform,

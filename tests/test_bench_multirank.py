@@ -1,0 +1,51 @@
+"""The multi-rank (replicas) path of bench.py on the CPU: two gloo ranks.
+Each rank advances its own replica, the job time is the slowest rank's, the
+job's ns/day is the sum over ranks, each rank builds its own seeded
+replica, and the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_ms = [12.5, 17.25][rank]
+    out[rank] = bench.max_over_ranks(local_ms, world, "cpu")
+    d, _ = bench.make_workload("c0", rank)
+    out[10 + rank] = float(np.asarray(d["pos"]).sum())
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time_and_own_replicas():
+    port = _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+    assert out[0] == out[1] == 17.25
+    assert out[10] != out[11]          # the replicas are different seeded systems
+    one = bench.weak_scaling_ns_day(0.001, 0.15, 1)
+    assert bench.weak_scaling_ns_day(0.001, 0.15, 2) == pytest.approx(2 * one)
+    assert one == pytest.approx(0.001 * 1e-3 * 86400.0 / 0.15e-3)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    import sys
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "c0"])
+    bench.run_reference(bench.parse())
+    assert capsys.readouterr().out == ""
