@@ -370,6 +370,10 @@ def run_ours(args):
                 "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop/FMA x 2032 MHz (max SM clock)"}
         if clocks and clocks.get("sm_mhz"):
             roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / 2032.0)
+        f32_meas, f64_meas = lfe.alu_peak()
+        roof["peak_measured_fma_fp32"] = f32_meas
+        roof["peak_measured_fma_fp64"] = f64_meas
+        roof["frac_of_measured_fma"] = achieved / f32_meas
         # end to end through the public API with host buffers
         e2e = None
         if args.e2e_steps > 0:

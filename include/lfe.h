@@ -286,6 +286,15 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
  * serves the batched-replica workload's "sizes chosen by an autotuner". */
 int lfe_autotune(lfe_system* sys, int reps, const char* cache_path, double* best_ms, int* params);
 
+/* Measured arithmetic throughput of the current device in TFLOP/s (FMA =
+ * 2 flops): 8 independent FMA chains per thread over 8 blocks of 256 threads
+ * per multiprocessor, best of three timed launches (CUDA events), for FP32
+ * and FP64 (either pointer may be NULL to skip).  A measured denominator
+ * beside the unit-count peak (SMs x 128 FP32 lanes x 2 x clock) that the pair
+ * kernel's ALU roofline is quoted against; allocates 2 KB of device memory
+ * for the result sink.  Errors: LFE_ERR_CUDA.  The paper has no counterpart. */
+int lfe_alu_peak(double* fp32_tflops, double* fp64_tflops);
+
 /* Batched replicas (lambda windows, solvents, solutes; sizes may differ):
  * lfe_batch_create groups existing systems (not copied; they must outlive
  * the batch and must not be destroyed while it exists).  lfe_batch_step

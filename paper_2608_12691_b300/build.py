@@ -9,7 +9,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblfe.so")
-SOURCES = ["nonbonded.cu", "pme.cu", "dyn.cu", "engine.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["nonbonded.cu", "pme.cu", "dyn.cu", "engine.cu", "noalloc.cu", "adjoint.cu", "probe.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

@@ -31,10 +31,22 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
     "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
+
+
+def alu_peak():
+    """Measured FP32 and FP64 FMA throughput of the current device, TFLOP/s
+    (lfe_alu_peak)."""
+    lib = load()
+    f32 = ctypes.c_double()
+    f64 = ctypes.c_double()
+    rc = lib.lfe_alu_peak(ctypes.byref(f32), ctypes.byref(f64))
+    if rc != 0:
+        raise LfeError(rc, "lfe_alu_peak failed")
+    return f32.value, f64.value
 
 
 class LfeError(RuntimeError):
@@ -116,6 +128,8 @@ def load():
     lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
     lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
+    lib.lfe_alu_peak.argtypes = [vp, vp]
+    lib.lfe_alu_peak.restype = ctypes.c_int
     lib.lfe_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, vp, vp]
     lib.lfe_autotune.restype = ctypes.c_int
     lib.lfe_time_stages.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp,
