@@ -382,7 +382,7 @@ __global__ void k_dafed_step(SysView<real> s, DafedView d)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     if (s.flags[FL_ERROR] & ERRB_OVERFLOW) return;   // step skipped (see k_integrate)
-    const unsigned long long step = s.lam->step;
+    const unsigned long long step = s.lam->step - 1ull;   // k_theta has advanced the counter
     double n0, n1, n2;
     normals3<double>(make_uint4((unsigned)k, (unsigned)step, (unsigned)(step >> 32), 2u), d.key, n0, n1, n2);
     const double m = d.mass[k];
@@ -651,7 +651,9 @@ __global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real
         }
         return;
     }
-    const unsigned long long step = s.lam->step;
+    // the kicks were drawn by k_noise; the counter is not read here (k_theta
+    // advances it concurrently)
+    const unsigned long long step = 0ull;
     if (G.kind == GROUP_WATER) integrate_group<real, GROUP_WATER, 3>(s, g, G, step);
     else if (G.kind == GROUP_STAR && G.natom == 4) integrate_group<real, GROUP_STAR, 4>(s, g, G, step);
     else if (G.kind == GROUP_STAR && G.natom == 3) integrate_group<real, GROUP_STAR, 3>(s, g, G, step);
@@ -795,7 +797,10 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const int lane = threadIdx.x;
     LamState* L = s.lam;
     long long* E = s.E;
-    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) return;   // step skipped (see k_integrate)
+    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {   // step skipped (see k_integrate): no advance
+        if (lane < E_N) E[lane] = 0;
+        return;
+    }
     const double Uvv = efix(E, E_PAIR_VV) + efix(E, E_EXCL_VV) + efix(E, E_14_VV) + efix(E, E_REC_VV) + t.const_vv;
     const double Uuu = efix(E, E_PAIR_UU) + efix(E, E_EXCL_UU) + efix(E, E_14_UU) + efix(E, E_REC_UU) + t.const_uu;
     const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
@@ -839,19 +844,14 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
         L->dUdl = dUdl; L->U = U; L->V_std = V0; L->V_exp = V1;
         if (!isfinite(U) || !isfinite(thn)) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
+        // the step ends here: its counter (the Philox counter of the atoms,
+        // theta and the auxiliary angles) advances; k_dafed_step, which
+        // follows in the same stream, uses the value before the advance
+        L->step = stepn;
     }
-}
-
-// end of a step, after the atoms and theta have moved: advance the step
-// counter (the Philox counter of both integrators), clear the energy
-// accumulators, and (inside the captured graph) choose whether the
-// conditional neighbour-list rebuild runs
-template <typename real>
-__global__ void k_step_end(SysView<real> s, ThetaView<real> t)
-{
-    const int lane = threadIdx.x;
-    if (lane == 0 && !(s.flags[FL_ERROR] & ERRB_OVERFLOW)) s.lam->step += 1;
-    if (lane < E_N) s.E[lane] = 0;
+    // every energy accumulator has been read: clear them for the next step
+    __syncwarp();
+    if (lane < E_N) E[lane] = 0;
 }
 
 // first node of a captured step: the neighbour list is rebuilt (by the
@@ -879,12 +879,6 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     k_theta<real><<<1, 32, 0, st>>>(s, t);
 }
 
-template <typename real>
-void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
-{
-    k_step_end<real><<<1, 32, 0, st>>>(s, t);
-}
-
 #define LFE_INST_DYN(real)                                                                               \
     template void launch_set_lambda<real>(const SysView<real>&, double, cudaStream_t);                    \
     template void launch_eval_out<real>(const SysView<real>&, double*, double*, double, double, double,   \
@@ -901,8 +895,8 @@ void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStrea
     template void launch_dafed_force<real>(const SysView<real>&, const DafedView&, cudaStream_t);            \
     template void launch_dafed_step<real>(const SysView<real>&, const DafedView&, cudaStream_t);             \
     template void launch_dafed_probe<real>(const SysView<real>&, const DafedView&, double, double*, cudaStream_t); \
-    template void launch_rebuild_cond<real>(const SysView<real>&, cudaGraphConditionalHandle, cudaStream_t);    \
-    template void launch_step_end<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);
+    template void launch_rebuild_cond<real>(const SysView<real>&, cudaGraphConditionalHandle, cudaStream_t);
+
 LFE_INST_DYN(float)
 LFE_INST_DYN(double)
 

@@ -1247,7 +1247,6 @@ struct System final : SystemBase {
         launch_integrate(S, G, s0);
         launch_theta(S, T, s0);
         launch_dafed_step(S, D, s0);
-        launch_step_end(S, T, s0);
     }
 
     void note_batch_steps(int n) override
@@ -1286,7 +1285,6 @@ struct System final : SystemBase {
         CK(cudaEventRecord(ev_join[0], br[0]));
         launch_integrate(S, G, s0);
         CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
-        launch_step_end(S, T, s0);
         CK(cudaStreamEndCapture(s0, &graph));
         CK(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
     }
@@ -1310,7 +1308,6 @@ struct System final : SystemBase {
         launch_integrate(S, G, st);
         launch_theta(S, T, st);
         launch_dafed_step(S, D, st);
-        launch_step_end(S, T, st);
         CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (h_flags[FL_REBUILD]) {

@@ -281,7 +281,6 @@ template <typename real> void launch_dafed_probe(const SysView<real>& s, const D
 // alongside the force evaluation
 template <typename real> void launch_prestep(const SysView<real>& s, const StepView<real>& g,
                                              const ThetaView<real>& t, cudaStream_t st);
-template <typename real> void launch_step_end(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
 template <typename real> void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st);
 template <typename real> void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st);
 template <typename real> void launch_eval_out(const SysView<real>& s, double* forces, double* terms,
