@@ -133,8 +133,9 @@ struct System final : SystemBase {
     int nsm = 148;              // multiprocessors of the device
     double const_vv = 0, const_uu = 0, const_uv = 0;
     cudaStream_t cs = nullptr, cs2 = nullptr;
-    cudaStream_t br[4] = {nullptr, nullptr, nullptr, nullptr};   // capture branches
-    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_built = nullptr, ev_join[4] = {nullptr, nullptr, nullptr, nullptr};
+    static constexpr int NBR = 5;
+    cudaStream_t br[NBR] = {};   // capture branches
+    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_built = nullptr, ev_join[NBR] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* h_flags = nullptr;        // pinned
@@ -187,7 +188,7 @@ struct System final : SystemBase {
         if (h_state) cudaFreeHost(h_state);
         if (cs) cudaStreamDestroy(cs);
         if (cs2) cudaStreamDestroy(cs2);
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < NBR; ++k) {
             if (br[k]) cudaStreamDestroy(br[k]);
             if (ev_join[k]) cudaEventDestroy(ev_join[k]);
         }
@@ -684,7 +685,7 @@ struct System final : SystemBase {
         // the octanol box, 0.153 with the pair branch first)
         int prio_lo = 0, prio_hi = 0;
         CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < NBR; ++k) {
             CK(cudaStreamCreateWithPriority(&br[k], cudaStreamNonBlocking, (k == 1 || k == 2) ? prio_hi : prio_lo));
             CK(cudaEventCreateWithFlags(&ev_join[k], cudaEventDisableTiming));
         }
@@ -995,25 +996,22 @@ struct System final : SystemBase {
         CK(cudaStreamEndCapture(cs2, &body_out));
     }
 
-    // The evaluation as four concurrent branches (used inside the captured
-    // step graph): pair kernel | FP32 PME chain | FP64 PME energy branch (it
-    // starts once the first FP32 pass has left the FP64 copy of the charge
-    // grid) | FP64 solute-solvent energies, exclusions and bonded terms.  The
-    // branches only meet in atomic fixed-point accumulators, so their order
-    // does not change any result.  B300 runs the FP64 branches on the FP64
-    // pipes while the FP32 pair and PME kernels use the FP32 pipes.
-    // the evaluation as four concurrent branches; with a theta view, the
-    // step's force-independent integrator parts run in the fourth branch.
-    // With a conditional handle the first branch starts with the step's
-    // conditional rebuild of the neighbour list: only the pair kernel and the
-    // solute-solvent energies (last in the fourth branch, after the rebuild)
-    // read the list and the cluster-sorted copy, so the PME, exclusion and
-    // bonded work runs beside the rebuild.
+    // The evaluation as five concurrent branches (used inside the captured
+    // step graph and timed by the autotuner): pair kernel | FP32 PME chain |
+    // df64 energy branch of the reciprocal sum (it starts once the first FP32
+    // pass has left the FP64 copy of the charge grid) | exclusions, bonded
+    // terms (and, with a theta view, the step's force-independent integrator
+    // parts) | FP64 solute-solvent energies.  The branches only meet in
+    // atomic fixed-point accumulators, so their order does not change any
+    // result.  With a conditional handle the first branch starts with the
+    // step's conditional rebuild of the neighbour list: only the pair kernel
+    // and the solute-solvent energies read the list and the cluster-sorted
+    // copy, so the PME, exclusion and bonded work runs beside the rebuild.
     void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr,
                                const cudaGraphConditionalHandle* rebuild = nullptr)
     {
         CK(cudaEventRecord(ev_fork, s0));
-        for (int k = 0; k < 4; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
+        for (int k = 0; k < NBR; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
         if (rebuild) {
             launch_rebuild_cond(S, *rebuild, br[0]);
             add_cond_build(br[0], *rebuild);
@@ -1056,9 +1054,9 @@ struct System final : SystemBase {
         launch_excl(S, X, br[3]);
         launch_bonded(S, B, br[3]);
         launch_dafed_force(S, D, br[3]);
-        CK(cudaStreamWaitEvent(br[3], ev_built, 0));
-        launch_uv_energy(S, N, uv_blocks, br[3]);
-        for (int k = 0; k < 4; ++k) {
+        CK(cudaStreamWaitEvent(br[4], ev_built, 0));
+        launch_uv_energy(S, N, uv_blocks, br[4]);
+        for (int k = 0; k < NBR; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
             CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
         }
