@@ -266,7 +266,7 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
                     const char** names, double* ms, int max_n);
 
 /* Autotuner: choose the evaluation's launch shapes for this system by
- * timing its captured evaluation graph (the four concurrent branches of the
+ * timing its captured evaluation graph (the five concurrent branches of the
  * step) on the device: blocks of the pair kernel per multiprocessor (1 up to
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
  * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
