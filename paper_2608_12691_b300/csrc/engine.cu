@@ -1064,7 +1064,7 @@ struct System final : SystemBase {
 
     // ------------------------------------------------------- autotuner
     // Launch shapes of the evaluation, chosen by timing the captured
-    // evaluation graph (its four concurrent branches, as in the step) for
+    // evaluation graph (its five concurrent branches, as in the step) for
     // each candidate: blocks of the pair kernel per multiprocessor, blocks
     // of the FP64 solute-solvent energy kernel, lines per block of the df64
     // transform passes.  One knob at a time (coordinate descent), each
