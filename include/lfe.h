@@ -96,6 +96,9 @@ typedef struct {
     double opes_sigma;        /* step: kernel width on theta */
     int opes_max_kernels;     /* step: kernel capacity per bias (default 1024 if <= 0) */
     unsigned long long seed;  /* step: Philox4x32-10 key */
+    double lambda_temperature; /* step: theta's thermostat temperature, K (<= 0: `temperature`).  A hot
+                                * theta is the lambda-d-AFED protocol (Section 3.2: 5000-10000 K with
+                                * masses 1e4-1e6 amu nm^2); the OPES biases keep the physical beta */
 } lfe_params;
 
 /* System description (host arrays, copied by lfe_create).

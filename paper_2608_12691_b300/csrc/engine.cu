@@ -217,6 +217,7 @@ struct System final : SystemBase {
         if (!(p.r_cut > 0)) fail(LFE_ERR_ARG, "r_cut must be positive");
         if (p.r_switch >= p.r_cut) fail(LFE_ERR_ARG, "r_switch must be below r_cut (or negative for none)");
         if (!(p.ewald_alpha > 0)) fail(LFE_ERR_ARG, "ewald_alpha must be positive");
+        if (!std::isfinite(p.lambda_temperature)) fail(LFE_ERR_ARG, "lambda_temperature must be finite");
         if (p.pme_order != 4) fail(LFE_ERR_ARG, "pme_order must be 4");
         if (p.precision != LFE_FP32_MIXED && p.precision != LFE_FP64) fail(LFE_ERR_ARG, "unknown precision");
         if (!finite_all(t.pos, 3 * (size_t)n) || !finite_all(t.charge, n) || !finite_all(t.sigma, n) ||
@@ -629,7 +630,7 @@ struct System final : SystemBase {
         T.m = p.lambda_mass;
         T.dt = p.dt;
         T.a_fric = std::exp(-p.lambda_friction * p.dt);
-        T.kT = KB * p.temperature;
+        T.kT = KB * (p.lambda_temperature > 0 ? p.lambda_temperature : p.temperature);
         T.stride = p.opes_stride;
         T.max_k = p.opes_max_kernels > 0 ? p.opes_max_kernels : 1024;
         T.sigma = p.opes_sigma > 0 ? p.opes_sigma : 0.1;
@@ -923,7 +924,7 @@ struct System final : SystemBase {
         G.kT = (real)(KB * temperature);
         T.dt = dt;
         T.a_fric = std::exp(-P.lambda_friction * dt);
-        T.kT = KB * temperature;
+        T.kT = KB * (P.lambda_temperature > 0 ? P.lambda_temperature : temperature);
         D.dt = dt;
         D.a_fric = std::exp(-dafed_friction * dt);
         invalidate_graph();

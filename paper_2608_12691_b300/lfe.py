@@ -77,6 +77,7 @@ class Params(ctypes.Structure):
         ("opes_sigma", ctypes.c_double),
         ("opes_max_kernels", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
+        ("lambda_temperature", ctypes.c_double),
     ]
 
 
@@ -214,6 +215,7 @@ class System:
         pr.opes_sigma = float(d.get("opes_sigma", 0.1))
         pr.opes_max_kernels = int(d.get("opes_max_kernels", 1024))
         pr.seed = int(seed)
+        pr.lambda_temperature = float(d.get("lambda_temperature", 0.0))
         for k, v in over.items():
             setattr(pr, k, v)
         self.params = pr

@@ -42,8 +42,8 @@ def oracle_steps(d, nsteps):
                                       nrm, d["box"], pairs, lens)
         dV = std.bias(th)[1] + exp.bias(th)[1]
         th, p = D.theta_step(th, p, e["dUdl"], dl, dV, d["lambda_mass"], d["dt"], d["lambda_friction"],
-                             d["temperature"], D.theta_normal(step, SEED))
-        if (step + 1) % d["opes_stride"] == 0:
+                             d.get("lambda_temperature") or d["temperature"], D.theta_normal(step, SEED))
+        if d["opes_stride"] and (step + 1) % d["opes_stride"] == 0:
             std.deposit(th)
             exp.deposit(th)
     oracle_steps.ti = ti
@@ -70,6 +70,27 @@ def test_steps_match_oracle(precision, tx, tv):
     assert ext["n_kernels_std"] == len(std.c) and ext["n_kernels_exp"] == len(exp.c)
     assert ext["theta"] == pytest.approx(th, abs=1e-8 if precision == lfe.LFE_FP64 else 1e-5)
     assert ext["p_theta"] == pytest.approx(p, rel=1e-6 if precision == lfe.LFE_FP64 else 2e-3, abs=1e-9)
+
+
+@pytest.mark.parametrize("precision,tx", [(lfe.LFE_FP64, 2e-8), (lfe.LFE_FP32_MIXED, 5e-6)])
+def test_hot_theta_steps_match_oracle(precision, tx):
+    # lambda-d-AFED (Section 3.2): theta thermostatted at 5000 K with a heavy
+    # mass, no OPES deposits; the atoms stay at the physical temperature
+    d = water_system()
+    d.update(lambda_temperature=5000.0, lambda_mass=1e4, opes_stride=0)
+    n = 4
+    g = lfe.System(d, precision=precision, seed=SEED)
+    g.step(n)
+    pos, vel, ext = g.get_state()
+    x, v, th, p, std, exp = oracle_steps(d, n)
+    assert np.abs(min_image(pos - x, d["box"])).max() < tx
+    assert ext["n_kernels_std"] == 0 and ext["n_kernels_exp"] == 0
+    assert ext["theta"] == pytest.approx(th, abs=1e-8 if precision == lfe.LFE_FP64 else 1e-5)
+    assert ext["p_theta"] == pytest.approx(p, rel=1e-6 if precision == lfe.LFE_FP64 else 2e-3, abs=1e-9)
+    # the same steps at the physical temperature move theta differently
+    d2 = dict(d, lambda_temperature=0.0)
+    _, _, th2, p2, _, _ = oracle_steps(d2, n)
+    assert abs(p2 - p) > 1e-3 * abs(p)
 
 
 def test_constraints_hold_after_many_steps():
