@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-dafed", action="store_true", help="skip the flexible-solute d-AFED leg")
     p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default launch shapes (e.g. for a per-kernel launch list)")
     p.add_argument("--batch-replicas", type=int, default=32,
                    help="replicas in the batched leg (half water, half octanol; 0 skips it)")
     p.add_argument("--batch-steps", type=int, default=40)
@@ -321,7 +323,7 @@ def run_ours(args):
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     dt_ps = float(d["dt"])
     g = lfe.System(d, precision=prec, seed=2608 + rank)
-    tune_ms, tune = g.autotune(reps=20)
+    tune_ms, tune = (None, None) if args.no_autotune else g.autotune(reps=20)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
     stream = torch.cuda.current_stream()
@@ -415,7 +417,7 @@ def run_ours(args):
                           if prec == lfe.LFE_FP32_MIXED else "FP64", "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single replica",
                           "pairs_per_step": n_pairs, "tiles": n_tiles,
-                          "autotuned": dict(tune, eval_ms=tune_ms),
+                          "autotuned": dict(tune, eval_ms=tune_ms) if tune else None,
                           "tile_efficiency": n_pairs / (256.0 * n_tiles) if n_tiles else None},
                "pair_interactions_per_s": n_pairs / (ms_step * 1e-3) * world,
                "wall_ms_per_step": wall / args.steps * 1e3,
