@@ -350,7 +350,7 @@ def run_ours(args):
     rebuilds = int(ext1["n_rebuilds"] - ext0["n_rebuilds"])
     # kernels of one captured step (FP32 systems): rebuild decision, pair
     # kernel; spread, plane transform, column pass, inverse plane transform,
-    # gather; FP64 energy branch (two transform passes, column pass); kicks
+    # gather; df64 energy branch (two transform passes, column pass); kicks
     # and OPES bias, exclusions/1-4, bonded, FP64 uv energies; integrator,
     # theta (which also ends the step).  A neighbour-list build adds 11 kernels (column keys,
     # column scan, scatter, column sort, slot assignment, tile search, tile

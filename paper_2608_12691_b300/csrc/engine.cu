@@ -1679,7 +1679,7 @@ struct System final : SystemBase {
             launch_spread(S, M, st);
             CK(cudaEventRecord(ev[3], st));
             if (M.planes) {
-                // fwd: planes (+ the FP64 energy branch); conv: the column
+                // fwd: planes (+ the df64 energy branch); conv: the column
                 // pass with its axis-0 transforms; inv: planes
                 launch_planes(M, PLANE_FWD_FIX, st);
                 if (dual) {

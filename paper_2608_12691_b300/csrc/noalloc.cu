@@ -196,7 +196,7 @@ __global__ void k_na_gather(NaGeom g, const double* pos, const double* q, const 
     forces[3 * a + 2] = -qa * (g.K[2] / g.L[2]) * gz;
 }
 
-// class energies = reciprocal (FP64 branch) + self + neutralising background
+// class energies = reciprocal (FP64 transform) + self + neutralising background
 __global__ void k_na_finalize(NaScratch* sc, double alpha, double V, double* energies)
 {
     const double self_c = -KE * alpha / sqrt(PI);

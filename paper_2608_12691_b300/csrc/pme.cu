@@ -21,7 +21,7 @@ namespace lfe {
 // spreads the 16 points of plane j0 of the atom's 4 x 4 x 4 stencil.  The
 // products are formed in the same order as by one lane per atom.  Weights
 // and products in FP64: the fixed-point grid is shared by the force branch
-// and the FP64 energy branch, whose class energies set dU/dlambda to 1e-6
+// and the df64 energy branch, whose class energies set dU/dlambda to 1e-6
 // relative.
 template <typename real>
 __global__ void k_spread(SysView<real> s, PmeView<real> p)
