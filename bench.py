@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-dafed", action="store_true", help="skip the flexible-solute d-AFED leg")
     p.add_argument("--e2e-steps", type=int, default=200)
+    p.add_argument("--tune-cache", default=None,
+                   help="JSON autotuner cache shared by every system of the run (default: none for the main "
+                        "system, a temporary one for the batched replicas)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the default launch shapes (e.g. for a per-kernel launch list)")
     p.add_argument("--batch-replicas", type=int, default=32,
@@ -228,7 +231,7 @@ def batched_leg(args, stream, flush):
     t_gen = time.perf_counter() - t0
     reps = [lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=7000 + r, theta0=d["lam"]) for r, d in enumerate(dicts)]
     # systems of one kind share a tuning entry: the first of each kind is timed
-    cache = os.path.join(tempfile.mkdtemp(), "lfe_tune.json")
+    cache = args.tune_cache or os.path.join(tempfile.mkdtemp(), "lfe_tune.json")
     tuned = [g.autotune(reps=10, cache_path=cache)[1] for g in reps]
     b = lfe.Batch(reps)
     for frac, fric in ((0.05, 100.0), (0.25, 50.0), (0.5, 20.0), (1.0, None)):
@@ -323,7 +326,7 @@ def run_ours(args):
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     dt_ps = float(d["dt"])
     g = lfe.System(d, precision=prec, seed=2608 + rank)
-    tune_ms, tune = (None, None) if args.no_autotune else g.autotune(reps=20)
+    tune_ms, tune = (None, None) if args.no_autotune else g.autotune(reps=20, cache_path=args.tune_cache)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
     stream = torch.cuda.current_stream()
