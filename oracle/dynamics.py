@@ -319,3 +319,37 @@ def dafed_step(s, p, Fs, m, dt, gamma, T, normal):
     v = a * v + math.sqrt(KB * T * (1.0 - a * a) / m) * normal
     x = x + 0.5 * dt * v
     return wrap_angle(x), m * v
+
+
+# ------------------------------------------------- lambda replica exchange
+
+def hrex_delta(lam_a, lam_b, uuv_i, usoft_i, uuv_j, usoft_j):
+    """Energy change of swapping lambda between replica i (at lam_a) and
+    replica j (at lam_b).  With the potential linear in the two basis
+    energies (Eq. 4), U(x; lam) = U_0(x) + h_A(lam) U_uv(x) + h_B(lam) U_soft(x),
+    so  [U(x_i; b) + U(x_j; a)] - [U(x_i; a) + U(x_j; b)]
+      = (h_A(b) - h_A(a)) (U_uv,i - U_uv,j) + (h_B(b) - h_B(a)) (U_soft,i - U_soft,j)."""
+    from oracle.reference import switching
+    ha, hb = switching(lam_a)[:2], switching(lam_b)[:2]
+    return (hb[0] - ha[0]) * (uuv_i - uuv_j) + (hb[1] - ha[1]) * (usoft_i - usoft_j)
+
+
+def hrex_attempt(lams, uuv, usoft, T, seed, attempt):
+    """One exchange attempt over a ladder (replicas listed in lambda order,
+    lams[k] the lambda of the k-th): the pairs (k, k+1) with k of the
+    attempt's parity are tried; pair k is accepted with probability
+    min(1, exp(-beta Delta_k)), using the uniform (x + 0.5)/2^32 of the first
+    Philox4x32-10 word at counter (k, attempt_lo, attempt_hi, 3).  Returns
+    (accepted flags [n-1], new lambda of each replica)."""
+    n = len(lams)
+    beta = 1.0 / (KB * T)
+    acc = [0] * max(n - 1, 0)
+    new = list(lams)
+    key = seed_key(seed)
+    for k in range(attempt % 2, n - 1, 2):
+        d = hrex_delta(lams[k], lams[k + 1], uuv[k], usoft[k], uuv[k + 1], usoft[k + 1])
+        u = uniforms((k, attempt & _MASK, attempt >> 32, 3), key)[0]
+        if d <= 0.0 or u < math.exp(-beta * d):
+            acc[k] = 1
+            new[k], new[k + 1] = lams[k + 1], lams[k]
+    return acc, new

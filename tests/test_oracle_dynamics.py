@@ -141,3 +141,46 @@ def test_nve_energy_drift_small_box():
     q = len(energies) // 4
     drift = abs(energies[-q:].mean() - energies[:q].mean())
     assert drift / ke(v) < 2e-3
+
+
+# ---------------------------------------------------- lambda replica exchange
+
+def test_hrex_delta_is_the_swapped_energy_difference():
+    # the basis form of the swap energy equals the difference of four full
+    # evaluations (Eq. 4 at both lambdas for both configurations)
+    d = S.make_c0()
+    rng = np.random.default_rng(5)
+    xi = d["pos"]
+    xj = S.f32(d["pos"] + rng.normal(0.0, 0.003, d["pos"].shape))
+    a, b = 0.45, 0.8
+    ei = R.evaluate(d, a, level=1, pos=xi, with_bonded=False)
+    ej = R.evaluate(d, b, level=1, pos=xj, with_bonded=False)
+    eib = R.evaluate(d, b, level=1, pos=xi, with_bonded=False)
+    eja = R.evaluate(d, a, level=1, pos=xj, with_bonded=False)
+    direct = (eib["U"] + eja["U"]) - (ei["U"] + ej["U"])
+    Ei, Ej = R.nonbonded(d, level=1, pos=xi)[0], R.nonbonded(d, level=1, pos=xj)[0]
+    basis = D.hrex_delta(a, b, Ei["U_uv"], Ei["U_soft"], Ej["U_uv"], Ej["U_soft"])
+    assert basis == pytest.approx(direct, rel=1e-9, abs=1e-9)
+
+
+def test_hrex_attempt_metropolis_rules():
+    T, seed = 298.0, 11
+    # equal configurations: Delta = 0, always accepted, lambdas swap pairwise
+    acc, new = D.hrex_attempt([0.1, 0.5, 0.9, 1.0], [3.0] * 4, [2.0] * 4, T, seed, attempt=0)
+    assert acc == [1, 0, 1] and new == [0.5, 0.1, 1.0, 0.9]
+    # odd attempts try the other pairs
+    acc, new = D.hrex_attempt([0.1, 0.5, 0.9, 1.0], [3.0] * 4, [2.0] * 4, T, seed, attempt=1)
+    assert acc == [0, 1, 0] and new == [0.1, 0.9, 0.5, 1.0]
+    # a huge uphill Delta is rejected
+    acc, _ = D.hrex_attempt([0.5, 1.0], [1e6, 0.0], [0.0, 0.0], T, seed, attempt=0)
+    assert D.hrex_delta(0.5, 1.0, 1e6, 0.0, 0.0, 0.0) > 0 and acc == [0]
+    # the acceptance frequency of a fixed Delta matches exp(-beta Delta)
+    lam = [0.6, 0.7]
+    hA = [R.switching(x)[0] for x in lam]
+    dU = 0.7 / (hA[1] - hA[0])          # U_uv difference that gives Delta = 0.7 kJ/mol
+    delta = D.hrex_delta(0.6, 0.7, dU, 0.0, 0.0, 0.0)
+    assert delta == pytest.approx(0.7)
+    n = 4000
+    hits = sum(D.hrex_attempt(lam, [dU, 0.0], [0.0, 0.0], T, seed, attempt=2 * t)[0][0] for t in range(n))
+    p = math.exp(-0.7 / (0.0083144626 * T))
+    assert abs(hits / n - p) < 4 * math.sqrt(p * (1 - p) / n)
