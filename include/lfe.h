@@ -268,6 +268,11 @@ int lfe_restore(lfe_system* sys, const char* path);
 int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
                     const char** names, double* ms, int max_n);
 
+/* Set theta (wrapped into [0, 2)) and its momentum; lambda follows Eq. 3.
+ * For replicas held at a fixed lambda (lambda_mass <= 0) this sets lambda.
+ * Synchronises the device.  Errors: LFE_ERR_ARG (non-finite input). */
+int lfe_set_theta(lfe_system* sys, double theta, double p_theta);
+
 /* Autotuner: choose the evaluation's launch shapes for this system by
  * timing its captured evaluation graph (the five concurrent branches of the
  * step) on the device: blocks of the pair kernel per multiprocessor (1 up to
@@ -312,6 +317,25 @@ int lfe_alu_peak(double* fp32_tflops, double* fp64_tflops);
 int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out);
 int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms, void* stream);
 int lfe_batch_step(lfe_batch* b, int n_steps, void* stream);
+
+/* Lambda replica exchange (the paper's HREX reference protocol, Section 2.6,
+ * on the linear-basis potential of Eq. 4).  `ladder` lists n >= 2 replicas
+ * of the batch (indices) in increasing lambda; each must have a frozen theta
+ * (lambda_mass <= 0).  Every replica of the ladder is evaluated at its own
+ * lambda (positions as they stand), and the pairs (k, k+1) with k of the
+ * parity of `attempt` are tried: the swap changes the total energy by
+ * Delta = (h_A(l_k+1) - h_A(l_k)) (U_uv,k - U_uv,k+1)
+ *       + (h_B(l_k+1) - h_B(l_k)) (U_soft,k - U_soft,k+1)
+ * and is accepted when Delta <= 0 or u < exp(-Delta / k_B T), u = (x + 0.5)/2^32
+ * with x the first word of Philox4x32-10 at counter (k, attempt_lo,
+ * attempt_hi, 3) under key (seed_lo, seed_hi).  An accepted pair exchanges
+ * the two replicas' lambdas (theta set to the new lambda, p_theta 0) and
+ * its two ladder entries, so that `ladder` stays in lambda order.
+ * accepted[n-1] (may be NULL): 1 for each accepted pair.  Errors:
+ * LFE_ERR_ARG (ladder, temperature, dynamical theta), others from the
+ * evaluations. */
+int lfe_batch_exchange(lfe_batch* b, int n, int* ladder, double temperature, unsigned long long seed,
+                       unsigned long long attempt, int* accepted, void* stream);
 const char* lfe_batch_last_error(const lfe_batch* b);
 void lfe_batch_destroy(lfe_batch* b);
 

@@ -104,6 +104,8 @@ struct SystemBase {
     virtual void recover(cudaStream_t st) = 0;
     virtual cudaStream_t side_stream() = 0;
     virtual void autotune(int reps, const char* cache_path, double* best_ms, int* params) = 0;
+    virtual void set_theta(double theta, double p_theta) = 0;
+    virtual void lambda_state(double* lam, double* mass) = 0;
     unsigned generation = 0;   // bumped whenever device buffers are reallocated
 };
 
@@ -1230,6 +1232,33 @@ struct System final : SystemBase {
         if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 0; }
     }
 
+    // theta (wrapped into [0, 2)), its momentum, and the lambda of Eq. 3 with
+    // its switching functions
+    void set_theta(double theta, double p_theta) override
+    {
+        if (!std::isfinite(theta) || !std::isfinite(p_theta)) fail(LFE_ERR_ARG, "theta and p_theta must be finite");
+        CK(cudaDeviceSynchronize());
+        LamState L;
+        CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
+        double th = theta - 2.0 * std::floor(theta / 2.0);
+        if (!(th >= 0.0 && th < 2.0)) th = 0.0;
+        L.theta = th;
+        L.p_theta = p_theta;
+        L.dlam_dtheta = th <= 1.0 ? 1.0 : -1.0;
+        L.lambda = th <= 1.0 ? th : 2.0 - th;
+        switching_fns(L.lambda, L.hA, L.hB, L.dhA, L.dhB);
+        CK(cudaMemcpy(S.lam, &L, sizeof(L), cudaMemcpyHostToDevice));
+    }
+
+    void lambda_state(double* lam, double* mass) override
+    {
+        CK(cudaDeviceSynchronize());
+        LamState L;
+        CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
+        if (lam) *lam = L.lambda;
+        if (mass) *mass = T.m;
+    }
+
     cudaStream_t side_stream() override { return cs2; }
 
     void record_step(cudaStream_t s0) override
@@ -2089,6 +2118,26 @@ int lfe_autotune(lfe_system* sys, int reps, const char* cache_path, double* best
     return guard(sys, [&] { sys->impl->autotune(reps, cache_path, best_ms, params); });
 }
 
+int lfe_set_theta(lfe_system* sys, double theta, double p_theta)
+{
+    return guard(sys, [&] { sys->impl->set_theta(theta, p_theta); });
+}
+
+namespace {
+// Philox4x32-10 (Salmon et al. 2011) on the host, for the exchange uniforms
+void philox_host(unsigned c[4], unsigned k0, unsigned k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * c[0], p1 = 0xCD9E8D57ull * c[2];
+        const unsigned n0 = (unsigned)(p1 >> 32) ^ c[1] ^ k0, n1 = (unsigned)p1;
+        const unsigned n2 = (unsigned)(p0 >> 32) ^ c[3] ^ k1, n3 = (unsigned)p0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+}  // namespace
+
 int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out)
 {
     if (out) *out = nullptr;
@@ -2131,6 +2180,59 @@ int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms, vo
             b->err = "replica " + std::to_string(i) + ": " + b->sys[i]->err;
             return rc;
         }
+    }
+    return LFE_OK;
+}
+
+int lfe_batch_exchange(lfe_batch* b, int n, int* ladder, double temperature, unsigned long long seed,
+                       unsigned long long attempt, int* accepted, void* stream)
+{
+    if (!b || !ladder || n < 2 || !(temperature > 0) || !std::isfinite(temperature)) {
+        if (b) b->err = "lfe_batch_exchange: bad arguments (ladder of >= 2 replicas, temperature > 0)";
+        return LFE_ERR_ARG;
+    }
+    try {
+        std::vector<char> seen(b->sys.size(), 0);
+        std::vector<double> lam(n), uuv(n), us(n);
+        for (int k = 0; k < n; ++k) {
+            const int r = ladder[k];
+            if (r < 0 || r >= (int)b->sys.size() || seen[r]) fail(LFE_ERR_ARG, "ladder entries must be distinct replica indices");
+            seen[r] = 1;
+            double m = 0;
+            b->sys[r]->impl->lambda_state(&lam[k], &m);
+            if (m > 0) fail(LFE_ERR_ARG, "replica " + std::to_string(r) + " has a dynamical theta (lambda_mass > 0)");
+            if (k > 0 && !(lam[k] >= lam[k - 1])) fail(LFE_ERR_ARG, "ladder must list the replicas in lambda order");
+        }
+        // the basis energies of every configuration at its own lambda
+        for (int k = 0; k < n; ++k) {
+            double t[LFE_NTERMS];
+            b->sys[ladder[k]]->impl->eval(lam[k], nullptr, t, 0, (cudaStream_t)stream);
+            uuv[k] = t[4];
+            us[k] = t[5];
+        }
+        const double beta = 1.0 / (lfe::KB * temperature);
+        for (int k = 0; k + 1 < n; ++k)
+            if (accepted) accepted[k] = 0;
+        for (int k = (int)(attempt & 1ull); k + 1 < n; k += 2) {
+            double ha, hb, hA2, hB2, d0, d1;
+            lfe::switching_fns(lam[k], ha, hb, d0, d1);
+            lfe::switching_fns(lam[k + 1], hA2, hB2, d0, d1);
+            // Eq. 4 is linear in the basis energies: the swap changes the
+            // total energy by (dh_A)(U_uv,i - U_uv,j) + (dh_B)(U_soft,i - U_soft,j)
+            const double delta = (hA2 - ha) * (uuv[k] - uuv[k + 1]) + (hB2 - hb) * (us[k] - us[k + 1]);
+            unsigned c[4] = {(unsigned)k, (unsigned)(attempt & 0xffffffffull), (unsigned)(attempt >> 32), 3u};
+            philox_host(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+            const double u = (c[0] + 0.5) / 4294967296.0;
+            if (delta <= 0.0 || u < std::exp(-beta * delta)) {
+                b->sys[ladder[k]]->impl->set_theta(lam[k + 1], 0.0);
+                b->sys[ladder[k + 1]]->impl->set_theta(lam[k], 0.0);
+                std::swap(ladder[k], ladder[k + 1]);
+                if (accepted) accepted[k] = 1;
+            }
+        }
+    } catch (const Failure& e) {
+        b->err = e.msg;
+        return e.code;
     }
     return LFE_OK;
 }

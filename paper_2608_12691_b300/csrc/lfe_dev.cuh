@@ -106,7 +106,7 @@ __device__ __forceinline__ double warp_sum_d(double v)
 }
 
 // h_A, h_B and their lambda-derivatives (Eq. 7-10), FP64.
-__device__ __forceinline__ void switching_fns(double lam, double& hA, double& hB, double& dA, double& dB)
+__host__ __device__ __forceinline__ void switching_fns(double lam, double& hA, double& hB, double& dA, double& dB)
 {
     double x = (lam - 0.35) / 0.65;
     double s32 = 0.0, d32 = 0.0;

@@ -31,8 +31,8 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
-    "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_batch_exchange", "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
 
@@ -129,6 +129,11 @@ def load():
     lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
     lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
+    lib.lfe_set_theta.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    lib.lfe_set_theta.restype = ctypes.c_int
+    lib.lfe_batch_exchange.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_ulonglong,
+                                       ctypes.c_ulonglong, vp, vp]
+    lib.lfe_batch_exchange.restype = ctypes.c_int
     lib.lfe_alu_peak.argtypes = [vp, vp]
     lib.lfe_alu_peak.restype = ctypes.c_int
     lib.lfe_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_char_p, vp, vp]
@@ -405,6 +410,10 @@ class System:
                                                out.ctypes.data))
         return out
 
+    def set_theta(self, theta, p_theta=0.0):
+        """Set theta and its momentum (lambda follows Eq. 3; lfe_set_theta)."""
+        self._check(self._lib.lfe_set_theta(self.h, float(theta), float(p_theta)))
+
     def autotune(self, reps=20, cache_path=None):
         """Choose the evaluation's launch shapes by timing (lfe_autotune).
         Returns (median evaluation ms, {pair_blocks_per_sm, uv_blocks,
@@ -445,6 +454,15 @@ class Batch:
 
     def step(self, n, stream=None):
         self._check(self._lib.lfe_batch_step(self.h, int(n), _stream_ptr(stream)))
+
+    def exchange(self, ladder, temperature, seed, attempt, stream=None):
+        """One lambda-exchange attempt over `ladder` (replica indices in lambda
+        order; lfe_batch_exchange).  Returns (new ladder, accepted flags)."""
+        lad = np.ascontiguousarray(ladder, dtype=np.int32).copy()
+        acc = np.zeros(max(len(lad) - 1, 0), dtype=np.int32)
+        self._check(self._lib.lfe_batch_exchange(self.h, len(lad), lad.ctypes.data, float(temperature), int(seed),
+                                                 int(attempt), acc.ctypes.data, _stream_ptr(stream)))
+        return lad, acc
 
     def eval(self, lambdas):
         lam = np.ascontiguousarray(lambdas, dtype=np.float64)
