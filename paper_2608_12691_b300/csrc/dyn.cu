@@ -859,12 +859,10 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
 // than skin/2 from where the list was built; no rebuild once a rebuild has
 // overflowed (the steps after it are no-ops until the host regrows the list)
 template <typename real>
-__global__ void k_rebuild_cond(SysView<real> s, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h2,
-                               int two)
+__global__ void k_rebuild_cond(SysView<real> s, cudaGraphConditionalHandle h)
 {
     const int rb = s.flags[FL_REBUILD] && !(s.flags[FL_ERROR] & ERRB_OVERFLOW);
     cudaGraphSetConditional(h, rb ? 1u : 0u);
-    if (two) cudaGraphSetConditional(h2, rb ? 1u : 0u);
     if (rb) s.flags[FL_NREBUILD] += 1;
     s.flags[FL_REBUILD] = 0;
 }
@@ -872,16 +870,7 @@ __global__ void k_rebuild_cond(SysView<real> s, cudaGraphConditionalHandle h, cu
 template <typename real>
 void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st)
 {
-    k_rebuild_cond<real><<<1, 1, 0, st>>>(s, h, h, 0);
-}
-
-// one decision for two conditional nodes (the tile list and, in another
-// branch, the solute-solvent pair list)
-template <typename real>
-void launch_rebuild_cond2(const SysView<real>& s, cudaGraphConditionalHandle h, cudaGraphConditionalHandle h2,
-                          cudaStream_t st)
-{
-    k_rebuild_cond<real><<<1, 1, 0, st>>>(s, h, h2, 1);
+    k_rebuild_cond<real><<<1, 1, 0, st>>>(s, h);
 }
 
 template <typename real>
@@ -906,9 +895,7 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_dafed_force<real>(const SysView<real>&, const DafedView&, cudaStream_t);            \
     template void launch_dafed_step<real>(const SysView<real>&, const DafedView&, cudaStream_t);             \
     template void launch_dafed_probe<real>(const SysView<real>&, const DafedView&, double, double*, cudaStream_t); \
-    template void launch_rebuild_cond<real>(const SysView<real>&, cudaGraphConditionalHandle, cudaStream_t);    \
-    template void launch_rebuild_cond2<real>(const SysView<real>&, cudaGraphConditionalHandle,                  \
-                                             cudaGraphConditionalHandle, cudaStream_t);
+    template void launch_rebuild_cond<real>(const SysView<real>&, cudaGraphConditionalHandle, cudaStream_t);
 
 LFE_INST_DYN(float)
 LFE_INST_DYN(double)

@@ -977,10 +977,7 @@ struct System final : SystemBase {
 
     // Appends to the graph being captured on st a conditional node (handle h)
     // whose body rebuilds the neighbour list; st continues after it.
-    // part: BUILD_ALL the whole list, BUILD_TILES the tile list only,
-    // BUILD_UV the solute-solvent pair list made from it
-    enum { BUILD_ALL = 0, BUILD_TILES = 1, BUILD_UV = 2 };
-    void add_cond_build(cudaStream_t st, cudaGraphConditionalHandle h, int part = BUILD_ALL)
+    void add_cond_build(cudaStream_t st, cudaGraphConditionalHandle h)
     {
         cudaStreamCaptureStatus status;
         cudaGraph_t g = nullptr;
@@ -997,9 +994,7 @@ struct System final : SystemBase {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
         CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        if (part == BUILD_TILES) launch_build_tiles(S, N, cs2);
-        else if (part == BUILD_UV) launch_build_uv(S, N, cs2, false);
-        else launch_build_nbl(S, N, cs2);
+        launch_build_nbl(S, N, cs2);
         cudaGraph_t body_out = nullptr;
         CK(cudaStreamEndCapture(cs2, &body_out));
     }
@@ -1016,19 +1011,13 @@ struct System final : SystemBase {
     // and the solute-solvent energies read the list and the cluster-sorted
     // copy, so the PME, exclusion and bonded work runs beside the rebuild.
     void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr,
-                               const cudaGraphConditionalHandle* rebuild = nullptr,
-                               const cudaGraphConditionalHandle* rebuild_uv = nullptr)
+                               const cudaGraphConditionalHandle* rebuild = nullptr)
     {
         CK(cudaEventRecord(ev_fork, s0));
         for (int k = 0; k < NBR; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
-        // with a second handle the tile list is rebuilt here and the
-        // solute-solvent pair list in the uv branch, so the pair kernel does
-        // not wait for the latter
-        const bool split = rebuild && rebuild_uv && n_ucl > 0;
         if (rebuild) {
-            if (split) launch_rebuild_cond2(S, *rebuild, *rebuild_uv, br[0]);
-            else launch_rebuild_cond(S, *rebuild, br[0]);
-            add_cond_build(br[0], *rebuild, split ? BUILD_TILES : BUILD_ALL);
+            launch_rebuild_cond(S, *rebuild, br[0]);
+            add_cond_build(br[0], *rebuild);
         }
         CK(cudaEventRecord(ev_built, br[0]));
         if (pre) launch_prestep(S, G, *pre, br[3]);
@@ -1069,7 +1058,6 @@ struct System final : SystemBase {
         launch_bonded(S, B, br[3]);
         launch_dafed_force(S, D, br[3]);
         CK(cudaStreamWaitEvent(br[4], ev_built, 0));
-        if (split) add_cond_build(br[4], *rebuild_uv, BUILD_UV);
         launch_uv_energy(S, N, uv_blocks, br[4]);
         for (int k = 0; k < NBR; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
@@ -1314,10 +1302,9 @@ struct System final : SystemBase {
         cudaStreamCaptureStatus status;
         cudaGraph_t g = nullptr;
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
-        cudaGraphConditionalHandle h, h_uv;
+        cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        if (n_ucl > 0) CK(cudaGraphConditionalHandleCreate(&h_uv, g, 0, cudaGraphCondAssignDefault));
-        eval_kernels_branched(s0, &T, &h, n_ucl > 0 ? &h_uv : nullptr);
+        eval_kernels_branched(s0, &T, &h);
         // atoms and theta move concurrently; the step ends when both are done
         CK(cudaEventRecord(ev_fork, s0));
         CK(cudaStreamWaitEvent(br[0], ev_fork, 0));

@@ -236,10 +236,6 @@ inline void launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 }
 
 template <typename real> void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st);
-// the build in two parts: the tile list (everything the pair kernel reads)
-// and the dense solute-solvent pair list made from it
-template <typename real> void launch_build_tiles(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st);
-template <typename real> void launch_build_uv(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st, bool pdl);
 template <typename real> void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st);
 template <typename real> int pairs_blocks_per_sm();
 template <typename real> void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nblocks, cudaStream_t st);
@@ -286,8 +282,6 @@ template <typename real> void launch_dafed_probe(const SysView<real>& s, const D
 template <typename real> void launch_prestep(const SysView<real>& s, const StepView<real>& g,
                                              const ThetaView<real>& t, cudaStream_t st);
 template <typename real> void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st);
-template <typename real> void launch_rebuild_cond2(const SysView<real>& s, cudaGraphConditionalHandle h,
-                                                   cudaGraphConditionalHandle h2, cudaStream_t st);
 template <typename real> void launch_set_lambda(const SysView<real>& s, double lam, cudaStream_t st);
 template <typename real> void launch_eval_out(const SysView<real>& s, double* forces, double* terms,
                                               double const_vv, double const_uu, double const_uv,

@@ -730,9 +730,8 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
 
 // The build is a chain of kernels on one stream: every kernel after the
 // first is launched as a programmatic dependent of the one before it.
-// column sort, slot assignment, tile search, tile scan, placement + masks
 template <typename real>
-void launch_build_tiles(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st)
+void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st)
 {
     const int B = 256;
     bool pdl = false;   // the first kernel follows whatever preceded the build
@@ -751,26 +750,13 @@ void launch_build_tiles(const SysView<real>& s, const NblView<real>& nb, cudaStr
     const long long pq = ((long long)nb.stage_cap + 15) / 16;   // blocks of four warps x four tiles
     const long long pmax = (long long)nb.n_sm * PLACE_BLOCKS_PER_SM;
     launch_k(true, k_place<real>, (int)(pq < pmax ? pq : pmax), 128, 0, st, s, nb);
-}
-
-// the dense solute-solvent pair list from the placed tiles (count, scan,
-// write); pdl: the first kernel directly follows k_place in the stream
-template <typename real>
-void launch_build_uv(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st, bool pdl)
-{
-    if (s.n_ucl == 0) return;
-    const int ub = (nb.uv_tiles_max * 32 + 127) / 128;
-    launch_k(pdl, k_uv_pairs<real, 0>, ub, 128, 0, st, s, nb);
-    launch_k(true, k_scan_block<0>, 1, 1024, 0, st, nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV,
-             nb.uv_cap, s.flags + FL_ERROR, (int*)nullptr, (int*)nullptr);
-    launch_k(true, k_uv_pairs<real, 1>, ub, 128, 0, st, s, nb);
-}
-
-template <typename real>
-void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st)
-{
-    launch_build_tiles(s, nb, st);
-    launch_build_uv(s, nb, st, true);
+    if (s.n_ucl > 0) {
+        const int ub = (nb.uv_tiles_max * 32 + 127) / 128;
+        launch_k(true, k_uv_pairs<real, 0>, ub, 128, 0, st, s, nb);
+        launch_k(true, k_scan_block<0>, 1, 1024, 0, st, nb.uv_cnt, nb.uv_off, nb.uv_tiles_max, s.flags + FL_NUV,
+                 nb.uv_cap, s.flags + FL_ERROR, (int*)nullptr, (int*)nullptr);
+        launch_k(true, k_uv_pairs<real, 1>, ub, 128, 0, st, s, nb);
+    }
 }
 
 // ------------------------------------------------------------ pair kernel
@@ -1214,8 +1200,6 @@ void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t 
 
 #define LFE_INST(real)                                                                             \
     template void launch_build_nbl<real>(const SysView<real>&, const NblView<real>&, cudaStream_t); \
-    template void launch_build_tiles<real>(const SysView<real>&, const NblView<real>&, cudaStream_t); \
-    template void launch_build_uv<real>(const SysView<real>&, const NblView<real>&, cudaStream_t, bool); \
     template void launch_pairs<real>(const SysView<real>&, const NblView<real>&, int, cudaStream_t); \
     template int pairs_blocks_per_sm<real>();                                                          \
     template void launch_uv_energy<real>(const SysView<real>&, const NblView<real>&, int, cudaStream_t); \
