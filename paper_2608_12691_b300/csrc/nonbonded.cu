@@ -243,38 +243,6 @@ __global__ void k_assign(SysView<real> s, NblView<real> nb)
             const int cnt = min(nb.col_start[lo + 1] - nb.col_start[lo], COL_MAX);
             if (rank < cnt) a = nb.tmp2[nb.col_start[lo] + rank];
         }
-        // a full solvent cluster (the warp holds it, in z order): its four
-        // 8-slot sub-clusters become the quadrants of the cluster in (x, y),
-        // each in z order -- boxes of about 0.32 x 0.32 x 0.64 nm instead of
-        // 0.64 x 0.64 x 0.16 nm z-slabs, so fewer j atoms lie within
-        // r_cut + skin of a sub-cluster (the tiles' i side)
-        const unsigned FULL = 0xffffffffu;
-        const int lane = slot & 31;
-        if (__all_sync(FULL, a >= 0)) {
-            const R4<real> pa = s.x[a];
-            const float px = (float)wrap_box(pa.x, s.L[0], s.invL[0]);
-            const float py = (float)wrap_box(pa.y, s.L[1], s.invL[1]);
-            int rx = 0;
-            for (int m = 0; m < 32; ++m) {
-                const float xm = __shfl_sync(FULL, px, m);
-                rx += (xm < px) || (xm == px && m < lane);
-            }
-            const int half = rx >= 16 ? 1 : 0;
-            int ry = 0;
-            for (int m = 0; m < 32; ++m) {
-                const float ym = __shfl_sync(FULL, py, m);
-                const int hm = __shfl_sync(FULL, half, m);
-                ry += hm == half && ((ym < py) || (ym == py && m < lane));
-            }
-            const int q = 2 * half + (ry >= 8 ? 1 : 0);
-            unsigned bq[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) bq[k] = __ballot_sync(FULL, q == k);
-            const int myq = lane >> 3;
-            const unsigned mq = myq == 0 ? bq[0] : (myq == 1 ? bq[1] : (myq == 2 ? bq[2] : bq[3]));
-            const int src = (int)__fns(mq, 0, (lane & 7) + 1);
-            a = __shfl_sync(FULL, a, src);
-        }
     }
     s.perm[slot] = a;
     R4<real> o;
