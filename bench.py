@@ -16,6 +16,7 @@ import json
 
 import numpy as np
 import os
+import shutil
 import statistics
 import subprocess
 import sys
@@ -231,8 +232,11 @@ def batched_leg(args, stream, flush):
     t_gen = time.perf_counter() - t0
     reps = [lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=7000 + r, theta0=d["lam"]) for r, d in enumerate(dicts)]
     # systems of one kind share a tuning entry: the first of each kind is timed
-    cache = args.tune_cache or os.path.join(tempfile.mkdtemp(), "lfe_tune.json")
+    tmpdir = None if args.tune_cache else tempfile.mkdtemp()
+    cache = args.tune_cache or os.path.join(tmpdir, "lfe_tune.json")
     tuned = [g.autotune(reps=10, cache_path=cache)[1] for g in reps]
+    if tmpdir:
+        shutil.rmtree(tmpdir, ignore_errors=True)
     b = lfe.Batch(reps)
     for frac, fric in ((0.05, 100.0), (0.25, 50.0), (0.5, 20.0), (1.0, None)):
         for d, g in zip(dicts, reps):
