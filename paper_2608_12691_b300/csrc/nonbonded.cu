@@ -1002,6 +1002,157 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs(SysVie
     }
 }
 
+// The FP64 pair kernel.  One warp walks a contiguous chunk of the
+// (I8-sorted) tile list, one 8 x 32 tile at a time, in three phases per tile.  Lane l holds j entry l of the
+// tile; the 8 i atoms are broadcast from a per-warp shared-memory record.
+// (1) Every lane tests its j atom against the 8 i atoms (mask bit and
+// r < r_cut); the pairs in range are listed in shared memory, i atom by i
+// atom (ballot and prefix count), one byte (i, j) per pair.  (2) The list is
+// evaluated 32 pairs at a time, one pair per lane, so nearly every lane of
+// every round computes a pair in range (about 36 % of a tile's 256 slots are
+// in range); the j record comes from its owner lane by shuffles, and each
+// pair's force g (r_j - r_i) goes to a per-warp [3][8][32] shared matrix at
+// (i, j).  (3) Lane j adds its column: the j atom's force, and its share of
+// each i atom's force, which stays in registers over consecutive tiles of
+// the same I8 and is added over the warp when I8 changes.  No atomics except
+// the final fixed-point force and energy sums.  The tile's class (vv, uu or
+// uv) and shift are uniform, so the branches on them are warp-uniform.
+// Solute-solvent energies are not accumulated here (k_uv_energy forms them).
+// With B300's few FP64 units the pair arithmetic dominates, and listing the
+// pairs cuts it to the pairs in range (octanol box: 1.47 ms against 2.17 ms
+// for the lane-per-j-entry kernel); in FP32, where latency dominates, the
+// lane-per-j-entry kernel is faster (45.8 against 54.8 us) and is used.
+template <typename real>
+__global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs_listed(SysView<real> s, NblView<real> nb)
+{
+    __shared__ R4<real> sxq[4][8];        // [warp][i atom] x, y, z (shifted for the tile), sqrt(k_e) q
+    __shared__ R2<real> slj[4][8];        // [warp][i atom] sigma/2, 2 sqrt(eps)
+    __shared__ unsigned char slist[4][256];   // [warp][pair] (i << 5) | j of the pairs in range
+    __shared__ real sw[4][3][8][32];      // [warp][component][i][j] g (r_j - r_i) of each pair in range
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
+    const unsigned lt = (1u << lane) - 1u;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    int ntiles = s.flags[FL_NTILES];
+    if (ntiles > nb.cap) ntiles = nb.cap;
+    const int t0 = (int)(((long long)ntiles * warp) / nwarp);
+    const int t1 = (int)(((long long)ntiles * (warp + 1)) / nwarp);
+    if (t0 >= t1) return;
+    const PairConst<real> c = pair_const(s);
+    int curI = -1;
+    R4<real> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
+    real fx[8], fy[8], fz[8];
+    real evv = 0, euu = 0;
+    int npairs = 0;
+    // the next tile's records are loaded while the current one is computed
+    int4 tl_n = nb.tiles[t0];
+    unsigned mk_n = nb.masks[(size_t)t0 * 32 + lane];
+    int sj_n = nb.jidx[(size_t)t0 * 32 + lane];
+    R4<real> pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
+    R2<real> lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
+    for (int t = t0; t < t1; ++t) {
+        const int4 tl = tl_n;
+        const unsigned mc = mk_n;
+        const int slot_j = sj_n;
+        R4<real> pj = pj_n;
+        const R2<real> ljv = lj_n;
+        if (t + 1 < t1) {
+            tl_n = nb.tiles[t + 1];
+            mk_n = nb.masks[(size_t)(t + 1) * 32 + lane];
+            sj_n = nb.jidx[(size_t)(t + 1) * 32 + lane];
+            pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
+            lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
+        }
+        if (tl.x != curI) {
+            if (curI >= 0) flush_i8(s, curI, fx, fy, fz);
+            curI = tl.x;
+            if (lane < 8) {
+                pown = s.xq[curI * 8 + lane];
+                slj[wl][lane] = s.lj[curI * 8 + lane];
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) fx[k] = fy[k] = fz[k] = 0;
+        }
+        const int sh = tl.y;
+        const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
+        // shift the far-side atom down by L so that the subtraction below is
+        // the only rounding in the pair vector
+        if (lane < 8)
+            sxq[wl][lane] = R4<real>{sx == 1 ? pown.x - s.L[0] : pown.x, sy == 1 ? pown.y - s.L[1] : pown.y,
+                                     sz == 1 ? pown.z - s.L[2] : pown.z, pown.w};
+        if (sx == -1) pj.x -= s.L[0];
+        if (sy == -1) pj.y -= s.L[1];
+        if (sz == -1) pj.z -= s.L[2];
+        __syncwarp();
+        // (1) list the pairs in range
+        unsigned vb = 0u;
+        int np = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const R4<real> pi = sxq[wl][k];
+            const real dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const real r2 = dx * dx + dy * dy + dz * dz;
+            const bool in = ((mc >> k) & 1u) && r2 < c.rc2;
+            const unsigned bal = __ballot_sync(FULL, in);
+            if (in) slist[wl][np + __popc(bal & lt)] = (unsigned char)((k << 5) | lane);
+            vb |= (in ? 1u : 0u) << k;
+            np += __popc(bal);
+        }
+        __syncwarp();
+        // (2) one pair per lane
+        const bool uv = tl.z == 2;
+        real e0 = 0;
+        for (int r0 = 0; r0 < np; r0 += 32) {
+            const int idx = r0 + lane;
+            const bool act = idx < np;
+            const int code = act ? (int)slist[wl][idx] : 0;
+            const int k = code >> 5, j = code & 31;
+            const real xj = __shfl_sync(FULL, pj.x, j), yj = __shfl_sync(FULL, pj.y, j);
+            const real zj = __shfl_sync(FULL, pj.z, j), qj = __shfl_sync(FULL, pj.w, j);
+            const real sj = __shfl_sync(FULL, ljv.x, j), ej = __shfl_sync(FULL, ljv.y, j);
+            if (act) {
+                const R4<real> pi = sxq[wl][k];
+                const R2<real> li = slj[wl][k];
+                const real dx = xj - pi.x, dy = yj - pi.y, dz = zj - pi.z;
+                const real r2 = dx * dx + dy * dy + dz * dz;
+                real ec, v;
+                const real g = pair_force(r2, pi.w * qj, li.x + sj, li.y * ej, uv, c, ec, v);
+                sw[wl][0][k][j] = g * dx;
+                sw[wl][1][k][j] = g * dy;
+                sw[wl][2][k][j] = g * dz;
+                e0 += ec + v;
+                ++npairs;
+            }
+        }
+        __syncwarp();
+        // (3) the column of lane j: its j force and its shares of the i forces
+        real fjx = 0, fjy = 0, fjz = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if ((vb >> k) & 1u) {
+                const real wx = sw[wl][0][k][lane], wy = sw[wl][1][k][lane], wz = sw[wl][2][k][lane];
+                fjx += wx; fjy += wy; fjz += wz;
+                fx[k] -= wx; fy[k] -= wy; fz[k] -= wz;
+            }
+        }
+        __syncwarp();
+        if (slot_j >= 0)
+            flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
+        if (tl.z == 0) evv += e0;
+        else if (tl.z == 1) euu += e0;
+    }
+    flush_i8(s, curI, fx, fy, fz);
+    const long long a0 = __double2ll_rn(warp_sum_d((double)evv) * ESCALE);
+    const long long a1 = __double2ll_rn(warp_sum_d((double)euu) * ESCALE);
+    const long long a4 = warp_sum_ll((long long)npairs);
+    if (lane == 0) {
+        if (a0) atomic_add_ll(&s.E[E_PAIR_VV], a0);
+        if (a1) atomic_add_ll(&s.E[E_PAIR_UU], a1);
+        atomic_add_ll(&s.E[E_NPAIRS], a4);
+    }
+}
+
 // Solute-solvent basis energies U_uv (real-space part) and U_soft in FP64
 // over the dense solute-solvent pair list.  They set dU/dlambda = h_A' U_uv +
 // h_B' U_soft, whose tolerance (1e-6 relative) is below what FP32 pair
@@ -1069,7 +1220,10 @@ template <typename real>
 int pairs_blocks_per_sm()
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs<real>, 128, 0) != cudaSuccess || nb < 1) nb = 1;
+    cudaError_t e;
+    if constexpr (sizeof(real) == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs_listed<real>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs<real>, 128, 0);
+    if (e != cudaSuccess || nb < 1) nb = 1;
     return nb;
 }
 
@@ -1078,7 +1232,8 @@ void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, c
 {
     const int B = 128;
     int blocks = (nwarps * 32 + B - 1) / B;
-    k_pairs<real><<<blocks, B, 0, st>>>(s, nb);
+    if constexpr (sizeof(real) == 8) k_pairs_listed<real><<<blocks, B, 0, st>>>(s, nb);
+    else k_pairs<real><<<blocks, B, 0, st>>>(s, nb);
 }
 
 // ------------------------------------------------- exclusions and 1-4 pairs
