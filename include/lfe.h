@@ -275,7 +275,8 @@ int lfe_set_theta(lfe_system* sys, double theta, double p_theta);
 
 /* Autotuner: choose the evaluation's launch shapes for this system by
  * timing its captured evaluation graph (the five concurrent branches of the
- * step) on the device: blocks of the pair kernel per multiprocessor (1 up to
+ * step; the expected time of a step with a list rebuild one step in four,
+ * from the graph timed with and without a preceding rebuild) on the device: blocks of the pair kernel per multiprocessor (1 up to
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
  * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
  * passes (4 or 16), one knob at a time, each candidate replayed `reps`

@@ -1011,13 +1011,15 @@ struct System final : SystemBase {
     // and the solute-solvent energies read the list and the cluster-sorted
     // copy, so the PME, exclusion and bonded work runs beside the rebuild.
     void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr,
-                               const cudaGraphConditionalHandle* rebuild = nullptr)
+                               const cudaGraphConditionalHandle* rebuild = nullptr, bool build_first = false)
     {
         CK(cudaEventRecord(ev_fork, s0));
         for (int k = 0; k < NBR; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
         if (rebuild) {
             launch_rebuild_cond(S, *rebuild, br[0]);
             add_cond_build(br[0], *rebuild);
+        } else if (build_first) {
+            launch_build_nbl(S, N, br[0]);   // an unconditional rebuild (autotuner)
         }
         CK(cudaEventRecord(ev_built, br[0]));
         if (pre) launch_prestep(S, G, *pre, br[3]);
@@ -1067,8 +1069,9 @@ struct System final : SystemBase {
 
     // ------------------------------------------------------- autotuner
     // Launch shapes of the evaluation, chosen by timing the captured
-    // evaluation graph (its five concurrent branches, as in the step) for
-    // each candidate: blocks of the pair kernel per multiprocessor, blocks
+    // evaluation graph (its five concurrent branches, as in the step; with
+    // and without a preceding list rebuild, weighted 1:3) for each
+    // candidate: blocks of the pair kernel per multiprocessor, blocks
     // of the FP64 solute-solvent energy kernel, lines per block of the df64
     // transform passes.  One knob at a time (coordinate descent), each
     // candidate replayed `reps` times after three untimed replays; the
@@ -1150,12 +1153,12 @@ struct System final : SystemBase {
         ++generation;   // batches that hold this system's step recapture it
     }
 
-    double time_eval_graph(int reps)
+    double time_eval_graph(int reps, bool with_build)
     {
         cudaGraph_t g = nullptr;
         cudaGraphExec_t e = nullptr;
         CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        eval_kernels_branched(cs);
+        eval_kernels_branched(cs, nullptr, nullptr, with_build);
         CK(cudaStreamEndCapture(cs, &g));
         CK(cudaGraphInstantiate(&e, g, 0));
         for (int r = 0; r < 3; ++r) CK(cudaGraphLaunch(e, cs));
@@ -1195,9 +1198,14 @@ struct System final : SystemBase {
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, cs));
         const int bmax = pairs_blocks_per_sm<real>();
+        // the expected evaluation time of a step: a quarter of the steps start
+        // with a list rebuild (the pair kernel then waits for it), the rest
+        // do not
+        constexpr double REBUILD_FRACTION = 0.25;
         auto measure = [&](const int* c) {
             apply_tuning(c);
-            return time_eval_graph(reps);
+            return (1.0 - REBUILD_FRACTION) * time_eval_graph(reps, false) +
+                   REBUILD_FRACTION * time_eval_graph(reps, true);
         };
         best = measure(v);
         for (int b = 1; b <= bmax; ++b) {
