@@ -12,7 +12,6 @@
 // into one complex grid for the single inverse transform.
 #include "lfe_views.cuh"
 #include "pme_dev.cuh"
-#include <climits>
 #include <type_traits>
 
 namespace lfe {
@@ -23,25 +22,14 @@ namespace lfe {
 // products are formed in the same order as by one lane per atom.  Weights
 // and products in FP64: the fixed-point grid is shared by the force branch
 // and the df64 energy branch, whose class energies set dU/dlambda to 1e-6
-// relative.  A block holds 32 consecutive atoms (molecules are contiguous in
-// the caller's order, so their stencils overlap): when the block's points
-// fit in SPREAD_LOCAL grid points (in unwrapped grid indices, so a block
-// that straddles a periodic face does not), they are first added in shared
-// memory and then flushed with one global atomic per touched point and
-// grid; otherwise every point goes straight to the global grids.  Integer
-// sums: the result is the same either way.
-constexpr int SPREAD_LOCAL = 2048;
-
+// relative.
 template <typename real>
-__global__ void __launch_bounds__(128) k_spread(SysView<real> s, PmeView<real> p)
+__global__ void k_spread(SysView<real> s, PmeView<real> p)
 {
-    __shared__ long long acc[2][SPREAD_LOCAL];   // [solvent, solute][local point]
-    __shared__ int sbox[4][6];                   // [warp] min f - 3 and max f per dimension
     const unsigned FULL = 0xffffffffu;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int atom = tid >> 2, sub = tid & 3;
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int lb = lane & ~3;
+    const int lb = (threadIdx.x & 31) & ~3;
     int a = -1;
     real q = 0;
     R4<real> xq;
@@ -68,72 +56,21 @@ __global__ void __launch_bounds__(128) k_spread(SysView<real> s, PmeView<real> p
         t2[k] = __shfl_sync(FULL, th[k], lb + 2);
     }
     const int f0 = __shfl_sync(FULL, f, lb), f1 = __shfl_sync(FULL, f, lb + 1), f2 = __shfl_sync(FULL, f, lb + 2);
-    const bool live = a >= 0 && q != (real)0;
-    // the block's box in unwrapped grid indices: [min f - 3, max f] per dimension
-    int bx[6] = {live ? f0 - 3 : INT_MAX, live ? f1 - 3 : INT_MAX, live ? f2 - 3 : INT_MAX,
-                 live ? f0 : INT_MIN, live ? f1 : INT_MIN, live ? f2 : INT_MIN};
+    if (a < 0 || q == (real)0) return;
+    long long* grid = p.Qfix + (s.sol[a] ? p.KK : 0);
+    const double th0 = sub == 0 ? t0[0] : (sub == 1 ? t0[1] : (sub == 2 ? t0[2] : t0[3]));
+    const int k0 = wrapk(f0 - sub, p.K[0]);
+    const double a0 = (double)q * th0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int j1 = 0; j1 < 4; ++j1) {
+        const int k1 = wrapk(f1 - j1, p.K[1]);
+        const double a1 = a0 * t1[j1];
+        const int row = (k0 * p.K[1] + k1) * p.K[2];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            bx[d] = min(bx[d], __shfl_xor_sync(FULL, bx[d], o));
-            bx[3 + d] = max(bx[3 + d], __shfl_xor_sync(FULL, bx[3 + d], o));
+        for (int j2 = 0; j2 < 4; ++j2) {
+            const int k2 = wrapk(f2 - j2, p.K[2]);
+            atomic_add_ll(&grid[row + k2], __double2ll_rn(a1 * t2[j2] * QSCALE));
         }
-    if (lane == 0)
-        for (int d = 0; d < 6; ++d) sbox[wl][d] = bx[d];
-    __syncthreads();
-    int lo[3], e[3];
-    bool any = true;
-    long long vol = 1;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int l = sbox[0][d], h = sbox[0][3 + d];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-            l = min(l, sbox[w][d]);
-            h = max(h, sbox[w][3 + d]);
-        }
-        lo[d] = l;
-        e[d] = h - l + 1;
-        if (h < l) any = false;
-        vol *= (long long)max(e[d], 0);
-    }
-    if (!any) return;   // block-uniform: no atom of the block spreads
-    const bool local = vol <= SPREAD_LOCAL;
-    if (local) {
-        for (int i = threadIdx.x; i < 2 * (int)vol; i += blockDim.x) acc[i / (int)vol][i % (int)vol] = 0;
-        __syncthreads();
-    }
-    if (live) {
-        const int g = s.sol[a] ? 1 : 0;
-        long long* grid = p.Qfix + (g ? p.KK : 0);
-        const double th0 = sub == 0 ? t0[0] : (sub == 1 ? t0[1] : (sub == 2 ? t0[2] : t0[3]));
-        const int u0 = f0 - sub;
-        const double a0 = (double)q * th0;
-#pragma unroll
-        for (int j1 = 0; j1 < 4; ++j1) {
-            const int u1 = f1 - j1;
-            const double a1 = a0 * t1[j1];
-            const int row = (wrapk(u0, p.K[0]) * p.K[1] + wrapk(u1, p.K[1])) * p.K[2];
-            const int lrow = ((u0 - lo[0]) * e[1] + (u1 - lo[1])) * e[2];
-#pragma unroll
-            for (int j2 = 0; j2 < 4; ++j2) {
-                const int u2 = f2 - j2;
-                const long long v = __double2ll_rn(a1 * t2[j2] * QSCALE);
-                if (local) atomicAdd(reinterpret_cast<unsigned long long*>(&acc[g][lrow + (u2 - lo[2])]),
-                                     static_cast<unsigned long long>(v));
-                else atomic_add_ll(&grid[row + wrapk(u2, p.K[2])], v);
-            }
-        }
-    }
-    if (!local) return;
-    __syncthreads();
-    for (int i = threadIdx.x; i < (int)vol; i += blockDim.x) {
-        const int l2 = i % e[2], l1 = (i / e[2]) % e[1], l0 = i / (e[1] * e[2]);
-        const int k = (wrapk(lo[0] + l0, p.K[0]) * p.K[1] + wrapk(lo[1] + l1, p.K[1])) * p.K[2] +
-                      wrapk(lo[2] + l2, p.K[2]);
-        const long long v0 = acc[0][i], v1 = acc[1][i];
-        if (v0) atomic_add_ll(&p.Qfix[k], v0);
-        if (v1) atomic_add_ll(&p.Qfix[p.KK + k], v1);
     }
 }
 
