@@ -199,8 +199,8 @@ def dafed_leg(args, stream, flush):
              opes_dE_std=30.0 * 4.184, opes_dE_exp=5.0 * 4.184, opes_sigma=0.10)
     g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242)
     g.set_dafed(S.DIPEPTIDE_CVS, 1000.0, 50.0, temperature=1000.0, friction=25.0)
-    g.autotune(reps=20)
     equilibrate(g, d, stream)
+    g.autotune(reps=20)
     g.step(20, stream)
     torch.cuda.synchronize()
     k = max(20, min(200, args.steps))
@@ -231,18 +231,18 @@ def batched_leg(args, stream, flush):
         dicts.append(d)
     t_gen = time.perf_counter() - t0
     reps = [lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=7000 + r, theta0=d["lam"]) for r, d in enumerate(dicts)]
-    # systems of one kind share a tuning entry: the first of each kind is timed
-    tmpdir = None if args.tune_cache else tempfile.mkdtemp()
-    cache = args.tune_cache or os.path.join(tmpdir, "lfe_tune.json")
-    tuned = [g.autotune(reps=10, cache_path=cache)[1] for g in reps]
-    if tmpdir:
-        shutil.rmtree(tmpdir, ignore_errors=True)
     b = lfe.Batch(reps)
     for frac, fric in ((0.05, 100.0), (0.25, 50.0), (0.5, 20.0), (1.0, None)):
         for d, g in zip(dicts, reps):
             g.set_integrator(float(d["dt"]) * frac, fric if fric else float(d["friction"]), float(d["temperature"]))
         b.step(200 if fric else args.warmup, stream)
     torch.cuda.synchronize()
+    # systems of one kind share a tuning entry: the first of each kind is timed
+    tmpdir = None if args.tune_cache else tempfile.mkdtemp()
+    cache = args.tune_cache or os.path.join(tmpdir, "lfe_tune.json")
+    tuned = [g.autotune(reps=20, cache_path=cache)[1] for g in reps]
+    if tmpdir:
+        shutil.rmtree(tmpdir, ignore_errors=True)
     for g in reps:
         g.get_state()
     K = args.batch_steps
@@ -330,13 +330,15 @@ def run_ours(args):
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     dt_ps = float(d["dt"])
     g = lfe.System(d, precision=prec, seed=2608 + rank)
-    tune_ms, tune = (None, None) if args.no_autotune else g.autotune(reps=20, cache_path=args.tune_cache)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     equilibrate(g, d, stream)
+    # launch shapes chosen on the equilibrated system (the tuner steps it
+    # from a saved state and restores it)
+    tune_ms, tune = (None, None) if args.no_autotune else g.autotune(reps=40, cache_path=args.tune_cache)
     g.step(args.warmup, stream)
     torch.cuda.synchronize()
     _, _, ext0 = g.get_state()

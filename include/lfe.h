@@ -274,21 +274,25 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
 int lfe_set_theta(lfe_system* sys, double theta, double p_theta);
 
 /* Autotuner: choose the evaluation's launch shapes for this system by
- * timing its captured evaluation graph (the five concurrent branches of the
- * step; the expected time of a step with a list rebuild one step in four,
- * from the graph timed with and without a preceding rebuild) on the device: blocks of the pair kernel per multiprocessor (1 up to
+ * timing it on the device: when the system steps (dt > 0), the mean time
+ * of `reps` captured steps from a saved state (a temporary checkpoint file
+ * in /tmp, restored before every candidate and at the end); otherwise, or
+ * when the trial steps fail, its captured evaluation graph (the five
+ * concurrent branches of the step, timed with and without a preceding list
+ * rebuild, weighted 1:3).  Knobs: blocks of the pair kernel per multiprocessor (1 up to
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
  * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
- * passes (4 or 16), one knob at a time, each candidate replayed `reps`
- * (1..10000) times, the median deciding (a candidate must be 2 % faster than
- * the current choice to replace it).  The replays leave the state
+ * passes (4 or 16), one knob at a time, `reps` (1..10000) steps or graph
+ * replays per candidate (mean step time, or the median replay), a candidate
+ * replacing the current choice only when 2 % faster.  The replays leave the state
  * (positions, velocities, theta, counters, accumulators) as it was; the next
- * lfe_step recaptures its graph with the chosen shapes.  Launch shapes change
+ * lfe_step recaptures its graph with the chosen shapes.  Call it on an
+ * equilibrated system (the stepped objective needs stable dynamics).  Launch shapes change
  * only how work is split over blocks and warps, so results stay within the
  * precision mode's tolerance (summation order).  cache_path (or NULL): a JSON
  * file of tuned entries keyed on the device, atom counts, density, cutoff,
  * grid and precision; a matching entry is applied without timing, a new one
- * is added.  Outputs (each may be NULL): best_ms = median evaluation time of
+ * is added.  Outputs (each may be NULL): best_ms = the objective (ms) of
  * the choice; params[4] = (pair blocks per SM, uv energy blocks, df64 lines,
  * 1 if taken from the cache else 0).  Errors: LFE_ERR_ARG (reps out of range,
  * cache not writable), LFE_ERR_CUDA.  Not part of the paper's method: it

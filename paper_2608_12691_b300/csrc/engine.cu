@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <unistd.h>
 #include <memory>
 #include <string>
 #include <vector>
@@ -1198,12 +1199,61 @@ struct System final : SystemBase {
         CK(cudaDeviceSynchronize());
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, cs));
         const int bmax = pairs_blocks_per_sm<real>();
+        // Step-based objective when the system steps: the mean time of `reps`
+        // captured steps (with the rebuilds the dynamics needs) from a saved
+        // state that is restored before every candidate and at the end.  It
+        // falls back to the evaluation graph when the state cannot be saved
+        // or the trial steps fail (e.g. a packed start that needs its
+        // equilibration first).
+        std::string ck;
+        int nreb0 = 0;
+        bool by_steps = P.dt > 0;
+        if (by_steps) {
+            char tmpl[] = "/tmp/lfe_tune_XXXXXX";
+            const int fd = mkstemp(tmpl);
+            if (fd < 0) {
+                by_steps = false;
+            } else {
+                close(fd);
+                ck = tmpl;
+            }
+        }
+        auto time_steps_from_saved = [&]() -> double {
+            restore(ck.c_str());
+            step(3, cs);
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventRecord(e0, cs));
+            step(reps, cs);
+            CK(cudaEventRecord(e1, cs));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            recover_overflow(cs);
+            check_flags(cs);
+            return ms / reps;
+        };
+        if (by_steps) {
+            CK(cudaMemcpy(&nreb0, S.flags + FL_NREBUILD, sizeof(int), cudaMemcpyDeviceToHost));
+            checkpoint(ck.c_str());
+            try {
+                apply_tuning(v);
+                time_steps_from_saved();
+            } catch (const Failure&) {
+                by_steps = false;
+                restore(ck.c_str());
+            }
+        }
         // the expected evaluation time of a step: a quarter of the steps start
         // with a list rebuild (the pair kernel then waits for it), the rest
         // do not
         constexpr double REBUILD_FRACTION = 0.25;
         auto measure = [&](const int* c) {
             apply_tuning(c);
+            if (by_steps) return time_steps_from_saved();
             return (1.0 - REBUILD_FRACTION) * time_eval_graph(reps, false) +
                    REBUILD_FRACTION * time_eval_graph(reps, true);
         };
@@ -1228,6 +1278,12 @@ struct System final : SystemBase {
             if (t < 0.98 * best) { best = t; v[2] = c[2]; }
         }
         apply_tuning(v);
+        if (by_steps) {
+            // back to the saved state (the counters of rebuilds as before)
+            restore(ck.c_str());
+            CK(cudaMemcpy(S.flags + FL_NREBUILD, &nreb0, sizeof(int), cudaMemcpyHostToDevice));
+        }
+        if (!ck.empty()) unlink(ck.c_str());
         // the replays only accumulated forces and energies: clear them
         CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, cs));
         CK(cudaMemsetAsync(S.F, 0, sizeof(long long) * 3 * (size_t)n_pad, cs));
