@@ -56,7 +56,7 @@ def parse():
                    help="JSON autotuner cache shared by every system of the run (default: none for the main "
                         "system, a temporary one for the batched replicas)")
     p.add_argument("--no-autotune", action="store_true",
-                   help="keep the default launch shapes (e.g. for a per-kernel launch list)")
+                   help="keep the default launch shapes in every leg (e.g. for a per-kernel launch list)")
     p.add_argument("--batch-replicas", type=int, default=32,
                    help="replicas in the batched leg (half water, half octanol; 0 skips it)")
     p.add_argument("--batch-steps", type=int, default=40)
@@ -200,7 +200,8 @@ def dafed_leg(args, stream, flush):
     g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242)
     g.set_dafed(S.DIPEPTIDE_CVS, 1000.0, 50.0, temperature=1000.0, friction=25.0)
     equilibrate(g, d, stream)
-    g.autotune(reps=20)
+    if not args.no_autotune:
+        g.autotune(reps=20)
     g.step(20, stream)
     torch.cuda.synchronize()
     k = max(20, min(200, args.steps))
@@ -240,7 +241,7 @@ def batched_leg(args, stream, flush):
     # systems of one kind share a tuning entry: the first of each kind is timed
     tmpdir = None if args.tune_cache else tempfile.mkdtemp()
     cache = args.tune_cache or os.path.join(tmpdir, "lfe_tune.json")
-    tuned = [g.autotune(reps=20, cache_path=cache)[1] for g in reps]
+    tuned = [] if args.no_autotune else [g.autotune(reps=20, cache_path=cache)[1] for g in reps]
     if tmpdir:
         shutil.rmtree(tmpdir, ignore_errors=True)
     for g in reps:
