@@ -16,7 +16,6 @@ import json
 
 import numpy as np
 import os
-import shutil
 import statistics
 import subprocess
 import sys
