@@ -481,6 +481,10 @@ __global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long l
     __syncthreads();
     R2<real>* r = smem_fft<real, false>(a, b, nc, K0, LD, 1, p.rad[0], p.nrad[0], twf, +1);
     double evv = 0, euu = 0, euv = 0;
+    // df64: the energy products and their per-thread sums stay in df64 (FP32
+    // pipes); one conversion to double per thread at the end
+    real evv2 = (real)0, euu2 = (real)0, euv2 = (real)0;
+    constexpr bool DF = std::is_same<real, df64>::value;
     const real hA = MODE != CONV_ENERGY ? (real)lam->hA : (real)0;
     for (int e = threadIdx.x; e < nc * K0; e += blockDim.x) {
         const int c = e / K0, k0 = e - c * K0;
@@ -509,10 +513,17 @@ __global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long l
         const real G = p.conv_pre * p.gfac[0][k0] * p.gfac[1][k1] * p.gfac[2][k2] / msq;
         const bool self = (c == pc && k0 == n0);
         if (MODE != CONV_POTENTIAL) {
-            const double mult = self ? 1.0 : 2.0;
-            evv += mult * 0.5 * (double)G * ((double)qv.x * (double)qv.x + (double)qv.y * (double)qv.y);
-            euu += mult * 0.5 * (double)G * ((double)qu.x * (double)qu.x + (double)qu.y * (double)qu.y);
-            euv += mult * (double)G * ((double)qu.x * (double)qv.x + (double)qu.y * (double)qv.y);
+            if constexpr (DF) {
+                const real g = self ? G * (real)0.5 : G;   // halving or doubling by 2 is exact
+                evv2 += g * (qv.x * qv.x + qv.y * qv.y);
+                euu2 += g * (qu.x * qu.x + qu.y * qu.y);
+                euv2 += (g + g) * (qu.x * qv.x + qu.y * qv.y);
+            } else {
+                const double mult = self ? 1.0 : 2.0;
+                evv += mult * 0.5 * (double)G * ((double)qv.x * (double)qv.x + (double)qv.y * (double)qv.y);
+                euu += mult * 0.5 * (double)G * ((double)qu.x * (double)qu.x + (double)qu.y * (double)qu.y);
+                euv += mult * (double)G * ((double)qu.x * (double)qv.x + (double)qu.y * (double)qv.y);
+            }
         }
         if (MODE != CONV_ENERGY) {
             // W = G [(Q_v + h_A Q_u) + i (Q_u + h_A Q_v)]; at -m the class
@@ -528,6 +539,11 @@ __global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long l
     }
     if (MODE != CONV_POTENTIAL) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if constexpr (DF) {
+            evv = (double)evv2;
+            euu = (double)euu2;
+            euv = (double)euv2;
+        }
         const double v0 = warp_sum_d(evv), v1 = warp_sum_d(euu), v2 = warp_sum_d(euv);
         if (lane == 0) { red[0][warp] = v0; red[1][warp] = v1; red[2][warp] = v2; }
         __syncthreads();
