@@ -217,8 +217,9 @@ def dafed_leg(args, stream, flush):
 def batched_leg(args, stream, flush):
     """Replicas at lambda_r = r/(R-1), alternately the water system (12,020
     atoms, 2 fs) and the octanol system (13,520 atoms, 1 fs): mixed precision
-    advanced together (one graph launch per step) versus the same replicas in
-    FP64 advanced one after another with their own graphs."""
+    advanced together (one graph launch per step), the same replicas one after
+    another with their own graphs, and both forms again in FP64 from the same
+    states."""
     import torch
     from paper_2608_12691_b300 import lfe
     from paper_2608_12691_b300 import systems as S
@@ -253,19 +254,31 @@ def batched_leg(args, stream, flush):
     ms_step = sum(ms) / K
     ns_day = sum(float(d["dt"]) for d in dicts) * 1e-3 * 86400.0 / (ms_step * 1e-3)
     pairs = sum(g.eval(d["lam"])[0]["n_pairs"] for g, d in zip(reps, dicts))
-    # FP64, one replica after another
+    dt_sum = sum(float(d["dt"]) for d in dicts)
+    # mixed precision, one replica after another (each with its own graph)
+    kmix = max(3, K // 8)
+    tmix = sum(sum(time_steps(g, kmix, stream, flush)) / kmix for g in reps)
+    # FP64 from the same states: one replica after another, then batched
     k64 = max(3, K // 8)
     t64 = 0.0
+    reps64 = []
     for d, g in zip(dicts, reps):
         p, v, _ = g.get_state()
-        g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=1)
+        g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=1, theta0=d["lam"])
         g64.set_positions(p)
         g64.set_velocities(v)
         g64.step(2, stream)
         torch.cuda.synchronize()
         t64 += sum(time_steps(g64, k64, stream, flush)) / k64
+        reps64.append(g64)
+    b64 = lfe.Batch(reps64)
+    b64.step(2, stream)
+    torch.cuda.synchronize()
+    t64b = sum(time_steps(b64, k64, stream, flush)) / k64
+    b64.close()
+    for g64 in reps64:
         g64.close()
-    ns_day64 = sum(float(d["dt"]) for d in dicts) * 1e-3 * 86400.0 / (t64 * 1e-3)
+    ns_day64 = dt_sum * 1e-3 * 86400.0 / (t64 * 1e-3)
     b.close()
     for g in reps:
         g.close()
@@ -275,6 +288,10 @@ def batched_leg(args, stream, flush):
                               "pair_interactions_per_s": pairs / (ms_step * 1e-3), "steps": K},
             "fp64_per_replica": {"ms_per_step_all_replicas": t64, "ns_per_day_x_replica": ns_day64,
                                  "steps": k64},
+            "mixed_per_replica": {"ms_per_step_all_replicas": tmix,
+                                  "ns_per_day_x_replica": dt_sum * 1e-3 * 86400.0 / (tmix * 1e-3), "steps": kmix},
+            "fp64_batched": {"ms_per_step": t64b, "ns_per_day_x_replica": dt_sum * 1e-3 * 86400.0 / (t64b * 1e-3),
+                             "steps": k64},
             "speedup_mixed_batched_vs_fp64_per_replica": ns_day / ns_day64,
             "setup_s": t_gen}
 
