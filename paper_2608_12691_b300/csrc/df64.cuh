@@ -15,6 +15,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 namespace lfe {
 
 struct df64 {
@@ -32,34 +34,81 @@ struct df64 {
     }
 };
 
-__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e)
+// correctly rounded float operations, never contracted into FMAs (the
+// host versions serve the host-side check of these algorithms)
+__host__ __device__ __forceinline__ float df_add(float a, float b)
 {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    volatile float r = a + b;
+    return r;
+#endif
+}
+__host__ __device__ __forceinline__ float df_sub(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    volatile float r = a - b;
+    return r;
+#endif
+}
+__host__ __device__ __forceinline__ float df_mul(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    volatile float r = a * b;
+    return r;
+#endif
+}
+__host__ __device__ __forceinline__ float df_fma(float a, float b, float c)
+{
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(a, b, c);
+#else
+    return std::fma(a, b, c);
+#endif
+}
+__host__ __device__ __forceinline__ float df_div(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fdiv_rn(a, b);
+#else
+    volatile float r = a / b;
+    return r;
+#endif
+}
+
+__host__ __device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e)
+{
+    s = df_add(a, b);
+    const float bb = df_sub(s, a);
+    e = df_add(df_sub(a, df_sub(s, bb)), df_sub(b, bb));
 }
 
 // |a| >= |b| (or a == 0)
-__device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e)
+__host__ __device__ __forceinline__ void df_fast_two_sum(float a, float b, float& s, float& e)
 {
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
+    s = df_add(a, b);
+    e = df_sub(b, df_sub(s, a));
 }
 
-__device__ __forceinline__ df64 operator+(df64 a, df64 b)
+__host__ __device__ __forceinline__ df64 operator+(df64 a, df64 b)
 {
     float s1, s2, t1, t2;
     df_two_sum(a.hi, b.hi, s1, s2);
     df_two_sum(a.lo, b.lo, t1, t2);
-    s2 = __fadd_rn(s2, t1);
+    s2 = df_add(s2, t1);
     df_fast_two_sum(s1, s2, s1, s2);
-    s2 = __fadd_rn(s2, t2);
+    s2 = df_add(s2, t2);
     df64 r;
     df_fast_two_sum(s1, s2, r.hi, r.lo);
     return r;
 }
 
-__device__ __forceinline__ df64 operator-(df64 a)
+__host__ __device__ __forceinline__ df64 operator-(df64 a)
 {
     df64 r;
     r.hi = -a.hi;
@@ -67,31 +116,31 @@ __device__ __forceinline__ df64 operator-(df64 a)
     return r;
 }
 
-__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__host__ __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
 
-__device__ __forceinline__ df64 operator*(df64 a, df64 b)
+__host__ __device__ __forceinline__ df64 operator*(df64 a, df64 b)
 {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
+    const float p = df_mul(a.hi, b.hi);
+    float e = df_fma(a.hi, b.hi, -p);
+    e = df_fma(a.hi, b.lo, e);
+    e = df_fma(a.lo, b.hi, e);
     df64 r;
     df_fast_two_sum(p, e, r.hi, r.lo);
     return r;
 }
 
-__device__ __forceinline__ df64 operator/(df64 a, df64 b)
+__host__ __device__ __forceinline__ df64 operator/(df64 a, df64 b)
 {
-    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float q1 = df_div(a.hi, b.hi);
     const df64 r = a - b * df64::of(q1);
-    const float q2 = __fdiv_rn(r.hi, b.hi);
+    const float q2 = df_div(r.hi, b.hi);
     df64 o;
     df_fast_two_sum(q1, q2, o.hi, o.lo);
     return o;
 }
 
-__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
-__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
-__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
+__host__ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+__host__ __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+__host__ __device__ __forceinline__ df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
 
 }  // namespace lfe
