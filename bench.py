@@ -133,6 +133,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(d, dt_ps):
     """The oracle as it stands (level 2: real-space pairs + naive-DFT SPME, FP64)
     timed on the host cores on one full force/energy evaluation of the same
@@ -143,7 +155,7 @@ def cpu_baseline(d, dt_ps):
     R.bonded(d)
     t = time.perf_counter() - t0
     return {"value": dt_ps * 1e-3 * 86400.0 / t, "unit": "ns/day", "cores": R.num_threads(),
-            "kind": "oracle",
+            "host_cpus": os.cpu_count(), "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"one full level-2 oracle force+energy evaluation of the same {len(d['charge'])}-atom "
                       f"system ({t:.2f} s); integration not included",
             "seconds_per_eval": t, "pair_interactions_per_s": E["n_pairs"] / t}
@@ -168,8 +180,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "atoms": len(d["charge"]), "dt_fs": dt_ps * 1e3},
             "pair_interactions_per_s": npairs / t,
-            "cpu_baseline": {"value": v, "unit": "ns/day", "cores": c["cores"], "kind": "oracle",
-                             "sample": c["sample"]},
+            "cpu_baseline": {"value": v, "unit": "ns/day", "cores": c["cores"], "host_cpus": c["host_cpus"],
+                             "cpu_model": c["cpu_model"], "kind": "oracle", "sample": c["sample"]},
             "e2e": {"value": v, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
