@@ -51,3 +51,48 @@ def test_create_without_gpu_reports_error():
     with pytest.raises(lfe.LfeError) as e:
         lfe.System(d)
     assert e.value.code == lfe.LFE_ERR_CUDA
+
+
+def _header_signatures():
+    src = open(os.path.join(ROOT, "include", "lfe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    sigs = {}
+    for ret, name, args in re.findall(r"([A-Za-z_][A-Za-z_0-9 ]*\**)\s*\b(lfe_[a-z_0-9]+)\s*\(([^()]*)\)\s*;",
+                                      src):
+        args = args.strip()
+        sigs[name] = (ret.split()[-1] if ret.strip() else ret,
+                      [] if args in ("", "void") else [a.strip() for a in args.split(",")])
+    return sigs
+
+
+def _c_kind(decl):
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    if "unsigned long long" in decl:
+        return "u64"
+    if "double" in decl:
+        return "f64"
+    if re.search(r"\bint\b", decl):
+        return "i32"
+    raise AssertionError(decl)
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_double: "f64", ctypes.c_int: "i32", ctypes.c_ulonglong: "u64"}[t]
+
+
+def test_binding_argument_types_match_header():
+    # every entry point the binding calls is marshalled with the header's
+    # argument count and kinds (pointer, int, double, 64-bit unsigned)
+    sigs = _header_signatures()
+    lib = lfe.load()
+    assert set(sigs) == set(lfe.EXPORTED)
+    for name, (ret, params) in sigs.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert [_ctypes_kind(t) for t in fn.argtypes] == [_c_kind(p) for p in params], name
+        want = {"int": ctypes.c_int, "void": None, "char*": ctypes.c_char_p, "*": ctypes.c_char_p}[ret]
+        assert fn.restype == want, (name, ret, fn.restype)
