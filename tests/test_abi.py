@@ -96,3 +96,29 @@ def test_binding_argument_types_match_header():
         assert [_ctypes_kind(t) for t in fn.argtypes] == [_c_kind(p) for p in params], name
         want = {"int": ctypes.c_int, "void": None, "char*": ctypes.c_char_p, "*": ctypes.c_char_p}[ret]
         assert fn.restype == want, (name, ret, fn.restype)
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    # the C compiler's offsets and sizes of lfe_params and lfe_topology equal
+    # those of the ctypes mirrors (field order, types and padding)
+    import subprocess
+    structs = {"lfe_params": lfe.Params, "lfe_topology": lfe.Topology}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lfe.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for row in subprocess.check_output([str(exe)], text=True).split("\n"):
+        if row:
+            c, f, v = row.split()
+            got[(c, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
