@@ -49,3 +49,23 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "c0"])
     bench.run_reference(bench.parse())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
+    import json
+    import sys
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "c0",
+                                      "--steps", "1", "--warmup", "0"])
+    bench.run_reference(bench.parse())
+    lines = [l for l in capsys.readouterr().out.split("\n") if l.strip()]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in rec, k
+    assert rec["impl"] == "reference" and rec["unit"] == "ns/day" and rec["value"] > 0
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["value"] == rec["value"]
+    assert rec["cpu_baseline"]["cores"] >= 1
+    assert rec["e2e"] == {"value": rec["value"], "unit": "ns/day", "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
