@@ -127,11 +127,27 @@ class Opes:
         a = r / self.rho_bar + self.eps
         return self.nu / self.beta * math.log(a), self.nu / self.beta * (dr / self.rho_bar) / a
 
-    def deposit(self, th):
-        w = math.exp(self.beta * self.bias(th)[0]) if self.kind == "std" else 1.0
+    def deposit(self, th, v_other=0.0):
+        """Append a kernel at th.  A Standard kernel's weight undoes the whole
+        bias the trajectory feels at th: exp(beta (V(th) + v_other)), with
+        v_other the other bias of the dual protocol at th (0 for a single
+        bias); both are taken before this deposit.  Explore weights are 1."""
+        w = math.exp(self.beta * (self.bias(th)[0] + v_other)) if self.kind == "std" else 1.0
         self.c.append(th - 2.0 * math.floor(th / 2.0))
         self.w.append(w)
         self.rho_bar = sum(self._rho(ck)[0] for ck in self.c) / len(self.c)
+
+
+def opes_dual_deposit(std, exp, th):
+    """Deposit at th into the biases of Eq. 14 (either may be None): each is
+    updated separately, the Standard weight uses the total bias at th, and
+    both biases are evaluated before either deposit."""
+    Vs = std.bias(th)[0] if std is not None else 0.0
+    Ve = exp.bias(th)[0] if exp is not None else 0.0
+    if std is not None:
+        std.deposit(th, v_other=Ve)
+    if exp is not None:
+        exp.deposit(th, v_other=Vs)
 
 
 # -------------------------------------------------------------- constraints
@@ -183,8 +199,10 @@ def langevin_middle_step(x, v, F, mass, dt, gamma, T, normals, box, pairs, lengt
     """One step of the Langevin middle scheme (Zhang et al. 2019, cited in
     Section 2.6): kick v += dt F/m; half drift; Ornstein-Uhlenbeck
     v = a v + sqrt(kT (1 - a^2)/m) R, a = exp(-gamma dt); half drift;
-    constrain the new positions; v = (x_new - x)/dt.  Atoms of mass 0 stay
-    fixed."""
+    constrain the new positions.  The velocity carried to the next step is
+    the post-noise one plus the constraint displacement over dt,
+    v = v_OU + (x_constrained - x_unconstrained)/dt (for an unconstrained
+    atom simply v_OU).  Atoms of mass 0 stay fixed."""
     w = np.where(mass > 0, 1.0 / np.where(mass > 0, mass, 1.0), 0.0)
     a = math.exp(-gamma * dt)
     v = v + dt * w[:, None] * F
@@ -193,8 +211,9 @@ def langevin_middle_step(x, v, F, mass, dt, gamma, T, normals, box, pairs, lengt
     v = a * v + sd[:, None] * normals
     xn = xn + 0.5 * dt * v
     if pairs:
-        xn = shake(xn, x, pairs, lengths, w, box)
-    v = (xn - x) / dt
+        xc = shake(xn, x, pairs, lengths, w, box)
+        v = v + (xc - xn) / dt
+        xn = xc
     v[w == 0.0] = 0.0
     xn[w == 0.0] = x[w == 0.0]
     return xn, v
