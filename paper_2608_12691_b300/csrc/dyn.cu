@@ -440,7 +440,9 @@ void launch_dafed_probe(const SysView<real>& s, const DafedView& d, double c, do
 // Langevin middle scheme per constraint group: kick v += dt F/m, half drift,
 // Ornstein-Uhlenbeck v = a v + sqrt(kT (1 - a^2)/m) R, half drift, constrain
 // the new positions along the old bond vectors (Newton iteration on the
-// group's Lagrange multipliers), v = (x_new - x)/dt.  All of it is done in
+// group's Lagrange multipliers); the velocity carried to the next step is the
+// post-noise velocity plus the constraint displacement over dt (for an
+// unconstrained atom the post-noise velocity itself).  All of it is done in
 // coordinates relative to the group's first atom (small numbers, so FP32
 // keeps full relative precision and the velocity comes from the displacement
 // itself, not from a difference of two absolute positions).  The group shape
@@ -466,6 +468,8 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
     real o0[3];
     real rel0[NA][3];
     real p[NA][3];
+    real vou[NA][3];   // post-noise velocity
+    real pu[NA][3];    // position before the constraints
     real w[NA];
     int slot[NA];
     // every load of the group is issued before any store (the stores that
@@ -510,7 +514,10 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
         for (int d = 0; d < 3; ++d) rel0[a][d] = a == 0 ? (real)0 : minimg(xa[d] - o0[d], s.L[d], s.invL[d]);
         if (w[a] == (real)0) {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) p[a][d] = rel0[a][d];
+            for (int d = 0; d < 3; ++d) {
+                p[a][d] = pu[a][d] = rel0[a][d];
+                vou[a][d] = (real)0;
+            }
             continue;
         }
         const real vv[3] = {va4[a].x, va4[a].y, va4[a].z};
@@ -521,7 +528,8 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
             real disp = (real)0.5 * g.dt * vd;
             vd = g.a_fric * vd + kick[a][d];
             disp += (real)0.5 * g.dt * vd;
-            p[a][d] = rel0[a][d] + disp;
+            p[a][d] = pu[a][d] = rel0[a][d] + disp;
+            vou[a][d] = vd;
         }
     }
     if (NC > 0) {
@@ -602,10 +610,14 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
         R4<real> xnew, vnew;
         if (w[a] == (real)0) {
             vnew.x = vnew.y = vnew.z = (real)0;
+        } else if (NC == 0) {
+            vnew.x = vou[a][0];
+            vnew.y = vou[a][1];
+            vnew.z = vou[a][2];
         } else {
-            vnew.x = (p[a][0] - rel0[a][0]) * inv_dt;
-            vnew.y = (p[a][1] - rel0[a][1]) * inv_dt;
-            vnew.z = (p[a][2] - rel0[a][2]) * inv_dt;
+            vnew.x = vou[a][0] + (p[a][0] - pu[a][0]) * inv_dt;
+            vnew.y = vou[a][1] + (p[a][1] - pu[a][1]) * inv_dt;
+            vnew.z = vou[a][2] + (p[a][2] - pu[a][2]) * inv_dt;
         }
         vnew.w = (real)0;
         xnew.x = (o0[0] + shift[0]) + p[a][0];
@@ -824,9 +836,14 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     }
     const unsigned long long stepn = step + 1;
     if (t.stride > 0 && (stepn % (unsigned long long)t.stride) == 0ull) {
-        double Vd, dVd;
-        opes_bias(t, 0, thn, Vd, dVd);
-        if (t.on[0]) opes_deposit(t, 0, thn, exp(t.beta * Vd));
+        // a Standard kernel is reweighted by the total bias at its centre,
+        // exp(beta (V_std + V_exp)), so that its density estimate converges
+        // to the unbiased distribution while the trajectory runs under the
+        // sum of both biases (Eq. 14); both are taken before either deposit
+        double Vs, dVs, Ve, dVe;
+        opes_bias(t, 0, thn, Vs, dVs);
+        opes_bias(t, 1, thn, Ve, dVe);
+        if (t.on[0]) opes_deposit(t, 0, thn, exp(t.beta * (Vs + Ve)));
         if (t.on[1]) opes_deposit(t, 1, thn, 1.0);
     }
     __syncwarp();

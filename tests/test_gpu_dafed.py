@@ -92,8 +92,7 @@ def oracle_steps(d, nsteps, s0):
             s[k], ps[k] = D.dafed_step(s[k], ps[k], Fs[k], MASS_S[k], d["dt"], 25.0, 1000.0,
                                        D.dafed_normal(k, step, SEED))
         if (step + 1) % d["opes_stride"] == 0:
-            std.deposit(th)
-            exp.deposit(th)
+            D.opes_dual_deposit(std, exp, th)
     return x, th, s, ps
 
 

@@ -44,14 +44,59 @@ def oracle_steps(d, nsteps):
         th, p = D.theta_step(th, p, e["dUdl"], dl, dV, d["lambda_mass"], d["dt"], d["lambda_friction"],
                              d.get("lambda_temperature") or d["temperature"], D.theta_normal(step, SEED))
         if d["opes_stride"] and (step + 1) % d["opes_stride"] == 0:
-            std.deposit(th)
-            exp.deposit(th)
+            D.opes_dual_deposit(std, exp, th)
     oracle_steps.ti = ti
     return x, v, th, p, std, exp
 
 
 def min_image(a, box):
     return a - box * np.round(a / box)
+
+
+def octanol_system():
+    # the octanol workload in small: 36 octanol-like chains (masses x 0.1,
+    # X-H bonds constrained as stars, bonds/angles/torsions, 1-2/1-3
+    # exclusions, scaled 1-4 pairs) around the frozen 20-atom solute,
+    # 992 atoms in a 2.8 nm box, stepped at the octanol time step (1 fs)
+    d = S.make_octanol_box(seed=31, n_chains=36, box_len=2.8, nx=6, ny=6, nz=2, r_cut=0.9, grid=24,
+                           lam=0.55)
+    d.update(dt=0.001, lambda_mass=20.0, lambda_friction=25.0, opes_stride=2,
+             opes_dE_std=30 * 4.184, opes_dE_exp=5 * 4.184, opes_sigma=0.1)
+    return d
+
+
+@pytest.mark.parametrize("precision,tx,tv", [(lfe.LFE_FP64, 2e-8, 1e-6), (lfe.LFE_FP32_MIXED, 5e-6, 5e-3)])
+def test_octanol_steps_match_oracle(precision, tx, tv):
+    d = octanol_system()
+    n = 4
+    g = lfe.System(d, precision=precision, seed=SEED)
+    g.step(n)
+    pos, vel, ext = g.get_state()
+    x, v, th, p, std, exp = oracle_steps(d, n)
+    dx = np.abs(min_image(pos - x, d["box"])).max()
+    assert dx < tx, dx
+    assert np.abs(vel - v).max() < tv * np.abs(v).max()
+    assert ext["step"] == n
+    assert ext["n_kernels_std"] == len(std.c) and ext["n_kernels_exp"] == len(exp.c)
+    assert ext["theta"] == pytest.approx(th, abs=1e-8 if precision == lfe.LFE_FP64 else 1e-5)
+
+
+def test_kinetic_temperature_matches_the_thermostat():
+    # Section 2.6: 298 K.  101 rigid waters (6 degrees of freedom each, the
+    # solute frozen) stepped at 1 fs with friction 10 ps^-1: after 1 ps the
+    # mean kinetic energy is 6/2 k_B T per water (equipartition)
+    d = water_system()
+    d.update(opes_stride=0)
+    g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=SEED)
+    g.step(1000)
+    kT = D.KB * d["temperature"]
+    ke = []
+    for _ in range(100):
+        g.step(20)
+        _, vel, _ = g.get_state()
+        ke.append(0.5 * (d["mass"][:, None] * vel * vel).sum())
+    n_w = len(d["waters"])
+    assert np.mean(ke) == pytest.approx(3.0 * n_w * kT, rel=0.04)
 
 
 @pytest.mark.parametrize("precision,tx,tv", [(lfe.LFE_FP64, 2e-8, 1e-6), (lfe.LFE_FP32_MIXED, 5e-6, 5e-3)])
