@@ -273,6 +273,19 @@ int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
  * Synchronises the device.  Errors: LFE_ERR_ARG (non-finite input). */
 int lfe_set_theta(lfe_system* sys, double theta, double p_theta);
 
+/* Neighbour-list capacity (Section 2.6 states the cutoff and switch the list
+ * serves; the list itself is this library's data structure).  Replaces the
+ * tile list by one holding exactly `tiles` tiles of 8 i atoms x 32 j atoms
+ * and flags a rebuild, so that the next step or evaluation builds the list
+ * again within it.  When a later build needs more tiles the library grows
+ * the list by itself: a build inside a captured step marks the step and the
+ * ones after it as skipped, and the next synchronising call (or every 64
+ * steps) grows the list, rebuilds it and replays the skipped steps; results
+ * are those of an uncapped list.  Meant for memory-constrained callers and
+ * for exercising that recovery.  Synchronises the device.  Errors:
+ * LFE_ERR_ARG (tiles < 1), LFE_ERR_CUDA. */
+int lfe_set_list_capacity(lfe_system* sys, int tiles);
+
 /* Autotuner: choose the evaluation's launch shapes for this system by
  * timing it on the device: when the system steps (dt > 0), the mean time
  * of `reps` captured steps from a saved state (a temporary checkpoint file
@@ -344,15 +357,15 @@ int lfe_batch_exchange(lfe_batch* b, int n, int* ladder, double temperature, uns
 const char* lfe_batch_last_error(const lfe_batch* b);
 void lfe_batch_destroy(lfe_batch* b);
 
-/* Reciprocal-space (smooth PME) part of Eq. 4 for one configuration,
- * without any device allocation.  The paper has no counterpart: this entry
- * exists for callers that cannot let a library call cudaMalloc -- code that
- * runs while another framework captures the stream into a CUDA graph in the
- * global capture mode (allocation calls are not permitted then), processes
- * whose device memory belongs to a pool or allocator that forbids hidden
- * allocations, and services that must not grow their memory after start-up.
+/* Smooth-PME reciprocal-space class energies and forces of one
+ * configuration, computed without any device allocation.  The paper has no
+ * counterpart: this entry exists for callers that cannot let a library call
+ * cudaMalloc -- processes whose device memory belongs to a pool or allocator
+ * that forbids hidden allocations, services that must not grow their memory
+ * after start-up, and code running where allocation calls are not
+ * permitted.  A call issues only kernel launches and memsets on `stream`.
  *
- * The grids live in one fixed file-scope device array sized for
+ * The grids and tables live in one fixed file-scope device array sized for
  * LFE_NOALLOC_MAX_GRID grid points (about 4.4 MB), which every GPU that loads
  * the library holds until the process exits; larger grids are rejected with
  * LFE_ERR_ARG.  All pointers are device memory on the current device:
@@ -361,13 +374,13 @@ void lfe_batch_destroy(lfe_batch* b);
  *   neutralising background) E_vv, E_uu, E_uv.
  * box [3] and grid [3] are host arrays; lambda selects h_A(lambda) for the
  * forces (solvent atoms feel phi_v + h_A phi_u, solute atoms phi_u + h_A
- * phi_v).  Work is queued on `stream`; outputs are complete when the stream
- * reaches the end of the call.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and should come before any
- * stream capture.  Every call shares the array: calls that overlap on the
- * GPU (different streams, or threads without ordering) race and give wrong
- * results.  Errors: LFE_ERR_ARG (sizes, grid too large), LFE_ERR_CUDA; the
- * message is available from lfe_last_error(NULL). */
+ * phi_v).  Outputs are complete when the stream reaches the end of the call.
+ * The first call on a device (with that device current) looks up the
+ * array's device address with cudaGetSymbolAddress.  Every call shares the
+ * array and overwrites what the last call left there: calls that overlap on
+ * the GPU (different streams, or threads without ordering) race and give
+ * wrong results.  Errors: LFE_ERR_ARG (sizes, grid too large), LFE_ERR_CUDA;
+ * the message is available from lfe_last_error(NULL). */
 #define LFE_NOALLOC_MAX_GRID 110592   /* 48 x 48 x 48 */
 int lfe_pme_noalloc(int n, const double* pos, const double* charge, const unsigned char* solute,
                     const double* box, double alpha, const int* grid, double lambda,

@@ -106,6 +106,7 @@ struct SystemBase {
     virtual cudaStream_t side_stream() = 0;
     virtual void autotune(int reps, const char* cache_path, double* best_ms, int* params) = 0;
     virtual void set_theta(double theta, double p_theta) = 0;
+    virtual void set_list_capacity(int tiles) = 0;
     virtual void lambda_state(double* lam, double* mass) = 0;
     unsigned generation = 0;   // bumped whenever device buffers are reallocated
 };
@@ -1296,6 +1297,21 @@ struct System final : SystemBase {
         if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 0; }
     }
 
+    // Replace the tile list by one of exactly `tiles` tiles (the build kernels
+    // never write past it) and flag a rebuild: the next step or evaluation
+    // builds the list again, and when it needs more tiles the overflow path
+    // (skipped steps, growth, rebuild, replay) takes over.
+    void set_list_capacity(int tiles) override
+    {
+        if (tiles < 1) fail(LFE_ERR_ARG, "list capacity must be at least one tile");
+        CK(cudaDeviceSynchronize());
+        grow_tiles(tiles, tiles);
+        N.cap = tiles;
+        N.stage_cap = tiles;
+        const int one = 1;
+        CK(cudaMemcpy(S.flags + FL_REBUILD, &one, sizeof(int), cudaMemcpyHostToDevice));
+    }
+
     // theta (wrapped into [0, 2)), its momentum, and the lambda of Eq. 3 with
     // its switching functions
     void set_theta(double theta, double p_theta) override
@@ -2185,6 +2201,11 @@ int lfe_autotune(lfe_system* sys, int reps, const char* cache_path, double* best
 int lfe_set_theta(lfe_system* sys, double theta, double p_theta)
 {
     return guard(sys, [&] { sys->impl->set_theta(theta, p_theta); });
+}
+
+int lfe_set_list_capacity(lfe_system* sys, int tiles)
+{
+    return guard(sys, [&] { sys->impl->set_list_capacity(tiles); });
 }
 
 namespace {

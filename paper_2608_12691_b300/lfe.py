@@ -31,7 +31,7 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
     "lfe_batch_exchange", "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
@@ -131,6 +131,8 @@ def load():
     lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
     lib.lfe_set_theta.argtypes = [vp, ctypes.c_double, ctypes.c_double]
     lib.lfe_set_theta.restype = ctypes.c_int
+    lib.lfe_set_list_capacity.argtypes = [vp, ctypes.c_int]
+    lib.lfe_set_list_capacity.restype = ctypes.c_int
     lib.lfe_batch_exchange.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_ulonglong,
                                        ctypes.c_ulonglong, vp, vp]
     lib.lfe_batch_exchange.restype = ctypes.c_int
@@ -413,6 +415,11 @@ class System:
     def set_theta(self, theta, p_theta=0.0):
         """Set theta and its momentum (lambda follows Eq. 3; lfe_set_theta)."""
         self._check(self._lib.lfe_set_theta(self.h, float(theta), float(p_theta)))
+
+    def set_list_capacity(self, tiles):
+        """Shrink or grow the neighbour-list tile capacity; the list is
+        rebuilt by the next step or evaluation (lfe_set_list_capacity)."""
+        self._check(self._lib.lfe_set_list_capacity(self.h, int(tiles)))
 
     def autotune(self, reps=20, cache_path=None):
         """Choose the evaluation's launch shapes by timing (lfe_autotune).
