@@ -1,28 +1,28 @@
 // noalloc.cu -- reciprocal-space (smooth PME) evaluation that allocates no
 // device memory.
 //
-// Some callers cannot let a library call cudaMalloc: code that runs while
-// another framework is capturing the stream into a CUDA graph under the
-// global capture mode (where allocation calls are not permitted), callers
-// whose device memory is owned by a pool or an allocator that forbids hidden
-// allocations, and long-running services that must not grow their memory
-// after start-up.  For them, lfe_pme_noalloc keeps every intermediate grid in
-// one file-scope __device__ array of fixed size, which every GPU that loads
-// this library holds until the process exits.  The caller still provides the
-// inputs and the outputs in device memory.
+// Some callers cannot let a library call cudaMalloc: processes whose device
+// memory is owned by a pool or an allocator that forbids hidden allocations,
+// long-running services that must not grow their memory after start-up, and
+// code running where allocation calls are not permitted.  For them,
+// lfe_pme_noalloc keeps every intermediate grid and table in one file-scope
+// __device__ array of fixed size, which every GPU that loads this library
+// holds until the process exits.  The caller still provides the inputs and
+// the outputs in device memory; a call issues only kernel launches and
+// memsets on the caller's stream.
 //
 // The arithmetic is the one of the system path: order-4 B-spline spreading
 // into fixed-point class grids, the packed FP32 transform for the forces and
 // the FP64 transform for the class energies, the same influence function and
 // class split (U_vv, U_uu, U_uv and the h_A-weighted class potentials).
 #include <cmath>
-#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "lfe.h"
 #include "lfe_views.cuh"
+#include "pme_dev.cuh"
 
 namespace lfe {
 
@@ -46,14 +46,6 @@ struct NaScratch {
 // the scratch array: shared by every call on a device, it keeps the last
 // call's contents; every call clears what must start at zero
 __device__ __align__(256) NaScratch g_na_scratch;
-
-// host copy of the tables uploaded by each call
-struct NaTables {
-    float gfac[3][NA_MAX_K], msq[3][NA_MAX_K];
-    R2<float> tw[3][NA_MAX_K];
-    double gfac64[3][NA_MAX_K], msq64[3][NA_MAX_K];
-    R2<double> tw64[3][NA_MAX_K];
-};
 
 std::mutex g_na_mutex;
 NaScratch* g_na_addr[256] = {};   // device address of g_na_scratch, per device
@@ -93,32 +85,37 @@ __global__ void k_na_sums(int n, const double* q, const unsigned char* sol, NaSc
     }
 }
 
-__device__ __forceinline__ int na_wrapk(int k, int K) { return k < 0 ? k + K : (k >= K ? k - K : k); }
+// influence-function factors exp(-pi^2 m^2 / alpha^2) |b(m)|^2 with the
+// order-4 B-spline moduli, squared reciprocal vectors m^2 (m = k / L for
+// k <= K/2, (k - K) / L above) and twiddles exp(2 pi i k / K) of every axis,
+// in FP64 and (rounded) FP32: one thread per (axis, k)
+struct NaBox {
+    double L[3];
+    int K[3];
+    double alpha;
+};
 
-// fractional grid coordinate of a caller position (any value, also outside
-// the box); base f in [0, K), offset w in [0, 1)
-__device__ __forceinline__ void na_coord(double x, double L, int K, int& f, double& w)
+__global__ void k_na_tables(NaBox b, NaScratch* sc)
 {
-    double u = x / L;
-    u -= floor(u);
-    u *= K;
-    if (!(u >= 0.0 && u < (double)K)) u = 0.0;
-    const double fl = floor(u);
-    f = min(max((int)fl, 0), K - 1);
-    w = u - fl;
-}
-
-__device__ __forceinline__ void na_bspline4(double w, double th[4], double dth[4])
-{
-    const double w2 = w * w, w3 = w2 * w, o = 1.0 - w;
-    th[0] = w3 / 6.0;
-    th[1] = (-3.0 * w3 + 3.0 * w2 + 3.0 * w + 1.0) / 6.0;
-    th[2] = (3.0 * w3 - 6.0 * w2 + 4.0) / 6.0;
-    th[3] = o * o * o / 6.0;
-    dth[0] = 0.5 * w2;
-    dth[1] = 0.5 * (-3.0 * w2 + 2.0 * w + 1.0);
-    dth[2] = 0.5 * (3.0 * w2 - 4.0 * w);
-    dth[3] = -0.5 * o * o;
+    const int d = blockIdx.x;
+    const int K = b.K[d];
+    for (int m = threadIdx.x; m < K; m += blockDim.x) {
+        // |b(m)|^-2 = |sum_{k=0..2} M4(k+1) e^{2 pi i m k / K}|^2, M4(1..3) = 1/6, 2/3, 1/6
+        const double c1 = cospi(2.0 * m / K), s1 = sinpi(2.0 * m / K);
+        const double c2 = cospi(4.0 * m / K), s2 = sinpi(4.0 * m / K);
+        const double re = 1.0 / 6.0 + (2.0 / 3.0) * c1 + (1.0 / 6.0) * c2;
+        const double im = (2.0 / 3.0) * s1 + (1.0 / 6.0) * s2;
+        const double b2 = 1.0 / (re * re + im * im);
+        const int mm = (m <= K / 2) ? m : m - K;
+        const double mr = mm / b.L[d];
+        const double gf = exp(-PI * PI * mr * mr / (b.alpha * b.alpha)) * b2;
+        sc->gfac64[d][m] = gf;
+        sc->msq64[d][m] = mr * mr;
+        sc->tw64[d][m] = R2<double>{c1, s1};
+        sc->gfac[d][m] = (float)gf;
+        sc->msq[d][m] = (float)(mr * mr);
+        sc->tw[d][m] = R2<float>{(float)c1, (float)s1};
+    }
 }
 
 struct NaGeom {
@@ -139,17 +136,17 @@ __global__ void k_na_spread(NaGeom g, const double* pos, const double* q, const 
     double th[3][4], dth[4];
     for (int d = 0; d < 3; ++d) {
         double w;
-        na_coord(pos[3 * a + d], g.L[d], g.K[d], f[d], w);
-        na_bspline4(w, th[d], dth);
+        grid_coord<double, double>(pos[3 * a + d], g.K[d] / g.L[d], g.K[d], f[d], w);
+        bspline4<double>(w, th[d], dth);
     }
     for (int j0 = 0; j0 < 4; ++j0) {
-        const int k0 = na_wrapk(f[0] - j0, g.K[0]);
+        const int k0 = wrapk(f[0] - j0, g.K[0]);
         for (int j1 = 0; j1 < 4; ++j1) {
-            const int k1 = na_wrapk(f[1] - j1, g.K[1]);
+            const int k1 = wrapk(f[1] - j1, g.K[1]);
             const double a1 = qa * th[0][j0] * th[1][j1];
             const int row = (k0 * g.K[1] + k1) * g.K[2];
             for (int j2 = 0; j2 < 4; ++j2) {
-                const int k2 = na_wrapk(f[2] - j2, g.K[2]);
+                const int k2 = wrapk(f[2] - j2, g.K[2]);
                 atomic_add_ll(&grid[row + k2], __double2ll_rn(a1 * th[2][j2] * QSCALE));
             }
         }
@@ -169,18 +166,18 @@ __global__ void k_na_gather(NaGeom g, const double* pos, const double* q, const 
     double th[3][4], dth[3][4];
     for (int d = 0; d < 3; ++d) {
         double w;
-        na_coord(pos[3 * a + d], g.L[d], g.K[d], f[d], w);
-        na_bspline4(w, th[d], dth[d]);
+        grid_coord<double, double>(pos[3 * a + d], g.K[d] / g.L[d], g.K[d], f[d], w);
+        bspline4<double>(w, th[d], dth[d]);
     }
     double gx = 0, gy = 0, gz = 0;
     for (int j0 = 0; j0 < 4; ++j0) {
-        const int k0 = na_wrapk(f[0] - j0, g.K[0]);
+        const int k0 = wrapk(f[0] - j0, g.K[0]);
         for (int j1 = 0; j1 < 4; ++j1) {
-            const int k1 = na_wrapk(f[1] - j1, g.K[1]);
+            const int k1 = wrapk(f[1] - j1, g.K[1]);
             const int row = (k0 * g.K[1] + k1) * g.K[2];
             double sx = 0, sz = 0;
             for (int j2 = 0; j2 < 4; ++j2) {
-                const int k2 = na_wrapk(f[2] - j2, g.K[2]);
+                const int k2 = wrapk(f[2] - j2, g.K[2]);
                 const R2<float> w = sc->Z[row + k2];
                 const double phi = u ? (double)w.y : (double)w.x;
                 sx += th[2][j2] * phi;
@@ -259,34 +256,18 @@ extern "C" int lfe_pme_noalloc(int n, const double* pos, const double* charge, c
         }
         sc = g_na_addr[dev];
     }
-    // influence-function factors and twiddles for this box and grid
-    NaTables tab;
-    std::memset(&tab, 0, sizeof(tab));
-    const double V = box[0] * box[1] * box[2];
-    for (int d = 0; d < 3; ++d) {
-        const int K = grid[d];
-        for (int m = 0; m < K; ++m) {
-            double re = 0, im = 0;
-            const double mk[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
-            for (int k = 0; k < 3; ++k) {
-                re += mk[k] * std::cos(2.0 * PI * m * k / K);
-                im += mk[k] * std::sin(2.0 * PI * m * k / K);
-            }
-            const double b2 = 1.0 / (re * re + im * im);
-            const int mm = (m <= K / 2) ? m : m - K;
-            const double mr = mm / box[d];
-            const double gf = std::exp(-PI * PI * mr * mr / (alpha * alpha)) * b2;
-            tab.gfac64[d][m] = gf;
-            tab.msq64[d][m] = mr * mr;
-            tab.tw64[d][m] = R2<double>{std::cos(2.0 * PI * m / K), std::sin(2.0 * PI * m / K)};
-            tab.gfac[d][m] = (float)gf;
-            tab.msq[d][m] = (float)(mr * mr);
-            tab.tw[d][m] = R2<float>{(float)tab.tw64[d][m].x, (float)tab.tw64[d][m].y};
-        }
-    }
+    // influence-function factors and twiddles for this box and grid, formed
+    // on the device from arguments passed by value
     NaScratch* dsc = sc;
-    cudaError_t e = cudaMemcpyAsync(&dsc->gfac[0][0], &tab, sizeof(tab), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(dsc->Qfix, 0, sizeof(long long) * 2 * LFE_NOALLOC_MAX_GRID, st);
+    const double V = box[0] * box[1] * box[2];
+    NaBox nb{};
+    for (int d = 0; d < 3; ++d) {
+        nb.L[d] = box[d];
+        nb.K[d] = grid[d];
+    }
+    nb.alpha = alpha;
+    k_na_tables<<<3, NA_MAX_K, 0, st>>>(nb, dsc);
+    cudaError_t e = cudaMemsetAsync(dsc->Qfix, 0, sizeof(long long) * 2 * LFE_NOALLOC_MAX_GRID, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dsc->E, 0, sizeof(long long) * E_N, st);
     if (e != cudaSuccess) return na_fail(LFE_ERR_CUDA, std::string("lfe_pme_noalloc: ") + cudaGetErrorString(e));
 
