@@ -27,29 +27,36 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) on 1 B300"
-# algorithmic FP32 operations per interacting pair (counting convention in the
-# design notes: pair vector 3, r^2 5, 1/r and r 3, Coulomb 8 + erfc/exp 12,
-# LJ 15, switch 8, force vector and Newton's third law 9, energy 2, class 2)
-FLOPS_PER_PAIR = 67
+# algorithmic FP32 operations per interacting pair, itemised: minimum image 9,
+# r^2 5, rsqrt 1, erfc + exp 12, Coulomb 4, LJ 8, switch 8, force vector and
+# Newton's third law 12 (58 in all; about two of them go to the special
+# function unit)
+FLOPS_PER_PAIR = 58
 # DRAM bytes (read + write) of one k_pairs<float> launch on the octanol workload, from an ncu
 # capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum); None until
-# the current version has been captured (lane-per-j-entry kernel: 7.153 MB read, 0 written)
-PAIR_DRAM_BYTES_OCTANOL = 7.15264e6 + 0.0
-SM_COUNT = 148
+# the current version has been captured
+PAIR_DRAM_BYTES_OCTANOL = None
 FP32_LANES_PER_SM = 128
+MAX_SM_MHZ = 2032.0
+# timed evaluations of the reference arm at most (one level-2 oracle
+# evaluation of the octanol box takes 0.2-0.5 s on the host cores)
+REFERENCE_MAX_STEPS = 200
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
-    p.add_argument("--warmup", type=int, default=50)
+    p.add_argument("--steps", type=int, default=None,
+                   help="timed steps (default 2000; 20 oracle evaluations for --impl reference)")
+    p.add_argument("--warmup", type=int, default=None, help="untimed warm-up steps (default 50; 3 for the oracle)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="octanol", choices=["octanol", "water", "c0"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--no-dafed", action="store_true", help="skip the flexible-solute d-AFED leg")
+    p.add_argument("--no-errors", action="store_true",
+                   help="skip the oracle-error leg (every output of both precisions against levels 1 and 2)")
     p.add_argument("--e2e-steps", type=int, default=200)
     p.add_argument("--tune-cache", default=None,
                    help="JSON autotuner cache shared by every system of the run (default: none for the main "
@@ -61,7 +68,19 @@ def parse():
     p.add_argument("--batch-steps", type=int, default=40)
     p.add_argument("--profile-case", action="store_true",
                    help="build the workload, run 3 staged evaluations and exit (a small case for ncu)")
-    return p.parse_args()
+    a = p.parse_args()
+    ref = a.impl == "reference"
+    if a.steps is None:
+        a.steps = 20 if ref else 2000
+    if a.warmup is None:
+        a.warmup = 3 if ref else 50
+    return a
+
+
+def run_config(d, desc):
+    """The workload description shared by both arms of the bench."""
+    return {"workload": desc, "atoms": len(d["charge"]), "dt_fs": float(d["dt"]) * 1e3,
+            "l2": "flushed between steps (256 MiB write)", "data": "seeded synthetic stand-in"}
 
 
 def make_workload(name, rank):
@@ -145,43 +164,109 @@ def cpu_model():
     return None
 
 
-def cpu_baseline(d, dt_ps):
-    """The oracle as it stands (level 2: real-space pairs + naive-DFT SPME, FP64)
-    timed on the host cores on one full force/energy evaluation of the same
-    system; converted to the step's ns/day."""
+def oracle_timed(d, level, reps):
+    """Median host time of `reps` oracle evaluations (nonbonded + bonded) of
+    system d at the given level, and the last evaluation's results."""
     from oracle import reference as R
-    t0 = time.perf_counter()
-    E, F0, Fuv, Fs = R.nonbonded(d, level=2)
-    R.bonded(d)
-    t = time.perf_counter() - t0
-    return {"value": dt_ps * 1e-3 * 86400.0 / t, "unit": "ns/day", "cores": R.num_threads(),
+    times = []
+    out = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        E, F0, Fuv, Fs = R.nonbonded(d, level=level)
+        Ub, Fb = R.bonded(d)
+        times.append(time.perf_counter() - t0)
+        out = (E, F0, Fuv, Fs, Ub, Fb)
+    return statistics.median(times), times, out
+
+
+def cpu_baseline(d, dt_ps, reps=3):
+    """The oracle as it stands timed on the host cores on full force/energy
+    evaluations of the same system: level 2 (real-space pairs + naive-DFT
+    smooth PME on the GPU's grid, the approximation the GPU computes) and
+    level 1 (real-space pairs + direct Ewald k-sum, the definition), medians
+    of `reps` each; value = level 2 converted to the step's ns/day.  Returns
+    (baseline, {level: results}) so that the results serve the error leg."""
+    from oracle import reference as R
+    t2, all2, r2 = oracle_timed(d, 2, reps)
+    t1, all1, r1 = oracle_timed(d, 1, reps)
+    n_pairs = r2[0]["n_pairs"]
+    base = {"value": dt_ps * 1e-3 * 86400.0 / t2, "unit": "ns/day", "cores": R.num_threads(),
             "host_cpus": os.cpu_count(), "cpu_model": cpu_model(), "kind": "oracle",
-            "sample": f"one full level-2 oracle force+energy evaluation of the same {len(d['charge'])}-atom "
-                      f"system ({t:.2f} s); integration not included",
-            "seconds_per_eval": t, "pair_interactions_per_s": E["n_pairs"] / t}
+            "label": "definitional FP64 oracle, not an optimised CPU MD engine",
+            "sample": f"median of {reps} full level-2 oracle force+energy evaluations of the same "
+                      f"{len(d['charge'])}-atom system ({t2:.3f} s each); integration not included",
+            "seconds_per_eval": t2, "seconds_per_eval_all": all2, "pair_interactions_per_s": n_pairs / t2,
+            "level1": {"seconds_per_eval": t1, "seconds_per_eval_all": all1,
+                       "ns_per_day": dt_ps * 1e-3 * 86400.0 / t1, "pair_interactions_per_s": n_pairs / t1}}
+    return base, {1: r1, 2: r2}
+
+
+def output_errors(terms, F, res, lam, solute):
+    """Errors of every output of one GPU evaluation against one oracle level:
+    forces (relative RMS over all atoms and over the solute, largest component
+    error relative to the RMS atomic force), U, the class energies and
+    dU/dlambda (absolute, kJ/mol, and relative)."""
+    from oracle import reference as R
+    E, F0, Fuv, Fs, Ub, Fb = res
+    hA, hB, dA, dB = R.switching(lam)
+    Fo = F0 + hA * Fuv + hB * Fs + Fb
+    sol = np.asarray(solute).astype(bool)
+    out = {"F_rel_rms": float(np.linalg.norm(F - Fo) / np.linalg.norm(Fo)),
+           "F_rel_rms_solute": float(np.linalg.norm(F[sol] - Fo[sol]) / np.linalg.norm(Fo[sol])),
+           "F_max_over_rms": float(np.abs(F - Fo).max() / np.sqrt((Fo * Fo).sum(1).mean()))}
+    ref = {"U": E["U_vv"] + E["U_uu"] + hA * E["U_uv"] + hB * E["U_soft"] + Ub,
+           "dUdl": dA * E["U_uv"] + dB * E["U_soft"],
+           "U_vv": E["U_vv"], "U_uu": E["U_uu"], "U_uv": E["U_uv"], "U_soft": E["U_soft"], "U_bonded": Ub}
+    for k, v in ref.items():
+        err = float(terms[k] - v)
+        out[k] = {"abs": err, "rel": abs(err) / abs(v) if v else None}
+    return out
+
+
+def error_leg(systems, oracle_cache):
+    """Every output of both precision modes against the level-2 oracle (the
+    same smooth PME on the same grid, the parity bar) and the level-1 oracle
+    (exact Ewald; dominated by the PME discretisation of the grid), on the
+    seeded frames named in `systems` (name -> (d, lambda))."""
+    from paper_2608_12691_b300 import lfe
+    out = {}
+    for name, (d, lam) in systems.items():
+        res = oracle_cache.get(name) or {lv: oracle_timed(d, lv, 1)[2] for lv in (2, 1)}
+        row = {"atoms": len(d["charge"]), "lambda": lam}
+        for pname, prec in (("fp32_mixed", lfe.LFE_FP32_MIXED), ("fp64", lfe.LFE_FP64)):
+            g = lfe.System(d, precision=prec)
+            terms, F = g.eval(lam)
+            g.close()
+            row[pname] = {f"vs_level{lv}": output_errors(terms, F, res[lv], lam, d["solute"]) for lv in (2, 1)}
+        out[name] = row
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import reference as R
     d, desc = make_workload(args.workload, 0)
     dt_ps = float(d["dt"])
-    times = []
-    npairs = 0
-    for i in range(args.warmup + args.steps if args.steps <= 3 else min(args.steps, 3)):
-        c = cpu_baseline(d, dt_ps)
-        times.append(c["seconds_per_eval"])
-        npairs = c["pair_interactions_per_s"] * c["seconds_per_eval"]
-    t = statistics.median(times)
+    for _ in range(args.warmup):
+        oracle_timed(d, 2, 1)
+    k = min(args.steps, REFERENCE_MAX_STEPS)
+    _, times, res = oracle_timed(d, 2, k)
+    t = sum(times) / k
     v = dt_ps * 1e-3 * 86400.0 / t
+    npairs = res[0]["n_pairs"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ns/day", "n_gpus": args.gpus,
-            "steps": len(times), "warmup": 0, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": k, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "atoms": len(d["charge"]), "dt_fs": dt_ps * 1e3},
+            "config": run_config(d, desc),
             "pair_interactions_per_s": npairs / t,
-            "cpu_baseline": {"value": v, "unit": "ns/day", "cores": c["cores"], "host_cpus": c["host_cpus"],
-                             "cpu_model": c["cpu_model"], "kind": "oracle", "sample": c["sample"]},
+            "cpu_baseline": {"value": v, "unit": "ns/day", "cores": R.num_threads(), "host_cpus": os.cpu_count(),
+                             "cpu_model": cpu_model(), "kind": "oracle",
+                             "label": "definitional FP64 oracle, not an optimised CPU MD engine",
+                             "sample": f"each step one full level-2 oracle force+energy evaluation of the same "
+                                       f"{len(d['charge'])}-atom system (mean {t:.3f} s over {k}); integration "
+                                       f"not included"},
             "e2e": {"value": v, "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -358,6 +443,7 @@ def run_ours(args):
     d, desc = make_workload(args.workload, rank)
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     dt_ps = float(d["dt"])
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     g = lfe.System(d, precision=prec, seed=2608 + rank)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
@@ -403,13 +489,15 @@ def run_ours(args):
         stages = g.time_stages(float(ext1["lambda"]), reps=min(args.steps, 300), stream=stream)
         pair_ms = stages["pairs"]
         achieved = n_pairs * FLOPS_PER_PAIR / (pair_ms * 1e-3) / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2032e6 / 1e12
+        peak = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
         traffic = PAIR_DRAM_BYTES_OCTANOL if (args.workload == "octanol" and prec == lfe.LFE_FP32_MIXED) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_pairs<float>", "kernel_ms": pair_ms,
-                "peak_basis": "148 SMs x 128 FP32 lanes x 2 flop/FMA x 2032 MHz (max SM clock)"}
+                "flops_per_pair": FLOPS_PER_PAIR,
+                "peak_basis": f"{n_sm} SMs (device properties) x 128 FP32 lanes x 2 flop/FMA x 2032 MHz "
+                              f"(max SM clock); unit-count peak, no measured FP32 peak in the pool's file"}
         if clocks and clocks.get("sm_mhz"):
-            roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / 2032.0)
+            roof["frac_at_measured_clock"] = achieved / (peak * clocks["sm_mhz"] / MAX_SM_MHZ)
         f32_meas, f64_meas = lfe.alu_peak()
         roof["peak_measured_fma_fp32"] = f32_meas
         roof["peak_measured_fma_fp64"] = f64_meas
@@ -443,26 +531,38 @@ def run_ours(args):
             m64 = sum(ms64) / k64
             fp64 = {"ns_per_day": dt_ps * 1e-3 * 86400.0 / (m64 * 1e-3), "ms_per_step": m64, "steps": k64}
             g64.close()
-        cpu = None if args.no_cpu else cpu_baseline(d, dt_ps)
+        cpu, ocache = (None, {}) if args.no_cpu else cpu_baseline(d, dt_ps)
+        errors = None
+        if not args.no_errors:
+            from paper_2608_12691_b300 import systems as S
+            frames = {"c1_octanol" if args.workload == "octanol" else args.workload: (d, float(d["lam"]))}
+            cache = {next(iter(frames)): ocache} if ocache else {}
+            if args.workload == "octanol":
+                c2 = S.make_c2(seed=2610)
+                frames["c2_water"] = (c2, float(c2["lam"]))
+                c4 = S.make_c4_frame(frame=5)
+                frames["c4_flexible"] = (c4, float(c4["lam"]))
+            errors = error_leg(frames, cache)
         batched = batched_leg(args, stream, flush) if args.batch_replicas > 1 else None
         dafed = dafed_leg(args, stream, flush) if not args.no_dafed else None
         out = {"metric": METRIC, "value": ns_day, "unit": "ns/day", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32" if prec == lfe.LFE_FP32_MIXED else "f64",
                "data": "synthetic",
-               "config": {"workload": desc, "atoms": len(d["charge"]), "dt_fs": dt_ps * 1e3,
-                          "precision": "FP32 arithmetic, int64 fixed-point force/energy sums, FP64 lambda/OPES"
-                          if prec == lfe.LFE_FP32_MIXED else "FP64", "l2": "flushed between steps (256 MiB write)",
-                          "parallelism": "replicas" if world > 1 else "single replica",
-                          "pairs_per_step": n_pairs, "tiles": n_tiles,
-                          "autotuned": dict(tune, eval_ms=tune_ms) if tune else None,
-                          "tile_efficiency": n_pairs / (256.0 * n_tiles) if n_tiles else None},
+               "config": run_config(d, desc),
+               "precision": "FP32 arithmetic, int64 fixed-point force/energy sums, FP64 lambda/OPES"
+               if prec == lfe.LFE_FP32_MIXED else "FP64",
+               "parallelism": "replicas" if world > 1 else "single replica",
+               "pairs_per_step": n_pairs, "tiles": n_tiles,
+               "tile_efficiency": n_pairs / (256.0 * n_tiles) if n_tiles else None,
+               "autotuned": dict(tune, eval_ms=tune_ms) if tune else None,
                "pair_interactions_per_s": n_pairs / (ms_step * 1e-3) * world,
                "wall_ms_per_step": wall / args.steps * 1e3,
                "neighbour_rebuilds": rebuilds,
                "gpu_launches": launches,
                "roofline": roof, "stages_ms": stages, "fp64": fp64, "batched": batched, "dafed": dafed,
                "cpu_baseline": cpu,
+               "oracle_errors": errors,
                "e2e": e2e,
                "clocks": clocks, "lambda_end": ext1["lambda"], "theta_end": ext1["theta"]}
         print(json.dumps(out), flush=True)

@@ -21,7 +21,7 @@
  *            order-n cardinal B-splines, transformed by a naive separable DFT
  *            (the defined PME approximation, Essmann 1995, Eq. 4.1-4.9).
  *
- * Readings where the paper is silent (each listed in the design notes):
+ * Readings where the paper is silent:
  *   - Lorentz-Berthelot mixing: sigma_ij = (sigma_i+sigma_j)/2,
  *     eps_ij = sqrt(eps_i eps_j).
  *   - LJ and soft-LJ are multiplied by the quintic switch

@@ -774,7 +774,7 @@ __device__ __forceinline__ void flush_force(const SysView<real>& s, int slot, lo
 // erfc(x) and exp(-x^2).  FP32: exp(-x^2) P(t), t = 1/(1 + p x), with a
 // degree-7 least-squares fit of erfc(x) exp(x^2) on [0, 4.2] (relative
 // error below 5e-8 in exact arithmetic; the fit is reproduced by
-// fit_erfc.py).  FP64: the library functions.
+// tests/fit_erfc.py).  FP64: the library functions.
 __device__ __forceinline__ void erfc_exp(float x, float& erfcv, float& ex)
 {
     const float t = __fdividef(1.0f, fmaf(0.345f, x, 1.0f));

@@ -69,3 +69,29 @@ def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys):
     assert rec["cpu_baseline"]["cores"] >= 1
     assert rec["e2e"] == {"value": rec["value"], "unit": "ns/day", "h2d_bytes_per_step": 0,
                           "d2h_bytes_per_step": 0}
+    # the driver's K and W are honoured, and the workload is described exactly
+    # as in the GPU arm's line
+    assert rec["steps"] == 1 and rec["warmup"] == 0
+    assert rec["config"] == bench.run_config(*bench.make_workload("c0", 0))
+
+
+def test_output_errors_of_the_oracle_against_itself_vanish():
+    from oracle import reference as R
+    from paper_2608_12691_b300 import systems as S
+    d = S.make_c0()
+    lam = 0.6
+    _, _, res = bench.oracle_timed(d, 2, 1)
+    E, F0, Fuv, Fs, Ub, Fb = res
+    hA, hB, dA, dB = R.switching(lam)
+    terms = {"U": E["U_vv"] + E["U_uu"] + hA * E["U_uv"] + hB * E["U_soft"] + Ub,
+             "dUdl": dA * E["U_uv"] + dB * E["U_soft"], "U_vv": E["U_vv"], "U_uu": E["U_uu"],
+             "U_uv": E["U_uv"], "U_soft": E["U_soft"], "U_bonded": Ub}
+    F = F0 + hA * Fuv + hB * Fs + Fb
+    out = bench.output_errors(terms, F, res, lam, d["solute"])
+    assert out["F_rel_rms"] == 0.0 and out["F_rel_rms_solute"] == 0.0 and out["F_max_over_rms"] == 0.0
+    assert all(out[k]["abs"] == 0.0 for k in terms)
+    # a perturbed solute force shows in the solute norm far more than in the total
+    F2 = F.copy()
+    F2[np.flatnonzero(d["solute"])[0]] *= 1.0 + 1e-4
+    out2 = bench.output_errors(terms, F2, res, lam, d["solute"])
+    assert out2["F_rel_rms_solute"] > 2 * out2["F_rel_rms"] > 0

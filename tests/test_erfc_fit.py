@@ -9,7 +9,7 @@ import re
 import numpy as np
 from scipy.special import erfc
 
-from paper_2608_12691_b300 import fit_erfc
+import fit_erfc
 
 SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                    "paper_2608_12691_b300", "csrc", "nonbonded.cu")

@@ -17,7 +17,13 @@ from paper_2608_12691_b300 import systems as S
 
 pytestmark = pytest.mark.gpu
 
-TOL = {lfe.LFE_FP32_MIXED: dict(F=1e-5, dU=1e-6, E=1e-6), lfe.LFE_FP64: dict(F=1e-9, dU=1e-8, E=1e-9)}
+# F: relative RMS over all atoms and over the solute atoms alone (the solute
+# carries a small share of the total force, so a solute-only error would hide
+# in the global norm); Fmax: the largest error of any force component against
+# the RMS atomic force (ten times the RMS bound: FP32 sums of a few hundred
+# pair terms per atom)
+TOL = {lfe.LFE_FP32_MIXED: dict(F=1e-5, Fmax=1e-4, dU=1e-6, E=1e-6),
+       lfe.LFE_FP64: dict(F=1e-9, Fmax=1e-8, dU=1e-8, E=1e-9)}
 
 
 @functools.lru_cache(maxsize=None)
@@ -106,6 +112,13 @@ def check(key, lam, precision):
     Fo = o["F"]
     rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
     assert rel <= tol["F"], f"{key} lam={lam}: force rel RMS {rel:.3e}"
+    sol = np.asarray(d["solute"]).astype(bool)
+    if sol.any() and not sol.all():
+        rel_u = np.linalg.norm(F[sol] - Fo[sol]) / np.linalg.norm(Fo[sol])
+        assert rel_u <= tol["F"], f"{key} lam={lam}: solute force rel RMS {rel_u:.3e}"
+    f_rms = np.sqrt((Fo * Fo).sum(axis=1).mean())
+    emax = np.abs(F - Fo).max() / f_rms
+    assert emax <= tol["Fmax"], f"{key} lam={lam}: max force error {emax:.3e} of the RMS force"
     scale_dU = abs(o["dA"] * o["E"]["U_uv"]) + abs(o["dB"] * o["E"]["U_soft"])
     err_dU = abs(terms["dUdl"] - o["dUdl"])
     assert err_dU <= tol["dU"] * max(abs(o["dUdl"]), 1e-300) or err_dU <= 1e-12 * max(scale_dU, 1.0), \
@@ -148,7 +161,7 @@ def test_transform_shapes(key, precision):
 
 @pytest.mark.parametrize("key", ["c2", "c1", "c4"])
 def test_full_size_parity_fp32(key):
-    for lam in (0.1, 0.5, 0.9):
+    for lam in (0.1, 0.5, 0.6, 0.9, 1.0):
         check(key, lam, lfe.LFE_FP32_MIXED)
 
 
