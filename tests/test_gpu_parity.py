@@ -17,11 +17,15 @@ from paper_2608_12691_b300 import systems as S
 
 pytestmark = pytest.mark.gpu
 
-# F: relative RMS over all atoms and over the solute atoms alone (the solute
-# carries a small share of the total force, so a solute-only error would hide
-# in the global norm); Fmax: the largest error of any force component against
-# the RMS atomic force (ten times the RMS bound: FP32 sums of a few hundred
-# pair terms per atom)
+# F: relative RMS over all atoms, and over the solute atoms alone once the
+# solute is coupled (lambda >= 0.6: the solute carries a small share of the
+# total force, so a solute-only error would hide in the global norm; below,
+# a rigid solute with all intramolecular pairs excluded feels a small
+# remainder of cancelling reciprocal and exclusion-correction forces, and a
+# relative norm of that remainder measures cancellation, so there the solute
+# atoms' RMS error is held to F times the RMS atomic force of the system);
+# Fmax: the largest error of any force component against the RMS atomic force
+# (ten times the RMS bound: FP32 sums of a few hundred pair terms per atom)
 TOL = {lfe.LFE_FP32_MIXED: dict(F=1e-5, Fmax=1e-4, dU=1e-6, E=1e-6),
        lfe.LFE_FP64: dict(F=1e-9, Fmax=1e-8, dU=1e-8, E=1e-9)}
 
@@ -113,10 +117,13 @@ def check(key, lam, precision):
     rel = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
     assert rel <= tol["F"], f"{key} lam={lam}: force rel RMS {rel:.3e}"
     sol = np.asarray(d["solute"]).astype(bool)
-    if sol.any() and not sol.all():
-        rel_u = np.linalg.norm(F[sol] - Fo[sol]) / np.linalg.norm(Fo[sol])
-        assert rel_u <= tol["F"], f"{key} lam={lam}: solute force rel RMS {rel_u:.3e}"
     f_rms = np.sqrt((Fo * Fo).sum(axis=1).mean())
+    if sol.any() and not sol.all():
+        if lam >= 0.6:
+            rel_u = np.linalg.norm(F[sol] - Fo[sol]) / np.linalg.norm(Fo[sol])
+            assert rel_u <= tol["F"], f"{key} lam={lam}: solute force rel RMS {rel_u:.3e}"
+        err_u = np.sqrt(((F[sol] - Fo[sol]) ** 2).sum(axis=1).mean()) / f_rms
+        assert err_u <= tol["F"], f"{key} lam={lam}: solute force RMS error {err_u:.3e} of the RMS force"
     emax = np.abs(F - Fo).max() / f_rms
     assert emax <= tol["Fmax"], f"{key} lam={lam}: max force error {emax:.3e} of the RMS force"
     scale_dU = abs(o["dA"] * o["E"]["U_uv"]) + abs(o["dB"] * o["E"]["U_soft"])
