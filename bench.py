@@ -32,10 +32,10 @@ METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) o
 # Newton's third law 12 (58 in all; about two of them go to the special
 # function unit)
 FLOPS_PER_PAIR = 58
-# DRAM bytes (read + write) of one k_pairs<float> launch on the octanol workload, from an ncu
-# capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum); None until
-# the current version has been captured
-PAIR_DRAM_BYTES_OCTANOL = None
+# DRAM bytes (read + write) of one k_pairs2 launch on the octanol workload, from an ncu
+# capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum, 7.160 MB
+# read, 0 written); None whenever the kernel has changed since the capture
+PAIR_DRAM_BYTES_OCTANOL = 7.159552e6 + 0.0
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2032.0
 # timed evaluations of the reference arm at most (one level-2 oracle
@@ -492,7 +492,7 @@ def run_ours(args):
         peak = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
         traffic = PAIR_DRAM_BYTES_OCTANOL if (args.workload == "octanol" and prec == lfe.LFE_FP32_MIXED) else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_pairs<float>", "kernel_ms": pair_ms,
+                "traffic": traffic, "kernel": "k_pairs2 (FP32, packed f32x2)", "kernel_ms": pair_ms,
                 "flops_per_pair": FLOPS_PER_PAIR,
                 "peak_basis": f"{n_sm} SMs (device properties) x 128 FP32 lanes x 2 flop/FMA x 2032 MHz "
                               f"(max SM clock); unit-count peak, no measured FP32 peak in the pool's file"}

@@ -864,18 +864,10 @@ __device__ __forceinline__ PairConst<real> pair_const(const SysView<real>& s)
 // the half its partner does not: 12, 6, 3 values) and two final butterfly
 // steps; lane 4 k then holds atom k's totals and writes them.
 template <typename real>
-__device__ __forceinline__ void flush_i8(const SysView<real>& s, int I8, real (&fx)[8], real (&fy)[8],
-                                         real (&fz)[8])
+__device__ __forceinline__ void flush_i8_v(const SysView<real>& s, int I8, real (&v)[24])
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    real v[24];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        v[3 * k] = fx[k];
-        v[3 * k + 1] = fy[k];
-        v[3 * k + 2] = fz[k];
-    }
 #pragma unroll
     for (int h = 12, o = 16; h >= 3; h >>= 1, o >>= 1) {
         const bool up = (lane & o) != 0;
@@ -896,24 +888,102 @@ __device__ __forceinline__ void flush_i8(const SysView<real>& s, int I8, real (&
     }
 }
 
-// One warp walks a contiguous chunk of the (I8-sorted) tile list, one 8 x 32
-// tile at a time.  Lane l holds j entry l of the tile (its force in
-// registers); the tile's 8 i atoms are read one at a time from a per-warp
-// shared-memory record (broadcast), so every step pairs one i atom with the
-// 32 j atoms, and a step none of whose pairs lies within the cutoff is
-// skipped by the whole warp (the j atoms of a tile are neighbours in the
-// column sort, so such steps are common).  Each lane keeps its share of the
-// 8 i-forces in registers over consecutive tiles of the same I8 and the warp
-// adds them when I8 changes.  The tile's class (vv, uu or uv) and shift are
-// uniform, so the branches on them are warp-uniform.  Solute-solvent
-// energies are not accumulated here (k_uv_energy forms them in FP64).
-// 4 resident blocks per multiprocessor (110 registers in FP32, no spills;
-// 5 or 6 blocks measured slower), 3 in FP64.
 template <typename real>
-__global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs(SysView<real> s, NblView<real> nb)
+__device__ __forceinline__ void flush_i8(const SysView<real>& s, int I8, real (&fx)[8], real (&fy)[8],
+                                         real (&fz)[8])
 {
-    __shared__ R4<real> sxq[4][8];   // [warp][i atom] x, y, z (shifted for the tile), sqrt(k_e) q
-    __shared__ R2<real> slj[4][8];   // [warp][i atom] sigma/2, 2 sqrt(eps)
+    real v[24];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        v[3 * k] = fx[k];
+        v[3 * k + 1] = fy[k];
+        v[3 * k + 2] = fz[k];
+    }
+    flush_i8_v(s, I8, v);
+}
+
+// ---------------------------------------------------- packed FP32 pair kernel
+// Blackwell issues two FP32 fused multiply-adds, multiplies or adds as one
+// packed instruction (f32x2).  k_pairs2 evaluates the pairs of a lane's j
+// atom with i atoms k and k + 4 of the tile as the two halves of float2
+// values, so one step covers two pairs: half the steps and about half the
+// instructions of the scalar kernel.  Each half rounds exactly like the
+// scalar code (the packed operations are per component fmaf/fmul/fadd in
+// round-to-nearest); the special-function operations (rsqrt, reciprocal,
+// exp2) run once per half.
+__device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+// pair_force for two pairs: (r2, qq, sigma_ij, 4 eps_ij) per half; returns g
+// per half (force on i = -g d, on j = +g d) and the energy ec + v per half.
+// Solvent-solvent and solute-solute classes only (the solute-solvent tiles
+// take the scalar routine with the soft basis).
+__device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, float2 e4, const PairConst<float>& c,
+                                              float2& e)
+{
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 r = mul2(r2, rinv);
+    const float2 ri2 = mul2(rinv, rinv);
+    const float2 x = mul2(p2(c.alpha), r);
+    const float2 den = fma2(p2(0.345f), x, p2(1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    float2 pp = p2(-0.23825677533960984f);
+    pp = fma2(pp, t, p2(1.0079999846654213f));
+    pp = fma2(pp, t, p2(-1.1369167351186891f));
+    pp = fma2(pp, t, p2(1.1592655395537621f));
+    pp = fma2(pp, t, p2(-0.30407340842765385f));
+    pp = fma2(pp, t, p2(0.33999728300708898f));
+    pp = fma2(pp, t, p2(0.17020566942397877f));
+    pp = fma2(pp, t, p2(0.0017784231330017291f));
+    const float2 xx = mul2(x, x);
+    const float2 ex = make_float2(__expf(-xx.x), __expf(-xx.y));
+    const float2 erfcv = mul2(pp, ex);
+    const float2 ec = mul2(mul2(qq, erfcv), rinv);
+    const float2 fc = mul2(fma2(mul2(qq, p2(c.tas)), ex, ec), ri2);
+    const float2 s2 = mul2(mul2(sg, sg), ri2);
+    const float2 s6 = mul2(mul2(s2, s2), s2);
+    float2 v = mul2(e4, fma2(s6, s6, neg2(s6)));
+    float2 fl = mul2(mul2(e4, mul2(s6, fma2(s6, p2(12.0f), p2(-6.0f)))), ri2);
+    const float2 rr = fma2(r, p2(c.swi), p2(-c.rsw_swi));
+    const float2 tt = make_float2(fmaxf(0.0f, rr.x), fmaxf(0.0f, rr.y));
+    const float2 tt2 = mul2(tt, tt);
+    const float2 inner = fma2(fma2(tt, p2(6.0f), p2(-15.0f)), tt, p2(10.0f));
+    const float2 S = fma2(neg2(mul2(tt2, tt)), inner, p2(1.0f));
+    const float2 omt = add2(p2(1.0f), neg2(tt));
+    const float2 dS = mul2(mul2(tt2, mul2(omt, omt)), p2(-30.0f * c.swi));
+    fl = fma2(fl, S, neg2(mul2(mul2(v, dS), rinv)));
+    v = mul2(v, S);
+    e = add2(ec, v);
+    return add2(fc, fl);
+}
+
+// One warp walks a contiguous chunk of the (I8-sorted) tile list, one 8 x 32
+// tile at a time; lane l holds j entry l.  Step kk = 0..3 pairs the j atom
+// with i atoms kk and kk + 4 (read as float2 halves from a per-warp shared
+// record, shifted for the tile) and is skipped by the whole warp when none of
+// its 64 pairs lies within the cutoff.  A lane's share of the 8 i-forces is
+// kept as float2 in its own column of a per-warp shared array over the tiles
+// of one I8 and added over the warp when I8 changes; the j-force stays in
+// registers and is flushed at the end of every tile.  The tile's class and
+// shift are uniform, so the branches on them are warp-uniform; solute-solvent
+// tiles take the scalar routine with the soft basis (their energies are
+// formed in FP64 by k_uv_energy).
+// Launch shape, measured on the octanol box (13,520 atoms, one wave, CUDA
+// events): 8 resident blocks of 4 warps (62 registers, the i-forces in
+// shared memory) 41.5 us; the same with the i-forces in registers (117
+// registers, 4 blocks) 41.4 us but a slower step (0.149 against 0.142 ms: the
+// kernel shares the GPU with the PME and integrator branches); software
+// prefetch of the next tile's records 42.5 us; the scalar kernel 45.8 us.
+constexpr int PAIR2_MIN_BLOCKS = 8;
+
+__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float> s, NblView<float> nb)
+{
+    // [warp][kk] (x_kk, x_kk+4, y_kk, y_kk+4), (z.., z.., q.., q..), (sigma/2.., .., 2 sqrt(eps).., ..)
+    __shared__ float4 sA[4][4], sB[4][4], sC[4][4];
+    __shared__ float2 sfi[4][12][32];   // [warp][3 kk + component][lane]: i atoms kk (x) and kk + 4 (y)
     const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
@@ -922,67 +992,125 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs(SysVie
     const int t0 = (int)(((long long)ntiles * warp) / nwarp);
     const int t1 = (int)(((long long)ntiles * (warp + 1)) / nwarp);
     if (t0 >= t1) return;
-    const PairConst<real> c = pair_const(s);
+    const PairConst<float> c = pair_const(s);
+    float* fA = reinterpret_cast<float*>(sA[wl]);
+    float* fB = reinterpret_cast<float*>(sB[wl]);
+    float* fC = reinterpret_cast<float*>(sC[wl]);
+    float2(&fi)[12][32] = sfi[wl];
+    const int hk = (lane & 3) * 4 + ((lane >> 2) & 1);   // lanes 0-7: place of atom `lane` in the records
     int curI = -1;
-    R4<real> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
-    real fx[8], fy[8], fz[8];
-    real evv = 0, euu = 0;
+    R4<float> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
+    float evv = 0, euu = 0;
     int npairs = 0;
-    // the next tile's records are loaded while the current one is computed
-    int4 tl_n = nb.tiles[t0];
-    unsigned mk_n = nb.masks[(size_t)t0 * 32 + lane];
-    int sj_n = nb.jidx[(size_t)t0 * 32 + lane];
-    R4<real> pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
-    R2<real> lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
-    for (int t = t0; t < t1; ++t) {
-        const int4 tl = tl_n;
-        const unsigned mc = mk_n;
-        const int slot_j = sj_n;
-        R4<real> pj = pj_n;
-        const R2<real> ljv = lj_n;
-        if (t + 1 < t1) {
-            tl_n = nb.tiles[t + 1];
-            mk_n = nb.masks[(size_t)(t + 1) * 32 + lane];
-            sj_n = nb.jidx[(size_t)(t + 1) * 32 + lane];
-            pj_n = s.xq[sj_n >= 0 ? sj_n : 0];
-            lj_n = s.lj[sj_n >= 0 ? sj_n : 0];
+    auto flush_i = [&](int I8) {
+        float v[24];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 ax = fi[3 * k][lane], ay = fi[3 * k + 1][lane], az = fi[3 * k + 2][lane];
+            v[3 * k] = ax.x; v[3 * k + 1] = ay.x; v[3 * k + 2] = az.x;
+            v[3 * k + 12] = ax.y; v[3 * k + 13] = ay.y; v[3 * k + 14] = az.y;
         }
+        flush_i8_v(s, I8, v);
+    };
+    for (int t = t0; t < t1; ++t) {
+        const int4 tl = nb.tiles[t];
+        const unsigned mc = nb.masks[(size_t)t * 32 + lane];
+        const int slot_j = nb.jidx[(size_t)t * 32 + lane];
+        R4<float> pj = s.xq[slot_j >= 0 ? slot_j : 0];
+        const R2<float> ljv = s.lj[slot_j >= 0 ? slot_j : 0];
         if (tl.x != curI) {
-            if (curI >= 0) flush_i8(s, curI, fx, fy, fz);
+            if (curI >= 0) flush_i(curI);
             curI = tl.x;
             if (lane < 8) {
                 pown = s.xq[curI * 8 + lane];
-                slj[wl][lane] = s.lj[curI * 8 + lane];
+                const R2<float> l = s.lj[curI * 8 + lane];
+                fC[hk] = l.x;
+                fC[hk + 2] = l.y;
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) fx[k] = fy[k] = fz[k] = 0;
+            for (int m = 0; m < 12; ++m) fi[m][lane] = p2(0.0f);
         }
         const int sh = tl.y;
         const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
         // shift the far-side atom down by L so that the subtraction below is
         // the only rounding in the pair vector
-        if (lane < 8)
-            sxq[wl][lane] = R4<real>{sx == 1 ? pown.x - s.L[0] : pown.x, sy == 1 ? pown.y - s.L[1] : pown.y,
-                                     sz == 1 ? pown.z - s.L[2] : pown.z, pown.w};
+        if (lane < 8) {
+            fA[hk] = sx == 1 ? pown.x - s.L[0] : pown.x;
+            fA[hk + 2] = sy == 1 ? pown.y - s.L[1] : pown.y;
+            fB[hk] = sz == 1 ? pown.z - s.L[2] : pown.z;
+            fB[hk + 2] = pown.w;
+        }
         if (sx == -1) pj.x -= s.L[0];
         if (sy == -1) pj.y -= s.L[1];
         if (sz == -1) pj.z -= s.L[2];
         __syncwarp();
-        const bool uv = tl.z == 2;
-        real fjx = 0, fjy = 0, fjz = 0, e0 = 0;
+        const float2 jx = p2(pj.x), jy = p2(pj.y), jz = p2(pj.z);
+        float fjx, fjy, fjz, e0;
+        if (tl.z != 2) {
+            const float2 qj = p2(pj.w), sgj = p2(ljv.x), ej = p2(ljv.y);
+            float2 fj2x = p2(0.0f), fj2y = p2(0.0f), fj2z = p2(0.0f), e2 = p2(0.0f);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const R4<real> pi = sxq[wl][k];
-            const real dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-            const real r2 = dx * dx + dy * dy + dz * dz;
-            if (((mc >> k) & 1u) && r2 < c.rc2) {
-                const R2<real> li = slj[wl][k];
-                real ec, v;
-                const real g = pair_force(r2, pi.w * pj.w, li.x + ljv.x, li.y * ljv.y, uv, c, ec, v);
-                fx[k] -= g * dx; fy[k] -= g * dy; fz[k] -= g * dz;
-                fjx += g * dx; fjy += g * dy; fjz += g * dz;
-                e0 += ec + v;
-                ++npairs;
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 A = sA[wl][kk], B = sB[wl][kk];
+                const float2 dx = add2(jx, neg2(make_float2(A.x, A.y)));
+                const float2 dy = add2(jy, neg2(make_float2(A.z, A.w)));
+                const float2 dz = add2(jz, neg2(make_float2(B.x, B.y)));
+                const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                const bool in0 = ((mc >> kk) & 1u) && r2.x < c.rc2;
+                const bool in1 = ((mc >> (kk + 4)) & 1u) && r2.y < c.rc2;
+                if (in0 || in1) {
+                    // a half out of range is evaluated at r^2 = 1 and weighted by 0
+                    const float4 C = sC[wl][kk];
+                    const float2 rs = make_float2(in0 ? r2.x : 1.0f, in1 ? r2.y : 1.0f);
+                    const float2 m = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
+                    float2 e;
+                    float2 g = pair_force2(rs, mul2(make_float2(B.z, B.w), qj), add2(make_float2(C.x, C.y), sgj),
+                                           mul2(make_float2(C.z, C.w), ej), c, e);
+                    g = mul2(g, m);
+                    const float2 gx = mul2(g, dx), gy = mul2(g, dy), gz = mul2(g, dz);
+                    fi[3 * kk][lane] = add2(fi[3 * kk][lane], neg2(gx));
+                    fi[3 * kk + 1][lane] = add2(fi[3 * kk + 1][lane], neg2(gy));
+                    fi[3 * kk + 2][lane] = add2(fi[3 * kk + 2][lane], neg2(gz));
+                    fj2x = add2(fj2x, gx);
+                    fj2y = add2(fj2y, gy);
+                    fj2z = add2(fj2z, gz);
+                    e2 = fma2(e, m, e2);
+                    npairs += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+                }
+            }
+            fjx = fj2x.x + fj2x.y;
+            fjy = fj2y.x + fj2y.y;
+            fjz = fj2z.x + fj2z.y;
+            e0 = e2.x + e2.y;
+        } else {
+            // solute-solvent tile: the scalar routine with the soft basis, both halves
+            fjx = fjy = fjz = e0 = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 A = sA[wl][kk], B = sB[wl][kk], C = sC[wl][kk];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float ix = h ? A.y : A.x, iy = h ? A.w : A.z, iz = h ? B.y : B.x, iq = h ? B.w : B.z;
+                    const float isg = h ? C.y : C.x, ie = h ? C.w : C.z;
+                    const float dx = pj.x - ix, dy = pj.y - iy, dz = pj.z - iz;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    if (((mc >> (kk + 4 * h)) & 1u) && r2 < c.rc2) {
+                        float ec, v;
+                        const float g = pair_force(r2, iq * pj.w, isg + ljv.x, ie * ljv.y, true, c, ec, v);
+                        const float gx = g * dx, gy = g * dy, gz = g * dz;
+                        float2 f0 = fi[3 * kk][lane], f1 = fi[3 * kk + 1][lane], f2 = fi[3 * kk + 2][lane];
+                        if (h) {
+                            f0.y -= gx; f1.y -= gy; f2.y -= gz;
+                        } else {
+                            f0.x -= gx; f1.x -= gy; f2.x -= gz;
+                        }
+                        fi[3 * kk][lane] = f0;
+                        fi[3 * kk + 1][lane] = f1;
+                        fi[3 * kk + 2][lane] = f2;
+                        fjx += gx; fjy += gy; fjz += gz;
+                        ++npairs;
+                    }
+                }
             }
         }
         __syncwarp();
@@ -991,7 +1119,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs(SysVie
         if (tl.z == 0) evv += e0;
         else if (tl.z == 1) euu += e0;
     }
-    flush_i8(s, curI, fx, fy, fz);
+    flush_i(curI);
     const long long a0 = __double2ll_rn(warp_sum_d((double)evv) * ESCALE);
     const long long a1 = __double2ll_rn(warp_sum_d((double)euu) * ESCALE);
     const long long a4 = warp_sum_ll((long long)npairs);
@@ -1215,14 +1343,14 @@ void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nbloc
     k_uv_energy<real><<<nblocks, 256, 0, st>>>(s, nb);
 }
 
-// blocks of k_pairs resident on one multiprocessor (its grid is one wave)
+// blocks of the pair kernel resident on one multiprocessor (its grid is one wave)
 template <typename real>
 int pairs_blocks_per_sm()
 {
     int nb = 0;
     cudaError_t e;
     if constexpr (sizeof(real) == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs_listed<real>, 128, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs<real>, 128, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs2, 128, 0);
     if (e != cudaSuccess || nb < 1) nb = 1;
     return nb;
 }
@@ -1231,9 +1359,9 @@ template <typename real>
 void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st)
 {
     const int B = 128;
-    int blocks = (nwarps * 32 + B - 1) / B;
+    const int blocks = (nwarps * 32 + B - 1) / B;
     if constexpr (sizeof(real) == 8) k_pairs_listed<real><<<blocks, B, 0, st>>>(s, nb);
-    else k_pairs<real><<<blocks, B, 0, st>>>(s, nb);
+    else k_pairs2<<<blocks, B, 0, st>>>(s, nb);
 }
 
 // ------------------------------------------------- exclusions and 1-4 pairs
