@@ -502,29 +502,27 @@ def run_ours(args):
         roof["peak_measured_fma_fp32"] = f32_meas
         roof["peak_measured_fma_fp64"] = f64_meas
         roof["frac_of_measured_fma"] = achieved / f32_meas
-        # end to end through the public API with host buffers
+        # end to end through the public API with host buffers: one lfe_step_io
+        # per step (host-to-device copy of the positions, the step, and the
+        # device-to-host copies of positions, velocities and the scalar state,
+        # replayed as one captured graph), from and into page-locked memory
         e2e = None
         if args.e2e_steps > 0:
             pin_pos = torch.from_numpy(pos).pin_memory()
             pin_vel = torch.empty_like(pin_pos).pin_memory()
-            pin_ext = torch.zeros(lfe.NEXT, dtype=torch.float64).pin_memory()
-            # untimed warm-up of the same calls (the first state read sets up
-            # its packing buffers)
-            for _ in range(5):
-                g.set_positions_ptr(pin_pos.data_ptr(), 0, stream)
-                g.step(1, stream)
-                g.get_state_into(pin_pos.data_ptr(), pin_vel.data_ptr(), pin_ext.data_ptr())
+            ext_buf = np.zeros(lfe.NEXT)
+            for _ in range(5):      # untimed: the first call captures its graph
+                g.step_io(pin_pos.data_ptr(), pin_pos.data_ptr(), pin_vel.data_ptr(), ext_buf.ctypes.data, stream)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for _ in range(args.e2e_steps):
-                g.set_positions_ptr(pin_pos.data_ptr(), 0, stream)
-                g.step(1, stream)
-                g.get_state_into(pin_pos.data_ptr(), pin_vel.data_ptr(), pin_ext.data_ptr())
+                g.step_io(pin_pos.data_ptr(), pin_pos.data_ptr(), pin_vel.data_ptr(), ext_buf.ctypes.data, stream)
             te = (time.perf_counter() - t0) / args.e2e_steps
             n = len(d["charge"])
             e2e = {"value": dt_ps * 1e-3 * 86400.0 / te, "unit": "ns/day",
-                   "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 6 * n * 8 + lfe.NEXT * 8,
-                   "calls": "lfe_set_positions(host) + lfe_step(1) + lfe_get_state(host) per step"}
+                   "h2d_bytes_per_step": 3 * n * 8, "d2h_bytes_per_step": 6 * n * 8 + 16 * 8,
+                   "calls": "lfe_step_io per step: positions in, one step, positions + velocities + scalar state out "
+                            "(page-locked host buffers)"}
         fp64 = None
         if not args.no_fp64 and prec == lfe.LFE_FP32_MIXED:
             g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=2608)

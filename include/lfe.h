@@ -215,6 +215,26 @@ int lfe_step(lfe_system* sys, int n_steps, void* stream);
 #define LFE_NEXT 10
 int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext);
 
+/* One step with host input and output: the stepping of Section 2.6 with
+ * the configuration read back every step (the paper saves configurations
+ * every 200 fs; this serves callers that read or replace them every step),
+ * the equivalent of
+ * lfe_set_positions(pos_in, host) + lfe_step(1) + lfe_get_state(pos_out,
+ * vel_out, ext_out), replayed as one captured CUDA graph that holds the
+ * host-to-device copy, the step and the device-to-host copies, followed by
+ * one stream synchronisation.  pos_in [3N] (NULL: keep the device
+ * positions), pos_out [3N] and vel_out [3N] (either may be NULL) are host
+ * arrays in page-locked memory (cudaHostAlloc or cudaHostRegister;
+ * otherwise LFE_ERR_ARG), caller order; ext_out (ordinary host memory, may
+ * be NULL) receives the LFE_NEXT values of lfe_get_state.  pos_in is checked
+ * like lfe_set_positions (non-finite: LFE_ERR_ARG, nothing changed).  The
+ * graph is captured on the first call and again whenever the host pointers
+ * change.  A neighbour-list overflow inside the step is recovered (grow,
+ * rebuild, replay) before the call returns.  Returns after synchronising
+ * `stream`. */
+int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
+                void* stream);
+
 /* d-AFED (Eq. 15): n_cv torsions xi_k (atoms[4k .. 4k+3], the IUPAC sign:
  * atan2(|b2| b1 . (b2 x b3), (b1 x b2) . (b2 x b3)) with b1 = r_j - r_i,
  * b2 = r_k - r_j, b3 = r_l - r_k, minimum images) are coupled to auxiliary

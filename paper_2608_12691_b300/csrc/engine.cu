@@ -107,6 +107,8 @@ struct SystemBase {
     virtual void autotune(int reps, const char* cache_path, double* best_ms, int* params) = 0;
     virtual void set_theta(double theta, double p_theta) = 0;
     virtual void set_list_capacity(int tiles) = 0;
+    virtual void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
+                         cudaStream_t st) = 0;
     virtual void lambda_state(double* lam, double* mass) = 0;
     unsigned generation = 0;   // bumped whenever device buffers are reallocated
 };
@@ -187,6 +189,9 @@ struct System final : SystemBase {
         if (graph) cudaGraphDestroy(graph);
         if (pos_exec) cudaGraphExecDestroy(pos_exec);
         if (pos_graph) cudaGraphDestroy(pos_graph);
+        if (io_exec) cudaGraphExecDestroy(io_exec);
+        if (io_graph) cudaGraphDestroy(io_graph);
+        if (h_io_tail) cudaFreeHost(h_io_tail);
         for (void* p : allocs) cudaFree(p);
         if (h_flags) cudaFreeHost(h_flags);
         if (h_state) cudaFreeHost(h_state);
@@ -1397,6 +1402,113 @@ struct System final : SystemBase {
         CK(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
     }
 
+    // One step with host input and output as one captured graph: the copy of
+    // the new positions from page-locked host memory, their assignment and
+    // rebuild decision (as lfe_set_positions), the step (as lfe_step), the
+    // state packing and the copies into the caller's page-locked buffers (as
+    // lfe_get_state).  The graph is specific to the host pointers and is
+    // recaptured when they or the device buffers change.
+    cudaGraph_t io_graph = nullptr;
+    cudaGraphExec_t io_exec = nullptr;
+    const void* io_key[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned io_gen = ~0u;
+    double* h_io_tail = nullptr;   // pinned copy of the scalar state of the last io step
+
+    static bool host_pinned(const void* p)
+    {
+        if (!p) return true;
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return a.type == cudaMemoryTypeHost;
+    }
+
+    void capture_io_graph(const double* pos_in, double* pos_out, double* vel_out)
+    {
+        if (io_exec) { cudaGraphExecDestroy(io_exec); io_exec = nullptr; }
+        if (io_graph) { cudaGraphDestroy(io_graph); io_graph = nullptr; }
+        const size_t nv = 3 * (size_t)n;
+        cudaStream_t s0 = cs;
+        CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
+        if (pos_in) {
+            cudaGraphConditionalHandle hp;
+            CK(cudaGraphConditionalHandleCreate(&hp, g, 0, cudaGraphCondAssignDefault));
+            CK(cudaMemcpyAsync(d_pos, pos_in, sizeof(double) * nv, cudaMemcpyHostToDevice, s0));
+            launch_assign_positions(S, d_pos, s0);
+            launch_moved(S, G.skin_half2, hp, s0);
+            add_cond_build(s0, hp);
+        }
+        cudaGraphConditionalHandle h;
+        CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+        eval_kernels_branched(s0, &T, &h);
+        CK(cudaEventRecord(ev_fork, s0));
+        CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
+        launch_theta(S, T, br[0]);
+        launch_dafed_step(S, D, br[0]);
+        CK(cudaEventRecord(ev_join[0], br[0]));
+        launch_integrate(S, G, s0);
+        CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
+        launch_pack_state(S, T.st, d_state, s0);
+        CK(cudaMemcpyAsync(h_io_tail, d_state + 2 * nv, sizeof(double) * 16, cudaMemcpyDeviceToHost, s0));
+        if (pos_out) CK(cudaMemcpyAsync(pos_out, d_state, sizeof(double) * nv, cudaMemcpyDeviceToHost, s0));
+        if (vel_out) CK(cudaMemcpyAsync(vel_out, d_state + nv, sizeof(double) * nv, cudaMemcpyDeviceToHost, s0));
+        CK(cudaStreamEndCapture(s0, &io_graph));
+        CK(cudaGraphInstantiate(&io_exec, io_graph, cudaGraphInstantiateFlagUseNodePriority));
+        io_key[0] = pos_in;
+        io_key[1] = pos_out;
+        io_key[2] = vel_out;
+        io_gen = generation;
+    }
+
+    void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out, cudaStream_t st) override
+    {
+        if (!(P.dt > 0)) fail(LFE_ERR_STATE, "dt must be positive to step");
+        if (!host_pinned(pos_in) || !host_pinned(pos_out) || !host_pinned(vel_out))
+            fail(LFE_ERR_ARG, "host buffers of lfe_step_io must be page-locked");
+        if (pos_in && !finite_all(pos_in, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
+        if (eager || pos_pending || since_check > 0) {
+            // a queued overflow or pending position update is settled first
+            CK(cudaStreamSynchronize(st));
+            if (exec) recover_overflow(st);
+            if (pos_pending) settle_positions(st);
+            pos_pending = false;
+        }
+        if (eager) {
+            if (pos_in) set_positions(pos_in, 0, st);
+            step(1, st);
+            get_state(pos_out, vel_out, ext_out);
+            return;
+        }
+        if (!d_state) {
+            d_state = dalloc<double>(6 * (size_t)n + 16);
+            CK(cudaMallocHost(&h_state, sizeof(double) * (6 * (size_t)n + 16)));
+        }
+        if (!h_io_tail) CK(cudaMallocHost(&h_io_tail, sizeof(double) * 16));
+        if (!io_exec || io_gen != generation || io_key[0] != pos_in || io_key[1] != pos_out || io_key[2] != vel_out)
+            capture_io_graph(pos_in, pos_out, vel_out);
+        CK(cudaGraphLaunch(io_exec, st));
+        ++steps_requested;
+        CK(cudaStreamSynchronize(st));
+        const int err = (int)h_io_tail[10];
+        if (err) {
+            // the step was skipped (list overflow) or failed: the general path
+            // settles it and reads the state again
+            if (err & ERRB_OVERFLOW) {
+                if (!exec) capture_step_graph();
+                recover_overflow(st);
+            }
+            get_state(pos_out, vel_out, ext_out);
+            return;
+        }
+        if (ext_out)
+            for (int k = 0; k < LFE_NEXT; ++k) ext_out[k] = h_io_tail[k];
+    }
+
     // steps requested through lfe_step since creation, and launches since
     // the last overflow check
     unsigned long long steps_requested = 0;
@@ -2206,6 +2318,12 @@ int lfe_set_theta(lfe_system* sys, double theta, double p_theta)
 int lfe_set_list_capacity(lfe_system* sys, int tiles)
 {
     return guard(sys, [&] { sys->impl->set_list_capacity(tiles); });
+}
+
+int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
+                void* stream)
+{
+    return guard(sys, [&] { sys->impl->step_io(pos_in, pos_out, vel_out, ext_out, (cudaStream_t)stream); });
 }
 
 namespace {
