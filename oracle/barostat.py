@@ -15,8 +15,10 @@ standard Metropolis volume move it refers to:
 The N_mol ln(V'/V) term is the Jacobian of the scaled molecular centres; with
 it the chain samples p(V) proportional to V^N_mol exp(-beta (U + P V)).
 Reading: the centre that is scaled is the centre of mass (the published
-method allows any fixed molecular reference point; the Jacobian is the same).
-The CUDA path has no barostat yet.
+method allows any fixed molecular reference point; the Jacobian is the same);
+a molecule whose atoms are all massless (the frozen rigid solutes of the
+dynamics workloads) is scaled about its geometric centre, so that it keeps its
+shape and moves with the box.
 """
 import math
 
@@ -62,7 +64,8 @@ def scale_molecules(pos, mass, mol, box, s):
         idx = np.flatnonzero(mol == m)
         d = pos[idx] - pos[idx[0]]
         d -= box * np.round(d / box)                 # whole molecule
-        w = mass[idx] / mass[idx].sum()
+        mt = mass[idx].sum()
+        w = mass[idx] / mt if mt > 0.0 else np.full(idx.size, 1.0 / idx.size)
         com = pos[idx[0]] + (w[:, None] * d).sum(axis=0)
         out[idx] = s * com + (d - (w[:, None] * d).sum(axis=0))
     return out, s * box

@@ -93,3 +93,25 @@ def test_rejects_nonpositive_volume():
     out = B.volume_move(pos, box, np.ones(1), np.zeros(1, dtype=int), lambda x, b: 0.0, 0.0, 1.0, 2.5,
                         10.0, 0.0, 0.0)
     assert out[3] is False and out[1] is box
+
+
+def test_massless_molecule_scales_about_its_geometric_centre():
+    # a frozen rigid molecule (all masses 0) keeps its shape and its
+    # geometric centre scales with the box
+    box = np.array([3.0, 3.0, 3.0])
+    ring = np.array([[0.14 * np.cos(a), 0.14 * np.sin(a), 0.0] for a in np.linspace(0, 2 * np.pi, 6, endpoint=False)])
+    pos = np.vstack([ring + np.array([2.9, 1.0, 1.5]), [[0.5, 0.5, 0.5]]])
+    pos -= box * np.floor(pos / box)                 # split across the x face
+    mass = np.array([0.0] * 6 + [12.0])
+    mol = np.array([0] * 6 + [1])
+    s = 0.97
+    new, box_new = B.scale_molecules(pos, mass, mol, box, s)
+    d0 = pos[:6] - pos[0]
+    d0 -= box * np.round(d0 / box)
+    d1 = new[:6] - new[0]
+    d1 -= box_new * np.round(d1 / box_new)
+    assert np.allclose(d1, d0, atol=1e-12)
+    c0 = pos[0] + d0.mean(axis=0)
+    c1 = new[0] + d1.mean(axis=0)
+    assert np.allclose(c1, s * c0, atol=1e-12)
+    assert np.allclose(new[6], s * pos[6], atol=1e-12)
