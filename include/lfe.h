@@ -215,6 +215,29 @@ int lfe_step(lfe_system* sys, int n_steps, void* stream);
 #define LFE_NEXT 10
 int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext);
 
+/* Monte Carlo volume move (Section 2.6: the runs are isothermal-isobaric
+ * with a Monte Carlo barostat, Aqvist et al. 2004; the paper gives no
+ * equations): at the current lambda, V' = V + dv_max (2 u0 - 1) (nm^3);
+ * every box edge scales by s = (V'/V)^(1/3) and every molecule's centre of
+ * mass by s with its atoms moved rigidly (molecules = connected components
+ * of the exclusion list; a molecule of massless atoms scales about its
+ * geometric centre); accepted with probability min(1, exp(-(U' - U +
+ * P (V' - V)) / k_B T + N_mol ln(V'/V))), U the evaluation's potential energy
+ * at the current lambda, T the atoms' temperature, P in bar.  u0 and the
+ * acceptance uniform u1 are the first two words of Philox4x32-10 at counter
+ * (attempt_lo, attempt_hi, 0, 4) with key seed, as (x + 0.5) / 2^32.  A move
+ * whose box would break r_cut <= L/2, or V' <= 0, is rejected.  A rejected
+ * move restores positions and box exactly; an accepted one recomputes the
+ * box-dependent tables and constants, rebuilds the neighbour list and
+ * recaptures the step graph.  Velocities are unchanged.  Outputs (host, any
+ * may be NULL): accepted (0/1), box_out [3] (the box after the move),
+ * energies [2] (U before, U at the proposed state; equal when rejected before
+ * evaluation).  Synchronises the device.  Checkpoints store the box.
+ * Errors: LFE_ERR_ARG (non-finite pressure, dv_max <= 0), LFE_ERR_STATE
+ * (temperature <= 0). */
+int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsigned long long seed,
+                       unsigned long long attempt, int* accepted, double* box_out, double* energies);
+
 /* One step with host input and output: the stepping of Section 2.6 with
  * the configuration read back every step (the paper saves configurations
  * every 200 fs; this serves callers that read or replace them every step),

@@ -161,6 +161,59 @@ __global__ void k_moved(SysView<real> s, real skin_half2)
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_REBUILD], 1);
 }
 
+// Monte Carlo volume move (the NPT runs of Section 2.6): every molecule's
+// centre of mass (its geometric centre when all its atoms are massless) is
+// scaled by sc, its atoms moved rigidly with it; offsets from the molecule's
+// first atom are taken under the minimum image of the old box, in FP64.
+// One thread per molecule (molecules as CSR over caller-order atoms).
+template <typename real>
+__global__ void k_scale_molecules(SysView<real> s, const int* mstart, const int* matoms, const double* mass,
+                                  int n_mol, double sc, double L0, double L1, double L2)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n_mol) return;
+    const int b = mstart[m], e = mstart[m + 1];
+    const double L[3] = {L0, L1, L2};
+    const R4<real> p0r = s.x[matoms[b]];
+    const double p0[3] = {(double)p0r.x, (double)p0r.y, (double)p0r.z};
+    double c[3] = {0, 0, 0}, cu[3] = {0, 0, 0}, wsum = 0;
+    for (int k = b; k < e; ++k) {
+        const R4<real> p = s.x[matoms[k]];
+        const double w = mass[matoms[k]];
+        const double pv[3] = {(double)p.x, (double)p.y, (double)p.z};
+        for (int d = 0; d < 3; ++d) {
+            double dd = pv[d] - p0[d];
+            dd -= L[d] * rint(dd / L[d]);
+            c[d] += w * dd;
+            cu[d] += dd;
+        }
+        wsum += w;
+    }
+    const int na = e - b;
+    for (int d = 0; d < 3; ++d) c[d] = wsum > 0.0 ? c[d] / wsum : cu[d] / na;
+    for (int k = b; k < e; ++k) {
+        const int a = matoms[k];
+        const R4<real> p = s.x[a];
+        const double pv[3] = {(double)p.x, (double)p.y, (double)p.z};
+        double q[3];
+        for (int d = 0; d < 3; ++d) {
+            double dd = pv[d] - p0[d];
+            dd -= L[d] * rint(dd / L[d]);
+            q[d] = sc * (p0[d] + c[d]) + (dd - c[d]);
+        }
+        s.x[a] = R4<real>{(real)q[0], (real)q[1], (real)q[2], p.w};
+    }
+}
+
+template <typename real>
+void launch_scale_molecules(const SysView<real>& s, const int* mstart, const int* matoms, const double* mass,
+                            int n_mol, double sc, const double* L, cudaStream_t st)
+{
+    if (n_mol == 0) return;
+    k_scale_molecules<real><<<(n_mol + 127) / 128, 128, 0, st>>>(s, mstart, matoms, mass, n_mol, sc, L[0], L[1],
+                                                                    L[2]);
+}
+
 // positions, velocities (caller order, doubles) and the scalar state in one
 // buffer, so that lfe_get_state needs one copy: out[0, 3n) x, [3n, 6n) v,
 // then theta, p_theta, lambda, dU/dlambda, U, kernels of both biases, step,
@@ -904,6 +957,8 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
     template void launch_moved<real>(const SysView<real>&, real, cudaGraphConditionalHandle, cudaStream_t); \
     template void launch_pack_state<real>(const SysView<real>&, const OpesState*, double*, cudaStream_t);   \
+    template void launch_scale_molecules<real>(const SysView<real>&, const int*, const int*, const double*, int, \
+                                               double, const double*, cudaStream_t);                         \
     template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
     template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
     template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \

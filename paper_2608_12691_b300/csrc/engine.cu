@@ -39,6 +39,20 @@ struct Failure {
 
 [[noreturn]] void fail(int code, const std::string& m) { throw Failure{code, m}; }
 
+// Philox4x32-10 (Salmon et al. 2011) on the host, for the uniforms of the
+// lambda exchange and the Monte Carlo volume move
+void philox_host(unsigned c[4], unsigned k0, unsigned k1)
+{
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = 0xD2511F53ull * c[0], p1 = 0xCD9E8D57ull * c[2];
+        const unsigned n0 = (unsigned)(p1 >> 32) ^ c[1] ^ k0, n1 = (unsigned)p1;
+        const unsigned n2 = (unsigned)(p0 >> 32) ^ c[3] ^ k1, n3 = (unsigned)p0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
 // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so one
 // branch-free (vectorisable) sum answers for the whole array
 bool finite_all(const double* a, size_t n)
@@ -110,6 +124,8 @@ struct SystemBase {
     virtual void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                          cudaStream_t st) = 0;
     virtual void lambda_state(double* lam, double* mass) = 0;
+    virtual void mc_volume_move(double pressure_bar, double dv_max, unsigned long long seed,
+                                unsigned long long attempt, int* accepted, double* box_out, double* energies) = 0;
     unsigned generation = 0;   // bumped whenever device buffers are reallocated
 };
 
@@ -395,6 +411,7 @@ struct System final : SystemBase {
             std::vector<int> mol(n);
             for (int i = 0; i < n; ++i) mol[i] = find(i);
             N.mol = upload(mol);
+            h_mol = mol;
         }
 
         // ---------------------------------------------------- exclusions
@@ -451,20 +468,8 @@ struct System final : SystemBase {
                 // |b(m)|^2 with the order-4 spline values M4(1) = 1/6, M4(2) = 2/3, M4(3) = 1/6
                 std::vector<double> gf(K), ms(K);
                 std::vector<R2<double>> tw(K);
-                for (int m = 0; m < K; ++m) {
-                    double re = 0, im = 0;
-                    const double mk[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
-                    for (int k = 0; k < 3; ++k) {
-                        re += mk[k] * std::cos(2.0 * PI * m * k / K);
-                        im += mk[k] * std::sin(2.0 * PI * m * k / K);
-                    }
-                    const double b2 = 1.0 / (re * re + im * im);
-                    const int mm = (m <= K / 2) ? m : m - K;
-                    const double mr = mm / p.box[d];
-                    gf[m] = std::exp(-PI * PI * mr * mr / (p.ewald_alpha * p.ewald_alpha)) * b2;
-                    ms[m] = mr * mr;
-                    tw[m] = R2<double>{std::cos(2.0 * PI * m / K), std::sin(2.0 * PI * m / K)};
-                }
+                pme_axis_tables(K, p.box[d], gf, ms);
+                for (int m = 0; m < K; ++m) tw[m] = R2<double>{std::cos(2.0 * PI * m / K), std::sin(2.0 * PI * m / K)};
                 std::vector<real> gfr(K), msr(K);
                 std::vector<R2<real>> twr(K);
                 for (int m = 0; m < K; ++m) {
@@ -767,6 +772,26 @@ struct System final : SystemBase {
 
     // self and neutralising-background energies of each class (they depend
     // on the charges only)
+    // influence-function factor exp(-pi^2 m^2 / alpha^2) |b(m)|^2 and m^2 of
+    // one axis (m = k / L for k <= K/2, (k - K) / L above) with the order-4
+    // B-spline moduli |b(m)|^-2 = |sum_{k=0..2} M4(k+1) e^{2 pi i m k / K}|^2
+    void pme_axis_tables(int K, double L, std::vector<double>& gf, std::vector<double>& ms) const
+    {
+        for (int m = 0; m < K; ++m) {
+            double re = 0, im = 0;
+            const double mk[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+            for (int k = 0; k < 3; ++k) {
+                re += mk[k] * std::cos(2.0 * PI * m * k / K);
+                im += mk[k] * std::sin(2.0 * PI * m * k / K);
+            }
+            const double b2 = 1.0 / (re * re + im * im);
+            const int mm = (m <= K / 2) ? m : m - K;
+            const double mr = mm / L;
+            gf[m] = std::exp(-PI * PI * mr * mr / (P.ewald_alpha * P.ewald_alpha)) * b2;
+            ms[m] = mr * mr;
+        }
+    }
+
     void constant_energies()
     {
         std::vector<unsigned char> is_u(n, 0);
@@ -1335,6 +1360,156 @@ struct System final : SystemBase {
         CK(cudaMemcpy(S.lam, &L, sizeof(L), cudaMemcpyHostToDevice));
     }
 
+    // ---------------------------------------------------- barostat
+    // Molecules (connected components of the exclusion graph, numbered in
+    // order of their lowest atom) as CSR over caller-order atoms, and the
+    // masses in FP64, set up on the first volume move.
+    std::vector<int> h_mol;
+    int n_mol = 0;
+    int* d_mstart = nullptr;
+    int* d_matoms = nullptr;
+    double* d_mass = nullptr;
+    R4<real>* d_xsave = nullptr;
+
+    void setup_molecules()
+    {
+        if (d_mstart) return;
+        std::vector<int> id(n, -1), order;
+        std::vector<int> root_id(n, -1);
+        for (int i = 0; i < n; ++i) {
+            const int r = h_mol[i];
+            if (root_id[r] < 0) root_id[r] = n_mol++;
+            id[i] = root_id[r];
+        }
+        std::vector<int> start(n_mol + 1, 0), atoms(n);
+        for (int i = 0; i < n; ++i) start[id[i] + 1]++;
+        for (int m = 0; m < n_mol; ++m) start[m + 1] += start[m];
+        std::vector<int> fill(n_mol, 0);
+        for (int i = 0; i < n; ++i) atoms[start[id[i]] + fill[id[i]]++] = i;
+        d_mstart = upload(start);
+        d_matoms = upload(atoms);
+        d_mass = upload(h_mass);
+        d_xsave = dalloc<R4<real>>(n);
+    }
+
+    // New box lengths: every box-dependent table and constant follows (the
+    // column geometry keeps its column counts, the reciprocal-space tables,
+    // grid scales, convolution prefactor and the self / background energies
+    // are recomputed), graphs are recaptured and the neighbour list is
+    // rebuilt by the next step or evaluation.
+    void set_box(const double* box)
+    {
+        for (int d = 0; d < 3; ++d) {
+            if (!(box[d] > 0) || !std::isfinite(box[d])) fail(LFE_ERR_ARG, "box lengths must be positive");
+            if (!(P.r_cut <= 0.5 * box[d])) fail(LFE_ERR_ARG, "r_cut must not exceed half of every box length");
+        }
+        CK(cudaDeviceSynchronize());
+        for (int d = 0; d < 3; ++d) {
+            P.box[d] = box[d];
+            S.L[d] = (real)box[d];
+            S.invL[d] = (real)(1.0 / box[d]);
+        }
+        N.cinvx = (real)(N.ncx / box[0]);
+        N.cinvy = (real)(N.ncy / box[1]);
+        const double V = box[0] * box[1] * box[2];
+        for (int d = 0; d < 3; ++d) {
+            const int K = M.K[d];
+            std::vector<double> gf(K), ms(K);
+            pme_axis_tables(K, box[d], gf, ms);
+            std::vector<real> gfr(K), msr(K);
+            for (int m = 0; m < K; ++m) {
+                gfr[m] = (real)gf[m];
+                msr[m] = (real)ms[m];
+            }
+            CK(cudaMemcpy(const_cast<real*>(M.gfac[d]), gfr.data(), sizeof(real) * K, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(const_cast<real*>(M.msq[d]), msr.data(), sizeof(real) * K, cudaMemcpyHostToDevice));
+            M.kscale[d] = (real)(K / box[d]);
+            M.kscale64[d] = K / box[d];
+            if (dual) {
+                CK(cudaMemcpy(const_cast<double*>(M64.gfac[d]), gf.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(const_cast<double*>(M64.msq[d]), ms.data(), sizeof(double) * K, cudaMemcpyHostToDevice));
+                std::vector<df64> gf2(K), ms2(K);
+                for (int m = 0; m < K; ++m) {
+                    gf2[m] = df64(gf[m]);
+                    ms2[m] = df64(ms[m]);
+                }
+                CK(cudaMemcpy(const_cast<df64*>(M2.gfac[d]), gf2.data(), sizeof(df64) * K, cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(const_cast<df64*>(M2.msq[d]), ms2.data(), sizeof(df64) * K, cudaMemcpyHostToDevice));
+                M64.kscale[d] = K / box[d];
+                M64.kscale64[d] = K / box[d];
+                M2.kscale[d] = df64(K / box[d]);
+                M2.kscale64[d] = K / box[d];
+            }
+        }
+        M.conv_pre = (real)(KE / (PI * V));
+        if (dual) {
+            M64.conv_pre = KE / (PI * V);
+            M2.conv_pre = df64(KE / (PI * V));
+        }
+        constant_energies();
+        const int one = 1;
+        CK(cudaMemcpy(S.flags + FL_REBUILD, &one, sizeof(int), cudaMemcpyHostToDevice));
+        invalidate_graph();
+        ++generation;
+    }
+
+    // One Monte Carlo volume move at the current lambda (Section 2.6's NPT
+    // runs; Aqvist et al. 2004): V' = V + dv_max (2 u0 - 1), every molecule
+    // scaled about its centre of mass, accepted with probability
+    // min(1, exp(-(U' - U + P (V' - V)) / kT + N_mol ln(V'/V))), with u0 and
+    // the acceptance uniform u1 the first two words of Philox4x32-10 at
+    // counter (attempt_lo, attempt_hi, 0, 4) and key seed, as (x + 0.5) / 2^32.
+    // A rejected move restores the positions and the box exactly.
+    void mc_volume_move(double pressure_bar, double dv_max, unsigned long long seed, unsigned long long attempt,
+                        int* accepted, double* box_out, double* energies) override
+    {
+        if (!std::isfinite(pressure_bar) || !(dv_max > 0) || !std::isfinite(dv_max))
+            fail(LFE_ERR_ARG, "pressure must be finite and dv_max positive");
+        if (!(P.temperature > 0)) fail(LFE_ERR_STATE, "the barostat needs a positive temperature");
+        setup_molecules();
+        double lam = 0.0;
+        lambda_state(&lam, nullptr);
+        double t0[LFE_NTERMS], t1[LFE_NTERMS];
+        eval(lam, nullptr, t0, 0, nullptr);
+        unsigned c[4] = {(unsigned)attempt, (unsigned)(attempt >> 32), 0u, 4u};
+        philox_host(c, (unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+        const double u0 = (c[0] + 0.5) / 4294967296.0, u1 = (c[1] + 0.5) / 4294967296.0;
+        const double box0[3] = {P.box[0], P.box[1], P.box[2]};
+        const double V = box0[0] * box0[1] * box0[2];
+        const double Vn = V + dv_max * (2.0 * u0 - 1.0);
+        bool acc = false;
+        double U1 = t0[0];
+        if (Vn > 0.0) {
+            const double sc = std::cbrt(Vn / V);
+            const double box1[3] = {sc * box0[0], sc * box0[1], sc * box0[2]};
+            bool fits = true;
+            for (int d = 0; d < 3; ++d) fits = fits && P.r_cut <= 0.5 * box1[d];
+            if (fits) {
+                CK(cudaMemcpy(d_xsave, S.x, sizeof(R4<real>) * n, cudaMemcpyDeviceToDevice));
+                launch_scale_molecules(S, d_mstart, d_matoms, d_mass, n_mol, sc, box0, nullptr);
+                CK(cudaGetLastError());
+                set_box(box1);
+                eval(lam, nullptr, t1, 0, nullptr);
+                U1 = t1[0];
+                const double kT = 0.0083144626 * P.temperature;
+                const double Pk = pressure_bar * 0.0602214076;
+                const double x = -(U1 - t0[0] + Pk * (Vn - V)) / kT + n_mol * std::log(Vn / V);
+                acc = u1 < (x >= 0.0 ? 1.0 : std::exp(x));
+                if (!acc) {
+                    CK(cudaMemcpy(S.x, d_xsave, sizeof(R4<real>) * n, cudaMemcpyDeviceToDevice));
+                    set_box(box0);
+                }
+            }
+        }
+        if (accepted) *accepted = acc ? 1 : 0;
+        if (box_out)
+            for (int d = 0; d < 3; ++d) box_out[d] = P.box[d];
+        if (energies) {
+            energies[0] = t0[0];
+            energies[1] = U1;
+        }
+    }
+
     void lambda_state(double* lam, double* mass) override
     {
         CK(cudaDeviceSynchronize());
@@ -1766,6 +1941,7 @@ struct System final : SystemBase {
     struct CkHeader {
         char magic[8];
         int version, precision, n, max_k, n_cv, pad;
+        double box[3];
     };
 
     void checkpoint(const char* path) override
@@ -1774,8 +1950,9 @@ struct System final : SystemBase {
         check_flags(nullptr);
         CkHeader h{};
         std::memcpy(h.magic, "LFECKPT1", 8);
-        h.version = 2;
+        h.version = 3;
         h.precision = precision;
+        for (int d = 0; d < 3; ++d) h.box[d] = P.box[d];
         h.n = n;
         h.max_k = T.max_k;
         h.n_cv = D.n;
@@ -1831,9 +2008,10 @@ struct System final : SystemBase {
         if (stored != fnv1a(buf.data(), body)) fail(LFE_ERR_ARG, "checkpoint checksum mismatch");
         CkHeader h;
         std::memcpy(&h, buf.data(), sizeof(h));
-        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 2 || h.precision != precision || h.n != n ||
+        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 3 || h.precision != precision || h.n != n ||
             h.max_k != T.max_k || h.n_cv != D.n)
             fail(LFE_ERR_ARG, "checkpoint header does not match this system");
+        if (h.box[0] != P.box[0] || h.box[1] != P.box[1] || h.box[2] != P.box[2]) set_box(h.box);
         size_t off = sizeof(CkHeader);
         auto get_dev = [&](void* d, size_t sz) {
             CK(cudaMemcpy(d, buf.data() + off, sz, cudaMemcpyHostToDevice));
@@ -2320,26 +2498,20 @@ int lfe_set_list_capacity(lfe_system* sys, int tiles)
     return guard(sys, [&] { sys->impl->set_list_capacity(tiles); });
 }
 
+int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsigned long long seed,
+                       unsigned long long attempt, int* accepted, double* box_out, double* energies)
+{
+    return guard(sys, [&] { sys->impl->mc_volume_move(pressure_bar, dv_max, seed, attempt, accepted, box_out,
+                                                       energies); });
+}
+
 int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                 void* stream)
 {
     return guard(sys, [&] { sys->impl->step_io(pos_in, pos_out, vel_out, ext_out, (cudaStream_t)stream); });
 }
 
-namespace {
-// Philox4x32-10 (Salmon et al. 2011) on the host, for the exchange uniforms
-void philox_host(unsigned c[4], unsigned k0, unsigned k1)
-{
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = 0xD2511F53ull * c[0], p1 = 0xCD9E8D57ull * c[2];
-        const unsigned n0 = (unsigned)(p1 >> 32) ^ c[1] ^ k0, n1 = (unsigned)p1;
-        const unsigned n2 = (unsigned)(p0 >> 32) ^ c[3] ^ k1, n3 = (unsigned)p0;
-        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-}
-}  // namespace
+
 
 int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out)
 {

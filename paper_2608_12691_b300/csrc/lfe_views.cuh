@@ -290,6 +290,9 @@ template <typename real> void launch_assign_positions(const SysView<real>& s, co
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
 // refresh the sorted copy after new positions and set conditional h to
 // "rebuild" when an atom has moved more than skin/2 since the last build
+template <typename real> void launch_scale_molecules(const SysView<real>& s, const int* mstart, const int* matoms,
+                                                     const double* mass, int n_mol, double sc, const double* L,
+                                                     cudaStream_t st);
 template <typename real> void launch_pack_state(const SysView<real>& s, const OpesState* o, double* out,
                                                 cudaStream_t st);
 template <typename real> void launch_moved(const SysView<real>& s, real skin_half2, cudaGraphConditionalHandle h,

@@ -31,7 +31,7 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
     "lfe_batch_exchange", "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
@@ -135,6 +135,9 @@ def load():
     lib.lfe_set_list_capacity.restype = ctypes.c_int
     lib.lfe_step_io.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.lfe_step_io.restype = ctypes.c_int
+    lib.lfe_mc_volume_move.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_ulonglong,
+                                       vp, vp, vp]
+    lib.lfe_mc_volume_move.restype = ctypes.c_int
     lib.lfe_batch_exchange.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_ulonglong,
                                        ctypes.c_ulonglong, vp, vp]
     lib.lfe_batch_exchange.restype = ctypes.c_int
@@ -330,6 +333,16 @@ class System:
         keys = ["theta", "p_theta", "lambda", "dUdl", "U", "n_kernels_std", "n_kernels_exp", "step",
                 "n_rebuilds", "n_tiles"]
         return pos, vel, dict(zip(keys, ext))
+
+    def mc_volume_move(self, pressure_bar, dv_max, seed, attempt):
+        """One Monte Carlo volume move (lfe_mc_volume_move).  Returns
+        (accepted, box [3], (U before, U proposed))."""
+        acc = ctypes.c_int()
+        box = np.zeros(3)
+        en = np.zeros(2)
+        self._check(self._lib.lfe_mc_volume_move(self.h, float(pressure_bar), float(dv_max), int(seed), int(attempt),
+                                                 ctypes.byref(acc), box.ctypes.data, en.ctypes.data))
+        return bool(acc.value), box, (float(en[0]), float(en[1]))
 
     def step_io(self, pos_in_ptr, pos_out_ptr, vel_out_ptr, ext_out_ptr, stream=None):
         """One step with host input/output in one captured graph (lfe_step_io);
