@@ -350,7 +350,16 @@ def batched_leg(args, stream, flush):
         assert np.isfinite(pos).all()
     ms_step = sum(ms) / K
     ns_day = sum(float(d["dt"]) for d in dicts) * 1e-3 * 86400.0 / (ms_step * 1e-3)
+    # the FP32 replicas' shared pair-kernel launch at batched scale (CUDA
+    # events around launches of it alone, between steps)
+    pair_ms = b.time_pairs(reps=20, stream=stream)
     pairs = sum(g.eval(d["lam"])[0]["n_pairs"] for g, d in zip(reps, dicts))
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    batch_roof = {"bound": "alu", "kernel": "k_pairs2_batch (all FP32 replicas, one launch)",
+                  "kernel_ms": pair_ms, "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR,
+                  "achieved": pairs * FLOPS_PER_PAIR / (pair_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
+    batch_roof["frac"] = batch_roof["achieved"] / peak
     dt_sum = sum(float(d["dt"]) for d in dicts)
     # mixed precision, one replica after another (each with its own graph)
     kmix = max(3, K // 8)
@@ -390,6 +399,7 @@ def batched_leg(args, stream, flush):
             "fp64_batched": {"ms_per_step": t64b, "ns_per_day_x_replica": dt_sum * 1e-3 * 86400.0 / (t64b * 1e-3),
                              "steps": k64},
             "speedup_mixed_batched_vs_fp64_per_replica": ns_day / ns_day64,
+            "roofline_pairs": batch_roof,
             "setup_s": t_gen}
 
 

@@ -367,17 +367,24 @@ int lfe_alu_peak(double* fp32_tflops, double* fp64_tflops);
 /* Batched replicas (lambda windows, solvents, solutes; sizes may differ):
  * lfe_batch_create groups existing systems (not copied; they must outlive
  * the batch and must not be destroyed while it exists).  lfe_batch_step
- * advances every replica n_steps with one graph launch per step: the graph
- * holds each replica's full step (evaluation, integrators, its own
- * device-side neighbour-list rebuild) as an independent chain, so the GPU
- * runs the replicas concurrently; results are identical to stepping each
- * system alone.  lfe_batch_eval evaluates replica i at lambdas[i] and writes
+ * advances every replica n_steps with one graph launch per step: each
+ * replica's rebuild decision and device-side neighbour-list rebuild, PME,
+ * exclusion, bonded and integrator kernels form its own chain, and the pair
+ * kernels of all FP32 replicas run as ONE launch over their concatenated
+ * tile lists once every list is ready (FP64 replicas keep their own);
+ * results are identical to stepping each system alone (the pair kernel's
+ * partial sums cover fixed chunks of each system's tiles, whichever warp
+ * takes them).  lfe_batch_time_pairs (ms, host) is the mean device time of
+ * that shared launch over `reps` launches at the current lists (the forces
+ * and energies it adds are cleared afterwards; call it between steps).
+ * lfe_batch_eval evaluates replica i at lambdas[i] and writes
  * energy_terms[i][LFE_NTERMS] (host); positions and velocities are read with
  * lfe_get_state on each system.  Errors of a batch call are described by
  * lfe_batch_last_error. */
 int lfe_batch_create(lfe_system* const* systems, int n, lfe_batch** out);
 int lfe_batch_eval(lfe_batch* b, const double* lambdas, double* energy_terms, void* stream);
 int lfe_batch_step(lfe_batch* b, int n_steps, void* stream);
+int lfe_batch_time_pairs(lfe_batch* b, int reps, double* ms, void* stream);
 
 /* Lambda replica exchange (the paper's HREX reference protocol, Section 2.6,
  * on the linear-basis potential of Eq. 4).  `ladder` lists n >= 2 replicas

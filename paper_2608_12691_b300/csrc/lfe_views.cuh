@@ -236,6 +236,13 @@ inline void launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_
 }
 
 template <typename real> void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStream_t st);
+// one FP32 system's share of a pair-kernel launch over many systems
+struct PairJob {
+    SysView<float> s;
+    NblView<float> nb;
+};
+void launch_pairs_batch(const PairJob* jobs, int njobs, int nblocks, cudaStream_t st);
+int pairs_batch_blocks();   // one resident wave of the launch over many systems
 template <typename real> void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st);
 template <typename real> int pairs_blocks_per_sm();
 template <typename real> void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nblocks, cudaStream_t st);

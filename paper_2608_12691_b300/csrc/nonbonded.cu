@@ -960,49 +960,55 @@ __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, f
     return add2(fc, fl);
 }
 
-// One warp walks a contiguous chunk of the (I8-sorted) tile list, one 8 x 32
-// tile at a time; lane l holds j entry l.  Step kk = 0..3 pairs the j atom
-// with i atoms kk and kk + 4 (read as float2 halves from a per-warp shared
-// record, shifted for the tile) and is skipped by the whole warp when none of
-// its 64 pairs lies within the cutoff.  A lane's share of the 8 i-forces is
-// kept as float2 in its own column of a per-warp shared array over the tiles
-// of one I8 and added over the warp when I8 changes; the j-force stays in
-// registers and is flushed at the end of every tile.  The tile's class and
-// shift are uniform, so the branches on them are warp-uniform; solute-solvent
-// tiles take the scalar routine with the soft basis (their energies are
-// formed in FP64 by k_uv_energy).
+// The tile list is cut into chunks of PAIR_CHUNK consecutive tiles; a warp
+// takes whole chunks.  Lane l holds j entry l of a tile; step kk = 0..3
+// pairs the j atom with i atoms kk and kk + 4 (read as float2 halves from a
+// per-warp shared record, shifted for the tile) and is skipped by the whole
+// warp when none of its 64 pairs lies within the cutoff.  A lane's share of
+// the 8 i-forces is kept as float2 in its own column of a per-warp shared
+// array and added over the warp when the sub-cluster changes or the chunk
+// ends; the lane's FP32 energy sums are turned into fixed point at the same
+// points.  So every partial sum covers a set of tiles fixed by the list
+// alone (a chunk, or its part of one sub-cluster): the results do not depend
+// on which warp takes which chunk, and a launch over many systems gives each
+// system the bits of its own launch.  The j-force stays in registers and is
+// flushed at the end of every tile.  The tile's class and shift are uniform,
+// so the branches on them are warp-uniform; solute-solvent tiles take the
+// scalar routine with the soft basis (their energies are formed in FP64 by
+// k_uv_energy).
 // Launch shape, measured on the octanol box (13,520 atoms, one wave, CUDA
-// events): 8 resident blocks of 4 warps (62 registers, the i-forces in
-// shared memory) 41.5 us; the same with the i-forces in registers (117
-// registers, 4 blocks) 41.4 us but a slower step (0.149 against 0.142 ms: the
-// kernel shares the GPU with the PME and integrator branches); software
-// prefetch of the next tile's records 42.5 us; the scalar kernel 45.8 us.
-constexpr int PAIR2_MIN_BLOCKS = 8;
+// events): 8 resident blocks of 4 warps (i-forces in shared memory) 41.5 us;
+// the same with the i-forces in registers (4 blocks) 41.4 us but a slower
+// step (0.149 against 0.142 ms: the kernel shares the GPU with the PME and
+// integrator branches); software prefetch of the next tile 42.5 us; the
+// scalar kernel 45.8 us.
+constexpr int PAIR2_MIN_BLOCKS = 6;
+constexpr int PAIR_CHUNK = 8;
 
-__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float> s, NblView<float> nb)
-{
+struct Pair2Shared {
     // [warp][kk] (x_kk, x_kk+4, y_kk, y_kk+4), (z.., z.., q.., q..), (sigma/2.., .., 2 sqrt(eps).., ..)
-    __shared__ float4 sA[4][4], sB[4][4], sC[4][4];
-    __shared__ float2 sfi[4][12][32];   // [warp][3 kk + component][lane]: i atoms kk (x) and kk + 4 (y)
-    const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    int ntiles = s.flags[FL_NTILES];
-    if (ntiles > nb.cap) ntiles = nb.cap;
-    const int t0 = (int)(((long long)ntiles * warp) / nwarp);
-    const int t1 = (int)(((long long)ntiles * (warp + 1)) / nwarp);
-    if (t0 >= t1) return;
-    const PairConst<float> c = pair_const(s);
-    float* fA = reinterpret_cast<float*>(sA[wl]);
-    float* fB = reinterpret_cast<float*>(sB[wl]);
-    float* fC = reinterpret_cast<float*>(sC[wl]);
-    float2(&fi)[12][32] = sfi[wl];
-    const int hk = (lane & 3) * 4 + ((lane >> 2) & 1);   // lanes 0-7: place of atom `lane` in the records
-    int curI = -1;
-    R4<float> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
-    float evv = 0, euu = 0;
+    float4 sA[4][4], sB[4][4], sC[4][4];
+    float2 sfi[4][12][32];   // [warp][3 kk + component][lane]: i atoms kk (x) and kk + 4 (y)
+};
+
+struct Pair2Acc {
+    long long evv = 0, euu = 0;   // fixed-point energies (ESCALE)
     int npairs = 0;
-    auto flush_i = [&](int I8) {
+};
+
+// chunks [c0, c1) of one system, by one warp
+__device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const NblView<float>& nb, int ntiles, int c0,
+                                              int c1, Pair2Shared& sh, Pair2Acc& acc)
+{
+    const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
+    const PairConst<float> c = pair_const(s);
+    float* fA = reinterpret_cast<float*>(sh.sA[wl]);
+    float* fB = reinterpret_cast<float*>(sh.sB[wl]);
+    float* fC = reinterpret_cast<float*>(sh.sC[wl]);
+    float2(&fi)[12][32] = sh.sfi[wl];
+    const int hk = (lane & 3) * 4 + ((lane >> 2) & 1);   // lanes 0-7: place of atom `lane` in the records
+    float evv = 0, euu = 0;
+    auto flush = [&](int I8) {
         float v[24];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -1011,122 +1017,184 @@ __global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float>
             v[3 * k + 12] = ax.y; v[3 * k + 13] = ay.y; v[3 * k + 14] = az.y;
         }
         flush_i8_v(s, I8, v);
+        acc.evv += to_fixed(evv, ESCALE);
+        acc.euu += to_fixed(euu, ESCALE);
+        evv = euu = 0;
     };
-    for (int t = t0; t < t1; ++t) {
-        const int4 tl = nb.tiles[t];
-        const unsigned mc = nb.masks[(size_t)t * 32 + lane];
-        const int slot_j = nb.jidx[(size_t)t * 32 + lane];
-        R4<float> pj = s.xq[slot_j >= 0 ? slot_j : 0];
-        const R2<float> ljv = s.lj[slot_j >= 0 ? slot_j : 0];
-        if (tl.x != curI) {
-            if (curI >= 0) flush_i(curI);
-            curI = tl.x;
-            if (lane < 8) {
-                pown = s.xq[curI * 8 + lane];
-                const R2<float> l = s.lj[curI * 8 + lane];
-                fC[hk] = l.x;
-                fC[hk + 2] = l.y;
-            }
-#pragma unroll
-            for (int m = 0; m < 12; ++m) fi[m][lane] = p2(0.0f);
-        }
-        const int sh = tl.y;
-        const int sx = sh % 3 - 1, sy = (sh / 3) % 3 - 1, sz = sh / 9 - 1;
-        // shift the far-side atom down by L so that the subtraction below is
-        // the only rounding in the pair vector
-        if (lane < 8) {
-            fA[hk] = sx == 1 ? pown.x - s.L[0] : pown.x;
-            fA[hk + 2] = sy == 1 ? pown.y - s.L[1] : pown.y;
-            fB[hk] = sz == 1 ? pown.z - s.L[2] : pown.z;
-            fB[hk + 2] = pown.w;
-        }
-        if (sx == -1) pj.x -= s.L[0];
-        if (sy == -1) pj.y -= s.L[1];
-        if (sz == -1) pj.z -= s.L[2];
-        __syncwarp();
-        const float2 jx = p2(pj.x), jy = p2(pj.y), jz = p2(pj.z);
-        float fjx, fjy, fjz, e0;
-        if (tl.z != 2) {
-            const float2 qj = p2(pj.w), sgj = p2(ljv.x), ej = p2(ljv.y);
-            float2 fj2x = p2(0.0f), fj2y = p2(0.0f), fj2z = p2(0.0f), e2 = p2(0.0f);
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const float4 A = sA[wl][kk], B = sB[wl][kk];
-                const float2 dx = add2(jx, neg2(make_float2(A.x, A.y)));
-                const float2 dy = add2(jy, neg2(make_float2(A.z, A.w)));
-                const float2 dz = add2(jz, neg2(make_float2(B.x, B.y)));
-                const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-                const bool in0 = ((mc >> kk) & 1u) && r2.x < c.rc2;
-                const bool in1 = ((mc >> (kk + 4)) & 1u) && r2.y < c.rc2;
-                if (in0 || in1) {
-                    // a half out of range is evaluated at r^2 = 1 and weighted by 0
-                    const float4 C = sC[wl][kk];
-                    const float2 rs = make_float2(in0 ? r2.x : 1.0f, in1 ? r2.y : 1.0f);
-                    const float2 m = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
-                    float2 e;
-                    float2 g = pair_force2(rs, mul2(make_float2(B.z, B.w), qj), add2(make_float2(C.x, C.y), sgj),
-                                           mul2(make_float2(C.z, C.w), ej), c, e);
-                    g = mul2(g, m);
-                    const float2 gx = mul2(g, dx), gy = mul2(g, dy), gz = mul2(g, dz);
-                    fi[3 * kk][lane] = add2(fi[3 * kk][lane], neg2(gx));
-                    fi[3 * kk + 1][lane] = add2(fi[3 * kk + 1][lane], neg2(gy));
-                    fi[3 * kk + 2][lane] = add2(fi[3 * kk + 2][lane], neg2(gz));
-                    fj2x = add2(fj2x, gx);
-                    fj2y = add2(fj2y, gy);
-                    fj2z = add2(fj2z, gz);
-                    e2 = fma2(e, m, e2);
-                    npairs += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+    for (int ch = c0; ch < c1; ++ch) {
+        const int ta = ch * PAIR_CHUNK, tb = min(ta + PAIR_CHUNK, ntiles);
+        int curI = -1;
+        R4<float> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
+        for (int t = ta; t < tb; ++t) {
+            const int4 tl = nb.tiles[t];
+            const unsigned mc = nb.masks[(size_t)t * 32 + lane];
+            const int slot_j = nb.jidx[(size_t)t * 32 + lane];
+            R4<float> pj = s.xq[slot_j >= 0 ? slot_j : 0];
+            const R2<float> ljv = s.lj[slot_j >= 0 ? slot_j : 0];
+            if (tl.x != curI) {
+                if (curI >= 0) flush(curI);
+                curI = tl.x;
+                if (lane < 8) {
+                    pown = s.xq[curI * 8 + lane];
+                    const R2<float> l = s.lj[curI * 8 + lane];
+                    fC[hk] = l.x;
+                    fC[hk + 2] = l.y;
                 }
+#pragma unroll
+                for (int m = 0; m < 12; ++m) fi[m][lane] = p2(0.0f);
             }
-            fjx = fj2x.x + fj2x.y;
-            fjy = fj2y.x + fj2y.y;
-            fjz = fj2z.x + fj2z.y;
-            e0 = e2.x + e2.y;
-        } else {
-            // solute-solvent tile: the scalar routine with the soft basis, both halves
-            fjx = fjy = fjz = e0 = 0.0f;
+            const int sh3 = tl.y;
+            const int sx = sh3 % 3 - 1, sy = (sh3 / 3) % 3 - 1, sz = sh3 / 9 - 1;
+            // shift the far-side atom down by L so that the subtraction below is
+            // the only rounding in the pair vector
+            if (lane < 8) {
+                fA[hk] = sx == 1 ? pown.x - s.L[0] : pown.x;
+                fA[hk + 2] = sy == 1 ? pown.y - s.L[1] : pown.y;
+                fB[hk] = sz == 1 ? pown.z - s.L[2] : pown.z;
+                fB[hk + 2] = pown.w;
+            }
+            if (sx == -1) pj.x -= s.L[0];
+            if (sy == -1) pj.y -= s.L[1];
+            if (sz == -1) pj.z -= s.L[2];
+            __syncwarp();
+            const float2 jx = p2(pj.x), jy = p2(pj.y), jz = p2(pj.z);
+            float fjx, fjy, fjz, e0;
+            if (tl.z != 2) {
+                const float2 qj = p2(pj.w), sgj = p2(ljv.x), ej = p2(ljv.y);
+                float2 fj2x = p2(0.0f), fj2y = p2(0.0f), fj2z = p2(0.0f), e2 = p2(0.0f);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const float4 A = sA[wl][kk], B = sB[wl][kk], C = sC[wl][kk];
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float4 A = sh.sA[wl][kk], B = sh.sB[wl][kk];
+                    const float2 dx = add2(jx, neg2(make_float2(A.x, A.y)));
+                    const float2 dy = add2(jy, neg2(make_float2(A.z, A.w)));
+                    const float2 dz = add2(jz, neg2(make_float2(B.x, B.y)));
+                    const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                    const bool in0 = ((mc >> kk) & 1u) && r2.x < c.rc2;
+                    const bool in1 = ((mc >> (kk + 4)) & 1u) && r2.y < c.rc2;
+                    if (in0 || in1) {
+                        // a half out of range is evaluated at r^2 = 1 and weighted by 0
+                        const float4 C = sh.sC[wl][kk];
+                        const float2 rs = make_float2(in0 ? r2.x : 1.0f, in1 ? r2.y : 1.0f);
+                        const float2 m = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
+                        float2 e;
+                        float2 g = pair_force2(rs, mul2(make_float2(B.z, B.w), qj), add2(make_float2(C.x, C.y), sgj),
+                                               mul2(make_float2(C.z, C.w), ej), c, e);
+                        g = mul2(g, m);
+                        const float2 gx = mul2(g, dx), gy = mul2(g, dy), gz = mul2(g, dz);
+                        fi[3 * kk][lane] = add2(fi[3 * kk][lane], neg2(gx));
+                        fi[3 * kk + 1][lane] = add2(fi[3 * kk + 1][lane], neg2(gy));
+                        fi[3 * kk + 2][lane] = add2(fi[3 * kk + 2][lane], neg2(gz));
+                        fj2x = add2(fj2x, gx);
+                        fj2y = add2(fj2y, gy);
+                        fj2z = add2(fj2z, gz);
+                        e2 = fma2(e, m, e2);
+                        acc.npairs += (in0 ? 1 : 0) + (in1 ? 1 : 0);
+                    }
+                }
+                fjx = fj2x.x + fj2x.y;
+                fjy = fj2y.x + fj2y.y;
+                fjz = fj2z.x + fj2z.y;
+                e0 = e2.x + e2.y;
+            } else {
+                // solute-solvent tile: the scalar routine with the soft basis, both halves
+                fjx = fjy = fjz = e0 = 0.0f;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const float ix = h ? A.y : A.x, iy = h ? A.w : A.z, iz = h ? B.y : B.x, iq = h ? B.w : B.z;
-                    const float isg = h ? C.y : C.x, ie = h ? C.w : C.z;
-                    const float dx = pj.x - ix, dy = pj.y - iy, dz = pj.z - iz;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    if (((mc >> (kk + 4 * h)) & 1u) && r2 < c.rc2) {
-                        float ec, v;
-                        const float g = pair_force(r2, iq * pj.w, isg + ljv.x, ie * ljv.y, true, c, ec, v);
-                        const float gx = g * dx, gy = g * dy, gz = g * dz;
-                        float2 f0 = fi[3 * kk][lane], f1 = fi[3 * kk + 1][lane], f2 = fi[3 * kk + 2][lane];
-                        if (h) {
-                            f0.y -= gx; f1.y -= gy; f2.y -= gz;
-                        } else {
-                            f0.x -= gx; f1.x -= gy; f2.x -= gz;
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float4 A = sh.sA[wl][kk], B = sh.sB[wl][kk], C = sh.sC[wl][kk];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float ix = h ? A.y : A.x, iy = h ? A.w : A.z, iz = h ? B.y : B.x, iq = h ? B.w : B.z;
+                        const float isg = h ? C.y : C.x, ie = h ? C.w : C.z;
+                        const float dx = pj.x - ix, dy = pj.y - iy, dz = pj.z - iz;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        if (((mc >> (kk + 4 * h)) & 1u) && r2 < c.rc2) {
+                            float ec, v;
+                            const float g = pair_force(r2, iq * pj.w, isg + ljv.x, ie * ljv.y, true, c, ec, v);
+                            const float gx = g * dx, gy = g * dy, gz = g * dz;
+                            float2 f0 = fi[3 * kk][lane], f1 = fi[3 * kk + 1][lane], f2 = fi[3 * kk + 2][lane];
+                            if (h) {
+                                f0.y -= gx; f1.y -= gy; f2.y -= gz;
+                            } else {
+                                f0.x -= gx; f1.x -= gy; f2.x -= gz;
+                            }
+                            fi[3 * kk][lane] = f0;
+                            fi[3 * kk + 1][lane] = f1;
+                            fi[3 * kk + 2][lane] = f2;
+                            fjx += gx; fjy += gy; fjz += gz;
+                            ++acc.npairs;
                         }
-                        fi[3 * kk][lane] = f0;
-                        fi[3 * kk + 1][lane] = f1;
-                        fi[3 * kk + 2][lane] = f2;
-                        fjx += gx; fjy += gy; fjz += gz;
-                        ++npairs;
                     }
                 }
             }
+            __syncwarp();
+            if (slot_j >= 0)
+                flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
+            if (tl.z == 0) evv += e0;
+            else if (tl.z == 1) euu += e0;
         }
-        __syncwarp();
-        if (slot_j >= 0)
-            flush_force(s, slot_j, to_fixed(fjx, FSCALE), to_fixed(fjy, FSCALE), to_fixed(fjz, FSCALE));
-        if (tl.z == 0) evv += e0;
-        else if (tl.z == 1) euu += e0;
+        if (curI >= 0) flush(curI);
     }
-    flush_i(curI);
-    const long long a0 = __double2ll_rn(warp_sum_d((double)evv) * ESCALE);
-    const long long a1 = __double2ll_rn(warp_sum_d((double)euu) * ESCALE);
-    const long long a4 = warp_sum_ll((long long)npairs);
-    if (lane == 0) {
+}
+
+// the warp's energy and pair-count sums into the system's accumulators
+__device__ __forceinline__ void pairs2_store(const SysView<float>& s, Pair2Acc& acc)
+{
+    const long long a0 = warp_sum_ll(acc.evv), a1 = warp_sum_ll(acc.euu), a4 = warp_sum_ll((long long)acc.npairs);
+    if ((threadIdx.x & 31) == 0) {
         if (a0) atomic_add_ll(&s.E[E_PAIR_VV], a0);
         if (a1) atomic_add_ll(&s.E[E_PAIR_UU], a1);
-        atomic_add_ll(&s.E[E_NPAIRS], a4);
+        if (a4) atomic_add_ll(&s.E[E_NPAIRS], a4);
+    }
+    acc = Pair2Acc{};
+}
+
+// one system: the warps share out its chunks evenly
+__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float> s, NblView<float> nb)
+{
+    __shared__ Pair2Shared sh;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    const int ntiles = min(s.flags[FL_NTILES], nb.cap);
+    const int nch = (ntiles + PAIR_CHUNK - 1) / PAIR_CHUNK;
+    const int c0 = (int)(((long long)nch * warp) / nwarp), c1 = (int)(((long long)nch * (warp + 1)) / nwarp);
+    if (c0 >= c1) return;
+    Pair2Acc acc;
+    pairs2_chunks(s, nb, ntiles, c0, c1, sh, acc);
+    pairs2_store(s, acc);
+}
+
+// many systems in one launch: the chunks of every system form one index
+// range that the warps share out evenly; each system's tiles, constants and
+// accumulators are its own, and its results are those of a launch of its own
+__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2_batch(const PairJob* jobs, int njobs)
+{
+    __shared__ Pair2Shared sh;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    // total chunks over the systems (lane r sums systems r, r + 32, ...)
+    long long part = 0;
+    for (int r = lane; r < njobs; r += 32) {
+        const int nt = min(jobs[r].s.flags[FL_NTILES], jobs[r].nb.cap);
+        part += (nt + PAIR_CHUNK - 1) / PAIR_CHUNK;
+    }
+    const long long total = __shfl_sync(FULL, warp_sum_ll(part), 0);
+    const long long g0 = (total * warp) / nwarp, g1 = (total * (warp + 1)) / nwarp;
+    if (g0 >= g1) return;
+    long long off = 0;
+    Pair2Acc acc;
+    for (int r = 0; r < njobs && off < g1; ++r) {
+        const SysView<float>& s = jobs[r].s;
+        const NblView<float>& nb = jobs[r].nb;
+        const int nt = min(s.flags[FL_NTILES], nb.cap);
+        const int nch = (nt + PAIR_CHUNK - 1) / PAIR_CHUNK;
+        const long long a = max(g0, off), b = min(g1, off + nch);
+        if (a < b) {
+            pairs2_chunks(s, nb, nt, (int)(a - off), (int)(b - off), sh, acc);
+            pairs2_store(s, acc);
+        }
+        off += nch;
     }
 }
 
@@ -1353,6 +1421,21 @@ int pairs_blocks_per_sm()
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs2, 128, 0);
     if (e != cudaSuccess || nb < 1) nb = 1;
     return nb;
+}
+
+int pairs_batch_blocks()
+{
+    int dev = 0, nsm = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || nsm < 1)
+        nsm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs2_batch, 128, 0) != cudaSuccess || nb < 1) nb = 1;
+    return nsm * nb;
+}
+
+void launch_pairs_batch(const PairJob* jobs, int njobs, int nblocks, cudaStream_t st)
+{
+    if (njobs > 0) k_pairs2_batch<<<nblocks, 128, 0, st>>>(jobs, njobs);
 }
 
 template <typename real>

@@ -31,7 +31,7 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step", "lfe_batch_time_pairs",
     "lfe_batch_exchange", "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
@@ -150,6 +150,8 @@ def load():
     lib.lfe_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
     lib.lfe_batch_eval.argtypes = [vp, vp, vp, vp]
     lib.lfe_batch_step.argtypes = [vp, ctypes.c_int, vp]
+    lib.lfe_batch_time_pairs.argtypes = [vp, ctypes.c_int, vp, vp]
+    lib.lfe_batch_time_pairs.restype = ctypes.c_int
     lib.lfe_batch_destroy.argtypes = [vp]
     lib.lfe_batch_destroy.restype = None
     lib.lfe_batch_last_error.argtypes = [vp]
@@ -482,6 +484,13 @@ class Batch:
 
     def step(self, n, stream=None):
         self._check(self._lib.lfe_batch_step(self.h, int(n), _stream_ptr(stream)))
+
+    def time_pairs(self, reps=20, stream=None):
+        """Mean device time (ms) of the FP32 replicas' shared pair-kernel launch
+        (lfe_batch_time_pairs); call between steps."""
+        ms = ctypes.c_double()
+        self._check(self._lib.lfe_batch_time_pairs(self.h, int(reps), ctypes.byref(ms), _stream_ptr(stream)))
+        return ms.value
 
     def exchange(self, ladder, temperature, seed, attempt, stream=None):
         """One lambda-exchange attempt over `ladder` (replica indices in lambda
