@@ -37,6 +37,17 @@
  *     s_C k_e q_i q_j / r + s_LJ LJ(r), unswitched and uncut.
  *   - Pairs with eps_ij = 0 carry no LJ or soft-LJ term.
  *
+ * Optional soft-core coupling (the conventional alternative the paper sets
+ * its linear-basis method against; the paper gives no formula): with
+ * sc_alpha > 0 the solute-solvent Lennard-Jones term is replaced, at the
+ * given sc_lambda, by the soft-core form of Beutler et al. (1994)
+ *   U_sc(r, l) = 4 eps_ij l^p [1/D^2 - 1/D] S(r),  D = sc_alpha (1 - l) + (r/sigma_ij)^6,
+ * p = sc_power; the solute-solvent Coulomb terms stay in U_uv (weighted by
+ * h_A), U_soft holds U_sc at sc_lambda (weighted by 1), and E[24] holds
+ *   dU_sc/dl = 4 eps_ij S [p l^(p-1) (1/D^2 - 1/D) + sc_alpha l^p (2/D^3 - 1/D^2)],
+ * so that U = U_vv + U_uu + h_A U_uv + U_soft and
+ * dU/dl = h_A' U_uv + E[24], F = F0 + h_A Fuv + Fsoft.
+ *
  * Units: nm, kJ/mol, e.  k_e = 138.935458 kJ mol^-1 nm e^-2.
  *
  * Energy array E[ORC_NE] layout (all kJ/mol):
@@ -49,6 +60,7 @@
  *  18 excl_vv       19 excl_uu       20 excl_uv
  *  21 pair14_vv     22 pair14_uu
  *  23 number of non-excluded pairs with r < r_c (as a double)
+ *  24 dU_sc/dlambda (soft-core coupling only; 0 otherwise)
  * Force arrays (each [3N], any may be NULL) hold -grad of one basis:
  *   F0    = -grad (U_vv + U_uu)
  *   Fuv   = -grad U_uv
@@ -70,7 +82,7 @@
 #endif
 
 #define ORC_KE 138.935458
-#define ORC_NE 24
+#define ORC_NE 25
 #define ORC_PI 3.14159265358979323846
 
 typedef struct {
@@ -82,6 +94,9 @@ typedef struct {
     int kmax[3];       /* level 1: |m_d| <= kmax[d] */
     int grid[3];       /* level 2: K1, K2, K3 */
     int order;         /* level 2: B-spline order n */
+    double sc_alpha;   /* > 0: soft-core solute-solvent LJ at sc_lambda (see above) */
+    double sc_power;
+    double sc_lambda;
 } orc_params;
 
 /* ---------------------------------------------------------------- helpers */
@@ -164,12 +179,14 @@ static void real_space(const orc_params* p, int n, const double* pos, const doub
 {
     const double rc = p->r_cut, rs = p->r_switch, a = p->alpha;
     const double rc2 = rc * rc;
-    double e_c[3] = {0, 0, 0}, e_lj[3] = {0, 0, 0}, e_soft = 0.0, npairs = 0.0;
+    double e_c[3] = {0, 0, 0}, e_lj[3] = {0, 0, 0}, e_soft = 0.0, npairs = 0.0, e_dsc = 0.0;
+    const int sc = p->sc_alpha > 0.0;
+    const double lam = p->sc_lambda, sa = p->sc_alpha, sp = p->sc_power;
 
 #pragma omp parallel
     {
         char* mark = (char*)calloc((size_t)n, 1);
-        double tc[3] = {0, 0, 0}, tlj[3] = {0, 0, 0}, tsoft = 0.0, tnp = 0.0;
+        double tc[3] = {0, 0, 0}, tlj[3] = {0, 0, 0}, tsoft = 0.0, tnp = 0.0, tdsc = 0.0;
 #pragma omp for schedule(dynamic, 16)
         for (int i = 0; i < n; ++i) {
             for (int e = ex_start[i]; e < ex_start[i + 1]; ++e) mark[ex_list[e]] = 1;
@@ -194,6 +211,24 @@ static void real_space(const orc_params* p, int n, const double* pos, const doub
                 double ep = sqrt(eps[i] * eps[j]);
                 double dS, S = orc_switch(r, rc, rs, &dS);
                 double elj = 0.0, delj = 0.0;
+                if (sc && c == 2) {
+                    /* soft-core solute-solvent LJ at lambda (the soft slot) */
+                    if (ep > 0.0 && s > 0.0) {
+                        double x6 = pow(r / s, 6), D = sa * (1.0 - lam) + x6;
+                        double lp = pow(lam, sp), u = 1.0 / (D * D) - 1.0 / D;
+                        double du_dD = -2.0 / (D * D * D) + 1.0 / (D * D);
+                        double es = 4.0 * ep * lp * u * S;
+                        double des = 4.0 * ep * lp * (du_dD * 6.0 * x6 / r * S + u * dS);
+                        double dl = 4.0 * ep * S * (sp * pow(lam, sp - 1.0) * u + sa * lp * (2.0 / (D * D * D) - 1.0 / (D * D)));
+                        tsoft += 0.5 * es;
+                        tdsc += 0.5 * dl;
+                        double gs = des / r;
+                        fs[0] += gs * d[0]; fs[1] += gs * d[1]; fs[2] += gs * d[2];
+                    }
+                    double g = dec / r;
+                    fuv[0] += g * d[0]; fuv[1] += g * d[1]; fuv[2] += g * d[2];
+                    continue;
+                }
                 if (ep > 0.0) {
                     double sr6 = pow(s / r, 6);
                     double v = 4.0 * ep * (sr6 * sr6 - sr6);
@@ -230,6 +265,7 @@ static void real_space(const orc_params* p, int n, const double* pos, const doub
         {
             for (int c = 0; c < 3; ++c) { e_c[c] += tc[c]; e_lj[c] += tlj[c]; }
             e_soft += tsoft;
+            e_dsc += tdsc;
             npairs += tnp;
         }
         free(mark);
@@ -238,6 +274,7 @@ static void real_space(const orc_params* p, int n, const double* pos, const doub
     E[15] += e_lj[0]; E[16] += e_lj[1]; E[17] += e_lj[2];
     E[3] += e_soft;
     E[23] += npairs;
+    E[24] += e_dsc;
 }
 
 static double* basis_for_class(int c, double* F0, double* Fuv)

@@ -24,7 +24,7 @@ E_NAMES = [
     "lj_vv", "lj_uu", "lj_uv",
     "excl_vv", "excl_uu", "excl_uv",
     "p14_vv", "p14_uu",
-    "n_pairs",
+    "n_pairs", "dUsc_dl",
 ]
 NE = len(E_NAMES)
 
@@ -39,6 +39,9 @@ class _Params(ctypes.Structure):
         ("kmax", ctypes.c_int * 3),
         ("grid", ctypes.c_int * 3),
         ("order", ctypes.c_int),
+        ("sc_alpha", ctypes.c_double),
+        ("sc_power", ctypes.c_double),
+        ("sc_lambda", ctypes.c_double),
     ]
 
 
@@ -144,11 +147,14 @@ def kmax_for(box, alpha, tol=1e-17):
 
 
 def nonbonded(sysd, level=2, alpha=None, kmax=None, grid=None, order=None,
-              r_cut=None, r_switch=None, solute=None, pos=None, forces=True):
+              r_cut=None, r_switch=None, solute=None, pos=None, forces=True, sc_lambda=None):
     """Basis energies and basis forces of the nonbonded part of Eq. 4.
 
     Returns (E dict, F0, Fuv, Fsoft) with F0 = -grad(U_vv + U_uu),
     Fuv = -grad U_uv, Fsoft = -grad U_soft, each (N, 3) or None.
+    With sysd["sc_alpha"] > 0 (soft-core coupling) the soft slot holds the
+    soft-core solute-solvent LJ at sc_lambda and E["dUsc_dl"] its lambda
+    derivative (see lfe_oracle.c).
     """
     L = lib()
     box = np.asarray(sysd["box"], dtype=np.float64)
@@ -174,6 +180,12 @@ def nonbonded(sysd, level=2, alpha=None, kmax=None, grid=None, order=None,
         p.kmax[k] = int(km[k])
         p.grid[k] = int(g[k])
     p.order = int(sysd["order"] if order is None else order)
+    p.sc_alpha = float(sysd.get("sc_alpha", 0.0) or 0.0)
+    p.sc_power = float(sysd.get("sc_power", 1.0) or 1.0)
+    if p.sc_alpha > 0.0:
+        if sc_lambda is None:
+            raise ValueError("soft-core coupling needs sc_lambda")
+        p.sc_lambda = float(sc_lambda)
     E = np.zeros(NE)
     F = [np.zeros((n, 3)) if forces else None for _ in range(3)]
     rc = L.orc_nonbonded(
@@ -215,16 +227,20 @@ def evaluate(sysd, lam, level=2, with_bonded=True, **kw):
     dU/dlambda = h_A'(lambda) U_uv + h_B'(lambda) U_soft (the lambda
     dependence enters only through h_A and h_B, Section 2.2).
     """
-    E, F0, Fuv, Fs = nonbonded(sysd, level=level, **kw)
+    sc = float(sysd.get("sc_alpha", 0.0) or 0.0) > 0.0
+    E, F0, Fuv, Fs = nonbonded(sysd, level=level, sc_lambda=lam if sc else None, **kw)
     hA, hB, dhA, dhB = switching(lam)
     Ub, Fb = (0.0, None)
     if with_bonded:
         Ub, Fb = bonded(sysd, pos=kw.get("pos"))
-    U = E["U_vv"] + E["U_uu"] + hA * E["U_uv"] + hB * E["U_soft"] + Ub
-    dU = dhA * E["U_uv"] + dhB * E["U_soft"]
+    # linear-basis coupling: h_B weights the capped soft basis; soft-core
+    # coupling: the soft slot is already the soft-core term at lambda
+    wS, dS = (1.0, E["dUsc_dl"]) if sc else (hB, dhB * E["U_soft"])
+    U = E["U_vv"] + E["U_uu"] + hA * E["U_uv"] + wS * E["U_soft"] + Ub
+    dU = dhA * E["U_uv"] + dS
     F = None
     if F0 is not None:
-        F = F0 + hA * Fuv + hB * Fs
+        F = F0 + hA * Fuv + wS * Fs
         if Fb is not None:
             F = F + Fb
     return {"U": U, "dUdl": dU, "F": F, "E": E, "U_bonded": Ub,
