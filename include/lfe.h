@@ -99,6 +99,16 @@ typedef struct {
     double lambda_temperature; /* step: theta's thermostat temperature, K (<= 0: `temperature`).  A hot
                                 * theta is the lambda-d-AFED protocol (Section 3.2: 5000-10000 K with
                                 * masses 1e4-1e6 amu nm^2); the OPES biases keep the physical beta */
+    double sc_alpha;          /* > 0: soft-core coupling instead of the linear-basis soft term: the
+                               * solute-solvent LJ is the Beutler et al. (1994) form at lambda,
+                               * 4 eps l^p [1/D^2 - 1/D] S(r), D = sc_alpha (1 - l) + (r/sigma)^6
+                               * (the paper contrasts its Eq. 4-6 coupling with soft-core and gives
+                               * no formula); the solute-solvent Coulomb terms keep h_A.  Then
+                               * U = U_vv + U_uu + h_A U_uv + U_soft with U_soft the soft-core term
+                               * at lambda, dU/dl = h_A' U_uv + dU_soft/dl.  Parameter gradients and
+                               * lambda exchange (which rely on the linear basis) are refused.
+                               * 0: linear-basis coupling (default) */
+    double sc_power;          /* p of the soft-core form (>= 1 when sc_alpha > 0) */
 } lfe_params;
 
 /* System description (host arrays, copied by lfe_create).

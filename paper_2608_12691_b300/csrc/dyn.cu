@@ -79,8 +79,10 @@ __global__ void k_eval_out(SysView<real> s, double* forces, double* terms, doubl
         const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + cuv;
         const double Us = efix(E, E_PAIR_SOFT);
         const double Ub = efix(E, E_BONDED);
-        const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub + efix(E, E_DAFED);
-        const double dU = L->dhA * Uuv + L->dhB * Us;
+        // soft-core coupling: U_soft is already the soft-core term at lambda
+        const bool sc = s.sc_alpha > 0.0;
+        const double U = Uvv + Uuu + L->hA * Uuv + (sc ? Us : L->hB * Us) + Ub + efix(E, E_DAFED);
+        const double dU = L->dhA * Uuv + (sc ? efix(E, E_DSC) : L->dhB * Us);
         if (terms) {
             terms[0] = U; terms[1] = dU; terms[2] = Uvv; terms[3] = Uuu; terms[4] = Uuv;
             terms[5] = Us; terms[6] = Ub; terms[7] = (double)E[E_NPAIRS]; terms[8] = L->hA; terms[9] = L->hB;
@@ -871,8 +873,9 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
     const double Us = efix(E, E_PAIR_SOFT);
     const double Ub = efix(E, E_BONDED);
-    const double dUdl = L->dhA * Uuv + L->dhB * Us;
-    const double U = Uvv + Uuu + L->hA * Uuv + L->hB * Us + Ub + efix(E, E_DAFED);
+    const bool sc = s.sc_alpha > 0.0;   // soft-core coupling: U_soft is the term at lambda
+    const double dUdl = L->dhA * Uuv + (sc ? efix(E, E_DSC) : L->dhB * Us);
+    const double U = Uvv + Uuu + L->hA * Uuv + (sc ? Us : L->hB * Us) + Ub + efix(E, E_DAFED);
     const double th = L->theta;
     const double V0 = t.pre->V[0], dV0 = t.pre->dV[0], V1 = t.pre->V[1], dV1 = t.pre->dV[1];
     const unsigned long long step = L->step;

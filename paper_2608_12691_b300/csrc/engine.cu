@@ -132,6 +132,7 @@ struct SystemBase {
     virtual void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                          cudaStream_t st) = 0;
     virtual void lambda_state(double* lam, double* mass) = 0;
+    virtual bool soft_core() const = 0;
     virtual void mc_volume_move(double pressure_bar, double dv_max, unsigned long long seed,
                                 unsigned long long attempt, int* accepted, double* box_out, double* energies) = 0;
     unsigned generation = 0;   // bumped whenever device buffers are reallocated
@@ -251,6 +252,9 @@ struct System final : SystemBase {
         if (p.r_switch >= p.r_cut) fail(LFE_ERR_ARG, "r_switch must be below r_cut (or negative for none)");
         if (!(p.ewald_alpha > 0)) fail(LFE_ERR_ARG, "ewald_alpha must be positive");
         if (!std::isfinite(p.lambda_temperature)) fail(LFE_ERR_ARG, "lambda_temperature must be finite");
+        if (!(p.sc_alpha >= 0.0) || !std::isfinite(p.sc_alpha)) fail(LFE_ERR_ARG, "sc_alpha must be >= 0");
+        if (p.sc_alpha > 0.0 && !(p.sc_power >= 1.0 && std::isfinite(p.sc_power)))
+            fail(LFE_ERR_ARG, "sc_power must be >= 1 with soft-core coupling");
         if (p.pme_order != 4) fail(LFE_ERR_ARG, "pme_order must be 4");
         if (p.precision != LFE_FP32_MIXED && p.precision != LFE_FP64) fail(LFE_ERR_ARG, "unknown precision");
         if (!finite_all(t.pos, 3 * (size_t)n) || !finite_all(t.charge, n) || !finite_all(t.sigma, n) ||
@@ -327,6 +331,8 @@ struct System final : SystemBase {
         }
         S.alpha = (real)p.ewald_alpha;
         S.two_a_sqrtpi = (real)(2.0 * p.ewald_alpha / std::sqrt(PI));
+        S.sc_alpha = p.sc_alpha;
+        S.sc_power = p.sc_alpha > 0.0 ? p.sc_power : 1.0;
         S.x = upload(hx);
         S.v = upload(hv);
         S.xref = dalloc<R4<real>>(n);
@@ -1510,6 +1516,8 @@ struct System final : SystemBase {
         }
     }
 
+    bool soft_core() const override { return P.sc_alpha > 0.0; }
+
     void lambda_state(double* lam, double* mass) override
     {
         CK(cudaDeviceSynchronize());
@@ -2177,6 +2185,7 @@ struct System final : SystemBase {
     // of each solute atom.
     void param_grad(double lam, double* dU, double* d2U, double* basis, int on_device, cudaStream_t st) override
     {
+        if (P.sc_alpha > 0.0) fail(LFE_ERR_STATE, "parameter gradients need the linear-basis coupling (sc_alpha = 0)");
         if (!(lam >= 0.0 && lam <= 1.0)) fail(LFE_ERR_ARG, "lambda must be in [0, 1]");
         if (n_u == 0) fail(LFE_ERR_ARG, "the system has no solute atoms");
         settle_positions(st);
@@ -2696,6 +2705,8 @@ int lfe_batch_exchange(lfe_batch* b, int n, int* ladder, double temperature, uns
             const int r = ladder[k];
             if (r < 0 || r >= (int)b->sys.size() || seen[r]) fail(LFE_ERR_ARG, "ladder entries must be distinct replica indices");
             seen[r] = 1;
+            if (b->sys[r]->impl->soft_core())
+                fail(LFE_ERR_STATE, "lambda exchange needs the linear-basis coupling (sc_alpha = 0)");
             double m = 0;
             b->sys[r]->impl->lambda_state(&lam[k], &m);
             if (m > 0) fail(LFE_ERR_ARG, "replica " + std::to_string(r) + " has a dynamical theta (lambda_mass > 0)");

@@ -29,7 +29,8 @@ enum {
     E_14_VV, E_14_UU, E_14_UV,
     E_REC_VV, E_REC_UU, E_REC_UV,
     E_BONDED, E_NPAIRS, E_DAFED,
-    E_N = 16
+    E_DSC,          // dU_soft/dlambda of the soft-core coupling
+    E_N = 17
 };
 
 // error / control flags

@@ -23,6 +23,8 @@ struct SysView {
     real sw_inv_w;  // 1 / (r_cut - r_switch)
     real alpha;     // Ewald alpha
     real two_a_sqrtpi;
+    double sc_alpha;   // > 0: soft-core coupling of the solute-solvent LJ (see lfe_params)
+    double sc_power;
     // master state, caller order
     R4<real>* x;
     R4<real>* v;

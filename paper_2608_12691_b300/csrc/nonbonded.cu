@@ -803,6 +803,8 @@ __device__ __forceinline__ void erfc_exp(double x, double& erfcv, double& ex)
 template <typename real>
 struct PairConst {
     real rc2, swi, rsw_swi, alpha, tas, hA, hB;
+    bool sc;                 // soft-core coupling of the solute-solvent LJ
+    real sc_a1l, sc_lp;      // sc_alpha (1 - lambda), lambda^p
 };
 
 template <typename real>
@@ -828,6 +830,21 @@ __device__ __forceinline__ real pair_force(real r2, real qq, real sg, real e4, b
     fl = fl * S - v * dS * rinv;
     v *= S;
     real g = fc + fl;
+    if (uv && c.sc) {
+        // soft-core coupling: the solute-solvent LJ is the Beutler form at
+        // lambda, e4 l^p (1/D^2 - 1/D) S(r) with D = alpha (1 - l) + (r/sigma)^6;
+        // Coulomb keeps the h_A weight
+        real gs = 0;
+        if (e4 != (real)0) {
+            const real x6 = (real)1 / s6;     // (r / sigma_ij)^6
+            const real D = c.sc_a1l + x6, iD = (real)1 / D;
+            const real u = iD * iD - iD;
+            const real du = (iD - (real)2 * iD * iD) * iD;   // d(1/D^2 - 1/D)/dD
+            const real e = e4 * c.sc_lp;
+            gs = -e * (du * (real)6 * x6 * rinv * S + u * dS) * rinv;
+        }
+        return c.hA * fc + gs;
+    }
     if (uv) {
         // capped soft basis (Eq. 5-6): identical to LJ for r >= sigma_ij
         real fs = fl;
@@ -856,6 +873,13 @@ __device__ __forceinline__ PairConst<real> pair_const(const SysView<real>& s)
     c.tas = s.two_a_sqrtpi;
     c.hA = (real)s.lam->hA;
     c.hB = (real)s.lam->hB;
+    c.sc = s.sc_alpha > 0.0;
+    c.sc_a1l = c.sc_lp = 0;
+    if (c.sc) {
+        const double l = s.lam->lambda;
+        c.sc_a1l = (real)(s.sc_alpha * (1.0 - l));
+        c.sc_lp = (real)pow(l, s.sc_power);
+    }
     return c;
 }
 
@@ -1362,7 +1386,11 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
     const int n = min(s.flags[FL_NUV], nb.uv_cap);
     const double rc2 = (double)s.rc2, rsw = (double)s.rsw, swi = (double)s.sw_inv_w;
     const double alpha = (double)s.alpha;
-    double euv = 0.0, esoft = 0.0;
+    const bool sc = s.sc_alpha > 0.0;
+    const double lam = s.lam->lambda;
+    const double a1l = sc ? s.sc_alpha * (1.0 - lam) : 0.0, lp = sc ? pow(lam, s.sc_power) : 0.0;
+    const double dlp = sc ? (s.sc_power == 1.0 ? 1.0 : s.sc_power * pow(lam, s.sc_power - 1.0)) : 0.0;
+    double euv = 0.0, esoft = 0.0, edsc = 0.0;
     // consecutive pairs go to consecutive blocks, so that a list shorter than
     // the grid still spreads over every SM's FP64 units
     for (int w = threadIdx.x * gridDim.x + blockIdx.x; w < n; w += gridDim.x * blockDim.x) {
@@ -1381,7 +1409,15 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
         double e = qq * erfc(alpha * r) / r;
         const double sg = 0.5 * ((double)s.sig[a] + (double)s.sig[b]);
         const double ep = sqrt((double)s.eps[a] * (double)s.eps[b]);
-        if (ep > 0.0) {
+        if (ep > 0.0 && sc) {
+            // soft-core coupling at lambda: the energy and its lambda derivative
+            const double tt = fmax(0.0, (r - rsw) * swi);
+            const double S = 1.0 - tt * tt * tt * (10.0 - 15.0 * tt + 6.0 * tt * tt);
+            const double x2 = r2 / (sg * sg), x6 = x2 * x2 * x2;
+            const double D = a1l + x6, iD = 1.0 / D, u = iD * iD - iD;
+            esoft += 4.0 * ep * lp * u * S;
+            edsc += 4.0 * ep * S * (dlp * u + s.sc_alpha * lp * (2.0 * iD - 1.0) * iD * iD);
+        } else if (ep > 0.0) {
             const double tt = fmax(0.0, (r - rsw) * swi);
             const double S = 1.0 - tt * tt * tt * (10.0 - 15.0 * tt + 6.0 * tt * tt);
             const double s2 = sg * sg / r2, s6 = s2 * s2 * s2;
@@ -1398,9 +1434,11 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
     }
     const long long a0 = __double2ll_rn(warp_sum_d(euv) * ESCALE);
     const long long a1 = __double2ll_rn(warp_sum_d(esoft) * ESCALE);
+    const long long a2 = sc ? __double2ll_rn(warp_sum_d(edsc) * ESCALE) : 0ll;
     if ((threadIdx.x & 31) == 0) {
         if (a0) atomic_add_ll(&s.E[E_PAIR_UV], a0);
         if (a1) atomic_add_ll(&s.E[E_PAIR_SOFT], a1);
+        if (a2) atomic_add_ll(&s.E[E_DSC], a2);
     }
 }
 

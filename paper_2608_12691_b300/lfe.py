@@ -78,6 +78,8 @@ class Params(ctypes.Structure):
         ("opes_max_kernels", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
         ("lambda_temperature", ctypes.c_double),
+        ("sc_alpha", ctypes.c_double),
+        ("sc_power", ctypes.c_double),
     ]
 
 
@@ -230,6 +232,8 @@ class System:
         pr.opes_max_kernels = int(d.get("opes_max_kernels", 1024))
         pr.seed = int(seed)
         pr.lambda_temperature = float(d.get("lambda_temperature", 0.0))
+        pr.sc_alpha = float(d.get("sc_alpha", 0.0) or 0.0)
+        pr.sc_power = float(d.get("sc_power", 1.0) or 1.0)
         for k, v in over.items():
             setattr(pr, k, v)
         self.params = pr
