@@ -414,6 +414,26 @@ int lfe_batch_time_pairs(lfe_batch* b, int reps, double* ms, void* stream);
  * evaluations. */
 int lfe_batch_exchange(lfe_batch* b, int n, int* ladder, double temperature, unsigned long long seed,
                        unsigned long long attempt, int* accepted, void* stream);
+/* The same exchange on the device, inside lfe_batch_step: after every
+ * `stride` batch steps (stride <= 0 switches it off) a captured exchange
+ * graph is enqueued on the step's stream -- an evaluation of every replica
+ * of the ladder at its own lambda and current configuration (with its own
+ * conditional list rebuild), then one device kernel that takes the
+ * attempt's Metropolis decisions exactly as lfe_batch_exchange does (same
+ * Delta, same Philox counter (k, attempt_lo, attempt_hi, 3), attempts
+ * numbered from 0 when the exchange is set) and swaps the lambdas and the
+ * ladder entries on the device.  The host takes no decision and reads no
+ * energy; before each attempt it checks each replica's list-overflow flag
+ * (regrowing a list that overflowed, so that no energy comes from a
+ * truncated list).  lfe_batch_set_exchange validates the ladder as
+ * lfe_batch_exchange does and resets the counters; lfe_batch_exchange_state
+ * (synchronises) reads back the ladder [n], the number of attempts and the
+ * accepted swaps per ladder position [n-1] (any pointer may be NULL; the
+ * replicas' lambdas are read with lfe_get_state).  Errors: LFE_ERR_ARG,
+ * LFE_ERR_STATE (soft-core coupling; no exchange set). */
+int lfe_batch_set_exchange(lfe_batch* b, int n, const int* ladder, double temperature, unsigned long long seed,
+                           int stride);
+int lfe_batch_exchange_state(lfe_batch* b, int* ladder, unsigned long long* attempts, unsigned long long* accepted);
 const char* lfe_batch_last_error(const lfe_batch* b);
 void lfe_batch_destroy(lfe_batch* b);
 

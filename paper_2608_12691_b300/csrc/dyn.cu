@@ -927,6 +927,64 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     if (lane < E_N) E[lane] = 0;
 }
 
+// Lambda replica exchange on the device (the paper's HREX protocol, Section
+// 2.6, on the linear-basis potential of Eq. 4): one attempt over the ladder
+// (replica indices in increasing lambda), from the basis energies U_uv and
+// U_soft that the exchange evaluation has just written for every replica at
+// its current configuration (terms[r][4], terms[r][5]).  The pairs (k, k+1)
+// of the attempt's parity are tried; Delta = (h_A(l_k+1) - h_A(l_k))
+// (U_uv,k - U_uv,k+1) + (h_B(l_k+1) - h_B(l_k)) (U_soft,k - U_soft,k+1); the
+// pair is accepted when Delta <= 0 or u < exp(-beta Delta), u = (x + 0.5) /
+// 2^32 with x the first word of Philox4x32-10 at counter (k, attempt_lo,
+// attempt_hi, 3).  An accepted pair exchanges the two replicas' lambdas
+// (theta = lambda, p_theta = 0) and their ladder entries.  One thread.
+__device__ void set_lambda_state(LamState* L, double lam)
+{
+    double hA, hB, dA, dB;
+    switching_fns(lam, hA, hB, dA, dB);
+    L->theta = lam;
+    L->p_theta = 0.0;
+    L->dlam_dtheta = 1.0;
+    L->lambda = lam;
+    L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
+}
+
+__global__ void k_hrex(LamState* const* lams, const double* terms, int* ladder, int n, double beta, uint2 key,
+                       unsigned long long* attempt, unsigned long long* accepted)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long a = *attempt;
+    for (int k = (int)(a & 1ull); k + 1 < n; k += 2) {
+        const int ri = ladder[k], rj = ladder[k + 1];
+        LamState* Li = lams[ri];
+        LamState* Lj = lams[rj];
+        const double li = Li->lambda, lj = Lj->lambda;
+        double hAi, hBi, hAj, hBj, d0, d1;
+        switching_fns(li, hAi, hBi, d0, d1);
+        switching_fns(lj, hAj, hBj, d0, d1);
+        const double* ti = terms + (size_t)ri * LFE_NTERMS;
+        const double* tj = terms + (size_t)rj * LFE_NTERMS;
+        const double delta = (hAj - hAi) * (ti[4] - tj[4]) + (hBj - hBi) * (ti[5] - tj[5]);
+        const uint4 r = philox4x32_10(make_uint4((unsigned)k, (unsigned)a, (unsigned)(a >> 32), 3u), key);
+        const double u = (r.x + 0.5) / 4294967296.0;
+        if (delta <= 0.0 || u < exp(-beta * delta)) {
+            set_lambda_state(Li, lj);
+            set_lambda_state(Lj, li);
+            ladder[k] = rj;
+            ladder[k + 1] = ri;
+            accepted[k] += 1ull;
+        }
+    }
+    *attempt = a + 1ull;
+}
+
+void launch_hrex(LamState* const* lams, const double* terms, int* ladder, int n, double beta, unsigned long long seed,
+                 unsigned long long* attempt, unsigned long long* accepted, cudaStream_t st)
+{
+    k_hrex<<<1, 32, 0, st>>>(lams, terms, ladder, n, beta,
+                             make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32)), attempt, accepted);
+}
+
 // first node of a captured step: the neighbour list is rebuilt (by the
 // conditional node that follows) when the previous step left an atom more
 // than skin/2 from where the list was built; no rebuild once a rebuild has

@@ -122,6 +122,11 @@ struct SystemBase {
     virtual void record_eval(cudaStream_t s, bool with_pairs) = 0;
     virtual void record_post(cudaStream_t s) = 0;
     virtual bool pair_job(PairJob* out) = 0;   // false for FP64 systems
+    // the evaluation of the device-side lambda exchange: rebuild decision and
+    // conditional rebuild, every evaluation kernel, and the output kernel
+    // writing the energy terms to `terms` (device) and consuming the forces
+    virtual void record_exchange_eval(cudaStream_t s, double* terms) = 0;
+    virtual LamState* lam_state_device() = 0;
     virtual void note_batch_steps(int n) = 0;
     virtual bool overflow_pending(cudaStream_t st) = 0;
     virtual void recover(cudaStream_t st) = 0;
@@ -1565,6 +1570,15 @@ struct System final : SystemBase {
         record_post(s0);
     }
 
+    void record_exchange_eval(cudaStream_t s0, double* terms) override
+    {
+        record_pre(s0);
+        record_eval(s0, true);
+        launch_eval_out(S, nullptr, terms, const_vv, const_uu, const_uv, s0);
+    }
+
+    LamState* lam_state_device() override { return S.lam; }
+
     bool pair_job(PairJob* out) override
     {
         if constexpr (std::is_same<real, float>::value) {
@@ -2302,6 +2316,42 @@ struct lfe_batch {
     int since_check = 0;
     std::vector<unsigned> gens;
     std::string err;
+    // device-side lambda exchange every `ex_stride` batch steps: its own
+    // captured graph (the replicas' evaluations, then k_hrex), enqueued by
+    // lfe_batch_step after the step graph without synchronising; the ladder,
+    // the attempt counter and the accepted counts stay on the device
+    int ex_stride = 0, ex_n = 0;
+    unsigned long long ex_seed = 0;
+    double ex_beta = 0.0;
+    unsigned long long ex_steps = 0;          // batch steps since the exchange was set
+    int* d_ladder = nullptr;
+    unsigned long long* d_ex_ctr = nullptr;   // [0] attempts, [1 .. n-1] accepted per ladder position
+    double* d_ex_terms = nullptr;             // [replicas][LFE_NTERMS]
+    LamState** d_ex_lams = nullptr;
+    cudaGraph_t ex_graph = nullptr;
+    cudaGraphExec_t ex_exec = nullptr;
+    std::vector<int> ex_members;
+
+    void capture_exchange()
+    {
+        if (ex_exec) { cudaGraphExecDestroy(ex_exec); ex_exec = nullptr; }
+        if (ex_graph) { cudaGraphDestroy(ex_graph); ex_graph = nullptr; }
+        std::vector<LamState*> lams(sys.size());
+        for (size_t i = 0; i < sys.size(); ++i) lams[i] = sys[i]->impl->lam_state_device();
+        CK(cudaMemcpy(d_ex_lams, lams.data(), sizeof(LamState*) * sys.size(), cudaMemcpyHostToDevice));
+        CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+        CK(cudaEventRecord(fork, s0));
+        for (int i : ex_members) {
+            CK(cudaStreamWaitEvent(lanes[i], fork, 0));
+            sys[i]->impl->record_exchange_eval(lanes[i], d_ex_terms + (size_t)i * LFE_NTERMS);
+            CK(cudaEventRecord(join[i], lanes[i]));
+            CK(cudaStreamWaitEvent(s0, join[i], 0));
+        }
+        launch_hrex(d_ex_lams, d_ex_terms, d_ladder, ex_n, ex_beta, ex_seed, d_ex_ctr, d_ex_ctr + 1, s0);
+        CK(cudaStreamEndCapture(s0, &ex_graph));
+        CK(cudaGraphInstantiate(&ex_exec, ex_graph, 0));
+    }
+
     // the FP32 replicas' pair kernels run as one launch (k_pairs2_batch)
     PairJob* d_jobs = nullptr;
     int n_jobs = 0, jobs_cap = 0;
@@ -2320,6 +2370,12 @@ struct lfe_batch {
         if (s0) cudaStreamDestroy(s0);
         if (s_pair) cudaStreamDestroy(s_pair);
         if (d_jobs) cudaFree(d_jobs);
+        if (ex_exec) cudaGraphExecDestroy(ex_exec);
+        if (ex_graph) cudaGraphDestroy(ex_graph);
+        if (d_ladder) cudaFree(d_ladder);
+        if (d_ex_ctr) cudaFree(d_ex_ctr);
+        if (d_ex_terms) cudaFree(d_ex_terms);
+        if (d_ex_lams) cudaFree(d_ex_lams);
     }
 
     // the descriptors of the FP32 replicas (views of their device buffers,
@@ -2385,6 +2441,8 @@ struct lfe_batch {
     {
         if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
         if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+        if (ex_exec) { cudaGraphExecDestroy(ex_exec); ex_exec = nullptr; }
+        if (ex_graph) { cudaGraphDestroy(ex_graph); ex_graph = nullptr; }
     }
 
     // one step of every replica: each replica's rebuild decision and
@@ -2447,12 +2505,23 @@ struct lfe_batch {
     {
         if (exec && stale()) invalidate();
         if (!exec) capture();
+        if (ex_stride > 0 && !ex_exec) capture_exchange();
         for (int k = 0; k < n; ++k) {
             CK(cudaGraphLaunch(exec, st));
             for (auto* s : sys) s->impl->note_batch_steps(1);
+            if (ex_stride > 0 && (++ex_steps % (unsigned long long)ex_stride) == 0ull) {
+                // an overflowed list must be regrown before the exchange reads energies
+                if (since_check > 0) {
+                    check(st);
+                    if (!exec) capture();
+                }
+                if (!ex_exec) capture_exchange();
+                CK(cudaGraphLaunch(ex_exec, st));
+            }
             if (++since_check >= 64) {
                 check(st);
                 if (!exec) capture();
+                if (ex_stride > 0 && !ex_exec) capture_exchange();
             }
         }
     }
@@ -2751,6 +2820,76 @@ int lfe_batch_step(lfe_batch* b, int n_steps, void* stream)
     if (!b || n_steps < 0) return LFE_ERR_ARG;
     try {
         b->step(n_steps, (cudaStream_t)stream);
+    } catch (const Failure& e) {
+        b->err = e.msg;
+        return e.code;
+    }
+    return LFE_OK;
+}
+
+int lfe_batch_set_exchange(lfe_batch* b, int n, const int* ladder, double temperature, unsigned long long seed,
+                           int stride)
+{
+    if (!b) return LFE_ERR_ARG;
+    try {
+        CK(cudaDeviceSynchronize());
+        if (stride <= 0) {
+            b->ex_stride = 0;
+            return LFE_OK;
+        }
+        if (!ladder || n < 2 || !(temperature > 0) || !std::isfinite(temperature))
+            fail(LFE_ERR_ARG, "lfe_batch_set_exchange: ladder of >= 2 replicas and temperature > 0 required");
+        std::vector<char> seen(b->sys.size(), 0);
+        double prev = -1.0;
+        for (int k = 0; k < n; ++k) {
+            const int r = ladder[k];
+            if (r < 0 || r >= (int)b->sys.size() || seen[r]) fail(LFE_ERR_ARG, "ladder entries must be distinct replica indices");
+            seen[r] = 1;
+            if (b->sys[r]->impl->soft_core())
+                fail(LFE_ERR_STATE, "lambda exchange needs the linear-basis coupling (sc_alpha = 0)");
+            double lam = 0, m = 0;
+            b->sys[r]->impl->lambda_state(&lam, &m);
+            if (m > 0) fail(LFE_ERR_ARG, "replica " + std::to_string(r) + " has a dynamical theta (lambda_mass > 0)");
+            if (!(lam >= prev)) fail(LFE_ERR_ARG, "ladder must list the replicas in lambda order");
+            prev = lam;
+        }
+        const size_t R = b->sys.size();
+        if (!b->d_ladder) {
+            CK(cudaMalloc(&b->d_ladder, sizeof(int) * R));
+            CK(cudaMalloc(&b->d_ex_ctr, sizeof(unsigned long long) * R));
+            CK(cudaMalloc(&b->d_ex_terms, sizeof(double) * LFE_NTERMS * R));
+            CK(cudaMalloc(&b->d_ex_lams, sizeof(LamState*) * R));
+        }
+        CK(cudaMemcpy(b->d_ladder, ladder, sizeof(int) * n, cudaMemcpyHostToDevice));
+        CK(cudaMemset(b->d_ex_ctr, 0, sizeof(unsigned long long) * R));
+        CK(cudaMemset(b->d_ex_terms, 0, sizeof(double) * LFE_NTERMS * R));
+        b->ex_members.assign(ladder, ladder + n);
+        b->ex_n = n;
+        b->ex_seed = seed;
+        b->ex_beta = 1.0 / (lfe::KB * temperature);
+        b->ex_stride = stride;
+        b->ex_steps = 0;
+        if (b->ex_exec) { cudaGraphExecDestroy(b->ex_exec); b->ex_exec = nullptr; }
+        if (b->ex_graph) { cudaGraphDestroy(b->ex_graph); b->ex_graph = nullptr; }
+    } catch (const Failure& e) {
+        b->err = e.msg;
+        return e.code;
+    }
+    return LFE_OK;
+}
+
+int lfe_batch_exchange_state(lfe_batch* b, int* ladder, unsigned long long* attempts, unsigned long long* accepted)
+{
+    if (!b) return LFE_ERR_ARG;
+    try {
+        if (!b->d_ladder) fail(LFE_ERR_STATE, "no device exchange has been set");
+        CK(cudaDeviceSynchronize());
+        if (ladder) CK(cudaMemcpy(ladder, b->d_ladder, sizeof(int) * b->ex_n, cudaMemcpyDeviceToHost));
+        std::vector<unsigned long long> c(b->sys.size());
+        CK(cudaMemcpy(c.data(), b->d_ex_ctr, sizeof(unsigned long long) * c.size(), cudaMemcpyDeviceToHost));
+        if (attempts) *attempts = c[0];
+        if (accepted)
+            for (int k = 0; k + 1 < b->ex_n; ++k) accepted[k] = c[1 + k];
     } catch (const Failure& e) {
         b->err = e.msg;
         return e.code;

@@ -245,6 +245,8 @@ struct PairJob {
 };
 void launch_pairs_batch(const PairJob* jobs, int njobs, int nblocks, cudaStream_t st);
 int pairs_batch_blocks();   // one resident wave of the launch over many systems
+void launch_hrex(LamState* const* lams, const double* terms, int* ladder, int n, double beta, unsigned long long seed,
+                 unsigned long long* attempt, unsigned long long* accepted, cudaStream_t st);
 template <typename real> void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, cudaStream_t st);
 template <typename real> int pairs_blocks_per_sm();
 template <typename real> void launch_uv_energy(const SysView<real>& s, const NblView<real>& nb, int nblocks, cudaStream_t st);

@@ -31,7 +31,8 @@ EXPORTED = [
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step", "lfe_batch_time_pairs",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step", "lfe_batch_time_pairs", "lfe_batch_set_exchange",
+    "lfe_batch_exchange_state",
     "lfe_batch_exchange", "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
 NOALLOC_MAX_GRID = 110592
@@ -154,6 +155,10 @@ def load():
     lib.lfe_batch_step.argtypes = [vp, ctypes.c_int, vp]
     lib.lfe_batch_time_pairs.argtypes = [vp, ctypes.c_int, vp, vp]
     lib.lfe_batch_time_pairs.restype = ctypes.c_int
+    lib.lfe_batch_set_exchange.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int]
+    lib.lfe_batch_set_exchange.restype = ctypes.c_int
+    lib.lfe_batch_exchange_state.argtypes = [vp, vp, vp, vp]
+    lib.lfe_batch_exchange_state.restype = ctypes.c_int
     lib.lfe_batch_destroy.argtypes = [vp]
     lib.lfe_batch_destroy.restype = None
     lib.lfe_batch_last_error.argtypes = [vp]
@@ -488,6 +493,23 @@ class Batch:
 
     def step(self, n, stream=None):
         self._check(self._lib.lfe_batch_step(self.h, int(n), _stream_ptr(stream)))
+
+    def set_exchange(self, ladder, temperature, seed, stride):
+        """Device-side lambda exchange every `stride` batch steps
+        (lfe_batch_set_exchange; stride <= 0 switches it off)."""
+        lad = np.ascontiguousarray(ladder, dtype=np.int32)
+        self._check(self._lib.lfe_batch_set_exchange(self.h, len(lad), lad.ctypes.data, float(temperature), int(seed),
+                                                     int(stride)))
+
+    def exchange_state(self):
+        """(ladder, attempts, accepted per ladder position) of the device-side
+        exchange (lfe_batch_exchange_state)."""
+        n = len(self.systems)
+        lad = np.zeros(n, dtype=np.int32)
+        att = ctypes.c_ulonglong()
+        acc = np.zeros(max(n - 1, 1), dtype=np.uint64)
+        self._check(self._lib.lfe_batch_exchange_state(self.h, lad.ctypes.data, ctypes.byref(att), acc.ctypes.data))
+        return lad, int(att.value), acc
 
     def time_pairs(self, reps=20, stream=None):
         """Mean device time (ms) of the FP32 replicas' shared pair-kernel launch

@@ -75,3 +75,43 @@ def test_exchange_rejects_bad_ladders():
     b.close()
     g1.close()
     g2.close()
+
+
+def test_device_exchange_inside_batch_steps_matches_oracle():
+    # lfe_batch_set_exchange: an attempt after every batch step, decided on
+    # the device from each replica's configuration after the step; the
+    # oracle's attempt on the same configurations gives the same swaps
+    ds = [dict(d, dt=0.001) for d in replicas()]
+    gs = [lfe.System(d, precision=lfe.LFE_FP64, theta0=d["lam"], seed=100 + k) for k, d in enumerate(ds)]
+    b = lfe.Batch(gs)
+    ladder = list(range(len(gs)))
+    lam_of = {k: LAMS[k] for k in range(len(gs))}
+    b.set_exchange(ladder, T, SEED, 1)
+    n_acc = n_rej = 0
+    for attempt in range(6):
+        b.step(1)
+        pos = [g.get_state()[0] for g in gs]
+        E = [R.nonbonded(dict(d, pos=p), level=2)[0] for d, p in zip(ds, pos)]
+        order = list(ladder)
+        acc_o, new_o = D.hrex_attempt([lam_of[r] for r in order], [E[r]["U_uv"] for r in order],
+                                      [E[r]["U_soft"] for r in order], T, SEED, attempt)
+        for p_, r in enumerate(order):
+            lam_of[r] = new_o[p_]
+        for k, a in enumerate(acc_o):
+            if a:
+                ladder[k], ladder[k + 1] = ladder[k + 1], ladder[k]
+        lad_dev, attempts, acc = b.exchange_state()
+        assert attempts == attempt + 1
+        assert list(lad_dev) == ladder
+        for r, g in enumerate(gs):
+            assert g.get_state()[2]["lambda"] == pytest.approx(lam_of[r], abs=1e-15)
+        tried = range(attempt % 2, len(gs) - 1, 2)
+        n_acc += sum(acc_o[k] for k in tried)
+        n_rej += sum(1 - acc_o[k] for k in tried)
+    assert n_acc > 0 and n_rej > 0
+    b.set_exchange(ladder, T, SEED, 0)      # off: plain batch steps again, no more attempts
+    b.step(2)
+    assert b.exchange_state()[1] == 6
+    b.close()
+    for g in gs:
+        g.close()
