@@ -486,11 +486,11 @@ def run_ours(args):
     # kernel; spread, plane transform, column pass, inverse plane transform,
     # gather; df64 energy branch (two transform passes, column pass); kicks
     # and OPES bias, exclusions/1-4, bonded, FP64 uv energies; integrator,
-    # theta (which also ends the step).  A neighbour-list build adds 12 kernels (column keys,
+    # theta (which also ends the step).  A neighbour-list build adds 11 kernels (column keys,
     # column scan, scatter, column sort, slot assignment, tile search, tile
-    # scan, placement + masks, j-entry order, uv pair count, scan, write).
+    # scan, placement + masks, uv pair count, scan, write).
     per_step = 17 if prec == lfe.LFE_FP32_MIXED else 14
-    launches = args.steps * per_step + rebuilds * 12
+    launches = args.steps * per_step + rebuilds * 11
     n_tiles = int(ext1["n_tiles"])
 
     out = None

@@ -101,24 +101,6 @@ void launch_eval_out(const SysView<real>& s, double* forces, double* terms, doub
     k_eval_out<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, forces, terms, cvv, cuu, cuv);
 }
 
-// master positions from caller doubles; refresh the sorted copy in the
-// current slot order
-template <typename real>
-__global__ void k_assign_positions(SysView<real> s, const double* pos)
-{
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= s.n) return;
-    R4<real> p;
-    p.x = (real)pos[3 * a]; p.y = (real)pos[3 * a + 1]; p.z = (real)pos[3 * a + 2]; p.w = (real)0;
-    s.x[a] = p;
-}
-
-template <typename real>
-void launch_assign_positions(const SysView<real>& s, const double* pos, cudaStream_t st)
-{
-    k_assign_positions<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos);
-}
-
 template <typename real>
 __global__ void k_refresh_sorted(SysView<real> s)
 {
@@ -139,16 +121,19 @@ void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st)
     k_refresh_sorted<real><<<(s.n + 255) / 256, 256, 0, st>>>(s);
 }
 
-// after new positions: refresh the sorted copy and raise the rebuild flag
-// when an atom lies more than skin/2 from where the list was built
+// new positions from caller doubles (caller order): assign the master copy,
+// refresh the cluster-sorted copy in the current slot order, and raise the
+// rebuild flag when an atom lies more than skin/2 from where the list was
+// built (a non-finite position raises it too)
 template <typename real>
-__global__ void k_moved(SysView<real> s, real skin_half2)
+__global__ void k_assign_moved(SysView<real> s, const double* pos, real skin_half2)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     bool far = false;
     if (a < s.n) {
         const int slot = s.iperm[a];
-        const R4<real> x = s.x[a];
+        const R4<real> x{(real)pos[3 * a], (real)pos[3 * a + 1], (real)pos[3 * a + 2], (real)0};
+        s.x[a] = x;
         const R4<real> xr = s.xref[a];
         R4<real> o = s.xq[slot];
         o.x = sorted_coord(x.x, xr.x, s.L[0], s.invL[0]);
@@ -158,9 +143,15 @@ __global__ void k_moved(SysView<real> s, real skin_half2)
         const real dx = minimg(x.x - xr.x, s.L[0], s.invL[0]);
         const real dy = minimg(x.y - xr.y, s.L[1], s.invL[1]);
         const real dz = minimg(x.z - xr.z, s.L[2], s.invL[2]);
-        far = !(dx * dx + dy * dy + dz * dz <= skin_half2);   // also true for a non-finite position
+        far = !(dx * dx + dy * dy + dz * dz <= skin_half2);
     }
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_REBUILD], 1);
+}
+
+template <typename real>
+void launch_assign_moved(const SysView<real>& s, const double* pos, real skin_half2, cudaStream_t st)
+{
+    k_assign_moved<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos, skin_half2);
 }
 
 // Monte Carlo volume move (the NPT runs of Section 2.6): every molecule's
@@ -243,22 +234,6 @@ template <typename real>
 void launch_pack_state(const SysView<real>& s, const OpesState* o, double* out, cudaStream_t st)
 {
     k_pack_state<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, o, out);
-}
-
-// the conditional rebuild node of a captured graph follows the rebuild flag
-template <typename real>
-__global__ void k_cond_rebuild(SysView<real> s, cudaGraphConditionalHandle h)
-{
-    const int rb = s.flags[FL_REBUILD];
-    cudaGraphSetConditional(h, rb ? 1u : 0u);
-    s.flags[FL_REBUILD] = 0;
-}
-
-template <typename real>
-void launch_moved(const SysView<real>& s, real skin_half2, cudaGraphConditionalHandle h, cudaStream_t st)
-{
-    k_moved<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, skin_half2);
-    k_cond_rebuild<real><<<1, 1, 0, st>>>(s, h);
 }
 
 // Dihedral of atoms (i, j, k, l) from r_ij = x_i - x_j, r_kj = x_k - x_j,
@@ -1014,9 +989,8 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_set_lambda<real>(const SysView<real>&, double, cudaStream_t);                    \
     template void launch_eval_out<real>(const SysView<real>&, double*, double*, double, double, double,   \
                                         cudaStream_t);                                                    \
-    template void launch_assign_positions<real>(const SysView<real>&, const double*, cudaStream_t);        \
+    template void launch_assign_moved<real>(const SysView<real>&, const double*, real, cudaStream_t);       \
     template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
-    template void launch_moved<real>(const SysView<real>&, real, cudaGraphConditionalHandle, cudaStream_t); \
     template void launch_pack_state<real>(const SysView<real>&, const OpesState*, double*, cudaStream_t);   \
     template void launch_scale_molecules<real>(const SysView<real>&, const int*, const int*, const double*, int, \
                                                double, const double*, cudaStream_t);                         \

@@ -4,6 +4,7 @@
 // checkpoints and the C-ABI entry points declared in include/lfe.h.
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <unistd.h>
@@ -55,14 +56,20 @@ void philox_host(unsigned c[4], unsigned k0, unsigned k1)
 
 // x * 0 is 0 for every finite x and NaN for an infinity or a NaN, so one
 // branch-free (vectorisable) sum answers for the whole array
+// every value finite: an IEEE double is infinite or NaN exactly when its 11
+// exponent bits are all ones, and then adding 1 to the exponent field carries
+// into the sign bit; integer AND/ADD/OR only, so the loop vectorises and runs
+// at memory speed (positions just written by a device copy are read from DRAM)
 bool finite_all(const double* a, size_t n)
 {
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    size_t i = 0;
-    for (; i + 4 <= n; i += 4)
-        for (int k = 0; k < 4; ++k) acc[k] += a[i + k] * 0.0;
-    for (; i < n; ++i) acc[0] += a[i] * 0.0;
-    return std::isfinite(acc[0] + acc[1] + acc[2] + acc[3]);
+    const uint64_t E = 0x7ff0000000000000ull, ONE = 0x0010000000000000ull;
+    uint64_t acc = 0;
+    for (size_t i = 0; i < n; ++i) {
+        uint64_t b;
+        std::memcpy(&b, a + i, sizeof b);
+        acc |= (b & E) + ONE;
+    }
+    return (acc >> 63) == 0;
 }
 
 bool radix_plan(int K, int* rad, int* nrad)
@@ -927,8 +934,8 @@ struct System final : SystemBase {
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        launch_assign_positions(S, d_pos, s0);
-        launch_moved(S, G.skin_half2, h, s0);
+        launch_assign_moved(S, d_pos, G.skin_half2, s0);
+        launch_rebuild_cond(S, h, s0);
         add_cond_build(s0, h);
         CK(cudaStreamEndCapture(s0, &pos_graph));
         CK(cudaGraphInstantiate(&pos_exec, pos_graph, 0));
@@ -1663,12 +1670,10 @@ struct System final : SystemBase {
         cudaGraph_t g = nullptr;
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
         if (pos_in) {
-            cudaGraphConditionalHandle hp;
-            CK(cudaGraphConditionalHandleCreate(&hp, g, 0, cudaGraphCondAssignDefault));
+            // the step's own conditional rebuild (first branch below) acts
+            // on the flag that the new positions raise
             CK(cudaMemcpyAsync(d_pos, pos_in, sizeof(double) * nv, cudaMemcpyHostToDevice, s0));
-            launch_assign_positions(S, d_pos, s0);
-            launch_moved(S, G.skin_half2, hp, s0);
-            add_cond_build(s0, hp);
+            launch_assign_moved(S, d_pos, G.skin_half2, s0);
         }
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
