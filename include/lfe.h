@@ -329,9 +329,11 @@ int lfe_set_theta(lfe_system* sys, double theta, double p_theta);
 /* Neighbour-list capacity (Section 2.6 states the cutoff and switch the list
  * serves; the list itself is this library's data structure).  Replaces the
  * tile list by one holding exactly `tiles` tiles of 8 i atoms x 32 j atoms
- * and flags a rebuild, so that the next step or evaluation builds the list
- * again within it.  When a later build needs more tiles the library grows
- * the list by itself: a build inside a captured step marks the step and the
+ * (and, with a solute, the solute-solvent pair list by one of `tiles` solute
+ * tiles and 32 x `tiles` pairs) and flags a rebuild, so that the next step
+ * or evaluation builds the lists again within them.  When a later build
+ * needs more room the library grows the lists by itself: a build inside a
+ * captured step marks the step and the
  * ones after it as skipped, and the next synchronising call (or every 64
  * steps) grows the list, rebuilds it and replays the skipped steps; results
  * are those of an uncapped list.  Meant for memory-constrained callers and

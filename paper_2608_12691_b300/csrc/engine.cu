@@ -404,11 +404,7 @@ struct System final : SystemBase {
         N.stage_cap = N.cap;
         N.stage_hdr = dalloc<int4>(N.stage_cap);
         N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
-        N.uv_tiles_max = std::max(1, n_ucl * 512);
-        N.uv_cnt = dalloc<int>(N.uv_tiles_max);
-        N.uv_off = dalloc<int>(N.uv_tiles_max + 1);
-        N.uv_cap = std::max(1024, n_u * 2048);
-        N.uvp = dalloc<int4>(N.uv_cap);
+        grow_uv(std::max(1, n_ucl * 512), std::max(1024, n_u * 2048));
         N.cut2 = (float)((p.r_cut + skin) * (p.r_cut + skin));
         N.skin_half2 = (float)(0.25 * skin * skin);
         {
@@ -879,9 +875,41 @@ struct System final : SystemBase {
         invalidate_graph();
     }
 
-    // growth after an overflow seen in the flags
+    // the solute-solvent pair list: tiles of solute sub-clusters it can take
+    // (counts and offsets) and pairs it can hold
+    void grow_uv(int tiles, int pairs)
+    {
+        ++generation;
+        dfree(N.uv_cnt);
+        dfree(N.uv_off);
+        dfree(N.uvp);
+        N.uv_tiles_max = tiles;
+        N.uv_cnt = dalloc<int>(N.uv_tiles_max);
+        N.uv_off = dalloc<int>(N.uv_tiles_max + 1);
+        N.uv_cap = pairs;
+        N.uvp = dalloc<int4>(N.uv_cap);
+        invalidate_graph();
+    }
+
+    // a build that wanted more room than some list has (flags as last read)
+    bool list_short() const
+    {
+        return h_flags[FL_NTILES] > N.cap || h_flags[FL_NSTAGE] > N.stage_cap || h_flags[FL_NUVT] > N.uv_tiles_max ||
+               h_flags[FL_NUV] > N.uv_cap;
+    }
+
+    // growth after an overflow seen in the flags: every list that ran short
+    // is doubled past what the build asked for (the tile list at least
+    // doubles).  A build whose solute-solvent tiles did not all fit counted
+    // the pairs of the first ones only, so the pair list is then sized for
+    // the bound of 256 pairs per tile.
     void grow_for_flags()
     {
+        const int uvt = h_flags[FL_NUVT], uvp = h_flags[FL_NUV];
+        if (uvt > N.uv_tiles_max || uvp > N.uv_cap) {
+            const long long pairs = std::max<long long>(2LL * uvp, uvt > N.uv_tiles_max ? 256LL * uvt : 0LL);
+            grow_uv(std::max(N.uv_tiles_max, 2 * uvt), (int)std::max<long long>(N.uv_cap, pairs));
+        }
         grow_tiles(std::max(h_flags[FL_NTILES], N.cap) * 2, 2 * h_flags[FL_NSTAGE]);
     }
 
@@ -903,8 +931,8 @@ struct System final : SystemBase {
         launch_build_nbl(S, N, st);
         CK(cudaMemcpyAsync(h_flags, S.flags, sizeof(int) * FL_N, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (h_flags[FL_NTILES] > N.cap || h_flags[FL_NSTAGE] > N.stage_cap) {
-            grow_tiles(2 * h_flags[FL_NTILES], 2 * h_flags[FL_NSTAGE]);
+        if (list_short()) {
+            grow_for_flags();
             int zero = 0;
             CK(cudaMemcpy(S.flags + FL_ERROR, &zero, sizeof(int), cudaMemcpyHostToDevice));
             launch_build_nbl(S, N, st);
@@ -1356,6 +1384,7 @@ struct System final : SystemBase {
         grow_tiles(tiles, tiles);
         N.cap = tiles;
         N.stage_cap = tiles;
+        if (S.n_ucl > 0) grow_uv(tiles, 32 * tiles);
         const int one = 1;
         CK(cudaMemcpy(S.flags + FL_REBUILD, &one, sizeof(int), cudaMemcpyHostToDevice));
     }

@@ -678,7 +678,10 @@ __global__ void __launch_bounds__(128) k_uv_pairs(SysView<real> s, NblView<real>
     const int lane = threadIdx.x & 31;
     if (t >= nb.uv_tiles_max) return;
     const int nuvt = s.n_ucl > 0 ? min(nb.tile_off[4 * s.n_ucl], nb.cap) : 0;
-    if (t == 0 && lane == 0 && !WRITE && nuvt > nb.uv_tiles_max) atomicOr(&s.flags[FL_ERROR], ERRB_OVERFLOW);
+    if (t == 0 && lane == 0 && !WRITE) {
+        s.flags[FL_NUVT] = nuvt;
+        if (nuvt > nb.uv_tiles_max) atomicOr(&s.flags[FL_ERROR], ERRB_OVERFLOW);
+    }
     unsigned keep = 0u;   // row of lane i < 8: bits k of kept pairs (i, k)
     int4 tl = make_int4(0, 13, 0, 0);
     int js = -1;
