@@ -578,6 +578,34 @@ def octanol_chain(rng, dihedral_sd=8.0):
     return xyz, bonds
 
 
+def _separate_chains(seed, xyzs, centres, fixed_xyz, box, r_min=0.13, rounds=20):
+    """Chains (list of (27, 3) arrays around their slot centres) redrawn
+    until no atom of one comes within r_min of an atom of another or of
+    fixed_xyz: each round, every chain in such a contact (the later one of
+    a chain-chain pair) gets a new conformation and flip at its slot, from
+    a generator of its own (seeded by seed), so that starts without such
+    contacts are left as drawn."""
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng([seed, 1])
+    xyzs = [np.asarray(x, dtype=np.float64) for x in xyzs]
+    n_f = len(fixed_xyz)
+    for _ in range(rounds):
+        allx = np.concatenate([fixed_xyz] + xyzs)
+        owner = np.concatenate([np.full(n_f, -1)] + [np.full(len(x), c) for c, x in enumerate(xyzs)])
+        tree = cKDTree(np.mod(allx, box), boxsize=np.asarray(box, dtype=np.float64))
+        pr = tree.query_pairs(r_min, output_type="ndarray")
+        a, b = owner[pr[:, 0]], owner[pr[:, 1]]
+        hit = np.unique(np.maximum(a[a != b], b[a != b]))
+        if hit.size == 0:
+            break
+        for c in hit:
+            xyz, _ = octanol_chain(rng)
+            if rng.random() < 0.5:
+                xyz = xyz * np.array([1.0, -1.0, -1.0])
+            xyzs[c] = centres[c] + xyz
+    return xyzs
+
+
 def make_octanol_box(seed=2609, n_chains=500, box_len=4.8, nx=12, ny=11, nz=4, lam=None,
                      mass_scale=0.1, r_cut=1.0, grid=48):
     """Octanol-like solvation box: n_chains 27-atom chains packed in nz layers
@@ -610,8 +638,9 @@ def make_octanol_box(seed=2609, n_chains=500, box_len=4.8, nx=12, ny=11, nz=4, l
     if len(keep) < n_chains:
         raise ValueError("not enough chain slots")
     keep = np.sort(rng.choice(keep, size=n_chains, replace=False))
-    for k in keep:
-        xyz, bonds = chains[k]
+    placed = _separate_chains(seed, [chains[k][0] for k in keep], slots[keep], sxyz, box)
+    for k, xyz in zip(keep, placed):
+        bonds = chains[k][1]
         q = np.array([OCT_Q[e] for e in OCT_ELEM])
         q[7] = -0.18 + 0.68     # neutralise: the carbon bonded to O carries +0.50 e
         sig = np.array([OCT_LJ[e][0] for e in OCT_ELEM])
