@@ -231,6 +231,73 @@ def theta_step(theta, p_theta, dUdl, dlam_dtheta, dV, m, dt, gamma, T, normal):
     return th - 2.0 * math.floor(th / 2.0), m * vt
 
 
+# ----------------------------------- regulated Nose-Hoover-Langevin (RNHL)
+# Section 2.6 couples the extended variables to the regulated Nose-Hoover-
+# Langevin thermostat of Abreu and Tuckerman (time constant 40 fs, friction
+# 25 ps^-1, regulation parameter 1) without restating it.  Written here from
+# that method's definition, for one variable of mass m at temperature T:
+#   kinetic function  K(p) = n kT ln cosh(p / sqrt(n m kT)),
+#   dx/dt   = K'(p) = sqrt(n kT / m) tanh(p / sqrt(n m kT))   (regulated velocity,
+#             bounded by sqrt(n kT / m); p / m as n -> infinity)
+#   dp/dt   = f - v_eta p                                       (Nose-Hoover friction)
+#   dv_eta  = (p K'(p) - kT) / Q dt - gamma v_eta dt + sqrt(2 gamma kT / Q) dW,
+#   Q = kT tau^2.
+# Its invariant density is exp(-(U(x) + K(p) + Q v_eta^2 / 2) / kT): the
+# position marginal is Boltzmann, <p K'(p)> = kT, <v_eta^2> = kT / Q.
+# Reading: the step keeps the leapfrog middle layout of the atoms (full
+# kick, half drift, thermostat, half drift) with the thermostat part split
+# symmetrically as NH(dt/2) OU(dt) NH(dt/2), where NH(h) is
+#   v_eta += h/2 G(p); p *= exp(-v_eta h); v_eta += h/2 G(p), with
+# G(p) = (p K'(p) - kT) / Q, and OU(dt) the exact Ornstein-Uhlenbeck step of
+# v_eta with the variable's standard normal.
+
+def regulated_velocity(p, m, kT, n):
+    """K'(p) = sqrt(n kT / m) tanh(p / sqrt(n m kT))."""
+    return np.sqrt(n * kT / m) * np.tanh(p / np.sqrt(n * m * kT))
+
+
+def nhl_thermostat(p, v_eta, m, kT, Q, gamma, n, dt, normal):
+    """The thermostat part of one RNHL step: NH(dt/2), OU(dt), NH(dt/2)."""
+    def nh(p, v_eta, h):
+        v_eta = v_eta + 0.5 * h * (p * regulated_velocity(p, m, kT, n) - kT) / Q
+        p = p * np.exp(-v_eta * h)
+        v_eta = v_eta + 0.5 * h * (p * regulated_velocity(p, m, kT, n) - kT) / Q
+        return p, v_eta
+    p, v_eta = nh(p, v_eta, 0.5 * dt)
+    a = math.exp(-gamma * dt)
+    v_eta = a * v_eta + np.sqrt(kT * (1.0 - a * a) / Q) * normal
+    p, v_eta = nh(p, v_eta, 0.5 * dt)
+    return p, v_eta
+
+
+def rnhl_step(x, p, v_eta, f, m, dt, gamma, T, tau, n, normal):
+    """One RNHL step of a variable at x with momentum p under force f:
+    p += dt f; x += dt/2 K'(p); thermostat; x += dt/2 K'(p).  Works on
+    scalars and on numpy arrays of independent variables."""
+    kT = KB * T
+    Q = kT * tau * tau
+    p = p + dt * f
+    x = x + 0.5 * dt * regulated_velocity(p, m, kT, n)
+    p, v_eta = nhl_thermostat(p, v_eta, m, kT, Q, gamma, n, dt, normal)
+    x = x + 0.5 * dt * regulated_velocity(p, m, kT, n)
+    return x, p, v_eta
+
+
+def theta_step_rnhl(theta, p_theta, v_eta, dUdl, dlam_dtheta, dV, m, dt, gamma, T, tau, n, normal):
+    """theta_step under RNHL: the same generalized force, theta wrapped
+    into [0, 2).  Returns (theta, p_theta, v_eta)."""
+    f = -dlam_dtheta * dUdl - dV
+    th, p, v_eta = rnhl_step(theta, p_theta, v_eta, f, m, dt, gamma, T, tau, n, normal)
+    return th - 2.0 * math.floor(th / 2.0), p, v_eta
+
+
+def dafed_step_rnhl(s, p, v_eta, Fs, m, dt, gamma, T, tau, n, normal):
+    """dafed_step under RNHL at the auxiliary temperature T; s wrapped into
+    [-pi, pi).  Returns (s, p, v_eta)."""
+    x, p, v_eta = rnhl_step(s, p, v_eta, Fs, m, dt, gamma, T, tau, n, normal)
+    return wrap_angle(x), p, v_eta
+
+
 # ------------------------------------------------ thermodynamic integration
 # Eq. 2: Delta G = integral over lambda in [0, 1] of <dU/dlambda>_lambda.  The
 # conditional mean is accumulated in TI_BINS equal bins of lambda (bin b holds
