@@ -279,7 +279,8 @@ int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* 
  * coupling forces join the atomic forces and the coupling energy joins U.
  * n_cv = 0 removes the coupling.  Indices out of range, a repeated atom in a
  * torsion, kappa < 0, mass <= 0 or non-finite input: LFE_ERR_ARG.  The
- * auxiliary angles and momenta are part of checkpoints (a checkpoint restores
+ * auxiliary angles, momenta and thermostat velocities are part of
+ * checkpoints (a checkpoint restores
  * only into a system with the same number of coupled torsions).
  * Paper values: 1000 K, 50 amu nm^2 rad^-2, kappa 1000 kJ mol^-1 rad^-2. */
 int lfe_set_dafed(lfe_system* sys, int n_cv, const int* atoms, const double* kappa, const double* mass,
@@ -289,6 +290,35 @@ int lfe_set_dafed(lfe_system* sys, int n_cv, const int* atoms, const double* kap
  * [n_cv] at the current positions (host arrays, any may be NULL).
  * Synchronises. */
 int lfe_dafed_state(lfe_system* sys, double* s, double* p_s, double* xi);
+
+/* Thermostat of the extended variables: theta (when lambda_mass > 0) and
+ * the d-AFED auxiliary angles (Section 2.6 couples them to a regulated
+ * Nose-Hoover-Langevin thermostat with time constant 40 fs, friction
+ * 25 ps^-1 and regulation parameter 1, citing Abreu and Tuckerman; the
+ * paper gives no equations, and these are that method's).
+ * kind LFE_EXT_LANGEVIN (the default): each variable takes the atoms' middle
+ * scheme, Langevin with its own friction (lambda_friction for theta, the
+ * d-AFED friction for the auxiliary angles).  kind LFE_EXT_RNHL: each variable
+ * x of mass m, momentum p and temperature T (kT = k_B T) moves with the
+ * regulated velocity dx/dt = sqrt(n kT / m) tanh(p / sqrt(n m kT)), n =
+ * n_reg, has dp/dt = f - v_eta p, and its thermostat velocity follows
+ * dv_eta = (p dx/dt - kT) / Q dt - gamma v_eta dt + sqrt(2 gamma kT / Q) dW
+ * with Q = kT tau^2 (tau in ps) and gamma the same friction as above; the
+ * position marginal stays Boltzmann.  One step: p += dt f; x += dt/2 dx/dt;
+ * NH(dt/2), the exact Ornstein-Uhlenbeck step of v_eta over dt (the
+ * variable's standard normal), NH(dt/2), where NH(h) is v_eta += h/2 G,
+ * p *= exp(-v_eta h), v_eta += h/2 G with G = (p dx/dt - kT) / Q; x += dt/2
+ * dx/dt.  Every thermostat velocity is set to 0; the velocities are part of
+ * checkpoints.  Synchronises.  Errors: LFE_ERR_ARG (unknown kind; for RNHL,
+ * tau or n_reg not finite and > 0). */
+#define LFE_EXT_LANGEVIN 0
+#define LFE_EXT_RNHL 1
+int lfe_set_ext_thermostat(lfe_system* sys, int kind, double tau, double n_reg);
+
+/* Thermostat velocities v_eta of theta (one value) and of the d-AFED
+ * auxiliary angles (n_cv values), host arrays, either may be NULL; zero
+ * under the Langevin thermostat.  Synchronises. */
+int lfe_ext_thermostat_state(lfe_system* sys, double* v_eta_theta, double* v_eta_aux);
 
 /* Eq. 16 at the current positions: mass_out[k] = c [sum_i |d xi_k / d r_i|^2
  * / m_i]^-1 over the four atoms of torsion k (atoms of mass 0 are fixed and

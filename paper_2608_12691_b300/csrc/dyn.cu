@@ -404,8 +404,48 @@ __global__ void k_dafed_force(SysView<real> s, DafedView d)
     if ((threadIdx.x & 31) == 0 && v) atomic_add_ll(&s.E[E_DAFED], v);
 }
 
-// the auxiliary variables' middle-scheme step at their own temperature
-// (normal from Philox at counter (k, step_lo, step_hi, 2))
+// One step of an extended variable (x, p) of mass m under force f at
+// temperature kT, with the variable's standard normal n0: the leapfrog
+// middle layout (full kick, half drift, thermostat, half drift).  Langevin
+// (kind 0): the thermostat is the exact Ornstein-Uhlenbeck step of the
+// velocity, a = exp(-gamma dt).  Regulated Nose-Hoover-Langevin (kind 1,
+// Section 2.6's thermostat of the extended variables): the drift is the
+// regulated velocity K'(p) = sqrt(n kT / m) tanh(p / sqrt(n m kT)) of the
+// kinetic function K(p) = n kT ln cosh(p / sqrt(n m kT)), and the
+// thermostat is NH(dt/2) OU(dt) NH(dt/2) on (p, v_eta): NH(h) is v_eta +=
+// h/2 G; p *= exp(-v_eta h); v_eta += h/2 G with G = (p K'(p) - kT) / Q,
+// Q = kT tau^2, and OU the exact Ornstein-Uhlenbeck step of v_eta.  Its
+// invariant density is exp(-(U + K(p) + Q v_eta^2 / 2) / kT).
+__device__ __forceinline__ void ext_step(const ExtThermo& th, double m, double kT, double dt, double a_fric,
+                                         double f, double n0, double& x, double& p, double& v_eta)
+{
+    if (th.kind == 1) {
+        const double Q = kT * th.tau * th.tau;
+        const double c = sqrt(th.n_reg * kT / m), pc = sqrt(th.n_reg * m * kT);
+        p += dt * f;
+        x += 0.5 * dt * c * tanh(p / pc);
+        double ve = v_eta;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const double h = 0.5 * dt;
+            ve += 0.5 * h * (p * c * tanh(p / pc) - kT) / Q;
+            p *= exp(-ve * h);
+            ve += 0.5 * h * (p * c * tanh(p / pc) - kT) / Q;
+            if (half == 0) ve = a_fric * ve + sqrt(kT * (1.0 - a_fric * a_fric) / Q) * n0;
+        }
+        x += 0.5 * dt * c * tanh(p / pc);
+        v_eta = ve;
+    } else {
+        double v = p / m + dt * f / m;
+        x += 0.5 * dt * v;
+        v = a_fric * v + sqrt(kT * (1.0 - a_fric * a_fric) / m) * n0;
+        x += 0.5 * dt * v;
+        p = m * v;
+    }
+}
+
+// the auxiliary variables' step at their own temperature (normal from
+// Philox at counter (k, step_lo, step_hi, 2))
 template <typename real>
 __global__ void k_dafed_step(SysView<real> s, DafedView d)
 {
@@ -415,13 +455,11 @@ __global__ void k_dafed_step(SysView<real> s, DafedView d)
     const unsigned long long step = s.lam->step - 1ull;   // k_theta has advanced the counter
     double n0, n1, n2;
     normals3<double>(make_uint4((unsigned)k, (unsigned)step, (unsigned)(step >> 32), 2u), d.key, n0, n1, n2);
-    const double m = d.mass[k];
-    double v = d.p[k] / m + d.dt * d.fs[k] / m;
-    double x = d.s[k] + 0.5 * d.dt * v;
-    v = d.a_fric * v + sqrt(d.kT * (1.0 - d.a_fric * d.a_fric) / m) * n0;
-    x += 0.5 * d.dt * v;
+    double x = d.s[k], p = d.p[k], ve = d.veta ? d.veta[k] : 0.0;
+    ext_step(d.th, d.mass[k], d.kT, d.dt, d.a_fric, d.fs[k], n0, x, p, ve);
     d.s[k] = wrap_pi(x);
-    d.p[k] = m * v;
+    d.p[k] = p;
+    if (d.veta) d.veta[k] = ve;
 }
 
 template <typename real>
@@ -854,16 +892,11 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const double th = L->theta;
     const double V0 = t.pre->V[0], dV0 = t.pre->dV[0], V1 = t.pre->V[1], dV1 = t.pre->dV[1];
     const unsigned long long step = L->step;
-    double thn = th, pn = L->p_theta;
+    double thn = th, pn = L->p_theta, ven = L->v_eta;
     if (t.m > 0.0) {
         const double f = -L->dlam_dtheta * dUdl - dV0 - dV1;
-        double v = pn / t.m + t.dt * f / t.m;
-        thn = th + 0.5 * t.dt * v;
-        const double n0 = t.pre->noise;
-        v = t.a_fric * v + sqrt(t.kT * (1.0 - t.a_fric * t.a_fric) / t.m) * n0;
-        thn += 0.5 * t.dt * v;
+        ext_step(t.th, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
         thn -= 2.0 * floor(thn / 2.0);
-        pn = t.m * v;
     }
     const unsigned long long stepn = step + 1;
     if (t.stride > 0 && (stepn % (unsigned long long)t.stride) == 0ull) {
@@ -887,7 +920,7 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         const double lam = thn <= 1.0 ? thn : 2.0 - thn;
         double hA, hB, dA, dB;
         switching_fns(lam, hA, hB, dA, dB);
-        L->theta = thn; L->p_theta = pn; L->lambda = lam;
+        L->theta = thn; L->p_theta = pn; L->v_eta = ven; L->lambda = lam;
         L->dlam_dtheta = thn <= 1.0 ? 1.0 : -1.0;
         L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
         L->dUdl = dUdl; L->U = U; L->V_std = V0; L->V_exp = V1;

@@ -4,6 +4,7 @@
 // checkpoints and the C-ABI entry points declared in include/lfe.h.
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -114,6 +115,8 @@ struct SystemBase {
     virtual void set_dafed(int n, const int* atoms, const double* kappa, const double* mass, double temperature,
                            double friction, const double* s0) = 0;
     virtual void dafed_state(double* s, double* p, double* xi) = 0;
+    virtual void set_ext_thermostat(int kind, double tau, double n_reg) = 0;
+    virtual void ext_thermostat_state(double* v_theta, double* v_aux) = 0;
     virtual void dafed_masses(int n, const int* atoms, double c, double* out) = 0;
     virtual void set_solute_params(const double* q, const double* sig, const double* eps, int on_device,
                                    cudaStream_t st) = 0;
@@ -667,6 +670,7 @@ struct System final : SystemBase {
         T.dt = p.dt;
         T.a_fric = std::exp(-p.lambda_friction * p.dt);
         T.kT = KB * (p.lambda_temperature > 0 ? p.lambda_temperature : p.temperature);
+        T.th = ext_th;
         T.stride = p.opes_stride;
         T.max_k = p.opes_max_kernels > 0 ? p.opes_max_kernels : 1024;
         T.sigma = p.opes_sigma > 0 ? p.opes_sigma : 0.1;
@@ -1957,7 +1961,7 @@ struct System final : SystemBase {
         CK(cudaDeviceSynchronize());
         if (exec) recover_overflow(nullptr);
         for (void* ptr : {(void*)D.atoms, (void*)D.kappa, (void*)D.mass, (void*)D.s, (void*)D.p, (void*)D.fs,
-                          (void*)D.xi, (void*)d_probe})
+                          (void*)D.xi, (void*)D.veta, (void*)d_probe})
             if (ptr) dfree(ptr);
         D = DafedView{};
         d_probe = nullptr;
@@ -1970,6 +1974,8 @@ struct System final : SystemBase {
             D.p = dalloc<double>(n_cv);
             D.fs = dalloc<double>(n_cv);
             D.xi = dalloc<double>(n_cv);
+            D.veta = dalloc<double>(n_cv);
+            D.th = ext_th;
             d_probe = dalloc<double>(n_cv);
             D.dt = P.dt;
             dafed_friction = friction;
@@ -1988,6 +1994,40 @@ struct System final : SystemBase {
         }
         invalidate_graph();
         ++generation;
+    }
+
+    // Thermostat of theta and the auxiliary angles (Section 2.6): kind 0
+    // Langevin, kind 1 regulated Nose-Hoover-Langevin (see ext_step); every
+    // thermostat velocity starts from zero
+    ExtThermo ext_th{0, 0, 0.04, 1.0};
+
+    void set_ext_thermostat(int kind, double tau, double n_reg) override
+    {
+        if (kind != 0 && kind != 1) fail(LFE_ERR_ARG, "thermostat kind must be 0 (Langevin) or 1 (RNHL)");
+        if (kind == 1 && (!(tau > 0) || !std::isfinite(tau) || !(n_reg > 0) || !std::isfinite(n_reg)))
+            fail(LFE_ERR_ARG, "RNHL needs tau > 0 and a regulation parameter > 0");
+        CK(cudaDeviceSynchronize());
+        if (exec) recover_overflow(nullptr);
+        ext_th = ExtThermo{kind, 0, kind == 1 ? tau : 0.04, kind == 1 ? n_reg : 1.0};
+        T.th = ext_th;
+        D.th = ext_th;
+        const double zero = 0.0;
+        CK(cudaMemcpy(reinterpret_cast<char*>(S.lam) + offsetof(LamState, v_eta), &zero, sizeof(double),
+                      cudaMemcpyHostToDevice));
+        if (D.n) CK(cudaMemset(D.veta, 0, sizeof(double) * D.n));
+        invalidate_graph();
+        ++generation;
+    }
+
+    void ext_thermostat_state(double* v_theta, double* v_aux) override
+    {
+        CK(cudaDeviceSynchronize());
+        if (v_theta) {
+            LamState L;
+            CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));
+            *v_theta = L.v_eta;
+        }
+        if (v_aux && D.n) CK(cudaMemcpy(v_aux, D.veta, sizeof(double) * D.n, cudaMemcpyDeviceToHost));
     }
 
     void dafed_state(double* s_out, double* p_out, double* xi_out) override
@@ -2023,7 +2063,7 @@ struct System final : SystemBase {
     }
 
     // checkpoint layout: header | x | v | xref | LamState | OpesState | centre | weight | S | TI sums |
-    // TI counts | d-AFED s | d-AFED p | checksum
+    // TI counts | d-AFED s | d-AFED p | d-AFED thermostat velocities | checksum
     struct CkHeader {
         char magic[8];
         int version, precision, n, max_k, n_cv, pad;
@@ -2036,7 +2076,7 @@ struct System final : SystemBase {
         check_flags(nullptr);
         CkHeader h{};
         std::memcpy(h.magic, "LFECKPT1", 8);
-        h.version = 3;
+        h.version = 4;
         h.precision = precision;
         for (int d = 0; d < 3; ++d) h.box[d] = P.box[d];
         h.n = n;
@@ -2066,6 +2106,7 @@ struct System final : SystemBase {
         if (D.n) {
             put_dev(D.s, sizeof(double) * D.n);
             put_dev(D.p, sizeof(double) * D.n);
+            put_dev(D.veta, sizeof(double) * D.n);
         }
         uint64_t cs_ = fnv1a(buf.data(), buf.size());
         put(&cs_, sizeof(cs_));
@@ -2087,14 +2128,14 @@ struct System final : SystemBase {
         std::fclose(f);
         const size_t body = sizeof(CkHeader) + 3 * sizeof(R4<real>) * n + sizeof(LamState) + sizeof(OpesState) +
                             3 * sizeof(double) * 2 * T.max_k + (sizeof(double) + sizeof(unsigned long long)) * LFE_TI_BINS +
-                            2 * sizeof(double) * D.n;
+                            3 * sizeof(double) * D.n;
         if (buf.size() != body + sizeof(uint64_t)) fail(LFE_ERR_ARG, "checkpoint size does not match this system");
         uint64_t stored;
         std::memcpy(&stored, buf.data() + body, sizeof(stored));
         if (stored != fnv1a(buf.data(), body)) fail(LFE_ERR_ARG, "checkpoint checksum mismatch");
         CkHeader h;
         std::memcpy(&h, buf.data(), sizeof(h));
-        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 3 || h.precision != precision || h.n != n ||
+        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 4 || h.precision != precision || h.n != n ||
             h.max_k != T.max_k || h.n_cv != D.n)
             fail(LFE_ERR_ARG, "checkpoint header does not match this system");
         if (h.box[0] != P.box[0] || h.box[1] != P.box[1] || h.box[2] != P.box[2]) set_box(h.box);
@@ -2122,6 +2163,7 @@ struct System final : SystemBase {
         if (D.n) {
             get_dev(D.s, sizeof(double) * D.n);
             get_dev(D.p, sizeof(double) * D.n);
+            get_dev(D.veta, sizeof(double) * D.n);
         }
         int zero[FL_N] = {0, 0, 0, 0};
         CK(cudaMemcpy(S.flags, zero, sizeof(int) * 2, cudaMemcpyHostToDevice));
@@ -2666,6 +2708,16 @@ int lfe_set_dafed(lfe_system* sys, int n_cv, const int* atoms, const double* kap
 int lfe_dafed_state(lfe_system* sys, double* s, double* p_s, double* xi)
 {
     return guard(sys, [&] { sys->impl->dafed_state(s, p_s, xi); });
+}
+
+int lfe_set_ext_thermostat(lfe_system* sys, int kind, double tau, double n_reg)
+{
+    return guard(sys, [&] { sys->impl->set_ext_thermostat(kind, tau, n_reg); });
+}
+
+int lfe_ext_thermostat_state(lfe_system* sys, double* v_eta_theta, double* v_eta_aux)
+{
+    return guard(sys, [&] { sys->impl->ext_thermostat_state(v_eta_theta, v_eta_aux); });
 }
 
 int lfe_dafed_masses(lfe_system* sys, int n_cv, const int* atoms, double c, double* mass_out)

@@ -69,7 +69,8 @@ struct LamState {
     double dUdl, U;                 // last evaluated values
     double V_std, V_exp;            // last OPES bias values
     unsigned long long step;
-    double pad[3];
+    double v_eta;                   // theta's thermostat velocity (regulated Nose-Hoover-Langevin)
+    double pad[2];
 };
 
 // OPES state for the two biases (std = 0, exp = 1).

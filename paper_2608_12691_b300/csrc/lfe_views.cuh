@@ -164,6 +164,16 @@ struct StepView {
     real* noise;               // [3 n] Ornstein-Uhlenbeck kicks of the step, formed ahead by k_noise
 };
 
+// Thermostat of the extended variables (theta and the d-AFED auxiliary
+// angles, Section 2.6): kind 0 Langevin on the variable (friction gamma),
+// kind 1 regulated Nose-Hoover-Langevin with time constant tau (Q = kT
+// tau^2), regulation parameter n_reg and friction gamma on its velocity
+struct ExtThermo {
+    int kind;
+    int pad;
+    double tau, n_reg;
+};
+
 // d-AFED (Eq. 15): torsions coupled harmonically to auxiliary angles that
 // have their own mass and temperature
 struct DafedView {
@@ -177,6 +187,8 @@ struct DafedView {
     double* xi;               // [n] torsion values of the last evaluation
     double dt, a_fric, kT;    // time step, exp(-gamma dt), k_B T of the auxiliary variables
     uint2 key;
+    ExtThermo th;             // thermostat of the auxiliary variables
+    double* veta;             // [n] their thermostat velocities (regulated Nose-Hoover-Langevin)
 };
 
 // values of the theta step that depend only on the state at its start,
@@ -204,6 +216,7 @@ struct ThetaView {
     ThetaPre* pre;
     double* ti_sum;                 // [LFE_TI_BINS] sum of dU/dlambda per lambda bin (Eq. 2)
     unsigned long long* ti_cnt;     // [LFE_TI_BINS] samples per bin
+    ExtThermo th;                   // theta's thermostat
 };
 
 // FP64 geometry and Ewald constants of the parameter-gradient kernel

@@ -21,6 +21,8 @@ LFE_ERR_TIMEOUT = -5
 LFE_ERR_STATE = -6
 LFE_FP32_MIXED = 0
 LFE_FP64 = 1
+LFE_EXT_LANGEVIN = 0
+LFE_EXT_RNHL = 1
 NTERMS = 10
 NEXT = 10
 TI_BINS = 100
@@ -30,6 +32,7 @@ EXPORTED = [
     "lfe_create", "lfe_set_positions", "lfe_set_velocities", "lfe_set_integrator",
     "lfe_build_neighbors", "lfe_eval",
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
+    "lfe_set_ext_thermostat", "lfe_ext_thermostat_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
     "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step", "lfe_batch_time_pairs", "lfe_batch_set_exchange",
     "lfe_batch_exchange_state",
@@ -129,6 +132,8 @@ def load():
     lib.lfe_set_dafed.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp]
     lib.lfe_dafed_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_dafed_masses.argtypes = [vp, ctypes.c_int, vp, ctypes.c_double, vp]
+    lib.lfe_set_ext_thermostat.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.lfe_ext_thermostat_state.argtypes = [vp, vp, vp]
     lib.lfe_get_state.argtypes = [vp, vp, vp, vp]
     lib.lfe_checkpoint.argtypes = [vp, ctypes.c_char_p]
     lib.lfe_restore.argtypes = [vp, ctypes.c_char_p]
@@ -425,6 +430,18 @@ class System:
         self._check(self._lib.lfe_set_dafed(self.h, k, atoms.ctypes.data, kappa.ctypes.data, mass.ctypes.data,
                                             float(temperature), float(friction),
                                             None if s0a is None else s0a.ctypes.data))
+
+    def set_ext_thermostat(self, kind, tau=0.04, n_reg=1.0):
+        """Thermostat of theta and the d-AFED auxiliary angles
+        (lfe_set_ext_thermostat): LFE_EXT_LANGEVIN or LFE_EXT_RNHL."""
+        self._check(self._lib.lfe_set_ext_thermostat(self.h, int(kind), float(tau), float(n_reg)))
+
+    def ext_thermostat_state(self):
+        """(v_eta of theta, v_eta of the auxiliary angles [n_cv])."""
+        vt = ctypes.c_double()
+        va = np.zeros(max(getattr(self, "_dafed_n", 0), 1))
+        self._check(self._lib.lfe_ext_thermostat_state(self.h, ctypes.byref(vt), va.ctypes.data))
+        return vt.value, va[:getattr(self, "_dafed_n", 0)]
 
     def dafed_state(self):
         """(s, p_s, xi at the current positions), each [n_cv]."""
