@@ -77,9 +77,21 @@ def parse():
     return a
 
 
+# Section 2.6: the extended variables (theta, the d-AFED auxiliary angles)
+# are thermostatted by the regulated Nose-Hoover-Langevin thermostat with a
+# 40 fs time constant, 25 ps^-1 friction and regulation parameter 1
+EXT_THERMOSTAT = dict(tau=0.040, n_reg=1.0)
+
+
+def use_paper_thermostat(g):
+    from paper_2608_12691_b300 import lfe
+    g.set_ext_thermostat(lfe.LFE_EXT_RNHL, **EXT_THERMOSTAT)
+
+
 def run_config(d, desc):
     """The workload description shared by both arms of the bench."""
     return {"workload": desc, "atoms": len(d["charge"]), "dt_fs": float(d["dt"]) * 1e3,
+            "extended_thermostat": "regulated Nose-Hoover-Langevin, tau 40 fs, 25 ps^-1, regulation 1",
             "l2": "flushed between steps (256 MiB write)", "data": "seeded synthetic stand-in"}
 
 
@@ -295,6 +307,7 @@ def dafed_leg(args, stream, flush):
              opes_dE_std=30.0 * 4.184, opes_dE_exp=5.0 * 4.184, opes_sigma=0.10)
     g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242)
     g.set_dafed(S.DIPEPTIDE_CVS, 1000.0, 50.0, temperature=1000.0, friction=25.0)
+    use_paper_thermostat(g)
     equilibrate(g, d, stream)
     if not args.no_autotune:
         g.autotune(reps=20)
@@ -329,6 +342,8 @@ def batched_leg(args, stream, flush):
         dicts.append(d)
     t_gen = time.perf_counter() - t0
     reps = [lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=7000 + r, theta0=d["lam"]) for r, d in enumerate(dicts)]
+    for g in reps:
+        use_paper_thermostat(g)
     b = lfe.Batch(reps)
     for frac, fric in ((0.05, 100.0), (0.25, 50.0), (0.5, 20.0), (1.0, None)):
         for d, g in zip(dicts, reps):
@@ -371,6 +386,7 @@ def batched_leg(args, stream, flush):
     for d, g in zip(dicts, reps):
         p, v, _ = g.get_state()
         g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=1, theta0=d["lam"])
+        use_paper_thermostat(g64)
         g64.set_positions(p)
         g64.set_velocities(v)
         g64.step(2, stream)
@@ -455,6 +471,7 @@ def run_ours(args):
     dt_ps = float(d["dt"])
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     g = lfe.System(d, precision=prec, seed=2608 + rank)
+    use_paper_thermostat(g)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
     stream = torch.cuda.current_stream()
@@ -536,6 +553,7 @@ def run_ours(args):
         fp64 = None
         if not args.no_fp64 and prec == lfe.LFE_FP32_MIXED:
             g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=2608)
+            use_paper_thermostat(g64)
             g64.set_positions(pos)
             g64.set_velocities(vel)
             g64.step(5, stream)
