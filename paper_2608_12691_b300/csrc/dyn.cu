@@ -420,20 +420,25 @@ __device__ __forceinline__ void ext_step(const ExtThermo& th, double m, double k
                                          double f, double n0, double& x, double& p, double& v_eta)
 {
     if (th.kind == 1) {
-        const double Q = kT * th.tau * th.tau;
-        const double c = sqrt(th.n_reg * kT / m), pc = sqrt(th.n_reg * m * kT);
+        // K'(p) is taken three times (after the kick, after each friction
+        // scaling of p): G and the drifts reuse it while p is unchanged
+        const double iQ = 1.0 / (kT * th.tau * th.tau);
+        const double ipc = rsqrt(th.n_reg * m * kT), c = th.n_reg * kT * ipc;
+        const double q = 0.25 * dt;
         p += dt * f;
-        x += 0.5 * dt * c * tanh(p / pc);
+        double u = c * tanh(p * ipc);
+        x += 0.5 * dt * u;
         double ve = v_eta;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const double h = 0.5 * dt;
-            ve += 0.5 * h * (p * c * tanh(p / pc) - kT) / Q;
-            p *= exp(-ve * h);
-            ve += 0.5 * h * (p * c * tanh(p / pc) - kT) / Q;
-            if (half == 0) ve = a_fric * ve + sqrt(kT * (1.0 - a_fric * a_fric) / Q) * n0;
-        }
-        x += 0.5 * dt * c * tanh(p / pc);
+        ve += q * (p * u - kT) * iQ;
+        p *= exp(-ve * 0.5 * dt);
+        u = c * tanh(p * ipc);
+        ve += q * (p * u - kT) * iQ;
+        ve = a_fric * ve + sqrt(kT * (1.0 - a_fric * a_fric) * iQ) * n0;
+        ve += q * (p * u - kT) * iQ;
+        p *= exp(-ve * 0.5 * dt);
+        u = c * tanh(p * ipc);
+        ve += q * (p * u - kT) * iQ;
+        x += 0.5 * dt * u;
         v_eta = ve;
     } else {
         double v = p / m + dt * f / m;
@@ -895,8 +900,15 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     double thn = th, pn = L->p_theta, ven = L->v_eta;
     if (t.m > 0.0) {
         const double f = -L->dlam_dtheta * dUdl - dV0 - dV1;
-        ext_step(t.th, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
-        thn -= 2.0 * floor(thn / 2.0);
+        // one lane takes the step (its FP64 transcendentals run on a pipe
+        // with a small fraction of the FP32 rate); the others receive the result
+        if (lane == 0) {
+            ext_step(t.th, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
+            thn -= 2.0 * floor(thn / 2.0);
+        }
+        thn = __shfl_sync(0xffffffffu, thn, 0);
+        pn = __shfl_sync(0xffffffffu, pn, 0);
+        ven = __shfl_sync(0xffffffffu, ven, 0);
     }
     const unsigned long long stepn = step + 1;
     if (t.stride > 0 && (stepn % (unsigned long long)t.stride) == 0ull) {
