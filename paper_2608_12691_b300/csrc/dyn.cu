@@ -416,34 +416,32 @@ __global__ void k_dafed_force(SysView<real> s, DafedView d)
 // h/2 G; p *= exp(-v_eta h); v_eta += h/2 G with G = (p K'(p) - kT) / Q,
 // Q = kT tau^2, and OU the exact Ornstein-Uhlenbeck step of v_eta.  Its
 // invariant density is exp(-(U + K(p) + Q v_eta^2 / 2) / kT).
-__device__ __forceinline__ void ext_step(const ExtThermo& th, double m, double kT, double dt, double a_fric,
-                                         double f, double n0, double& x, double& p, double& v_eta)
+__device__ __forceinline__ void ext_step(const ExtThermo& th, const ExtConst& k, double m, double kT, double dt,
+                                         double a_fric, double f, double n0, double& x, double& p, double& v_eta)
 {
     if (th.kind == 1) {
         // K'(p) is taken three times (after the kick, after each friction
         // scaling of p): G and the drifts reuse it while p is unchanged
-        const double iQ = 1.0 / (kT * th.tau * th.tau);
-        const double ipc = rsqrt(th.n_reg * m * kT), c = th.n_reg * kT * ipc;
         const double q = 0.25 * dt;
         p += dt * f;
-        double u = c * tanh(p * ipc);
+        double u = k.c * tanh(p * k.ipc);
         x += 0.5 * dt * u;
         double ve = v_eta;
-        ve += q * (p * u - kT) * iQ;
+        ve += q * (p * u - kT) * k.iQ;
         p *= exp(-ve * 0.5 * dt);
-        u = c * tanh(p * ipc);
-        ve += q * (p * u - kT) * iQ;
-        ve = a_fric * ve + sqrt(kT * (1.0 - a_fric * a_fric) * iQ) * n0;
-        ve += q * (p * u - kT) * iQ;
+        u = k.c * tanh(p * k.ipc);
+        ve += q * (p * u - kT) * k.iQ;
+        ve = a_fric * ve + k.amp_eta * n0;
+        ve += q * (p * u - kT) * k.iQ;
         p *= exp(-ve * 0.5 * dt);
-        u = c * tanh(p * ipc);
-        ve += q * (p * u - kT) * iQ;
+        u = k.c * tanh(p * k.ipc);
+        ve += q * (p * u - kT) * k.iQ;
         x += 0.5 * dt * u;
         v_eta = ve;
     } else {
         double v = p / m + dt * f / m;
         x += 0.5 * dt * v;
-        v = a_fric * v + sqrt(kT * (1.0 - a_fric * a_fric) / m) * n0;
+        v = a_fric * v + k.amp * n0;
         x += 0.5 * dt * v;
         p = m * v;
     }
@@ -457,11 +455,12 @@ __global__ void k_dafed_step(SysView<real> s, DafedView d)
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
     if (s.flags[FL_ERROR] & ERRB_OVERFLOW) return;   // step skipped (see k_integrate)
-    const unsigned long long step = s.lam->step - 1ull;   // k_theta has advanced the counter
+    const unsigned long long step = d.pre->step;   // runs beside k_theta, which advances the counter
     double n0, n1, n2;
     normals3<double>(make_uint4((unsigned)k, (unsigned)step, (unsigned)(step >> 32), 2u), d.key, n0, n1, n2);
     double x = d.s[k], p = d.p[k], ve = d.veta ? d.veta[k] : 0.0;
-    ext_step(d.th, d.mass[k], d.kT, d.dt, d.a_fric, d.fs[k], n0, x, p, ve);
+    const double m = d.mass[k];
+    ext_step(d.th, ext_const(d.th, m, d.kT, d.a_fric), m, d.kT, d.dt, d.a_fric, d.fs[k], n0, x, p, ve);
     d.s[k] = wrap_pi(x);
     d.p[k] = p;
     if (d.veta) d.veta[k] = ve;
@@ -866,6 +865,7 @@ __global__ void k_theta_pre(SysView<real> s, ThetaView<real> t)
         t.pre->V[0] = V0; t.pre->V[1] = V1;
         t.pre->dV[0] = dV0; t.pre->dV[1] = dV1;
         t.pre->noise = n0;
+        t.pre->step = step;
     }
 }
 
@@ -886,44 +886,28 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         if (lane < E_N) E[lane] = 0;
         return;
     }
-    const double Uvv = efix(E, E_PAIR_VV) + efix(E, E_EXCL_VV) + efix(E, E_14_VV) + efix(E, E_REC_VV) + t.const_vv;
-    const double Uuu = efix(E, E_PAIR_UU) + efix(E, E_EXCL_UU) + efix(E, E_14_UU) + efix(E, E_REC_UU) + t.const_uu;
-    const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
-    const double Us = efix(E, E_PAIR_SOFT);
-    const double Ub = efix(E, E_BONDED);
-    const bool sc = s.sc_alpha > 0.0;   // soft-core coupling: U_soft is the term at lambda
-    const double dUdl = L->dhA * Uuv + (sc ? efix(E, E_DSC) : L->dhB * Us);
-    const double U = Uvv + Uuu + L->hA * Uuv + (sc ? Us : L->hB * Us) + Ub + efix(E, E_DAFED);
-    const double th = L->theta;
-    const double V0 = t.pre->V[0], dV0 = t.pre->dV[0], V1 = t.pre->V[1], dV1 = t.pre->dV[1];
-    const unsigned long long step = L->step;
-    double thn = th, pn = L->p_theta, ven = L->v_eta;
-    if (t.m > 0.0) {
-        const double f = -L->dlam_dtheta * dUdl - dV0 - dV1;
-        // one lane takes the step (its FP64 transcendentals run on a pipe
-        // with a small fraction of the FP32 rate); the others receive the result
-        if (lane == 0) {
-            ext_step(t.th, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
+    // the scalar work of the step is lane 0's (FP64 on a pipe with a small
+    // fraction of the FP32 rate, one dependent chain); the warp joins for an
+    // OPES deposit
+    double thn = 0.0;
+    unsigned long long stepn = 0;
+    if (lane == 0) {
+        const double Uvv = efix(E, E_PAIR_VV) + efix(E, E_EXCL_VV) + efix(E, E_14_VV) + efix(E, E_REC_VV) + t.const_vv;
+        const double Uuu = efix(E, E_PAIR_UU) + efix(E, E_EXCL_UU) + efix(E, E_14_UU) + efix(E, E_REC_UU) + t.const_uu;
+        const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
+        const double Us = efix(E, E_PAIR_SOFT);
+        const double Ub = efix(E, E_BONDED);
+        const bool sc = s.sc_alpha > 0.0;   // soft-core coupling: U_soft is the term at lambda
+        const double dUdl = L->dhA * Uuv + (sc ? efix(E, E_DSC) : L->dhB * Us);
+        const double U = Uvv + Uuu + L->hA * Uuv + (sc ? Us : L->hB * Us) + Ub + efix(E, E_DAFED);
+        double pn = L->p_theta, ven = L->v_eta;
+        thn = L->theta;
+        if (t.m > 0.0) {
+            const double f = -L->dlam_dtheta * dUdl - t.pre->dV[0] - t.pre->dV[1];
+            ext_step(t.th, t.tc, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
             thn -= 2.0 * floor(thn / 2.0);
         }
-        thn = __shfl_sync(0xffffffffu, thn, 0);
-        pn = __shfl_sync(0xffffffffu, pn, 0);
-        ven = __shfl_sync(0xffffffffu, ven, 0);
-    }
-    const unsigned long long stepn = step + 1;
-    if (t.stride > 0 && (stepn % (unsigned long long)t.stride) == 0ull) {
-        // a Standard kernel is reweighted by the total bias at its centre,
-        // exp(beta (V_std + V_exp)), so that its density estimate converges
-        // to the unbiased distribution while the trajectory runs under the
-        // sum of both biases (Eq. 14); both are taken before either deposit
-        double Vs, dVs, Ve, dVe;
-        opes_bias(t, 0, thn, Vs, dVs);
-        opes_bias(t, 1, thn, Ve, dVe);
-        if (t.on[0]) opes_deposit(t, 0, thn, exp(t.beta * (Vs + Ve)));
-        if (t.on[1]) opes_deposit(t, 1, thn, 1.0);
-    }
-    __syncwarp();
-    if (lane == 0) {
+        stepn = L->step + 1;
         // Eq. 2: the mean force is accumulated in lambda bins (at the lambda
         // of this step's evaluation)
         const int bin = min(LFE_TI_BINS - 1, max(0, (int)floor(L->lambda * LFE_TI_BINS)));
@@ -935,12 +919,24 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         L->theta = thn; L->p_theta = pn; L->v_eta = ven; L->lambda = lam;
         L->dlam_dtheta = thn <= 1.0 ? 1.0 : -1.0;
         L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
-        L->dUdl = dUdl; L->U = U; L->V_std = V0; L->V_exp = V1;
+        L->dUdl = dUdl; L->U = U; L->V_std = t.pre->V[0]; L->V_exp = t.pre->V[1];
         if (!isfinite(U) || !isfinite(thn)) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
         // the step ends here: its counter (the Philox counter of the atoms,
-        // theta and the auxiliary angles) advances; k_dafed_step, which
-        // follows in the same stream, uses the value before the advance
+        // theta and the auxiliary angles) advances
         L->step = stepn;
+    }
+    stepn = __shfl_sync(0xffffffffu, stepn, 0);
+    if (t.stride > 0 && (stepn % (unsigned long long)t.stride) == 0ull) {
+        // a Standard kernel is reweighted by the total bias at its centre,
+        // exp(beta (V_std + V_exp)), so that its density estimate converges
+        // to the unbiased distribution while the trajectory runs under the
+        // sum of both biases (Eq. 14); both are taken before either deposit
+        thn = __shfl_sync(0xffffffffu, thn, 0);
+        double Vs, dVs, Ve, dVe;
+        opes_bias(t, 0, thn, Vs, dVs);
+        opes_bias(t, 1, thn, Ve, dVe);
+        if (t.on[0]) opes_deposit(t, 0, thn, exp(t.beta * (Vs + Ve)));
+        if (t.on[1]) opes_deposit(t, 1, thn, 1.0);
     }
     // every energy accumulator has been read: clear them for the next step
     __syncwarp();

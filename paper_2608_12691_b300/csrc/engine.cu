@@ -671,6 +671,7 @@ struct System final : SystemBase {
         T.a_fric = std::exp(-p.lambda_friction * p.dt);
         T.kT = KB * (p.lambda_temperature > 0 ? p.lambda_temperature : p.temperature);
         T.th = ext_th;
+        T.tc = ext_const(T.th, T.m, T.kT, T.a_fric);
         T.stride = p.opes_stride;
         T.max_k = p.opes_max_kernels > 0 ? p.opes_max_kernels : 1024;
         T.sigma = p.opes_sigma > 0 ? p.opes_sigma : 0.1;
@@ -1019,6 +1020,7 @@ struct System final : SystemBase {
         T.kT = KB * (P.lambda_temperature > 0 ? P.lambda_temperature : temperature);
         D.dt = dt;
         D.a_fric = std::exp(-dafed_friction * dt);
+        T.tc = ext_const(T.th, T.m, T.kT, T.a_fric);
         invalidate_graph();
         ++generation;
     }
@@ -1647,6 +1649,24 @@ struct System final : SystemBase {
         recover_overflow(st);
     }
 
+    // the end of a captured step: atoms, theta and the auxiliary angles move
+    // concurrently (three branches); the step ends when all are done
+    void record_ext_steps(cudaStream_t s0)
+    {
+        CK(cudaEventRecord(ev_fork, s0));
+        CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
+        launch_theta(S, T, br[0]);
+        CK(cudaEventRecord(ev_join[0], br[0]));
+        if (D.n) {
+            CK(cudaStreamWaitEvent(br[1], ev_fork, 0));
+            launch_dafed_step(S, D, br[1]);
+            CK(cudaEventRecord(ev_join[1], br[1]));
+        }
+        launch_integrate(S, G, s0);
+        CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
+        if (D.n) CK(cudaStreamWaitEvent(s0, ev_join[1], 0));
+    }
+
     void capture_step_graph()
     {
         cudaStream_t s0 = cs;
@@ -1657,14 +1677,7 @@ struct System final : SystemBase {
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         eval_kernels_branched(s0, &T, &h);
-        // atoms and theta move concurrently; the step ends when both are done
-        CK(cudaEventRecord(ev_fork, s0));
-        CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
-        launch_theta(S, T, br[0]);
-        launch_dafed_step(S, D, br[0]);
-        CK(cudaEventRecord(ev_join[0], br[0]));
-        launch_integrate(S, G, s0);
-        CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
+        record_ext_steps(s0);
         CK(cudaStreamEndCapture(s0, &graph));
         CK(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
     }
@@ -1711,13 +1724,7 @@ struct System final : SystemBase {
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         eval_kernels_branched(s0, &T, &h);
-        CK(cudaEventRecord(ev_fork, s0));
-        CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
-        launch_theta(S, T, br[0]);
-        launch_dafed_step(S, D, br[0]);
-        CK(cudaEventRecord(ev_join[0], br[0]));
-        launch_integrate(S, G, s0);
-        CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
+        record_ext_steps(s0);
         launch_pack_state(S, T.st, d_state, s0);
         CK(cudaMemcpyAsync(h_io_tail, d_state + 2 * nv, sizeof(double) * 16, cudaMemcpyDeviceToHost, s0));
         if (pos_out) CK(cudaMemcpyAsync(pos_out, d_state, sizeof(double) * nv, cudaMemcpyDeviceToHost, s0));
@@ -1976,6 +1983,7 @@ struct System final : SystemBase {
             D.xi = dalloc<double>(n_cv);
             D.veta = dalloc<double>(n_cv);
             D.th = ext_th;
+            D.pre = T.pre;
             d_probe = dalloc<double>(n_cv);
             D.dt = P.dt;
             dafed_friction = friction;
@@ -2010,6 +2018,7 @@ struct System final : SystemBase {
         if (exec) recover_overflow(nullptr);
         ext_th = ExtThermo{kind, 0, kind == 1 ? tau : 0.04, kind == 1 ? n_reg : 1.0};
         T.th = ext_th;
+        T.tc = ext_const(T.th, T.m, T.kT, T.a_fric);
         D.th = ext_th;
         const double zero = 0.0;
         CK(cudaMemcpy(reinterpret_cast<char*>(S.lam) + offsetof(LamState, v_eta), &zero, sizeof(double),

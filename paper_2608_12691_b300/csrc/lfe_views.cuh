@@ -174,6 +174,29 @@ struct ExtThermo {
     double tau, n_reg;
 };
 
+// constants of one extended variable's step (mass m, k_B T, a = exp(-gamma
+// dt)): amp = sqrt(kT (1 - a^2) / m) (Langevin); iQ = 1 / (kT tau^2), ipc =
+// 1 / sqrt(n m kT), c = n kT ipc = sqrt(n kT / m), amp_eta = sqrt(kT (1 -
+// a^2) iQ) (regulated Nose-Hoover-Langevin)
+struct ExtConst {
+    double amp, iQ, ipc, c, amp_eta;
+};
+
+__host__ __device__ inline ExtConst ext_const(const ExtThermo& th, double m, double kT, double a_fric)
+{
+    ExtConst k{};
+    k.amp = m > 0.0 ? sqrt(kT * (1.0 - a_fric * a_fric) / m) : 0.0;
+    if (th.kind == 1 && m > 0.0 && kT > 0.0) {
+        k.iQ = 1.0 / (kT * th.tau * th.tau);
+        k.ipc = 1.0 / sqrt(th.n_reg * m * kT);
+        k.c = th.n_reg * kT * k.ipc;
+        k.amp_eta = sqrt(kT * (1.0 - a_fric * a_fric) * k.iQ);
+    }
+    return k;
+}
+
+struct ThetaPre;
+
 // d-AFED (Eq. 15): torsions coupled harmonically to auxiliary angles that
 // have their own mass and temperature
 struct DafedView {
@@ -189,6 +212,7 @@ struct DafedView {
     uint2 key;
     ExtThermo th;             // thermostat of the auxiliary variables
     double* veta;             // [n] their thermostat velocities (regulated Nose-Hoover-Langevin)
+    const ThetaPre* pre;      // the step's counter (formed at its start)
 };
 
 // values of the theta step that depend only on the state at its start,
@@ -196,7 +220,7 @@ struct DafedView {
 struct ThetaPre {
     double V[2], dV[2];        // both OPES biases and their theta-derivatives at theta
     double noise;              // the theta integrator's standard normal
-    double pad;
+    unsigned long long step;   // the step counter at the start of the step
 };
 
 template <typename real>
@@ -217,6 +241,7 @@ struct ThetaView {
     double* ti_sum;                 // [LFE_TI_BINS] sum of dU/dlambda per lambda bin (Eq. 2)
     unsigned long long* ti_cnt;     // [LFE_TI_BINS] samples per bin
     ExtThermo th;                   // theta's thermostat
+    ExtConst tc;                    // its constants at m, kT, a_fric
 };
 
 // FP64 geometry and Ewald constants of the parameter-gradient kernel
