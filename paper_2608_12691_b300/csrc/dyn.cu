@@ -439,7 +439,7 @@ __device__ __forceinline__ void ext_step(const ExtThermo& th, const ExtConst& k,
         x += 0.5 * dt * u;
         v_eta = ve;
     } else {
-        double v = p / m + dt * f / m;
+        double v = (p + dt * f) * k.im;
         x += 0.5 * dt * v;
         v = a_fric * v + k.amp * n0;
         x += 0.5 * dt * v;
@@ -459,8 +459,7 @@ __global__ void k_dafed_step(SysView<real> s, DafedView d)
     double n0, n1, n2;
     normals3<double>(make_uint4((unsigned)k, (unsigned)step, (unsigned)(step >> 32), 2u), d.key, n0, n1, n2);
     double x = d.s[k], p = d.p[k], ve = d.veta ? d.veta[k] : 0.0;
-    const double m = d.mass[k];
-    ext_step(d.th, ext_const(d.th, m, d.kT, d.a_fric), m, d.kT, d.dt, d.a_fric, d.fs[k], n0, x, p, ve);
+    ext_step(d.th, d.ec[k], d.mass[k], d.kT, d.dt, d.a_fric, d.fs[k], n0, x, p, ve);
     d.s[k] = wrap_pi(x);
     d.p[k] = p;
     if (d.veta) d.veta[k] = ve;

@@ -1021,6 +1021,7 @@ struct System final : SystemBase {
         D.dt = dt;
         D.a_fric = std::exp(-dafed_friction * dt);
         T.tc = ext_const(T.th, T.m, T.kT, T.a_fric);
+        dafed_consts();
         invalidate_graph();
         ++generation;
     }
@@ -1968,10 +1969,11 @@ struct System final : SystemBase {
         CK(cudaDeviceSynchronize());
         if (exec) recover_overflow(nullptr);
         for (void* ptr : {(void*)D.atoms, (void*)D.kappa, (void*)D.mass, (void*)D.s, (void*)D.p, (void*)D.fs,
-                          (void*)D.xi, (void*)D.veta, (void*)d_probe})
+                          (void*)D.xi, (void*)D.veta, (void*)d_dafed_ec, (void*)d_probe})
             if (ptr) dfree(ptr);
         D = DafedView{};
         d_probe = nullptr;
+        d_dafed_ec = nullptr;
         if (n_cv > 0) {
             D.n = n_cv;
             D.atoms = upload(at);
@@ -1984,12 +1986,15 @@ struct System final : SystemBase {
             D.veta = dalloc<double>(n_cv);
             D.th = ext_th;
             D.pre = T.pre;
+            d_dafed_ec = dalloc<ExtConst>(n_cv);
+            D.ec = d_dafed_ec;
             d_probe = dalloc<double>(n_cv);
             D.dt = P.dt;
             dafed_friction = friction;
             D.a_fric = std::exp(-friction * P.dt);
             D.kT = KB * temperature;
             D.key = G.key;
+            dafed_consts();
             if (s0) {
                 std::vector<double> w(n_cv);
                 for (int k = 0; k < n_cv; ++k) w[k] = s0[k] - 2.0 * PI * std::floor((s0[k] + PI) / (2.0 * PI));
@@ -2008,6 +2013,18 @@ struct System final : SystemBase {
     // Langevin, kind 1 regulated Nose-Hoover-Langevin (see ext_step); every
     // thermostat velocity starts from zero
     ExtThermo ext_th{0, 0, 0.04, 1.0};
+    ExtConst* d_dafed_ec = nullptr;   // D.ec
+
+    // the auxiliary variables' step constants at their masses, kT and friction
+    void dafed_consts()
+    {
+        if (!D.n) return;
+        std::vector<double> m(D.n);
+        CK(cudaMemcpy(m.data(), D.mass, sizeof(double) * D.n, cudaMemcpyDeviceToHost));
+        std::vector<ExtConst> k(D.n);
+        for (int i = 0; i < D.n; ++i) k[i] = ext_const(D.th, m[i], D.kT, D.a_fric);
+        CK(cudaMemcpy(d_dafed_ec, k.data(), sizeof(ExtConst) * D.n, cudaMemcpyHostToDevice));
+    }
 
     void set_ext_thermostat(int kind, double tau, double n_reg) override
     {
@@ -2024,6 +2041,7 @@ struct System final : SystemBase {
         CK(cudaMemcpy(reinterpret_cast<char*>(S.lam) + offsetof(LamState, v_eta), &zero, sizeof(double),
                       cudaMemcpyHostToDevice));
         if (D.n) CK(cudaMemset(D.veta, 0, sizeof(double) * D.n));
+        dafed_consts();
         invalidate_graph();
         ++generation;
     }

@@ -111,7 +111,8 @@ __device__ __forceinline__ double warp_sum_d(double v)
 // h_A, h_B and their lambda-derivatives (Eq. 7-10), FP64.
 __host__ __device__ __forceinline__ void switching_fns(double lam, double& hA, double& hB, double& dA, double& dB)
 {
-    double x = (lam - 0.35) / 0.65;
+    constexpr double INV_W = 1.0 / 0.65;   // S32 runs over lambda in [0.35, 1]: no division at run time
+    double x = (lam - 0.35) * INV_W;
     double s32 = 0.0, d32 = 0.0;
     if (x >= 1.0) { s32 = 1.0; }
     else if (x > 0.0) {
@@ -128,8 +129,8 @@ __host__ __device__ __forceinline__ void switching_fns(double lam, double& hA, d
     }
     hA = s32;
     hB = s22 - s32;
-    dA = d32 / 0.65;
-    dB = d22 - d32 / 0.65;
+    dA = d32 * INV_W;
+    dB = d22 - d32 * INV_W;
 }
 
 // ---------------------------------------------------------- Philox4x32-10

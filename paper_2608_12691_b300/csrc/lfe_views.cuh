@@ -175,16 +175,18 @@ struct ExtThermo {
 };
 
 // constants of one extended variable's step (mass m, k_B T, a = exp(-gamma
-// dt)): amp = sqrt(kT (1 - a^2) / m) (Langevin); iQ = 1 / (kT tau^2), ipc =
-// 1 / sqrt(n m kT), c = n kT ipc = sqrt(n kT / m), amp_eta = sqrt(kT (1 -
-// a^2) iQ) (regulated Nose-Hoover-Langevin)
+// dt)), formed once per setting so that the step itself divides by nothing:
+// im = 1 / m, amp = sqrt(kT (1 - a^2) / m) (Langevin); iQ = 1 / (kT tau^2),
+// ipc = 1 / sqrt(n m kT), c = n kT ipc = sqrt(n kT / m), amp_eta = sqrt(kT
+// (1 - a^2) iQ) (regulated Nose-Hoover-Langevin)
 struct ExtConst {
-    double amp, iQ, ipc, c, amp_eta;
+    double im, amp, iQ, ipc, c, amp_eta;
 };
 
 __host__ __device__ inline ExtConst ext_const(const ExtThermo& th, double m, double kT, double a_fric)
 {
     ExtConst k{};
+    k.im = m > 0.0 ? 1.0 / m : 0.0;
     k.amp = m > 0.0 ? sqrt(kT * (1.0 - a_fric * a_fric) / m) : 0.0;
     if (th.kind == 1 && m > 0.0 && kT > 0.0) {
         k.iQ = 1.0 / (kT * th.tau * th.tau);
@@ -213,6 +215,7 @@ struct DafedView {
     ExtThermo th;             // thermostat of the auxiliary variables
     double* veta;             // [n] their thermostat velocities (regulated Nose-Hoover-Langevin)
     const ThetaPre* pre;      // the step's counter (formed at its start)
+    const ExtConst* ec;       // [n] constants of each variable's step
 };
 
 // values of the theta step that depend only on the state at its start,
