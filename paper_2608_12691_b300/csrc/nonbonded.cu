@@ -1009,7 +1009,12 @@ __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, f
 // step (0.149 against 0.142 ms: the kernel shares the GPU with the PME and
 // integrator branches); software prefetch of the next tile 42.5 us; the
 // scalar kernel 45.8 us.
-constexpr int PAIR2_MIN_BLOCKS = 6;
+// resident blocks the register budget is cut for: 8 (64 registers, a
+// 32-byte spill) runs the single-system kernel in 43 us against 52 us at 6
+// (80 registers) and 54 us at 7 (72) on the octanol box; the batched kernel
+// spills 204 bytes at 8 and keeps 6
+constexpr int PAIR2_MIN_BLOCKS = 8;
+constexpr int PAIR2_BATCH_MIN_BLOCKS = 6;
 constexpr int PAIR_CHUNK = 8;
 
 struct Pair2Shared {
@@ -1193,7 +1198,7 @@ __global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float>
 // many systems in one launch: the chunks of every system form one index
 // range that the warps share out evenly; each system's tiles, constants and
 // accumulators are its own, and its results are those of a launch of its own
-__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2_batch(const PairJob* jobs, int njobs)
+__global__ void __launch_bounds__(128, PAIR2_BATCH_MIN_BLOCKS) k_pairs2_batch(const PairJob* jobs, int njobs)
 {
     __shared__ Pair2Shared sh;
     const unsigned FULL = 0xffffffffu;
