@@ -1056,7 +1056,6 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
     for (int ch = c0; ch < c1; ++ch) {
         const int ta = ch * PAIR_CHUNK, tb = min(ta + PAIR_CHUNK, ntiles);
         int curI = -1;
-        R4<float> pown = {0, 0, 0, 0};   // lanes 0-7: i atom 8 curI + lane, unshifted
         for (int t = ta; t < tb; ++t) {
             const int4 tl = nb.tiles[t];
             const unsigned mc = nb.masks[(size_t)t * 32 + lane];
@@ -1067,7 +1066,6 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
                 if (curI >= 0) flush(curI);
                 curI = tl.x;
                 if (lane < 8) {
-                    pown = s.xq[curI * 8 + lane];
                     const R2<float> l = s.lj[curI * 8 + lane];
                     fC[hk] = l.x;
                     fC[hk + 2] = l.y;
@@ -1080,6 +1078,9 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
             // shift the far-side atom down by L so that the subtraction below is
             // the only rounding in the pair vector
             if (lane < 8) {
+                // i atom 8 curI + lane, read again for every tile (an L1 hit)
+                // rather than held in registers across the sub-cluster's tiles
+                const R4<float> pown = s.xq[curI * 8 + lane];
                 fA[hk] = sx == 1 ? pown.x - s.L[0] : pown.x;
                 fA[hk + 2] = sy == 1 ? pown.y - s.L[1] : pown.y;
                 fB[hk] = sz == 1 ? pown.z - s.L[2] : pown.z;
