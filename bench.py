@@ -92,6 +92,7 @@ def run_config(d, desc):
     """The workload description shared by both arms of the bench."""
     return {"workload": desc, "atoms": len(d["charge"]), "dt_fs": float(d["dt"]) * 1e3,
             "extended_thermostat": "regulated Nose-Hoover-Langevin, tau 40 fs, 25 ps^-1, regulation 1",
+            "list_buffer": "chosen by lfe_autotune among 0.10-0.26 nm (0.10 without autotuning)",
             "l2": "flushed between steps (256 MiB write)", "data": "seeded synthetic stand-in"}
 
 
@@ -305,7 +306,7 @@ def dafed_leg(args, stream, flush):
     d = dict(S.make_c4_frame(frame=0))
     d.update(dt=0.001, lambda_mass=20.0, lambda_friction=25.0, opes_stride=500,
              opes_dE_std=30.0 * 4.184, opes_dE_exp=5.0 * 4.184, opes_sigma=0.10)
-    g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242)
+    g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=4242, skin=0.0)   # buffer left to the autotuner
     g.set_dafed(S.DIPEPTIDE_CVS, 1000.0, 50.0, temperature=1000.0, friction=25.0)
     use_paper_thermostat(g)
     equilibrate(g, d, stream)
@@ -350,9 +351,12 @@ def batched_leg(args, stream, flush):
             g.set_integrator(float(d["dt"]) * frac, fric if fric else float(d["friction"]), float(d["temperature"]))
         b.step(200 if fric else args.warmup, stream)
     torch.cuda.synchronize()
-    # replicas keep the default launch shapes: the autotuner times one system
-    # stepping alone, and its choices measured no better for 32 replicas
-    # sharing the GPU (2.76-2.84 ms against 2.74-2.75 ms per batched step);
+    # replicas keep the default launch shapes and the 0.10 nm list buffer:
+    # the autotuner times one system stepping alone, and its choices measured
+    # no better for 32 replicas sharing the GPU (2.76-2.84 ms against
+    # 2.74-2.75 ms per batched step; buffers of 0.16 and 0.22 nm, which
+    # shorten a single system's step, gave 2.60 and 2.68 ms against 2.58 ms:
+    # with 32 replicas the pair work, not the rebuilds, sets the step);
     # --tune-cache applies a cache's entries to them
     tuned = [g.autotune(reps=20, cache_path=args.tune_cache)[1] for g in reps] \
         if (args.tune_cache and not args.no_autotune) else []
@@ -470,7 +474,7 @@ def run_ours(args):
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     dt_ps = float(d["dt"])
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    g = lfe.System(d, precision=prec, seed=2608 + rank)
+    g = lfe.System(d, precision=prec, seed=2608 + rank, skin=0.0)   # buffer left to the autotuner
     use_paper_thermostat(g)
     terms0, _ = g.eval(d["lam"])
     n_pairs = terms0["n_pairs"]
@@ -552,7 +556,9 @@ def run_ours(args):
                             "(page-locked host buffers)"}
         fp64 = None
         if not args.no_fp64 and prec == lfe.LFE_FP32_MIXED:
-            g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=2608)
+            # the same workload and list buffer as the mixed system
+            g64 = lfe.System(d, precision=lfe.LFE_FP64, seed=2608,
+                             skin=(tune["skin_pm"] * 1e-3) if tune else 0.1)
             use_paper_thermostat(g64)
             g64.set_positions(pos)
             g64.set_velocities(vel)

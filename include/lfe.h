@@ -82,7 +82,8 @@ typedef struct {
     double ewald_alpha;       /* Ewald splitting parameter, nm^-1 */
     int pme_grid[3];          /* PME grid; each a product of 2, 3 and 5, 8..128 */
     int pme_order;            /* B-spline order; must be 4 */
-    double skin;              /* neighbour-list buffer, nm (default 0.1 if <= 0) */
+    double skin;              /* neighbour-list buffer, nm: > 0 fixed; <= 0 0.1 until
+                                 lfe_autotune chooses it */
     int precision;            /* LFE_FP32_MIXED or LFE_FP64 */
     double temperature;       /* step: K */
     double friction;          /* step: atoms' Langevin friction, 1/ps */
@@ -380,19 +381,24 @@ int lfe_set_list_capacity(lfe_system* sys, int tiles);
  * rebuild, weighted 1:3).  Knobs: blocks of the pair kernel per multiprocessor (1 up to
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
  * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
- * passes (4 or 16), one knob at a time, `reps` (1..10000) steps or graph
+ * passes (4 or 16) and, when lfe_params.skin <= 0 and the objective is the
+ * stepped one, the neighbour-list buffer (0.10, 0.14, 0.18, 0.22 or 0.26 nm:
+ * a wider buffer means fewer rebuilds and longer tile lists; after a change
+ * the pair kernel's blocks are tuned again), one knob at a time, `reps`
+ * (1..10000) steps or graph
  * replays per candidate (mean step time, or the median replay), a candidate
  * replacing the current choice only when 2 % faster.  The replays leave the state
  * (positions, velocities, theta, counters, accumulators) as it was; the next
  * lfe_step recaptures its graph with the chosen shapes.  Call it on an
  * equilibrated system (the stepped objective needs stable dynamics).  Launch shapes change
- * only how work is split over blocks and warps, so results stay within the
+ * only how work is split over blocks and warps, and the buffer only which
+ * tiles hold the pairs within the cutoff, so results stay within the
  * precision mode's tolerance (summation order).  cache_path (or NULL): a JSON
  * file of tuned entries keyed on the device, atom counts, density, cutoff,
  * grid and precision; a matching entry is applied without timing, a new one
  * is added.  Outputs (each may be NULL): best_ms = the objective (ms) of
- * the choice; params[4] = (pair blocks per SM, uv energy blocks, df64 lines,
- * 1 if taken from the cache else 0).  Errors: LFE_ERR_ARG (reps out of range,
+ * the choice; params[5] = (pair blocks per SM, uv energy blocks, df64 lines,
+ * 1 if taken from the cache else 0, list buffer in 1e-3 nm).  Errors: LFE_ERR_ARG (reps out of range,
  * cache not writable), LFE_ERR_CUDA.  Not part of the paper's method: it
  * serves the batched-replica workload's "sizes chosen by an autotuner". */
 int lfe_autotune(lfe_system* sys, int reps, const char* cache_path, double* best_ms, int* params);

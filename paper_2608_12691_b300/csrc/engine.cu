@@ -383,6 +383,7 @@ struct System final : SystemBase {
 
         // ---------------------------------------------------- neighbours
         double skin = p.skin > 0 ? p.skin : 0.1;
+        skin_auto = !(p.skin > 0);
         P.skin = skin;
         const double V = p.box[0] * p.box[1] * p.box[2];
         N.col_of = dalloc<int>(n_solv);
@@ -1193,9 +1194,10 @@ struct System final : SystemBase {
                 out = std::strtod(line.c_str() + at + t.size(), nullptr);
                 return true;
             };
-            double a, b, c, d;
+            double a, b, c, d, e;
             if (num("pair_blocks_per_sm", a) && num("uv_blocks", b) && num("df64_lines", c) && num("eval_ms", d)) {
                 v[0] = (int)a; v[1] = (int)b; v[2] = (int)c; *ms = d;
+                if (num("skin_pm", e)) v[3] = (int)e;
                 return true;
             }
         }
@@ -1218,8 +1220,8 @@ struct System final : SystemBase {
         char buf[768];
         std::snprintf(buf, sizeof(buf),
                       "{\"key\": \"%s\", \"pair_blocks_per_sm\": %d, \"uv_blocks\": %d, \"df64_lines\": %d, "
-                      "\"eval_ms\": %.6f}",
-                      key.c_str(), v[0], v[1], v[2], ms);
+                      "\"skin_pm\": %d, \"eval_ms\": %.6f}",
+                      key.c_str(), v[0], v[1], v[2], v[3], ms);
         keep.push_back(buf);
         std::ofstream f(path, std::ios::trunc);
         if (!f) fail(LFE_ERR_ARG, "cannot write the tuning cache " + path);
@@ -1234,8 +1236,34 @@ struct System final : SystemBase {
         pair_warps = nsm * 4 * std::min(std::max(v[0], 1), bmax);
         uv_blocks = std::max(v[1], 1);
         M2.lines = v[2] == 4 ? 4 : 0;
+        if (skin_auto && v[3] > 0 && v[3] != skin_pm()) set_skin(v[3] * 1e-3);
         invalidate_graph();
         ++generation;   // batches that hold this system's step recapture it
+    }
+
+    // List buffer (nm): the list holds pairs within r_cut + skin and is
+    // rebuilt once an atom has moved more than skin/2 since the last build.
+    // A new buffer takes effect with a rebuild at the current positions
+    // before the next evaluation.
+    bool skin_auto = false;   // the caller left the buffer to lfe_autotune
+    static constexpr int SKIN_CANDIDATES_PM[5] = {100, 140, 180, 220, 260};
+    int skin_pm() const { return (int)std::lround(P.skin * 1e3); }
+
+    void set_skin(double skin)
+    {
+        P.skin = skin;
+        N.cut2 = (float)((P.r_cut + skin) * (P.r_cut + skin));
+        N.skin_half2 = (float)(0.25 * skin * skin);
+        G.skin_half2 = (real)(0.25 * skin * skin);
+        force_rebuild();
+        invalidate_graph();
+        ++generation;
+    }
+
+    void force_rebuild()
+    {
+        const int one = 1;
+        CK(cudaMemcpy(S.flags + FL_REBUILD, &one, sizeof(int), cudaMemcpyHostToDevice));
     }
 
     double time_eval_graph(int reps, bool with_build)
@@ -1268,12 +1296,12 @@ struct System final : SystemBase {
     {
         if (reps < 1 || reps > 10000) fail(LFE_ERR_ARG, "reps must be in [1, 10000]");
         const std::string key = tune_key();
-        int v[3] = {pairs_blocks_per_sm<real>(), nsm * 2, 16};
+        int v[4] = {pairs_blocks_per_sm<real>(), nsm * 2, 16, skin_pm()};
         double best = 0.0;
         if (cache_path && cache_find(cache_path, key, v, &best)) {
             apply_tuning(v);
             if (best_ms) *best_ms = best;
-            if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 1; }
+            if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 1; params[4] = v[3]; }
             return;
         }
         // a valid list for the current positions, nothing pending
@@ -1342,24 +1370,40 @@ struct System final : SystemBase {
                    REBUILD_FRACTION * time_eval_graph(reps, true);
         };
         best = measure(v);
-        for (int b = 1; b <= bmax; ++b) {
-            if (b == v[0]) continue;
-            int c[3] = {b, v[1], v[2]};
-            const double t = measure(c);
-            if (t < 0.98 * best) { best = t; v[0] = b; }
-        }
+        auto pair_blocks = [&]() {
+            for (int b = 1; b <= bmax; ++b) {
+                if (b == v[0]) continue;
+                int c[4] = {b, v[1], v[2], v[3]};
+                const double t = measure(c);
+                if (t < 0.98 * best) { best = t; v[0] = b; }
+            }
+        };
+        pair_blocks();
         if (n_ucl > 0) {
             for (int ub : {nsm / 2, nsm, nsm * 4, nsm * 8}) {
                 if (ub < 1 || ub == v[1]) continue;
-                int c[3] = {v[0], ub, v[2]};
+                int c[4] = {v[0], ub, v[2], v[3]};
                 const double t = measure(c);
                 if (t < 0.98 * best) { best = t; v[1] = ub; }
             }
         }
         if (dual) {
-            int c[3] = {v[0], v[1], v[2] == 16 ? 4 : 16};
+            int c[4] = {v[0], v[1], v[2] == 16 ? 4 : 16, v[3]};
             const double t = measure(c);
             if (t < 0.98 * best) { best = t; v[2] = c[2]; }
+        }
+        // the list buffer, when the caller left it to the tuner (stepped
+        // objective only: its cost is the rebuild rate against longer tile
+        // lists), then the pair kernel's blocks again for the chosen lists
+        if (skin_auto && by_steps) {
+            const int before = v[3];
+            for (int sk : SKIN_CANDIDATES_PM) {
+                if (sk == v[3]) continue;
+                int c[4] = {v[0], v[1], v[2], sk};
+                const double t = measure(c);
+                if (t < 0.98 * best) { best = t; v[3] = sk; }
+            }
+            if (v[3] != before) pair_blocks();
         }
         apply_tuning(v);
         if (by_steps) {
@@ -1377,7 +1421,7 @@ struct System final : SystemBase {
         check_flags(cs);
         if (cache_path) cache_store(cache_path, key, v, best);
         if (best_ms) *best_ms = best;
-        if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 0; }
+        if (params) { params[0] = v[0]; params[1] = v[1]; params[2] = v[2]; params[3] = 0; params[4] = v[3]; }
     }
 
     // Replace the tile list by one of exactly `tiles` tiles (the build kernels
@@ -2095,6 +2139,7 @@ struct System final : SystemBase {
         char magic[8];
         int version, precision, n, max_k, n_cv, pad;
         double box[3];
+        double skin;      // list buffer of the run that wrote it
     };
 
     void checkpoint(const char* path) override
@@ -2103,7 +2148,8 @@ struct System final : SystemBase {
         check_flags(nullptr);
         CkHeader h{};
         std::memcpy(h.magic, "LFECKPT1", 8);
-        h.version = 4;
+        h.version = 5;
+        h.skin = P.skin;
         h.precision = precision;
         for (int d = 0; d < 3; ++d) h.box[d] = P.box[d];
         h.n = n;
@@ -2162,7 +2208,7 @@ struct System final : SystemBase {
         if (stored != fnv1a(buf.data(), body)) fail(LFE_ERR_ARG, "checkpoint checksum mismatch");
         CkHeader h;
         std::memcpy(&h, buf.data(), sizeof(h));
-        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 4 || h.precision != precision || h.n != n ||
+        if (std::memcmp(h.magic, "LFECKPT1", 8) != 0 || h.version != 5 || h.precision != precision || h.n != n ||
             h.max_k != T.max_k || h.n_cv != D.n)
             fail(LFE_ERR_ARG, "checkpoint header does not match this system");
         if (h.box[0] != P.box[0] || h.box[1] != P.box[1] || h.box[2] != P.box[2]) set_box(h.box);
@@ -2197,6 +2243,9 @@ struct System final : SystemBase {
         build_neighbors(nullptr);
         CK(cudaMemcpy(S.x, xcur.data(), xcur.size(), cudaMemcpyHostToDevice));
         refresh_sorted(nullptr);
+        // a list built at the saved reference positions with a smaller
+        // buffer than the writer's may miss pairs at the current positions
+        if (h.skin > P.skin) force_rebuild();
         CK(cudaDeviceSynchronize());
         LamState L;
         CK(cudaMemcpy(&L, S.lam, sizeof(L), cudaMemcpyDeviceToHost));

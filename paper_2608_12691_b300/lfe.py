@@ -471,14 +471,15 @@ class System:
         self._check(self._lib.lfe_set_list_capacity(self.h, int(tiles)))
 
     def autotune(self, reps=20, cache_path=None):
-        """Choose the evaluation's launch shapes by timing (lfe_autotune).
-        Returns (median evaluation ms, {pair_blocks_per_sm, uv_blocks,
-        df64_lines, from_cache})."""
+        """Choose the evaluation's launch shapes (and, for skin <= 0, the list
+        buffer) by timing (lfe_autotune).  Returns (objective ms,
+        {pair_blocks_per_sm, uv_blocks, df64_lines, from_cache, skin_pm})."""
         best = ctypes.c_double()
-        params = (ctypes.c_int * 4)()
+        params = (ctypes.c_int * 5)()
         path = None if cache_path is None else str(cache_path).encode()
         self._check(self._lib.lfe_autotune(self.h, int(reps), path, ctypes.byref(best), params))
-        return best.value, dict(zip(["pair_blocks_per_sm", "uv_blocks", "df64_lines", "from_cache"], list(params)))
+        return best.value, dict(zip(["pair_blocks_per_sm", "uv_blocks", "df64_lines", "from_cache", "skin_pm"],
+                                    list(params)))
 
     def time_stages(self, lam, reps=10, stream=None, max_n=32):
         names = (ctypes.c_char_p * max_n)()

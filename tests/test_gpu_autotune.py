@@ -54,3 +54,53 @@ def test_autotune_rejects_bad_reps():
     t, _ = g.eval(0.5)
     assert np.isfinite(t["U"])
     g.close()
+
+
+def small_water(lam=0.62):
+    d = S.make_water_box(seed=21, n_waters=101, box_len=1.45, solute="ring12", n_side=5,
+                         r_cut=0.7, grid=16, lam=lam)
+    d.update(dt=0.001, lambda_mass=0.0, opes_stride=0)
+    return d
+
+
+def test_autotune_chooses_the_list_buffer_when_left_to_it():
+    d = small_water()
+    g = lfe.System(d, precision=lfe.LFE_FP32_MIXED, skin=0.0)
+    g.step(20)
+    t0, F0 = g.eval(0.5)
+    p0, v0, e0 = g.get_state()
+    ms, par = g.autotune(reps=10)
+    assert par["skin_pm"] in (100, 140, 180, 220, 260)
+    p1, v1, e1 = g.get_state()
+    assert np.array_equal(p0, p1) and np.array_equal(v0, v1) and e1["step"] == e0["step"]
+    t1, F1 = g.eval(0.5)
+    assert np.linalg.norm(F1 - F0) / np.linalg.norm(F0) < 1e-6
+    assert abs(t1["n_pairs"] - t0["n_pairs"]) <= 2
+    g.step(20)
+    assert np.isfinite(g.get_state()[0]).all()
+    # a fixed buffer is never changed
+    h = lfe.System(d, precision=lfe.LFE_FP32_MIXED, skin=0.12)
+    h.step(20)
+    _, ph = h.autotune(reps=10)
+    assert ph["skin_pm"] == 120
+
+
+def test_restore_into_a_narrower_buffer_rebuilds_the_list(tmp_path):
+    # the writer's list (0.26 nm buffer) is only rebuilt after an atom moved
+    # 0.13 nm; a reader with a 0.10 nm buffer rebuilds at the restored
+    # positions, so its forces are those of the current configuration
+    from oracle import reference as R
+    d = small_water()
+    a = lfe.System(d, precision=lfe.LFE_FP32_MIXED, skin=0.26, seed=3)
+    a.step(60)
+    path = tmp_path / "wide.ckpt"
+    a.checkpoint(path)
+    pos, _, _ = a.get_state()
+    b = lfe.System(d, precision=lfe.LFE_FP32_MIXED, skin=0.10, seed=3)
+    b.restore(path)
+    t, F = b.eval(0.5)
+    E, F0, Fuv, Fs = R.nonbonded(dict(d, pos=pos.astype(np.float32)), level=2)
+    hA, hB, _, _ = R.switching(0.5)
+    Fo = F0 + hA * Fuv + hB * Fs
+    assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) < 1e-5
+    assert abs(t["n_pairs"] - E["n_pairs"]) <= 2
