@@ -261,7 +261,9 @@ int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsi
  * arrays in page-locked memory (cudaHostAlloc or cudaHostRegister;
  * otherwise LFE_ERR_ARG), caller order; ext_out (ordinary host memory, may
  * be NULL) receives the LFE_NEXT values of lfe_get_state.  pos_in is checked
- * like lfe_set_positions (non-finite: LFE_ERR_ARG, nothing changed).  The
+ * on the device, inside the graph (a coordinate that is not finite: the
+ * step leaves the state as it was, the outputs receive that state, and the
+ * call returns LFE_ERR_ARG).  The
  * graph is captured on the first call and again whenever the host pointers
  * change.  A neighbour-list overflow inside the step is recovered (grow,
  * rebuild, replay) before the call returns.  Returns after synchronising

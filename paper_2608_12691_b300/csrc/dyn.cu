@@ -129,6 +129,7 @@ template <typename real>
 __global__ void k_assign_moved(SysView<real> s, const double* pos, real skin_half2)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s.flags[FL_ERROR] & ERRB_BADPOS) return;   // refused by k_check_positions: nothing changes
     bool far = false;
     if (a < s.n) {
         const int slot = s.iperm[a];
@@ -152,6 +153,23 @@ template <typename real>
 void launch_assign_moved(const SysView<real>& s, const double* pos, real skin_half2, cudaStream_t st)
 {
     k_assign_moved<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos, skin_half2);
+}
+
+// new positions (caller doubles) checked on the device before they are
+// assigned: any coordinate that is not finite raises ERRB_BADPOS, and the
+// step that follows leaves the state as it was
+template <typename real>
+__global__ void k_check_positions(SysView<real> s, const double* pos)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool bad = i < 3 * s.n && !isfinite(pos[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_ERROR], ERRB_BADPOS);
+}
+
+template <typename real>
+void launch_check_positions(const SysView<real>& s, const double* pos, cudaStream_t st)
+{
+    k_check_positions<real><<<(3 * s.n + 255) / 256, 256, 0, st>>>(s, pos);
 }
 
 // Monte Carlo volume move (the NPT runs of Section 2.6): every molecule's
@@ -454,7 +472,7 @@ __global__ void k_dafed_step(SysView<real> s, DafedView d)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= d.n) return;
-    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) return;   // step skipped (see k_integrate)
+    if (s.flags[FL_ERROR] & ERRB_SKIP) return;   // step skipped (see k_integrate)
     const unsigned long long step = d.pre->step;   // runs beside k_theta, which advances the counter
     double n0, n1, n2;
     normals3<double>(make_uint4((unsigned)k, (unsigned)step, (unsigned)(step >> 32), 2u), d.key, n0, n1, n2);
@@ -724,9 +742,10 @@ __global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.n_groups) return;
     const Group G = g.groups[gi];
-    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {
-        // the neighbour list was truncated: consume the forces, leave the
-        // state untouched (the host regrows the list and replays the step)
+    if (s.flags[FL_ERROR] & ERRB_SKIP) {
+        // the neighbour list was truncated (the host regrows it and replays
+        // the step) or the new positions were refused: consume the forces,
+        // leave the state untouched
         for (int a = 0; a < G.natom; ++a) {
             const int atom = G.atom[a], slot = s.iperm[atom];
             s.F[slot] = 0; s.F[s.n_pad + slot] = 0; s.F[2 * s.n_pad + slot] = 0;
@@ -881,7 +900,7 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     const int lane = threadIdx.x;
     LamState* L = s.lam;
     long long* E = s.E;
-    if (s.flags[FL_ERROR] & ERRB_OVERFLOW) {   // step skipped (see k_integrate): no advance
+    if (s.flags[FL_ERROR] & ERRB_SKIP) {   // step skipped (see k_integrate): no advance
         if (lane < E_N) E[lane] = 0;
         return;
     }
@@ -1007,10 +1026,12 @@ void launch_hrex(LamState* const* lams, const double* terms, int* ladder, int n,
 template <typename real>
 __global__ void k_rebuild_cond(SysView<real> s, cudaGraphConditionalHandle h)
 {
-    const int rb = s.flags[FL_REBUILD] && !(s.flags[FL_ERROR] & ERRB_OVERFLOW);
+    const int err = s.flags[FL_ERROR];
+    const int rb = s.flags[FL_REBUILD] && !(err & ERRB_SKIP);
     cudaGraphSetConditional(h, rb ? 1u : 0u);
     if (rb) s.flags[FL_NREBUILD] += 1;
-    s.flags[FL_REBUILD] = 0;
+    // a step skipped for refused positions keeps a pending rebuild for the next one
+    if (!(err & ERRB_BADPOS)) s.flags[FL_REBUILD] = 0;
 }
 
 template <typename real>
@@ -1030,6 +1051,7 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_eval_out<real>(const SysView<real>&, double*, double*, double, double, double,   \
                                         cudaStream_t);                                                    \
     template void launch_assign_moved<real>(const SysView<real>&, const double*, real, cudaStream_t);       \
+    template void launch_check_positions<real>(const SysView<real>&, const double*, cudaStream_t);         \
     template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
     template void launch_pack_state<real>(const SysView<real>&, const OpesState*, double*, cudaStream_t);   \
     template void launch_scale_molecules<real>(const SysView<real>&, const int*, const int*, const double*, int, \

@@ -1764,6 +1764,7 @@ struct System final : SystemBase {
             // the step's own conditional rebuild (first branch below) acts
             // on the flag that the new positions raise
             CK(cudaMemcpyAsync(d_pos, pos_in, sizeof(double) * nv, cudaMemcpyHostToDevice, s0));
+            launch_check_positions(S, d_pos, s0);
             launch_assign_moved(S, d_pos, G.skin_half2, s0);
         }
         cudaGraphConditionalHandle h;
@@ -1787,7 +1788,6 @@ struct System final : SystemBase {
         if (!(P.dt > 0)) fail(LFE_ERR_STATE, "dt must be positive to step");
         if (!host_pinned(pos_in) || !host_pinned(pos_out) || !host_pinned(vel_out))
             fail(LFE_ERR_ARG, "host buffers of lfe_step_io must be page-locked");
-        if (pos_in && !finite_all(pos_in, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
         if (eager || pos_pending || since_check > 0) {
             // a queued overflow or pending position update is settled first
             CK(cudaStreamSynchronize(st));
@@ -1796,6 +1796,7 @@ struct System final : SystemBase {
             pos_pending = false;
         }
         if (eager) {
+            if (pos_in && !finite_all(pos_in, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
             if (pos_in) set_positions(pos_in, 0, st);
             step(1, st);
             get_state(pos_out, vel_out, ext_out);
@@ -1812,6 +1813,14 @@ struct System final : SystemBase {
         ++steps_requested;
         CK(cudaStreamSynchronize(st));
         const int err = (int)h_io_tail[10];
+        if (err & ERRB_BADPOS) {
+            // the positions were checked on the device and refused: the step
+            // left the state as it was (the outputs hold that state)
+            const int rest = err & ~ERRB_BADPOS;
+            CK(cudaMemcpy(S.flags + FL_ERROR, &rest, sizeof(int), cudaMemcpyHostToDevice));
+            --steps_requested;
+            fail(LFE_ERR_ARG, "non-finite position");
+        }
         if (err) {
             // the step was skipped (list overflow) or failed: the general path
             // settles it and reads the state again

@@ -36,7 +36,10 @@ enum {
 // error / control flags
 enum { FL_REBUILD = 0, FL_ERROR = 1, FL_NTILES = 2, FL_NREBUILD = 3, FL_NUV = 4, FL_NSTAGE = 5, FL_NUVT = 6,
        FL_N = 8 };
-enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4 };
+// ERRB_BADPOS: the positions handed to a host-I/O step were not all finite;
+// the step is skipped like one after a list overflow (ERRB_SKIP)
+enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4, ERRB_BADPOS = 8 };
+enum { ERRB_SKIP = ERRB_OVERFLOW | ERRB_BADPOS };
 
 // one coordinate wrapped into [0, L) (the positions the neighbour list is
 // built from)

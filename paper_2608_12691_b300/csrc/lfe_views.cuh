@@ -343,6 +343,7 @@ template <typename real> void launch_eval_out(const SysView<real>& s, double* fo
 // build (the rebuild itself follows launch_rebuild_cond's conditional node)
 template <typename real> void launch_assign_moved(const SysView<real>& s, const double* pos, real skin_half2,
                                                   cudaStream_t st);
+template <typename real> void launch_check_positions(const SysView<real>& s, const double* pos, cudaStream_t st);
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
 template <typename real> void launch_scale_molecules(const SysView<real>& s, const int* mstart, const int* matoms,
                                                      const double* mass, int n_mol, double sc, const double* L,

@@ -74,3 +74,31 @@ def test_step_io_refuses_pageable_buffers_and_bad_positions():
     assert ext["step"] == 0
     g.step_io(None, None, None, None)
     assert g.get_state()[2]["step"] == 1
+
+
+def test_refused_positions_leave_the_trajectory_as_it_was():
+    # positions are checked on the device inside the captured step: a call
+    # with a non-finite coordinate changes nothing, so a run with one refused
+    # call in its middle equals a run without it, bit for bit
+    import torch
+    d = water_system()
+    n = len(d["charge"])
+    a = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=SEED)
+    b = lfe.System(d, precision=lfe.LFE_FP32_MIXED, seed=SEED)
+    pa, va, pb, vb = pinned((n, 3)), pinned((n, 3)), pinned((n, 3)), pinned((n, 3))
+    bad = pinned((n, 3))
+    ea, eb = np.zeros(lfe.NEXT), np.zeros(lfe.NEXT)
+    pa.copy_(torch.from_numpy(np.asarray(d["pos"], dtype=np.float64)))
+    pb.copy_(pa)
+    for k in range(12):
+        if k == 6:
+            bad.copy_(pa)
+            bad[17, 0] = float("inf")
+            with pytest.raises(lfe.LfeError) as e:
+                a.step_io(bad.data_ptr(), None, None, None)
+            assert e.value.code == lfe.LFE_ERR_ARG
+        a.step_io(pa.data_ptr(), pa.data_ptr(), va.data_ptr(), ea.ctypes.data)
+        b.step_io(pb.data_ptr(), pb.data_ptr(), vb.data_ptr(), eb.ctypes.data)
+        assert torch.equal(pa, pb) and torch.equal(va, vb)
+        assert np.array_equal(ea, eb)
+    assert eb[7] == 12
