@@ -375,7 +375,7 @@ def batched_leg(args, stream, flush):
     pairs = sum(g.eval(d["lam"])[0]["n_pairs"] for g, d in zip(reps, dicts))
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    batch_roof = {"bound": "alu", "kernel": "k_pairs2_batch (all FP32 replicas, one launch)",
+    batch_roof = {"bound": "alu", "kernel": "k_pairs2 (all FP32 replicas, one launch)",
                   "kernel_ms": pair_ms, "pairs_per_launch": pairs, "flops_per_pair": FLOPS_PER_PAIR,
                   "achieved": pairs * FLOPS_PER_PAIR / (pair_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s"}
     batch_roof["frac"] = batch_roof["achieved"] / peak

@@ -2513,9 +2513,9 @@ struct lfe_batch {
         CK(cudaGraphInstantiate(&ex_exec, ex_graph, 0));
     }
 
-    // the FP32 replicas' pair kernels run as one launch (k_pairs2_batch)
-    PairJob* d_jobs = nullptr;
-    int n_jobs = 0, jobs_cap = 0;
+    // the FP32 replicas' pair kernels run as one launch (k_pairs2, one row of its grid per replica)
+    std::vector<PairJob> h_jobs;
+    int n_jobs = 0;
     std::vector<int> shared;     // replica i takes part in the shared launch
     int pair_blocks = 0;
 
@@ -2530,7 +2530,6 @@ struct lfe_batch {
         if (pairs_done) cudaEventDestroy(pairs_done);
         if (s0) cudaStreamDestroy(s0);
         if (s_pair) cudaStreamDestroy(s_pair);
-        if (d_jobs) cudaFree(d_jobs);
         if (ex_exec) cudaGraphExecDestroy(ex_exec);
         if (ex_graph) cudaGraphDestroy(ex_graph);
         if (d_ladder) cudaFree(d_ladder);
@@ -2543,23 +2542,16 @@ struct lfe_batch {
     // refreshed whenever the graph is recaptured)
     void upload_jobs()
     {
-        std::vector<PairJob> jobs;
+        h_jobs.clear();
         shared.assign(sys.size(), 0);
         for (size_t i = 0; i < sys.size(); ++i) {
             PairJob j;
             if (sys[i]->impl->pair_job(&j)) {
-                jobs.push_back(j);
+                h_jobs.push_back(j);
                 shared[i] = 1;
             }
         }
-        n_jobs = (int)jobs.size();
-        if (n_jobs > jobs_cap) {
-            if (d_jobs) cudaFree(d_jobs);
-            d_jobs = nullptr;
-            CK(cudaMalloc(&d_jobs, sizeof(PairJob) * n_jobs));
-            jobs_cap = n_jobs;
-        }
-        if (n_jobs) CK(cudaMemcpy(d_jobs, jobs.data(), sizeof(PairJob) * n_jobs, cudaMemcpyHostToDevice));
+        n_jobs = (int)h_jobs.size();
         // one resident wave: measured on 16 water + 16 octanol replicas, the
         // batch step takes 2.58 ms with it, 2.78 / 3.19 / 3.92 / 5.88 ms with
         // 4 / 3 / 2 / 1 blocks per multiprocessor (the shared launch is the
@@ -2579,18 +2571,16 @@ struct lfe_batch {
         cudaEvent_t a, b;
         CK(cudaEventCreate(&a));
         CK(cudaEventCreate(&b));
-        launch_pairs_batch(d_jobs, n_jobs, pair_blocks, st);
+        launch_pairs_batch(h_jobs.data(), n_jobs, pair_blocks, st);
         CK(cudaEventRecord(a, st));
-        for (int r = 0; r < reps; ++r) launch_pairs_batch(d_jobs, n_jobs, pair_blocks, st);
+        for (int r = 0; r < reps; ++r) launch_pairs_batch(h_jobs.data(), n_jobs, pair_blocks, st);
         CK(cudaEventRecord(b, st));
         CK(cudaEventSynchronize(b));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, a, b));
         cudaEventDestroy(a);
         cudaEventDestroy(b);
-        std::vector<PairJob> jobs(n_jobs);
-        CK(cudaMemcpy(jobs.data(), d_jobs, sizeof(PairJob) * n_jobs, cudaMemcpyDeviceToHost));
-        for (auto& j : jobs) {
+        for (auto& j : h_jobs) {
             CK(cudaMemsetAsync(j.s.F, 0, sizeof(long long) * 3 * (size_t)j.s.n_pad, st));
             CK(cudaMemsetAsync(j.s.E, 0, sizeof(long long) * E_N, st));
         }
@@ -2625,7 +2615,7 @@ struct lfe_batch {
             CK(cudaStreamWaitEvent(s_pair, fork, 0));
             for (size_t i = 0; i < sys.size(); ++i)
                 if (shared[i]) CK(cudaStreamWaitEvent(s_pair, built[i], 0));
-            launch_pairs_batch(d_jobs, n_jobs, pair_blocks, s_pair);
+            launch_pairs_batch(h_jobs.data(), n_jobs, pair_blocks, s_pair);
             CK(cudaEventRecord(pairs_done, s_pair));
         }
         for (size_t i = 0; i < sys.size(); ++i) {

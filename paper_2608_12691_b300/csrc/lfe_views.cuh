@@ -284,6 +284,13 @@ struct PairJob {
     SysView<float> s;
     NblView<float> nb;
 };
+// the systems of one batched pair launch, passed by value (kernel parameter
+// space holds up to 32,764 bytes: 60 systems of 520 bytes)
+constexpr int PAIR_BATCH_MAX = 60;
+struct PairJobs {
+    PairJob j[PAIR_BATCH_MAX];
+};
+// jobs: a host array (captured by value into the launches)
 void launch_pairs_batch(const PairJob* jobs, int njobs, int nblocks, cudaStream_t st);
 int pairs_batch_blocks();   // one resident wave of the launch over many systems
 void launch_hrex(LamState* const* lams, const double* terms, int* ladder, int n, double beta, unsigned long long seed,

@@ -1009,12 +1009,10 @@ __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, f
 // step (0.149 against 0.142 ms: the kernel shares the GPU with the PME and
 // integrator branches); software prefetch of the next tile 42.5 us; the
 // scalar kernel 45.8 us.
-// resident blocks the register budget is cut for: 8 (64 registers, a
-// 32-byte spill) runs the single-system kernel in 43 us against 52 us at 6
-// (80 registers) and 54 us at 7 (72) on the octanol box; the batched kernel
-// spills 204 bytes at 8 and keeps 6
+// resident blocks the register budget is cut for: 8 (64 registers) runs the
+// kernel in 43 us against 52 us at 6 (80 registers) and 54 us at 7 (72) on
+// the octanol box
 constexpr int PAIR2_MIN_BLOCKS = 8;
-constexpr int PAIR2_BATCH_MIN_BLOCKS = 6;
 constexpr int PAIR_CHUNK = 8;
 
 struct Pair2Shared {
@@ -1181,10 +1179,9 @@ __device__ __forceinline__ void pairs2_store(const SysView<float>& s, Pair2Acc& 
     acc = Pair2Acc{};
 }
 
-// one system: the warps share out its chunks evenly
-__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float> s, NblView<float> nb)
+// one system's chunks shared out evenly over the warps of the blocks along x
+__device__ __forceinline__ void pairs2_system(const SysView<float>& s, const NblView<float>& nb, Pair2Shared& sh)
 {
-    __shared__ Pair2Shared sh;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = min(s.flags[FL_NTILES], nb.cap);
@@ -1196,39 +1193,16 @@ __global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(SysView<float>
     pairs2_store(s, acc);
 }
 
-// many systems in one launch: the chunks of every system form one index
-// range that the warps share out evenly; each system's tiles, constants and
-// accumulators are its own, and its results are those of a launch of its own
-__global__ void __launch_bounds__(128, PAIR2_BATCH_MIN_BLOCKS) k_pairs2_batch(const PairJob* jobs, int njobs)
+// One launch for one or many systems: blockIdx.y picks the system, whose
+// views are read from the launch's parameter space (a uniform index); its
+// blocks along x share out its chunks.  A single system is a launch with one
+// row, so a system stepped alone and the same system in a batched launch run
+// the same compiled code over the same chunks: their results are identical
+// bit for bit.
+__global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(const __grid_constant__ PairJobs P)
 {
     __shared__ Pair2Shared sh;
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    // total chunks over the systems (lane r sums systems r, r + 32, ...)
-    long long part = 0;
-    for (int r = lane; r < njobs; r += 32) {
-        const int nt = min(jobs[r].s.flags[FL_NTILES], jobs[r].nb.cap);
-        part += (nt + PAIR_CHUNK - 1) / PAIR_CHUNK;
-    }
-    const long long total = __shfl_sync(FULL, warp_sum_ll(part), 0);
-    const long long g0 = (total * warp) / nwarp, g1 = (total * (warp + 1)) / nwarp;
-    if (g0 >= g1) return;
-    long long off = 0;
-    Pair2Acc acc;
-    for (int r = 0; r < njobs && off < g1; ++r) {
-        const SysView<float>& s = jobs[r].s;
-        const NblView<float>& nb = jobs[r].nb;
-        const int nt = min(s.flags[FL_NTILES], nb.cap);
-        const int nch = (nt + PAIR_CHUNK - 1) / PAIR_CHUNK;
-        const long long a = max(g0, off), b = min(g1, off + nch);
-        if (a < b) {
-            pairs2_chunks(s, nb, nt, (int)(a - off), (int)(b - off), sh, acc);
-            pairs2_store(s, acc);
-        }
-        off += nch;
-    }
+    pairs2_system(P.j[blockIdx.y].s, P.j[blockIdx.y].nb, sh);
 }
 
 // The FP64 pair kernel.  One warp walks a contiguous chunk of the
@@ -1476,13 +1450,21 @@ int pairs_batch_blocks()
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
                                                    cudaSuccess || nsm < 1)
         nsm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs2_batch, 128, 0) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pairs2, 128, 0) != cudaSuccess || nb < 1) nb = 1;
     return nsm * nb;
 }
 
+// jobs: host array; up to PAIR_BATCH_MAX systems per launch, each with
+// nblocks / (systems in the launch) blocks (at least one)
 void launch_pairs_batch(const PairJob* jobs, int njobs, int nblocks, cudaStream_t st)
 {
-    if (njobs > 0) k_pairs2_batch<<<nblocks, 128, 0, st>>>(jobs, njobs);
+    for (int j0 = 0; j0 < njobs; j0 += PAIR_BATCH_MAX) {
+        const int cnt = min(PAIR_BATCH_MAX, njobs - j0);
+        PairJobs P;
+        for (int k = 0; k < cnt; ++k) P.j[k] = jobs[j0 + k];
+        const int gx = max(1, nblocks / cnt);
+        k_pairs2<<<dim3(gx, cnt), 128, 0, st>>>(P);
+    }
 }
 
 template <typename real>
@@ -1490,8 +1472,12 @@ void launch_pairs(const SysView<real>& s, const NblView<real>& nb, int nwarps, c
 {
     const int B = 128;
     const int blocks = (nwarps * 32 + B - 1) / B;
-    if constexpr (sizeof(real) == 8) k_pairs_listed<real><<<blocks, B, 0, st>>>(s, nb);
-    else k_pairs2<<<blocks, B, 0, st>>>(s, nb);
+    if constexpr (sizeof(real) == 8) {
+        k_pairs_listed<real><<<blocks, B, 0, st>>>(s, nb);
+    } else {
+        PairJob j{s, nb};
+        launch_pairs_batch(&j, 1, blocks, st);
+    }
 }
 
 // ------------------------------------------------- exclusions and 1-4 pairs
