@@ -32,10 +32,17 @@ METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) o
 # Newton's third law 12 (58 in all; about two of them go to the special
 # function unit)
 FLOPS_PER_PAIR = 58
-# DRAM bytes (read + write) of one k_pairs2 launch on the octanol workload, from an ncu
-# capture of the current kernel version (dram__bytes_read.sum + dram__bytes_write.sum, 7.175 MB
-# read, 0 written); None whenever the kernel has changed since the capture
-PAIR_DRAM_BYTES_OCTANOL = 7.174656e6 + 0.0
+# From one ncu capture of the current k_pairs2 on the octanol profile case
+# (36,610 tiles of the 0.10 nm-buffer list): DRAM bytes (dram__bytes_read.sum
+# 7,173,376 + dram__bytes_write.sum 0) and counted FP32 operations (2 FFMA +
+# 4 FFMA2 + FADD + 2 FADD2 + FMUL + 2 FMUL2, predicated-on thread
+# instructions: 4.396e8), both per tile, for scaling to the tile count of
+# the timed launch (the tile records dominate the traffic, and every tile
+# runs the same instruction stream); None whenever the kernel has changed
+# since the capture
+PAIR_CAPTURE_TILES = 36610
+PAIR_DRAM_BYTES_PER_TILE = 7173376.0 / PAIR_CAPTURE_TILES
+PAIR_COUNTED_FLOPS_PER_TILE = 4.396e8 / PAIR_CAPTURE_TILES
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2032.0
 # timed evaluations of the reference arm at most (one level-2 oracle
@@ -521,7 +528,8 @@ def run_ours(args):
         pair_ms = stages["pairs"]
         achieved = n_pairs * FLOPS_PER_PAIR / (pair_ms * 1e-3) / 1e12
         peak = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
-        traffic = PAIR_DRAM_BYTES_OCTANOL if (args.workload == "octanol" and prec == lfe.LFE_FP32_MIXED) else None
+        octanol32 = args.workload == "octanol" and prec == lfe.LFE_FP32_MIXED
+        traffic = PAIR_DRAM_BYTES_PER_TILE * n_tiles if octanol32 else None
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_pairs2 (FP32, packed f32x2)", "kernel_ms": pair_ms,
                 "flops_per_pair": FLOPS_PER_PAIR,
@@ -533,6 +541,13 @@ def run_ours(args):
         roof["peak_measured_fma_fp32"] = f32_meas
         roof["peak_measured_fma_fp64"] = f64_meas
         roof["frac_of_measured_fma"] = achieved / f32_meas
+        if octanol32:
+            # the FP32 pipes' own count (every evaluated pair slot, in range or
+            # not), per tile from the ncu capture, over the live kernel time
+            counted = PAIR_COUNTED_FLOPS_PER_TILE * n_tiles / (pair_ms * 1e-3) / 1e12
+            roof["counted_fp32_tflops"] = counted
+            roof["frac_counted_fp32"] = counted / peak
+            roof["traffic_basis"] = f"ncu per-tile figures of a {PAIR_CAPTURE_TILES}-tile capture x {n_tiles} tiles"
         # end to end through the public API with host buffers: one lfe_step_io
         # per step (host-to-device copy of the positions, the step, and the
         # device-to-host copies of positions, velocities and the scalar state,
@@ -617,7 +632,8 @@ def run_profile_case(args):
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
     g = lfe.System(d, precision=prec)
     stages = g.time_stages(d["lam"], reps=3)
-    print(json.dumps({"profile_case": args.workload, "stages_ms": stages}))
+    _, _, ext = g.get_state()
+    print(json.dumps({"profile_case": args.workload, "stages_ms": stages, "tiles": int(ext["n_tiles"])}))
 
 
 def main():
