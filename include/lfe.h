@@ -384,9 +384,9 @@ int lfe_set_list_capacity(lfe_system* sys, int tiles);
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
  * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
  * passes (4 or 16) and, when lfe_params.skin <= 0 and the objective is the
- * stepped one, the neighbour-list buffer (0.10, 0.14, 0.18, 0.22 or 0.26 nm:
- * a wider buffer means fewer rebuilds and longer tile lists; after a change
- * the pair kernel's blocks are tuned again), one knob at a time, `reps`
+ * stepped one, the neighbour-list buffer (0.10, 0.14, 0.18, 0.22 or 0.26 nm,
+ * each with every pair-kernel block count: a wider buffer means fewer
+ * rebuilds and longer tile lists), one knob at a time otherwise, `reps`
  * (1..10000) steps or graph
  * replays per candidate (mean step time, or the median replay), a candidate
  * replacing the current choice only when 2 % faster.  The replays leave the state

@@ -1396,14 +1396,18 @@ struct System final : SystemBase {
         // objective only: its cost is the rebuild rate against longer tile
         // lists), then the pair kernel's blocks again for the chosen lists
         if (skin_auto && by_steps) {
-            const int before = v[3];
+            // every buffer with every pair-kernel block count: the two trade
+            // against each other (a longer list wants the kernel to keep more
+            // of the GPU), so one knob at a time can stop at a worse pair
+            const int sk0 = v[3];
             for (int sk : SKIN_CANDIDATES_PM) {
-                if (sk == v[3]) continue;
-                int c[4] = {v[0], v[1], v[2], sk};
-                const double t = measure(c);
-                if (t < 0.98 * best) { best = t; v[3] = sk; }
+                if (sk == sk0) continue;
+                for (int b = 1; b <= bmax; ++b) {
+                    int c[4] = {b, v[1], v[2], sk};
+                    const double t = measure(c);
+                    if (t < 0.98 * best) { best = t; v[0] = b; v[3] = sk; }
+                }
             }
-            if (v[3] != before) pair_blocks();
         }
         apply_tuning(v);
         if (by_steps) {
