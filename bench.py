@@ -548,6 +548,12 @@ def run_ours(args):
             roof["counted_fp32_tflops"] = counted
             roof["frac_counted_fp32"] = counted / peak
             roof["traffic_basis"] = f"ncu per-tile figures of a {PAIR_CAPTURE_TILES}-tile capture x {n_tiles} tiles"
+        if "pairs_full" in stages:
+            # the same launch with the grid that fills every multiprocessor
+            # (the step keeps fewer blocks to leave room for the PME branches)
+            full_ms = stages["pairs_full"]
+            roof["kernel_ms_full_grid"] = full_ms
+            roof["frac_full_grid"] = n_pairs * FLOPS_PER_PAIR / (full_ms * 1e-3) / 1e12 / peak
         # end to end through the public API with host buffers: one lfe_step_io
         # per step (host-to-device copy of the positions, the step, and the
         # device-to-host copies of positions, velocities and the scalar state,

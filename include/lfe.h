@@ -349,8 +349,12 @@ int lfe_checkpoint(lfe_system* sys, const char* path);
 int lfe_restore(lfe_system* sys, const char* path);
 
 /* Mean device time (ms) of each kernel stage over `reps` eager evaluations at
- * lambda, timed with CUDA events on `stream`.  names/ms arrays of length
- * max_n; returns the number of stages written (>= 0) or an error code. */
+ * lambda, timed with CUDA events on `stream`: list build, pair kernel (the
+ * step's launch shape), PME stages, exclusions, bonded terms, output, FP64
+ * solute-solvent energies and, for FP32 systems, "pairs_full" (the pair
+ * kernel once more with a grid that fills every multiprocessor).  names/ms
+ * arrays of length max_n; returns the number of stages written (>= 0) or an
+ * error code. */
 int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,
                     const char** names, double* ms, int max_n);
 

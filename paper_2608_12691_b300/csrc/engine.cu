@@ -2277,9 +2277,9 @@ struct System final : SystemBase {
     {
         static const char* stage_names[] = {"nbl_build", "pairs", "pme_spread", "pme_fft_fwd", "pme_conv",
                                             "pme_fft_inv", "pme_gather", "excl_14", "bonded", "eval_out",
-                                            "uv_energy_fp64"};
-        const int ns = 11;
-        std::vector<cudaEvent_t> ev(ns + 1);
+                                            "uv_energy_fp64", "pairs_full"};
+        const int ns = 12;
+        std::vector<cudaEvent_t> ev(ns + 2);
         for (auto& e : ev) CK(cudaEventCreate(&e));
         std::vector<double> acc(ns, 0.0);
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
@@ -2345,11 +2345,24 @@ struct System final : SystemBase {
             float tu = 0;
             CK(cudaEventElapsedTime(&tu, ev[2], ev[11]));
             acc[10] += tu;
+            // the pair kernel once more with the grid that fills every
+            // multiprocessor (the step's tuned shape may leave room for the
+            // concurrent branches); its forces are cleared again
+            if constexpr (std::is_same<real, float>::value) {
+                CK(cudaEventRecord(ev[12], st));
+                launch_pairs(S, N, nsm * 4 * pairs_blocks_per_sm<real>(), st);
+                CK(cudaEventRecord(ev[13], st));
+                launch_eval_out(S, nullptr, nullptr, const_vv, const_uu, const_uv, st);
+                CK(cudaEventSynchronize(ev[13]));
+                float tf = 0;
+                CK(cudaEventElapsedTime(&tf, ev[12], ev[13]));
+                acc[11] += tf;
+            }
         }
         CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
         for (auto& e : ev) cudaEventDestroy(e);
         check_flags(st);
-        const int m = std::min(ns, max_n);
+        const int m = std::min(std::is_same<real, float>::value ? ns : ns - 1, max_n);
         for (int k = 0; k < m; ++k) {
             if (names) names[k] = stage_names[k];
             if (ms) ms[k] = reps > 0 ? acc[k] / reps : 0.0;

@@ -104,3 +104,17 @@ def test_restore_into_a_narrower_buffer_rebuilds_the_list(tmp_path):
     Fo = F0 + hA * Fuv + hB * Fs
     assert np.linalg.norm(F - Fo) / np.linalg.norm(Fo) < 1e-5
     assert abs(t["n_pairs"] - E["n_pairs"]) <= 2
+
+
+@pytest.mark.parametrize("precision", [lfe.LFE_FP32_MIXED, lfe.LFE_FP64])
+def test_stage_timer_lists_the_stages_and_leaves_results_alone(precision):
+    d = small_water()
+    g = lfe.System(d, precision=precision)
+    t0, F0 = g.eval(0.4)
+    st = g.time_stages(0.7, reps=3)
+    names = ["nbl_build", "pairs", "pme_spread", "pme_fft_fwd", "pme_conv", "pme_fft_inv", "pme_gather",
+             "excl_14", "bonded", "eval_out", "uv_energy_fp64"]
+    assert list(st)[:11] == names and all(v > 0 for v in st.values())
+    assert ("pairs_full" in st) == (precision == lfe.LFE_FP32_MIXED)
+    t1, F1 = g.eval(0.4)
+    assert np.array_equal(F0, F1) and t1["U"] == t0["U"] and t1["dUdl"] == t0["dUdl"]
