@@ -697,47 +697,85 @@ __global__ void k_conv(PmeView<real> p, long long* E, const LamState* lam)
 }
 
 // ----------------------------------------------------------------- gather
+// Forces from the potential grid: four lanes per atom, as in the spread.
+// Lane d < 3 forms the B-spline weights and derivatives of dimension d
+// (lane 3 repeats dimension 2) and shares them by shuffles; lane j0 then
+// reads the 16 points of plane j0 of the atom's 4 x 4 x 4 stencil, and the
+// four partial gradients are added by two butterfly steps.  Four times the
+// warps of one lane per atom, each with a quarter of the dependent grid
+// reads.
 template <typename real>
 __global__ void k_gather(SysView<real> s, PmeView<real> p)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= s.n) return;
-    const real q = s.q[a];
-    if (q == (real)0) return;
-    const bool u = s.sol[a] != 0;
-    const R4<real> xq = s.x[a];
-    real th[3][4], dth[3][4];
-    int f[3];
-    real xs[3] = {xq.x, xq.y, xq.z};
-    for (int d = 0; d < 3; ++d) {
-        real w;
-        grid_coord(xs[d], p.kscale64[d], p.K[d], f[d], w);
-        bspline4(w, th[d], dth[d]);
+    const unsigned FULL = 0xffffffffu;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = tid >> 2, sub = tid & 3;
+    const int lb = (threadIdx.x & 31) & ~3;
+    const bool live = a < s.n;
+    real q = 0;
+    bool u = false;
+    R4<real> xq;
+    xq.x = xq.y = xq.z = xq.w = (real)0;
+    if (live) {
+        q = s.q[a];
+        xq = s.x[a];
+        u = s.sol[a] != 0;
     }
+    real th[4], dth[4];
+    int f;
+    {
+        const int d = sub < 3 ? sub : 2;
+        const real x = d == 0 ? xq.x : (d == 1 ? xq.y : xq.z);
+        real w;
+        grid_coord(x, p.kscale64[d], p.K[d], f, w);
+        bspline4(w, th, dth);
+    }
+    real t0[4], d0[4], t1[4], d1[4], t2[4], d2[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        t0[k] = __shfl_sync(FULL, th[k], lb);
+        d0[k] = __shfl_sync(FULL, dth[k], lb);
+        t1[k] = __shfl_sync(FULL, th[k], lb + 1);
+        d1[k] = __shfl_sync(FULL, dth[k], lb + 1);
+        t2[k] = __shfl_sync(FULL, th[k], lb + 2);
+        d2[k] = __shfl_sync(FULL, dth[k], lb + 2);
+    }
+    const int f0 = __shfl_sync(FULL, f, lb), f1 = __shfl_sync(FULL, f, lb + 1), f2 = __shfl_sync(FULL, f, lb + 2);
     real gx = 0, gy = 0, gz = 0;
-    for (int j0 = 0; j0 < 4; ++j0) {
-        const int k0 = wrapk(f[0] - j0, p.K[0]);
+    if (live && q != (real)0) {
+        const real t0j = sub == 0 ? t0[0] : (sub == 1 ? t0[1] : (sub == 2 ? t0[2] : t0[3]));
+        const real d0j = sub == 0 ? d0[0] : (sub == 1 ? d0[1] : (sub == 2 ? d0[2] : d0[3]));
+        const int k0 = wrapk(f0 - sub, p.K[0]);
+#pragma unroll
         for (int j1 = 0; j1 < 4; ++j1) {
-            const int k1 = wrapk(f[1] - j1, p.K[1]);
+            const int k1 = wrapk(f1 - j1, p.K[1]);
             const int row = (k0 * p.K[1] + k1) * p.K[2];
-            real sx = 0, sy = 0, sz = 0;
+            real sx = 0, sz = 0;
+#pragma unroll
             for (int j2 = 0; j2 < 4; ++j2) {
-                const int k2 = wrapk(f[2] - j2, p.K[2]);
+                const int k2 = wrapk(f2 - j2, p.K[2]);
                 const R2<real> w = p.Z[row + k2];
                 const real phi = u ? w.y : w.x;
-                sx += th[2][j2] * phi;
-                sz += dth[2][j2] * phi;
+                sx += t2[j2] * phi;
+                sz += d2[j2] * phi;
             }
-            gx += dth[0][j0] * th[1][j1] * sx;
-            gy += th[0][j0] * dth[1][j1] * sx;
-            gz += th[0][j0] * th[1][j1] * sz;
-            (void)sy;
+            gx += d0j * t1[j1] * sx;
+            gy += t0j * d1[j1] * sx;
+            gz += t0j * t1[j1] * sz;
         }
     }
-    const real fx = -q * p.kscale[0] * gx, fy = -q * p.kscale[1] * gy, fz = -q * p.kscale[2] * gz;
-    atomic_add_ll(&s.Fa[a], to_fixed(fx, FSCALE));
-    atomic_add_ll(&s.Fa[s.n + a], to_fixed(fy, FSCALE));
-    atomic_add_ll(&s.Fa[2 * s.n + a], to_fixed(fz, FSCALE));
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        gx += __shfl_xor_sync(FULL, gx, o);
+        gy += __shfl_xor_sync(FULL, gy, o);
+        gz += __shfl_xor_sync(FULL, gz, o);
+    }
+    if (sub == 0 && live && q != (real)0) {
+        const real fx = -q * p.kscale[0] * gx, fy = -q * p.kscale[1] * gy, fz = -q * p.kscale[2] * gz;
+        atomic_add_ll(&s.Fa[a], to_fixed(fx, FSCALE));
+        atomic_add_ll(&s.Fa[s.n + a], to_fixed(fy, FSCALE));
+        atomic_add_ll(&s.Fa[2 * s.n + a], to_fixed(fz, FSCALE));
+    }
 }
 
 template <typename real>
@@ -756,7 +794,7 @@ void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int 
 template <typename real>
 void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st)
 {
-    k_gather<real><<<(s.n + 127) / 128, 128, 0, st>>>(s, p);
+    k_gather<real><<<(4 * s.n + 127) / 128, 128, 0, st>>>(s, p);
 }
 
 // energy64 (FP32 systems): the energy branch in df64 (about 48 bits).  The

@@ -34,7 +34,9 @@ template <typename real, typename wreal>
 __device__ __forceinline__ void grid_coord(real x, double ks, int K, int& f, wreal& w)
 {
     double u = (double)x * ks;
-    u -= (double)K * floor(u / (double)K);
+    // wrapped into [0, K) by whole periods; the division is skipped for the
+    // usual coordinate already inside (the result is the same)
+    if (!(u >= 0.0 && u < (double)K)) u -= (double)K * floor(u / (double)K);
     if (!(u >= 0.0 && u < (double)K)) u = 0.0;
     const double fl = floor(u);
     f = min(max((int)fl, 0), K - 1);
