@@ -23,6 +23,32 @@ namespace lfe {
 // and products in FP64: the fixed-point grid is shared by the force branch
 // and the df64 energy branch, whose class energies set dU/dlambda to 1e-6
 // relative.
+// round-to-nearest-even of x to int64 (saturating beyond 2^63, NaN to 0),
+// the result of __double2ll_rn, with integer operations only: x = m 2^sh
+// with the 53-bit significand m, shifted into place and rounded on the bits
+// shifted out.  The spread's conversions then stay off the FP64 pipe, which
+// its products keep busy.
+__device__ __forceinline__ long long d2ll_rn_int(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ffull);
+    const unsigned long long frac = b & 0xfffffffffffffull;
+    const unsigned long long m = frac | 0x10000000000000ull;
+    const int sh = e - 1075;
+    unsigned long long mag;
+    if (sh >= 0) {
+        mag = sh > 10 ? 0x7fffffffffffffffull : (m << sh);
+    } else if (sh < -53 || e == 0) {
+        mag = 0ull;
+    } else {
+        const int r = -sh;
+        const unsigned long long q = m >> r, rem = m & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+        mag = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    }
+    if (e == 2047 && frac) mag = 0ull;
+    return (b >> 63) ? -(long long)mag : (long long)mag;
+}
+
 template <typename real>
 __global__ void k_spread(SysView<real> s, PmeView<real> p)
 {
@@ -60,7 +86,9 @@ __global__ void k_spread(SysView<real> s, PmeView<real> p)
     long long* grid = p.Qfix + (s.sol[a] ? p.KK : 0);
     const double th0 = sub == 0 ? t0[0] : (sub == 1 ? t0[1] : (sub == 2 ? t0[2] : t0[3]));
     const int k0 = wrapk(f0 - sub, p.K[0]);
-    const double a0 = (double)q * th0;
+    // the grid scale is a power of two: applied first, it changes no bit
+    // of the products
+    const double a0 = (double)q * th0 * QSCALE;
 #pragma unroll
     for (int j1 = 0; j1 < 4; ++j1) {
         const int k1 = wrapk(f1 - j1, p.K[1]);
@@ -69,7 +97,7 @@ __global__ void k_spread(SysView<real> s, PmeView<real> p)
 #pragma unroll
         for (int j2 = 0; j2 < 4; ++j2) {
             const int k2 = wrapk(f2 - j2, p.K[2]);
-            atomic_add_ll(&grid[row + k2], __double2ll_rn(a1 * t2[j2] * QSCALE));
+            atomic_add_ll(&grid[row + k2], d2ll_rn_int(a1 * t2[j2]));
         }
     }
 }
