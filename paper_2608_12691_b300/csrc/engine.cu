@@ -181,7 +181,7 @@ struct System final : SystemBase {
     cudaStream_t cs = nullptr, cs2 = nullptr;
     static constexpr int NBR = 5;
     cudaStream_t br[NBR] = {};   // capture branches
-    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_built = nullptr, ev_join[NBR] = {};
+    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_q = nullptr, ev_built = nullptr, ev_join[NBR] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* h_flags = nullptr;        // pinned
@@ -243,6 +243,7 @@ struct System final : SystemBase {
         }
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_z) cudaEventDestroy(ev_z);
+        if (ev_q) cudaEventDestroy(ev_q);
         if (ev_built) cudaEventDestroy(ev_built);
     }
 
@@ -555,6 +556,7 @@ struct System final : SystemBase {
                 M2.phi_u = nullptr;
                 M2.Zraw64 = nullptr;
                 M2.Zin64 = M64.Z;
+                M2.Qfix = M.Qfix;   // read directly by the captured step (FFT_FROM_FIX_KEEP)
             }
             const int Kmax = std::max(M.K[0], std::max(M.K[1], M.K[2]));
             if (fft_smem<real>(Kmax) > 48 * 1024 || (dual && fft_smem<double>(Kmax) > 48 * 1024))
@@ -734,6 +736,7 @@ struct System final : SystemBase {
         }
         CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_z, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_q, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_built, cudaEventDisableTiming));
         build_neighbors(nullptr);
         CK(cudaStreamSynchronize(nullptr));
@@ -1110,9 +1113,15 @@ struct System final : SystemBase {
         CK(cudaEventRecord(ev_built, br[0]));
         if (pre) launch_prestep(S, G, *pre, br[3]);
         launch_pairs(S, N, pair_warps, br[0]);
+        // with both layouts in planes, the energy branch reads the
+        // fixed-point charge grids itself as soon as the spread is done,
+        // beside the FP32 plane pass (no FP64 copy); the grids are cleared
+        // once both passes have read them
+        const bool early = dual && M.planes && M2.planes;
         launch_spread(S, M, br[1]);
         if (M.planes) {
-            launch_planes(M, PLANE_FWD_FIX, br[1]);
+            if (early) CK(cudaEventRecord(ev_q, br[1]));
+            launch_planes(M, early ? PLANE_FWD_KEEP : PLANE_FWD_FIX, br[1]);
             CK(cudaEventRecord(ev_z, br[1]));
             launch_columns(M, S.E, S.lam, dual ? CONV_POTENTIAL : CONV_BOTH, br[1]);
             launch_planes(M, PLANE_INV, br[1]);
@@ -1128,14 +1137,22 @@ struct System final : SystemBase {
         }
         launch_gather(S, M, br[1]);
         if (dual) {
-            CK(cudaStreamWaitEvent(br[2], ev_z, 0));
-            if (M2.planes) {
-                // per-axis passes of 4-line blocks for the axes 2 and 1 (many
-                // small blocks beside the other branches), then the column pass
+            if (early) {
+                // per-axis passes for the axes 2 and 1 (many small blocks
+                // beside the other branches), then the column pass
+                CK(cudaStreamWaitEvent(br[2], ev_q, 0));
+                launch_fft(M2, 2, +1, FFT_FROM_FIX_KEEP, br[2]);
+                CK(cudaStreamWaitEvent(br[2], ev_z, 0));
+                CK(cudaMemsetAsync(M.Qfix, 0, sizeof(long long) * 2 * (size_t)M.KK, br[2]));
+                launch_fft(M2, 1, +1, 0, br[2]);
+                launch_columns(M2, S.E, S.lam, CONV_ENERGY, br[2]);
+            } else if (M2.planes) {
+                CK(cudaStreamWaitEvent(br[2], ev_z, 0));
                 launch_fft(M2, 2, +1, 0, br[2]);
                 launch_fft(M2, 1, +1, 0, br[2]);
                 launch_columns(M2, S.E, S.lam, CONV_ENERGY, br[2]);
             } else {
+                CK(cudaStreamWaitEvent(br[2], ev_z, 0));
                 launch_fft(M2, 2, +1, 0, br[2]);
                 launch_fft(M2, 1, +1, 0, br[2]);
                 launch_fft(M2, 0, +1, 0, br[2]);

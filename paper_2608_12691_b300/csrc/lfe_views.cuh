@@ -310,10 +310,17 @@ enum { CONV_BOTH = 0, CONV_ENERGY = 1, CONV_POTENTIAL = 2 };
 template <typename real> void launch_conv(const PmeView<real>& p, long long* E, const LamState* lam, int mode,
                                           cudaStream_t st);
 template <typename real> void launch_gather(const SysView<real>& s, const PmeView<real>& p, cudaStream_t st);
-// plane / column transform: PLANE_FWD_FIX reads the fixed-point grids (and
-// writes the FP64 copy when Zraw64 is set), PLANE_FWD transforms Z in place,
-// PLANE_INV is the inverse transform of axes 1 and 2
-enum { PLANE_FWD_FIX = 0, PLANE_FWD = 1, PLANE_INV = 2 };
+// plane / column transform: PLANE_FWD_FIX reads the fixed-point grids,
+// clears them and writes the FP64 copy when Zraw64 is set; PLANE_FWD_KEEP
+// reads them and leaves them (another pass reads them too; the grids are
+// cleared once both have); PLANE_FWD transforms Z in place, PLANE_INV is the
+// inverse transform of axes 1 and 2
+enum { PLANE_FWD_FIX = 0, PLANE_FWD = 1, PLANE_INV = 2, PLANE_FWD_KEEP = 3 };
+// axis-2 input of a per-axis pass (launch_fft from_fixed): FFT_FROM_Z the
+// transform grid (or the FP64 copy), FFT_FROM_FIX the fixed-point grids
+// (cleared, FP64 copy written), FFT_FROM_FIX_KEEP the fixed-point grids left
+// as they are
+enum { FFT_FROM_Z = 0, FFT_FROM_FIX = 1, FFT_FROM_FIX_KEEP = 2 };
 template <typename real> void launch_planes(const PmeView<real>& p, int mode, cudaStream_t st);
 // axis-0 transform of every column group with the convolution (mode as for
 // launch_conv); CONV_POTENTIAL and CONV_BOTH end with the inverse axis-0 transform

@@ -237,9 +237,10 @@ __device__ R2<real>* smem_fft(R2<real>* a, R2<real>* b, int nl, int K, int ls, i
 // (16 in FP32, 4 in FP64, whose scarce units want more blocks in flight)
 // lines, in shared memory, by the Stockham autosort formulation (radix 2, 3,
 // 4, 5 stages).  AXIS 2 lines are contiguous; AXIS 1 and 0 lines are loaded
-// as FFT_NL contiguous columns.  FROMFIX: the input is the pair of
-// fixed-point charge grids (consumed and zeroed here).
-template <typename real, int AXIS, bool FROMFIX, int FFT_NL>
+// as FFT_NL contiguous columns.  FROMFIX (FFT_FROM_FIX or
+// FFT_FROM_FIX_KEEP): the input is the pair of fixed-point charge grids,
+// consumed and zeroed here or left for another reader.
+template <typename real, int AXIS, int FROMFIX, int FFT_NL>
 __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -278,14 +279,16 @@ __global__ void __launch_bounds__(256) k_fft(PmeView<real> p, int sign)
         if (l < nl) {
             const int g = gidx(l, t);
             R2<real> v;
-            if (FROMFIX) {
+            if (FROMFIX != FFT_FROM_Z) {
                 const double qv = (double)p.Qfix[g] * (1.0 / QSCALE);
                 const double qu = (double)p.Qfix[p.KK + g] * ((double)p.qu_scale / QSCALE);
                 v.x = (real)qv;
                 v.y = (real)qu;
-                p.Qfix[g] = 0;
-                p.Qfix[p.KK + g] = 0;
-                if (p.Zraw64) {
+                if (FROMFIX == FFT_FROM_FIX) {
+                    p.Qfix[g] = 0;
+                    p.Qfix[p.KK + g] = 0;
+                }
+                if (FROMFIX == FFT_FROM_FIX && p.Zraw64) {
                     R2<double> w;
                     w.x = qv;
                     w.y = qu;
@@ -345,12 +348,14 @@ void launch_fft_nl(const PmeView<real>& p, int axis, int sign, int from_fixed, c
     if (axis == 2) blocks = (p.K[0] * p.K[1] + NL - 1) / NL;
     else blocks = p.K[axis == 1 ? 0 : 1] * ((p.K[2] + NL - 1) / NL);
     if (axis == 2) {
-        if (from_fixed) k_fft<real, 2, true, NL><<<blocks, threads, smem, st>>>(p, sign);
-        else k_fft<real, 2, false, NL><<<blocks, threads, smem, st>>>(p, sign);
+        if (from_fixed == FFT_FROM_FIX) k_fft<real, 2, FFT_FROM_FIX, NL><<<blocks, threads, smem, st>>>(p, sign);
+        else if (from_fixed == FFT_FROM_FIX_KEEP)
+            k_fft<real, 2, FFT_FROM_FIX_KEEP, NL><<<blocks, threads, smem, st>>>(p, sign);
+        else k_fft<real, 2, FFT_FROM_Z, NL><<<blocks, threads, smem, st>>>(p, sign);
     } else if (axis == 1) {
-        k_fft<real, 1, false, NL><<<blocks, threads, smem, st>>>(p, sign);
+        k_fft<real, 1, FFT_FROM_Z, NL><<<blocks, threads, smem, st>>>(p, sign);
     } else {
-        k_fft<real, 0, false, NL><<<blocks, threads, smem, st>>>(p, sign);
+        k_fft<real, 0, FFT_FROM_Z, NL><<<blocks, threads, smem, st>>>(p, sign);
     }
 }
 
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(PmeView<real> p)
         for (int u = 0; u < LOAD_BATCH; ++u) {
             const int e = e0 + u * PLANE_THREADS + threadIdx.x;
             if (e < KP) {
-                if (MODE == PLANE_FWD_FIX) {
+                if (MODE == PLANE_FWD_FIX || MODE == PLANE_FWD_KEEP) {
                     qa[u] = p.Qfix[base + e];
                     qb[u] = p.Qfix[p.KK + base + e];
                 } else {
@@ -430,14 +435,16 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(PmeView<real> p)
             const int k1 = e / K2, k2 = e - k1 * K2;
             const int g = base + e;
             R2<real> v;
-            if (MODE == PLANE_FWD_FIX) {
+            if (MODE == PLANE_FWD_FIX || MODE == PLANE_FWD_KEEP) {
                 const double qv = (double)qa[u] * (1.0 / QSCALE);
                 const double qu = (double)qb[u] * ((double)p.qu_scale / QSCALE);
                 v.x = (real)qv;
                 v.y = (real)qu;
-                p.Qfix[g] = 0;
-                p.Qfix[p.KK + g] = 0;
-                if (p.Zraw64) {
+                if (MODE == PLANE_FWD_FIX) {
+                    p.Qfix[g] = 0;
+                    p.Qfix[p.KK + g] = 0;
+                }
+                if (MODE == PLANE_FWD_FIX && p.Zraw64) {
                     R2<double> w;
                     w.x = qv;
                     w.y = qu;
@@ -623,6 +630,7 @@ void planes_setup(const PmeView<real>& p)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     allow_max_smem(k_plane<real, PLANE_FWD_FIX>, optin);
+    allow_max_smem(k_plane<real, PLANE_FWD_KEEP>, optin);
     allow_max_smem(k_plane<real, PLANE_FWD>, optin);
     allow_max_smem(k_plane<real, PLANE_INV>, optin);
     allow_max_smem(k_columns<real, CONV_ENERGY>, optin);
@@ -646,6 +654,7 @@ void launch_planes(const PmeView<real>& p, int mode, cudaStream_t st)
 {
     const size_t sm = planes_smem(p);
     if (mode == PLANE_FWD_FIX) k_plane<real, PLANE_FWD_FIX><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
+    else if (mode == PLANE_FWD_KEEP) k_plane<real, PLANE_FWD_KEEP><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
     else if (mode == PLANE_FWD) k_plane<real, PLANE_FWD><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
     else k_plane<real, PLANE_INV><<<p.K[0], PLANE_THREADS, sm, st>>>(p);
 }
