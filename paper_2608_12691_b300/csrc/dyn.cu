@@ -894,8 +894,45 @@ void launch_prestep(const SysView<real>& s, const StepView<real>& g, const Theta
     k_theta_pre<real><<<1, 32, 0, st>>>(s, t);
 }
 
+// theta's step once dU/dlambda is known: it needs only the coupling
+// energies (solute-solvent pair, exclusion and 1-4, and reciprocal class
+// energies, and the soft basis), so in the captured step it runs as soon as
+// those are in, beside the force kernels that finish later.  One lane: FP64
+// on a pipe with a small fraction of the FP32 rate, one dependent chain.
+// The lambda state is not touched here (the force kernels still read it).
 template <typename real>
-__global__ void k_theta(SysView<real> s, ThetaView<real> t)
+__device__ __forceinline__ void theta_step_body(const SysView<real>& s, const ThetaView<real>& t)
+{
+    if (s.flags[FL_ERROR] & ERRB_SKIP) return;   // step skipped (see k_integrate)
+    const LamState* L = s.lam;
+    const long long* E = s.E;
+    const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
+    const double Us = efix(E, E_PAIR_SOFT);
+    const bool sc = s.sc_alpha > 0.0;   // soft-core coupling: U_soft is the term at lambda
+    const double dUdl = L->dhA * Uuv + (sc ? efix(E, E_DSC) : L->dhB * Us);
+    double thn = L->theta, pn = L->p_theta, ven = L->v_eta;
+    if (t.m > 0.0) {
+        const double f = -L->dlam_dtheta * dUdl - t.pre->dV[0] - t.pre->dV[1];
+        ext_step(t.th, t.tc, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
+        thn -= 2.0 * floor(thn / 2.0);
+    }
+    t.pre->dUdl = dUdl;
+    t.pre->theta = thn;
+    t.pre->p_theta = pn;
+    t.pre->v_eta = ven;
+}
+
+template <typename real>
+__global__ void k_theta_step(SysView<real> s, ThetaView<real> t)
+{
+    if (threadIdx.x == 0) theta_step_body(s, t);
+}
+
+// the end of the step, once every kernel of it has run: U, the TI bin of
+// Eq. 2, the new lambda state (Eq. 3) from k_theta_step's theta, OPES
+// deposits, the step counter, and the energy accumulators cleared
+template <typename real>
+__device__ __forceinline__ void theta_commit_body(const SysView<real>& s, const ThetaView<real>& t)
 {
     const int lane = threadIdx.x;
     LamState* L = s.lam;
@@ -904,9 +941,6 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         if (lane < E_N) E[lane] = 0;
         return;
     }
-    // the scalar work of the step is lane 0's (FP64 on a pipe with a small
-    // fraction of the FP32 rate, one dependent chain); the warp joins for an
-    // OPES deposit
     double thn = 0.0;
     unsigned long long stepn = 0;
     if (lane == 0) {
@@ -915,16 +949,10 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         const double Uuv = efix(E, E_PAIR_UV) + efix(E, E_EXCL_UV) + efix(E, E_14_UV) + efix(E, E_REC_UV) + t.const_uv;
         const double Us = efix(E, E_PAIR_SOFT);
         const double Ub = efix(E, E_BONDED);
-        const bool sc = s.sc_alpha > 0.0;   // soft-core coupling: U_soft is the term at lambda
-        const double dUdl = L->dhA * Uuv + (sc ? efix(E, E_DSC) : L->dhB * Us);
+        const bool sc = s.sc_alpha > 0.0;
         const double U = Uvv + Uuu + L->hA * Uuv + (sc ? Us : L->hB * Us) + Ub + efix(E, E_DAFED);
-        double pn = L->p_theta, ven = L->v_eta;
-        thn = L->theta;
-        if (t.m > 0.0) {
-            const double f = -L->dlam_dtheta * dUdl - t.pre->dV[0] - t.pre->dV[1];
-            ext_step(t.th, t.tc, t.m, t.kT, t.dt, t.a_fric, f, t.pre->noise, thn, pn, ven);
-            thn -= 2.0 * floor(thn / 2.0);
-        }
+        const double dUdl = t.pre->dUdl;
+        thn = t.pre->theta;
         stepn = L->step + 1;
         // Eq. 2: the mean force is accumulated in lambda bins (at the lambda
         // of this step's evaluation)
@@ -934,7 +962,7 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
         const double lam = thn <= 1.0 ? thn : 2.0 - thn;
         double hA, hB, dA, dB;
         switching_fns(lam, hA, hB, dA, dB);
-        L->theta = thn; L->p_theta = pn; L->v_eta = ven; L->lambda = lam;
+        L->theta = thn; L->p_theta = t.pre->p_theta; L->v_eta = t.pre->v_eta; L->lambda = lam;
         L->dlam_dtheta = thn <= 1.0 ? 1.0 : -1.0;
         L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
         L->dUdl = dUdl; L->U = U; L->V_std = t.pre->V[0]; L->V_exp = t.pre->V[1];
@@ -959,6 +987,21 @@ __global__ void k_theta(SysView<real> s, ThetaView<real> t)
     // every energy accumulator has been read: clear them for the next step
     __syncwarp();
     if (lane < E_N) E[lane] = 0;
+}
+
+template <typename real>
+__global__ void k_theta_commit(SysView<real> s, ThetaView<real> t)
+{
+    theta_commit_body(s, t);
+}
+
+// both in one launch (one warp), where nothing runs beside them
+template <typename real>
+__global__ void k_theta(SysView<real> s, ThetaView<real> t)
+{
+    if (threadIdx.x == 0) theta_step_body(s, t);
+    __syncwarp();
+    theta_commit_body(s, t);
 }
 
 // Lambda replica exchange on the device (the paper's HREX protocol, Section
@@ -1041,6 +1084,18 @@ void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, c
 }
 
 template <typename real>
+void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
+{
+    k_theta_step<real><<<1, 32, 0, st>>>(s, t);
+}
+
+template <typename real>
+void launch_theta_commit(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
+{
+    k_theta_commit<real><<<1, 32, 0, st>>>(s, t);
+}
+
+template <typename real>
 void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
 {
     k_theta<real><<<1, 32, 0, st>>>(s, t);
@@ -1059,6 +1114,8 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
     template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
     template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \
+    template void launch_theta_step<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);    \
+    template void launch_theta_commit<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);  \
     template void launch_prestep<real>(const SysView<real>&, const StepView<real>&, const ThetaView<real>&,  \
                                        cudaStream_t);                                                       \
     template void launch_dafed_force<real>(const SysView<real>&, const DafedView&, cudaStream_t);            \

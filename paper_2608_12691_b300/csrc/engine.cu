@@ -181,7 +181,8 @@ struct System final : SystemBase {
     cudaStream_t cs = nullptr, cs2 = nullptr;
     static constexpr int NBR = 5;
     cudaStream_t br[NBR] = {};   // capture branches
-    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_q = nullptr, ev_built = nullptr, ev_join[NBR] = {};
+    cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_q = nullptr, ev_ex = nullptr, ev_rec = nullptr, ev_built = nullptr,
+                ev_join[NBR] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* h_flags = nullptr;        // pinned
@@ -244,6 +245,8 @@ struct System final : SystemBase {
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_z) cudaEventDestroy(ev_z);
         if (ev_q) cudaEventDestroy(ev_q);
+        if (ev_ex) cudaEventDestroy(ev_ex);
+        if (ev_rec) cudaEventDestroy(ev_rec);
         if (ev_built) cudaEventDestroy(ev_built);
     }
 
@@ -737,6 +740,8 @@ struct System final : SystemBase {
         CK(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_z, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_q, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_ex, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_rec, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_built, cudaEventDisableTiming));
         build_neighbors(nullptr);
         CK(cudaStreamSynchronize(nullptr));
@@ -1159,11 +1164,24 @@ struct System final : SystemBase {
                 launch_conv(M2, S.E, S.lam, CONV_ENERGY, br[2]);
             }
         }
+        // with the regulated thermostat, theta's step (a chain of FP64
+        // transcendentals) is taken as soon as dU/dlambda is known
+        const bool theta_early = pre && pre->th.kind == 1;
         launch_excl(S, X, br[3]);
+        if (theta_early) CK(cudaEventRecord(ev_ex, br[3]));
         launch_bonded(S, B, br[3]);
         launch_dafed_force(S, D, br[3]);
         CK(cudaStreamWaitEvent(br[4], ev_built, 0));
         launch_uv_energy(S, N, uv_blocks, br[4]);
+        if (theta_early) {
+            // theta's step needs dU/dlambda only: the solute-solvent, the
+            // exclusion and 1-4 and the reciprocal class energies; it runs as
+            // soon as they are in (the step's end commits it)
+            CK(cudaEventRecord(ev_rec, dual ? br[2] : br[1]));
+            CK(cudaStreamWaitEvent(br[4], ev_ex, 0));
+            CK(cudaStreamWaitEvent(br[4], ev_rec, 0));
+            launch_theta_step(S, *pre, br[4]);
+        }
         for (int k = 0; k < NBR; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
             CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
@@ -1715,13 +1733,16 @@ struct System final : SystemBase {
         recover_overflow(st);
     }
 
-    // the end of a captured step: atoms, theta and the auxiliary angles move
+    // the end of a captured step (after eval_kernels_branched with theta's
+    // view, which has taken theta's step under the regulated thermostat):
+    // atoms, theta (its commit, or its whole step) and the auxiliary angles
     // concurrently (three branches); the step ends when all are done
     void record_ext_steps(cudaStream_t s0)
     {
         CK(cudaEventRecord(ev_fork, s0));
         CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
-        launch_theta(S, T, br[0]);
+        if (T.th.kind == 1) launch_theta_commit(S, T, br[0]);
+        else launch_theta(S, T, br[0]);
         CK(cudaEventRecord(ev_join[0], br[0]));
         if (D.n) {
             CK(cudaStreamWaitEvent(br[1], ev_fork, 0));

@@ -224,6 +224,9 @@ struct ThetaPre {
     double V[2], dV[2];        // both OPES biases and their theta-derivatives at theta
     double noise;              // the theta integrator's standard normal
     unsigned long long step;   // the step counter at the start of the step
+    // formed by k_theta_step once dU/dlambda is known, taken over by
+    // k_theta_commit at the end of the step
+    double dUdl, theta, p_theta, v_eta;
 };
 
 template <typename real>
@@ -333,7 +336,14 @@ template <typename real> void planes_setup(const PmeView<real>& p);
 template <typename real> void energy_columns_setup(const PmeView<real>& p);
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
 template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
+// theta's step: k_theta_step (dU/dlambda and the new theta, momentum and
+// thermostat velocity, kept in ThetaPre) then k_theta_commit (U, the TI bin,
+// the lambda state, OPES deposits, the step counter, clearing the energy
+// accumulators); launch_theta runs both as one launch
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+template <typename real> void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+template <typename real> void launch_theta_commit(const SysView<real>& s, const ThetaView<real>& t,
+                                                  cudaStream_t st);
 // d-AFED: forces of Eq. 15 on the atoms and the auxiliary variables (with
 // the coupling energy), and the auxiliary variables' step
 template <typename real> void launch_dafed_force(const SysView<real>& s, const DafedView& d, cudaStream_t st);
