@@ -362,6 +362,7 @@ struct TileShared {
     int wsum[32];
     int r0;                        // staging slots reserved by the round
     int cnt[27];                   // tiles per shift
+    float4 ia[8];                  // the sub-cluster's atoms at the build (padding: far away)
 };
 
 // one (I8, shift) search by the whole block; returns the number of tiles
@@ -437,6 +438,19 @@ __device__ int tile_search(const SysView<real>& s, const NblView<real>& nb, int 
                             d2 += g * g;
                         }
                         keep = d2 < nb.cut2;
+                        // within the list cut of the box: kept only when within
+                        // it of one of the sub-cluster's atoms (a pair in range
+                        // before the next rebuild is within the cut now)
+                        if (keep) {
+                            float m = 3.0e38f;
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const float4 q = sm.ia[k];
+                                const float dx = pv[0] - q.x, dy = pv[1] - q.y, dz = pv[2] - q.z;
+                                m = fminf(m, dx * dx + dy * dy + dz * dz);
+                            }
+                            keep = m < nb.cut2;
+                        }
                     }
                     const unsigned kbu = __ballot_sync(0xffffffffu, keep);
                     if (lane == 0) sm.kb[c] = kbu;
@@ -525,6 +539,14 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblV
     }
     const unsigned allow = __ballot_sync(0xffffffffu, ok);   // the same in every warp
     if (tid < 27) sm.cnt[tid] = 0;
+    if (tid < 8) {
+        const int slot = I8 * 8 + tid;
+        const bool real_atom = live && slot < s.n_pad && s.perm[slot] >= 0;
+        const R4<real> q = real_atom ? s.xq[slot] : R4<real>{0, 0, 0, 0};
+        sm.ia[tid] = real_atom ? make_float4((float)q.x, (float)q.y, (float)q.z, 1.f)
+                               : make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
+    }
+    __syncthreads();
     for (unsigned m = allow; m; m &= m - 1u) {
         const int sh = __ffs(m) - 1;
         const int count = tile_search(s, nb, I8, sh, sm);
