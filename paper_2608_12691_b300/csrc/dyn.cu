@@ -753,7 +753,7 @@ __global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real
         }
         return;
     }
-    // the kicks were drawn by k_noise; the counter is not read here (k_theta
+    // the kicks were drawn by k_prestep; the counter is not read here (k_theta
     // advances it concurrently)
     const unsigned long long step = 0ull;
     if (G.kind == GROUP_WATER) integrate_group<real, GROUP_WATER, 3>(s, g, G, step);
@@ -773,7 +773,7 @@ void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStrea
 // sqrt(k_B T (1 - a^2) / m) R with R from Philox4x32-10 at counter
 // (atom, step) and Box-Muller; 0 for frozen atoms
 template <typename real>
-__global__ void k_noise(SysView<real> s, StepView<real> g)
+__device__ __forceinline__ void noise_body(const SysView<real>& s, const StepView<real>& g)
 {
     const int atom = blockIdx.x * blockDim.x + threadIdx.x;
     if (atom >= s.n) return;
@@ -869,7 +869,7 @@ __device__ void opes_deposit(const ThetaView<real>& t, int b, double th, double 
 // OPES biases at the current theta and the theta integrator's normal (one
 // warp); they depend only on the state at the start of the step
 template <typename real>
-__global__ void k_theta_pre(SysView<real> s, ThetaView<real> t)
+__device__ __forceinline__ void theta_pre_body(const SysView<real>& s, const ThetaView<real>& t)
 {
     const LamState* L = s.lam;
     const double th = L->theta;
@@ -887,11 +887,23 @@ __global__ void k_theta_pre(SysView<real> s, ThetaView<real> t)
     }
 }
 
+// the step's force-independent parts in one launch: blocks 0 .. nb-1 draw
+// the atoms' kicks, the last block's first warp forms both OPES biases and
+// theta's normal
+template <typename real>
+__global__ void k_prestep(SysView<real> s, StepView<real> g, ThetaView<real> t)
+{
+    if (blockIdx.x == gridDim.x - 1) {
+        if (threadIdx.x < 32) theta_pre_body(s, t);
+        return;
+    }
+    noise_body(s, g);
+}
+
 template <typename real>
 void launch_prestep(const SysView<real>& s, const StepView<real>& g, const ThetaView<real>& t, cudaStream_t st)
 {
-    k_noise<real><<<(s.n + 127) / 128, 128, 0, st>>>(s, g);
-    k_theta_pre<real><<<1, 32, 0, st>>>(s, t);
+    k_prestep<real><<<(s.n + 127) / 128 + 1, 128, 0, st>>>(s, g, t);
 }
 
 // theta's step once dU/dlambda is known: it needs only the coupling
