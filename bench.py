@@ -513,8 +513,10 @@ def run_ours(args):
     # kernels of one captured step (FP32 systems): rebuild decision, pair
     # kernel; spread, plane transform, column pass, inverse plane transform,
     # gather; df64 energy branch (two transform passes, column pass); kicks
-    # and OPES bias, exclusions/1-4, bonded, FP64 uv energies; integrator,
-    # theta (which also ends the step).  A neighbour-list build adds 11 kernels (column keys,
+    # with the OPES biases (one launch), exclusions/1-4, bonded, FP64 uv
+    # energies, theta's step (the regulated thermostat's, once dU/dlambda is
+    # in); integrator, theta's commit (which also ends the step); the FP64
+    # form has no df64 branch.  A neighbour-list build adds 11 kernels (column keys,
     # column scan, scatter, column sort, slot assignment, tile search, tile
     # scan, placement + masks, uv pair count, scan, write).
     per_step = 17 if prec == lfe.LFE_FP32_MIXED else 14
