@@ -1409,9 +1409,12 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
         const double r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 < rc2)) continue;
         const int a = s.perm[pr.x], b = s.perm[pr.y];
-        const double r = sqrt(r2);
+        // one reciprocal square root serves r, 1/r and 1/r^2 (every FP64
+        // division on this per-pair chain is a long dependent sequence)
+        const double rinv = rsqrt(r2);
+        const double r = r2 * rinv, rinv2 = rinv * rinv;
         const double qq = KE * (double)s.q[a] * (double)s.q[b];
-        double e = qq * erfc(alpha * r) / r;
+        double e = qq * erfc(alpha * r) * rinv;
         const double sg = 0.5 * ((double)s.sig[a] + (double)s.sig[b]);
         const double ep = sqrt((double)s.eps[a] * (double)s.eps[b]);
         if (ep > 0.0 && sc) {
@@ -1425,7 +1428,7 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
         } else if (ep > 0.0) {
             const double tt = fmax(0.0, (r - rsw) * swi);
             const double S = 1.0 - tt * tt * tt * (10.0 - 15.0 * tt + 6.0 * tt * tt);
-            const double s2 = sg * sg / r2, s6 = s2 * s2 * s2;
+            const double s2 = sg * sg * rinv2, s6 = s2 * s2 * s2;
             const double v = 4.0 * ep * (s6 * s6 - s6) * S;
             e += v;
             if (r < sg) {
