@@ -271,6 +271,17 @@ int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsi
 int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                 void* stream);
 
+/* lfe_step_io with the positions and velocities as floats: pos_in, pos_out
+ * and vel_out are float arrays [3N] in page-locked host memory (same
+ * ownership, checks, NULL meanings and errors as lfe_step_io); ext_out stays
+ * double [LFE_NEXT].  The input is widened exactly to the device coordinate
+ * type, so an FP32 system steps from the same bits as through lfe_step_io
+ * with the same floats widened to double; the outputs are the device state
+ * rounded to float (the device positions and velocities of an FP32 system
+ * are floats already).  Halves the bytes crossing the host link. */
+int lfe_step_io_f32(lfe_system* sys, const float* pos_in, float* pos_out, float* vel_out, double* ext_out,
+                    void* stream);
+
 /* d-AFED (Eq. 15): n_cv torsions xi_k (atoms[4k .. 4k+3], the IUPAC sign:
  * atan2(|b2| b1 . (b2 x b3), (b1 x b2) . (b2 x b3)) with b1 = r_j - r_i,
  * b2 = r_k - r_j, b3 = r_l - r_k, minimum images) are coupled to auxiliary

@@ -125,8 +125,8 @@ void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st)
 // refresh the cluster-sorted copy in the current slot order, and raise the
 // rebuild flag when an atom lies more than skin/2 from where the list was
 // built (a non-finite position raises it too)
-template <typename real>
-__global__ void k_assign_moved(SysView<real> s, const double* pos, real skin_half2)
+template <typename real, typename TIO>
+__global__ void k_assign_moved(SysView<real> s, const TIO* pos, real skin_half2)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (s.flags[FL_ERROR] & ERRB_BADPOS) return;   // refused by k_check_positions: nothing changes
@@ -149,27 +149,27 @@ __global__ void k_assign_moved(SysView<real> s, const double* pos, real skin_hal
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_REBUILD], 1);
 }
 
-template <typename real>
-void launch_assign_moved(const SysView<real>& s, const double* pos, real skin_half2, cudaStream_t st)
+template <typename real, typename TIO>
+void launch_assign_moved(const SysView<real>& s, const TIO* pos, real skin_half2, cudaStream_t st)
 {
-    k_assign_moved<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos, skin_half2);
+    k_assign_moved<real, TIO><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos, skin_half2);
 }
 
-// new positions (caller doubles) checked on the device before they are
-// assigned: any coordinate that is not finite raises ERRB_BADPOS, and the
-// step that follows leaves the state as it was
-template <typename real>
-__global__ void k_check_positions(SysView<real> s, const double* pos)
+// new positions (caller doubles or floats) checked on the device before
+// they are assigned: any coordinate that is not finite raises ERRB_BADPOS,
+// and the step that follows leaves the state as it was
+template <typename real, typename TIO>
+__global__ void k_check_positions(SysView<real> s, const TIO* pos)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const bool bad = i < 3 * s.n && !isfinite(pos[i]);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_ERROR], ERRB_BADPOS);
 }
 
-template <typename real>
-void launch_check_positions(const SysView<real>& s, const double* pos, cudaStream_t st)
+template <typename real, typename TIO>
+void launch_check_positions(const SysView<real>& s, const TIO* pos, cudaStream_t st)
 {
-    k_check_positions<real><<<(3 * s.n + 255) / 256, 256, 0, st>>>(s, pos);
+    k_check_positions<real, TIO><<<(3 * s.n + 255) / 256, 256, 0, st>>>(s, pos);
 }
 
 // Monte Carlo volume move (the NPT runs of Section 2.6): every molecule's
@@ -229,19 +229,18 @@ void launch_scale_molecules(const SysView<real>& s, const int* mstart, const int
 // buffer, so that lfe_get_state needs one copy: out[0, 3n) x, [3n, 6n) v,
 // then theta, p_theta, lambda, dU/dlambda, U, kernels of both biases, step,
 // rebuilds, the error bits, the tile count
-template <typename real>
-__global__ void k_pack_state(SysView<real> s, const OpesState* o, double* out)
+template <typename real, typename TIO>
+__global__ void k_pack_state(SysView<real> s, const OpesState* o, TIO* out, double* e)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a < s.n) {
         const R4<real> x = s.x[a], v = s.v[a];
-        out[3 * a] = x.x; out[3 * a + 1] = x.y; out[3 * a + 2] = x.z;
-        double* ov = out + 3 * (size_t)s.n;
-        ov[3 * a] = v.x; ov[3 * a + 1] = v.y; ov[3 * a + 2] = v.z;
+        out[3 * a] = (TIO)x.x; out[3 * a + 1] = (TIO)x.y; out[3 * a + 2] = (TIO)x.z;
+        TIO* ov = out + 3 * (size_t)s.n;
+        ov[3 * a] = (TIO)v.x; ov[3 * a + 1] = (TIO)v.y; ov[3 * a + 2] = (TIO)v.z;
     }
     if (a == 0) {
         const LamState* L = s.lam;
-        double* e = out + 6 * (size_t)s.n;
         e[0] = L->theta; e[1] = L->p_theta; e[2] = L->lambda; e[3] = L->dUdl; e[4] = L->U;
         e[5] = o->n[0]; e[6] = o->n[1]; e[7] = (double)L->step;
         e[8] = s.flags[FL_NREBUILD]; e[9] = s.flags[FL_NTILES]; e[10] = s.flags[FL_ERROR];
@@ -251,7 +250,15 @@ __global__ void k_pack_state(SysView<real> s, const OpesState* o, double* out)
 template <typename real>
 void launch_pack_state(const SysView<real>& s, const OpesState* o, double* out, cudaStream_t st)
 {
-    k_pack_state<real><<<(s.n + 255) / 256, 256, 0, st>>>(s, o, out);
+    k_pack_state<real, double><<<(s.n + 255) / 256, 256, 0, st>>>(s, o, out, out + 6 * (size_t)s.n);
+}
+
+// the same with positions and velocities as floats (xv [6n]) and the scalar
+// state (tail [16]) in FP64
+template <typename real>
+void launch_pack_state_f32(const SysView<real>& s, const OpesState* o, float* xv, double* tail, cudaStream_t st)
+{
+    k_pack_state<real, float><<<(s.n + 255) / 256, 256, 0, st>>>(s, o, xv, tail);
 }
 
 // Dihedral of atoms (i, j, k, l) from r_ij = x_i - x_j, r_kj = x_k - x_j,
@@ -1117,8 +1124,12 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_set_lambda<real>(const SysView<real>&, double, cudaStream_t);                    \
     template void launch_eval_out<real>(const SysView<real>&, double*, double*, double, double, double,   \
                                         cudaStream_t);                                                    \
-    template void launch_assign_moved<real>(const SysView<real>&, const double*, real, cudaStream_t);       \
-    template void launch_check_positions<real>(const SysView<real>&, const double*, cudaStream_t);         \
+    template void launch_assign_moved<real, double>(const SysView<real>&, const double*, real, cudaStream_t); \
+    template void launch_assign_moved<real, float>(const SysView<real>&, const float*, real, cudaStream_t);   \
+    template void launch_check_positions<real, double>(const SysView<real>&, const double*, cudaStream_t);   \
+    template void launch_check_positions<real, float>(const SysView<real>&, const float*, cudaStream_t);     \
+    template void launch_pack_state_f32<real>(const SysView<real>&, const OpesState*, float*, double*,      \
+                                              cudaStream_t);                                                 \
     template void launch_refresh_sorted<real>(const SysView<real>&, cudaStream_t);                         \
     template void launch_pack_state<real>(const SysView<real>&, const OpesState*, double*, cudaStream_t);   \
     template void launch_scale_molecules<real>(const SysView<real>&, const int*, const int*, const double*, int, \

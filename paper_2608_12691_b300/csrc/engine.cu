@@ -61,6 +61,18 @@ void philox_host(unsigned c[4], unsigned k0, unsigned k1)
 // exponent bits are all ones, and then adding 1 to the exponent field carries
 // into the sign bit; integer AND/ADD/OR only, so the loop vectorises and runs
 // at memory speed (positions just written by a device copy are read from DRAM)
+bool finite_all(const float* a, size_t n)
+{
+    const uint32_t E = 0x7f800000u, ONE = 0x00800000u;
+    uint32_t acc = 0;
+    for (size_t i = 0; i < n; ++i) {
+        uint32_t b;
+        std::memcpy(&b, a + i, sizeof b);
+        acc |= (b & E) + ONE;
+    }
+    return (acc >> 31) == 0;
+}
+
 bool finite_all(const double* a, size_t n)
 {
     const uint64_t E = 0x7ff0000000000000ull, ONE = 0x0010000000000000ull;
@@ -146,6 +158,8 @@ struct SystemBase {
     virtual void set_list_capacity(int tiles) = 0;
     virtual void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                          cudaStream_t st) = 0;
+    virtual void step_io_f32(const float* pos_in, float* pos_out, float* vel_out, double* ext_out,
+                             cudaStream_t st) = 0;
     virtual void lambda_state(double* lam, double* mass) = 0;
     virtual bool soft_core() const = 0;
     virtual void mc_volume_move(double pressure_bar, double dv_max, unsigned long long seed,
@@ -1792,11 +1806,26 @@ struct System final : SystemBase {
         return a.type == cudaMemoryTypeHost;
     }
 
-    void capture_io_graph(const double* pos_in, double* pos_out, double* vel_out)
+    // the host element type of the graph (8: double, 4: float) is part of its key
+    template <typename TIO>
+    void capture_io_graph(const TIO* pos_in, TIO* pos_out, TIO* vel_out)
     {
         if (io_exec) { cudaGraphExecDestroy(io_exec); io_exec = nullptr; }
         if (io_graph) { cudaGraphDestroy(io_graph); io_graph = nullptr; }
         const size_t nv = 3 * (size_t)n;
+        constexpr bool F32 = sizeof(TIO) == 4;
+        // device staging: the input positions, then the packed positions and
+        // velocities (the doubles' staging is the state-packing buffer)
+        TIO* d_in;
+        TIO* d_xv;
+        if constexpr (F32) {
+            d_in = d_io32;
+            d_xv = d_io32 + nv;
+        } else {
+            d_in = d_pos;
+            d_xv = d_state;
+        }
+        double* d_tail = d_state + 6 * (size_t)n;
         cudaStream_t s0 = cs;
         CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
         cudaStreamCaptureStatus status;
@@ -1805,31 +1834,51 @@ struct System final : SystemBase {
         if (pos_in) {
             // the step's own conditional rebuild (first branch below) acts
             // on the flag that the new positions raise
-            CK(cudaMemcpyAsync(d_pos, pos_in, sizeof(double) * nv, cudaMemcpyHostToDevice, s0));
-            launch_check_positions(S, d_pos, s0);
-            launch_assign_moved(S, d_pos, G.skin_half2, s0);
+            CK(cudaMemcpyAsync(d_in, pos_in, sizeof(TIO) * nv, cudaMemcpyHostToDevice, s0));
+            launch_check_positions(S, (const TIO*)d_in, s0);
+            launch_assign_moved(S, (const TIO*)d_in, G.skin_half2, s0);
         }
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         eval_kernels_branched(s0, &T, &h);
         record_ext_steps(s0);
-        launch_pack_state(S, T.st, d_state, s0);
-        CK(cudaMemcpyAsync(h_io_tail, d_state + 2 * nv, sizeof(double) * 16, cudaMemcpyDeviceToHost, s0));
-        if (pos_out) CK(cudaMemcpyAsync(pos_out, d_state, sizeof(double) * nv, cudaMemcpyDeviceToHost, s0));
-        if (vel_out) CK(cudaMemcpyAsync(vel_out, d_state + nv, sizeof(double) * nv, cudaMemcpyDeviceToHost, s0));
+        if constexpr (F32)
+            launch_pack_state_f32(S, T.st, d_xv, d_tail, s0);
+        else
+            launch_pack_state(S, T.st, d_state, s0);
+        CK(cudaMemcpyAsync(h_io_tail, d_tail, sizeof(double) * 16, cudaMemcpyDeviceToHost, s0));
+        if (pos_out) CK(cudaMemcpyAsync(pos_out, d_xv, sizeof(TIO) * nv, cudaMemcpyDeviceToHost, s0));
+        if (vel_out) CK(cudaMemcpyAsync(vel_out, d_xv + nv, sizeof(TIO) * nv, cudaMemcpyDeviceToHost, s0));
         CK(cudaStreamEndCapture(s0, &io_graph));
         CK(cudaGraphInstantiate(&io_exec, io_graph, cudaGraphInstantiateFlagUseNodePriority));
         io_key[0] = pos_in;
         io_key[1] = pos_out;
         io_key[2] = vel_out;
+        io_key[3] = (const void*)sizeof(TIO);
         io_gen = generation;
     }
 
-    void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out, cudaStream_t st) override
+    float* d_io32 = nullptr;   // [9n] float staging of lfe_step_io_f32
+
+    // the state as floats (positions and velocities) for the float variant's
+    // rare general paths
+    void get_state_f32(float* pos, float* vel, double* ext)
     {
+        const size_t nv = 3 * (size_t)n;
+        std::vector<double> p(pos ? nv : 0), v(vel ? nv : 0);
+        get_state(pos ? p.data() : nullptr, vel ? v.data() : nullptr, ext);
+        for (size_t i = 0; i < p.size(); ++i) pos[i] = (float)p[i];
+        for (size_t i = 0; i < v.size(); ++i) vel[i] = (float)v[i];
+    }
+
+    template <typename TIO>
+    void step_io_t(const TIO* pos_in, TIO* pos_out, TIO* vel_out, double* ext_out, cudaStream_t st)
+    {
+        constexpr bool F32 = sizeof(TIO) == 4;
+        const char* who = F32 ? "lfe_step_io_f32" : "lfe_step_io";
         if (!(P.dt > 0)) fail(LFE_ERR_STATE, "dt must be positive to step");
         if (!host_pinned(pos_in) || !host_pinned(pos_out) || !host_pinned(vel_out))
-            fail(LFE_ERR_ARG, "host buffers of lfe_step_io must be page-locked");
+            fail(LFE_ERR_ARG, std::string("host buffers of ") + who + " must be page-locked");
         if (eager || pos_pending || since_check > 0) {
             // a queued overflow or pending position update is settled first
             CK(cudaStreamSynchronize(st));
@@ -1837,19 +1886,34 @@ struct System final : SystemBase {
             if (pos_pending) settle_positions(st);
             pos_pending = false;
         }
+        auto state_out = [&] {
+            if constexpr (F32)
+                get_state_f32(pos_out, vel_out, ext_out);
+            else
+                get_state(pos_out, vel_out, ext_out);
+        };
         if (eager) {
             if (pos_in && !finite_all(pos_in, 3 * (size_t)n)) fail(LFE_ERR_ARG, "non-finite position");
-            if (pos_in) set_positions(pos_in, 0, st);
+            if (pos_in) {
+                if constexpr (F32) {
+                    const std::vector<double> p(pos_in, pos_in + 3 * (size_t)n);
+                    set_positions(p.data(), 0, st);
+                } else {
+                    set_positions(pos_in, 0, st);
+                }
+            }
             step(1, st);
-            get_state(pos_out, vel_out, ext_out);
+            state_out();
             return;
         }
         if (!d_state) {
             d_state = dalloc<double>(6 * (size_t)n + 16);
             CK(cudaMallocHost(&h_state, sizeof(double) * (6 * (size_t)n + 16)));
         }
+        if (F32 && !d_io32) d_io32 = dalloc<float>(9 * (size_t)n);
         if (!h_io_tail) CK(cudaMallocHost(&h_io_tail, sizeof(double) * 16));
-        if (!io_exec || io_gen != generation || io_key[0] != pos_in || io_key[1] != pos_out || io_key[2] != vel_out)
+        if (!io_exec || io_gen != generation || io_key[0] != pos_in || io_key[1] != pos_out ||
+            io_key[2] != vel_out || io_key[3] != (const void*)sizeof(TIO))
             capture_io_graph(pos_in, pos_out, vel_out);
         CK(cudaGraphLaunch(io_exec, st));
         ++steps_requested;
@@ -1870,11 +1934,22 @@ struct System final : SystemBase {
                 if (!exec) capture_step_graph();
                 recover_overflow(st);
             }
-            get_state(pos_out, vel_out, ext_out);
+            state_out();
             return;
         }
         if (ext_out)
             for (int k = 0; k < LFE_NEXT; ++k) ext_out[k] = h_io_tail[k];
+    }
+
+    void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out, cudaStream_t st) override
+    {
+        step_io_t(pos_in, pos_out, vel_out, ext_out, st);
+    }
+
+    void step_io_f32(const float* pos_in, float* pos_out, float* vel_out, double* ext_out,
+                     cudaStream_t st) override
+    {
+        step_io_t(pos_in, pos_out, vel_out, ext_out, st);
     }
 
     // steps requested through lfe_step since creation, and launches since
@@ -2914,6 +2989,12 @@ int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsi
 {
     return guard(sys, [&] { sys->impl->mc_volume_move(pressure_bar, dv_max, seed, attempt, accepted, box_out,
                                                        energies); });
+}
+
+int lfe_step_io_f32(lfe_system* sys, const float* pos_in, float* pos_out, float* vel_out, double* ext_out,
+                    void* stream)
+{
+    return guard(sys, [&] { sys->impl->step_io_f32(pos_in, pos_out, vel_out, ext_out, (cudaStream_t)stream); });
 }
 
 int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* vel_out, double* ext_out,

@@ -365,15 +365,18 @@ template <typename real> void launch_eval_out(const SysView<real>& s, double* fo
 // new positions from caller doubles: master and sorted copies, and the
 // rebuild flag raised when an atom has moved more than skin/2 since the last
 // build (the rebuild itself follows launch_rebuild_cond's conditional node)
-template <typename real> void launch_assign_moved(const SysView<real>& s, const double* pos, real skin_half2,
-                                                  cudaStream_t st);
-template <typename real> void launch_check_positions(const SysView<real>& s, const double* pos, cudaStream_t st);
+template <typename real, typename TIO> void launch_assign_moved(const SysView<real>& s, const TIO* pos,
+                                                                real skin_half2, cudaStream_t st);
+template <typename real, typename TIO> void launch_check_positions(const SysView<real>& s, const TIO* pos,
+                                                                   cudaStream_t st);
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);
 template <typename real> void launch_scale_molecules(const SysView<real>& s, const int* mstart, const int* matoms,
                                                      const double* mass, int n_mol, double sc, const double* L,
                                                      cudaStream_t st);
 template <typename real> void launch_pack_state(const SysView<real>& s, const OpesState* o, double* out,
                                                 cudaStream_t st);
+template <typename real> void launch_pack_state_f32(const SysView<real>& s, const OpesState* o, float* xv,
+                                                    double* tail, cudaStream_t st);
 // phi: FP64 grid of the class potentials (phi_v real, phi_u imaginary)
 template <typename real> void launch_param_grad(const SysView<real>& s, const NblView<real>& nb,
                                                 const ExclView<real>& ex, const PmeView<real>& pm,

@@ -102,3 +102,43 @@ def test_refused_positions_leave_the_trajectory_as_it_was():
         assert torch.equal(pa, pb) and torch.equal(va, vb)
         assert np.array_equal(ea, eb)
     assert eb[7] == 12
+
+
+@pytest.mark.parametrize("precision,capacity", [(lfe.LFE_FP32_MIXED, None), (lfe.LFE_FP32_MIXED, 8),
+                                                (lfe.LFE_FP64, None)])
+def test_float_host_buffers_step_as_the_doubles(precision, capacity):
+    # lfe_step_io_f32 fed the same floats as lfe_step_io gets widened to
+    # double: the same trajectory, outputs equal to the doubles rounded to
+    # float (exactly the doubles for an FP32 system, whose state is float)
+    import torch
+    d = water_system()
+    n = len(d["charge"])
+    a = lfe.System(d, precision=precision, seed=SEED)
+    b = lfe.System(d, precision=precision, seed=SEED)
+    if capacity:
+        a.set_list_capacity(capacity)
+        b.set_list_capacity(capacity)
+    pa, va = pinned((n, 3)), pinned((n, 3))
+    pin32 = torch.zeros((n, 3), dtype=torch.float32).pin_memory()
+    pb, vb = (torch.zeros((n, 3), dtype=torch.float32).pin_memory() for _ in range(2))
+    ea, eb = np.zeros(lfe.NEXT), np.zeros(lfe.NEXT)
+    pin32.copy_(torch.from_numpy(np.asarray(d["pos"], dtype=np.float32)))
+    for k in range(25):
+        pa.copy_(pin32.double())
+        feed = k % 5 != 4          # every fifth step keeps the device positions
+        a.step_io(pa.data_ptr() if feed else None, pa.data_ptr(), va.data_ptr(), ea.ctypes.data)
+        b.step_io_f32(pin32.data_ptr() if feed else None, pb.data_ptr(), vb.data_ptr(), eb.ctypes.data)
+        assert torch.equal(pb, pa.float()) and torch.equal(vb, va.float())
+        if precision == lfe.LFE_FP32_MIXED:
+            assert torch.equal(pb.double(), pa) and torch.equal(vb.double(), va)
+        assert np.array_equal(ea, eb)
+        pin32.copy_(pb)
+    assert eb[7] == 25
+    # refusals as for the doubles
+    pin32[3, 1] = float("inf")
+    with pytest.raises(lfe.LfeError) as e:
+        b.step_io_f32(pin32.data_ptr(), pb.data_ptr(), None, None)
+    assert e.value.code == lfe.LFE_ERR_ARG
+    assert b.get_state()[2]["step"] == 25
+    with pytest.raises(lfe.LfeError):
+        b.step_io_f32(np.zeros(3 * n, dtype=np.float32).ctypes.data, None, None, None)
