@@ -196,7 +196,7 @@ struct System final : SystemBase {
     static constexpr int NBR = 5;
     cudaStream_t br[NBR] = {};   // capture branches
     cudaEvent_t ev_fork = nullptr, ev_z = nullptr, ev_q = nullptr, ev_ex = nullptr, ev_rec = nullptr, ev_built = nullptr,
-                ev_join[NBR] = {};
+                ev_uv = nullptr, ev_join[NBR] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int* h_flags = nullptr;        // pinned
@@ -262,6 +262,7 @@ struct System final : SystemBase {
         if (ev_ex) cudaEventDestroy(ev_ex);
         if (ev_rec) cudaEventDestroy(ev_rec);
         if (ev_built) cudaEventDestroy(ev_built);
+        if (ev_uv) cudaEventDestroy(ev_uv);
     }
 
     void create(const lfe_params& p, const lfe_topology& t)
@@ -757,6 +758,7 @@ struct System final : SystemBase {
         CK(cudaEventCreateWithFlags(&ev_ex, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_rec, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ev_built, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ev_uv, cudaEventDisableTiming));
         build_neighbors(nullptr);
         CK(cudaStreamSynchronize(nullptr));
         {
@@ -1118,8 +1120,13 @@ struct System final : SystemBase {
     // step's conditional rebuild of the neighbour list: only the pair kernel
     // and the solute-solvent energies read the list and the cluster-sorted
     // copy, so the PME, exclusion and bonded work runs beside the rebuild.
+    // join = false (the step graphs): the branches are left open, each with
+    // its end recorded in ev_join[k] and the end of the solute-solvent energy
+    // kernel (the last reader of the positions outside branches 0, 1 and 3)
+    // in ev_uv; record_ext_steps continues them
     void eval_kernels_branched(cudaStream_t s0, const ThetaView<real>* pre = nullptr,
-                               const cudaGraphConditionalHandle* rebuild = nullptr, bool build_first = false)
+                               const cudaGraphConditionalHandle* rebuild = nullptr, bool build_first = false,
+                               bool join = true)
     {
         CK(cudaEventRecord(ev_fork, s0));
         for (int k = 0; k < NBR; ++k) CK(cudaStreamWaitEvent(br[k], ev_fork, 0));
@@ -1187,6 +1194,7 @@ struct System final : SystemBase {
         launch_dafed_force(S, D, br[3]);
         CK(cudaStreamWaitEvent(br[4], ev_built, 0));
         launch_uv_energy(S, N, uv_blocks, br[4]);
+        CK(cudaEventRecord(ev_uv, br[4]));
         if (theta_early) {
             // theta's step needs dU/dlambda only: the solute-solvent, the
             // exclusion and 1-4 and the reciprocal class energies; it runs as
@@ -1198,7 +1206,7 @@ struct System final : SystemBase {
         }
         for (int k = 0; k < NBR; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
-            CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
+            if (join) CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
         }
     }
 
@@ -1747,25 +1755,42 @@ struct System final : SystemBase {
         recover_overflow(st);
     }
 
-    // the end of a captured step (after eval_kernels_branched with theta's
-    // view, which has taken theta's step under the regulated thermostat):
-    // atoms, theta (its commit, or its whole step) and the auxiliary angles
-    // concurrently (three branches); the step ends when all are done
+    // the end of a captured step, continuing the open branches of
+    // eval_kernels_branched (theta's view given; under the regulated
+    // thermostat theta's step has been taken on branch 4):
+    //  - the atoms' integrator on branch 3 once the forces are complete
+    //    (pairs on branch 0, reciprocal gather on 1, exclusions, bonded and
+    //    d-AFED forces on 3) and the last other reader of the positions (the
+    //    solute-solvent energies on 4) is done; it does not wait for the
+    //    df64 energy branch or theta's step;
+    //  - theta's commit (or its whole step) on branch 4 once every reader of
+    //    the lambda state in branches 0-3 is done (it does not wait for the
+    //    integrator, which reads no lambda state);
+    //  - the auxiliary angles' step on branch 1 once their forces (branch 3)
+    //    are in.
+    // The step ends when all three are done.
     void record_ext_steps(cudaStream_t s0)
     {
-        CK(cudaEventRecord(ev_fork, s0));
-        CK(cudaStreamWaitEvent(br[0], ev_fork, 0));
-        if (T.th.kind == 1) launch_theta_commit(S, T, br[0]);
-        else launch_theta(S, T, br[0]);
-        CK(cudaEventRecord(ev_join[0], br[0]));
+        CK(cudaStreamWaitEvent(br[4], ev_join[0], 0));
+        CK(cudaStreamWaitEvent(br[4], ev_join[1], 0));
+        CK(cudaStreamWaitEvent(br[4], ev_join[2], 0));
+        CK(cudaStreamWaitEvent(br[4], ev_join[3], 0));
+        if (T.th.kind == 1) launch_theta_commit(S, T, br[4]);
+        else launch_theta(S, T, br[4]);
+        CK(cudaEventRecord(ev_join[4], br[4]));
+        // (the waits below read the branch ends recorded by the evaluation:
+        // each ev_join is recorded again only after its last reader)
+        CK(cudaStreamWaitEvent(br[3], ev_join[0], 0));
+        CK(cudaStreamWaitEvent(br[3], ev_join[1], 0));
+        CK(cudaStreamWaitEvent(br[3], ev_uv, 0));
+        launch_integrate(S, G, br[3]);
         if (D.n) {
-            CK(cudaStreamWaitEvent(br[1], ev_fork, 0));
+            CK(cudaStreamWaitEvent(br[1], ev_join[3], 0));
             launch_dafed_step(S, D, br[1]);
-            CK(cudaEventRecord(ev_join[1], br[1]));
         }
-        launch_integrate(S, G, s0);
-        CK(cudaStreamWaitEvent(s0, ev_join[0], 0));
-        if (D.n) CK(cudaStreamWaitEvent(s0, ev_join[1], 0));
+        CK(cudaEventRecord(ev_join[1], br[1]));
+        CK(cudaEventRecord(ev_join[3], br[3]));
+        for (int k = 0; k < NBR; ++k) CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
     }
 
     void capture_step_graph()
@@ -1777,7 +1802,7 @@ struct System final : SystemBase {
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        eval_kernels_branched(s0, &T, &h);
+        eval_kernels_branched(s0, &T, &h, false, false);
         record_ext_steps(s0);
         CK(cudaStreamEndCapture(s0, &graph));
         CK(cudaGraphInstantiate(&exec, graph, cudaGraphInstantiateFlagUseNodePriority));
@@ -1840,7 +1865,7 @@ struct System final : SystemBase {
         }
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        eval_kernels_branched(s0, &T, &h);
+        eval_kernels_branched(s0, &T, &h, false, false);
         record_ext_steps(s0);
         if constexpr (F32)
             launch_pack_state_f32(S, T.st, d_xv, d_tail, s0);

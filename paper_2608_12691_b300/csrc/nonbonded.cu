@@ -960,6 +960,30 @@ __device__ __forceinline__ void flush_i8(const SysView<real>& s, int I8, real (&
 // scalar code (the packed operations are per component fmaf/fmul/fadd in
 // round-to-nearest); the special-function operations (rsqrt, reciprocal,
 // exp2) run once per half.
+// The special-function unit's approximations (PTX rsqrt/rcp/ex2 .approx)
+// in their flush-to-zero form: no subnormal handling around them.  For any
+// pair within the cutoff the arguments and results are far from the
+// subnormal range (r^2 of two atoms, 1 + 0.345 x >= 1, 2^y with y > -126
+// while alpha r_c < 9), so the results are those of the non-flushing forms,
+// with fewer instructions per pair.
+__device__ __forceinline__ float rsq_ftz(float a)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float rcp_ftz(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ float ex2_ftz(float a)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ float2 p2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -969,16 +993,20 @@ __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y
 // pair_force for two pairs: (r2, qq, sigma_ij, 4 eps_ij) per half; returns g
 // per half (force on i = -g d, on j = +g d) and the energy ec + v per half.
 // Solvent-solvent and solute-solute classes only (the solute-solvent tiles
-// take the scalar routine with the soft basis).
+// take the scalar routine with the soft basis).  exp(-x^2) is 2^(-x^2 log2 e).
+// The switching variable is clamped to [0, 1] (a saturating fma; for a pair
+// within the cutoff it lies in [0, 1) already), so a half evaluated at
+// r^2 = 1e30 (a pair out of range) gives exactly zero force and energy:
+// erfc and the Gaussian underflow to 0, (sigma/r)^6 to 0, and S(1) = 0.
 __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, float2 e4, const PairConst<float>& c,
                                               float2& e)
 {
-    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv = make_float2(rsq_ftz(r2.x), rsq_ftz(r2.y));
     const float2 r = mul2(r2, rinv);
     const float2 ri2 = mul2(rinv, rinv);
     const float2 x = mul2(p2(c.alpha), r);
     const float2 den = fma2(p2(0.345f), x, p2(1.0f));
-    const float2 t = make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y));
+    const float2 t = make_float2(rcp_ftz(den.x), rcp_ftz(den.y));
     float2 pp = p2(-0.23825677533960984f);
     pp = fma2(pp, t, p2(1.0079999846654213f));
     pp = fma2(pp, t, p2(-1.1369167351186891f));
@@ -987,8 +1015,8 @@ __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, f
     pp = fma2(pp, t, p2(0.33999728300708898f));
     pp = fma2(pp, t, p2(0.17020566942397877f));
     pp = fma2(pp, t, p2(0.0017784231330017291f));
-    const float2 xx = mul2(x, x);
-    const float2 ex = make_float2(__expf(-xx.x), __expf(-xx.y));
+    const float2 xx = mul2(mul2(x, x), p2(-1.4426950408889634f));
+    const float2 ex = make_float2(ex2_ftz(xx.x), ex2_ftz(xx.y));
     const float2 erfcv = mul2(pp, ex);
     const float2 ec = mul2(mul2(qq, erfcv), rinv);
     const float2 fc = mul2(fma2(mul2(qq, p2(c.tas)), ex, ec), ri2);
@@ -996,8 +1024,7 @@ __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, f
     const float2 s6 = mul2(mul2(s2, s2), s2);
     float2 v = mul2(e4, fma2(s6, s6, neg2(s6)));
     float2 fl = mul2(mul2(e4, mul2(s6, fma2(s6, p2(12.0f), p2(-6.0f)))), ri2);
-    const float2 rr = fma2(r, p2(c.swi), p2(-c.rsw_swi));
-    const float2 tt = make_float2(fmaxf(0.0f, rr.x), fmaxf(0.0f, rr.y));
+    const float2 tt = make_float2(__saturatef(fmaf(r.x, c.swi, -c.rsw_swi)), __saturatef(fmaf(r.y, c.swi, -c.rsw_swi)));
     const float2 tt2 = mul2(tt, tt);
     const float2 inner = fma2(fma2(tt, p2(6.0f), p2(-15.0f)), tt, p2(10.0f));
     const float2 S = fma2(neg2(mul2(tt2, tt)), inner, p2(1.0f));
@@ -1124,15 +1151,15 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
                     const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
                     const bool in0 = ((mc >> kk) & 1u) && r2.x < c.rc2;
                     const bool in1 = ((mc >> (kk + 4)) & 1u) && r2.y < c.rc2;
-                    if (in0 || in1) {
-                        // a half out of range is evaluated at r^2 = 1 and weighted by 0
+                    if (__any_sync(0xffffffffu, in0 || in1)) {
+                        // a half out of range is evaluated at r^2 = 1e30, where
+                        // pair_force2 returns exact zeros (a warp-uniform branch:
+                        // lanes with no pair in range take part with zeros)
                         const float4 C = sh.sC[wl][kk];
-                        const float2 rs = make_float2(in0 ? r2.x : 1.0f, in1 ? r2.y : 1.0f);
-                        const float2 m = make_float2(in0 ? 1.0f : 0.0f, in1 ? 1.0f : 0.0f);
+                        const float2 rs = make_float2(in0 ? r2.x : 1e30f, in1 ? r2.y : 1e30f);
                         float2 e;
                         float2 g = pair_force2(rs, mul2(make_float2(B.z, B.w), qj), add2(make_float2(C.x, C.y), sgj),
                                                mul2(make_float2(C.z, C.w), ej), c, e);
-                        g = mul2(g, m);
                         const float2 gx = mul2(g, dx), gy = mul2(g, dy), gz = mul2(g, dz);
                         fi[3 * kk][lane] = add2(fi[3 * kk][lane], neg2(gx));
                         fi[3 * kk + 1][lane] = add2(fi[3 * kk + 1][lane], neg2(gy));
@@ -1140,7 +1167,7 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
                         fj2x = add2(fj2x, gx);
                         fj2y = add2(fj2y, gy);
                         fj2z = add2(fj2z, gz);
-                        e2 = fma2(e, m, e2);
+                        e2 = add2(e, e2);
                         acc.npairs += (in0 ? 1 : 0) + (in1 ? 1 : 0);
                     }
                 }
