@@ -75,6 +75,9 @@ def parse():
     p.add_argument("--batch-steps", type=int, default=40)
     p.add_argument("--profile-case", action="store_true",
                    help="build the workload, run 3 staged evaluations and exit (a small case for ncu)")
+    p.add_argument("--prune", type=float, default=None,
+                   help="inner buffer (nm) of the pruned pair list (lfe_set_list_prune) for the profile case")
+    p.add_argument("--skin", type=float, default=None, help="list buffer (nm) of the profile case")
     a = p.parse_args()
     ref = a.impl == "reference"
     if a.steps is None:
@@ -653,7 +656,9 @@ def run_profile_case(args):
     torch.cuda.set_device(0)
     d, _ = make_workload(args.workload, 0)
     prec = lfe.LFE_FP64 if args.precision == "fp64" else lfe.LFE_FP32_MIXED
-    g = lfe.System(d, precision=prec)
+    g = lfe.System(d, precision=prec, **({"skin": args.skin} if args.skin else {}))
+    if args.prune:
+        g.set_list_prune(args.prune)
     stages = g.time_stages(d["lam"], reps=3)
     _, _, ext = g.get_state()
     print(json.dumps({"profile_case": args.workload, "stages_ms": stages, "tiles": int(ext["n_tiles"])}))

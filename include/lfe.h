@@ -221,9 +221,12 @@ int lfe_step(lfe_system* sys, int n_steps, void* stream);
  * NULL) receives LFE_NEXT doubles: [theta, p_theta, lambda, dU/dlambda, U,
  * n_kernels_std, n_kernels_exp, step, neighbour rebuilds done by lfe_step
  * (and by evaluations that found a rebuild left pending by the last step),
- * tiles of the current neighbour list (8 i atoms x 32 j atoms each)].
+ * tiles of the current neighbour list (8 i atoms x 32 j atoms each), pairs
+ * within r_cut counted by the last step's pair kernel, tiles of the pruned
+ * list (lfe_set_list_prune; 0 before the first pruning), prunings done by
+ * lfe_step].
  * Synchronises the device and reports errors raised by queued steps. */
-#define LFE_NEXT 10
+#define LFE_NEXT 13
 int lfe_get_state(lfe_system* sys, double* pos, double* vel, double* ext);
 
 /* Monte Carlo volume move (Section 2.6: the runs are isothermal-isobaric
@@ -270,6 +273,21 @@ int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsi
  * `stream`. */
 int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                 void* stream);
+
+/* Dynamic pruning of the neighbour list (a buffered pair list pruned
+ * between rebuilds): with an inner buffer 0 < b < the list buffer (skin),
+ * the pair kernel of lfe_step works on a list cut from the built one, which
+ * keeps a j entry of a tile when it lies within r_cut + b of one of the
+ * tile's i atoms whose pair with it is computed; the cut is made in the
+ * step graph (a conditional node after the conditional rebuild) after every
+ * rebuild and whenever an atom has moved more than b/2 since the last cut,
+ * so every pair within r_cut is still evaluated and the results equal those
+ * of the full list up to the order of FP32 partial sums.  The list buffer
+ * then only sets how often the list is rebuilt.  b = 0 (the default), or b
+ * not below the list buffer, switches it off.  lfe_eval, the batched
+ * replicas and eager stepping always use the built list.  Recaptures the
+ * step graphs.  Errors: LFE_ERR_ARG (b < 0 or not finite). */
+int lfe_set_list_prune(lfe_system* sys, double inner_buffer);
 
 /* lfe_step_io with the positions and velocities as floats: pos_in, pos_out
  * and vel_out are float arrays [3N] in page-locked host memory (same
@@ -363,7 +381,9 @@ int lfe_restore(lfe_system* sys, const char* path);
  * lambda, timed with CUDA events on `stream`: list build, pair kernel (the
  * step's launch shape), PME stages, exclusions, bonded terms, output, FP64
  * solute-solvent energies and, for FP32 systems, "pairs_full" (the pair
- * kernel once more with a grid that fills every multiprocessor).  names/ms
+ * kernel once more with a grid that fills every multiprocessor); with
+ * pruning on (lfe_set_list_prune), "prune" (cutting the pruned list from
+ * the built one) and "pairs_pruned" (the pair kernel on it).  names/ms
  * arrays of length max_n; returns the number of stages written (>= 0) or an
  * error code. */
 int lfe_time_stages(lfe_system* sys, double lambda, int reps, void* stream,

@@ -126,11 +126,11 @@ void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st)
 // rebuild flag when an atom lies more than skin/2 from where the list was
 // built (a non-finite position raises it too)
 template <typename real, typename TIO>
-__global__ void k_assign_moved(SysView<real> s, const TIO* pos, real skin_half2)
+__global__ void k_assign_moved(SysView<real> s, const TIO* pos, real skin_half2, real prune_half2)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (s.flags[FL_ERROR] & ERRB_BADPOS) return;   // refused by k_check_positions: nothing changes
-    bool far = false;
+    bool far = false, pfar = false;
     if (a < s.n) {
         const int slot = s.iperm[a];
         const R4<real> x{(real)pos[3 * a], (real)pos[3 * a + 1], (real)pos[3 * a + 2], (real)0};
@@ -145,14 +145,25 @@ __global__ void k_assign_moved(SysView<real> s, const TIO* pos, real skin_half2)
         const real dy = minimg(x.y - xr.y, s.L[1], s.invL[1]);
         const real dz = minimg(x.z - xr.z, s.L[2], s.invL[2]);
         far = !(dx * dx + dy * dy + dz * dz <= skin_half2);
+        if (prune_half2 > (real)0) {
+            const R4<real> xp = s.xpr[a];
+            const real ex = minimg(x.x - xp.x, s.L[0], s.invL[0]);
+            const real ey = minimg(x.y - xp.y, s.L[1], s.invL[1]);
+            const real ez = minimg(x.z - xp.z, s.L[2], s.invL[2]);
+            pfar = !(ex * ex + ey * ey + ez * ez <= prune_half2);
+        }
     }
-    if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&s.flags[FL_REBUILD], 1);
+    const bool any_far = __any_sync(0xffffffffu, far), any_pfar = __any_sync(0xffffffffu, pfar);
+    if ((threadIdx.x & 31) == 0) {
+        if (any_far) atomicOr(&s.flags[FL_REBUILD], 1);
+        if (any_pfar) atomicOr(&s.flags[FL_PRUNE], 1);
+    }
 }
 
 template <typename real, typename TIO>
-void launch_assign_moved(const SysView<real>& s, const TIO* pos, real skin_half2, cudaStream_t st)
+void launch_assign_moved(const SysView<real>& s, const TIO* pos, real skin_half2, real prune_half2, cudaStream_t st)
 {
-    k_assign_moved<real, TIO><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos, skin_half2);
+    k_assign_moved<real, TIO><<<(s.n + 255) / 256, 256, 0, st>>>(s, pos, skin_half2, prune_half2);
 }
 
 // new positions (caller doubles or floats) checked on the device before
@@ -243,7 +254,8 @@ __global__ void k_pack_state(SysView<real> s, const OpesState* o, TIO* out, doub
         const LamState* L = s.lam;
         e[0] = L->theta; e[1] = L->p_theta; e[2] = L->lambda; e[3] = L->dUdl; e[4] = L->U;
         e[5] = o->n[0]; e[6] = o->n[1]; e[7] = (double)L->step;
-        e[8] = s.flags[FL_NREBUILD]; e[9] = s.flags[FL_NTILES]; e[10] = s.flags[FL_ERROR];
+        e[8] = s.flags[FL_NREBUILD]; e[9] = s.flags[FL_NTILES]; e[10] = L->npairs; e[11] = s.flags[FL_PTILES];
+        e[12] = s.flags[FL_NPRUNE]; e[13] = s.flags[FL_ERROR];
     }
 }
 
@@ -572,7 +584,7 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
     // clear the forces would otherwise order the next atom's loads after
     // them), in two dependent rounds: indices and per-atom records, then the
     // slot-indexed forces and sorted records
-    R4<real> xa4[NA], va4[NA], xr4[NA], xq4[NA];
+    R4<real> xa4[NA], va4[NA], xr4[NA], xq4[NA], xp4[NA];
     real kick[NA][3];
     long long fl[NA][3], fla[NA][3];
 #pragma unroll
@@ -582,6 +594,7 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
         xa4[a] = s.x[atom];
         va4[a] = s.v[atom];
         xr4[a] = s.xref[atom];
+        xp4[a] = g.prune_half2 > (real)0 ? s.xpr[atom] : R4<real>{0, 0, 0, 0};
         w[a] = s.invm[atom];
 #pragma unroll
         for (int d = 0; d < 3; ++d) kick[a][d] = g.noise[3 * atom + d];
@@ -699,7 +712,7 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
 #pragma unroll
     for (int d = 0; d < 3; ++d) shift[d] = -s.L[d] * floor((o0[d] + p[0][d]) * s.invL[d]);
     const real inv_dt = (real)1 / g.dt;
-    bool rebuild = false, bad = false;
+    bool rebuild = false, bad = false, prune = false;
 #pragma unroll
     for (int a = 0; a < NA; ++a) {
         const int atom = G.atom[a];
@@ -733,12 +746,21 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
         const real dy = minimg(xnew.y - xr.y, s.L[1], s.invL[1]);
         const real dz = minimg(xnew.z - xr.z, s.L[2], s.invL[2]);
         if (dx * dx + dy * dy + dz * dz > g.skin_half2) rebuild = true;
+        if (g.prune_half2 > (real)0) {
+            const R4<real> xp = xp4[a];
+            const real ex = minimg(xnew.x - xp.x, s.L[0], s.invL[0]);
+            const real ey = minimg(xnew.y - xp.y, s.L[1], s.invL[1]);
+            const real ez = minimg(xnew.z - xp.z, s.L[2], s.invL[2]);
+            if (ex * ex + ey * ey + ez * ez > g.prune_half2) prune = true;
+        }
     }
     // one atomic per warp (thousands of groups cross the skin at once)
     const unsigned act = __activemask();
     const bool any_rebuild = __any_sync(act, rebuild), any_bad = __any_sync(act, bad);
+    const bool any_prune = __any_sync(act, prune);
     if ((threadIdx.x & 31) == __ffs(act) - 1) {
         if (any_rebuild && !s.flags[FL_REBUILD]) atomicOr(&s.flags[FL_REBUILD], 1);
+        if (any_prune && !s.flags[FL_PRUNE]) atomicOr(&s.flags[FL_PRUNE], 1);
         if (any_bad) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
     }
 }
@@ -985,6 +1007,7 @@ __device__ __forceinline__ void theta_commit_body(const SysView<real>& s, const 
         L->dlam_dtheta = thn <= 1.0 ? 1.0 : -1.0;
         L->hA = hA; L->hB = hB; L->dhA = dA; L->dhB = dB;
         L->dUdl = dUdl; L->U = U; L->V_std = t.pre->V[0]; L->V_exp = t.pre->V[1];
+        L->npairs = (double)E[E_NPAIRS];
         if (!isfinite(U) || !isfinite(thn)) atomicOr(&s.flags[FL_ERROR], ERRB_NONFINITE);
         // the step ends here: its counter (the Philox counter of the atoms,
         // theta and the auxiliary angles) advances
@@ -1102,6 +1125,25 @@ void launch_rebuild_cond(const SysView<real>& s, cudaGraphConditionalHandle h, c
     k_rebuild_cond<real><<<1, 1, 0, st>>>(s, h);
 }
 
+// after the conditional rebuild: the pruned list is cut again when an atom
+// has moved more than half the inner buffer since the last pruning, or the
+// list was just built (the build raises FL_PRUNE); not after a skipped step
+template <typename real>
+__global__ void k_prune_cond(SysView<real> s, cudaGraphConditionalHandle h)
+{
+    const int err = s.flags[FL_ERROR];
+    const int pr = s.flags[FL_PRUNE] && !(err & ERRB_SKIP);
+    cudaGraphSetConditional(h, pr ? 1u : 0u);
+    if (pr) s.flags[FL_NPRUNE] += 1;
+    if (!(err & ERRB_SKIP)) s.flags[FL_PRUNE] = 0;
+}
+
+template <typename real>
+void launch_prune_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st)
+{
+    k_prune_cond<real><<<1, 1, 0, st>>>(s, h);
+}
+
 template <typename real>
 void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
 {
@@ -1124,8 +1166,11 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_set_lambda<real>(const SysView<real>&, double, cudaStream_t);                    \
     template void launch_eval_out<real>(const SysView<real>&, double*, double*, double, double, double,   \
                                         cudaStream_t);                                                    \
-    template void launch_assign_moved<real, double>(const SysView<real>&, const double*, real, cudaStream_t); \
-    template void launch_assign_moved<real, float>(const SysView<real>&, const float*, real, cudaStream_t);   \
+    template void launch_assign_moved<real, double>(const SysView<real>&, const double*, real, real,       \
+                                                     cudaStream_t);                                        \
+    template void launch_assign_moved<real, float>(const SysView<real>&, const float*, real, real,         \
+                                                    cudaStream_t);                                         \
+    template void launch_prune_cond<real>(const SysView<real>&, cudaGraphConditionalHandle, cudaStream_t);  \
     template void launch_check_positions<real, double>(const SysView<real>&, const double*, cudaStream_t);   \
     template void launch_check_positions<real, float>(const SysView<real>&, const float*, cudaStream_t);     \
     template void launch_pack_state_f32<real>(const SysView<real>&, const OpesState*, float*, double*,      \

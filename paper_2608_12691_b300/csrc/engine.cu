@@ -156,6 +156,7 @@ struct SystemBase {
     virtual void autotune(int reps, const char* cache_path, double* best_ms, int* params) = 0;
     virtual void set_theta(double theta, double p_theta) = 0;
     virtual void set_list_capacity(int tiles) = 0;
+    virtual void set_list_prune(double inner) = 0;
     virtual void step_io(const double* pos_in, double* pos_out, double* vel_out, double* ext_out,
                          cudaStream_t st) = 0;
     virtual void step_io_f32(const float* pos_in, float* pos_out, float* vel_out, double* ext_out,
@@ -179,6 +180,24 @@ struct System final : SystemBase {
     std::vector<void*> allocs;
     SysView<real> S{};
     NblView<real> N{};
+    // the pruned list (dynamic pruning between rebuilds, off unless an inner
+    // buffer below the list buffer is set): its arrays, sized like the built
+    // list's, and the pruning's work arrays
+    int4* pt_tiles = nullptr;
+    int* pt_jidx = nullptr;
+    unsigned char* pt_masks = nullptr;
+    PruneView PV{};
+    double prune_skin = 0.0;      // inner buffer (nm); 0 = no pruning
+    bool prune_on() const { return prune_skin > 0.0 && prune_skin < P.skin; }
+    NblView<real> pruned_view() const
+    {
+        NblView<real> v = N;
+        v.tiles = pt_tiles;
+        v.jidx = pt_jidx;
+        v.masks = pt_masks;
+        v.ntiles_flag = FL_PTILES;
+        return v;
+    }
     ExclView<real> X{};
     PmeView<real> M{};
     PmeView<double> M64{};      // FP32 systems: FP64 copy of the packed charge grid (and the adjoint's FP64 pass)
@@ -370,6 +389,8 @@ struct System final : SystemBase {
         S.x = upload(hx);
         S.v = upload(hv);
         S.xref = dalloc<R4<real>>(n);
+        S.xpr = dalloc<R4<real>>(n);
+        CK(cudaMemset(S.xpr, 0, sizeof(R4<real>) * n));
         S.invm = upload(hw);
         d_q = upload(hq);
         d_sig = upload(hs);
@@ -420,10 +441,19 @@ struct System final : SystemBase {
         N.tile_cnt = dalloc<int>(27 * 4 * (size_t)n_cl);
         N.tile_tot = dalloc<int>(4 * (size_t)n_cl);
         N.tile_off = dalloc<int>(4 * (size_t)n_cl + 1);
+        N.ntiles_flag = FL_NTILES;
+        PV.cnt = dalloc<int>(4 * (size_t)n_cl);
+        PV.off = dalloc<int>(4 * (size_t)n_cl + 1);
+        CK(cudaMemset(PV.cnt, 0, sizeof(int) * 4 * (size_t)n_cl));
         N.cap = 1024;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
         N.masks = dalloc<unsigned char>((size_t)N.cap * 32);
+        pt_tiles = dalloc<int4>(N.cap);
+        pt_jidx = dalloc<int>((size_t)N.cap * 32);
+        pt_masks = dalloc<unsigned char>((size_t)N.cap * 32);
+        PV.kb = dalloc<unsigned>(N.cap);
+        PV.base = dalloc<int>(N.cap);
         N.stage_cap = N.cap;
         N.stage_hdr = dalloc<int4>(N.stage_cap);
         N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
@@ -895,10 +925,20 @@ struct System final : SystemBase {
         dfree(N.masks);
         dfree(N.stage_hdr);
         dfree(N.stage_j);
+        dfree(pt_tiles);
+        dfree(pt_jidx);
+        dfree(pt_masks);
+        dfree(PV.kb);
+        dfree(PV.base);
         N.cap = need + 256;
         N.tiles = dalloc<int4>(N.cap);
         N.jidx = dalloc<int>((size_t)N.cap * 32);
         N.masks = dalloc<unsigned char>((size_t)N.cap * 32);
+        pt_tiles = dalloc<int4>(N.cap);
+        pt_jidx = dalloc<int>((size_t)N.cap * 32);
+        pt_masks = dalloc<unsigned char>((size_t)N.cap * 32);
+        PV.kb = dalloc<unsigned>(N.cap);
+        PV.base = dalloc<int>(N.cap);
         N.stage_cap = std::max(N.cap, need_stage + 256);
         N.stage_hdr = dalloc<int4>(N.stage_cap);
         N.stage_j = dalloc<int>((size_t)N.stage_cap * 32);
@@ -992,7 +1032,7 @@ struct System final : SystemBase {
         CK(cudaStreamGetCaptureInfo(s0, &status, nullptr, &g, nullptr, nullptr, nullptr));
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-        launch_assign_moved(S, d_pos, G.skin_half2, s0);
+        launch_assign_moved(S, d_pos, G.skin_half2, G.prune_half2, s0);
         launch_rebuild_cond(S, h, s0);
         add_cond_build(s0, h);
         CK(cudaStreamEndCapture(s0, &pos_graph));
@@ -1109,6 +1149,30 @@ struct System final : SystemBase {
         CK(cudaStreamEndCapture(cs2, &body_out));
     }
 
+    // Appends to the graph being captured on st a conditional node (handle h)
+    // whose body cuts the pruned list from the built one; st continues after it.
+    void add_cond_prune(cudaStream_t st, cudaGraphConditionalHandle h)
+    {
+        cudaStreamCaptureStatus status;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        CK(cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &ndeps));
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        launch_prune(S, N, pruned_view(), PV, cs2);
+        cudaGraph_t body_out = nullptr;
+        CK(cudaStreamEndCapture(cs2, &body_out));
+    }
+
     // The evaluation as five concurrent branches (used inside the captured
     // step graph and timed by the autotuner): pair kernel | FP32 PME chain |
     // df64 energy branch of the reciprocal sum (it starts once the first FP32
@@ -1138,7 +1202,19 @@ struct System final : SystemBase {
         }
         CK(cudaEventRecord(ev_built, br[0]));
         if (pre) launch_prestep(S, G, *pre, br[3]);
-        launch_pairs(S, N, pair_warps, br[0]);
+        // with pruning, the step's pair kernel runs on the pruned list, cut
+        // again (conditional node) when it is due
+        const bool pruned = rebuild && prune_on();
+        if (pruned) {
+            cudaStreamCaptureStatus status;
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamGetCaptureInfo(br[0], &status, nullptr, &g, nullptr, nullptr, nullptr));
+            cudaGraphConditionalHandle hp;
+            CK(cudaGraphConditionalHandleCreate(&hp, g, 0, cudaGraphCondAssignDefault));
+            launch_prune_cond(S, hp, br[0]);
+            add_cond_prune(br[0], hp);
+        }
+        launch_pairs(S, pruned ? pruned_view() : N, pair_warps, br[0]);
         // with both layouts in planes, the energy branch reads the
         // fixed-point charge grids itself as soon as the spread is done,
         // beside the FP32 plane pass (no FP64 copy); the grids are cleared
@@ -1312,7 +1388,31 @@ struct System final : SystemBase {
         N.cut2 = (float)((P.r_cut + skin) * (P.r_cut + skin));
         N.skin_half2 = (float)(0.25 * skin * skin);
         G.skin_half2 = (real)(0.25 * skin * skin);
+        prune_consts();
         force_rebuild();
+        invalidate_graph();
+        ++generation;
+    }
+
+    // inner buffer b (nm) of the pruned list: pairs within r_cut + b of the
+    // pruning positions, pruned again once an atom has moved b/2; active only
+    // while b is below the list buffer
+    void prune_consts()
+    {
+        const double b = prune_on() ? prune_skin : 0.0;
+        PV.cut2 = (float)((P.r_cut + b) * (P.r_cut + b));
+        G.prune_half2 = (real)(0.25 * b * b);
+    }
+
+    void set_list_prune(double inner) override
+    {
+        if (!std::isfinite(inner) || inner < 0.0) fail(LFE_ERR_ARG, "the inner buffer must be finite and >= 0");
+        CK(cudaDeviceSynchronize());
+        if (exec) recover_overflow(nullptr);
+        prune_skin = inner;
+        prune_consts();
+        const int one = 1;
+        CK(cudaMemcpy(S.flags + FL_PRUNE, &one, sizeof(int), cudaMemcpyHostToDevice));
         invalidate_graph();
         ++generation;
     }
@@ -1861,7 +1961,7 @@ struct System final : SystemBase {
             // on the flag that the new positions raise
             CK(cudaMemcpyAsync(d_in, pos_in, sizeof(TIO) * nv, cudaMemcpyHostToDevice, s0));
             launch_check_positions(S, (const TIO*)d_in, s0);
-            launch_assign_moved(S, (const TIO*)d_in, G.skin_half2, s0);
+            launch_assign_moved(S, (const TIO*)d_in, G.skin_half2, G.prune_half2, s0);
         }
         cudaGraphConditionalHandle h;
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
@@ -1943,7 +2043,7 @@ struct System final : SystemBase {
         CK(cudaGraphLaunch(io_exec, st));
         ++steps_requested;
         CK(cudaStreamSynchronize(st));
-        const int err = (int)h_io_tail[10];
+        const int err = (int)h_io_tail[13];
         if (err & ERRB_BADPOS) {
             // the positions were checked on the device and refused: the step
             // left the state as it was (the outputs hold that state)
@@ -2069,7 +2169,7 @@ struct System final : SystemBase {
             if (pos) CK(cudaMemcpyAsync(pos, d_state, sizeof(double) * nv, cudaMemcpyDeviceToHost, nullptr));
             if (vel) CK(cudaMemcpyAsync(vel, d_state + nv, sizeof(double) * nv, cudaMemcpyDeviceToHost, nullptr));
             CK(cudaStreamSynchronize(nullptr));
-            const int err = (int)h_state[6 * (size_t)n + 10];
+            const int err = (int)h_state[6 * (size_t)n + 13];
             if (!err) break;
             if (pass == 1 || !(err & ERRB_OVERFLOW)) {
                 check_flags(nullptr);   // reports the error (clears the bit)
@@ -2417,7 +2517,8 @@ struct System final : SystemBase {
                                             "pme_fft_inv", "pme_gather", "excl_14", "bonded", "eval_out",
                                             "uv_energy_fp64", "pairs_full"};
         const int ns = 12;
-        std::vector<cudaEvent_t> ev(ns + 2);
+        std::vector<cudaEvent_t> ev(ns + 5);
+        double acc_prune = 0.0, acc_pruned_pairs = 0.0;
         for (auto& e : ev) CK(cudaEventCreate(&e));
         std::vector<double> acc(ns, 0.0);
         CK(cudaMemcpyAsync(lam_save, S.lam, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
@@ -2496,14 +2597,36 @@ struct System final : SystemBase {
                 CK(cudaEventElapsedTime(&tf, ev[12], ev[13]));
                 acc[11] += tf;
             }
+            // with pruning: the pruning of the built list, and the pair kernel
+            // on the pruned list in the step's shape
+            if (prune_on()) {
+                CK(cudaEventRecord(ev[14], st));
+                launch_prune(S, N, pruned_view(), PV, st);
+                CK(cudaEventRecord(ev[15], st));
+                launch_pairs(S, pruned_view(), pair_warps, st);
+                CK(cudaEventRecord(ev[16], st));
+                launch_eval_out(S, nullptr, nullptr, const_vv, const_uu, const_uv, st);
+                CK(cudaEventSynchronize(ev[16]));
+                float a = 0, b = 0;
+                CK(cudaEventElapsedTime(&a, ev[14], ev[15]));
+                CK(cudaEventElapsedTime(&b, ev[15], ev[16]));
+                acc_prune += a;
+                acc_pruned_pairs += b;
+            }
         }
         CK(cudaMemcpyAsync(S.lam, lam_save, sizeof(LamState), cudaMemcpyDeviceToDevice, st));
         for (auto& e : ev) cudaEventDestroy(e);
         check_flags(st);
-        const int m = std::min(std::is_same<real, float>::value ? ns : ns - 1, max_n);
+        std::vector<std::pair<const char*, double>> out;
+        for (int k = 0; k < (std::is_same<real, float>::value ? ns : ns - 1); ++k) out.emplace_back(stage_names[k], acc[k]);
+        if (prune_on()) {
+            out.emplace_back("prune", acc_prune);
+            out.emplace_back("pairs_pruned", acc_pruned_pairs);
+        }
+        const int m = std::min((int)out.size(), max_n);
         for (int k = 0; k < m; ++k) {
-            if (names) names[k] = stage_names[k];
-            if (ms) ms[k] = reps > 0 ? acc[k] / reps : 0.0;
+            if (names) names[k] = out[k].first;
+            if (ms) ms[k] = reps > 0 ? out[k].second / reps : 0.0;
         }
         return m;
     }
@@ -3014,6 +3137,11 @@ int lfe_mc_volume_move(lfe_system* sys, double pressure_bar, double dv_max, unsi
 {
     return guard(sys, [&] { sys->impl->mc_volume_move(pressure_bar, dv_max, seed, attempt, accepted, box_out,
                                                        energies); });
+}
+
+int lfe_set_list_prune(lfe_system* sys, double inner_buffer)
+{
+    return guard(sys, [&] { sys->impl->set_list_prune(inner_buffer); });
 }
 
 int lfe_step_io_f32(lfe_system* sys, const float* pos_in, float* pos_out, float* vel_out, double* ext_out,

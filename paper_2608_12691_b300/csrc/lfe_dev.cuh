@@ -33,9 +33,10 @@ enum {
     E_N = 17
 };
 
-// error / control flags
+// error / control flags (FL_PRUNE: the pruned pair list is due; FL_PTILES:
+// its tile count; FL_NPRUNE: prunings done by steps)
 enum { FL_REBUILD = 0, FL_ERROR = 1, FL_NTILES = 2, FL_NREBUILD = 3, FL_NUV = 4, FL_NSTAGE = 5, FL_NUVT = 6,
-       FL_N = 8 };
+       FL_PRUNE = 7, FL_PTILES = 8, FL_NPRUNE = 9, FL_N = 10 };
 // ERRB_BADPOS: the positions handed to a host-I/O step were not all finite;
 // the step is skipped like one after a list overflow (ERRB_SKIP)
 enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4, ERRB_BADPOS = 8 };
@@ -73,7 +74,8 @@ struct LamState {
     double V_std, V_exp;            // last OPES bias values
     unsigned long long step;
     double v_eta;                   // theta's thermostat velocity (regulated Nose-Hoover-Langevin)
-    double pad[2];
+    double npairs;                  // pairs within r_cut counted by the last step's pair kernel
+    double pad;
 };
 
 // OPES state for the two biases (std = 0, exp = 1).

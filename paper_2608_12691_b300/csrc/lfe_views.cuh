@@ -29,6 +29,7 @@ struct SysView {
     R4<real>* x;
     R4<real>* v;
     R4<real>* xref;     // positions at the last neighbour-list build
+    R4<real>* xpr;      // positions at the last pruning of the pair list
     real* invm;
     const real* q;      // charges (e)
     const real* sig;
@@ -90,6 +91,20 @@ struct NblView {
     int uv_cap;
     int uv_tiles_max;     // capacity of uv_cnt / uv_off
     int n_sm;             // multiprocessors of the device (grid-stride kernels)
+    int ntiles_flag;      // flags slot holding the tile count (FL_NTILES; FL_PTILES for the pruned list)
+};
+
+// Dynamic pruning of the tile list: between rebuilds, a shorter list is cut
+// from the built one, keeping the j entries within r_cut + inner buffer of
+// one of their tile's i atoms at the positions of the pruning; it is pruned
+// again once an atom has moved more than half the inner buffer since.
+struct PruneView {
+    float cut2;           // (r_cut + inner buffer)^2
+    unsigned* kb;         // [cap] per tile of the built list: j entries kept
+    int* base;            // [cap] place of the tile's first kept entry in its sub-cluster's output
+                          // (bit 30: the tile ends a run of one shift and class)
+    int* cnt;             // [4 n_cl_max] pruned tiles per i sub-cluster (zeroed by the scan)
+    int* off;             // [4 n_cl_max + 1] first pruned tile of each i sub-cluster
 };
 
 template <typename real>
@@ -161,6 +176,7 @@ struct StepView {
     real dt, a_fric, kT;       // a = exp(-gamma dt)
     uint2 key;
     real skin_half2;
+    real prune_half2;          // (inner buffer / 2)^2 of the pruned list (0: no pruning)
     real* noise;               // [3 n] Ornstein-Uhlenbeck kicks of the step, formed ahead by k_noise
 };
 
@@ -364,9 +380,15 @@ template <typename real> void launch_eval_out(const SysView<real>& s, double* fo
                                               cudaStream_t st);
 // new positions from caller doubles: master and sorted copies, and the
 // rebuild flag raised when an atom has moved more than skin/2 since the last
-// build (the rebuild itself follows launch_rebuild_cond's conditional node)
+// build (the rebuild itself follows launch_rebuild_cond's conditional node);
+// the pruning flag likewise for half the inner buffer (prune_half2 > 0)
 template <typename real, typename TIO> void launch_assign_moved(const SysView<real>& s, const TIO* pos,
-                                                                real skin_half2, cudaStream_t st);
+                                                                real skin_half2, real prune_half2, cudaStream_t st);
+// the conditional pruning of the step graph: its decision kernel and, for
+// the node's body, the pruning itself (built list nb -> pruned list np)
+template <typename real> void launch_prune_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cudaStream_t st);
+template <typename real> void launch_prune(const SysView<real>& s, const NblView<real>& nb, const NblView<real>& np,
+                                           const PruneView& pv, cudaStream_t st);
 template <typename real, typename TIO> void launch_check_positions(const SysView<real>& s, const TIO* pos,
                                                                    cudaStream_t st);
 template <typename real> void launch_refresh_sorted(const SysView<real>& s, cudaStream_t st);

@@ -263,7 +263,10 @@ __global__ void k_assign(SysView<real> s, NblView<real> nb)
     }
     s.xq[slot] = o;
     s.lj[slot] = l;
-    if (blockIdx.x == 0 && threadIdx.x == 0) s.flags[FL_NSTAGE] = 0;   // the tile staging list starts empty
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s.flags[FL_NSTAGE] = 0;   // the tile staging list starts empty
+        s.flags[FL_PRUNE] = 1;    // a pruned list, where one is used, is cut from the new list
+    }
     // the warp holds one cluster: bounding boxes of the cluster (the partner
     // side of the tile search) and of its four 8-slot sub-clusters (the i
     // side); a sub-cluster without atoms gets a negative half extent
@@ -784,6 +787,169 @@ void launch_build_nbl(const SysView<real>& s, const NblView<real>& nb, cudaStrea
     }
 }
 
+// ---------------------------------------------------- dynamic list pruning
+// Between rebuilds the pair kernel can run on a shorter list cut from the
+// built one (dynamic pruning of a buffered pair list): a j entry is kept when
+// it lies within r_cut + b_in of one of the tile's i atoms whose pair with it
+// is computed, at the positions of the pruning; every pair that comes within
+// r_cut before the next pruning is kept as long as no atom moves more than
+// b_in / 2 meanwhile (the integrator raises FL_PRUNE when one does).  Kept
+// entries keep their order and their mask bytes; each run of tiles of one i
+// sub-cluster, shift and class is packed into as few tiles as its kept
+// entries need.  Three kernels: the keep masks and output places of each
+// sub-cluster's tiles (one warp per sub-cluster), a scan of the sub-clusters'
+// output counts, and the copy (one warp per tile).
+
+// one warp per i sub-cluster, its 8 atoms held by every lane: for each of
+// its built tiles (PRUNE_BATCH at a time, loads first) the kept j entries
+// (bit l = entry l), the place of the tile's first kept entry in the
+// sub-cluster's output (runs of one shift and class start on a whole tile)
+// and whether the tile ends its run; then the output tile count
+constexpr int PRUNE_BATCH = 8;
+
+template <typename real>
+__global__ void __launch_bounds__(128) k_prune_count(SysView<real> s, NblView<real> nb, PruneView pv)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const int I8 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (I8 >= 4 * nb.n_cl_max) return;
+    const int ntot = min(s.flags[FL_NTILES], nb.cap);
+    const int t0 = min(nb.tile_off[I8], ntot), t1 = min(nb.tile_off[I8 + 1], ntot);
+    real ix[8], iy[8], iz[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const R4<real> q = t0 < t1 ? s.xq[I8 * 8 + r] : R4<real>{0, 0, 0, 0};
+        ix[r] = q.x;
+        iy[r] = q.y;
+        iz[r] = q.z;
+    }
+    int pos = 0;     // entries placed (the same value in every lane)
+    int prev = -1;   // run key of the previous tile
+    for (int c = t0; c < t1; c += PRUNE_BATCH) {
+        int4 h[PRUNE_BATCH];
+        int sj[PRUNE_BATCH];
+        unsigned mk[PRUNE_BATCH];
+        R4<real> pj[PRUNE_BATCH];
+#pragma unroll
+        for (int u = 0; u < PRUNE_BATCH; ++u) {
+            const int t = c + u;
+            const bool in = t < t1;
+            h[u] = in ? nb.tiles[t] : make_int4(0, 13, 0, 0);
+            sj[u] = in ? nb.jidx[(size_t)t * 32 + lane] : -1;
+            mk[u] = in ? nb.masks[(size_t)t * 32 + lane] : 0u;
+        }
+        const int4 hn = c + PRUNE_BATCH < t1 ? nb.tiles[c + PRUNE_BATCH] : make_int4(0, -1, 0, 0);
+#pragma unroll
+        for (int u = 0; u < PRUNE_BATCH; ++u) pj[u] = sj[u] >= 0 ? s.xq[sj[u]] : R4<real>{0, 0, 0, 0};
+#pragma unroll
+        for (int u = 0; u < PRUNE_BATCH; ++u) {
+            const int t = c + u;
+            if (t >= t1) break;
+            int sv[3];
+            shift_vec(h[u].y, sv);
+            const real px = pj[u].x + (real)sv[0] * s.L[0];
+            const real py = pj[u].y + (real)sv[1] * s.L[1];
+            const real pz = pj[u].z + (real)sv[2] * s.L[2];
+            real m2 = (real)3.0e38f;
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const real dx = px - ix[r], dy = py - iy[r], dz = pz - iz[r];
+                const real d2 = dx * dx + dy * dy + dz * dz;
+                if ((mk[u] >> r) & 1u) m2 = fmin(m2, d2);
+            }
+            const unsigned kb = __ballot_sync(0xffffffffu, sj[u] >= 0 && mk[u] && m2 < (real)pv.cut2);
+            const int key = h[u].y * 4 + h[u].z;
+            if (key != prev) {
+                pos = (pos + 31) & ~31;
+                prev = key;
+            }
+            const int4 hx = u + 1 < PRUNE_BATCH ? h[u + 1] : hn;
+            const bool close = t + 1 >= t1 || hx.y * 4 + hx.z != key;
+            if (lane == 0) {
+                pv.kb[t] = kb;
+                pv.base[t] = pos | (close ? (1 << 30) : 0);
+            }
+            pos += __popc(kb);
+        }
+    }
+    pos = (pos + 31) & ~31;
+    if (lane == 0) pv.cnt[I8] = pos >> 5;
+}
+
+// one warp per built tile (PRUNE_WBATCH at a time, loads first): its kept
+// entries (and, for a run's last tile, the padding of the run's last output
+// tile) to their places; then the positions of this pruning become the
+// reference of the next decision
+constexpr int PRUNE_WBATCH = 4;
+
+template <typename real>
+__global__ void __launch_bounds__(128) k_prune_write(SysView<real> s, NblView<real> nb, NblView<real> np,
+                                                     PruneView pv)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int ntot = min(s.flags[FL_NTILES], nb.cap);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int t0 = w; t0 < ntot; t0 += PRUNE_WBATCH * nwarps) {
+        int4 h[PRUNE_WBATCH];
+        unsigned kb[PRUNE_WBATCH];
+        int bw[PRUNE_WBATCH], o[PRUNE_WBATCH], sj[PRUNE_WBATCH];
+        unsigned char mk[PRUNE_WBATCH];
+#pragma unroll
+        for (int u = 0; u < PRUNE_WBATCH; ++u) {
+            const int t = t0 + u * nwarps;
+            const bool in = t < ntot;
+            h[u] = in ? nb.tiles[t] : make_int4(0, 0, 0, 0);
+            kb[u] = in ? pv.kb[t] : 0u;
+            bw[u] = in ? pv.base[t] : 0;
+            sj[u] = in ? nb.jidx[(size_t)t * 32 + lane] : -1;
+            mk[u] = in ? nb.masks[(size_t)t * 32 + lane] : (unsigned char)0;
+        }
+#pragma unroll
+        for (int u = 0; u < PRUNE_WBATCH; ++u) o[u] = pv.off[h[u].x];
+#pragma unroll
+        for (int u = 0; u < PRUNE_WBATCH; ++u) {
+            if (t0 + u * nwarps >= ntot) break;
+            const int base = bw[u] & ((1 << 30) - 1);
+            if ((kb[u] >> lane) & 1u) {
+                const int p = base + __popc(kb[u] & lt);
+                const int dt = o[u] + (p >> 5);
+                if (dt < np.cap) {
+                    np.jidx[(size_t)dt * 32 + (p & 31)] = sj[u];
+                    np.masks[(size_t)dt * 32 + (p & 31)] = mk[u];
+                    if ((p & 31) == 0) np.tiles[dt] = make_int4(h[u].x, h[u].y, h[u].z, 0);
+                }
+            }
+            if ((bw[u] >> 30) & 1) {
+                const int pend = base + __popc(kb[u]);
+                const int dt = o[u] + (pend >> 5);
+                if ((pend & 31) != 0 && lane >= (pend & 31) && dt < np.cap) {
+                    np.jidx[(size_t)dt * 32 + lane] = -1;
+                    np.masks[(size_t)dt * 32 + lane] = 0;
+                }
+            }
+        }
+    }
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < s.n; a += gridDim.x * blockDim.x) s.xpr[a] = s.x[a];
+}
+
+template <typename real>
+void launch_prune(const SysView<real>& s, const NblView<real>& nb, const NblView<real>& np, const PruneView& pv,
+                  cudaStream_t st)
+{
+    const int B = 128;
+    const int grid_t = nb.n_sm * 8;
+    launch_k(false, k_prune_count<real>, (4 * nb.n_cl_max * 32 + B - 1) / B, B, 0, st, s, nb, pv);
+    launch_k(true, k_scan_block<0>, 1, 1024, 0, st, pv.cnt, pv.off, 4 * nb.n_cl_max, s.flags + FL_PTILES, np.cap,
+             s.flags + FL_ERROR, (int*)nullptr, (int*)nullptr);
+    launch_k(true, k_prune_write<real>, grid_t, B, 0, st, s, nb, np, pv);
+}
+
 // ------------------------------------------------------------ pair kernel
 template <typename real>
 __device__ __forceinline__ void flush_force(const SysView<real>& s, int slot, long long fx, long long fy,
@@ -1233,7 +1399,7 @@ __device__ __forceinline__ void pairs2_system(const SysView<float>& s, const Nbl
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    const int ntiles = min(s.flags[FL_NTILES], nb.cap);
+    const int ntiles = min(s.flags[nb.ntiles_flag], nb.cap);
     const int nch = (ntiles + PAIR_CHUNK - 1) / PAIR_CHUNK;
     const int c0 = (int)(((long long)nch * warp) / nwarp), c1 = (int)(((long long)nch * (warp + 1)) / nwarp);
     if (c0 >= c1) return;
@@ -1286,7 +1452,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 ? 4 : 3) k_pairs_listed
     const unsigned lt = (1u << lane) - 1u;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    int ntiles = s.flags[FL_NTILES];
+    int ntiles = s.flags[nb.ntiles_flag];
     if (ntiles > nb.cap) ntiles = nb.cap;
     const int t0 = (int)(((long long)ntiles * warp) / nwarp);
     const int t1 = (int)(((long long)ntiles * (warp + 1)) / nwarp);
@@ -1651,6 +1817,8 @@ void launch_excl(const SysView<real>& s, const ExclView<real>& ex, cudaStream_t 
 
 #define LFE_INST(real)                                                                             \
     template void launch_build_nbl<real>(const SysView<real>&, const NblView<real>&, cudaStream_t); \
+    template void launch_prune<real>(const SysView<real>&, const NblView<real>&, const NblView<real>&,  \
+                                     const PruneView&, cudaStream_t);                                    \
     template void launch_pairs<real>(const SysView<real>&, const NblView<real>&, int, cudaStream_t); \
     template int pairs_blocks_per_sm<real>();                                                          \
     template void launch_uv_energy<real>(const SysView<real>&, const NblView<real>&, int, cudaStream_t); \

@@ -24,7 +24,7 @@ LFE_FP64 = 1
 LFE_EXT_LANGEVIN = 0
 LFE_EXT_RNHL = 1
 NTERMS = 10
-NEXT = 10
+NEXT = 13
 TI_BINS = 100
 TERM_NAMES = ["U", "dUdl", "U_vv", "U_uu", "U_uv", "U_soft", "U_bonded", "n_pairs", "hA", "hB"]
 
@@ -34,7 +34,7 @@ EXPORTED = [
     "lfe_param_grad", "lfe_set_solute_params", "lfe_ti", "lfe_set_dafed", "lfe_dafed_state",
     "lfe_set_ext_thermostat", "lfe_ext_thermostat_state",
     "lfe_dafed_masses", "lfe_step", "lfe_get_state", "lfe_checkpoint", "lfe_restore",
-    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_step_io_f32", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step", "lfe_batch_time_pairs", "lfe_batch_set_exchange",
+    "lfe_time_stages", "lfe_autotune", "lfe_alu_peak", "lfe_set_theta", "lfe_set_list_capacity", "lfe_step_io", "lfe_step_io_f32", "lfe_set_list_prune", "lfe_mc_volume_move", "lfe_batch_create", "lfe_batch_eval", "lfe_batch_step", "lfe_batch_time_pairs", "lfe_batch_set_exchange",
     "lfe_batch_exchange_state",
     "lfe_batch_exchange", "lfe_batch_destroy", "lfe_batch_last_error", "lfe_last_error", "lfe_destroy", "lfe_pme_noalloc",
 ]
@@ -145,6 +145,8 @@ def load():
     lib.lfe_step_io.restype = ctypes.c_int
     lib.lfe_step_io_f32.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.lfe_step_io_f32.restype = ctypes.c_int
+    lib.lfe_set_list_prune.argtypes = [vp, ctypes.c_double]
+    lib.lfe_set_list_prune.restype = ctypes.c_int
     lib.lfe_mc_volume_move.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_ulonglong,
                                        vp, vp, vp]
     lib.lfe_mc_volume_move.restype = ctypes.c_int
@@ -349,7 +351,7 @@ class System:
         ext = np.zeros(NEXT)
         self._check(self._lib.lfe_get_state(self.h, pos.ctypes.data, vel.ctypes.data, ext.ctypes.data))
         keys = ["theta", "p_theta", "lambda", "dUdl", "U", "n_kernels_std", "n_kernels_exp", "step",
-                "n_rebuilds", "n_tiles"]
+                "n_rebuilds", "n_tiles", "n_pairs_step", "n_tiles_pruned", "n_prunes"]
         return pos, vel, dict(zip(keys, ext))
 
     def mc_volume_move(self, pressure_bar, dv_max, seed, attempt):
@@ -367,6 +369,11 @@ class System:
         the pointers are page-locked host buffers (0/None for NULL)."""
         self._check(self._lib.lfe_step_io(self.h, pos_in_ptr or None, pos_out_ptr or None, vel_out_ptr or None,
                                           ext_out_ptr or None, _stream_ptr(stream)))
+
+    def set_list_prune(self, inner_buffer):
+        """Dynamic pruning of the neighbour list between rebuilds
+        (lfe_set_list_prune); inner buffer in nm, 0 switches it off."""
+        self._check(self._lib.lfe_set_list_prune(self.h, float(inner_buffer)))
 
     def step_io_f32(self, pos_in_ptr, pos_out_ptr, vel_out_ptr, ext_out_ptr, stream=None):
         """lfe_step_io with float positions and velocities (lfe_step_io_f32);
