@@ -284,9 +284,10 @@ int lfe_step_io(lfe_system* sys, const double* pos_in, double* pos_out, double* 
  * so every pair within r_cut is still evaluated and the results equal those
  * of the full list up to the order of FP32 partial sums.  The list buffer
  * then only sets how often the list is rebuilt.  b = 0 (the default), or b
- * not below the list buffer, switches it off.  lfe_eval, the batched
- * replicas and eager stepping always use the built list.  Recaptures the
- * step graphs.  Errors: LFE_ERR_ARG (b < 0 or not finite). */
+ * not below the list buffer, switches it off.  A system in a batch
+ * (lfe_batch_*) prunes in the batch's steps the same way; lfe_eval and
+ * eager stepping always use the built list.  Recaptures the step graphs.
+ * Errors: LFE_ERR_ARG (b < 0 or not finite). */
 int lfe_set_list_prune(lfe_system* sys, double inner_buffer);
 
 /* lfe_step_io with the positions and velocities as floats: pos_in, pos_out

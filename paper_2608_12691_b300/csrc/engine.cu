@@ -1100,7 +1100,9 @@ struct System final : SystemBase {
         CK(cudaMemcpy(S.v, hv.data(), sizeof(R4<real>) * n, cudaMemcpyHostToDevice));
     }
 
-    void eval_kernels(cudaStream_t st) { record_eval(st, true); }
+    // evaluations outside the step graphs run on the built list (a pruned
+    // list is only cut inside recorded steps)
+    void eval_kernels(cudaStream_t st) { record_eval_on(st, true, N); }
 
     void eval(double lam, double* forces, double* terms, int out_on_device, cudaStream_t st) override
     {
@@ -1791,11 +1793,23 @@ struct System final : SystemBase {
         CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
         launch_rebuild_cond(S, h, s0);
         add_cond_build(s0, h);
+        if (prune_on()) {
+            cudaGraphConditionalHandle hp;
+            CK(cudaGraphConditionalHandleCreate(&hp, g, 0, cudaGraphCondAssignDefault));
+            launch_prune_cond(S, hp, s0);
+            add_cond_prune(s0, hp);
+        }
     }
 
-    void record_eval(cudaStream_t s0, bool with_pairs) override
+    // the pair list of the recorded steps: the pruned one when pruning is on
+    // (record_pre then cuts it when due)
+    NblView<real> step_list() const { return prune_on() ? pruned_view() : N; }
+
+    void record_eval(cudaStream_t s0, bool with_pairs) override { record_eval_on(s0, with_pairs, step_list()); }
+
+    void record_eval_on(cudaStream_t s0, bool with_pairs, const NblView<real>& list)
     {
-        if (with_pairs) launch_pairs(S, N, pair_warps, s0);
+        if (with_pairs) launch_pairs(S, list, pair_warps, s0);
         launch_uv_energy(S, N, uv_blocks, s0);
         launch_pme(S, M, dual ? &M2 : nullptr, s0);
         launch_excl(S, X, s0);
@@ -1831,7 +1845,7 @@ struct System final : SystemBase {
     {
         if constexpr (std::is_same<real, float>::value) {
             out->s = S;
-            out->nb = N;
+            out->nb = step_list();
             return true;
         }
         return false;

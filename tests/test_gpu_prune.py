@@ -113,3 +113,32 @@ def test_buffers_that_cannot_prune_switch_it_off():
     t, _ = g.eval(0.5, forces=False)
     g.step(1)
     assert g.get_state()[2]["n_pairs_step"] == t["n_pairs"]
+
+
+def test_batched_replicas_prune_like_single_systems():
+    # the batch's shared pair launch runs on each replica's pruned list: every
+    # replica ends bit-identical to the same system stepped alone with pruning
+    def replica(seed, nw, side, box, lam, prec):
+        d = S.make_water_box(seed=seed, n_waters=nw, box_len=box, solute="ring12", n_side=side,
+                             r_cut=0.7, grid=16, lam=lam)
+        d.update(dt=0.001, lambda_mass=20.0, lambda_friction=25.0, opes_stride=5,
+                 opes_dE_std=30 * 4.184, opes_dE_exp=5 * 4.184, opes_sigma=0.1)
+        g = lfe.System(d, precision=prec, seed=seed, skin=0.2)
+        g.set_list_prune(0.03)
+        return g
+    specs = [(31, 101, 5, 1.45, 0.2, lfe.LFE_FP32_MIXED), (32, 180, 6, 1.75, 0.55, lfe.LFE_FP32_MIXED),
+             (33, 101, 5, 1.45, 0.9, lfe.LFE_FP64)]
+    batched = [replica(*sp) for sp in specs]
+    alone = [replica(*sp) for sp in specs]
+    b = lfe.Batch(batched)
+    b.step(30)
+    for s in alone:
+        s.step(30)
+    for sb, sa in zip(batched, alone):
+        pb, vb, eb = sb.get_state()
+        pa, va, ea = sa.get_state()
+        assert np.array_equal(pb, pa) and np.array_equal(vb, va)
+        assert eb["theta"] == ea["theta"] and eb["step"] == ea["step"] == 30
+        assert eb["n_prunes"] == ea["n_prunes"] > 1
+        assert 0 < eb["n_tiles_pruned"] < eb["n_tiles"]
+    b.close()
