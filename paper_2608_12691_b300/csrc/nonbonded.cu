@@ -1633,6 +1633,9 @@ __global__ void __launch_bounds__(256) k_uv_energy(SysView<real> s, NblView<real
         }
         euv += e;
     }
+    // a warp without a pair in range (most of a grid spread over every SM)
+    // skips the FP64 reductions
+    if (!__any_sync(0xffffffffu, euv != 0.0 || esoft != 0.0 || edsc != 0.0)) return;
     const long long a0 = __double2ll_rn(warp_sum_d(euv) * ESCALE);
     const long long a1 = __double2ll_rn(warp_sum_d(esoft) * ESCALE);
     const long long a2 = sc ? __double2ll_rn(warp_sum_d(edsc) * ESCALE) : 0ll;
@@ -1712,7 +1715,10 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int a = tid >> 2, sub = tid & 3;
-    double acc[6] = {0, 0, 0, 0, 0, 0};   // excl vv, uu, uv, 14 vv, uu, uv
+    // per-thread energy sums in the working precision (a few terms each),
+    // added over the warp in FP64: the FP64 pipe, which several kernels of
+    // the step share, does only the warp sums
+    real acc[6] = {0, 0, 0, 0, 0, 0};   // excl vv, uu, uv, 14 vv, uu, uv
     real fx = 0, fy = 0, fz = 0;
     if (a < s.n) {
         // master positions, charges sqrt(k_e) q and (sigma / 2, 2 sqrt(eps)),
@@ -1784,7 +1790,7 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
                     const int slotk = (is14 ? 3 : 0) + cls;
 #pragma unroll
                     for (int c = 0; c < 6; ++c)
-                        if (c == slotk) acc[c] += (double)en;   // constant indices: acc stays in registers
+                        if (c == slotk) acc[c] += en;   // constant indices: acc stays in registers
                 }
             }
           }
@@ -1802,7 +1808,7 @@ __global__ void k_excl(SysView<real> s, ExclView<real> ex)
     }
     const int lane = threadIdx.x & 31;
     for (int c = 0; c < 6; ++c) {
-        long long v = __double2ll_rn(warp_sum_d(acc[c]) * ESCALE);
+        long long v = __double2ll_rn(warp_sum_d((double)acc[c]) * ESCALE);
         if (lane == 0 && v) atomic_add_ll(&s.E[(c < 3 ? E_EXCL_VV : E_14_VV) + (c % 3)], v);
     }
 }
