@@ -1268,7 +1268,7 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
     };
     for (int ch = c0; ch < c1; ++ch) {
         const int ta = ch * PAIR_CHUNK, tb = min(ta + PAIR_CHUNK, ntiles);
-        int curI = -1;
+        int curI = -1, curSh = -1;
         for (int t = ta; t < tb; ++t) {
             const int4 tl = nb.tiles[t];
             const unsigned mc = nb.masks[(size_t)t * 32 + lane];
@@ -1278,6 +1278,7 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
             if (tl.x != curI) {
                 if (curI >= 0) flush(curI);
                 curI = tl.x;
+                curSh = -1;
                 if (lane < 8) {
                     const R2<float> l = s.lj[curI * 8 + lane];
                     fC[hk] = l.x;
@@ -1289,15 +1290,20 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
             const int sh3 = tl.y;
             const int sx = sh3 % 3 - 1, sy = (sh3 / 3) % 3 - 1, sz = sh3 / 9 - 1;
             // shift the far-side atom down by L so that the subtraction below is
-            // the only rounding in the pair vector
-            if (lane < 8) {
-                // i atom 8 curI + lane, read again for every tile (an L1 hit)
-                // rather than held in registers across the sub-cluster's tiles
-                const R4<float> pown = s.xq[curI * 8 + lane];
-                fA[hk] = sx == 1 ? pown.x - s.L[0] : pown.x;
-                fA[hk + 2] = sy == 1 ? pown.y - s.L[1] : pown.y;
-                fB[hk] = sz == 1 ? pown.z - s.L[2] : pown.z;
-                fB[hk + 2] = pown.w;
+            // the only rounding in the pair vector; the i record is written
+            // again only when the sub-cluster or the shift changes (tiles come
+            // in runs of one sub-cluster and shift)
+            if (sh3 != curSh) {
+                curSh = sh3;
+                if (lane < 8) {
+                    // i atom 8 curI + lane, read again (an L1 hit) rather than
+                    // held in registers across the sub-cluster's tiles
+                    const R4<float> pown = s.xq[curI * 8 + lane];
+                    fA[hk] = sx == 1 ? pown.x - s.L[0] : pown.x;
+                    fA[hk + 2] = sy == 1 ? pown.y - s.L[1] : pown.y;
+                    fB[hk] = sz == 1 ? pown.z - s.L[2] : pown.z;
+                    fB[hk + 2] = pown.w;
+                }
             }
             if (sx == -1) pj.x -= s.L[0];
             if (sy == -1) pj.y -= s.L[1];
