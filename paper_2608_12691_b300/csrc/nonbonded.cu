@@ -1269,6 +1269,7 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
     for (int ch = c0; ch < c1; ++ch) {
         const int ta = ch * PAIR_CHUNK, tb = min(ta + PAIR_CHUNK, ntiles);
         int curI = -1, curSh = -1;
+        float offx = 0.0f, offy = 0.0f, offz = 0.0f;   // the j side's shift (-L where the code says -1)
         for (int t = ta; t < tb; ++t) {
             const int4 tl = nb.tiles[t];
             const unsigned mc = nb.masks[(size_t)t * 32 + lane];
@@ -1288,13 +1289,16 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
                 for (int m = 0; m < 12; ++m) fi[m][lane] = p2(0.0f);
             }
             const int sh3 = tl.y;
-            const int sx = sh3 % 3 - 1, sy = (sh3 / 3) % 3 - 1, sz = sh3 / 9 - 1;
             // shift the far-side atom down by L so that the subtraction below is
-            // the only rounding in the pair vector; the i record is written
-            // again only when the sub-cluster or the shift changes (tiles come
-            // in runs of one sub-cluster and shift)
+            // the only rounding in the pair vector; the i record and the j
+            // side's offsets change only with the sub-cluster or the shift
+            // (tiles come in runs of one sub-cluster and shift)
             if (sh3 != curSh) {
                 curSh = sh3;
+                const int sx = sh3 % 3 - 1, sy = (sh3 / 3) % 3 - 1, sz = sh3 / 9 - 1;
+                offx = sx == -1 ? -s.L[0] : 0.0f;
+                offy = sy == -1 ? -s.L[1] : 0.0f;
+                offz = sz == -1 ? -s.L[2] : 0.0f;
                 if (lane < 8) {
                     // i atom 8 curI + lane, read again (an L1 hit) rather than
                     // held in registers across the sub-cluster's tiles
@@ -1305,9 +1309,9 @@ __device__ __forceinline__ void pairs2_chunks(const SysView<float>& s, const Nbl
                     fB[hk + 2] = pown.w;
                 }
             }
-            if (sx == -1) pj.x -= s.L[0];
-            if (sy == -1) pj.y -= s.L[1];
-            if (sz == -1) pj.z -= s.L[2];
+            pj.x += offx;
+            pj.y += offy;
+            pj.z += offz;
             __syncwarp();
             const float2 jx = p2(pj.x), jy = p2(pj.y), jz = p2(pj.z);
             float fjx, fjy, fjz, e0;
