@@ -487,6 +487,20 @@ struct System final : SystemBase {
             for (int i = 0; i < n; ++i) mol[i] = find(i);
             N.mol = upload(mol);
             h_mol = mol;
+            // each atom's exclusion partners as a bitmask over its molecule's
+            // atom indices, for molecules within 63 consecutive indices of
+            // their lowest atom (the mask build tests a partner with one bit)
+            std::vector<int> span(n, 0);
+            for (int i = 0; i < n; ++i) span[mol[i]] = std::max(span[mol[i]], i - mol[i]);
+            std::vector<unsigned long long> exm(n, 0ull);
+            for (int i = 0; i < n; ++i) {
+                if (span[mol[i]] > 62) {
+                    exm[i] = 1ull << 63;
+                    continue;
+                }
+                for (int k = cnt[i]; k < cnt[i + 1]; ++k) exm[i] |= 1ull << (lst[k] - mol[i]);
+            }
+            N.exm = upload(exm);
         }
 
         // ---------------------------------------------------- exclusions

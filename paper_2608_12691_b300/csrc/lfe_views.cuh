@@ -83,7 +83,9 @@ struct NblView {
     float skin_half2;     // (skin / 2)^2
     const int* ex_start;  // exclusion CSR, caller order [n + 1]
     const int* ex_list;
-    const int* mol;       // [n] molecule id (connected component of the exclusions)
+    const int* mol;       // [n] molecule id (connected component of the exclusions: its lowest atom)
+    const unsigned long long* exm;   // [n] exclusion partners as bits of (partner - molecule id), bit 63 set:
+                                     // the molecule spans more than 63 atom indices (search the list)
     // dense solute-solvent pair list (pairs within r_cut + skin at build time)
     int* uv_cnt;          // [n_ucl_tiles_max] per-tile counts
     int* uv_off;          // [n_ucl_tiles_max + 1]
@@ -304,11 +306,12 @@ struct PairJob {
     NblView<float> nb;
 };
 // the systems of one batched pair launch, passed by value (kernel parameter
-// space holds up to 32,764 bytes: 60 systems of 520 bytes)
+// space holds up to 32,764 bytes: 60 systems of 536 bytes)
 constexpr int PAIR_BATCH_MAX = 60;
 struct PairJobs {
     PairJob j[PAIR_BATCH_MAX];
 };
+static_assert(sizeof(PairJobs) <= 32764, "the batched pair launch's systems must fit the kernel parameter space");
 // jobs: a host array (captured by value into the launches)
 void launch_pairs_batch(const PairJob* jobs, int njobs, int nblocks, cudaStream_t st);
 int pairs_batch_blocks();   // one resident wave of the launch over many systems

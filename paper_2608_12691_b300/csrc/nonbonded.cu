@@ -577,8 +577,10 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_tiles(SysView<real> s, NblV
 // atom) and transposed by shuffles.  A warp takes four staged tiles at a
 // time (lane = 8 tile + row), grid-striding over the staging list.
 // Exclusions are searched only for rows whose molecule appears among the j
-// atoms: each excluded partner's slot is looked up in the tile's ascending j
-// slots by bisection.
+// atoms: for a molecule within 63 consecutive atom indices, each such j
+// entry is tested against the row atom's exclusion bitmask (one bit per
+// molecule-local index); otherwise each excluded partner's slot is looked up
+// in the tile's ascending j slots by bisection.
 constexpr int PLACE_BLOCKS_PER_SM = 16;
 constexpr int PLACE_EX_BATCH = 8;     // exclusions looked up per batch of loads
 
@@ -588,6 +590,7 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
     pdl_wait();
     pdl_trigger();
     __shared__ int jsl[4][4][33];   // [warp][tile][k]: j slot (INT_MAX if empty)
+    __shared__ unsigned char jloc[4][4][32];   // [warp][tile][k]: j atom - its molecule id (255: none or > 62)
     const int lane = threadIdx.x & 31, wl = (threadIdx.x >> 5) & 3;
     const int g = lane >> 3, r = lane & 7;
     const int nst = min(s.flags[FL_NSTAGE], nb.stage_cap);
@@ -623,6 +626,7 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             jsl[wl][u][lane] = js[u] >= 0 ? js[u] : 0x7fffffff;
+            jloc[wl][u][lane] = (b[u] >= 0 && b[u] - jm[u] <= 62) ? (unsigned char)(b[u] - jm[u]) : (unsigned char)255;
             const unsigned bal = __ballot_sync(0xffffffffu, b[u] >= 0);
             if (dest[u] >= 0) {
                 nb.jidx[(size_t)dest[u] * 32 + lane] = js[u];
@@ -652,7 +656,16 @@ __global__ void __launch_bounds__(128) k_place(SysView<real> s, NblView<real> nb
         if (mydest >= 0) {
             const int* sl = jsl[wl][g];
             if (a >= 0) m = valid & ~before;
-            if (m & same) {
+            const unsigned long long xm = (m & same) ? nb.exm[a] : 0ull;
+            if ((m & same) && !(xm >> 63)) {
+                // the row's molecule within 63 indices: entry k of the same
+                // molecule is excluded when its bit in the row atom's mask is set
+                for (unsigned t = m & same; t; t &= t - 1u) {
+                    const int k = __ffs(t) - 1;
+                    const int bl = jloc[wl][g][k];
+                    if (bl < 63 && ((xm >> bl) & 1ull)) m &= ~(1u << k);
+                }
+            } else if (m & same) {
                 // excluded partners' slots, PLACE_EX_BATCH loads in flight
                 const int e0 = nb.ex_start[a], e1 = nb.ex_start[a + 1];
                 for (int eb = e0; eb < e1; eb += PLACE_EX_BATCH) {
