@@ -1145,29 +1145,13 @@ struct System final : SystemBase {
     // whose body rebuilds the neighbour list; st continues after it.
     void add_cond_build(cudaStream_t st, cudaGraphConditionalHandle h)
     {
-        cudaStreamCaptureStatus status;
-        cudaGraph_t g = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t ndeps = 0;
-        CK(cudaStreamGetCaptureInfo(st, &status, nullptr, &g, &deps, nullptr, &ndeps));
-        cudaGraphNodeParams cp{};
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
-        cp.conditional.size = 1;
-        cudaGraphNode_t node;
-        CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_build_nbl(S, N, cs2);
-        cudaGraph_t body_out = nullptr;
-        CK(cudaStreamEndCapture(cs2, &body_out));
+        add_cond_node(st, h, [&](cudaStream_t c) { launch_build_nbl(S, N, c); });
     }
 
-    // Appends to the graph being captured on st a conditional node (handle h)
-    // whose body cuts the pruned list from the built one; st continues after it.
-    void add_cond_prune(cudaStream_t st, cudaGraphConditionalHandle h)
+    // a conditional node (handle h) whose body `body` records on the stream it
+    // is given; st continues after it
+    template <class Body>
+    void add_cond_node(cudaStream_t st, cudaGraphConditionalHandle h, Body body)
     {
         cudaStreamCaptureStatus status;
         cudaGraph_t g = nullptr;
@@ -1181,12 +1165,19 @@ struct System final : SystemBase {
         cp.conditional.size = 1;
         cudaGraphNode_t node;
         CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
         CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
-        CK(cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-        launch_prune(S, N, pruned_view(), PV, cs2);
+        CK(cudaStreamBeginCaptureToGraph(cs2, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        body(cs2);
         cudaGraph_t body_out = nullptr;
         CK(cudaStreamEndCapture(cs2, &body_out));
+    }
+
+    // Appends to the graph being captured on st a conditional node (handle h)
+    // whose body cuts the pruned list from the built one; st continues after it.
+    void add_cond_prune(cudaStream_t st, cudaGraphConditionalHandle h)
+    {
+        add_cond_node(st, h, [&](cudaStream_t c) { launch_prune(S, N, pruned_view(), PV, c); });
     }
 
     // The evaluation as five concurrent branches (used inside the captured
@@ -1913,7 +1904,10 @@ struct System final : SystemBase {
         CK(cudaStreamWaitEvent(br[3], ev_uv, 0));
         launch_integrate(S, G, br[3]);
         if (D.n) {
+            // after its forces (branch 3) and after the rebuild (branch 0),
+            // whose list overflow skips the step's state updates
             CK(cudaStreamWaitEvent(br[1], ev_join[3], 0));
+            CK(cudaStreamWaitEvent(br[1], ev_join[0], 0));
             launch_dafed_step(S, D, br[1]);
         }
         CK(cudaEventRecord(ev_join[1], br[1]));
