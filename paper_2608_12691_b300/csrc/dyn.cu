@@ -768,6 +768,7 @@ __device__ __forceinline__ void integrate_group(const SysView<real>& s, const St
 template <typename real>
 __global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real> g)
 {
+    pdl_wait();   // launched as a programmatic dependent in the step graph: every input complete from here
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (gi >= g.n_groups) return;
     const Group G = g.groups[gi];
@@ -793,9 +794,9 @@ __global__ void __launch_bounds__(64) k_integrate(SysView<real> s, StepView<real
 }
 
 template <typename real>
-void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st)
+void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st, bool pdl)
 {
-    k_integrate<real><<<(g.n_groups + 63) / 64, 64, 0, st>>>(s, g);
+    launch_k(pdl, k_integrate<real>, (g.n_groups + 63) / 64, 64, 0, st, s, g);
 }
 
 // Ornstein-Uhlenbeck kick of every atom for the current step:
@@ -966,6 +967,8 @@ __device__ __forceinline__ void theta_step_body(const SysView<real>& s, const Th
 template <typename real>
 __global__ void k_theta_step(SysView<real> s, ThetaView<real> t)
 {
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0) theta_step_body(s, t);
 }
 
@@ -1034,6 +1037,7 @@ __device__ __forceinline__ void theta_commit_body(const SysView<real>& s, const 
 template <typename real>
 __global__ void k_theta_commit(SysView<real> s, ThetaView<real> t)
 {
+    pdl_wait();
     theta_commit_body(s, t);
 }
 
@@ -1145,15 +1149,15 @@ void launch_prune_cond(const SysView<real>& s, cudaGraphConditionalHandle h, cud
 }
 
 template <typename real>
-void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
+void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st, bool pdl)
 {
-    k_theta_step<real><<<1, 32, 0, st>>>(s, t);
+    launch_k(pdl, k_theta_step<real>, 1, 32, 0, st, s, t);
 }
 
 template <typename real>
-void launch_theta_commit(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st)
+void launch_theta_commit(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st, bool pdl)
 {
-    k_theta_commit<real><<<1, 32, 0, st>>>(s, t);
+    launch_k(pdl, k_theta_commit<real>, 1, 32, 0, st, s, t);
 }
 
 template <typename real>
@@ -1180,10 +1184,10 @@ void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t
     template void launch_scale_molecules<real>(const SysView<real>&, const int*, const int*, const double*, int, \
                                                double, const double*, cudaStream_t);                         \
     template void launch_bonded<real>(const SysView<real>&, const BondView<real>&, cudaStream_t);          \
-    template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t);       \
+    template void launch_integrate<real>(const SysView<real>&, const StepView<real>&, cudaStream_t, bool); \
     template void launch_theta<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);         \
-    template void launch_theta_step<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);    \
-    template void launch_theta_commit<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t);  \
+    template void launch_theta_step<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t, bool); \
+    template void launch_theta_commit<real>(const SysView<real>&, const ThetaView<real>&, cudaStream_t, bool); \
     template void launch_prestep<real>(const SysView<real>&, const StepView<real>&, const ThetaView<real>&,  \
                                        cudaStream_t);                                                       \
     template void launch_dafed_force<real>(const SysView<real>&, const DafedView&, cudaStream_t);            \

@@ -1281,11 +1281,13 @@ struct System final : SystemBase {
         if (theta_early) {
             // theta's step needs dU/dlambda only: the solute-solvent, the
             // exclusion and 1-4 and the reciprocal class energies; it runs as
-            // soon as they are in (the step's end commits it)
-            CK(cudaEventRecord(ev_rec, dual ? br[2] : br[1]));
-            CK(cudaStreamWaitEvent(br[4], ev_ex, 0));
-            CK(cudaStreamWaitEvent(br[4], ev_rec, 0));
-            launch_theta_step(S, *pre, br[4]);
+            // soon as they are in (the step's end commits it), on the branch
+            // of the reciprocal energies as a programmatic dependent of their
+            // last kernel
+            cudaStream_t tb = theta_branch();
+            CK(cudaStreamWaitEvent(tb, ev_ex, 0));
+            CK(cudaStreamWaitEvent(tb, ev_uv, 0));
+            launch_theta_step(S, *pre, tb, true);
         }
         for (int k = 0; k < NBR; ++k) {
             CK(cudaEventRecord(ev_join[k], br[k]));
@@ -1874,44 +1876,47 @@ struct System final : SystemBase {
         recover_overflow(st);
     }
 
+    // theta's branch: the reciprocal energies' (the df64 branch 2 of FP32
+    // systems, the PME branch 1 of FP64 systems)
+    cudaStream_t theta_branch() const { return dual ? br[2] : br[1]; }
+
     // the end of a captured step, continuing the open branches of
     // eval_kernels_branched (theta's view given; under the regulated
-    // thermostat theta's step has been taken on branch 4):
+    // thermostat theta's step has been taken on theta's branch):
     //  - the atoms' integrator on branch 3 once the forces are complete
     //    (pairs on branch 0, reciprocal gather on 1, exclusions, bonded and
     //    d-AFED forces on 3) and the last other reader of the positions (the
-    //    solute-solvent energies on 4) is done; it does not wait for the
-    //    df64 energy branch or theta's step;
-    //  - theta's commit (or its whole step) on branch 4 once every reader of
-    //    the lambda state in branches 0-3 is done (it does not wait for the
-    //    integrator, which reads no lambda state);
+    //    solute-solvent energies on 4) is done;
+    //  - theta's commit (or its whole step) on theta's branch once every
+    //    reader of the lambda state is done;
     //  - the auxiliary angles' step on branch 1 once their forces (branch 3)
-    //    are in.
-    // The step ends when all three are done.
+    //    and the pair branch (whose rebuild can raise a list overflow, which
+    //    skips the step's state updates) are in.
+    // The integrator and the commit are programmatic dependents of the pair
+    // kernel and of theta's step (both let their dependents be scheduled
+    // early): they are in place when their last prerequisite ends.
     void record_ext_steps(cudaStream_t s0)
     {
-        CK(cudaStreamWaitEvent(br[4], ev_join[0], 0));
-        CK(cudaStreamWaitEvent(br[4], ev_join[1], 0));
-        CK(cudaStreamWaitEvent(br[4], ev_join[2], 0));
-        CK(cudaStreamWaitEvent(br[4], ev_join[3], 0));
-        if (T.th.kind == 1) launch_theta_commit(S, T, br[4]);
-        else launch_theta(S, T, br[4]);
-        CK(cudaEventRecord(ev_join[4], br[4]));
-        // (the waits below read the branch ends recorded by the evaluation:
-        // each ev_join is recorded again only after its last reader)
+        const bool early = T.th.kind == 1;
+        cudaStream_t tb = early ? theta_branch() : br[4];
+        // the waits below read the branch ends recorded by the evaluation
+        for (int k = 0; k < NBR; ++k)
+            if (br[k] != tb) CK(cudaStreamWaitEvent(tb, ev_join[k], 0));
+        if (early) launch_theta_commit(S, T, tb, true);
+        else launch_theta(S, T, tb);
+        CK(cudaEventRecord(ev_rec, tb));
         CK(cudaStreamWaitEvent(br[3], ev_join[0], 0));
         CK(cudaStreamWaitEvent(br[3], ev_join[1], 0));
         CK(cudaStreamWaitEvent(br[3], ev_uv, 0));
-        launch_integrate(S, G, br[3]);
+        launch_integrate(S, G, br[3], true);
         if (D.n) {
-            // after its forces (branch 3) and after the rebuild (branch 0),
-            // whose list overflow skips the step's state updates
             CK(cudaStreamWaitEvent(br[1], ev_join[3], 0));
             CK(cudaStreamWaitEvent(br[1], ev_join[0], 0));
             launch_dafed_step(S, D, br[1]);
         }
         CK(cudaEventRecord(ev_join[1], br[1]));
         CK(cudaEventRecord(ev_join[3], br[3]));
+        CK(cudaStreamWaitEvent(s0, ev_rec, 0));
         for (int k = 0; k < NBR; ++k) CK(cudaStreamWaitEvent(s0, ev_join[k], 0));
     }
 

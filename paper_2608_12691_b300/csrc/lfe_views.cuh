@@ -354,15 +354,19 @@ template <typename real> size_t columns_smem(const PmeView<real>& p);
 template <typename real> void planes_setup(const PmeView<real>& p);
 template <typename real> void energy_columns_setup(const PmeView<real>& p);
 template <typename real> void launch_bonded(const SysView<real>& s, const BondView<real>& b, cudaStream_t st);
-template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st);
+// pdl: launched as a programmatic dependent of the kernel before it in the
+// stream (the kernels wait for their prerequisites before reading anything)
+template <typename real> void launch_integrate(const SysView<real>& s, const StepView<real>& g, cudaStream_t st,
+                                               bool pdl = false);
 // theta's step: k_theta_step (dU/dlambda and the new theta, momentum and
 // thermostat velocity, kept in ThetaPre) then k_theta_commit (U, the TI bin,
 // the lambda state, OPES deposits, the step counter, clearing the energy
 // accumulators); launch_theta runs both as one launch
 template <typename real> void launch_theta(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
-template <typename real> void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st);
+template <typename real> void launch_theta_step(const SysView<real>& s, const ThetaView<real>& t, cudaStream_t st,
+                                                bool pdl = false);
 template <typename real> void launch_theta_commit(const SysView<real>& s, const ThetaView<real>& t,
-                                                  cudaStream_t st);
+                                                  cudaStream_t st, bool pdl = false);
 // d-AFED: forces of Eq. 15 on the atoms and the auxiliary variables (with
 // the coupling energy), and the auxiliary variables' step
 template <typename real> void launch_dafed_force(const SysView<real>& s, const DafedView& d, cudaStream_t st);

@@ -1439,6 +1439,9 @@ __device__ __forceinline__ void pairs2_system(const SysView<float>& s, const Nbl
 // bit for bit.
 __global__ void __launch_bounds__(128, PAIR2_MIN_BLOCKS) k_pairs2(const __grid_constant__ PairJobs P)
 {
+    // the step's end kernels, programmatic dependents, may be scheduled from
+    // here on; each waits for this grid to complete before it reads anything
+    pdl_trigger();
     __shared__ Pair2Shared sh;
     pairs2_system(P.j[blockIdx.y].s, P.j[blockIdx.y].nb, sh);
 }

@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(PLANE_THREADS) k_plane(PmeView<real> p)
 template <typename real, int MODE>
 __global__ void __launch_bounds__(COL_THREADS) k_columns(PmeView<real> p, long long* E, const LamState* lam)
 {
+    pdl_trigger();   // (theta's step, a programmatic dependent in the step graph, waits for completion)
     extern __shared__ unsigned char smem_raw[];
     __shared__ double red[3][COL_THREADS / 32];
     const int K0 = p.K[0], K1 = p.K[1], K2 = p.K[2];
