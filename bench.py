@@ -34,7 +34,7 @@ METRIC = "ns/day & pair-interactions/s (mixed vs FP64, batched vs per-replica) o
 FLOPS_PER_PAIR = 58
 # From one ncu capture of the current k_pairs2 on the octanol profile case
 # (31,949 tiles of the 0.10 nm-buffer list): DRAM bytes (dram__bytes_read.sum
-# 6,353,664 + dram__bytes_write.sum 0) and counted FP32 operations (2 FFMA +
+# 6,353,920 + dram__bytes_write.sum 0) and counted FP32 operations (2 FFMA +
 # 4 FFMA2 + FADD + 2 FADD2 + FMUL + 2 FMUL2, predicated-on thread
 # instructions: 6.340e8; every lane of an executed step counts, the lanes
 # whose pairs are out of range computing zeros), both per tile, for scaling
@@ -42,7 +42,7 @@ FLOPS_PER_PAIR = 58
 # traffic, and every tile runs the same instruction stream); None whenever
 # the kernel has changed since the capture
 PAIR_CAPTURE_TILES = 31949
-PAIR_DRAM_BYTES_PER_TILE = 6353664.0 / PAIR_CAPTURE_TILES
+PAIR_DRAM_BYTES_PER_TILE = 6353920.0 / PAIR_CAPTURE_TILES
 PAIR_COUNTED_FLOPS_PER_TILE = 6.340e8 / PAIR_CAPTURE_TILES
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2032.0
