@@ -85,8 +85,30 @@ def solute_only():
     return d
 
 
+def far_exclusion():
+    # the ragged water box with two extra exclusions, each between the oxygens
+    # of two nearby waters far apart in index: the exclusion graph then joins
+    # them into molecules spanning more than 63 atom indices, whose masks the
+    # list placement builds by searching the exclusion lists (the bitmask path
+    # covers the other molecules)
+    d = small_ragged()
+    pos, box = np.asarray(d["pos"]), np.asarray(d["box"])
+    wat = np.asarray(d["waters"])
+    ox = wat[:, 0]
+    extra = []
+    for w0 in (0, 1):
+        dd = pos[ox] - pos[ox[w0]]
+        dd -= box * np.round(dd / box)
+        r = np.sqrt((dd * dd).sum(axis=1))
+        far = [w for w in np.argsort(r) if abs(int(ox[w]) - int(ox[w0])) > 70 and 0.0 < r[w] < 0.5]
+        extra.append((int(ox[w0]), int(ox[far[0]])))
+    d["excl"] = np.concatenate([np.asarray(d["excl"]), np.asarray(extra, dtype=np.int32)]).astype(np.int32)
+    return d
+
+
 SYSTEMS = {
     "c0": S.make_c0,
+    "far_excl": far_exclusion,
     "ragged": small_ragged,
     "odd_grid": odd_grid,
     "big_grid": big_grid,
@@ -152,7 +174,7 @@ LAMS = [0.0, 0.2, 0.35, 0.6, 1.0]
 
 
 @pytest.mark.parametrize("precision", [lfe.LFE_FP64, lfe.LFE_FP32_MIXED])
-@pytest.mark.parametrize("key", ["c0", "ragged", "nosolute", "soluteonly"])
+@pytest.mark.parametrize("key", ["c0", "ragged", "nosolute", "soluteonly", "far_excl"])
 def test_small_parity(key, precision):
     d = SYSTEMS[key]()
     for lam in LAMS + [d["lam"]]:
