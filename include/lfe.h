@@ -418,7 +418,7 @@ int lfe_set_list_capacity(lfe_system* sys, int tiles);
  * concurrent branches of the step, timed with and without a preceding list
  * rebuild, weighted 1:3).  Knobs: blocks of the pair kernel per multiprocessor (1 up to
  * the resident maximum), blocks of the FP64 solute-solvent energy kernel
- * (0.5 to 8 per multiprocessor) and lines per block of the df64 transform
+ * (0.5 to 4 per multiprocessor) and lines per block of the df64 transform
  * passes (4 or 16) and, when lfe_params.skin <= 0 and the objective is the
  * stepped one, the neighbour-list buffer (0.10, 0.14, 0.18, 0.22 or 0.26 nm,
  * each with every pair-kernel block count: a wider buffer means fewer
