@@ -1239,7 +1239,9 @@ __device__ __forceinline__ float2 pair_force2(float2 r2, float2 qq, float2 sg, f
 // scalar kernel 45.8 us.
 // resident blocks the register budget is cut for: 8 (64 registers) runs the
 // kernel in 43 us against 52 us at 6 (80 registers) and 54 us at 7 (72) on
-// the octanol box
+// the octanol box; inside the step, with the grid at 4 blocks per SM, budgets
+// of 79, 91 and 107 registers gave 114.8-115.6, 122.1-122.6 and 125.1-125.5
+// us per step against 115.2-117.4 at 64
 constexpr int PAIR2_MIN_BLOCKS = 8;
 constexpr int PAIR_CHUNK = 8;
 
