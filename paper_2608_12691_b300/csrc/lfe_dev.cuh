@@ -34,9 +34,10 @@ enum {
 };
 
 // error / control flags (FL_PRUNE: the pruned pair list is due; FL_PTILES:
-// its tile count; FL_NPRUNE: prunings done by steps)
+// its tile count; FL_NPRUNE: prunings done by steps; FL_PCHUNK, FL_PDONE: the
+// FP32 pair kernel's next chunk and finished warps, zero between launches)
 enum { FL_REBUILD = 0, FL_ERROR = 1, FL_NTILES = 2, FL_NREBUILD = 3, FL_NUV = 4, FL_NSTAGE = 5, FL_NUVT = 6,
-       FL_PRUNE = 7, FL_PTILES = 8, FL_NPRUNE = 9, FL_N = 10 };
+       FL_PRUNE = 7, FL_PTILES = 8, FL_NPRUNE = 9, FL_PCHUNK = 10, FL_PDONE = 11, FL_N = 12 };
 // ERRB_BADPOS: the positions handed to a host-I/O step were not all finite;
 // the step is skipped like one after a list overflow (ERRB_SKIP)
 enum { ERRB_OVERFLOW = 1, ERRB_NONFINITE = 2, ERRB_CONSTRAINT = 4, ERRB_BADPOS = 8 };

@@ -1419,18 +1419,36 @@ __device__ __forceinline__ void pairs2_store(const SysView<float>& s, Pair2Acc& 
     acc = Pair2Acc{};
 }
 
-// one system's chunks shared out evenly over the warps of the blocks along x
+// One system's chunks, handed out in order from the system's chunk counter
+// to the warps of the blocks along x as they become free, so that warps that
+// drew light chunks take more and the grid ends together.  A chunk's result
+// does not depend on the warp that evaluates it (its FP32 sums are formed
+// within the chunk, then added as fixed point), so the outcome is the same
+// for any assignment.  The last warp to finish sets both counters back to
+// zero for the next launch: every warp fences its last counter update before
+// it counts itself finished.
 __device__ __forceinline__ void pairs2_system(const SysView<float>& s, const NblView<float>& nb, Pair2Shared& sh)
 {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
     const int ntiles = min(s.flags[nb.ntiles_flag], nb.cap);
     const int nch = (ntiles + PAIR_CHUNK - 1) / PAIR_CHUNK;
-    const int c0 = (int)(((long long)nch * warp) / nwarp), c1 = (int)(((long long)nch * (warp + 1)) / nwarp);
-    if (c0 >= c1) return;
     Pair2Acc acc;
-    pairs2_chunks(s, nb, ntiles, c0, c1, sh, acc);
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(&s.flags[FL_PCHUNK], 1);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+        if (ch >= nch) break;
+        pairs2_chunks(s, nb, ntiles, ch, ch + 1, sh, acc);
+    }
     pairs2_store(s, acc);
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(&s.flags[FL_PDONE], 1) == nwarp - 1) {
+            atomicExch(&s.flags[FL_PCHUNK], 0);
+            atomicExch(&s.flags[FL_PDONE], 0);
+        }
+    }
 }
 
 // One launch for one or many systems: blockIdx.y picks the system, whose
