@@ -42,7 +42,7 @@ FLOPS_PER_PAIR = 58
 # traffic, and every tile runs the same instruction stream); None whenever
 # the kernel has changed since the capture
 PAIR_CAPTURE_TILES = 31949
-PAIR_DRAM_BYTES_PER_TILE = 6353920.0 / PAIR_CAPTURE_TILES
+PAIR_DRAM_BYTES_PER_TILE = 6347520.0 / PAIR_CAPTURE_TILES
 PAIR_COUNTED_FLOPS_PER_TILE = 6.340e8 / PAIR_CAPTURE_TILES
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2032.0
